@@ -1,0 +1,250 @@
+"""Seeded synthetic inputs for CP-ARLS-LEV.
+
+This module only makes inputs: sparse count tensors in coordinate (COO) form and
+Gaussian initial factor matrices.  It holds none of the method's arithmetic and is
+shared by the CUDA path's tests, the oracle's tests and the benchmark, so both sides
+of every comparison see byte-identical inputs.
+
+The real tensors of the paper (Uber, Amazon, Reddit from FROSTT, Table 6.1) are not
+available; these generators stand in for them with the same shapes, nonzero counts
+and the kind of value distribution the paper describes in Section 6 (counts, or
+log(1 + count) for the Reddit-like tensor).  The planted-model recipe:
+
+* component weights lambda_j ~ U[1, 2];
+* factor column j of mode m is a popularity profile times a random perturbation:
+  either a Dirichlet(0.1) vector (the small 60x50x40 tensor), or a Zipf(alpha)
+  popularity curve (i+1)^-alpha placed under a per-component random permutation
+  and multiplied by Gamma(1) noise (the large tensors);
+* each event picks a component with probability proportional to lambda, then one
+  index per mode from that component's columns; repeated coordinates add up to
+  counts.  The number of events is raised until the nonzero count reaches the
+  target (within 2 %).
+
+All randomness comes from numpy's Philox bit generator seeded explicitly.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+__all__ = [
+    "Coo",
+    "gaussian_factors",
+    "planted_cp_tensor",
+    "random_sparse_tensor",
+    "small_planted_tensor",
+    "uber_like_tensor",
+    "exact_lowrank_tensor",
+    "CONFIG_SMALL",
+    "CONFIG_UBER",
+]
+
+
+@dataclass
+class Coo:
+    """A sparse tensor in coordinate format: ``idx[m][e]`` is the 0-based index of
+    nonzero ``e`` in mode ``m`` (int32) and ``vals[e]`` its value."""
+
+    dims: tuple
+    idx: list
+    vals: np.ndarray
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def order(self) -> int:
+        return len(self.dims)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.vals.shape[0])
+
+    def as_dtype(self, dtype) -> "Coo":
+        return Coo(self.dims, self.idx, self.vals.astype(dtype), dict(self.meta))
+
+    def dense(self) -> np.ndarray:
+        """Dense copy (small tensors only)."""
+        X = np.zeros(self.dims, dtype=np.float64)
+        X[tuple(np.asarray(i, dtype=np.int64) for i in self.idx)] = self.vals
+        return X
+
+
+def _rng(seed: int, stream: int = 0) -> np.random.Generator:
+    return np.random.Generator(np.random.Philox(key=[int(seed) & (2**64 - 1), int(stream)]))
+
+
+def gaussian_factors(dims, rank: int, seed: int = 0) -> list:
+    """Initial factor matrices with standard Gaussian entries (Section 6: factor
+    matrices are initialised from a standard normal distribution).  Row-major
+    n_k x rank float64 arrays."""
+    g = _rng(seed, 101)
+    return [np.ascontiguousarray(g.standard_normal((int(n), rank))) for n in dims]
+
+
+def _linear(idx_cols, dims) -> np.ndarray:
+    lin = np.zeros(idx_cols[0].shape[0], dtype=np.uint64)
+    stride = 1
+    for col, n in zip(idx_cols, dims):
+        lin += col.astype(np.uint64) * np.uint64(stride)
+        stride *= int(n)
+    return lin
+
+
+def _unlinear(lin, dims) -> list:
+    out = []
+    rest = lin.copy()
+    for n in dims:
+        out.append((rest % np.uint64(n)).astype(np.int32))
+        rest //= np.uint64(n)
+    return out
+
+
+def _columns(g, dims, rank, zipf_alpha, dirichlet):
+    cols = []
+    for n in dims:
+        n = int(n)
+        if zipf_alpha is None:
+            C = g.dirichlet(np.full(n, dirichlet), size=rank).T  # n x rank
+        else:
+            base = (np.arange(n, dtype=np.float64) + 1.0) ** (-float(zipf_alpha))
+            C = np.empty((n, rank))
+            for j in range(rank):
+                perm = g.permutation(n)
+                C[:, j] = base[perm] * g.gamma(1.0, size=n)
+            C /= C.sum(axis=0, keepdims=True)
+        cols.append(np.ascontiguousarray(C))
+    return cols
+
+
+def _draw_events(g, cols, lam, events):
+    rank = lam.shape[0]
+    comp_counts = g.multinomial(events, lam / lam.sum())
+    idx_cols = [np.empty(events, dtype=np.int64) for _ in cols]
+    pos = 0
+    for j in range(rank):
+        c = int(comp_counts[j])
+        if c == 0:
+            continue
+        for m, C in enumerate(cols):
+            cdf = np.cumsum(C[:, j])
+            cdf /= cdf[-1]
+            u = g.random(c)
+            idx_cols[m][pos:pos + c] = np.minimum(np.searchsorted(cdf, u, side="right"), C.shape[0] - 1)
+        pos += c
+    return idx_cols
+
+
+def planted_cp_tensor(dims, rank, *, events=None, target_nnz=None, seed=0, zipf_alpha=None,
+                      dirichlet=0.1, log_counts=False, max_rounds=12) -> Coo:
+    """Count tensor drawn from a planted nonnegative CP model (see module doc).
+
+    Give either a fixed ``events`` count, or ``target_nnz``: then the event count is
+    searched (geometric then bisection on a fixed seed) until the number of distinct
+    coordinates is within 2 % of the target.
+    """
+    dims = tuple(int(n) for n in dims)
+    g0 = _rng(seed, 7)
+    lam = g0.uniform(1.0, 2.0, size=rank)
+    cols = _columns(g0, dims, rank, zipf_alpha, dirichlet)
+
+    def realise(ev):
+        g = _rng(seed, 11)
+        idx_cols = _draw_events(g, cols, lam, int(ev))
+        lin = _linear(idx_cols, dims)
+        uniq, counts = np.unique(lin, return_counts=True)
+        return uniq, counts
+
+    if events is not None:
+        uniq, counts = realise(events)
+        ev_used = int(events)
+    else:
+        target = int(target_nnz)
+        lo, hi = None, None
+        ev = target
+        uniq, counts = realise(ev)
+        for _ in range(max_rounds):
+            nz = uniq.shape[0]
+            if abs(nz - target) <= 0.02 * target:
+                break
+            if nz < target:
+                lo = ev
+                ev = ev * 2 if hi is None else (lo + hi) // 2
+            else:
+                hi = ev
+                ev = (lo + hi) // 2 if lo is not None else max(1, ev // 2)
+            uniq, counts = realise(ev)
+        ev_used = ev
+    idx = _unlinear(uniq, dims)
+    vals = counts.astype(np.float64)
+    if log_counts:
+        vals = np.log1p(vals)
+    return Coo(dims, idx, vals, {"events": ev_used, "rank": rank, "seed": seed,
+                                 "zipf_alpha": zipf_alpha, "lambda": lam})
+
+
+def small_planted_tensor(seed: int = 0) -> Coo:
+    """60 x 50 x 40 count tensor from 20,000 Poisson-process events of a planted
+    rank-4 nonnegative CP model with Dirichlet(0.1) factor columns."""
+    return planted_cp_tensor((60, 50, 40), 4, events=20000, seed=seed, dirichlet=0.1)
+
+
+def uber_like_tensor(seed: int = 0, target_nnz: int = 3_309_490) -> Coo:
+    """183 x 24 x 1140 x 1717 count tensor with about 3.31M nonzeros (the shape and
+    nonzero count of the Uber tensor, Table 6.1), planted rank 25, Zipf(1.1)
+    popularity."""
+    return planted_cp_tensor((183, 24, 1140, 1717), 25, target_nnz=target_nnz, seed=seed,
+                             zipf_alpha=1.1)
+
+
+def random_sparse_tensor(dims, nnz, seed=0, dtype=np.float64, positive=True) -> Coo:
+    """Uniformly random distinct coordinates with values in [0.5, 1.5) (or N(0,1))."""
+    dims = tuple(int(n) for n in dims)
+    g = _rng(seed, 3)
+    N = math.prod(dims)
+    nnz = min(int(nnz), N)
+    if N <= 4 * nnz + 1024:
+        lin = np.sort(g.choice(N, size=nnz, replace=False)).astype(np.uint64)
+    else:
+        lin = np.unique(g.integers(0, N, size=int(nnz * 1.3) + 16, dtype=np.uint64))
+        lin = np.sort(g.choice(lin, size=min(nnz, lin.shape[0]), replace=False))
+    idx = _unlinear(lin, dims)
+    vals = g.uniform(0.5, 1.5, size=lin.shape[0]) if positive else g.standard_normal(lin.shape[0])
+    return Coo(dims, idx, vals.astype(dtype), {"seed": seed})
+
+
+def exact_lowrank_tensor(dims, rank, seed=0, density=0.5) -> tuple:
+    """A sparse tensor that is exactly rank ``rank``: nonnegative factors with a
+    fraction of zero entries, all nonzero cells of the product kept.  Returns the COO
+    tensor and the planted (lambda, factors)."""
+    dims = tuple(int(n) for n in dims)
+    g = _rng(seed, 5)
+    facs = []
+    for n in dims:
+        F = g.uniform(0.5, 1.5, size=(n, rank)) * (g.random((n, rank)) < density)
+        # keep every row and column nonzero so the model has full rank
+        for j in range(rank):
+            if not F[:, j].any():
+                F[g.integers(0, n), j] = 1.0
+        for i in range(n):
+            if not F[i].any():
+                F[i, g.integers(0, rank)] = 1.0
+        facs.append(F)
+    lam = g.uniform(1.0, 2.0, size=rank)
+    X = np.einsum("r,ir,jr,kr->ijk", lam, *facs) if len(dims) == 3 else None
+    if X is None:
+        # general order: build by repeated outer products
+        X = np.zeros(dims)
+        for j in range(rank):
+            T = lam[j]
+            for F in facs:
+                T = np.multiply.outer(T, F[:, j])
+            X += T
+    nzc = np.nonzero(X)
+    idx = [c.astype(np.int32) for c in nzc]
+    return Coo(dims, idx, X[nzc].astype(np.float64), {"seed": seed}), lam, facs
+
+
+CONFIG_SMALL = dict(name="planted-60x50x40-r4", rank=4, samples=1024, tau=1.0, iters=10, seed=0)
+CONFIG_UBER = dict(name="uber-like-183x24x1140x1717-r25", rank=25, samples=2 ** 17,
+                   tau=2.0 ** -17, seed=0)
