@@ -1,0 +1,338 @@
+"""Benchmark of the GB300 CP-ARLS-LEV hot path.
+
+Workload (default): the 183 x 24 x 1140 x 1717 planted count tensor with about
+3.31M nonzeros (the shape and nonzero count of the paper's Uber tensor, Table 6.1;
+synthetic, planted rank 25, Zipf(1.1) popularity), CP rank 25, s = 2^17 samples
+per least-squares problem, hybrid threshold tau = 1/s, FP64.
+
+One step = one epoch of Alg. 3: eta = 5 outer iterations, each updating all 4 modes
+(sampling, sampled MTTKRP, solve, leverage refresh), then the exact fit -- i.e. 20
+mode updates through one cp_arls_lev call that continues the decomposition
+(iter_offset advances).  value = mode updates per second over the timed steps,
+inputs resident in HBM; L2 is flushed (a 256 MiB write) between timed steps.
+
+--impl reference times the FP64 CPU oracle (the paper's algorithm written plainly)
+on the same workload and prints the same JSON line with "impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "CP-ARLS-LEV mode-updates/sec (sampled-MTTKRP HBM GB/s in roofline)"
+UNIT = "mode-updates/s"
+RANK, SAMPLES, TAU_EXP, ETA = 25, 2 ** 17, 17, 5
+WORKLOAD = "uber-shaped 183x24x1140x1717 planted counts, ~3.31M nnz, r=25, s=2^17, tau=2^-17, FP64"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--cpu-sample-updates", type=int, default=4,
+                   help="mode updates the CPU baseline times (bounded sample)")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def make_workload():
+    import synth
+    coo = synth.uber_like_tensor(0)
+    init = synth.gaussian_factors(coo.dims, RANK, seed=0)
+    return coo, init
+
+
+def mttkrp_bytes(stats, d, b_val=8):
+    """Algorithmic bytes of the gather-scale-accumulate kernel summed over updates:
+    per sample its fibre position, start and weight (24 B) and its KRP row y_j
+    (8r B); per sampled nonzero its mode index and value (4 + b_val B); M is counted
+    once per update as written (n_k r 8 B, added by the caller)."""
+    return stats["sbar_total"] * (24 + 8 * RANK) + stats["nnz_sampled_total"] * (4 + b_val)
+
+
+def run_reference(args, rank):
+    import oracle
+    if rank != 0:
+        return 0
+    coo, init = make_workload()
+    idx = oracle.Index(coo)
+    s, tau = SAMPLES, 2.0 ** -TAU_EXP
+    fs = [a.copy() for a in init]
+    per_step = max(1, args.cpu_sample_updates)
+    times = []
+    k_total = args.warmup + args.steps
+    it = 0
+    for step in range(k_total):
+        t0 = time.perf_counter()
+        for u in range(per_step):
+            k = u % len(coo.dims)
+            res = oracle.mode_update(idx, fs, k, rank=RANK, samples=s, tau=tau, seed=0, it=it)
+            fs[k] = res["A"]
+            if k == len(coo.dims) - 1:
+                it += 1
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = per_step * len(times) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "step": f"{per_step} mode updates"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{per_step} mode updates per step of the same workload "
+                                   "(leverage of every mode recomputed by Householder QR per update)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(coo, init, n_updates):
+    """The oracle as it stands, timed on a bounded sample of the same workload."""
+    import oracle
+    idx = oracle.Index(coo)
+    fs = [a.copy() for a in init]
+    t0 = time.perf_counter()
+    for u in range(n_updates):
+        k = u % len(coo.dims)
+        res = oracle.mode_update(idx, fs, k, rank=RANK, samples=SAMPLES, tau=2.0 ** -TAU_EXP, seed=0, it=0)
+        fs[k] = res["A"]
+    dt = time.perf_counter() - t0
+    return {"value": n_updates / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n_updates} mode updates of the same workload (index built untimed)"}
+
+
+def count_launches(run_once):
+    """Kernels of libcpa launched by one step, counted with the torch profiler."""
+    try:
+        import torch
+        from torch.profiler import ProfilerActivity, profile
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            run_once()
+            torch.cuda.synchronize()
+        n = 0
+        for e in prof.events():
+            if e.device_type.name == "CUDA" and ("cpa::" in e.name or e.name.startswith("_ZN3cpa")):
+                n += 1
+        return n
+    except Exception:
+        return None
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank)
+    import torch
+    import paper_2006_16438_gb300 as cpa
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    coo, init = make_workload()
+    index = cpa.cpa_index_build(coo)
+    s, tau = SAMPLES, 2.0 ** -TAU_EXP
+    seed = rank  # independent decompositions per rank (random restarts)
+    fs = [torch.from_numpy(a).cuda() for a in init]
+    lam = torch.empty(RANK, dtype=torch.float64, device="cuda")
+    fitd = torch.empty(1, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    state = {"it": 0}
+
+    def step(profile=0):
+        res = cpa.cp_arls_lev(index, None, rank=RANK, samples=s, tau=tau, iters=ETA, seed=seed,
+                              iter_offset=state["it"], profile=profile, out=(fs, lam, fitd))
+        state["it"] += ETA
+        return res
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    launches_per_step = count_launches(lambda: step())
+    clocks = ClockSampler(local)
+    clocks.start()
+    times, stages, nnz_tot, sbar_tot = [], np.zeros(8), 0, 0
+    stat_acc = {"sbar_total": 0, "nnz_sampled_total": 0}
+    fits = []
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.add_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = step(profile=1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        st = res.stats
+        stages += np.array(st["stage_ms"])
+        stat_acc["sbar_total"] += st["sbar_total"]
+        stat_acc["nnz_sampled_total"] += st["nnz_sampled_total"]
+        fits.append(res.fit)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = sum(times)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    updates = args.steps * ETA * len(coo.dims)
+    value = updates * world / (total_ms / 1000.0)
+    peaks, peak_src = load_peaks()
+    n_updates = updates
+    # roofline of the gather-scale-accumulate MTTKRP kernel (stage 2)
+    mk_ms = stages[2]
+    mk_bytes = mttkrp_bytes(stat_acc, len(coo.dims) - 1) + sum(
+        n * RANK * 8 for n in coo.dims) * (n_updates // len(coo.dims))
+    mk_gbs = mk_bytes / (mk_ms / 1000.0) / 1e9 if mk_ms > 0 else None
+    stage_names = ["sample", "probe_krp_gram", "mttkrp", "solve", "leverage", "fit"]
+    stage_share = {nm: round(float(stages[i] / max(stages[6], 1e-9)), 4) for i, nm in enumerate(stage_names)}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "step": "1 epoch = 5 outer iterations x 4 mode updates + exact fit",
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": f"{world} independent replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "kernel": "k_mttkrp (gather-scale-accumulate)",
+                     "achieved": mk_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": (mk_gbs / peaks["hbm_gbs"]) if mk_gbs else None, "traffic": None,
+                     "peak_source": peak_src,
+                     "bytes_per_update": mk_bytes / n_updates, "ms_per_update": mk_ms / n_updates},
+        "stages_ms_per_update": {nm: float(stages[i] / n_updates) for i, nm in enumerate(stage_names)},
+        "stage_share": stage_share,
+        "nnz_sampled_per_update": stat_acc["nnz_sampled_total"] / n_updates,
+        "sbar_per_update": stat_acc["sbar_total"] / n_updates,
+        "fit": fits[-1] if fits else None,
+        "clocks": clk,
+        "gpu_launches": (launches_per_step * args.steps) if launches_per_step else None,
+    }
+    if rank == 0 and not args.no_e2e:
+        line["e2e"] = e2e(cpa, coo, init, args)
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(coo, init, args.cpu_sample_updates)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def e2e(cpa, coo, init, args):
+    """Same metric through cp_arls_lev_coo with HOST buffers: each step copies the
+    COO tensor and the factors in, builds the index, runs one epoch and copies the
+    factors, lambda and fit back."""
+    import torch
+    idx_bytes = sum(i.nbytes for i in coo.idx) + coo.vals.astype(np.float64).nbytes
+    fac_bytes = sum(a.nbytes for a in init)
+    times = []
+    fs = [a.copy() for a in init]
+    for i in range(max(1, min(3, args.steps)) + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = cpa.cp_arls_lev_coo(coo, fs, rank=RANK, samples=SAMPLES, tau=2.0 ** -TAU_EXP, iters=ETA,
+                                  seed=0, iter_offset=ETA * i)
+        t1 = time.perf_counter()
+        fs = res.factors
+        if i > 0:
+            times.append(t1 - t0)
+    per = sum(times) / len(times)
+    return {"value": ETA * len(coo.dims) / per, "unit": UNIT,
+            "h2d_bytes_per_step": int(idx_bytes + fac_bytes),
+            "d2h_bytes_per_step": int(fac_bytes + 8 * RANK + 8),
+            "note": "index build included in every step"}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

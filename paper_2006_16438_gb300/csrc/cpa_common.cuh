@@ -1,0 +1,193 @@
+// Shared device/host helpers of the CP-ARLS-LEV CUDA library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "../../include/cpa.h"
+
+namespace cpa {
+
+constexpr int kMaxOrder = 8;
+constexpr int kMaxRank = 64;
+constexpr int kWarp = 32;
+
+// ---------------------------------------------------------------------------
+// Device-side status: kernels record the first error here instead of trapping.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void set_status(int* status, int code) {
+  atomicCAS(status, 0, code);
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 64x64->128
+// multiplies with the published multipliers, xor-mixing with the round key, which
+// is advanced by the two published Weyl increments between rounds.
+// ---------------------------------------------------------------------------
+struct Philox4x64 {
+  static constexpr uint64_t kMulA = 0xD2E7470EE14C6C93ull;
+  static constexpr uint64_t kMulB = 0xCA5A826395121157ull;
+  static constexpr uint64_t kWeylA = 0x9E3779B97F4A7C15ull;
+  static constexpr uint64_t kWeylB = 0xBB67AE8584CAA73Bull;
+
+  __device__ __forceinline__ static void block(uint64_t& w0, uint64_t& w1, uint64_t& w2,
+                                               uint64_t& w3, uint64_t ka, uint64_t kb) {
+#pragma unroll
+    for (int rnd = 0; rnd < 10; ++rnd) {
+      const uint64_t a_lo = kMulA * w0, a_hi = __umul64hi(kMulA, w0);
+      const uint64_t b_lo = kMulB * w2, b_hi = __umul64hi(kMulB, w2);
+      const uint64_t n0 = b_hi ^ w1 ^ ka;
+      const uint64_t n2 = a_hi ^ w3 ^ kb;
+      w0 = n0;
+      w1 = b_lo;
+      w2 = n2;
+      w3 = a_lo;
+      ka += kWeylA;
+      kb += kWeylB;
+    }
+  }
+};
+
+// Domain tag of the sampling draws in the third counter word.
+constexpr uint64_t kDomainSample = 1ull << 32;
+
+// ---------------------------------------------------------------------------
+// Packed multi-index: other mode t occupies bits [off_t, off_t + bits_t) of a
+// 64-bit word.  The packing keeps the order of the linear index of Eq. 2.2 (both
+// compare i_{d-1} first, then i_{d-2}, ...), so sorted packed keys are sorted
+// linear keys and decoding needs only shifts and masks.
+// ---------------------------------------------------------------------------
+struct KeyLayout {
+  int d;                        // number of other modes
+  int mode[kMaxOrder];          // other modes, ascending
+  int bits[kMaxOrder];
+  int off[kMaxOrder];
+  int total_bits;
+  int64_t n[kMaxOrder];         // sizes of the other modes
+  uint64_t stride[kMaxOrder];   // linear-key strides prod_{u<t} n_u
+
+  __host__ __device__ __forceinline__ uint32_t get(uint64_t packed, int t) const {
+    return (uint32_t)((packed >> off[t]) & ((1ull << bits[t]) - 1ull));
+  }
+  __host__ __device__ __forceinline__ uint64_t linear(uint64_t packed) const {
+    uint64_t key = 0;
+    for (int t = 0; t < d; ++t) key += (uint64_t)get(packed, t) * stride[t];
+    return key;
+  }
+};
+
+inline int ceil_log2(int64_t n) {
+  int b = 0;
+  while (b < 63 && (1ll << b) < n) ++b;
+  return b < 1 ? 1 : b;
+}
+
+// Layout of the other modes of an update of mode k (k = -1: all `order` modes given
+// in `dims` are "other" modes, used by the stage entry points).
+inline bool make_layout(int order, const int64_t* dims, int k, KeyLayout* L) {
+  memset(L, 0, sizeof(*L));
+  int t = 0, off = 0;
+  uint64_t stride = 1;
+  for (int m = 0; m < order; ++m) {
+    if (m == k) continue;
+    L->mode[t] = m;
+    L->n[t] = dims[m];
+    L->bits[t] = ceil_log2(dims[m]);
+    L->off[t] = off;
+    L->stride[t] = stride;
+    off += L->bits[t];
+    stride *= (uint64_t)dims[m];
+    ++t;
+  }
+  L->d = t;
+  L->total_bits = off;
+  return off <= 63;
+}
+
+// ---------------------------------------------------------------------------
+// Device arena: one cudaMallocAsync block carved into aligned pieces.  A first
+// pass with base == nullptr only measures.
+// ---------------------------------------------------------------------------
+struct Arena {
+  char* base = nullptr;
+  size_t used = 0;
+  size_t cap = 0;
+  template <class T>
+  T* take(size_t count) {
+    size_t at = (used + 255) & ~size_t(255);
+    used = at + count * sizeof(T) + 1;
+    return base ? reinterpret_cast<T*>(base + at) : nullptr;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Error plumbing
+// ---------------------------------------------------------------------------
+#define CPA_CUDA_TRY(expr)                                                        \
+  do {                                                                            \
+    cudaError_t _e = (expr);                                                      \
+    if (_e != cudaSuccess) {                                                      \
+      if (getenv("CPA_VERBOSE"))                                                  \
+        fprintf(stderr, "cpa: %s failed at %s:%d: %s\n", #expr, __FILE__, __LINE__, \
+                cudaGetErrorString(_e));                                          \
+      return _e == cudaErrorMemoryAllocation ? CPA_ERR_OOM : CPA_ERR_CUDA;        \
+    }                                                                             \
+  } while (0)
+
+#define CPA_TRY(expr)            \
+  do {                           \
+    int _rc = (expr);            \
+    if (_rc < 0) return _rc;     \
+  } while (0)
+
+#define CPA_LAUNCH_CHECK() CPA_CUDA_TRY(cudaGetLastError())
+
+inline int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Count of items known only on the device (or a fixed host count if dptr is null).
+struct DevCount {
+  const int64_t* dptr = nullptr;
+  int64_t max = 0;
+  __device__ __forceinline__ int64_t get() const {
+    if (!dptr) return max;
+    int64_t v = *dptr;
+    return v < max ? (v < 0 ? 0 : v) : max;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Scan and radix sort (scan_sort.cu).  Both take a device scratch buffer of the
+// size their *_workspace function returns for the largest count they will see.
+// ---------------------------------------------------------------------------
+size_t scan_workspace(int64_t n_max);
+// out[i] = sum_{j<i} in[j] (exclusive) or sum_{j<=i} in[j] (inclusive) for
+// i < count; *total (device, may be null) = sum of all.  in may equal out.
+template <class T>
+int scan_u64(const T* in, uint64_t* out, DevCount count, bool inclusive, uint64_t* total,
+             void* scratch, cudaStream_t st);
+
+size_t sort_workspace(int64_t n_max);
+// Stable LSD radix sort (8-bit digits) of keys, and values if vals != null, on key
+// bits [begin_bit, end_bit).  Ping-pongs between the buffer pairs; *in_alt is set
+// to 1 if the sorted result is in keys_alt/vals_alt, 0 if in keys/vals.
+template <class V>
+int radix_sort(uint64_t* keys, uint64_t* keys_alt, V* vals, V* vals_alt, DevCount count,
+               int begin_bit, int end_bit, void* scratch, cudaStream_t st, int* in_alt);
+
+}  // namespace cpa

@@ -1,0 +1,71 @@
+// Internal types and cross-file entry points of the CP-ARLS-LEV CUDA library.
+#pragma once
+
+#include "cpa_common.cuh"
+
+// Opaque index of the C ABI (Section 5.3 fibre index, one per mode).
+struct cpa_index {
+  int order = 0;
+  int64_t dims[cpa::kMaxOrder] = {};
+  int64_t nnz = 0;
+  int val_dtype = CPA_F64;
+  double norm_x2 = 0.0;  // ||X||_F^2, FP64
+  struct Mode {
+    cpa::KeyLayout L;           // packed layout of the other modes
+    int64_t nfib = 0;           // F_k
+    uint64_t* keys = nullptr;   // F_k packed keys, ascending
+    uint64_t* off = nullptr;    // F_k + 1 offsets into ik/val
+    int32_t* ik = nullptr;      // nnz mode-k indices, fibre order (ascending within a fibre)
+    void* val = nullptr;        // nnz values (float or double)
+    uint64_t* dir = nullptr;    // (1 << dbits) + 1 bucket starts over the top key bits
+    int dbits = 0;
+    int dshift = 0;
+  } mode[cpa::kMaxOrder];
+  std::vector<void*> allocations;
+};
+
+namespace cpa {
+
+// Device view of one mode of the index, passed by value to kernels.
+template <class VT>
+struct FibreIndex {
+  const uint64_t* keys;
+  const uint64_t* off;
+  const int32_t* ik;
+  const VT* val;
+  const uint64_t* dir;
+  int64_t nfib;
+  int dshift;
+  int dbits;
+
+  // Fibre [*lo, *hi) of a packed key; empty range if the key has no nonzeros.
+  __device__ __forceinline__ void probe(uint64_t key, uint64_t* lo, uint64_t* hi) const {
+    const uint64_t b = dshift >= 64 ? 0 : (key >> dshift);
+    int64_t a = (int64_t)dir[b], z = (int64_t)dir[b + 1];
+    while (a < z) {  // lower bound in keys[a, z)
+      const int64_t mid = a + ((z - a) >> 1);
+      if (keys[mid] < key) a = mid + 1; else z = mid;
+    }
+    if (a < nfib && keys[a] == key) {
+      *lo = off[a];
+      *hi = off[a + 1];
+    } else {
+      *lo = *hi = 0;
+    }
+  }
+};
+
+template <class VT>
+inline FibreIndex<VT> fibre_view(const cpa_index* X, int k) {
+  const auto& M = X->mode[k];
+  return FibreIndex<VT>{M.keys, M.off, M.ik, reinterpret_cast<const VT*>(M.val), M.dir,
+                        M.nfib, M.dshift, M.dbits};
+}
+
+// index.cu
+int index_build(const cpa_coo* coo, cudaStream_t st, cpa_index** out);
+void index_free(cpa_index* X);
+int index_export(const cpa_index* X, int k, uint64_t* keys, uint64_t* off, int32_t* ik,
+                 void* val, cudaStream_t st);
+
+}  // namespace cpa

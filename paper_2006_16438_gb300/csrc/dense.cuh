@@ -1,0 +1,66 @@
+// Dense kernels of the per-mode update: Gram products, the r x r SPD factorisation
+// (Cholesky, pseudo-inverse fallback), leverage scores of factor rows with the
+// fixed-point sampling weights, and the row-wise normal-equation solve.
+#pragma once
+
+#include "cpa_internal.cuh"
+
+namespace cpa {
+
+// Result of factoring an r x r symmetric positive semidefinite matrix G.
+// kind 0: F holds the lower Cholesky factor of S G S (row-major), S = diag(scale).
+// kind 1: F holds the pseudo-inverse of S G S.
+// With normalize = 1, scale_c = 1/sqrt(G_cc) (0 for a zero column) and lambda_c =
+// sqrt(G_cc); otherwise scale = 1, lambda = sqrt(G_cc).  gram holds S G S.
+struct SmallFactor {
+  double F[kMaxRank * kMaxRank];
+  double gram[kMaxRank * kMaxRank];
+  double scale[kMaxRank];
+  double lambda[kMaxRank];
+  int kind;
+  int pad[3];
+};
+
+// Per-mode fixed-point distribution summary (device).
+struct DistInfo {
+  uint64_t T;     // sum of q
+  uint64_t maxq;  // largest q
+  int64_t nnzq;   // number of q > 0
+  int64_t pad;
+};
+
+// G += A^T A for a row-major n x r FP64 matrix (G must be zeroed by the caller).
+int gram_rows(const double* A, int64_t n, int r, double* G, cudaStream_t st);
+
+// Factor G (see SmallFactor).  rel_tol: a Cholesky pivot must exceed rel_tol times
+// the largest diagonal entry; otherwise the pseudo-inverse (eigenvalues above
+// rel_tol * largest) is used and `warn_bit` is OR-ed into *warn.
+int factor_spd(const double* G, int r, int normalize, double rel_tol, SmallFactor* out,
+               int* warn, int warn_bit, cudaStream_t st);
+
+// For every row a_i of A: lev_i = || L^{-1} S a_i ||^2 (kind 0) or a_i^T S F S a_i
+// (kind 1); q_i = round-half-even(2^62 lev_i / r) written to q (if non-null),
+// DistInfo maxq/nnzq accumulated (zeroed by the caller); rows divided by lambda
+// (columns with lambda = 0 untouched) and written to A_out if non-null (may be A).
+int lev_rows(const double* A, int64_t n, int r, const SmallFactor* f, double* lev,
+             uint64_t* q, DistInfo* info, double* A_out, cudaStream_t st);
+
+// A = M G^{-1} row by row with the factor of G (kind 0: two triangular solves;
+// kind 1: A = M F).
+int solve_rows(const double* M, int64_t n, int r, const SmallFactor* f, double* A,
+               cudaStream_t st);
+
+// A(:, c) /= lambda_c for lambda_c > 0.
+int scale_columns(double* A, int64_t n, int r, const double* lambda, cudaStream_t st);
+
+// C = inclusive prefix sum of q (in place allowed); info->T = total.
+int cdf_from_q(uint64_t* q, uint64_t* C, int64_t n, DistInfo* info, void* scan_scratch,
+               cudaStream_t st);
+
+inline unsigned grid_cap(int64_t blocks, int per_sm = 8) {
+  const int64_t cap = (int64_t)num_sms() * per_sm;
+  if (blocks < 1) blocks = 1;
+  return (unsigned)(blocks < cap ? blocks : cap);
+}
+
+}  // namespace cpa

@@ -1,0 +1,251 @@
+// KrpSamp + TnsrSamp + sampled normal equations (Section 5.2, Section 5.3).
+//
+// 1. probe:    one thread per sample finds its fibre [lo, lo + len) in the mode-k
+//              stream through the bucket directory and a short binary search.
+// 2. krp_gram: samples in tiles of 32: y_j = wgt_j * prod_t A_{m_t}(i_t, :) is formed
+//              (row gathers of the other factors), stored for step 4, and
+//              G += y_j y_j^T is accumulated per thread over upper-triangle pairs.
+// 3. scan:     pos = exclusive prefix of len (nnz of the sampled right-hand side).
+// 4. mttkrp:   the flattened list of sampled nonzeros is cut into equal chunks, one
+//              per warp (merge-path style, so one heavy fibre is split across many
+//              warps); lane c accumulates M(i_k, c) += wgt_j * x * y_j(c) with
+//              atomics, into shared memory when M fits, else straight to global.
+#include "mttkrp.cuh"
+
+namespace cpa {
+
+namespace {
+
+constexpr int kTileRows = 32;
+constexpr int kThreads = 256;
+constexpr int kChunk = 256;  // sampled nonzeros per warp work item
+
+__device__ __forceinline__ void pair_of(int p, int r, int* a, int* b) {
+  int row = 0, start = 0;
+  while (p >= start + (r - row)) {
+    start += r - row;
+    ++row;
+  }
+  *a = row;
+  *b = row + (p - start);
+}
+
+template <class VT>
+__global__ void k_probe(FibreIndex<VT> X, const uint64_t* __restrict__ idx, DevCount sbar,
+                        uint64_t* __restrict__ lo, uint32_t* __restrict__ len) {
+  const int64_t n = sbar.get();
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t a, b;
+    X.probe(idx[j], &a, &b);
+    lo[j] = a;
+    len[j] = (uint32_t)(b - a);
+  }
+}
+
+template <int PMAX>
+__global__ void __launch_bounds__(kThreads) k_krp_gram(FactorPtrs F, KeyLayout L, int r,
+                                                       const uint64_t* __restrict__ idx,
+                                                       const double* __restrict__ wgt,
+                                                       DevCount sbar, double* __restrict__ Y,
+                                                       double* __restrict__ G) {
+  extern __shared__ double tile[];  // kTileRows * r
+  __shared__ uint32_t rows[kTileRows][kMaxOrder];
+  __shared__ double wsh[kTileRows];
+  const int np = r * (r + 1) / 2;
+  int pa[PMAX], pb[PMAX];
+  double acc[PMAX];
+#pragma unroll
+  for (int q = 0; q < PMAX; ++q) {
+    const int p = threadIdx.x + q * kThreads;
+    if (p < np) pair_of(p, r, &pa[q], &pb[q]); else pa[q] = pb[q] = 0;
+    acc[q] = 0.0;
+  }
+  const int64_t n = sbar.get();
+  for (int64_t t0 = (int64_t)blockIdx.x * kTileRows; t0 < n; t0 += (int64_t)gridDim.x * kTileRows) {
+    const int cnt = (int)((n - t0) < kTileRows ? (n - t0) : kTileRows);
+    __syncthreads();
+    if (threadIdx.x < cnt) {
+      const uint64_t key = idx[t0 + threadIdx.x];
+      for (int t = 0; t < L.d; ++t) rows[threadIdx.x][t] = L.get(key, t);
+      wsh[threadIdx.x] = wgt[t0 + threadIdx.x];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kTileRows * r; i += kThreads) {
+      const int sl = i / r, c = i - sl * r;
+      double v = 0.0;
+      if (sl < cnt) {
+        v = wsh[sl];
+        for (int t = 0; t < L.d; ++t) v *= F.A[L.mode[t]][(int64_t)rows[sl][t] * r + c];
+        Y[(t0 + sl) * r + c] = v;
+      }
+      tile[i] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < PMAX; ++q) {
+      const int p = threadIdx.x + q * kThreads;
+      if (p < np) {
+        double s = 0.0;
+        for (int i = 0; i < cnt; ++i) s = fma(tile[i * r + pa[q]], tile[i * r + pb[q]], s);
+        acc[q] += s;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < PMAX; ++q) {
+    const int p = threadIdx.x + q * kThreads;
+    if (p < np && acc[q] != 0.0) {
+      atomicAdd(&G[pa[q] * r + pb[q]], acc[q]);
+      if (pa[q] != pb[q]) atomicAdd(&G[pb[q] * r + pa[q]], acc[q]);
+    }
+  }
+}
+
+__global__ void k_pos_end(DevCount sbar, const uint64_t* __restrict__ total, uint64_t* pos) {
+  pos[sbar.get()] = *total;
+}
+
+template <class VT, int CPL, bool kShared>
+__global__ void __launch_bounds__(kThreads) k_mttkrp(FibreIndex<VT> X, const double* __restrict__ Y,
+                                                     const double* __restrict__ wgt,
+                                                     const uint64_t* __restrict__ lo,
+                                                     const uint64_t* __restrict__ pos, DevCount sbar,
+                                                     const uint64_t* __restrict__ d_total, int r,
+                                                     int64_t nk, double* __restrict__ M) {
+  extern __shared__ double Ms[];
+  if (kShared) {
+    for (int64_t i = threadIdx.x; i < nk * r; i += kThreads) Ms[i] = 0.0;
+    __syncthreads();
+  }
+  const int64_t n = sbar.get();
+  const uint64_t total = *d_total;
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
+  for (uint64_t c0 = (uint64_t)gw * kChunk; c0 < total; c0 += (uint64_t)nwarps * kChunk) {
+    const uint64_t c1 = c0 + kChunk < total ? c0 + kChunk : total;
+    // last sample j with pos[j] <= c0
+    int64_t a = 0, b = n - 1;
+    while (a < b) {
+      const int64_t mid = (a + b + 1) >> 1;
+      if (pos[mid] <= c0) a = mid; else b = mid - 1;
+    }
+    int64_t j = a;
+    uint64_t e = c0;
+    while (e < c1) {
+      const uint64_t pj = pos[j], pj1 = pos[j + 1];
+      const uint64_t seg_end = pj1 < c1 ? pj1 : c1;
+      const uint64_t base = lo[j] + (e - pj);
+      const double w = wgt[j];
+      double coef[CPL];
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) {
+        const int c = lane + 32 * q;
+        coef[q] = c < r ? w * Y[j * r + c] : 0.0;
+      }
+      const int cnt = (int)(seg_end - e);
+      for (int b0 = 0; b0 < cnt; b0 += 32) {
+        int32_t ik_l = 0;
+        double v_l = 0.0;
+        if (b0 + lane < cnt) {
+          ik_l = X.ik[base + b0 + lane];
+          v_l = (double)X.val[base + b0 + lane];
+        }
+        const int nb = cnt - b0 < 32 ? cnt - b0 : 32;
+        for (int q2 = 0; q2 < nb; ++q2) {
+          const int32_t ik = __shfl_sync(0xffffffffu, ik_l, q2);
+          const double v = __shfl_sync(0xffffffffu, v_l, q2);
+#pragma unroll
+          for (int q = 0; q < CPL; ++q) {
+            const int c = lane + 32 * q;
+            if (c < r) {
+              if (kShared) atomicAdd(&Ms[(int64_t)ik * r + c], v * coef[q]);
+              else atomicAdd(&M[(int64_t)ik * r + c], v * coef[q]);
+            }
+          }
+        }
+      }
+      e = seg_end;
+      while (j + 1 < n && pos[j + 1] <= e) ++j;
+    }
+  }
+  if (kShared) {
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < nk * r; i += kThreads)
+      if (Ms[i] != 0.0) atomicAdd(&M[i], Ms[i]);
+  }
+}
+
+template <class VT>
+int run(const cpa_index* X, int k, const FactorPtrs& F, int r, const uint64_t* idx, const double* wgt,
+        DevCount sbar, double* M, double* G, MttkrpBuffers& B, cudaStream_t st, cudaEvent_t mid) {
+  const auto& mode = X->mode[k];
+  const FibreIndex<VT> fx = fibre_view<VT>(X, k);
+  const int64_t s = sbar.max;
+  const int sms = num_sms();
+  int64_t pb = ceil_div(s, kThreads);
+  k_probe<VT><<<(unsigned)(pb < sms * 16 ? pb : sms * 16), kThreads, 0, st>>>(fx, idx, sbar, B.lo,
+                                                                             B.len);
+  const int np = r * (r + 1) / 2;
+  int64_t tb = ceil_div(s, kTileRows);
+  const unsigned tgrid = (unsigned)(tb < sms * 2 ? tb : sms * 2);
+  const size_t tsm = sizeof(double) * kTileRows * r;
+  if (np <= kThreads)
+    k_krp_gram<1><<<tgrid, kThreads, tsm, st>>>(F, mode.L, r, idx, wgt, sbar, B.Y, G);
+  else if (np <= 4 * kThreads)
+    k_krp_gram<4><<<tgrid, kThreads, tsm, st>>>(F, mode.L, r, idx, wgt, sbar, B.Y, G);
+  else
+    k_krp_gram<9><<<tgrid, kThreads, tsm, st>>>(F, mode.L, r, idx, wgt, sbar, B.Y, G);
+  CPA_LAUNCH_CHECK();
+  CPA_TRY(scan_u64<uint32_t>(B.len, B.pos, sbar, false, B.total, B.scratch, st));
+  k_pos_end<<<1, 1, 0, st>>>(sbar, B.total, B.pos);
+  if (mid) CPA_CUDA_TRY(cudaEventRecord(mid, st));
+  const int64_t nk = X->dims[k];
+  const bool shared = nk * r * sizeof(double) <= 48 * 1024;
+  const size_t msm = shared ? sizeof(double) * nk * r : 0;
+  const unsigned mgrid = (unsigned)(shared ? sms : sms * 4);
+  if (r <= 32) {
+    if (shared)
+      k_mttkrp<VT, 1, true><<<mgrid, kThreads, msm, st>>>(fx, B.Y, wgt, B.lo, B.pos, sbar, B.total, r, nk, M);
+    else
+      k_mttkrp<VT, 1, false><<<mgrid, kThreads, 0, st>>>(fx, B.Y, wgt, B.lo, B.pos, sbar, B.total, r, nk, M);
+  } else {
+    if (shared)
+      k_mttkrp<VT, 2, true><<<mgrid, kThreads, msm, st>>>(fx, B.Y, wgt, B.lo, B.pos, sbar, B.total, r, nk, M);
+    else
+      k_mttkrp<VT, 2, false><<<mgrid, kThreads, 0, st>>>(fx, B.Y, wgt, B.lo, B.pos, sbar, B.total, r, nk, M);
+  }
+  CPA_LAUNCH_CHECK();
+  return CPA_OK;
+}
+
+}  // namespace
+
+size_t mttkrp_buffers_bytes(int64_t s, int r) {
+  Arena a;
+  MttkrpBuffers B;
+  mttkrp_buffers_carve(a, s, r, &B);
+  return a.used + 256;
+}
+
+void mttkrp_buffers_carve(Arena& a, int64_t s, int r, MttkrpBuffers* B) {
+  B->Y = a.take<double>((size_t)s * r);
+  B->lo = a.take<uint64_t>(s);
+  B->len = a.take<uint32_t>(s);
+  B->pos = a.take<uint64_t>(s + 1);
+  B->total = a.take<uint64_t>(1);
+  B->scratch = a.take<char>(scan_workspace(s));
+}
+
+int sampled_mttkrp(const cpa_index* X, int k, const FactorPtrs& F, int r, const uint64_t* idx_packed,
+                   const double* wgt, DevCount sbar, double* M, double* G, MttkrpBuffers& B,
+                   cudaStream_t st, cudaEvent_t mid) {
+  if (r < 1 || r > kMaxRank) return CPA_ERR_ARG;
+  if (sbar.max <= 0) return CPA_OK;
+  if (X->val_dtype == CPA_F32)
+    return run<float>(X, k, F, r, idx_packed, wgt, sbar, M, G, B, st, mid);
+  return run<double>(X, k, F, r, idx_packed, wgt, sbar, M, G, B, st, mid);
+}
+
+}  // namespace cpa

@@ -1,0 +1,34 @@
+// KrpSamp, TnsrSamp and the sampled normal-equation products (Section 5.2, 5.3).
+#pragma once
+
+#include "dense.cuh"
+
+namespace cpa {
+
+struct FactorPtrs {
+  const double* A[kMaxOrder];  // indexed by mode
+};
+
+// Buffers of one sampled MTTKRP (device), sized for s samples.
+struct MttkrpBuffers {
+  double* Y;          // s x r: y_j = wgt_j * z_j
+  uint64_t* lo;       // s: first nonzero of the fibre of sample j in the mode-k stream
+  uint32_t* len;      // s: fibre length
+  uint64_t* pos;      // s + 1: exclusive prefix of len; pos[sbar] = nnz of the sample
+  uint64_t* total;    // 1: nnz of the sampled right-hand side
+  char* scratch;      // scan workspace for s items
+};
+
+size_t mttkrp_buffers_bytes(int64_t s, int r);
+void mttkrp_buffers_carve(Arena& a, int64_t s, int r, MttkrpBuffers* B);
+
+// G += sum_j y_j y_j^T and M += sum_j wgt_j x(:, key_j) y_j^T over the sbar samples
+// (packed keys), with y_j = wgt_j prod_t A_{m_t}(i_t, :).  G and M must be zeroed
+// by the caller.  sbar: device count (max s).
+// If mid_event is non-null it is recorded on `st` right before the
+// gather-scale-accumulate kernel (after probe, KRP/Gram and the scan).
+int sampled_mttkrp(const cpa_index* X, int k, const FactorPtrs& F, int r,
+                   const uint64_t* idx_packed, const double* wgt, DevCount sbar, double* M,
+                   double* G, MttkrpBuffers& B, cudaStream_t st, cudaEvent_t mid_event = nullptr);
+
+}  // namespace cpa

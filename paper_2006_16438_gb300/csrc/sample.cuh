@@ -1,0 +1,80 @@
+// SkrpLev (Alg. 1) on the GPU: deterministic rows (Section 5.3), random rows with
+// rejection (Alg. 2), CombineRepeats (Section 4.1) -- all without host round trips.
+#pragma once
+
+#include "dense.cuh"
+
+namespace cpa {
+
+constexpr int kXsLimbs = 36;  // exact-sum accumulator: 36 x 32 bits from 2^-1074 up
+
+// Device scalars of one sampling pass.
+struct SampleState {
+  int status;
+  int no_det;
+  int need_topk;
+  int pad0;
+  int64_t ncand[kMaxOrder];
+  uint64_t cand_total;
+  uint64_t det_count;   // rows that passed p_i > tau (may exceed s)
+  int64_t sdet;
+  int64_t srnd;
+  int64_t nsort;        // sdet + srnd
+  int64_t sbar;         // rows after combining
+  int64_t nuniq;        // distinct keys in the sorted buffer
+  uint64_t attempts;
+  double pdet;
+  double alpha_star;
+  double thr[kMaxOrder];
+  uint64_t xs[kXsLimbs];  // exact-sum bins of p_det
+};
+
+// Per-mode distributions of the d other modes (device pointers).
+struct OtherDists {
+  const uint64_t* C[kMaxOrder];
+  const DistInfo* info[kMaxOrder];
+};
+
+struct SampleParams {
+  KeyLayout L;          // other modes of the update
+  OtherDists D;
+  int64_t s;
+  double tau;
+  uint64_t seed;
+  uint64_t iter;
+  int mode_k;
+  int reject_cap;
+  int64_t det_cap;
+};
+
+// Buffers of one sampling pass (device), sized by sample_buffers_bytes.
+struct SampleBuffers {
+  SampleState* state;
+  uint32_t* cand;       // sum_t n_t candidate indices (mode t at cand_off[t])
+  int64_t cand_off[kMaxOrder];
+  uint64_t* det_keys;   // det_cap packed keys
+  double* det_p;        // det_cap probabilities
+  uint64_t* sortA;      // s
+  uint64_t* sortB;      // s
+  uint32_t* flag;       // s
+  uint64_t* uid;        // s
+  uint64_t* run_start;  // s + 1
+  char* scratch;        // max(sort, scan) workspace for s items
+  // outputs
+  uint64_t* idx_packed; // s
+  uint32_t* cnt;        // s
+  double* wgt;          // s
+  uint64_t* idx_linear; // s (may be null)
+  uint64_t* raw_key;    // s_rnd raw per-slot linear keys (may be null)
+  double* raw_w;        // s_rnd raw per-slot weights (may be null)
+};
+
+size_t sample_buffers_bytes(const KeyLayout& L, int64_t s, int64_t det_cap);
+void sample_buffers_carve(Arena& a, const KeyLayout& L, int64_t s, int64_t det_cap,
+                          SampleBuffers* B);
+
+// Enqueue one SkrpLev pass.  If tau * s < 1 the deterministic set might exceed s;
+// then the call synchronises once to run the top-s selection.
+int skrp_lev(const SampleParams& P, SampleBuffers& B, cudaStream_t st);
+
+}  // namespace cpa
