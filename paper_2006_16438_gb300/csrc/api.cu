@@ -124,7 +124,7 @@ int refresh_distribution(double* A, int64_t n, int r, uint64_t* C, DistInfo* inf
                          double* lev_out, cudaStream_t st) {
   CPA_CUDA_TRY(cudaMemsetAsync(GA, 0, sizeof(double) * r * r, st));
   CPA_TRY(gram_rows(A, n, r, GA, st));
-  CPA_TRY(factor_spd(GA, r, 1, 1e-12, fac, warn, CPA_WARN_RANK_DEFICIENT_LEV, st));
+  CPA_TRY(factor_spd(GA, r, 1, 1, 1e-12, fac, warn, CPA_WARN_RANK_DEFICIENT_LEV, st));
   CPA_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(DistInfo), st));
   CPA_TRY(lev_rows(A, n, r, fac, lev_out, C, info, normalize_out ? A : nullptr, st));
   CPA_TRY(cdf_from_q(C, C, n, info, scan_scratch, st));
@@ -287,7 +287,7 @@ int cpa_leverage(const double* A, int64_t n, int32_t r, double* lev, void* strea
     CPA_CUDA_TRY(cudaMemsetAsync(G, 0, sizeof(double) * r * r, st));
     CPA_CUDA_TRY(cudaMemsetAsync(warn, 0, sizeof(int), st));
     CPA_TRY(gram_rows(A, n, r, G, st));
-    CPA_TRY(factor_spd(G, r, 1, 1e-12, f, warn, CPA_WARN_RANK_DEFICIENT_LEV, st));
+    CPA_TRY(factor_spd(G, r, 1, 1, 1e-12, f, warn, CPA_WARN_RANK_DEFICIENT_LEV, st));
     CPA_TRY(lev_rows(A, n, r, f, lev, nullptr, nullptr, nullptr, st));
     int hwarn = 0;
     CPA_CUDA_TRY(cudaMemcpyAsync(&hwarn, warn, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -446,12 +446,12 @@ int cpa_solve(const double* G, const double* M, int64_t n, int32_t r, double* A,
   double* GA = (double*)(fl + 1);
   int* warn = (int*)(GA + r * r);
   CPA_CUDA_TRY(cudaMemsetAsync(warn, 0, sizeof(int), st));
-  CPA_TRY(factor_spd(G, r, 0, 1e-13, fs, warn, CPA_WARN_SINGULAR_GRAM, st));
+  CPA_TRY(factor_spd(G, r, 0, 0, 1e-13, fs, warn, CPA_WARN_SINGULAR_GRAM, st));
   CPA_TRY(solve_rows(M, n, r, fs, A, st));
   CPA_CUDA_TRY(cudaMemsetAsync(GA, 0, sizeof(double) * r * r, st));
   CPA_TRY(gram_rows(A, n, r, GA, st));
   int dummy_warn_bit = 0;
-  CPA_TRY(factor_spd(GA, r, 1, 1e-12, fl, warn, dummy_warn_bit, st));
+  CPA_TRY(factor_spd(GA, r, 1, 1, 1e-12, fl, warn, dummy_warn_bit, st));
   k_copy_lambda<<<1, 64, 0, st>>>(fl, r, lambda);
   CPA_TRY(scale_columns(A, n, r, lambda, st));
   int hwarn = 0;
@@ -605,7 +605,7 @@ int cp_arls_lev(const cpa_index* X, const cpa_options* opt, double* lambda, doub
         CPA_TRY(sampled_mttkrp(X, k, F, r, SB.idx_packed, SB.wgt, DevCount{&SB.state->sbar, s}, M, Gs,
                                MB, st, mid));
         CPA_TRY(prof.mark(2));
-        CPA_TRY(factor_spd(Gs, r, 0, 1e-13, fsolve, warn, CPA_WARN_SINGULAR_GRAM, st));
+        CPA_TRY(factor_spd(Gs, r, 0, 0, 1e-13, fsolve, warn, CPA_WARN_SINGULAR_GRAM, st));
         CPA_TRY(solve_rows(M, nk, r, fsolve, Fm[k], st));
         CPA_TRY(prof.mark(3));
         CPA_TRY(refresh_distribution(Fm[k], nk, r, Cm[k], info + k, GA, flev, warn, scan_ws, true,

@@ -112,7 +112,7 @@ __device__ void jacobi_eigen_serial(double* a, double* v, int r) {
 }
 
 __global__ void __launch_bounds__(kFactorThreads) k_factor_spd(const double* __restrict__ G,
-                                                               int r, int normalize,
+                                                               int r, int normalize, int pivot,
                                                                double rel_tol,
                                                                SmallFactor* __restrict__ out,
                                                                int* warn, int warn_bit) {
@@ -120,7 +120,9 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor_spd(const double* __r
   double* S = sm;              // r x r scaled matrix
   double* L = sm + r * r;      // r x r factor / eigenvectors
   double* scale = L + r * r;   // r
-  __shared__ int ok;
+  double* dd = scale + r;      // r remaining diagonal (pivoted path)
+  __shared__ int ok, rank, piv;
+  __shared__ int perm[kMaxRank];
   __shared__ double dmax;
   const int tid = threadIdx.x;
   for (int c = tid; c < r; c += blockDim.x) {
@@ -129,6 +131,7 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor_spd(const double* __r
     out->lambda[c] = lam;
     scale[c] = normalize ? (lam > 0.0 ? 1.0 / lam : 0.0) : 1.0;
     out->scale[c] = scale[c];
+    perm[c] = c;
   }
   __syncthreads();
   for (int i = tid; i < r * r; i += blockDim.x) {
@@ -140,12 +143,63 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor_spd(const double* __r
   }
   if (tid == 0) {
     ok = 1;
+    rank = r;
     double m = 0.0;
     for (int c = 0; c < r; ++c) m = fmax(m, G[c * r + c] * scale[c] * scale[c]);
     dmax = m;
   }
   __syncthreads();
-  // right-looking-free Cholesky, column by column (row i > j in parallel)
+  if (pivot) {
+    // Cholesky with diagonal pivoting of P^T S P; stops at the numerical rank.
+    for (int j = 0; j < r; ++j) {
+      for (int i = j + tid; i < r; i += blockDim.x) {
+        double d = S[perm[i] * r + perm[i]];
+        for (int c = 0; c < j; ++c) d -= L[i * r + c] * L[i * r + c];
+        dd[i] = d;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        int p = j;
+        for (int i = j + 1; i < r; ++i)
+          if (dd[i] > dd[p]) p = i;
+        if (!(dd[p] > rel_tol * dmax)) {
+          rank = j;
+        } else {
+          if (p != j) {
+            const int t = perm[j];
+            perm[j] = perm[p];
+            perm[p] = t;
+            for (int c = 0; c < j; ++c) {
+              const double x = L[j * r + c];
+              L[j * r + c] = L[p * r + c];
+              L[p * r + c] = x;
+            }
+          }
+          L[j * r + j] = sqrt(dd[p]);
+        }
+        piv = p;
+      }
+      __syncthreads();
+      if (rank == j) break;
+      const double ljj = L[j * r + j];
+      for (int i = j + 1 + tid; i < r; i += blockDim.x) {
+        double t = S[perm[i] * r + perm[j]];
+        for (int c = 0; c < j; ++c) t -= L[i * r + c] * L[j * r + c];
+        L[i * r + j] = t / ljj;
+      }
+      __syncthreads();
+    }
+    for (int i = tid; i < r * r; i += blockDim.x) out->F[i] = L[i];
+    for (int c = tid; c < r; c += blockDim.x) out->perm[c] = perm[c];
+    if (tid == 0) {
+      out->kind = 0;
+      out->rank = rank;
+      if (rank < r) atomicOr(warn, warn_bit);
+    }
+    (void)piv;
+    return;
+  }
+  // plain Cholesky, column by column (rows below the pivot in parallel)
   for (int j = 0; j < r; ++j) {
     if (tid == 0) {
       double s = S[j * r + j];
@@ -165,7 +219,11 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor_spd(const double* __r
   }
   if (ok) {
     for (int i = tid; i < r * r; i += blockDim.x) out->F[i] = L[i];
-    if (tid == 0) out->kind = 0;
+    for (int c = tid; c < r; c += blockDim.x) out->perm[c] = c;
+    if (tid == 0) {
+      out->kind = 0;
+      out->rank = r;
+    }
     return;
   }
   // pseudo-inverse from the eigendecomposition of S
@@ -178,6 +236,7 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor_spd(const double* __r
       scale[c] = ev > rel_tol * emax ? 1.0 / ev : 0.0;  // reuse as inverse eigenvalues
     }
     out->kind = 1;
+    out->rank = r;
     atomicOr(warn, warn_bit);
   }
   __syncthreads();
@@ -204,13 +263,16 @@ __global__ void __launch_bounds__(kRowThreads) k_lev_rows(const double* A, int64
   double* sc = F + r * r;                 // r
   double* lam = sc + r;                   // r
   double* xs = lam + r;                   // kRowThreads * (r + 1)
+  __shared__ int perm[kMaxRank];
   const int ld = r + 1;
   for (int i = threadIdx.x; i < r * r; i += blockDim.x) F[i] = f->F[i];
   for (int i = threadIdx.x; i < r; i += blockDim.x) {
     sc[i] = f->scale[i];
     lam[i] = f->lambda[i];
+    perm[i] = f->perm[i];
   }
   const int kind = f->kind;
+  const int rank = f->rank;
   uint64_t my_max = 0;
   uint32_t my_nz = 0;
   for (int64_t row0 = (int64_t)blockIdx.x * kRowThreads; row0 < n;
@@ -226,12 +288,15 @@ __global__ void __launch_bounds__(kRowThreads) k_lev_rows(const double* A, int64
       double* x = xs + threadIdx.x * ld;
       double l = 0.0;
       if (kind == 0) {
-        // y = L^{-1} (S a): forward substitution in place, l = ||y||^2
-        for (int c = 0; c < r; ++c) {
-          double t = x[c] * sc[c];
-          for (int u = 0; u < c; ++u) t -= F[c * r + u] * x[u];
+        // y = L^{-1} P^T (S a) over the first `rank` pivots, l = ||y||^2; y is kept
+        // in the spare column block of the thread's own row (x[r] is free)
+        for (int c = 0; c < r; ++c) x[c] *= sc[c];
+        double* y = xs + (size_t)kRowThreads * ld + threadIdx.x * ld;
+        for (int c = 0; c < rank; ++c) {
+          double t = x[perm[c]];
+          for (int u = 0; u < c; ++u) t -= F[c * r + u] * y[u];
           t = t / F[c * r + c];
-          x[c] = t;
+          y[c] = t;
           l += t * t;
         }
       } else {
@@ -355,17 +420,17 @@ int gram_rows(const double* A, int64_t n, int r, double* G, cudaStream_t st) {
   return CPA_OK;
 }
 
-int factor_spd(const double* G, int r, int normalize, double rel_tol, SmallFactor* out, int* warn,
-               int warn_bit, cudaStream_t st) {
+int factor_spd(const double* G, int r, int normalize, int pivot, double rel_tol, SmallFactor* out,
+               int* warn, int warn_bit, cudaStream_t st) {
   if (r < 1 || r > kMaxRank) return CPA_ERR_ARG;
-  const size_t smem = sizeof(double) * (2 * r * r + r);
+  const size_t smem = sizeof(double) * (2 * r * r + 2 * r);
   static bool attr_done = false;
   if (!attr_done) {
     CPA_CUDA_TRY(cudaFuncSetAttribute(k_factor_spd, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(sizeof(double) * (2 * kMaxRank * kMaxRank + kMaxRank))));
+                                      (int)(sizeof(double) * (2 * kMaxRank * kMaxRank + 2 * kMaxRank))));
     attr_done = true;
   }
-  k_factor_spd<<<1, kFactorThreads, smem, st>>>(G, r, normalize, rel_tol, out, warn, warn_bit);
+  k_factor_spd<<<1, kFactorThreads, smem, st>>>(G, r, normalize, pivot, rel_tol, out, warn, warn_bit);
   CPA_LAUNCH_CHECK();
   return CPA_OK;
 }
@@ -374,12 +439,12 @@ int lev_rows(const double* A, int64_t n, int r, const SmallFactor* f, double* le
              DistInfo* info, double* A_out, cudaStream_t st) {
   if (r < 1 || r > kMaxRank) return CPA_ERR_ARG;
   if (n <= 0) return CPA_OK;
-  const size_t smem = sizeof(double) * ((size_t)r * r + 2 * r + (size_t)kRowThreads * (r + 1));
+  const size_t smem = sizeof(double) * ((size_t)r * r + 2 * r + 2 * (size_t)kRowThreads * (r + 1));
   static bool attr = false;
   if (!attr) {
     CPA_CUDA_TRY(cudaFuncSetAttribute(k_lev_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(sizeof(double) * (kMaxRank * kMaxRank + 2 * kMaxRank +
-                                                              kRowThreads * (kMaxRank + 1)))));
+                                                              2 * kRowThreads * (kMaxRank + 1)))));
     attr = true;
   }
   const unsigned grid = grid_cap(ceil_div(n, kRowThreads), 8);

@@ -8,7 +8,9 @@
 namespace cpa {
 
 // Result of factoring an r x r symmetric positive semidefinite matrix G.
-// kind 0: F holds the lower Cholesky factor of S G S (row-major), S = diag(scale).
+// kind 0: F holds the lower Cholesky factor L of P^T (S G S) P (row-major), the
+//         first `rank` columns only when pivoting found G singular; P is the
+//         permutation perm (identity without pivoting), S = diag(scale).
 // kind 1: F holds the pseudo-inverse of S G S.
 // With normalize = 1, scale_c = 1/sqrt(G_cc) (0 for a zero column) and lambda_c =
 // sqrt(G_cc); otherwise scale = 1, lambda = sqrt(G_cc).  gram holds S G S.
@@ -17,8 +19,10 @@ struct SmallFactor {
   double gram[kMaxRank * kMaxRank];
   double scale[kMaxRank];
   double lambda[kMaxRank];
+  int perm[kMaxRank];
   int kind;
-  int pad[3];
+  int rank;
+  int pad[2];
 };
 
 // Per-mode fixed-point distribution summary (device).
@@ -33,10 +37,13 @@ struct DistInfo {
 int gram_rows(const double* A, int64_t n, int r, double* G, cudaStream_t st);
 
 // Factor G (see SmallFactor).  rel_tol: a Cholesky pivot must exceed rel_tol times
-// the largest diagonal entry; otherwise the pseudo-inverse (eigenvalues above
-// rel_tol * largest) is used and `warn_bit` is OR-ed into *warn.
-int factor_spd(const double* G, int r, int normalize, double rel_tol, SmallFactor* out,
-               int* warn, int warn_bit, cudaStream_t st);
+// the largest diagonal entry.  pivot = 0: plain Cholesky; if a pivot fails, the
+// pseudo-inverse (eigenvalues above rel_tol * largest) is used.  pivot = 1:
+// diagonal pivoting (largest remaining diagonal first) stops at the numerical rank,
+// which is exact for leverage scores of rank-deficient matrices.  Either way a
+// singular G OR-s `warn_bit` into *warn.
+int factor_spd(const double* G, int r, int normalize, int pivot, double rel_tol,
+               SmallFactor* out, int* warn, int warn_bit, cudaStream_t st);
 
 // For every row a_i of A: lev_i = || L^{-1} S a_i ||^2 (kind 0) or a_i^T S F S a_i
 // (kind 1); q_i = round-half-even(2^62 lev_i / r) written to q (if non-null),

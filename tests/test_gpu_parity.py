@@ -127,10 +127,15 @@ def test_skrp_lev_bit_exact(case):
 
 
 def test_skrp_reject_limit():
-    levs = _levs([3, 3], 1, 5, 1.0)
+    # four heavy multi-indices hold all but ~1e-12 of the probability and are
+    # deterministic; the light ones stay random, so almost every draw is rejected
+    lev = np.array([0.5, 0.5 - 1e-12, 1e-12])
     with pytest.raises(cpa.CpaError) as e:
-        cpa.cpa_skrp_lev([cu(l) for l in levs], 1, samples=20, tau=1e-9, reject_cap=40)
+        cpa.cpa_skrp_lev([cu(lev), cu(lev)], 1, samples=20, tau=1e-9, reject_cap=40)
     assert e.value.code == -5
+    with pytest.raises(oracle.OracleError) as e2:
+        oracle.skrp_lev([oracle.ModeDist(lev, 1)] * 2, 20, 1e-9, 0, 0, 0, reject_cap=40)
+    assert e2.value.code == oracle.ERR_REJECT_LIMIT
 
 
 def test_skrp_det_cap():
@@ -291,7 +296,8 @@ def test_small_planted_hybrid():
     assert res.stats["sdet_last"] > 0
 
 
-@pytest.mark.parametrize("dims,nnz,r,s", [((37, 29, 41, 13), 20000, 6, 3000), ((40, 30, 20), 8000, 3, 500)])
+@pytest.mark.parametrize("dims,nnz,r,s", [((37, 29, 41, 13), 20000, 6, 3000), ((40, 30, 20), 8000, 3, 500),
+                                          ((30, 4, 20), 1500, 5, 400)])  # n_1 < r: rank-deficient factor
 def test_ragged_runs(dims, nnz, r, s):
     coo = synth.random_sparse_tensor(dims, nnz, seed=5)
     _compare_run(coo, r, s, 1.0 / s, 3, seed=9)
