@@ -212,6 +212,21 @@ int cpa_philox4x64(const uint64_t* ctr, const uint64_t* key, int64_t n, uint64_t
  *   A (device) n x r row-major doubles; lev (device) n doubles; 1 <= r <= 64. */
 int cpa_leverage(const double* A, int64_t n, int32_t r, double* lev, void* stream);
 
+/* The leverage scores of cpa_leverage, computed without allocating any memory.
+ * This entry point has no counterpart in the paper.  It is for callers that may not
+ * allocate device memory while running (for example a process that reserves the
+ * GPU's memory for its own pool at start-up, or a latency-critical loop where
+ * cudaMalloc/cudaFree would synchronise the device): they pass only A and lev.
+ *   A (device) n x r row-major doubles; lev (device) n doubles out;
+ *   1 <= r <= 64 (r > 64 returns CPA_ERR_UNSUPPORTED: the scratch holds r <= 64).
+ * Its scratch (the r x r Gram, its factorisation, a warning word) is a 128 KiB
+ * device array in the library, present on every GPU that loads the library until
+ * the process exits.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array: calls whose work overlaps on a GPU race on it.
+ * Same results, warnings and errors as cpa_leverage otherwise. */
+int cpa_leverage_noalloc(const double* A, int64_t n, int32_t r, double* lev, void* stream);
+
 /* Fixed-point sampling distribution of one mode (Lemma 5.3 draws
  * i ~ Multinomial(l/r)): q_i = round-half-even(2^62 * (lev_i / r)) and the inclusive
  * prefix sums C_i = q_0 + ... + q_i (device, n words).  info (host, 3 words) gets

@@ -38,7 +38,7 @@ FIT_EXACT = 1
 EXPORTED = [
     "cpa_options_default", "cpa_strerror", "cpa_index_build", "cpa_index_free", "cpa_index_info",
     "cpa_index_export", "cp_arls_lev", "cp_arls_lev_coo", "cpa_philox4x64", "cpa_leverage",
-    "cpa_cdf", "cpa_skrp_lev", "cpa_sampled_mttkrp", "cpa_solve", "cpa_fit",
+    "cpa_cdf", "cpa_skrp_lev", "cpa_sampled_mttkrp", "cpa_solve", "cpa_fit", "cpa_leverage_noalloc",
 ]
 
 
@@ -115,6 +115,7 @@ def _declare(lib):
         "cp_arls_lev_coo": ([P, P, P, P, I32, P, P], I32),
         "cpa_philox4x64": ([P, P, I64, P, P], I32),
         "cpa_leverage": ([P, I64, I32, P, P], I32),
+        "cpa_leverage_noalloc": ([P, I64, I32, P, P], I32),
         "cpa_cdf": ([P, I64, I32, P, P, P], I32),
         "cpa_skrp_lev": ([I32, P, P, I32, P, I32, U64, P, P, P, P, P], I32),
         "cpa_sampled_mttkrp": ([P, I32, P, I32, P, P, I64, P, P, P, P], I32),
@@ -329,6 +330,18 @@ def cpa_leverage(A):
     n, r = A.shape
     lev = torch.empty(n, dtype=torch.float64, device="cuda")
     rc = _check(_lib().cpa_leverage(_ptr(A), n, r, _ptr(lev), _stream()), "cpa_leverage")
+    return lev, rc
+
+
+def cpa_leverage_noalloc(A, lev=None):
+    """cpa_leverage without any device allocation inside the library (the caller
+    supplies the output ``lev``; the library's scratch is a fixed device array)."""
+    torch = _torch()
+    A = A.to(device="cuda", dtype=torch.float64).contiguous()
+    n, r = A.shape
+    if lev is None:
+        lev = torch.empty(n, dtype=torch.float64, device="cuda")
+    rc = _check(_lib().cpa_leverage_noalloc(_ptr(A), n, r, _ptr(lev), _stream()), "cpa_leverage_noalloc")
     return lev, rc
 
 
