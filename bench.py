@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-launch-count", action="store_true",
+                   help="skip counting kernels with the torch profiler (use under ncu)")
     p.add_argument("--cpu-sample-updates", type=int, default=4,
                    help="mode updates the CPU baseline times (bounded sample)")
     return p.parse_args()
@@ -237,7 +239,7 @@ def main():
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    launches_per_step = count_launches(lambda: step())
+    launches_per_step = None if args.no_launch_count else count_launches(lambda: step())
     clocks = ClockSampler(local)
     clocks.start()
     times, stages, nnz_tot, sbar_tot = [], np.zeros(8), 0, 0
@@ -260,6 +262,7 @@ def main():
         stat_acc["sbar_total"] += st["sbar_total"]
         stat_acc["nnz_sampled_total"] += st["nnz_sampled_total"]
         fits.append(res.fit)
+        last_stats = st
     torch.cuda.synchronize()
     clk = clocks.stop()
     total_ms = sum(times)
@@ -293,6 +296,8 @@ def main():
         "stages_ms_per_update": {nm: float(stages[i] / n_updates) for i, nm in enumerate(stage_names)},
         "stage_share": stage_share,
         "nnz_sampled_per_update": stat_acc["nnz_sampled_total"] / n_updates,
+        "last_update": {k: last_stats.get(k) for k in ("sdet_last", "pdet_last", "attempts_last", "sbar_last",
+                                                       "nnz_sampled_last")},
         "sbar_per_update": stat_acc["sbar_total"] / n_updates,
         "fit": fits[-1] if fits else None,
         "clocks": clk,

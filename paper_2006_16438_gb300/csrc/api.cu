@@ -8,6 +8,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "fit.cuh"
 #include "sample.cuh"
@@ -119,8 +120,8 @@ struct DevBuf {
 
 // Leverage distribution of one factor: lev (optional), CDF C, info; A normalised in
 // place when `normalize_out` (the update path), untouched otherwise.
-int refresh_distribution(double* A, int64_t n, int r, uint64_t* C, DistInfo* info, double* GA,
-                         SmallFactor* fac, int* warn, void* scan_scratch, bool normalize_out,
+int refresh_distribution(double* A, int64_t n, int r, uint64_t* C, DistInfo* info, double* Pm,
+                         double* GA, SmallFactor* fac, int* warn, void* scan_scratch, bool normalize_out,
                          double* lev_out, cudaStream_t st) {
   CPA_CUDA_TRY(cudaMemsetAsync(GA, 0, sizeof(double) * r * r, st));
   CPA_TRY(gram_rows(A, n, r, GA, st));
@@ -128,6 +129,7 @@ int refresh_distribution(double* A, int64_t n, int r, uint64_t* C, DistInfo* inf
   CPA_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(DistInfo), st));
   CPA_TRY(lev_rows(A, n, r, fac, lev_out, C, info, normalize_out ? A : nullptr, st));
   CPA_TRY(cdf_from_q(C, C, n, info, scan_scratch, st));
+  CPA_TRY(phat_from_cdf(C, n, info, Pm, st));
   return CPA_OK;
 }
 
@@ -137,9 +139,21 @@ struct Profiler {
   cudaStream_t st = nullptr;
   std::vector<cudaEvent_t> ev;
   std::vector<int> stage_of;  // stage of the interval ending at event i (-1: none)
+  std::vector<cudaEvent_t> pool;  // created ahead of a stream capture
+  void reserve(int n) {
+    for (int i = 0; i < n; ++i) {
+      cudaEvent_t e = nullptr;
+      if (cudaEventCreate(&e) == cudaSuccess) pool.push_back(e);
+    }
+  }
   cudaEvent_t make() {
     cudaEvent_t e = nullptr;
-    cudaEventCreate(&e);
+    if (!pool.empty()) {
+      e = pool.back();
+      pool.pop_back();
+    } else {
+      cudaEventCreate(&e);
+    }
     ev.push_back(e);
     stage_of.push_back(-1);
     return e;
@@ -149,7 +163,7 @@ struct Profiler {
     if (!on) return CPA_OK;
     cudaEvent_t e = make();
     stage_of.back() = stage;
-    CPA_CUDA_TRY(cudaEventRecord(e, st));
+    CPA_CUDA_TRY(record_event(e, st));
     return CPA_OK;
   }
   // an event for the caller to record later (it ends an interval of `stage`)
@@ -159,7 +173,8 @@ struct Profiler {
     stage_of.back() = stage;
     return e;
   }
-  void collect(cpa_stats* s) {
+  // add the intervals between consecutive marks to s->stage_ms
+  void collect_add(cpa_stats* s) {
     if (!on || !s) return;
     for (size_t i = 1; i < ev.size(); ++i) {
       if (stage_of[i] < 0) continue;
@@ -169,14 +184,10 @@ struct Profiler {
         s->stage_launches[stage_of[i]] += 1;
       }
     }
-    if (ev.size() >= 2) {
-      float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, ev.front(), ev.back()) == cudaSuccess) s->stage_ms[6] = ms;
-      s->stage_launches[6] = 1;
-    }
   }
   ~Profiler() {
     for (auto e : ev) cudaEventDestroy(e);
+    for (auto e : pool) cudaEventDestroy(e);
   }
 };
 
@@ -193,6 +204,324 @@ int check_options(const cpa_options* o) {
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------------------
+// Plan: the workspace of cp_arls_lev for one (index, rank, s, tau, ...) and the
+// instantiated CUDA graph of one outer iteration (every mode updated once).  The
+// Philox iteration lives in device memory and the graph advances it, so the graph
+// is replayed unchanged for every iteration and every later call.
+// ---------------------------------------------------------------------------
+namespace cpa {
+
+__global__ void k_advance_iter(uint64_t* it) { *it += 1; }
+
+struct Plan {
+  // key
+  int r = 0, D = 0, reject_cap = 0, profile = 0;
+  int64_t s = 0, det_cap = 0, det_buf = 0;
+  double tau = 0.0;
+  uint64_t seed = 0;
+  // workspace
+  char* base = nullptr;
+  double* Fm[kMaxOrder] = {};
+  uint64_t* Cm[kMaxOrder] = {};
+  double* Pm[kMaxOrder] = {};
+  DistInfo* info = nullptr;
+  double *M = nullptr, *Gs = nullptr, *GA = nullptr, *lam = nullptr, *fitd = nullptr, *fit_ws = nullptr;
+  SmallFactor *fsolve = nullptr, *flev = nullptr;
+  int* warn = nullptr;
+  DevStats* dstats = nullptr;
+  char* scan_ws = nullptr;
+  uint64_t* iter_dev = nullptr;
+  SampleBuffers SB[kMaxOrder];
+  MttkrpBuffers MB;
+  // graph of one outer iteration
+  bool use_graph = false;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  Profiler gprof;  // event nodes captured into the graph (profile = 1)
+
+  bool matches(const cpa_options* o) const {
+    return o->rank == r && o->samples == s && o->tau == tau && o->seed == seed &&
+           o->reject_cap == reject_cap && o->det_cap == det_cap && (o->profile != 0) == (profile != 0);
+  }
+
+  int init(const cpa_index* X, const cpa_options* o, cudaStream_t st) {
+    r = o->rank;
+    D = X->order;
+    s = o->samples;
+    tau = o->tau;
+    seed = o->seed;
+    reject_cap = o->reject_cap;
+    det_cap = o->det_cap;
+    profile = o->profile != 0;
+    det_buf = det_buffer_capacity(s, tau, det_cap);
+    use_graph = !(tau < 1.0 && tau * (double)s < 1.0);  // no top-s host sync possible
+    int64_t nmax = 1, nsum = 0;
+    for (int m = 0; m < D; ++m) {
+      nmax = std::max<int64_t>(nmax, X->dims[m]);
+      nsum += X->dims[m];
+    }
+    KeyLayout Lsum;
+    memset(&Lsum, 0, sizeof(Lsum));
+    Lsum.d = 1;
+    Lsum.n[0] = nsum;
+    Arena a;
+    for (int pass = 0; pass < 2; ++pass) {
+      a.used = 0;
+      for (int m = 0; m < D; ++m) {
+        Fm[m] = a.take<double>((size_t)X->dims[m] * r);
+        Cm[m] = a.take<uint64_t>(X->dims[m]);
+        Pm[m] = a.take<double>(X->dims[m]);
+      }
+      info = a.take<DistInfo>(kMaxOrder);
+      M = a.take<double>((size_t)nmax * r);
+      Gs = a.take<double>(r * r);
+      GA = a.take<double>(r * r);
+      lam = a.take<double>(kMaxRank);
+      fitd = a.take<double>(4);
+      fit_ws = a.take<double>(fit_buffers_bytes(D, r) / sizeof(double) + 1);
+      fsolve = a.take<SmallFactor>(1);
+      flev = a.take<SmallFactor>(1);
+      warn = a.take<int>(4);
+      dstats = a.take<DevStats>(1);
+      scan_ws = a.take<char>(scan_workspace(nmax));
+      iter_dev = a.take<uint64_t>(1);
+      sample_buffers_carve(a, Lsum, s, det_buf, &SB[0]);
+      mttkrp_buffers_carve(a, s, r, &MB);
+      if (pass == 0) {
+        if (cudaMalloc((void**)&a.base, a.used) != cudaSuccess) return CPA_ERR_OOM;
+        base = a.base;
+      }
+    }
+    // per-mode copies of the sample buffers differ only in the candidate offsets
+    for (int k = 0; k < D; ++k) {
+      SB[k] = SB[0];
+      const KeyLayout& L = X->mode[k].L;
+      int64_t off = 0;
+      for (int t = 0; t < L.d; ++t) {
+        SB[k].cand_off[t] = off;
+        off += L.n[t];
+      }
+      for (int t = L.d; t < kMaxOrder; ++t) SB[k].cand_off[t] = off;
+    }
+    CPA_CUDA_TRY(cudaMemsetAsync(SB[0].state, 0, sizeof(SampleState), st));
+    return CPA_OK;
+  }
+
+  // Enqueue one outer iteration: every mode updated once (Alg. 3 inner loop).
+  int enqueue_iteration(const cpa_index* X, Profiler& prof, cudaStream_t st) {
+    FactorPtrs F;
+    for (int m = 0; m < D; ++m) F.A[m] = Fm[m];
+    for (int k = 0; k < D; ++k) {
+      const auto& mode = X->mode[k];
+      SampleParams Ps;
+      memset(&Ps, 0, sizeof(Ps));
+      Ps.L = mode.L;
+      for (int t = 0; t < mode.L.d; ++t) {
+        Ps.D.C[t] = Cm[mode.L.mode[t]];
+        Ps.D.info[t] = info + mode.L.mode[t];
+        Ps.D.P[t] = Pm[mode.L.mode[t]];
+      }
+      Ps.s = s;
+      Ps.tau = tau;
+      Ps.seed = seed;
+      Ps.iter_ptr = iter_dev;
+      Ps.mode_k = k;
+      Ps.reject_cap = reject_cap;
+      Ps.det_cap = tau < 1.0 ? det_cap : 1;
+      Ps.det_buf = det_buf;
+      CPA_TRY(prof.mark(-1));
+      CPA_TRY(skrp_lev(Ps, SB[k], st, false));
+      CPA_TRY(prof.mark(0));
+      const int64_t nk = X->dims[k];
+      CPA_CUDA_TRY(cudaMemsetAsync(M, 0, sizeof(double) * nk * r, st));
+      CPA_CUDA_TRY(cudaMemsetAsync(Gs, 0, sizeof(double) * r * r, st));
+      cudaEvent_t mid = prof.pending(1);
+      CPA_TRY(sampled_mttkrp(X, k, F, r, SB[k].idx_packed, SB[k].wgt, DevCount{&SB[k].state->sbar, s}, M,
+                             Gs, MB, st, mid));
+      CPA_TRY(prof.mark(2));
+      CPA_TRY(factor_spd(Gs, r, 0, 0, 1e-13, fsolve, warn, CPA_WARN_SINGULAR_GRAM, st));
+      CPA_TRY(solve_rows(M, nk, r, fsolve, Fm[k], st));
+      CPA_TRY(prof.mark(3));
+      CPA_TRY(refresh_distribution(Fm[k], nk, r, Cm[k], info + k, Pm[k], GA, flev, warn, scan_ws, true,
+                                   nullptr, st));
+      k_copy_lambda<<<1, 64, 0, st>>>(flev, r, lam);
+      k_stats<<<1, 1, 0, st>>>(dstats, SB[k].state, MB.total, warn);
+      CPA_LAUNCH_CHECK();
+      CPA_TRY(prof.mark(4));
+    }
+    k_advance_iter<<<1, 1, 0, st>>>(iter_dev);
+    CPA_LAUNCH_CHECK();
+    return CPA_OK;
+  }
+
+  // Captured on a private stream (the legacy default stream cannot be captured);
+  // the graph is then launched on the caller's stream.
+  int capture(const cpa_index* X) {
+    cudaGraph_t g = nullptr;
+    if (!cap_stream) CPA_CUDA_TRY(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
+    gprof.on = profile != 0;
+    gprof.st = cap_stream;
+    if (gprof.on) gprof.reserve(6 * D);
+    CPA_CUDA_TRY(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
+    const int rc = enqueue_iteration(X, gprof, cap_stream);
+    const cudaError_t ec = cudaStreamEndCapture(cap_stream, &g);
+    if (rc < 0 || ec != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return rc < 0 ? rc : CPA_ERR_CUDA;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      exec = nullptr;
+      return CPA_ERR_CUDA;
+    }
+    return CPA_OK;
+  }
+
+  int run(const cpa_index* X, const cpa_options* opt, double* lambda, double* const* factors,
+          int32_t io_on_device, double* fit, cpa_stats* stats, cudaStream_t st);
+
+  ~Plan() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (base) {
+      cudaDeviceSynchronize();
+      cudaFree(base);
+    }
+  }
+};
+
+void plan_free(Plan* p) { delete p; }
+
+int Plan::run(const cpa_index* X, const cpa_options* opt, double* lambda, double* const* factors,
+              int32_t io_on_device, double* fit, cpa_stats* stats, cudaStream_t st) {
+  CPA_CUDA_TRY(cudaMemsetAsync(warn, 0, sizeof(int) * 4, st));
+  CPA_CUDA_TRY(cudaMemsetAsync(dstats, 0, sizeof(DevStats), st));
+  CPA_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(DistInfo) * kMaxOrder, st));
+  CPA_CUDA_TRY(cudaMemsetAsync(&SB[0].state->status, 0, sizeof(int), st));
+  const cudaMemcpyKind kin = io_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  for (int m = 0; m < D; ++m)
+    CPA_CUDA_TRY(cudaMemcpyAsync(Fm[m], factors[m], sizeof(double) * X->dims[m] * r, kin, st));
+  {
+    std::vector<double> ones(kMaxRank, 1.0);
+    const double nan4[4] = {NAN, NAN, NAN, NAN};
+    const uint64_t it0 = opt->iter_offset;
+    CPA_CUDA_TRY(cudaMemcpyAsync(lam, ones.data(), sizeof(double) * kMaxRank, cudaMemcpyHostToDevice, st));
+    CPA_CUDA_TRY(cudaMemcpyAsync(fitd, nan4, sizeof(nan4), cudaMemcpyHostToDevice, st));
+    CPA_CUDA_TRY(cudaMemcpyAsync(iter_dev, &it0, sizeof(it0), cudaMemcpyHostToDevice, st));
+    CPA_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  cudaEvent_t call0 = nullptr, call1 = nullptr;
+  if (profile) {
+    cudaEventCreate(&call0);
+    cudaEventCreate(&call1);
+    cudaEventRecord(call0, st);
+  }
+  // initial leverage distributions (Alg. 3: p_k <- l(A_k)/r for the initial guess)
+  for (int m = 0; m < D; ++m)
+    CPA_TRY(refresh_distribution(Fm[m], X->dims[m], r, Cm[m], info + m, Pm[m], GA, flev, warn, scan_ws,
+                                 false, nullptr, st));
+  if (use_graph && !exec) CPA_TRY(capture(X));
+  FactorPtrs F;
+  for (int m = 0; m < D; ++m) F.A[m] = Fm[m];
+  Profiler eprof;  // eager path
+  eprof.on = profile != 0;
+  eprof.st = st;
+  CPA_TRY(eprof.mark(-1));
+  cpa_stats acc;
+  memset(&acc, 0, sizeof(acc));
+  int iters_done = 0, epochs = 0, bad = 0;
+  double best = -INFINITY, fit_val = NAN;
+  const int eta = opt->epoch_len > 0 ? opt->epoch_len : 1;
+  int it = 0;
+  while (it < opt->iters) {
+    for (int l = 0; l < eta && it < opt->iters; ++l, ++it) {
+      if (use_graph) {
+        CPA_CUDA_TRY(cudaGraphLaunch(exec, st));
+        if (profile) {  // the captured events hold this replay's timestamps
+          CPA_CUDA_TRY(cudaStreamSynchronize(st));
+          gprof.collect_add(&acc);
+        }
+      } else {
+        CPA_TRY(enqueue_iteration(X, eprof, st));
+      }
+    }
+    iters_done = it;
+    if (opt->tol > 0.0 && opt->fit_mode == CPA_FIT_EXACT) {
+      CPA_TRY(eprof.mark(-1));
+      CPA_TRY(fit_enqueue(X, F, lam, r, fit_ws, fitd, st));
+      CPA_TRY(eprof.mark(5));
+      double f = 0.0;
+      int status = 0;
+      CPA_CUDA_TRY(cudaMemcpyAsync(&f, fitd, sizeof(double), cudaMemcpyDeviceToHost, st));
+      CPA_CUDA_TRY(cudaMemcpyAsync(&status, &SB[0].state->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CPA_CUDA_TRY(cudaStreamSynchronize(st));
+      if (status < 0) return status;
+      ++epochs;
+      fit_val = f;
+      if (f > best + opt->tol) {
+        best = f;
+        bad = 0;
+      } else if (++bad >= opt->patience) {
+        break;
+      }
+    }
+  }
+  if (!(opt->tol > 0.0) && opt->fit_mode == CPA_FIT_EXACT) {
+    CPA_TRY(eprof.mark(-1));
+    CPA_TRY(fit_enqueue(X, F, lam, r, fit_ws, fitd, st));
+    CPA_TRY(eprof.mark(5));
+    CPA_CUDA_TRY(cudaMemcpyAsync(&fit_val, fitd, sizeof(double), cudaMemcpyDeviceToHost, st));
+  }
+  if (profile) cudaEventRecord(call1, st);
+  int status = 0;
+  DevStats hs;
+  int hwarn = 0;
+  CPA_CUDA_TRY(cudaMemcpyAsync(&status, &SB[0].state->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CPA_CUDA_TRY(cudaMemcpyAsync(&hs, dstats, sizeof(hs), cudaMemcpyDeviceToHost, st));
+  CPA_CUDA_TRY(cudaMemcpyAsync(&hwarn, warn, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CPA_CUDA_TRY(cudaStreamSynchronize(st));
+  if (status < 0) return status;
+  const cudaMemcpyKind kout = io_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  for (int m = 0; m < D; ++m)
+    CPA_CUDA_TRY(cudaMemcpyAsync(factors[m], Fm[m], sizeof(double) * X->dims[m] * r, kout, st));
+  CPA_CUDA_TRY(cudaMemcpyAsync(lambda, lam, sizeof(double) * r, kout, st));
+  if (fit && io_on_device) CPA_CUDA_TRY(cudaMemcpyAsync(fit, fitd, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CPA_CUDA_TRY(cudaStreamSynchronize(st));
+  if (fit && !io_on_device) *fit = opt->fit_mode == CPA_FIT_EXACT ? fit_val : NAN;
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->iters_done = iters_done;
+    stats->mode_updates = iters_done * D;
+    stats->warnings = hwarn;
+    stats->epochs = epochs;
+    stats->sdet_last = hs.sdet_last;
+    stats->sbar_last = hs.sbar_last;
+    stats->nnz_sampled_last = hs.nnz_last;
+    stats->attempts_last = hs.attempts_last;
+    stats->pdet_last = hs.pdet_last;
+    stats->nnz_sampled_total = hs.nnz_total;
+    stats->sbar_total = hs.sbar_total;
+    if (profile) {
+      eprof.collect_add(stats);
+      for (int i = 0; i < 6; ++i) {
+        stats->stage_ms[i] += acc.stage_ms[i];
+        stats->stage_launches[i] += acc.stage_launches[i];
+      }
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, call0, call1) == cudaSuccess) stats->stage_ms[6] = ms;
+      stats->stage_launches[6] = 1;
+    }
+  }
+  if (call0) cudaEventDestroy(call0);
+  if (call1) cudaEventDestroy(call1);
+  return hwarn;
+}
+
+}  // namespace cpa
+
 
 extern "C" {
 
@@ -333,20 +662,25 @@ int cpa_skrp_lev(int32_t d, const int64_t* dims, const double* const* lev, int32
   if (!make_layout(d, dims, -1, &L)) return CPA_ERR_UNSUPPORTED;
   const int64_t s = opt->samples;
   const int64_t det_cap = opt->tau < 1.0 ? opt->det_cap : 1;
+  const int64_t det_buf = det_buffer_capacity(s, opt->tau, opt->det_cap);
   int64_t nmax = 1;
   for (int t = 0; t < d; ++t) nmax = std::max<int64_t>(nmax, dims[t]);
   DevBuf buf;
   Arena a;
   SampleBuffers B;
   uint64_t* Cs[kMaxOrder];
+  double* Ps[kMaxOrder];
   DistInfo* info = nullptr;
   char* scan_ws = nullptr;
   for (int pass = 0; pass < 2; ++pass) {
     a.used = 0;
-    for (int t = 0; t < d; ++t) Cs[t] = a.take<uint64_t>(dims[t]);
+    for (int t = 0; t < d; ++t) {
+      Cs[t] = a.take<uint64_t>(dims[t]);
+      Ps[t] = a.take<double>(dims[t]);
+    }
     info = a.take<DistInfo>(kMaxOrder);
     scan_ws = a.take<char>(scan_workspace(nmax));
-    sample_buffers_carve(a, L, s, det_cap, &B);
+    sample_buffers_carve(a, L, s, det_buf, &B);
     B.idx_linear = idx;
     if (pass == 0) {
       CPA_TRY(buf.alloc(a.used, st));
@@ -360,6 +694,7 @@ int cpa_skrp_lev(int32_t d, const int64_t* dims, const double* const* lev, int32
     k_q_from_lev<<<blocks(dims[t]), 256, 0, st>>>(lev[t], dims[t], r, Cs[t], info + t);
     CPA_LAUNCH_CHECK();
     CPA_TRY(cdf_from_q(Cs[t], Cs[t], dims[t], info + t, scan_ws, st));
+    CPA_TRY(phat_from_cdf(Cs[t], dims[t], info + t, Ps[t], st));
   }
   SampleParams P;
   memset(&P, 0, sizeof(P));
@@ -367,6 +702,7 @@ int cpa_skrp_lev(int32_t d, const int64_t* dims, const double* const* lev, int32
   for (int t = 0; t < d; ++t) {
     P.D.C[t] = Cs[t];
     P.D.info[t] = info + t;
+    P.D.P[t] = Ps[t];
   }
   P.s = s;
   P.tau = opt->tau;
@@ -375,7 +711,9 @@ int cpa_skrp_lev(int32_t d, const int64_t* dims, const double* const* lev, int32
   P.mode_k = mode_k;
   P.reject_cap = opt->reject_cap;
   P.det_cap = det_cap;
-  CPA_TRY(skrp_lev(P, B, st));
+  P.det_buf = det_buf;
+  P.iter_ptr = nullptr;
+  CPA_TRY(skrp_lev(P, B, st, true));
   SampleState h;
   CPA_CUDA_TRY(cudaMemcpyAsync(&h, B.state, sizeof(h), cudaMemcpyDeviceToHost, st));
   CPA_CUDA_TRY(cudaStreamSynchronize(st));
@@ -479,202 +817,48 @@ int cpa_fit(const cpa_index* X, const double* const* factors, const double* lamb
   return CPA_OK;
 }
 
-int cp_arls_lev(const cpa_index* X, const cpa_options* opt, double* lambda, double* const* factors,
+int cp_arls_lev(const cpa_index* Xc, const cpa_options* opt, double* lambda, double* const* factors,
                 int32_t io_on_device, double* fit, cpa_stats* stats) {
-  if (!X || !lambda || !factors) return CPA_ERR_ARG;
+  if (!Xc || !lambda || !factors) return CPA_ERR_ARG;
   CPA_TRY(check_options(opt));
+  cpa_index* X = const_cast<cpa_index*>(Xc);  // only the plan cache is modified
   const int D = X->order;
-  const int r = opt->rank;
-  const int64_t s = opt->samples;
-  const double tau = opt->tau;
-  const int64_t det_cap = tau < 1.0 ? opt->det_cap : 1;
-  cudaStream_t st = (cudaStream_t)opt->stream;
   for (int m = 0; m < D; ++m)
     if (!factors[m]) return CPA_ERR_ARG;
-  KeyLayout Lmax;  // candidate buffer must hold the largest sum of other-mode sizes
-  int64_t nmax = 1, nsum = 0;
-  for (int m = 0; m < D; ++m) {
-    nmax = std::max<int64_t>(nmax, X->dims[m]);
-    nsum += X->dims[m];
-  }
-  memset(&Lmax, 0, sizeof(Lmax));
-  Lmax.d = 1;
-  Lmax.n[0] = nsum;
-  // ---- workspace ----
-  DevBuf buf;
-  Arena a;
-  double* Fm[kMaxOrder];
-  uint64_t* Cm[kMaxOrder];
-  DistInfo* info = nullptr;
-  double *M = nullptr, *Gs = nullptr, *GA = nullptr, *lam = nullptr, *fitd = nullptr, *fit_ws = nullptr;
-  SmallFactor *fsolve = nullptr, *flev = nullptr;
-  int* warn = nullptr;
-  DevStats* dstats = nullptr;
-  char* scan_ws = nullptr;
-  SampleBuffers SB;
-  MttkrpBuffers MB;
-  for (int pass = 0; pass < 2; ++pass) {
-    a.used = 0;
-    for (int m = 0; m < D; ++m) {
-      Fm[m] = a.take<double>((size_t)X->dims[m] * r);
-      Cm[m] = a.take<uint64_t>(X->dims[m]);
+  cudaStream_t st = (cudaStream_t)opt->stream;
+  // a cached plan per index; a concurrent call on the same index gets its own
+  std::unique_lock<std::mutex> lock(X->plan_mu, std::try_to_lock);
+  Plan* own = nullptr;
+  Plan* P = nullptr;
+  if (lock.owns_lock()) {
+    if (X->plan && !X->plan->matches(opt)) {
+      plan_free(X->plan);
+      X->plan = nullptr;
     }
-    info = a.take<DistInfo>(kMaxOrder);
-    M = a.take<double>((size_t)nmax * r);
-    Gs = a.take<double>(r * r);
-    GA = a.take<double>(r * r);
-    lam = a.take<double>(kMaxRank);
-    fitd = a.take<double>(4);
-    fit_ws = a.take<double>(fit_buffers_bytes(D, r) / sizeof(double) + 1);
-    fsolve = a.take<SmallFactor>(1);
-    flev = a.take<SmallFactor>(1);
-    warn = a.take<int>(4);
-    dstats = a.take<DevStats>(1);
-    scan_ws = a.take<char>(scan_workspace(nmax));
-    sample_buffers_carve(a, Lmax, s, det_cap, &SB);
-    mttkrp_buffers_carve(a, s, r, &MB);
-    if (pass == 0) {
-      CPA_TRY(buf.alloc(a.used, st));
-      a.base = (char*)buf.p;
-    }
-  }
-  // SB.cand_off was computed for the single merged "mode"; per update it is reset below.
-  CPA_CUDA_TRY(cudaMemsetAsync(SB.state, 0, sizeof(SampleState), st));
-  CPA_CUDA_TRY(cudaMemsetAsync(warn, 0, sizeof(int) * 4, st));
-  CPA_CUDA_TRY(cudaMemsetAsync(dstats, 0, sizeof(DevStats), st));
-  CPA_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(DistInfo) * kMaxOrder, st));
-  const cudaMemcpyKind kin = io_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  for (int m = 0; m < D; ++m)
-    CPA_CUDA_TRY(cudaMemcpyAsync(Fm[m], factors[m], sizeof(double) * X->dims[m] * r, kin, st));
-  // initial leverage distributions (Alg. 3: p_k <- l(A_k)/r for the initial guess)
-  for (int m = 0; m < D; ++m)
-    CPA_TRY(refresh_distribution(Fm[m], X->dims[m], r, Cm[m], info + m, GA, flev, warn, scan_ws,
-                                 false, nullptr, st));
-  {
-    // lambda = 1 until the first solve; fit = NaN unless computed
-    std::vector<double> ones(kMaxRank, 1.0);
-    const double nan4[4] = {NAN, NAN, NAN, NAN};
-    CPA_CUDA_TRY(cudaMemcpyAsync(lam, ones.data(), sizeof(double) * kMaxRank, cudaMemcpyHostToDevice, st));
-    CPA_CUDA_TRY(cudaMemcpyAsync(fitd, nan4, sizeof(nan4), cudaMemcpyHostToDevice, st));
-    CPA_CUDA_TRY(cudaStreamSynchronize(st));
-  }
-  FactorPtrs F;
-  for (int m = 0; m < D; ++m) F.A[m] = Fm[m];
-  Profiler prof;
-  prof.on = opt->profile != 0;
-  prof.st = st;
-  CPA_TRY(prof.mark(-1));
-  int iters_done = 0, epochs = 0, bad = 0;
-  double best = -INFINITY, fit_val = NAN;
-  const int eta = opt->epoch_len > 0 ? opt->epoch_len : 1;
-  int it = 0;
-  while (it < opt->iters) {
-    for (int l = 0; l < eta && it < opt->iters; ++l, ++it) {
-      for (int k = 0; k < D; ++k) {
-        const auto& mode = X->mode[k];
-        SampleParams P;
-        memset(&P, 0, sizeof(P));
-        P.L = mode.L;
-        for (int t = 0; t < mode.L.d; ++t) {
-          P.D.C[t] = Cm[mode.L.mode[t]];
-          P.D.info[t] = info + mode.L.mode[t];
-          SB.cand_off[t] = 0;
-        }
-        {
-          int64_t off = 0;
-          for (int t = 0; t < mode.L.d; ++t) {
-            SB.cand_off[t] = off;
-            off += mode.L.n[t];
-          }
-          for (int t = mode.L.d; t < kMaxOrder; ++t) SB.cand_off[t] = off;
-        }
-        P.s = s;
-        P.tau = tau;
-        P.seed = opt->seed;
-        P.iter = opt->iter_offset + (uint64_t)it;
-        P.mode_k = k;
-        P.reject_cap = opt->reject_cap;
-        P.det_cap = det_cap;
-        CPA_TRY(prof.mark(-1));
-        CPA_TRY(skrp_lev(P, SB, st));
-        CPA_TRY(prof.mark(0));
-        const int64_t nk = X->dims[k];
-        CPA_CUDA_TRY(cudaMemsetAsync(M, 0, sizeof(double) * nk * r, st));
-        CPA_CUDA_TRY(cudaMemsetAsync(Gs, 0, sizeof(double) * r * r, st));
-        cudaEvent_t mid = prof.pending(1);
-        CPA_TRY(sampled_mttkrp(X, k, F, r, SB.idx_packed, SB.wgt, DevCount{&SB.state->sbar, s}, M, Gs,
-                               MB, st, mid));
-        CPA_TRY(prof.mark(2));
-        CPA_TRY(factor_spd(Gs, r, 0, 0, 1e-13, fsolve, warn, CPA_WARN_SINGULAR_GRAM, st));
-        CPA_TRY(solve_rows(M, nk, r, fsolve, Fm[k], st));
-        CPA_TRY(prof.mark(3));
-        CPA_TRY(refresh_distribution(Fm[k], nk, r, Cm[k], info + k, GA, flev, warn, scan_ws, true,
-                                     nullptr, st));
-        k_copy_lambda<<<1, 64, 0, st>>>(flev, r, lam);
-        k_stats<<<1, 1, 0, st>>>(dstats, SB.state, MB.total, warn);
-        CPA_LAUNCH_CHECK();
-        CPA_TRY(prof.mark(4));
+    if (!X->plan) {
+      X->plan = new (std::nothrow) Plan();
+      if (!X->plan) return CPA_ERR_OOM;
+      const int rc = X->plan->init(X, opt, st);
+      if (rc < 0) {
+        plan_free(X->plan);
+        X->plan = nullptr;
+        return rc;
       }
     }
-    iters_done = it;
-    if (opt->tol > 0.0 && opt->fit_mode == CPA_FIT_EXACT) {
-      CPA_TRY(prof.mark(-1));
-      CPA_TRY(fit_enqueue(X, F, lam, r, fit_ws, fitd, st));
-      CPA_TRY(prof.mark(5));
-      double f = 0.0;
-      int status = 0;
-      CPA_CUDA_TRY(cudaMemcpyAsync(&f, fitd, sizeof(double), cudaMemcpyDeviceToHost, st));
-      CPA_CUDA_TRY(cudaMemcpyAsync(&status, &SB.state->status, sizeof(int), cudaMemcpyDeviceToHost, st));
-      CPA_CUDA_TRY(cudaStreamSynchronize(st));
-      if (status < 0) return status;
-      ++epochs;
-      fit_val = f;
-      if (f > best + opt->tol) {
-        best = f;
-        bad = 0;
-      } else if (++bad >= opt->patience) {
-        break;
-      }
+    P = X->plan;
+  } else {
+    own = new (std::nothrow) Plan();
+    if (!own) return CPA_ERR_OOM;
+    const int rc = own->init(X, opt, st);
+    if (rc < 0) {
+      plan_free(own);
+      return rc;
     }
+    P = own;
   }
-  if (!(opt->tol > 0.0) && opt->fit_mode == CPA_FIT_EXACT) {
-    CPA_TRY(prof.mark(-1));
-    CPA_TRY(fit_enqueue(X, F, lam, r, fit_ws, fitd, st));
-    CPA_TRY(prof.mark(5));
-    CPA_CUDA_TRY(cudaMemcpyAsync(&fit_val, fitd, sizeof(double), cudaMemcpyDeviceToHost, st));
-  }
-  int status = 0;
-  DevStats hs;
-  CPA_CUDA_TRY(cudaMemcpyAsync(&status, &SB.state->status, sizeof(int), cudaMemcpyDeviceToHost, st));
-  CPA_CUDA_TRY(cudaMemcpyAsync(&hs, dstats, sizeof(hs), cudaMemcpyDeviceToHost, st));
-  int hwarn = 0;
-  CPA_CUDA_TRY(cudaMemcpyAsync(&hwarn, warn, sizeof(int), cudaMemcpyDeviceToHost, st));
-  CPA_CUDA_TRY(cudaStreamSynchronize(st));
-  if (status < 0) return status;
-  const cudaMemcpyKind kout = io_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  for (int m = 0; m < D; ++m)
-    CPA_CUDA_TRY(cudaMemcpyAsync(factors[m], Fm[m], sizeof(double) * X->dims[m] * r, kout, st));
-  CPA_CUDA_TRY(cudaMemcpyAsync(lambda, lam, sizeof(double) * r, kout, st));
-  if (fit && io_on_device)
-    CPA_CUDA_TRY(cudaMemcpyAsync(fit, fitd, sizeof(double), cudaMemcpyDeviceToDevice, st));
-  CPA_CUDA_TRY(cudaStreamSynchronize(st));
-  if (fit && !io_on_device) *fit = opt->fit_mode == CPA_FIT_EXACT ? fit_val : NAN;
-  if (stats) {
-    memset(stats, 0, sizeof(*stats));
-    stats->iters_done = iters_done;
-    stats->mode_updates = iters_done * D;
-    stats->warnings = hwarn;
-    stats->epochs = epochs;
-    stats->sdet_last = hs.sdet_last;
-    stats->sbar_last = hs.sbar_last;
-    stats->nnz_sampled_last = hs.nnz_last;
-    stats->attempts_last = hs.attempts_last;
-    stats->pdet_last = hs.pdet_last;
-    stats->nnz_sampled_total = hs.nnz_total;
-    stats->sbar_total = hs.sbar_total;
-    prof.collect(stats);
-  }
-  return hwarn;
+  const int rc = P->run(X, opt, lambda, factors, io_on_device, fit, stats, st);
+  if (own) plan_free(own);
+  return rc;
 }
 
 int cp_arls_lev_coo(const cpa_coo* coo, const cpa_options* opt, double* lambda, double* const* factors,

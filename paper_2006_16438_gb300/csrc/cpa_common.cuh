@@ -160,6 +160,16 @@ inline int num_sms() {
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// Record a timing event; inside a stream capture it becomes an event-record node of
+// the graph (cudaEventRecordExternal), so it is re-recorded at every replay.
+inline cudaError_t record_event(cudaEvent_t e, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t err = cudaStreamIsCapturing(st, &cs);
+  if (err != cudaSuccess) return err;
+  if (cs == cudaStreamCaptureStatusActive) return cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+  return cudaEventRecord(e, st);
+}
+
 // Count of items known only on the device (or a fixed host count if dptr is null).
 struct DevCount {
   const int64_t* dptr = nullptr;

@@ -1,7 +1,14 @@
 // Internal types and cross-file entry points of the CP-ARLS-LEV CUDA library.
 #pragma once
 
+#include <mutex>
+
 #include "cpa_common.cuh"
+
+namespace cpa {
+struct Plan;
+void plan_free(Plan* p);
+}  // namespace cpa
 
 // Opaque index of the C ABI (Section 5.3 fibre index, one per mode).
 struct cpa_index {
@@ -22,6 +29,9 @@ struct cpa_index {
     int dshift = 0;
   } mode[cpa::kMaxOrder];
   std::vector<void*> allocations;
+  // cached workspace + CUDA graph of one outer iteration (see api.cu)
+  cpa::Plan* plan = nullptr;
+  std::mutex plan_mu;
 };
 
 namespace cpa {

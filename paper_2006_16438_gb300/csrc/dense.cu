@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_rows(const double* __rest
 }
 
 // ---- r x r factorisation in one block -------------------------------------
-constexpr int kFactorThreads = 128;
+constexpr int kFactorThreads = 256;
 
 // Cyclic Jacobi eigendecomposition of the symmetric matrix in `a` (r x r,
 // overwritten by its eigenvalues on the diagonal), eigenvectors in the columns of
@@ -111,21 +111,39 @@ __device__ void jacobi_eigen_serial(double* a, double* v, int r) {
   }
 }
 
+// 1/sqrt(d) for d > 0 in FP64: FP32 seed, then two Newton steps
+// y <- y (3 - d y^2) / 2 in FP64 (about 24 -> 48 -> 96 correct bits).  GB300 FP64
+// division and square root cost hundreds of cycles each, so the factorisation keeps
+// them off its serial chain.
+__device__ __forceinline__ double rsqrt_newton(double d) {
+  double y = (double)rsqrtf((float)d);
+  if (!(y > 0.0) || isinf(y)) y = rsqrt(d);  // outside float range: library rsqrt
+  y = y * (1.5 - 0.5 * d * y * y);
+  y = y * (1.5 - 0.5 * d * y * y);
+  return y;
+}
+
+// Factor one r x r PSD matrix in one block (see SmallFactor):
+//  * right-looking Cholesky of S = diag(scale) G diag(scale), with diagonal pivoting
+//    (pivot = 1, stops at the numerical rank) or without (pivot = 0);
+//  * the inverse X = L^{-1} of the rank x rank factor by right-looking substitution;
+//  * pivot = 1: F = X (kind 0); pivot = 0: F = X^T X = S^{-1} (kind 2);
+//  * pivot = 0 and a pivot <= rel_tol * max diag: F = pinv(S) by Jacobi (kind 1).
 __global__ void __launch_bounds__(kFactorThreads) k_factor_spd(const double* __restrict__ G,
                                                                int r, int normalize, int pivot,
                                                                double rel_tol,
                                                                SmallFactor* __restrict__ out,
                                                                int* warn, int warn_bit) {
   extern __shared__ double sm[];
-  double* S = sm;              // r x r scaled matrix
-  double* L = sm + r * r;      // r x r factor / eigenvectors
-  double* scale = L + r * r;   // r
-  double* dd = scale + r;      // r remaining diagonal (pivoted path)
+  double* S = sm;              // r x r working matrix (L in its lower triangle)
+  double* X = sm + r * r;      // r x r inverse / eigenvectors
+  double* scale = X + r * r;   // r
+  double* y = scale + r;       // r: 1 / L_jj
   __shared__ int ok, rank, piv;
   __shared__ int perm[kMaxRank];
-  __shared__ double dmax;
-  const int tid = threadIdx.x;
-  for (int c = tid; c < r; c += blockDim.x) {
+  __shared__ double dmax, dcur;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int c = tid; c < r; c += nt) {
     const double g = G[c * r + c];
     const double lam = g > 0.0 ? sqrt(g) : 0.0;
     out->lambda[c] = lam;
@@ -134,183 +152,221 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor_spd(const double* __r
     perm[c] = c;
   }
   __syncthreads();
-  for (int i = tid; i < r * r; i += blockDim.x) {
-    const int a = i / r, b = i % r;
+  for (int i = tid; i < r * r; i += nt) {
+    const int a = i / r, b = i - a * r;
     const double v = G[i] * scale[a] * scale[b];
     S[i] = v;
     out->gram[i] = v;
-    L[i] = 0.0;
+    X[i] = 0.0;
   }
-  if (tid == 0) {
-    ok = 1;
-    rank = r;
+  __syncthreads();
+  if (tid < 32) {  // largest diagonal entry
     double m = 0.0;
-    for (int c = 0; c < r; ++c) m = fmax(m, G[c * r + c] * scale[c] * scale[c]);
-    dmax = m;
+    for (int c = tid; c < r; c += 32) m = fmax(m, S[c * r + c]);
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (tid == 0) {
+      dmax = m;
+      ok = 1;
+      rank = r;
+    }
   }
   __syncthreads();
-  if (pivot) {
-    // Cholesky with diagonal pivoting of P^T S P; stops at the numerical rank.
-    for (int j = 0; j < r; ++j) {
-      for (int i = j + tid; i < r; i += blockDim.x) {
-        double d = S[perm[i] * r + perm[i]];
-        for (int c = 0; c < j; ++c) d -= L[i * r + c] * L[i * r + c];
-        dd[i] = d;
-      }
-      __syncthreads();
-      if (tid == 0) {
-        int p = j;
-        for (int i = j + 1; i < r; ++i)
-          if (dd[i] > dd[p]) p = i;
-        if (!(dd[p] > rel_tol * dmax)) {
-          rank = j;
-        } else {
-          if (p != j) {
-            const int t = perm[j];
-            perm[j] = perm[p];
-            perm[p] = t;
-            for (int c = 0; c < j; ++c) {
-              const double x = L[j * r + c];
-              L[j * r + c] = L[p * r + c];
-              L[p * r + c] = x;
-            }
-          }
-          L[j * r + j] = sqrt(dd[p]);
-        }
-        piv = p;
-      }
-      __syncthreads();
-      if (rank == j) break;
-      const double ljj = L[j * r + j];
-      for (int i = j + 1 + tid; i < r; i += blockDim.x) {
-        double t = S[perm[i] * r + perm[j]];
-        for (int c = 0; c < j; ++c) t -= L[i * r + c] * L[j * r + c];
-        L[i * r + j] = t / ljj;
-      }
-      __syncthreads();
-    }
-    for (int i = tid; i < r * r; i += blockDim.x) out->F[i] = L[i];
-    for (int c = tid; c < r; c += blockDim.x) out->perm[c] = perm[c];
-    if (tid == 0) {
-      out->kind = 0;
-      out->rank = rank;
-      if (rank < r) atomicOr(warn, warn_bit);
-    }
-    (void)piv;
-    return;
-  }
-  // plain Cholesky, column by column (rows below the pivot in parallel)
   for (int j = 0; j < r; ++j) {
-    if (tid == 0) {
-      double s = S[j * r + j];
-      for (int c = 0; c < j; ++c) s -= L[j * r + c] * L[j * r + c];
-      if (!(s > rel_tol * dmax)) ok = 0;
-      else L[j * r + j] = sqrt(s);
+    if (tid < 32) {  // pivot choice and 1/sqrt of the pivot
+      int p = j;
+      if (pivot) {
+        double best = -1.0;
+        for (int i = j + tid; i < r; i += 32) {
+          const double d = S[i * r + i];
+          if (d > best) {
+            best = d;
+            p = i;
+          }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+          const int op = __shfl_xor_sync(0xffffffffu, p, o);
+          if (ob > best || (ob == best && op < p)) {
+            best = ob;
+            p = op;
+          }
+        }
+      }
+      const double d = S[p * r + p];
+      if (tid == 0) {
+        piv = p;
+        dcur = d;
+        if (!(d > rel_tol * dmax)) {
+          if (pivot) rank = j; else ok = 0;
+        } else {
+          y[j] = rsqrt_newton(d);
+        }
+      }
     }
     __syncthreads();
-    if (!ok) break;
-    const double ljj = L[j * r + j];
-    for (int i = j + 1 + tid; i < r; i += blockDim.x) {
-      double t = S[i * r + j];
-      for (int c = 0; c < j; ++c) t -= L[i * r + c] * L[j * r + c];
-      L[i * r + j] = t / ljj;
+    if (rank == j || !ok) break;
+    const int p = piv;
+    if (p != j) {  // symmetric swap of rows/columns j and p (includes computed L entries)
+      for (int c = tid; c < r; c += nt) {
+        const double t = S[j * r + c];
+        S[j * r + c] = S[p * r + c];
+        S[p * r + c] = t;
+      }
+      if (tid == 0) {
+        const int t = perm[j];
+        perm[j] = perm[p];
+        perm[p] = t;
+      }
+      __syncthreads();
+      for (int c = tid; c < r; c += nt) {
+        const double t = S[c * r + j];
+        S[c * r + j] = S[c * r + p];
+        S[c * r + p] = t;
+      }
+      __syncthreads();
+    }
+    const double yj = y[j];
+    for (int i = j + 1 + tid; i < r; i += nt) S[i * r + j] *= yj;  // column j of L
+    if (tid == 0) S[j * r + j] = dcur * yj;                        // L_jj = sqrt(d)
+    __syncthreads();
+    // trailing update of the lower triangle: S_ic -= L_ij L_cj for j < c <= i
+    const int m = r - j - 1;
+    const int npairs = m * (m + 1) / 2;
+    for (int q = tid; q < npairs; q += nt) {
+      // q -> (i, c) with c <= i, both offset by j + 1
+      int ii = (int)((sqrtf(8.0f * q + 1.0f) - 1.0f) * 0.5f);
+      while ((ii + 1) * (ii + 2) / 2 <= q) ++ii;
+      while (ii * (ii + 1) / 2 > q) --ii;
+      const int cc = q - ii * (ii + 1) / 2;
+      const int i = ii + j + 1, c = cc + j + 1;
+      const double v = S[i * r + c] - S[i * r + j] * S[c * r + j];
+      S[i * r + c] = v;
+      if (c != i) S[c * r + i] = v;  // keep the trailing block symmetric for swaps
     }
     __syncthreads();
   }
-  if (ok) {
-    for (int i = tid; i < r * r; i += blockDim.x) out->F[i] = L[i];
-    for (int c = tid; c < r; c += blockDim.x) out->perm[c] = c;
+  if (!ok) {  // plain Cholesky failed: pseudo-inverse from the eigendecomposition
+    for (int i = tid; i < r * r; i += nt) {
+      const int a = i / r, b = i - a * r;
+      S[i] = G[i] * scale[a] * scale[b];
+    }
+    __syncthreads();
+    if (tid == 0) {
+      jacobi_eigen_serial(S, X, r);
+      double emax = 0.0;
+      for (int c = 0; c < r; ++c) emax = fmax(emax, fabs(S[c * r + c]));
+      for (int c = 0; c < r; ++c) {
+        const double ev = S[c * r + c];
+        y[c] = ev > rel_tol * emax ? 1.0 / ev : 0.0;
+      }
+      out->kind = 1;
+      out->rank = r;
+      atomicOr(warn, warn_bit);
+    }
+    __syncthreads();
+    for (int i = tid; i < r * r; i += nt) {
+      const int a = i / r, b = i - a * r;
+      double s2 = 0.0;
+      for (int c = 0; c < r; ++c) s2 += X[a * r + c] * y[c] * X[b * r + c];
+      out->F[i] = s2;
+    }
+    for (int c = tid; c < r; c += nt) out->perm[c] = c;
+    return;
+  }
+  const int k = rank;
+  // X = L^{-1} (k x k), right-looking: row i of X is final once the rows above are
+  // folded in; y holds 1/L_ii.  X starts at zero and accumulates -sum L_iu X_uc.
+  for (int i = 0; i < k; ++i) {
+    const double yi = y[i];
+    for (int c = tid; c <= i; c += nt) X[i * r + c] = ((i == c ? 1.0 : 0.0) - X[i * r + c]) * yi;
+    __syncthreads();
+    const int rows = k - i - 1, cols = i + 1;
+    for (int q = tid; q < rows * cols; q += nt) {
+      const int i2 = i + 1 + q / cols, c = q % cols;
+      X[i2 * r + c] += S[i2 * r + i] * X[i * r + c];
+    }
+    __syncthreads();
+  }
+  if (pivot) {
+    for (int i = tid; i < r * r; i += nt) out->F[i] = X[i];
+    for (int c = tid; c < r; c += nt) out->perm[c] = perm[c];
     if (tid == 0) {
       out->kind = 0;
-      out->rank = r;
+      out->rank = k;
+      if (k < r) atomicOr(warn, warn_bit);
     }
     return;
   }
-  // pseudo-inverse from the eigendecomposition of S
-  if (tid == 0) {
-    jacobi_eigen_serial(S, L, r);
-    double emax = 0.0;
-    for (int c = 0; c < r; ++c) emax = fmax(emax, fabs(S[c * r + c]));
-    for (int c = 0; c < r; ++c) {
-      const double ev = S[c * r + c];
-      scale[c] = ev > rel_tol * emax ? 1.0 / ev : 0.0;  // reuse as inverse eigenvalues
-    }
-    out->kind = 1;
-    out->rank = r;
-    atomicOr(warn, warn_bit);
+  // F = X^T X = (L L^T)^{-1}
+  for (int i = tid; i < r * r; i += nt) {
+    const int a = i / r, b = i - a * r;
+    const int u0 = a > b ? a : b;
+    double s2 = 0.0;
+    for (int u = u0; u < r; ++u) s2 = fma(X[u * r + a], X[u * r + b], s2);
+    out->F[i] = s2;
   }
-  __syncthreads();
-  for (int i = tid; i < r * r; i += blockDim.x) {
-    const int a = i / r, b = i % r;
-    double s = 0.0;
-    for (int c = 0; c < r; ++c) s += L[a * r + c] * scale[c] * L[b * r + c];
-    out->F[i] = s;
+  for (int c = tid; c < r; c += nt) out->perm[c] = c;
+  if (tid == 0) {
+    out->kind = 2;
+    out->rank = r;
   }
 }
 
-// ---- per-row kernels: a block stages kRowThreads rows in shared memory ------
-// (coalesced), each thread then works on its own row with runtime loops over r;
-// the row stride r + 1 keeps the per-thread accesses spread over the banks.
-constexpr int kRowThreads = 128;
+// ---- per-row kernels -------------------------------------------------------
+constexpr int kRowThreads = 256;
 
+// Leverage of row a_i (one warp per row, lane c owns coordinate c and c + 32):
+// kind 0: y = X P^T (S a), l = ||y||^2 over the rank's coordinates;
+// kind 1: l = (S a)^T F (S a).
 __global__ void __launch_bounds__(kRowThreads) k_lev_rows(const double* A, int64_t n, int r,
                                                           const SmallFactor* __restrict__ f,
                                                           double* __restrict__ lev,
                                                           uint64_t* __restrict__ q,
                                                           DistInfo* info, double* A_out) {
   extern __shared__ double smem[];
-  double* F = smem;                       // r * r
-  double* sc = F + r * r;                 // r
-  double* lam = sc + r;                   // r
-  double* xs = lam + r;                   // kRowThreads * (r + 1)
+  double* F = smem;       // r * r
+  double* sc = F + r * r; // r
+  double* lam = sc + r;   // r
   __shared__ int perm[kMaxRank];
-  const int ld = r + 1;
   for (int i = threadIdx.x; i < r * r; i += blockDim.x) F[i] = f->F[i];
   for (int i = threadIdx.x; i < r; i += blockDim.x) {
     sc[i] = f->scale[i];
     lam[i] = f->lambda[i];
     perm[i] = f->perm[i];
   }
+  __syncthreads();
   const int kind = f->kind;
-  const int rank = f->rank;
+  const int k = kind == 0 ? f->rank : r;
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * kRowThreads + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * kRowThreads) >> 5;
   uint64_t my_max = 0;
   uint32_t my_nz = 0;
-  for (int64_t row0 = (int64_t)blockIdx.x * kRowThreads; row0 < n;
-       row0 += (int64_t)gridDim.x * kRowThreads) {
-    const int rows = (int)(n - row0 < kRowThreads ? n - row0 : kRowThreads);
-    __syncthreads();
-    for (int i = threadIdx.x; i < rows * r; i += kRowThreads) {
-      const int rr = i / r, c = i - rr * r;
-      xs[rr * ld + c] = A[row0 * r + i];
-    }
-    __syncthreads();
-    if (threadIdx.x < rows) {
-      double* x = xs + threadIdx.x * ld;
-      double l = 0.0;
-      if (kind == 0) {
-        // y = L^{-1} P^T (S a) over the first `rank` pivots, l = ||y||^2; y is kept
-        // in the spare column block of the thread's own row (x[r] is free)
-        for (int c = 0; c < r; ++c) x[c] *= sc[c];
-        double* y = xs + (size_t)kRowThreads * ld + threadIdx.x * ld;
-        for (int c = 0; c < rank; ++c) {
-          double t = x[perm[c]];
-          for (int u = 0; u < c; ++u) t -= F[c * r + u] * y[u];
-          t = t / F[c * r + c];
-          y[c] = t;
-          l += t * t;
-        }
-      } else {
-        for (int c = 0; c < r; ++c) x[c] *= sc[c];
-        for (int c = 0; c < r; ++c) {
-          double t = 0.0;
-          for (int u = 0; u < r; ++u) t += F[c * r + u] * x[u];
-          l += x[c] * t;
+  for (int64_t row = gw; row < n; row += nwarps) {
+    const double* a = A + row * r;
+    double part = 0.0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int c = lane + 32 * h;
+      if (c < k) {
+        double t = 0.0;
+        if (kind == 0) {
+          for (int u = 0; u <= c; ++u) {
+            const int pu = perm[u];
+            t = fma(F[c * r + u], a[pu] * sc[pu], t);
+          }
+          part = fma(t, t, part);
+        } else {
+          for (int u = 0; u < r; ++u) t = fma(F[c * r + u], a[u] * sc[u], t);
+          part = fma(a[c] * sc[c], t, part);
         }
       }
-      const int64_t row = row0 + threadIdx.x;
-      if (lev) lev[row] = l;
+    }
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (lane == 0) {
+      if (lev) lev[row] = part;
       if (q) {
-        double p = l / (double)r;
+        double p = part / (double)r;
         p = p > 0.0 ? (p < 1.0 ? p : 1.0) : 0.0;
         const uint64_t qi = __double2ull_rn(p * 4611686018427387904.0);  // 2^62
         q[row] = qi;
@@ -318,12 +374,11 @@ __global__ void __launch_bounds__(kRowThreads) k_lev_rows(const double* A, int64
         my_nz += qi > 0;
       }
     }
-    if (A_out) {  // normalised copy from the original rows (coalesced)
-      __syncthreads();
-      for (int i = threadIdx.x; i < rows * r; i += kRowThreads) {
-        const int c = i % r;
-        const double v = A[row0 * r + i];
-        A_out[row0 * r + i] = lam[c] > 0.0 ? v / lam[c] : v;
+    if (A_out) {
+      __syncwarp();
+      for (int c = lane; c < r; c += 32) {
+        const double v = a[c];
+        A_out[row * r + c] = lam[c] > 0.0 ? v / lam[c] : v;
       }
     }
   }
@@ -333,63 +388,32 @@ __global__ void __launch_bounds__(kRowThreads) k_lev_rows(const double* A, int64
       my_max = om > my_max ? om : my_max;
       my_nz += __shfl_xor_sync(0xffffffffu, my_nz, o);
     }
-    if ((threadIdx.x & 31) == 0) {
+    if (lane == 0) {
       atomicMax((unsigned long long*)&info->maxq, (unsigned long long)my_max);
       atomicAdd((unsigned long long*)&info->nnzq, (unsigned long long)my_nz);
     }
   }
 }
 
+// A = M F with F the explicit inverse (kind 2) or pseudo-inverse (kind 1) of G:
+// one thread per output element.
 __global__ void __launch_bounds__(kRowThreads) k_solve_rows(const double* __restrict__ M,
                                                             int64_t n, int r,
                                                             const SmallFactor* __restrict__ f,
                                                             double* __restrict__ A) {
   extern __shared__ double smem[];
-  double* F = smem;         // r * r
-  double* xs = F + r * r;   // kRowThreads * (r + 1)
-  const int ld = r + 1;
+  double* F = smem;  // r * r
   for (int i = threadIdx.x; i < r * r; i += blockDim.x) F[i] = f->F[i];
-  const int kind = f->kind;
-  for (int64_t row0 = (int64_t)blockIdx.x * kRowThreads; row0 < n;
-       row0 += (int64_t)gridDim.x * kRowThreads) {
-    const int rows = (int)(n - row0 < kRowThreads ? n - row0 : kRowThreads);
-    __syncthreads();
-    for (int i = threadIdx.x; i < rows * r; i += kRowThreads) {
-      const int rr = i / r, c = i - rr * r;
-      xs[rr * ld + c] = M[row0 * r + i];
-    }
-    __syncthreads();
-    if (threadIdx.x < rows) {
-      double* x = xs + threadIdx.x * ld;
-      if (kind == 0) {
-        // G = L L^T: L y = m, then L^T x = y (in place)
-        for (int c = 0; c < r; ++c) {
-          double t = x[c];
-          for (int u = 0; u < c; ++u) t -= F[c * r + u] * x[u];
-          x[c] = t / F[c * r + c];
-        }
-        for (int c = r - 1; c >= 0; --c) {
-          double t = x[c];
-          for (int u = c + 1; u < r; ++u) t -= F[u * r + c] * x[u];
-          x[c] = t / F[c * r + c];
-        }
-      }
-    }
-    __syncthreads();
-    if (kind == 0) {
-      for (int i = threadIdx.x; i < rows * r; i += kRowThreads) {
-        const int rr = i / r, c = i - rr * r;
-        A[row0 * r + i] = xs[rr * ld + c];
-      }
-    } else {
-      // pinv path: A = M F straight from global memory (rare fallback)
-      for (int i = threadIdx.x; i < rows * r; i += kRowThreads) {
-        const int rr = i / r, b = i - rr * r;
-        double t = 0.0;
-        for (int a = 0; a < r; ++a) t += M[(row0 + rr) * r + a] * F[a * r + b];
-        A[row0 * r + i] = t;
-      }
-    }
+  __syncthreads();
+  const int64_t total = n * r;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = e / r;
+    const int c = (int)(e - row * r);
+    const double* m = M + row * r;
+    double t = 0.0;
+    for (int u = 0; u < r; ++u) t = fma(m[u], F[u * r + c], t);
+    A[e] = t;
   }
 }
 
@@ -439,15 +463,8 @@ int lev_rows(const double* A, int64_t n, int r, const SmallFactor* f, double* le
              DistInfo* info, double* A_out, cudaStream_t st) {
   if (r < 1 || r > kMaxRank) return CPA_ERR_ARG;
   if (n <= 0) return CPA_OK;
-  const size_t smem = sizeof(double) * ((size_t)r * r + 2 * r + 2 * (size_t)kRowThreads * (r + 1));
-  static bool attr = false;
-  if (!attr) {
-    CPA_CUDA_TRY(cudaFuncSetAttribute(k_lev_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(sizeof(double) * (kMaxRank * kMaxRank + 2 * kMaxRank +
-                                                              2 * kRowThreads * (kMaxRank + 1)))));
-    attr = true;
-  }
-  const unsigned grid = grid_cap(ceil_div(n, kRowThreads), 8);
+  const size_t smem = sizeof(double) * ((size_t)r * r + 2 * r);
+  const unsigned grid = grid_cap(ceil_div(n, kRowThreads / 32), 16);
   k_lev_rows<<<grid, kRowThreads, smem, st>>>(A, n, r, f, lev, q, info, A_out);
   CPA_LAUNCH_CHECK();
   return CPA_OK;
@@ -457,15 +474,8 @@ int solve_rows(const double* M, int64_t n, int r, const SmallFactor* f, double* 
                cudaStream_t st) {
   if (r < 1 || r > kMaxRank) return CPA_ERR_ARG;
   if (n <= 0) return CPA_OK;
-  const size_t smem = sizeof(double) * ((size_t)r * r + (size_t)kRowThreads * (r + 1));
-  static bool attr = false;
-  if (!attr) {
-    CPA_CUDA_TRY(cudaFuncSetAttribute(k_solve_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(sizeof(double) * (kMaxRank * kMaxRank +
-                                                              kRowThreads * (kMaxRank + 1)))));
-    attr = true;
-  }
-  const unsigned grid = grid_cap(ceil_div(n, kRowThreads), 8);
+  const size_t smem = sizeof(double) * (size_t)r * r;
+  const unsigned grid = grid_cap(ceil_div(n * r, kRowThreads), 16);
   k_solve_rows<<<grid, kRowThreads, smem, st>>>(M, n, r, f, A);
   CPA_LAUNCH_CHECK();
   return CPA_OK;

@@ -334,6 +334,10 @@ int index_build(const cpa_coo* coo, cudaStream_t st, cpa_index** out) {
 void index_free(cpa_index* X) {
   if (!X) return;
   cudaDeviceSynchronize();
+  if (X->plan) {
+    plan_free(X->plan);
+    X->plan = nullptr;
+  }
   for (void* p : X->allocations) cudaFree(p);
   delete X;
 }

@@ -6,10 +6,11 @@
 //              (row gathers of the other factors), stored for step 4, and
 //              G += y_j y_j^T is accumulated per thread over upper-triangle pairs.
 // 3. scan:     pos = exclusive prefix of len (nnz of the sampled right-hand side).
-// 4. mttkrp:   the flattened list of sampled nonzeros is cut into equal chunks, one
-//              per warp (merge-path style, so one heavy fibre is split across many
-//              warps); lane c accumulates M(i_k, c) += wgt_j * x * y_j(c) with
-//              atomics, into shared memory when M fits, else straight to global.
+// 4. mttkrp:   the flattened list of sampled nonzeros is cut into groups of 32, one
+//              per warp at a time (so a heavy fibre is spread over many warps and a
+//              run of short fibres is resolved 32 at a time); lane c accumulates
+//              M(i_k, c) += wgt_j * x * y_j(c) with atomics, into shared memory when
+//              M fits, else straight to global memory.
 #include "mttkrp.cuh"
 
 namespace cpa {
@@ -18,7 +19,6 @@ namespace {
 
 constexpr int kTileRows = 32;
 constexpr int kThreads = 256;
-constexpr int kChunk = 256;  // sampled nonzeros per warp work item
 
 __device__ __forceinline__ void pair_of(int p, int r, int* a, int* b) {
   int row = 0, start = 0;
@@ -106,6 +106,19 @@ __global__ void k_pos_end(DevCount sbar, const uint64_t* __restrict__ total, uin
   pos[sbar.get()] = *total;
 }
 
+// last j in [0, n) with pos[j] <= e (pos ascending, pos[0] = 0 <= e)
+__device__ __forceinline__ int64_t sample_of(const uint64_t* __restrict__ pos, int64_t n, uint64_t e) {
+  int64_t a = 0, b = n - 1;
+  while (a < b) {
+    const int64_t mid = (a + b + 1) >> 1;
+    if (pos[mid] <= e) a = mid; else b = mid - 1;
+  }
+  return a;
+}
+
+// Lane-parallel gather: a warp takes 32 consecutive sampled nonzeros; each lane
+// resolves its own (sample, fibre offset, i_k, wgt_j * x) with independent loads, then
+// the warp walks the 32 nonzeros and lane c adds coef * y_j(c) into row i_k of M.
 template <class VT, int CPL, bool kShared>
 __global__ void __launch_bounds__(kThreads) k_mttkrp(FibreIndex<VT> X, const double* __restrict__ Y,
                                                      const double* __restrict__ wgt,
@@ -123,51 +136,31 @@ __global__ void __launch_bounds__(kThreads) k_mttkrp(FibreIndex<VT> X, const dou
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
-  for (uint64_t c0 = (uint64_t)gw * kChunk; c0 < total; c0 += (uint64_t)nwarps * kChunk) {
-    const uint64_t c1 = c0 + kChunk < total ? c0 + kChunk : total;
-    // last sample j with pos[j] <= c0
-    int64_t a = 0, b = n - 1;
-    while (a < b) {
-      const int64_t mid = (a + b + 1) >> 1;
-      if (pos[mid] <= c0) a = mid; else b = mid - 1;
+  for (uint64_t base = (uint64_t)gw * 32; base < total; base += (uint64_t)nwarps * 32) {
+    const uint64_t e = base + lane;
+    int64_t j = 0;
+    int32_t ik = 0;
+    double coef = 0.0;
+    if (e < total) {
+      j = sample_of(pos, n, e);
+      const uint64_t off = lo[j] + (e - pos[j]);
+      ik = X.ik[off];
+      coef = wgt[j] * (double)X.val[off];
     }
-    int64_t j = a;
-    uint64_t e = c0;
-    while (e < c1) {
-      const uint64_t pj = pos[j], pj1 = pos[j + 1];
-      const uint64_t seg_end = pj1 < c1 ? pj1 : c1;
-      const uint64_t base = lo[j] + (e - pj);
-      const double w = wgt[j];
-      double coef[CPL];
+    const int nb = total - base < 32 ? (int)(total - base) : 32;
+    for (int q = 0; q < nb; ++q) {
+      const int64_t jq = __shfl_sync(0xffffffffu, j, q);
+      const int32_t iq = __shfl_sync(0xffffffffu, ik, q);
+      const double cq = __shfl_sync(0xffffffffu, coef, q);
 #pragma unroll
-      for (int q = 0; q < CPL; ++q) {
-        const int c = lane + 32 * q;
-        coef[q] = c < r ? w * Y[j * r + c] : 0.0;
-      }
-      const int cnt = (int)(seg_end - e);
-      for (int b0 = 0; b0 < cnt; b0 += 32) {
-        int32_t ik_l = 0;
-        double v_l = 0.0;
-        if (b0 + lane < cnt) {
-          ik_l = X.ik[base + b0 + lane];
-          v_l = (double)X.val[base + b0 + lane];
-        }
-        const int nb = cnt - b0 < 32 ? cnt - b0 : 32;
-        for (int q2 = 0; q2 < nb; ++q2) {
-          const int32_t ik = __shfl_sync(0xffffffffu, ik_l, q2);
-          const double v = __shfl_sync(0xffffffffu, v_l, q2);
-#pragma unroll
-          for (int q = 0; q < CPL; ++q) {
-            const int c = lane + 32 * q;
-            if (c < r) {
-              if (kShared) atomicAdd(&Ms[(int64_t)ik * r + c], v * coef[q]);
-              else atomicAdd(&M[(int64_t)ik * r + c], v * coef[q]);
-            }
-          }
+      for (int u = 0; u < CPL; ++u) {
+        const int c = lane + 32 * u;
+        if (c < r) {
+          const double v = cq * Y[jq * r + c];
+          if (kShared) atomicAdd(&Ms[(int64_t)iq * r + c], v);
+          else atomicAdd(&M[(int64_t)iq * r + c], v);
         }
       }
-      e = seg_end;
-      while (j + 1 < n && pos[j + 1] <= e) ++j;
     }
   }
   if (kShared) {
@@ -200,7 +193,7 @@ int run(const cpa_index* X, int k, const FactorPtrs& F, int r, const uint64_t* i
   CPA_LAUNCH_CHECK();
   CPA_TRY(scan_u64<uint32_t>(B.len, B.pos, sbar, false, B.total, B.scratch, st));
   k_pos_end<<<1, 1, 0, st>>>(sbar, B.total, B.pos);
-  if (mid) CPA_CUDA_TRY(cudaEventRecord(mid, st));
+  if (mid) CPA_CUDA_TRY(record_event(mid, st));
   const int64_t nk = X->dims[k];
   const bool shared = nk * r * sizeof(double) <= 48 * 1024;
   const size_t msm = shared ? sizeof(double) * nk * r : 0;

@@ -20,9 +20,18 @@ namespace {
 
 constexpr int kThreads = 256;
 
-__device__ __forceinline__ double mode_prob(const uint64_t* __restrict__ C, uint64_t T, int64_t i) {
+__device__ __forceinline__ double mode_prob_from_cdf(const uint64_t* __restrict__ C, uint64_t T,
+                                                     int64_t i) {
   const uint64_t q = C[i] - (i > 0 ? C[i - 1] : 0ull);
   return __ddiv_rn(__ull2double_rn(q), __ull2double_rn(T));
+}
+
+__global__ void k_phat(const uint64_t* __restrict__ C, int64_t n, const DistInfo* __restrict__ info,
+                       double* __restrict__ p) {
+  const uint64_t T = info->T;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = mode_prob_from_cdf(C, T, i);
 }
 
 // smallest i with C[i] > t (C inclusive, C[n-1] = T > t)
@@ -39,7 +48,7 @@ __device__ __forceinline__ int64_t cdf_search(const uint64_t* __restrict__ C, in
 __device__ __forceinline__ double key_prob(const SampleParams& P, uint64_t packed) {
   double p = 0.0;
   for (int t = 0; t < P.L.d; ++t) {
-    const double pt = mode_prob(P.D.C[t], P.D.info[t]->T, P.L.get(packed, t));
+    const double pt = P.D.P[t][P.L.get(packed, t)];
     p = t == 0 ? pt : __dmul_rn(p, pt);
   }
   return p;
@@ -102,6 +111,55 @@ __device__ double xs_round(const uint64_t* bins_in) {
   return __longlong_as_double((long long)((bexp << 52) | (m & ((1ull << 52) - 1ull))));
 }
 
+// ---- combine table -------------------------------------------------------
+// CombineRepeats counts the repeats of each drawn key in an open-addressing table
+// (linear probing, 2^hbits >= 2 s slots); deterministic keys go in with their flag
+// bit clear, random ones with it set, so the two never merge.
+constexpr uint64_t kEmptyKey = ~0ull;
+
+__device__ __forceinline__ uint64_t slot_of(uint64_t key, int hbits) {
+  return (key * 0x9E3779B97F4A7C15ull) >> (64 - hbits);
+}
+
+__device__ __forceinline__ bool table_add(uint64_t* __restrict__ keys, uint32_t* __restrict__ cnt,
+                                          int hbits, uint64_t key) {
+  const uint64_t mask = (1ull << hbits) - 1ull;
+  uint64_t h = slot_of(key, hbits);
+  for (uint64_t probe = 0; probe <= mask; ++probe) {
+    const unsigned long long prev =
+        atomicCAS((unsigned long long*)&keys[h], (unsigned long long)kEmptyKey, (unsigned long long)key);
+    if (prev == kEmptyKey || prev == key) {
+      atomicAdd(&cnt[h], 1u);
+      return true;
+    }
+    h = (h + 1) & mask;
+  }
+  return false;
+}
+
+__device__ __forceinline__ uint32_t table_count(const uint64_t* __restrict__ keys,
+                                                const uint32_t* __restrict__ cnt, int hbits,
+                                                uint64_t key) {
+  const uint64_t mask = (1ull << hbits) - 1ull;
+  uint64_t h = slot_of(key, hbits);
+  for (uint64_t probe = 0; probe <= mask; ++probe) {
+    const uint64_t k = keys[h];
+    if (k == key) return cnt[h];
+    if (k == kEmptyKey) return 0;
+    h = (h + 1) & mask;
+  }
+  return 0;
+}
+
+// weight of a combined row (Eq. 4.4 with s_rnd) or 1 for a deterministic row
+__device__ __forceinline__ double row_weight(const SampleParams& P, uint64_t packed, bool det, uint64_t c,
+                                             double one_minus_pdet, int64_t srnd) {
+  if (det) return 1.0;
+  const double p = key_prob(P, packed);
+  return __dsqrt_rn(__ddiv_rn(__dmul_rn(__ull2double_rn(c), one_minus_pdet),
+                              __dmul_rn(p, __ll2double_rn(srnd))));
+}
+
 // ---- kernels ----------------------------------------------------------
 __global__ void k_prepare(SampleParams P, SampleState* S) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -143,7 +201,7 @@ __global__ void k_det_filter(SampleParams P, SampleState* S, uint32_t* __restric
     int t = 0;
     while (t + 1 < P.L.d && g >= offs[t + 1]) ++t;
     const int64_t i = g - offs[t];
-    const double p = mode_prob(P.D.C[t], P.D.info[t]->T, i);
+    const double p = P.D.P[t][i];
     if (p >= S->thr[t]) {
       const unsigned long long at = atomicAdd((unsigned long long*)&S->ncand[t], 1ull);
       cand[offs[t] + (int64_t)at] = (uint32_t)i;
@@ -187,13 +245,13 @@ __global__ void k_det_enum(SampleParams P, SampleState* S, const uint32_t* __res
       const uint64_t pos = rest % (uint64_t)nc[t];
       rest /= (uint64_t)nc[t];
       const uint32_t i = cand[offs[t] + (int64_t)pos];
-      const double pt = mode_prob(P.D.C[t], P.D.info[t]->T, i);
+      const double pt = P.D.P[t][i];
       p = t == 0 ? pt : __dmul_rn(p, pt);
       packed |= (uint64_t)i << P.L.off[t];
     }
     if (p > P.tau) {
       const unsigned long long at = atomicAdd((unsigned long long*)&S->det_count, 1ull);
-      if ((int64_t)at < P.det_cap) {
+      if ((int64_t)at < P.det_buf) {
         det_keys[at] = packed;
         det_p[at] = p;
       }
@@ -210,7 +268,11 @@ __global__ void k_det_enum(SampleParams P, SampleState* S, const uint32_t* __res
 __global__ void k_det_finish(SampleParams P, SampleState* S) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   int64_t sdet = (int64_t)S->det_count;
-  if (sdet > P.s) {
+  if (sdet > P.det_buf) {
+    // only reachable when tau * s >= 1 by rounding at the threshold: refuse
+    set_status(&S->status, CPA_ERR_DET_CAP);
+    sdet = 0;
+  } else if (sdet > P.s) {
     S->need_topk = 1;  // the host runs the top-s selection
     sdet = P.s;
   } else {
@@ -226,23 +288,25 @@ __global__ void k_det_finish(SampleParams P, SampleState* S) {
   S->nsort = sdet + srnd;
 }
 
-__global__ void k_copy_det(SampleState* S, const uint64_t* __restrict__ det_keys,
-                           uint64_t* __restrict__ sortbuf) {
+__global__ void k_insert_det(SampleState* S, const uint64_t* __restrict__ det_keys,
+                             uint64_t* __restrict__ hkeys, uint32_t* __restrict__ hcnt, int hbits) {
   const int64_t sdet = S->sdet;
   if (S->need_topk) return;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < sdet;
        j += (int64_t)gridDim.x * blockDim.x)
-    sortbuf[j] = det_keys[j];
+    if (!table_add(hkeys, hcnt, hbits, det_keys[j])) set_status(&S->status, CPA_ERR_UNSUPPORTED);
 }
 
 // Alg. 2 with one Philox counter per (slot, attempt)
 __global__ void __launch_bounds__(kThreads) k_rnd(SampleParams P, SampleState* S,
-                                                  uint64_t* __restrict__ sortbuf,
+                                                  uint64_t* __restrict__ hkeys,
+                                                  uint32_t* __restrict__ hcnt, int hbits,
                                                   uint64_t* __restrict__ raw_key,
                                                   double* __restrict__ raw_w) {
-  const int64_t srnd = S->srnd, sdet = S->sdet;
+  const int64_t srnd = S->srnd;
   const double pdet = S->pdet;
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const uint64_t iter = P.iter_ptr ? *P.iter_ptr : P.iter;
   uint64_t tries = 0;
   if (j < srnd) {
     uint64_t packed = 0;
@@ -256,13 +320,13 @@ __global__ void __launch_bounds__(kThreads) k_rnd(SampleParams P, SampleState* S
           w0 = (uint64_t)j;
           w1 = (uint64_t)a;
           w2 = (uint64_t)(uint32_t)P.mode_k | ((uint64_t)(t >> 2) << 16) | kDomainSample;
-          w3 = P.iter;
+          w3 = iter;
           Philox4x64::block(w0, w1, w2, w3, P.seed, 0ull);
         }
         const uint64_t u = (t & 3) == 0 ? w0 : (t & 3) == 1 ? w1 : (t & 3) == 2 ? w2 : w3;
         const uint64_t T = P.D.info[t]->T;
         const int64_t i = cdf_search(P.D.C[t], P.L.n[t], __umul64hi(u, T));
-        const double pt = mode_prob(P.D.C[t], T, i);
+        const double pt = P.D.P[t][i];
         p = t == 0 ? pt : __dmul_rn(p, pt);
         packed |= (uint64_t)i << P.L.off[t];
       }
@@ -273,7 +337,8 @@ __global__ void __launch_bounds__(kThreads) k_rnd(SampleParams P, SampleState* S
       }
     }
     if (!ok) set_status(&S->status, CPA_ERR_REJECT_LIMIT);
-    sortbuf[sdet + j] = (1ull << P.L.total_bits) | packed;
+    if (!table_add(hkeys, hcnt, hbits, (1ull << P.L.total_bits) | packed))
+      set_status(&S->status, CPA_ERR_UNSUPPORTED);
     if (raw_key) raw_key[j] = P.L.linear(packed);
     if (raw_w)
       raw_w[j] = __dsqrt_rn(__ddiv_rn(__dsub_rn(1.0, pdet), __dmul_rn(p, __ll2double_rn(srnd))));
@@ -283,54 +348,72 @@ __global__ void __launch_bounds__(kThreads) k_rnd(SampleParams P, SampleState* S
     atomicAdd((unsigned long long*)&S->attempts, (unsigned long long)tries);
 }
 
-__global__ void k_run_flags(const SampleState* S, const uint64_t* __restrict__ sorted,
-                            uint32_t* __restrict__ flag) {
-  const int64_t n = S->nsort;
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
-       j += (int64_t)gridDim.x * blockDim.x)
-    flag[j] = (j == 0 || sorted[j] != sorted[j - 1]) ? 1u : 0u;
-}
-
-__global__ void k_run_starts(SampleState* S, const uint32_t* __restrict__ flag,
-                             const uint64_t* __restrict__ uid, uint64_t* __restrict__ run_start) {
-  const int64_t n = S->nsort;
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
-       j += (int64_t)gridDim.x * blockDim.x)
-    if (flag[j]) run_start[uid[j]] = (uint64_t)j;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    const int64_t nu = n > 0 ? (int64_t)(uid[n - 1] + flag[n - 1]) : 0;
-    S->nuniq = nu;
-    S->sbar = nu;
-    run_start[nu] = (uint64_t)n;
+// occupied table slots -> output rows, unordered (warp-aggregated append)
+__global__ void k_table_compact(SampleParams P, SampleState* S, const uint64_t* __restrict__ hkeys,
+                                const uint32_t* __restrict__ hcnt, int hbits,
+                                uint64_t* __restrict__ idx_packed, uint32_t* __restrict__ cnt,
+                                double* __restrict__ wgt) {
+  const int64_t H = 1ll << hbits;
+  const int64_t srnd = S->srnd;
+  const double one_minus_pdet = __dsub_rn(1.0, S->pdet);
+  const uint64_t flag_bit = 1ull << P.L.total_bits;
+  const int lane = threadIdx.x & 31;
+  for (int64_t h0 = blockIdx.x * (int64_t)blockDim.x; h0 < H; h0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t h = h0 + threadIdx.x;
+    const uint64_t v = h < H ? hkeys[h] : kEmptyKey;
+    const bool occ = v != kEmptyKey;
+    const unsigned bal = __ballot_sync(0xffffffffu, occ);
+    unsigned long long base = 0;
+    if (lane == 0 && bal) base = atomicAdd((unsigned long long*)&S->sbar, (unsigned long long)__popc(bal));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (occ) {
+      const int64_t u = (int64_t)base + __popc(bal & ((1u << lane) - 1u));
+      const uint64_t packed = v & (flag_bit - 1ull);
+      const bool det = !(v & flag_bit);
+      const uint32_t c = det ? 1u : hcnt[h];
+      idx_packed[u] = packed;
+      cnt[u] = c;
+      wgt[u] = row_weight(P, packed, det, c, one_minus_pdet, srnd);
+    }
   }
 }
 
-// run u of the sorted buffer -> output row u
-__global__ void k_combine(SampleParams P, const SampleState* S, const uint64_t* __restrict__ sorted,
-                          const uint64_t* __restrict__ run_start, uint64_t* __restrict__ idx_packed,
-                          uint32_t* __restrict__ cnt, double* __restrict__ wgt,
-                          uint64_t* __restrict__ idx_linear) {
-  const int64_t nu = S->nuniq;
+// occupied table slots -> flagged keys (unordered), for the sorted output
+__global__ void k_table_collect(SampleState* S, const uint64_t* __restrict__ hkeys, int hbits,
+                                uint64_t* __restrict__ out) {
+  const int64_t H = 1ll << hbits;
+  const int lane = threadIdx.x & 31;
+  for (int64_t h0 = blockIdx.x * (int64_t)blockDim.x; h0 < H; h0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t h = h0 + threadIdx.x;
+    const uint64_t v = h < H ? hkeys[h] : kEmptyKey;
+    const bool occ = v != kEmptyKey;
+    const unsigned bal = __ballot_sync(0xffffffffu, occ);
+    unsigned long long base = 0;
+    if (lane == 0 && bal) base = atomicAdd((unsigned long long*)&S->sbar, (unsigned long long)__popc(bal));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (occ) out[(int64_t)base + __popc(bal & ((1u << lane) - 1u))] = v;
+  }
+}
+
+// sorted flagged keys (deterministic first, each block ascending) -> output rows
+__global__ void k_table_emit(SampleParams P, const SampleState* S, const uint64_t* __restrict__ sorted,
+                             const uint64_t* __restrict__ hkeys, const uint32_t* __restrict__ hcnt,
+                             int hbits, uint64_t* __restrict__ idx_packed, uint32_t* __restrict__ cnt,
+                             double* __restrict__ wgt, uint64_t* __restrict__ idx_linear) {
+  const int64_t nu = S->sbar;
   const int64_t srnd = S->srnd;
   const double one_minus_pdet = __dsub_rn(1.0, S->pdet);
   const uint64_t flag_bit = 1ull << P.L.total_bits;
   for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < nu;
        u += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t b = run_start[u];
-    const uint64_t c = run_start[u + 1] - b;
-    const uint64_t v = sorted[b];
+    const uint64_t v = sorted[u];
     const uint64_t packed = v & (flag_bit - 1ull);
+    const bool det = !(v & flag_bit);
+    const uint32_t c = det ? 1u : table_count(hkeys, hcnt, hbits, v);
     idx_packed[u] = packed;
     if (idx_linear) idx_linear[u] = P.L.linear(packed);
-    if (!(v & flag_bit)) {  // deterministic row
-      cnt[u] = 1;
-      wgt[u] = 1.0;
-    } else {
-      const double p = key_prob(P, packed);
-      cnt[u] = (uint32_t)c;
-      wgt[u] = __dsqrt_rn(__ddiv_rn(__dmul_rn(__ull2double_rn(c), one_minus_pdet),
-                                    __dmul_rn(p, __ll2double_rn(srnd))));
-    }
+    cnt[u] = c;
+    wgt[u] = row_weight(P, packed, det, c, one_minus_pdet, srnd);
   }
 }
 
@@ -343,14 +426,14 @@ __global__ void k_topk_keys(const SampleState* S, const double* __restrict__ det
 }
 
 __global__ void k_topk_take(SampleParams P, SampleState* S, const uint64_t* __restrict__ keys_by_p,
-                            uint64_t* __restrict__ sortbuf) {
+                            uint64_t* __restrict__ hkeys, uint32_t* __restrict__ hcnt, int hbits) {
   __shared__ uint64_t bins[kXsLimbs];
   for (int i = threadIdx.x; i < kXsLimbs; i += blockDim.x) bins[i] = 0;
   __syncthreads();
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < P.s;
        j += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t packed = keys_by_p[j];
-    sortbuf[j] = packed;
+    if (!table_add(hkeys, hcnt, hbits, packed)) set_status(&S->status, CPA_ERR_UNSUPPORTED);
     xs_add(bins, key_prob(P, packed));
   }
   __syncthreads();
@@ -366,6 +449,21 @@ __global__ void k_zero_bins(SampleState* S) {
   if (threadIdx.x < kXsLimbs) S->xs[threadIdx.x] = 0;
 }
 
+inline unsigned blocks_for(int64_t n);
+
+}  // namespace
+
+int phat_from_cdf(const uint64_t* C, int64_t n, const DistInfo* info, double* p, cudaStream_t st) {
+  if (n <= 0) return CPA_OK;
+  int64_t b = ceil_div(n, kThreads);
+  const int64_t cap = (int64_t)num_sms() * 8;
+  k_phat<<<(unsigned)(b < cap ? b : cap), kThreads, 0, st>>>(C, n, info, p);
+  CPA_LAUNCH_CHECK();
+  return CPA_OK;
+}
+
+namespace {
+
 inline unsigned blocks_for(int64_t n) {
   int64_t b = ceil_div(n > 0 ? n : 1, kThreads);
   const int64_t cap = (int64_t)num_sms() * 16;
@@ -374,10 +472,16 @@ inline unsigned blocks_for(int64_t n) {
 
 }  // namespace
 
-size_t sample_buffers_bytes(const KeyLayout& L, int64_t s, int64_t det_cap) {
+int64_t det_buffer_capacity(int64_t s, double tau, int64_t det_cap) {
+  if (!(tau < 1.0)) return 1;
+  if (tau * (double)s >= 1.0) return s < det_cap ? s : det_cap;
+  return det_cap;
+}
+
+size_t sample_buffers_bytes(const KeyLayout& L, int64_t s, int64_t det_buf) {
   Arena a;
   SampleBuffers B;
-  sample_buffers_carve(a, L, s, det_cap, &B);
+  sample_buffers_carve(a, L, s, det_buf, &B);
   return a.used + 256;
 }
 
@@ -395,9 +499,11 @@ void sample_buffers_carve(Arena& a, const KeyLayout& L, int64_t s, int64_t det_c
   B->det_p = a.take<double>(det_cap);
   B->sortA = a.take<uint64_t>(s);
   B->sortB = a.take<uint64_t>(s);
-  B->flag = a.take<uint32_t>(s);
-  B->uid = a.take<uint64_t>(s);
-  B->run_start = a.take<uint64_t>(s + 1);
+  int hb = 10;
+  while ((1ll << hb) < 2 * s) ++hb;
+  B->hbits = hb;
+  B->hkeys = a.take<uint64_t>(1ull << hb);
+  B->hcnt = a.take<uint32_t>(1ull << hb);
   const size_t ws_s = sort_workspace(s), ws_c = scan_workspace(s);
   const int64_t big = det_cap > s ? det_cap : s;
   const size_t ws_t = sort_workspace(big);
@@ -412,11 +518,13 @@ void sample_buffers_carve(Arena& a, const KeyLayout& L, int64_t s, int64_t det_c
   B->raw_w = nullptr;
 }
 
-int skrp_lev(const SampleParams& P, SampleBuffers& B, cudaStream_t st) {
+int skrp_lev(const SampleParams& P, SampleBuffers& B, cudaStream_t st, bool sorted_output) {
   SampleState* S = B.state;
   const int64_t* co = B.cand_off;
   int64_t total_cand = 0;
   for (int t = 0; t < P.L.d; ++t) total_cand += P.L.n[t];
+  CPA_CUDA_TRY(cudaMemsetAsync(B.hkeys, 0xff, sizeof(uint64_t) << B.hbits, st));
+  CPA_CUDA_TRY(cudaMemsetAsync(B.hcnt, 0, sizeof(uint32_t) << B.hbits, st));
   k_prepare<<<1, 32, 0, st>>>(P, S);
   const bool may_det = P.tau < 1.0;
   if (may_det) {
@@ -467,26 +575,31 @@ int skrp_lev(const SampleParams& P, SampleBuffers& B, cudaStream_t st) {
                                    64, ws, st, &alt));
       uint64_t* by_p = alt ? p_sorted : spare_v;
       k_zero_bins<<<1, 64, 0, st>>>(S);
-      k_topk_take<<<blocks_for(P.s), kThreads, 0, st>>>(P, S, by_p, B.sortA);
+      k_topk_take<<<blocks_for(P.s), kThreads, 0, st>>>(P, S, by_p, B.hkeys, B.hcnt, B.hbits);
       k_topk_finish<<<1, 32, 0, st>>>(S);
       CPA_LAUNCH_CHECK();
       CPA_CUDA_TRY(cudaFreeAsync(ka, st));
     }
   }
-  k_copy_det<<<blocks_for(P.s), kThreads, 0, st>>>(S, B.det_keys, B.sortA);
-  k_rnd<<<(unsigned)ceil_div(P.s, kThreads), kThreads, 0, st>>>(P, S, B.sortA, B.raw_key, B.raw_w);
+  k_insert_det<<<blocks_for(P.s), kThreads, 0, st>>>(S, B.det_keys, B.hkeys, B.hcnt, B.hbits);
+  k_rnd<<<(unsigned)ceil_div(P.s, kThreads), kThreads, 0, st>>>(P, S, B.hkeys, B.hcnt, B.hbits, B.raw_key,
+                                                                B.raw_w);
   CPA_LAUNCH_CHECK();
-  // combine: sort (flag bit keeps deterministic rows first), run-length encode
+  const int64_t H = 1ll << B.hbits;
+  if (!sorted_output) {
+    k_table_compact<<<blocks_for(H), kThreads, 0, st>>>(P, S, B.hkeys, B.hcnt, B.hbits, B.idx_packed,
+                                                        B.cnt, B.wgt);
+    CPA_LAUNCH_CHECK();
+    return CPA_OK;
+  }
+  // ascending output: deterministic keys (flag bit clear) first, then random ones
+  k_table_collect<<<blocks_for(H), kThreads, 0, st>>>(S, B.hkeys, B.hbits, B.sortA);
   int alt = 0;
-  const DevCount n_sort{&S->nsort, P.s};
-  CPA_TRY(radix_sort<uint64_t>(B.sortA, B.sortB, (uint64_t*)nullptr, (uint64_t*)nullptr, n_sort, 0,
-                               P.L.total_bits + 1, B.scratch, st, &alt));
+  CPA_TRY(radix_sort<uint64_t>(B.sortA, B.sortB, (uint64_t*)nullptr, (uint64_t*)nullptr,
+                               DevCount{&S->sbar, P.s}, 0, P.L.total_bits + 1, B.scratch, st, &alt));
   const uint64_t* sorted = alt ? B.sortB : B.sortA;
-  k_run_flags<<<blocks_for(P.s), kThreads, 0, st>>>(S, sorted, B.flag);
-  CPA_TRY(scan_u64<uint32_t>(B.flag, B.uid, n_sort, false, nullptr, B.scratch, st));
-  k_run_starts<<<blocks_for(P.s), kThreads, 0, st>>>(S, B.flag, B.uid, B.run_start);
-  k_combine<<<blocks_for(P.s), kThreads, 0, st>>>(P, S, sorted, B.run_start, B.idx_packed, B.cnt,
-                                                  B.wgt, B.idx_linear);
+  k_table_emit<<<blocks_for(P.s), kThreads, 0, st>>>(P, S, sorted, B.hkeys, B.hcnt, B.hbits, B.idx_packed,
+                                                     B.cnt, B.wgt, B.idx_linear);
   CPA_LAUNCH_CHECK();
   return CPA_OK;
 }

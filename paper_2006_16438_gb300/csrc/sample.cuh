@@ -29,11 +29,16 @@ struct SampleState {
   uint64_t xs[kXsLimbs];  // exact-sum bins of p_det
 };
 
-// Per-mode distributions of the d other modes (device pointers).
+// Per-mode distributions of the d other modes (device pointers): the inclusive
+// fixed-point CDF, its summary, and p_t(i) = q_i / T_t precomputed per row.
 struct OtherDists {
   const uint64_t* C[kMaxOrder];
   const DistInfo* info[kMaxOrder];
+  const double* P[kMaxOrder];
 };
+
+// p[i] = q_i / T (q_i = C_i - C_{i-1}), the IEEE quotient the sampler uses.
+int phat_from_cdf(const uint64_t* C, int64_t n, const DistInfo* info, double* p, cudaStream_t st);
 
 struct SampleParams {
   KeyLayout L;          // other modes of the update
@@ -41,10 +46,12 @@ struct SampleParams {
   int64_t s;
   double tau;
   uint64_t seed;
-  uint64_t iter;
+  uint64_t iter;               // outer iteration of the Philox counter ...
+  const uint64_t* iter_ptr;    // ... or read from device memory when non-null
   int mode_k;
   int reject_cap;
-  int64_t det_cap;
+  int64_t det_cap;             // candidate-product cap
+  int64_t det_buf;             // capacity of the deterministic key buffer
 };
 
 // Buffers of one sampling pass (device), sized by sample_buffers_bytes.
@@ -56,9 +63,9 @@ struct SampleBuffers {
   double* det_p;        // det_cap probabilities
   uint64_t* sortA;      // s
   uint64_t* sortB;      // s
-  uint32_t* flag;       // s
-  uint64_t* uid;        // s
-  uint64_t* run_start;  // s + 1
+  uint64_t* hkeys;      // 2^hbits combine-table keys
+  uint32_t* hcnt;       // 2^hbits repeat counts
+  int hbits;
   char* scratch;        // max(sort, scan) workspace for s items
   // outputs
   uint64_t* idx_packed; // s
@@ -69,12 +76,20 @@ struct SampleBuffers {
   double* raw_w;        // s_rnd raw per-slot weights (may be null)
 };
 
-size_t sample_buffers_bytes(const KeyLayout& L, int64_t s, int64_t det_cap);
-void sample_buffers_carve(Arena& a, const KeyLayout& L, int64_t s, int64_t det_cap,
+size_t sample_buffers_bytes(const KeyLayout& L, int64_t s, int64_t det_buf);
+void sample_buffers_carve(Arena& a, const KeyLayout& L, int64_t s, int64_t det_buf,
                           SampleBuffers* B);
 
+// Deterministic-buffer capacity for a pass: s suffices when tau * s >= 1, because
+// then fewer than 1/tau <= s rows can have p > tau.
+int64_t det_buffer_capacity(int64_t s, double tau, int64_t det_cap);
+
 // Enqueue one SkrpLev pass.  If tau * s < 1 the deterministic set might exceed s;
-// then the call synchronises once to run the top-s selection.
-int skrp_lev(const SampleParams& P, SampleBuffers& B, cudaStream_t st);
+// then the call synchronises once to run the top-s selection (never the case when
+// tau * s >= 1, so that path is free of host synchronisation).  sorted_output:
+// rows in the order of Alg. 1's cat (deterministic keys ascending, then random
+// keys ascending); otherwise rows come in table order, which the solve does not
+// depend on.
+int skrp_lev(const SampleParams& P, SampleBuffers& B, cudaStream_t st, bool sorted_output);
 
 }  // namespace cpa

@@ -1,11 +1,13 @@
 // Device prefix sums and stable LSD radix sort with device-side item counts.
 //
-// Both are plain multi-kernel designs: a scan is tile sums -> one-block scan of
-// the tile sums -> tile-local scans; a radix pass is a per-tile digit histogram ->
-// scan of the (digit-major) histogram -> stable scatter in which each warp ranks
-// its keys with __match_any_sync and a per-warp digit counter.  Item counts may
-// live on the device (DevCount) so that a sequence of launches can be enqueued
-// without a host round trip; grids are sized for the maximum count.
+// Both are multi-kernel designs: a scan is tile sums -> one-block scan of the tile
+// sums -> tile-local scans; a radix pass is a per-tile digit histogram -> scan of
+// the (digit-major) histogram -> stable scatter in which each warp ranks its keys
+// with per-bit ballots and a per-warp digit counter.  Up to 64 tiles (256K items)
+// the middle step is folded into the last kernel (each tile sums its predecessors
+// itself), so a scan is 2 launches and a radix pass 2.  Item counts may live on the
+// device (DevCount) so that a sequence of launches can be enqueued without a host
+// round trip; grids are sized for the maximum count.
 #include "cpa_common.cuh"
 
 namespace cpa {
@@ -87,14 +89,34 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tile_offsets(uint64_t* ti
   if (threadIdx.x == 0 && total_out) *total_out = carry;
 }
 
+constexpr int kFusedTiles = 64;  // up to this many tiles a tile sums its predecessors itself
+
+// fused = 1: tile_off holds raw tile sums and each block adds up the ones before it
 template <class T>
 __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const T* in, uint64_t* out,
                                                              DevCount count,
                                                              const uint64_t* __restrict__ tile_off,
-                                                             int inclusive) {
+                                                             int inclusive, int fused,
+                                                             uint64_t* total_out) {
   __shared__ uint64_t sm[32];
+  __shared__ uint64_t base_off;
   const int64_t n = count.get();
   const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  if (fused) {
+    if (threadIdx.x < 32) {
+      uint64_t acc = 0;
+      for (int t = threadIdx.x; t < (int)blockIdx.x; t += 32) acc += tile_off[t];
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (threadIdx.x == 0) base_off = acc;
+      if (blockIdx.x == gridDim.x - 1 && total_out) {
+        uint64_t tot = 0;
+        for (int t = threadIdx.x; t < (int)gridDim.x; t += 32) tot += tile_off[t];
+        for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        if (threadIdx.x == 0) *total_out = tot;
+      }
+    }
+    __syncthreads();
+  }
   if (base >= n) return;  // uniform over the block
   const int64_t g0 = base + (int64_t)threadIdx.x * kScanItems;
   uint64_t v[kScanItems];
@@ -106,7 +128,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const T* in, uint64
   }
   uint64_t bt;
   const uint64_t inc = block_inclusive_scan(local, sm, &bt);
-  uint64_t run = tile_off[blockIdx.x] + inc - local;
+  uint64_t run = (fused ? base_off : tile_off[blockIdx.x]) + inc - local;
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
     if (g0 + i < n) {
@@ -126,9 +148,21 @@ __device__ __forceinline__ int digit_of(uint64_t k, int shift, uint32_t mask) {
   return (int)((k >> shift) & mask);
 }
 
+// Lanes of the warp holding the same digit as this lane (valid lanes only), built
+// from one ballot per digit bit.
+__device__ __forceinline__ unsigned digit_peers(int d, bool valid, int bits) {
+  unsigned peers = __ballot_sync(0xffffffffu, valid);
+  for (int b = 0; b < bits; ++b) {
+    const bool bit = (d >> b) & 1;
+    const unsigned bal = __ballot_sync(0xffffffffu, bit && valid);
+    peers &= bit ? bal : ~bal;
+  }
+  return peers;
+}
+
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint64_t* __restrict__ keys,
                                                              DevCount count, int shift,
-                                                             uint32_t mask,
+                                                             uint32_t mask, int bits,
                                                              uint64_t* __restrict__ hist,
                                                              int64_t ntiles) {
   __shared__ uint32_t h[kRadix];
@@ -141,8 +175,8 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint64_t* __r
     for (int i = threadIdx.x; i < kSortTile; i += kSortThreads) {
       const int64_t g = base + i;
       const bool valid = g < n;
-      const int d = valid ? digit_of(keys[g], shift, mask) : kRadix + lane;
-      const unsigned peers = __match_any_sync(0xffffffffu, d);
+      const int d = valid ? digit_of(keys[g], shift, mask) : 0;
+      const unsigned peers = digit_peers(d, valid, bits);
       if (valid && lane == __ffs(peers) - 1) atomicAdd(&h[d], (uint32_t)__popc(peers));
     }
   }
@@ -151,21 +185,38 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint64_t* __r
     hist[(int64_t)d * ntiles + blockIdx.x] = h[d];
 }
 
+// fused = 1: `offsets` holds the raw digit-major histogram (ntiles <= kFusedTiles)
+// and each block derives its own output offsets from it.
 template <class V, bool kVals>
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     const uint64_t* __restrict__ keys_in, uint64_t* __restrict__ keys_out,
     const V* __restrict__ vals_in, V* __restrict__ vals_out, DevCount count, int shift,
-    uint32_t mask, const uint64_t* __restrict__ offsets, int64_t ntiles) {
+    uint32_t mask, int bits, const uint64_t* __restrict__ offsets, int64_t ntiles, int fused) {
   __shared__ uint32_t whist[kSortWarps][kRadix];
   __shared__ uint64_t tile_base[kRadix];
+  __shared__ uint64_t sm_scan[32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t n = count.get();
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
   if (base >= n) return;  // uniform over the block
   for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortThreads)
     (&whist[0][0])[i] = 0;
-  for (int d = threadIdx.x; d < kRadix; d += kSortThreads)
-    tile_base[d] = offsets[(int64_t)d * ntiles + blockIdx.x];
+  if (fused) {
+    // thread d: total of digit d over all tiles, and over the tiles before this one
+    const int d = threadIdx.x;  // kSortThreads == kRadix
+    uint64_t tot = 0, pre = 0;
+    for (int64_t t = 0; t < ntiles; ++t) {
+      const uint64_t v = offsets[(int64_t)d * ntiles + t];
+      tot += v;
+      if (t < blockIdx.x) pre += v;
+    }
+    uint64_t bt;
+    const uint64_t inc = block_inclusive_scan(tot, sm_scan, &bt);
+    tile_base[d] = inc - tot + pre;
+  } else {
+    for (int d = threadIdx.x; d < kRadix; d += kSortThreads)
+      tile_base[d] = offsets[(int64_t)d * ntiles + blockIdx.x];
+  }
   __syncthreads();
 
   uint64_t k[kSortItems];
@@ -180,9 +231,9 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     const bool valid = g < n;
     k[i] = valid ? keys_in[g] : 0ull;
     if (kVals) v[i] = valid ? vals_in[g] : V(0);
-    const int d = valid ? digit_of(k[i], shift, mask) : kRadix + lane;
+    const int d = valid ? digit_of(k[i], shift, mask) : kRadix;
     dg[i] = d;
-    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const unsigned peers = digit_peers(d, valid, bits);
     const uint32_t before = valid ? whist[warp][d] : 0u;
     __syncwarp();
     if (valid && lane == __ffs(peers) - 1) whist[warp][d] += (uint32_t)__popc(peers);
@@ -223,10 +274,15 @@ int scan_u64(const T* in, uint64_t* out, DevCount count, bool inclusive, uint64_
   const int64_t ntiles = ceil_div(count.max > 0 ? count.max : 1, kScanTile);
   uint64_t* tile_sums = reinterpret_cast<uint64_t*>(scratch);
   k_scan_tile_sums<T><<<(unsigned)ntiles, kScanThreads, 0, st>>>(in, count, tile_sums);
-  k_scan_tile_offsets<<<1, kScanThreads, 0, st>>>(tile_sums, ntiles, total);
-  if (count.max > 0)
+  if (ntiles <= kFusedTiles) {
+    // the tile kernel sums its predecessors' totals itself (and writes the total)
     k_scan_tiles<T><<<(unsigned)ntiles, kScanThreads, 0, st>>>(in, out, count, tile_sums,
-                                                                inclusive ? 1 : 0);
+                                                                inclusive ? 1 : 0, 1, total);
+  } else {
+    k_scan_tile_offsets<<<1, kScanThreads, 0, st>>>(tile_sums, ntiles, total);
+    k_scan_tiles<T><<<(unsigned)ntiles, kScanThreads, 0, st>>>(in, out, count, tile_sums,
+                                                                inclusive ? 1 : 0, 0, nullptr);
+  }
   CPA_LAUNCH_CHECK();
   return CPA_OK;
 }
@@ -256,19 +312,21 @@ int radix_sort(uint64_t* keys, uint64_t* keys_alt, V* vals, V* vals_alt, DevCoun
   V* src_v = vals;
   V* dst_v = vals_alt;
   int alt = 0;
+  const int fused = ntiles <= kFusedTiles ? 1 : 0;
   for (int shift = begin_bit; shift < end_bit; shift += 8) {
     const int w = end_bit - shift < 8 ? end_bit - shift : 8;
     const uint32_t mask = (1u << w) - 1u;
-    k_radix_hist<<<(unsigned)ntiles, kSortThreads, 0, st>>>(src_k, count, shift, mask, hist,
+    k_radix_hist<<<(unsigned)ntiles, kSortThreads, 0, st>>>(src_k, count, shift, mask, w, hist,
                                                             ntiles);
-    CPA_TRY(scan_u64<uint64_t>(hist, hist, DevCount{nullptr, nh}, false, nullptr, scan_scratch,
-                               st));
+    if (!fused)
+      CPA_TRY(scan_u64<uint64_t>(hist, hist, DevCount{nullptr, nh}, false, nullptr, scan_scratch,
+                                 st));
     if (vals)
       k_radix_scatter<V, true><<<(unsigned)ntiles, kSortThreads, 0, st>>>(
-          src_k, dst_k, src_v, dst_v, count, shift, mask, hist, ntiles);
+          src_k, dst_k, src_v, dst_v, count, shift, mask, w, hist, ntiles, fused);
     else
       k_radix_scatter<V, false><<<(unsigned)ntiles, kSortThreads, 0, st>>>(
-          src_k, dst_k, nullptr, nullptr, count, shift, mask, hist, ntiles);
+          src_k, dst_k, nullptr, nullptr, count, shift, mask, w, hist, ntiles, fused);
     CPA_LAUNCH_CHECK();
     uint64_t* tk = src_k;
     src_k = dst_k;
