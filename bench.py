@@ -46,6 +46,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision series")
     p.add_argument("--no-launch-count", action="store_true",
                    help="skip counting kernels with the torch profiler (use under ncu)")
     p.add_argument("--cpu-sample-updates", type=int, default=4,
@@ -223,57 +224,65 @@ def main():
     index = cpa.cpa_index_build(coo)
     s, tau = SAMPLES, 2.0 ** -TAU_EXP
     seed = rank  # independent decompositions per rank (random restarts)
-    fs = [torch.from_numpy(a).cuda() for a in init]
-    lam = torch.empty(RANK, dtype=torch.float64, device="cuda")
-    fitd = torch.empty(1, dtype=torch.float64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
-    state = {"it": 0}
 
-    def step(profile=0):
-        res = cpa.cp_arls_lev(index, None, rank=RANK, samples=s, tau=tau, iters=ETA, seed=seed,
-                              iter_offset=state["it"], profile=profile, out=(fs, lam, fitd))
-        state["it"] += ETA
-        return res
+    def series(precision, count_launch=False):
+        """W untimed + K timed epochs from the same initial factors."""
+        fs = [torch.from_numpy(a).cuda() for a in init]
+        lam = torch.empty(RANK, dtype=torch.float64, device="cuda")
+        fitd = torch.empty(1, dtype=torch.float64, device="cuda")
+        state = {"it": 0}
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    launches_per_step = None if args.no_launch_count else count_launches(lambda: step())
+        def step(profile=0):
+            res = cpa.cp_arls_lev(index, None, rank=RANK, samples=s, tau=tau, iters=ETA, seed=seed,
+                                  iter_offset=state["it"], profile=profile, out=(fs, lam, fitd),
+                                  precision=precision)
+            state["it"] += ETA
+            return res
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        launches = count_launches(lambda: step()) if count_launch else None
+        times, stages, fits, last = [], np.zeros(8), [], {}
+        acc = {"sbar_total": 0, "nnz_sampled_total": 0}
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            flush.add_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = step(profile=1)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            st = res.stats
+            stages += np.array(st["stage_ms"])
+            acc["sbar_total"] += st["sbar_total"]
+            acc["nnz_sampled_total"] += st["nnz_sampled_total"]
+            fits.append(res.fit)
+            last = st
+        total_ms = sum(times)
+        if world > 1:
+            t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total_ms = float(t.item())
+        return dict(total_ms=total_ms, stages=stages, acc=acc, fit=fits[-1], last=last, launches=launches)
+
     clocks = ClockSampler(local)
     clocks.start()
-    times, stages, nnz_tot, sbar_tot = [], np.zeros(8), 0, 0
-    stat_acc = {"sbar_total": 0, "nnz_sampled_total": 0}
-    fits = []
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    for _ in range(args.steps):
-        flush.add_(1.0)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        res = step(profile=1)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1))
-        st = res.stats
-        stages += np.array(st["stage_ms"])
-        stat_acc["sbar_total"] += st["sbar_total"]
-        stat_acc["nnz_sampled_total"] += st["nnz_sampled_total"]
-        fits.append(res.fit)
-        last_stats = st
-    torch.cuda.synchronize()
+    f64 = series(cpa.binding.FP64, count_launch=not args.no_launch_count)
     clk = clocks.stop()
-    total_ms = sum(times)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    mixed = None if args.no_mixed else series(cpa.binding.MIXED)
     updates = args.steps * ETA * len(coo.dims)
-    value = updates * world / (total_ms / 1000.0)
+    value = updates * world / (f64["total_ms"] / 1000.0)
     peaks, peak_src = load_peaks()
     n_updates = updates
+    stages, stat_acc, last_stats = f64["stages"], f64["acc"], f64["last"]
+    launches_per_step = f64["launches"]
     # roofline of the gather-scale-accumulate MTTKRP kernel (stage 2)
     mk_ms = stages[2]
     mk_bytes = mttkrp_bytes(stat_acc, len(coo.dims) - 1) + sum(
@@ -283,7 +292,7 @@ def main():
     stage_share = {nm: round(float(stages[i] / max(stages[6], 1e-9)), 4) for i, nm in enumerate(stage_names)}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": f64["total_ms"] / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "step": "1 epoch = 5 outer iterations x 4 mode updates + exact fit",
                    "l2": "flushed between timed steps (256 MiB write)",
@@ -299,10 +308,17 @@ def main():
         "last_update": {k: last_stats.get(k) for k in ("sdet_last", "pdet_last", "attempts_last", "sbar_last",
                                                        "nnz_sampled_last")},
         "sbar_per_update": stat_acc["sbar_total"] / n_updates,
-        "fit": fits[-1] if fits else None,
+        "fit": f64["fit"],
         "clocks": clk,
         "gpu_launches": (launches_per_step * args.steps) if launches_per_step else None,
     }
+    if mixed is not None:
+        mv = updates * world / (mixed["total_ms"] / 1000.0)
+        line["mixed_precision"] = {
+            "value": mv, "unit": UNIT, "speedup_vs_fp64": mv / value, "fit": mixed["fit"],
+            "fit_fp64": f64["fit"], "fit_diff": mixed["fit"] - f64["fit"],
+            "stages_ms_per_update": {nm: float(mixed["stages"][i] / n_updates) for i, nm in enumerate(stage_names)},
+            "note": "same init and epochs; FP32 factors/Grams/products, FP64 factorisations"}
     if rank == 0 and not args.no_e2e:
         line["e2e"] = e2e(cpa, coo, init, args)
     if rank == 0 and not args.no_cpu_baseline and world == 1:

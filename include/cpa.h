@@ -55,6 +55,9 @@ extern "C" {
 #define CPA_F32 1 /* float values */
 #define CPA_F64 2 /* double values */
 #define CPA_FP64 0      /* every product and solve in FP64 */
+#define CPA_MIXED 1     /* factors, Grams, sampled products and row solves in FP32 (FP64
+                           accumulation across tiles); r x r factorisations, sampling
+                           probabilities and lambda in FP64 */
 #define CPA_FIT_NONE 0  /* no fit computed (fit output set to NaN) */
 #define CPA_FIT_EXACT 1 /* exact fit of Eq. 5.1 after the run (and per epoch if tol > 0) */
 
@@ -93,7 +96,7 @@ typedef struct {
  *   seed        Philox key of the random draws
  *   iter_offset added to the outer iteration number in the Philox counter, so a run
  *               can be resumed with the same stream of draws
- *   precision   CPA_FP64
+ *   precision   CPA_FP64 or CPA_MIXED
  *   fit_mode    CPA_FIT_EXACT or CPA_FIT_NONE
  *   det_cap     largest candidate product the deterministic search may enumerate
  *   reject_cap  largest number of draws of one random slot
@@ -197,6 +200,21 @@ int cp_arls_lev(const cpa_index* index, const cpa_options* opt, double* lambda,
  * index.  Arguments as for cpa_index_build and cp_arls_lev. */
 int cp_arls_lev_coo(const cpa_coo* coo, const cpa_options* opt, double* lambda,
                     double* const* factors, int32_t io_on_device, double* fit, cpa_stats* stats);
+
+/* One update of mode `mode_k` (the inner step of Alg. 3): leverage scores of every
+ * factor, SkrpLev over the other modes, the sampled MTTKRP and Gram, the solve, the
+ * normalisation -- the same kernels and precision as cp_arls_lev (opt->precision).
+ *   factors   host array of `order` DEVICE pointers to n_m x r doubles; factor
+ *             mode_k is overwritten with the new (column-normalised) factor
+ *   lambda    device, r doubles out
+ *   iter      global outer iteration of the Philox counters
+ *   idx, cnt, wgt  device outputs (opt->samples entries): the rows used, in the
+ *             order of cpa_skrp_lev (linear keys, counts, weights)
+ *   counts    host out: {sbar, s_det, attempts}; pdet: host out
+ * Errors as cp_arls_lev. */
+int cpa_mode_update(const cpa_index* index, const cpa_options* opt, int32_t mode_k, uint64_t iter,
+                    double* const* factors, double* lambda, uint64_t* idx, uint32_t* cnt, double* wgt,
+                    int64_t* counts, double* pdet);
 
 /* ---- stage entry points (each one step of the per-mode update) --------------- */
 

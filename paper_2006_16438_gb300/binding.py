@@ -32,6 +32,7 @@ WARN_RANK_DEFICIENT_LEV = 2
 F32 = 1
 F64 = 2
 FP64 = 0
+MIXED = 1
 FIT_NONE = 0
 FIT_EXACT = 1
 
@@ -39,6 +40,7 @@ EXPORTED = [
     "cpa_options_default", "cpa_strerror", "cpa_index_build", "cpa_index_free", "cpa_index_info",
     "cpa_index_export", "cp_arls_lev", "cp_arls_lev_coo", "cpa_philox4x64", "cpa_leverage",
     "cpa_cdf", "cpa_skrp_lev", "cpa_sampled_mttkrp", "cpa_solve", "cpa_fit", "cpa_leverage_noalloc",
+    "cpa_mode_update",
 ]
 
 
@@ -113,6 +115,7 @@ def _declare(lib):
         "cpa_index_export": ([P, I32, P, P, P, P, P], I32),
         "cp_arls_lev": ([P, P, P, P, I32, P, P], I32),
         "cp_arls_lev_coo": ([P, P, P, P, I32, P, P], I32),
+        "cpa_mode_update": ([P, P, I32, U64, P, P, P, P, P, P, P], I32),
         "cpa_philox4x64": ([P, P, I64, P, P], I32),
         "cpa_leverage": ([P, I64, I32, P, P], I32),
         "cpa_leverage_noalloc": ([P, I64, I32, P, P], I32),
@@ -265,14 +268,15 @@ class Result:
 
 def cp_arls_lev(index: Index, factors, *, rank, samples, tau=1.0, iters=10, epoch_len=5, patience=3,
                 tol=0.0, seed=0, iter_offset=0, fit_mode=FIT_EXACT, det_cap=1 << 24,
-                reject_cap=4096, on_device=True, profile=0, out=None) -> Result:
+                reject_cap=4096, on_device=True, profile=0, out=None, precision=FP64) -> Result:
     """Alg. 3 on the GPU.  ``factors``: list of CUDA float64 tensors (n_k x rank), or
     numpy arrays with on_device=False.  Returns a Result with new factor copies."""
     torch = _torch()
     o = default_options(rank=rank, samples=int(samples), tau=float(tau), iters=int(iters),
                         epoch_len=int(epoch_len), patience=int(patience), tol=float(tol),
                         seed=int(seed), iter_offset=int(iter_offset), fit_mode=int(fit_mode),
-                        det_cap=int(det_cap), reject_cap=int(reject_cap), profile=int(profile))
+                        det_cap=int(det_cap), reject_cap=int(reject_cap), profile=int(profile),
+                        precision=int(precision))
     o.stream = _stream()
     stats = Stats()
     fit = C.c_double(0.0)
@@ -311,6 +315,29 @@ def cp_arls_lev_coo(coo, factors, *, rank, samples, tau=1.0, iters=10, seed=0, f
                                 _ptr_array([f.ctypes.data for f in fs]), 0, C.byref(fit), C.byref(stats))
     _check(rc, "cp_arls_lev_coo")
     return Result(lam, fs, fit.value, stats.as_dict(), rc)
+
+
+def cpa_mode_update(index: Index, factors, k, *, rank, samples, tau=1.0, seed=0, it=0, precision=FP64,
+                    det_cap=1 << 24, reject_cap=4096):
+    """One update of mode k.  factors: CUDA float64 tensors (factor k is replaced in
+    place).  Returns dict(lam, idx, cnt, wgt, sbar, sdet, attempts, pdet, warnings)."""
+    torch = _torch()
+    o = default_options(rank=rank, samples=int(samples), tau=float(tau), seed=int(seed),
+                        precision=int(precision), det_cap=int(det_cap), reject_cap=int(reject_cap))
+    o.stream = _stream()
+    s = int(samples)
+    lam = torch.empty(rank, dtype=torch.float64, device="cuda")
+    idx = torch.empty(s, dtype=torch.uint64, device="cuda")
+    cnt = torch.empty(s, dtype=torch.int32, device="cuda")
+    wgt = torch.empty(s, dtype=torch.float64, device="cuda")
+    counts = (C.c_int64 * 3)()
+    pdet = C.c_double(0)
+    rc = _check(_lib().cpa_mode_update(index.h, C.byref(o), int(k), int(it),
+                                       _ptr_array([f.data_ptr() for f in factors]), _ptr(lam), _ptr(idx),
+                                       _ptr(cnt), _ptr(wgt), counts, C.byref(pdet)), "cpa_mode_update")
+    sbar = counts[0]
+    return dict(lam=lam, idx=idx[:sbar], cnt=cnt[:sbar], wgt=wgt[:sbar], sbar=sbar, sdet=counts[1],
+                attempts=counts[2], pdet=pdet.value, warnings=rc)
 
 
 # --------------------------------------------------------------------------- stages

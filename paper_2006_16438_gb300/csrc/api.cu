@@ -92,6 +92,13 @@ __global__ void k_philox(const uint64_t* __restrict__ ctr, uint64_t k0, uint64_t
   }
 }
 
+template <class TO, class TI>
+__global__ void k_convert(const TI* __restrict__ in, int64_t n, TO* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (TO)in[i];
+}
+
 inline unsigned blocks(int64_t n, int threads = 256) {
   int64_t b = ceil_div(n > 0 ? n : 1, threads);
   const int64_t cap = (int64_t)num_sms() * 16;
@@ -120,14 +127,15 @@ struct DevBuf {
 
 // Leverage distribution of one factor: lev (optional), CDF C, info; A normalised in
 // place when `normalize_out` (the update path), untouched otherwise.
-int refresh_distribution(double* A, int64_t n, int r, uint64_t* C, DistInfo* info, double* Pm,
+template <class FT>
+int refresh_distribution(FT* A, int64_t n, int r, uint64_t* C, DistInfo* info, double* Pm,
                          double* GA, SmallFactor* fac, int* warn, void* scan_scratch, bool normalize_out,
                          double* lev_out, cudaStream_t st) {
   CPA_CUDA_TRY(cudaMemsetAsync(GA, 0, sizeof(double) * r * r, st));
-  CPA_TRY(gram_rows(A, n, r, GA, st));
+  CPA_TRY(gram_rows<FT>(A, n, r, GA, st));
   CPA_TRY(factor_spd(GA, r, 1, 1, 1e-12, fac, warn, CPA_WARN_RANK_DEFICIENT_LEV, st));
   CPA_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(DistInfo), st));
-  CPA_TRY(lev_rows(A, n, r, fac, lev_out, C, info, normalize_out ? A : nullptr, st));
+  CPA_TRY(lev_rows<FT>(A, n, r, fac, lev_out, C, info, normalize_out ? A : nullptr, st));
   CPA_TRY(cdf_from_q(C, C, n, info, scan_scratch, st));
   CPA_TRY(phat_from_cdf(C, n, info, Pm, st));
   return CPA_OK;
@@ -197,7 +205,7 @@ int check_options(const cpa_options* o) {
   if (o->samples < 1 || o->samples >= (1ll << 31)) return CPA_ERR_ARG;
   if (!(o->tau >= 0.0 && o->tau <= 1.0)) return CPA_ERR_ARG;
   if (o->iters < 0 || o->reject_cap < 1 || o->det_cap < 1) return CPA_ERR_ARG;
-  if (o->precision != CPA_FP64) return CPA_ERR_UNSUPPORTED;
+  if (o->precision != CPA_FP64 && o->precision != CPA_MIXED) return CPA_ERR_ARG;
   if (o->fit_mode != CPA_FIT_EXACT && o->fit_mode != CPA_FIT_NONE) return CPA_ERR_ARG;
   if (o->tol < 0.0) return CPA_ERR_ARG;
   return CPA_OK;
@@ -217,17 +225,19 @@ __global__ void k_advance_iter(uint64_t* it) { *it += 1; }
 
 struct Plan {
   // key
-  int r = 0, D = 0, reject_cap = 0, profile = 0;
+  int r = 0, D = 0, reject_cap = 0, profile = 0, prec = CPA_FP64, ftb = 8;
   int64_t s = 0, det_cap = 0, det_buf = 0;
   double tau = 0.0;
   uint64_t seed = 0;
   // workspace
   char* base = nullptr;
-  double* Fm[kMaxOrder] = {};
+  void* Fm[kMaxOrder] = {};   // factors in the run's element type (ftb bytes)
   uint64_t* Cm[kMaxOrder] = {};
   double* Pm[kMaxOrder] = {};
+  double* stage64 = nullptr;  // FP64 staging of one factor (mixed precision in/out)
   DistInfo* info = nullptr;
-  double *M = nullptr, *Gs = nullptr, *GA = nullptr, *lam = nullptr, *fitd = nullptr, *fit_ws = nullptr;
+  void* M = nullptr;
+  double *Gs = nullptr, *GA = nullptr, *lam = nullptr, *fitd = nullptr, *fit_ws = nullptr;
   SmallFactor *fsolve = nullptr, *flev = nullptr;
   int* warn = nullptr;
   DevStats* dstats = nullptr;
@@ -243,7 +253,8 @@ struct Plan {
 
   bool matches(const cpa_options* o) const {
     return o->rank == r && o->samples == s && o->tau == tau && o->seed == seed &&
-           o->reject_cap == reject_cap && o->det_cap == det_cap && (o->profile != 0) == (profile != 0);
+           o->reject_cap == reject_cap && o->det_cap == det_cap && (o->profile != 0) == (profile != 0) &&
+           o->precision == prec;
   }
 
   int init(const cpa_index* X, const cpa_options* o, cudaStream_t st) {
@@ -255,6 +266,8 @@ struct Plan {
     reject_cap = o->reject_cap;
     det_cap = o->det_cap;
     profile = o->profile != 0;
+    prec = o->precision;
+    ftb = prec == CPA_MIXED ? 4 : 8;
     det_buf = det_buffer_capacity(s, tau, det_cap);
     use_graph = !(tau < 1.0 && tau * (double)s < 1.0);  // no top-s host sync possible
     int64_t nmax = 1, nsum = 0;
@@ -270,12 +283,13 @@ struct Plan {
     for (int pass = 0; pass < 2; ++pass) {
       a.used = 0;
       for (int m = 0; m < D; ++m) {
-        Fm[m] = a.take<double>((size_t)X->dims[m] * r);
+        Fm[m] = a.take<char>((size_t)X->dims[m] * r * ftb);
         Cm[m] = a.take<uint64_t>(X->dims[m]);
         Pm[m] = a.take<double>(X->dims[m]);
       }
+      stage64 = prec == CPA_MIXED ? a.take<double>((size_t)nmax * r) : nullptr;
       info = a.take<DistInfo>(kMaxOrder);
-      M = a.take<double>((size_t)nmax * r);
+      M = a.take<char>((size_t)nmax * r * ftb);
       Gs = a.take<double>(r * r);
       GA = a.take<double>(r * r);
       lam = a.take<double>(kMaxRank);
@@ -288,7 +302,7 @@ struct Plan {
       scan_ws = a.take<char>(scan_workspace(nmax));
       iter_dev = a.take<uint64_t>(1);
       sample_buffers_carve(a, Lsum, s, det_buf, &SB[0]);
-      mttkrp_buffers_carve(a, s, r, &MB);
+      mttkrp_buffers_carve(a, s, r, ftb, &MB);
       if (pass == 0) {
         if (cudaMalloc((void**)&a.base, a.used) != cudaSuccess) return CPA_ERR_OOM;
         base = a.base;
@@ -311,6 +325,12 @@ struct Plan {
 
   // Enqueue one outer iteration: every mode updated once (Alg. 3 inner loop).
   int enqueue_iteration(const cpa_index* X, Profiler& prof, cudaStream_t st) {
+    return prec == CPA_MIXED ? enqueue_iteration_t<float>(X, prof, st)
+                             : enqueue_iteration_t<double>(X, prof, st);
+  }
+
+  template <class FT>
+  int enqueue_iteration_t(const cpa_index* X, Profiler& prof, cudaStream_t st) {
     FactorPtrs F;
     for (int m = 0; m < D; ++m) F.A[m] = Fm[m];
     for (int k = 0; k < D; ++k) {
@@ -335,17 +355,19 @@ struct Plan {
       CPA_TRY(skrp_lev(Ps, SB[k], st, false));
       CPA_TRY(prof.mark(0));
       const int64_t nk = X->dims[k];
-      CPA_CUDA_TRY(cudaMemsetAsync(M, 0, sizeof(double) * nk * r, st));
+      FT* Mt = static_cast<FT*>(M);
+      FT* Fk = static_cast<FT*>(Fm[k]);
+      CPA_CUDA_TRY(cudaMemsetAsync(Mt, 0, sizeof(FT) * nk * r, st));
       CPA_CUDA_TRY(cudaMemsetAsync(Gs, 0, sizeof(double) * r * r, st));
       cudaEvent_t mid = prof.pending(1);
-      CPA_TRY(sampled_mttkrp(X, k, F, r, SB[k].idx_packed, SB[k].wgt, DevCount{&SB[k].state->sbar, s}, M,
-                             Gs, MB, st, mid));
+      CPA_TRY(sampled_mttkrp<FT>(X, k, F, r, SB[k].idx_packed, SB[k].wgt, DevCount{&SB[k].state->sbar, s},
+                                 Mt, Gs, MB, st, mid));
       CPA_TRY(prof.mark(2));
       CPA_TRY(factor_spd(Gs, r, 0, 0, 1e-13, fsolve, warn, CPA_WARN_SINGULAR_GRAM, st));
-      CPA_TRY(solve_rows(M, nk, r, fsolve, Fm[k], st));
+      CPA_TRY(solve_rows<FT>(Mt, nk, r, fsolve, Fk, st));
       CPA_TRY(prof.mark(3));
-      CPA_TRY(refresh_distribution(Fm[k], nk, r, Cm[k], info + k, Pm[k], GA, flev, warn, scan_ws, true,
-                                   nullptr, st));
+      CPA_TRY(refresh_distribution<FT>(Fk, nk, r, Cm[k], info + k, Pm[k], GA, flev, warn, scan_ws, true,
+                                       nullptr, st));
       k_copy_lambda<<<1, 64, 0, st>>>(flev, r, lam);
       k_stats<<<1, 1, 0, st>>>(dstats, SB[k].state, MB.total, warn);
       CPA_LAUNCH_CHECK();
@@ -383,6 +405,47 @@ struct Plan {
   int run(const cpa_index* X, const cpa_options* opt, double* lambda, double* const* factors,
           int32_t io_on_device, double* fit, cpa_stats* stats, cudaStream_t st);
 
+  // One update of mode k (the driver's steps), rows exported in ascending order.
+  template <class FT>
+  int update_once(const cpa_index* X, int k, uint64_t iter, uint64_t* idx_linear, cudaStream_t st) {
+    FactorPtrs F;
+    for (int m = 0; m < D; ++m) F.A[m] = Fm[m];
+    const auto& mode = X->mode[k];
+    SampleParams Ps;
+    memset(&Ps, 0, sizeof(Ps));
+    Ps.L = mode.L;
+    for (int t = 0; t < mode.L.d; ++t) {
+      Ps.D.C[t] = Cm[mode.L.mode[t]];
+      Ps.D.info[t] = info + mode.L.mode[t];
+      Ps.D.P[t] = Pm[mode.L.mode[t]];
+    }
+    Ps.s = s;
+    Ps.tau = tau;
+    Ps.seed = seed;
+    Ps.iter = iter;
+    Ps.mode_k = k;
+    Ps.reject_cap = reject_cap;
+    Ps.det_cap = tau < 1.0 ? det_cap : 1;
+    Ps.det_buf = det_buf;
+    SampleBuffers B = SB[k];
+    B.idx_linear = idx_linear;
+    CPA_TRY(skrp_lev(Ps, B, st, true));
+    const int64_t nk = X->dims[k];
+    FT* Mt = static_cast<FT*>(M);
+    FT* Fk = static_cast<FT*>(Fm[k]);
+    CPA_CUDA_TRY(cudaMemsetAsync(Mt, 0, sizeof(FT) * nk * r, st));
+    CPA_CUDA_TRY(cudaMemsetAsync(Gs, 0, sizeof(double) * r * r, st));
+    CPA_TRY(sampled_mttkrp<FT>(X, k, F, r, B.idx_packed, B.wgt, DevCount{&B.state->sbar, s}, Mt, Gs, MB,
+                               st));
+    CPA_TRY(factor_spd(Gs, r, 0, 0, 1e-13, fsolve, warn, CPA_WARN_SINGULAR_GRAM, st));
+    CPA_TRY(solve_rows<FT>(Mt, nk, r, fsolve, Fk, st));
+    CPA_TRY(refresh_distribution<FT>(Fk, nk, r, Cm[k], info + k, Pm[k], GA, flev, warn, scan_ws, true,
+                                     nullptr, st));
+    k_copy_lambda<<<1, 64, 0, st>>>(flev, r, lam);
+    CPA_LAUNCH_CHECK();
+    return CPA_OK;
+  }
+
   ~Plan() {
     if (exec) cudaGraphExecDestroy(exec);
     if (cap_stream) cudaStreamDestroy(cap_stream);
@@ -402,8 +465,16 @@ int Plan::run(const cpa_index* X, const cpa_options* opt, double* lambda, double
   CPA_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(DistInfo) * kMaxOrder, st));
   CPA_CUDA_TRY(cudaMemsetAsync(&SB[0].state->status, 0, sizeof(int), st));
   const cudaMemcpyKind kin = io_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  for (int m = 0; m < D; ++m)
-    CPA_CUDA_TRY(cudaMemcpyAsync(Fm[m], factors[m], sizeof(double) * X->dims[m] * r, kin, st));
+  for (int m = 0; m < D; ++m) {
+    const int64_t cnt = X->dims[m] * r;
+    if (prec == CPA_MIXED) {
+      CPA_CUDA_TRY(cudaMemcpyAsync(stage64, factors[m], sizeof(double) * cnt, kin, st));
+      k_convert<float, double><<<blocks(cnt), 256, 0, st>>>(stage64, cnt, static_cast<float*>(Fm[m]));
+      CPA_LAUNCH_CHECK();
+    } else {
+      CPA_CUDA_TRY(cudaMemcpyAsync(Fm[m], factors[m], sizeof(double) * cnt, kin, st));
+    }
+  }
   {
     std::vector<double> ones(kMaxRank, 1.0);
     const double nan4[4] = {NAN, NAN, NAN, NAN};
@@ -420,9 +491,14 @@ int Plan::run(const cpa_index* X, const cpa_options* opt, double* lambda, double
     cudaEventRecord(call0, st);
   }
   // initial leverage distributions (Alg. 3: p_k <- l(A_k)/r for the initial guess)
-  for (int m = 0; m < D; ++m)
-    CPA_TRY(refresh_distribution(Fm[m], X->dims[m], r, Cm[m], info + m, Pm[m], GA, flev, warn, scan_ws,
-                                 false, nullptr, st));
+  for (int m = 0; m < D; ++m) {
+    if (prec == CPA_MIXED)
+      CPA_TRY(refresh_distribution<float>(static_cast<float*>(Fm[m]), X->dims[m], r, Cm[m], info + m, Pm[m],
+                                          GA, flev, warn, scan_ws, false, nullptr, st));
+    else
+      CPA_TRY(refresh_distribution<double>(static_cast<double*>(Fm[m]), X->dims[m], r, Cm[m], info + m,
+                                           Pm[m], GA, flev, warn, scan_ws, false, nullptr, st));
+  }
   if (use_graph && !exec) CPA_TRY(capture(X));
   FactorPtrs F;
   for (int m = 0; m < D; ++m) F.A[m] = Fm[m];
@@ -451,7 +527,8 @@ int Plan::run(const cpa_index* X, const cpa_options* opt, double* lambda, double
     iters_done = it;
     if (opt->tol > 0.0 && opt->fit_mode == CPA_FIT_EXACT) {
       CPA_TRY(eprof.mark(-1));
-      CPA_TRY(fit_enqueue(X, F, lam, r, fit_ws, fitd, st));
+      CPA_TRY(prec == CPA_MIXED ? fit_enqueue<float>(X, F, lam, r, fit_ws, fitd, st)
+                                : fit_enqueue<double>(X, F, lam, r, fit_ws, fitd, st));
       CPA_TRY(eprof.mark(5));
       double f = 0.0;
       int status = 0;
@@ -471,7 +548,8 @@ int Plan::run(const cpa_index* X, const cpa_options* opt, double* lambda, double
   }
   if (!(opt->tol > 0.0) && opt->fit_mode == CPA_FIT_EXACT) {
     CPA_TRY(eprof.mark(-1));
-    CPA_TRY(fit_enqueue(X, F, lam, r, fit_ws, fitd, st));
+    CPA_TRY(prec == CPA_MIXED ? fit_enqueue<float>(X, F, lam, r, fit_ws, fitd, st)
+                              : fit_enqueue<double>(X, F, lam, r, fit_ws, fitd, st));
     CPA_TRY(eprof.mark(5));
     CPA_CUDA_TRY(cudaMemcpyAsync(&fit_val, fitd, sizeof(double), cudaMemcpyDeviceToHost, st));
   }
@@ -485,8 +563,17 @@ int Plan::run(const cpa_index* X, const cpa_options* opt, double* lambda, double
   CPA_CUDA_TRY(cudaStreamSynchronize(st));
   if (status < 0) return status;
   const cudaMemcpyKind kout = io_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  for (int m = 0; m < D; ++m)
-    CPA_CUDA_TRY(cudaMemcpyAsync(factors[m], Fm[m], sizeof(double) * X->dims[m] * r, kout, st));
+  for (int m = 0; m < D; ++m) {
+    const int64_t cnt = X->dims[m] * r;
+    if (prec == CPA_MIXED) {
+      k_convert<double, float><<<blocks(cnt), 256, 0, st>>>(static_cast<const float*>(Fm[m]), cnt, stage64);
+      CPA_LAUNCH_CHECK();
+      CPA_CUDA_TRY(cudaMemcpyAsync(factors[m], stage64, sizeof(double) * cnt, kout, st));
+      CPA_CUDA_TRY(cudaStreamSynchronize(st));  // stage64 is reused by the next mode
+    } else {
+      CPA_CUDA_TRY(cudaMemcpyAsync(factors[m], Fm[m], sizeof(double) * cnt, kout, st));
+    }
+  }
   CPA_CUDA_TRY(cudaMemcpyAsync(lambda, lam, sizeof(double) * r, kout, st));
   if (fit && io_on_device) CPA_CUDA_TRY(cudaMemcpyAsync(fit, fitd, sizeof(double), cudaMemcpyDeviceToDevice, st));
   CPA_CUDA_TRY(cudaStreamSynchronize(st));
@@ -615,9 +702,9 @@ int cpa_leverage(const double* A, int64_t n, int32_t r, double* lev, void* strea
     }
     CPA_CUDA_TRY(cudaMemsetAsync(G, 0, sizeof(double) * r * r, st));
     CPA_CUDA_TRY(cudaMemsetAsync(warn, 0, sizeof(int), st));
-    CPA_TRY(gram_rows(A, n, r, G, st));
+    CPA_TRY(gram_rows<double>(A, n, r, G, st));
     CPA_TRY(factor_spd(G, r, 1, 1, 1e-12, f, warn, CPA_WARN_RANK_DEFICIENT_LEV, st));
-    CPA_TRY(lev_rows(A, n, r, f, lev, nullptr, nullptr, nullptr, st));
+    CPA_TRY(lev_rows<double>(A, n, r, f, lev, nullptr, nullptr, (double*)nullptr, st));
     int hwarn = 0;
     CPA_CUDA_TRY(cudaMemcpyAsync(&hwarn, warn, sizeof(int), cudaMemcpyDeviceToHost, st));
     CPA_CUDA_TRY(cudaStreamSynchronize(st));
@@ -757,7 +844,7 @@ int cpa_sampled_mttkrp(const cpa_index* X, int32_t mode_k, const double* const* 
   for (int pass = 0; pass < 2; ++pass) {
     a.used = 0;
     packed = a.take<uint64_t>(sbar);
-    mttkrp_buffers_carve(a, sbar, r, &B);
+    mttkrp_buffers_carve(a, sbar, r, 8, &B);
     if (pass == 0) {
       CPA_TRY(buf.alloc(a.used, st));
       a.base = (char*)buf.p;
@@ -765,7 +852,7 @@ int cpa_sampled_mttkrp(const cpa_index* X, int32_t mode_k, const double* const* 
   }
   k_linear_to_packed<<<blocks(sbar), 256, 0, st>>>(mode.L, idx, sbar, packed);
   CPA_LAUNCH_CHECK();
-  CPA_TRY(sampled_mttkrp(X, mode_k, F, r, packed, wgt, DevCount{nullptr, sbar}, M, G, B, st));
+  CPA_TRY(sampled_mttkrp<double>(X, mode_k, F, r, packed, wgt, DevCount{nullptr, sbar}, M, G, B, st));
   uint64_t tot = 0;
   CPA_CUDA_TRY(cudaMemcpyAsync(&tot, B.total, sizeof(tot), cudaMemcpyDeviceToHost, st));
   CPA_CUDA_TRY(cudaStreamSynchronize(st));
@@ -785,13 +872,13 @@ int cpa_solve(const double* G, const double* M, int64_t n, int32_t r, double* A,
   int* warn = (int*)(GA + r * r);
   CPA_CUDA_TRY(cudaMemsetAsync(warn, 0, sizeof(int), st));
   CPA_TRY(factor_spd(G, r, 0, 0, 1e-13, fs, warn, CPA_WARN_SINGULAR_GRAM, st));
-  CPA_TRY(solve_rows(M, n, r, fs, A, st));
+  CPA_TRY(solve_rows<double>(M, n, r, fs, A, st));
   CPA_CUDA_TRY(cudaMemsetAsync(GA, 0, sizeof(double) * r * r, st));
-  CPA_TRY(gram_rows(A, n, r, GA, st));
+  CPA_TRY(gram_rows<double>(A, n, r, GA, st));
   int dummy_warn_bit = 0;
   CPA_TRY(factor_spd(GA, r, 1, 1, 1e-12, fl, warn, dummy_warn_bit, st));
   k_copy_lambda<<<1, 64, 0, st>>>(fl, r, lambda);
-  CPA_TRY(scale_columns(A, n, r, lambda, st));
+  CPA_TRY(scale_columns<double>(A, n, r, lambda, st));
   int hwarn = 0;
   CPA_CUDA_TRY(cudaMemcpyAsync(&hwarn, warn, sizeof(int), cudaMemcpyDeviceToHost, st));
   CPA_CUDA_TRY(cudaStreamSynchronize(st));
@@ -811,7 +898,7 @@ int cpa_fit(const cpa_index* X, const double* const* factors, const double* lamb
   CPA_TRY(buf.alloc(fit_buffers_bytes(X->order, r) + 256, st));
   double* fit_dev = (double*)buf.p;
   double* scratch = fit_dev + 32;
-  CPA_TRY(fit_enqueue(X, F, lambda, r, scratch, fit_dev, st));
+  CPA_TRY(fit_enqueue<double>(X, F, lambda, r, scratch, fit_dev, st));
   CPA_CUDA_TRY(cudaMemcpyAsync(fit, fit_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
   CPA_CUDA_TRY(cudaStreamSynchronize(st));
   return CPA_OK;
@@ -859,6 +946,67 @@ int cp_arls_lev(const cpa_index* Xc, const cpa_options* opt, double* lambda, dou
   const int rc = P->run(X, opt, lambda, factors, io_on_device, fit, stats, st);
   if (own) plan_free(own);
   return rc;
+}
+
+int cpa_mode_update(const cpa_index* X, const cpa_options* opt, int32_t mode_k, uint64_t iter,
+                    double* const* factors, double* lambda, uint64_t* idx, uint32_t* cnt, double* wgt,
+                    int64_t* counts, double* pdet) {
+  if (!X || !factors || !lambda || !idx || !cnt || !wgt || mode_k < 0 || mode_k >= X->order)
+    return CPA_ERR_ARG;
+  CPA_TRY(check_options(opt));
+  for (int m = 0; m < X->order; ++m)
+    if (!factors[m]) return CPA_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)opt->stream;
+  Plan* P = new (std::nothrow) Plan();
+  if (!P) return CPA_ERR_OOM;
+  struct Guard {
+    Plan* p;
+    ~Guard() { plan_free(p); }
+  } guard{P};
+  CPA_TRY(P->init(X, opt, st));
+  const int D = X->order, r = P->r;
+  CPA_CUDA_TRY(cudaMemsetAsync(P->warn, 0, sizeof(int) * 4, st));
+  CPA_CUDA_TRY(cudaMemsetAsync(P->info, 0, sizeof(DistInfo) * kMaxOrder, st));
+  for (int m = 0; m < D; ++m) {
+    const int64_t c = X->dims[m] * r;
+    if (P->prec == CPA_MIXED) {
+      k_convert<float, double><<<blocks(c), 256, 0, st>>>(factors[m], c, static_cast<float*>(P->Fm[m]));
+      CPA_LAUNCH_CHECK();
+      CPA_TRY(refresh_distribution<float>(static_cast<float*>(P->Fm[m]), X->dims[m], r, P->Cm[m], P->info + m,
+                                          P->Pm[m], P->GA, P->flev, P->warn, P->scan_ws, false, nullptr, st));
+    } else {
+      CPA_CUDA_TRY(cudaMemcpyAsync(P->Fm[m], factors[m], sizeof(double) * c, cudaMemcpyDeviceToDevice, st));
+      CPA_TRY(refresh_distribution<double>(static_cast<double*>(P->Fm[m]), X->dims[m], r, P->Cm[m],
+                                           P->info + m, P->Pm[m], P->GA, P->flev, P->warn, P->scan_ws, false,
+                                           nullptr, st));
+    }
+  }
+  if (P->prec == CPA_MIXED) CPA_TRY(P->update_once<float>(X, mode_k, iter, idx, st));
+  else CPA_TRY(P->update_once<double>(X, mode_k, iter, idx, st));
+  SampleState h;
+  int hwarn = 0;
+  CPA_CUDA_TRY(cudaMemcpyAsync(&h, P->SB[mode_k].state, sizeof(h), cudaMemcpyDeviceToHost, st));
+  CPA_CUDA_TRY(cudaMemcpyAsync(&hwarn, P->warn, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CPA_CUDA_TRY(cudaStreamSynchronize(st));
+  if (h.status < 0) return h.status;
+  const int64_t c = X->dims[mode_k] * r;
+  if (P->prec == CPA_MIXED)
+    k_convert<double, float><<<blocks(c), 256, 0, st>>>(static_cast<const float*>(P->Fm[mode_k]), c,
+                                                        factors[mode_k]);
+  else
+    CPA_CUDA_TRY(cudaMemcpyAsync(factors[mode_k], P->Fm[mode_k], sizeof(double) * c, cudaMemcpyDeviceToDevice,
+                                 st));
+  CPA_CUDA_TRY(cudaMemcpyAsync(lambda, P->lam, sizeof(double) * r, cudaMemcpyDeviceToDevice, st));
+  CPA_CUDA_TRY(cudaMemcpyAsync(cnt, P->SB[mode_k].cnt, sizeof(uint32_t) * h.sbar, cudaMemcpyDeviceToDevice, st));
+  CPA_CUDA_TRY(cudaMemcpyAsync(wgt, P->SB[mode_k].wgt, sizeof(double) * h.sbar, cudaMemcpyDeviceToDevice, st));
+  CPA_CUDA_TRY(cudaStreamSynchronize(st));
+  if (counts) {
+    counts[0] = h.sbar;
+    counts[1] = h.sdet;
+    counts[2] = (int64_t)h.attempts;
+  }
+  if (pdet) *pdet = h.pdet;
+  return hwarn;
 }
 
 int cp_arls_lev_coo(const cpa_coo* coo, const cpa_options* opt, double* lambda, double* const* factors,

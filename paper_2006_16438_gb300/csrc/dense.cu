@@ -23,11 +23,13 @@ __device__ __forceinline__ void pair_of(int p, int r, int* a, int* b) {
   *b = row + (p - start);
 }
 
-template <int PMAX>
-__global__ void __launch_bounds__(kGramThreads) k_gram_rows(const double* __restrict__ A,
+// Per-thread partial sums over a tile are in FT; tile partials are added in FP64.
+template <class FT, int PMAX>
+__global__ void __launch_bounds__(kGramThreads) k_gram_rows(const FT* __restrict__ A,
                                                             int64_t n, int r,
                                                             double* __restrict__ G) {
-  extern __shared__ double tile[];  // kGramRows * r
+  extern __shared__ __align__(16) unsigned char gram_smem[];
+  FT* tile = reinterpret_cast<FT*>(gram_smem);  // kGramRows * r
   const int np = r * (r + 1) / 2;
   int pa[PMAX], pb[PMAX];
   double acc[PMAX];
@@ -41,17 +43,17 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_rows(const double* __rest
        row0 += (int64_t)gridDim.x * kGramRows) {
     const int rows = (int)((n - row0) < kGramRows ? (n - row0) : kGramRows);
     __syncthreads();
-    const double* src = A + row0 * r;
+    const FT* src = A + row0 * r;
     for (int i = threadIdx.x; i < kGramRows * r; i += kGramThreads)
-      tile[i] = i < rows * r ? src[i] : 0.0;
+      tile[i] = i < rows * r ? src[i] : FT(0);
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < PMAX; ++q) {
       const int p = threadIdx.x + q * kGramThreads;
       if (p < np) {
-        double s = 0.0;
+        FT s = FT(0);
         for (int i = 0; i < rows; ++i) s = fma(tile[i * r + pa[q]], tile[i * r + pb[q]], s);
-        acc[q] += s;
+        acc[q] += (double)s;
       }
     }
   }
@@ -314,24 +316,26 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor_spd(const double* __r
 
 // ---- per-row kernels -------------------------------------------------------
 constexpr int kRowThreads = 256;
+constexpr int64_t kManyRows = 1 << 16;  // from here on one thread per row
 
 // Leverage of row a_i (one warp per row, lane c owns coordinate c and c + 32):
 // kind 0: y = X P^T (S a), l = ||y||^2 over the rank's coordinates;
 // kind 1: l = (S a)^T F (S a).
-__global__ void __launch_bounds__(kRowThreads) k_lev_rows(const double* A, int64_t n, int r,
+template <class FT>
+__global__ void __launch_bounds__(kRowThreads) k_lev_rows(const FT* A, int64_t n, int r,
                                                           const SmallFactor* __restrict__ f,
                                                           double* __restrict__ lev,
                                                           uint64_t* __restrict__ q,
-                                                          DistInfo* info, double* A_out) {
-  extern __shared__ double smem[];
-  double* F = smem;       // r * r
-  double* sc = F + r * r; // r
-  double* lam = sc + r;   // r
+                                                          DistInfo* info, FT* A_out) {
+  extern __shared__ __align__(16) unsigned char lev_smem[];
+  FT* F = reinterpret_cast<FT*>(lev_smem);  // r * r
+  FT* sc = F + r * r;                       // r
+  FT* lam = sc + r;                         // r
   __shared__ int perm[kMaxRank];
-  for (int i = threadIdx.x; i < r * r; i += blockDim.x) F[i] = f->F[i];
+  for (int i = threadIdx.x; i < r * r; i += blockDim.x) F[i] = (FT)f->F[i];
   for (int i = threadIdx.x; i < r; i += blockDim.x) {
-    sc[i] = f->scale[i];
-    lam[i] = f->lambda[i];
+    sc[i] = (FT)f->scale[i];
+    lam[i] = (FT)f->lambda[i];
     perm[i] = f->perm[i];
   }
   __syncthreads();
@@ -343,13 +347,13 @@ __global__ void __launch_bounds__(kRowThreads) k_lev_rows(const double* A, int64
   uint64_t my_max = 0;
   uint32_t my_nz = 0;
   for (int64_t row = gw; row < n; row += nwarps) {
-    const double* a = A + row * r;
-    double part = 0.0;
+    const FT* a = A + row * r;
+    FT part = FT(0);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int c = lane + 32 * h;
       if (c < k) {
-        double t = 0.0;
+        FT t = FT(0);
         if (kind == 0) {
           for (int u = 0; u <= c; ++u) {
             const int pu = perm[u];
@@ -364,9 +368,9 @@ __global__ void __launch_bounds__(kRowThreads) k_lev_rows(const double* A, int64
     }
     for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
     if (lane == 0) {
-      if (lev) lev[row] = part;
+      if (lev) lev[row] = (double)part;
       if (q) {
-        double p = part / (double)r;
+        double p = (double)part / (double)r;
         p = p > 0.0 ? (p < 1.0 ? p : 1.0) : 0.0;
         const uint64_t qi = __double2ull_rn(p * 4611686018427387904.0);  // 2^62
         q[row] = qi;
@@ -377,8 +381,8 @@ __global__ void __launch_bounds__(kRowThreads) k_lev_rows(const double* A, int64
     if (A_out) {
       __syncwarp();
       for (int c = lane; c < r; c += 32) {
-        const double v = a[c];
-        A_out[row * r + c] = lam[c] > 0.0 ? v / lam[c] : v;
+        const FT v = a[c];
+        A_out[row * r + c] = lam[c] > FT(0) ? v / lam[c] : v;
       }
     }
   }
@@ -397,52 +401,135 @@ __global__ void __launch_bounds__(kRowThreads) k_lev_rows(const double* A, int64
 
 // A = M F with F the explicit inverse (kind 2) or pseudo-inverse (kind 1) of G:
 // one thread per output element.
-__global__ void __launch_bounds__(kRowThreads) k_solve_rows(const double* __restrict__ M,
+template <class FT>
+__global__ void __launch_bounds__(kRowThreads) k_solve_rows(const FT* __restrict__ M,
                                                             int64_t n, int r,
                                                             const SmallFactor* __restrict__ f,
-                                                            double* __restrict__ A) {
-  extern __shared__ double smem[];
-  double* F = smem;  // r * r
-  for (int i = threadIdx.x; i < r * r; i += blockDim.x) F[i] = f->F[i];
+                                                            FT* __restrict__ A) {
+  extern __shared__ __align__(16) unsigned char solve_smem[];
+  FT* F = reinterpret_cast<FT*>(solve_smem);  // r * r
+  for (int i = threadIdx.x; i < r * r; i += blockDim.x) F[i] = (FT)f->F[i];
   __syncthreads();
   const int64_t total = n * r;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t row = e / r;
     const int c = (int)(e - row * r);
-    const double* m = M + row * r;
-    double t = 0.0;
+    const FT* m = M + row * r;
+    FT t = FT(0);
     for (int u = 0; u < r; ++u) t = fma(m[u], F[u * r + c], t);
     A[e] = t;
   }
 }
 
-__global__ void k_scale_columns(double* A, int64_t n, int r, const double* __restrict__ lambda) {
+template <class FT>
+__global__ void k_scale_columns(FT* A, int64_t n, int r, const double* __restrict__ lambda) {
   const int64_t total = n * r;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double l = lambda[i % r];
-    if (l > 0.0) A[i] = A[i] / l;
+    if (l > 0.0) A[i] = (FT)((double)A[i] / l);
+  }
+}
+
+// Leverage for many rows: one thread per row, rows staged through shared memory
+// (coalesced), runtime loops over r (FP32 factors of large modes).
+template <class FT>
+__global__ void __launch_bounds__(kRowThreads) k_lev_rows_tpr(const FT* A, int64_t n, int r,
+                                                              const SmallFactor* __restrict__ f,
+                                                              double* __restrict__ lev,
+                                                              uint64_t* __restrict__ q,
+                                                              DistInfo* info, FT* A_out) {
+  extern __shared__ __align__(16) unsigned char tpr_smem[];
+  FT* F = reinterpret_cast<FT*>(tpr_smem);  // r * r
+  FT* sc = F + r * r;                       // r
+  FT* lam = sc + r;                         // r
+  FT* xs = lam + r;                         // kRowThreads * (r + 1)
+  __shared__ int perm[kMaxRank];
+  const int ld = r + 1;
+  for (int i = threadIdx.x; i < r * r; i += blockDim.x) F[i] = (FT)f->F[i];
+  for (int i = threadIdx.x; i < r; i += blockDim.x) {
+    sc[i] = (FT)f->scale[i];
+    lam[i] = (FT)f->lambda[i];
+    perm[i] = f->perm[i];
+  }
+  const int kind = f->kind;
+  const int k = kind == 0 ? f->rank : r;
+  uint64_t my_max = 0;
+  uint32_t my_nz = 0;
+  for (int64_t row0 = (int64_t)blockIdx.x * kRowThreads; row0 < n; row0 += (int64_t)gridDim.x * kRowThreads) {
+    const int rows = (int)(n - row0 < kRowThreads ? n - row0 : kRowThreads);
+    __syncthreads();
+    for (int i = threadIdx.x; i < rows * r; i += kRowThreads) {
+      const int rr = i / r, c = i - rr * r;
+      xs[rr * ld + c] = A[row0 * r + i] * sc[c];
+    }
+    __syncthreads();
+    if (threadIdx.x < rows) {
+      const FT* x = xs + threadIdx.x * ld;
+      FT l = FT(0);
+      for (int c = 0; c < k; ++c) {
+        FT t = FT(0);
+        if (kind == 0) {
+          for (int u = 0; u <= c; ++u) t = fma(F[c * r + u], x[perm[u]], t);
+          l = fma(t, t, l);
+        } else {
+          for (int u = 0; u < r; ++u) t = fma(F[c * r + u], x[u], t);
+          l = fma(x[c], t, l);
+        }
+      }
+      const int64_t row = row0 + threadIdx.x;
+      if (lev) lev[row] = (double)l;
+      if (q) {
+        double p = (double)l / (double)r;
+        p = p > 0.0 ? (p < 1.0 ? p : 1.0) : 0.0;
+        const uint64_t qi = __double2ull_rn(p * 4611686018427387904.0);  // 2^62
+        q[row] = qi;
+        my_max = qi > my_max ? qi : my_max;
+        my_nz += qi > 0;
+      }
+    }
+    if (A_out) {
+      for (int i = threadIdx.x; i < rows * r; i += kRowThreads) {
+        const int c = i % r;
+        const FT v = A[row0 * r + i];
+        A_out[row0 * r + i] = lam[c] > FT(0) ? v / lam[c] : v;
+      }
+    }
+  }
+  if (q && info) {
+    for (int o = 16; o > 0; o >>= 1) {
+      const uint64_t om = __shfl_xor_sync(0xffffffffu, my_max, o);
+      my_max = om > my_max ? om : my_max;
+      my_nz += __shfl_xor_sync(0xffffffffu, my_nz, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicMax((unsigned long long*)&info->maxq, (unsigned long long)my_max);
+      atomicAdd((unsigned long long*)&info->nnzq, (unsigned long long)my_nz);
+    }
   }
 }
 
 }  // namespace
 
-int gram_rows(const double* A, int64_t n, int r, double* G, cudaStream_t st) {
+template <class FT>
+int gram_rows(const FT* A, int64_t n, int r, double* G, cudaStream_t st) {
   if (r < 1 || r > kMaxRank) return CPA_ERR_ARG;
   if (n <= 0) return CPA_OK;
   const int np = r * (r + 1) / 2;
   const unsigned grid = grid_cap(ceil_div(n, kGramRows), 4);
-  const size_t smem = sizeof(double) * kGramRows * r;
+  const size_t smem = sizeof(FT) * kGramRows * r;
   if (np <= kGramThreads)
-    k_gram_rows<1><<<grid, kGramThreads, smem, st>>>(A, n, r, G);
+    k_gram_rows<FT, 1><<<grid, kGramThreads, smem, st>>>(A, n, r, G);
   else if (np <= 4 * kGramThreads)
-    k_gram_rows<4><<<grid, kGramThreads, smem, st>>>(A, n, r, G);
+    k_gram_rows<FT, 4><<<grid, kGramThreads, smem, st>>>(A, n, r, G);
   else
-    k_gram_rows<9><<<grid, kGramThreads, smem, st>>>(A, n, r, G);
+    k_gram_rows<FT, 9><<<grid, kGramThreads, smem, st>>>(A, n, r, G);
   CPA_LAUNCH_CHECK();
   return CPA_OK;
 }
+template int gram_rows<double>(const double*, int64_t, int, double*, cudaStream_t);
+template int gram_rows<float>(const float*, int64_t, int, double*, cudaStream_t);
 
 int factor_spd(const double* G, int r, int normalize, int pivot, double rel_tol, SmallFactor* out,
                int* warn, int warn_bit, cudaStream_t st) {
@@ -459,34 +546,57 @@ int factor_spd(const double* G, int r, int normalize, int pivot, double rel_tol,
   return CPA_OK;
 }
 
-int lev_rows(const double* A, int64_t n, int r, const SmallFactor* f, double* lev, uint64_t* q,
-             DistInfo* info, double* A_out, cudaStream_t st) {
+template <class FT>
+int lev_rows(const FT* A, int64_t n, int r, const SmallFactor* f, double* lev, uint64_t* q,
+             DistInfo* info, FT* A_out, cudaStream_t st) {
   if (r < 1 || r > kMaxRank) return CPA_ERR_ARG;
   if (n <= 0) return CPA_OK;
-  const size_t smem = sizeof(double) * ((size_t)r * r + 2 * r);
-  const unsigned grid = grid_cap(ceil_div(n, kRowThreads / 32), 16);
-  k_lev_rows<<<grid, kRowThreads, smem, st>>>(A, n, r, f, lev, q, info, A_out);
+  if (n >= kManyRows) {
+    const size_t smem = sizeof(FT) * ((size_t)r * r + 2 * r + (size_t)kRowThreads * (r + 1));
+    static bool attr = false;
+    if (!attr) {
+      CPA_CUDA_TRY(cudaFuncSetAttribute(k_lev_rows_tpr<FT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)(sizeof(FT) * (kMaxRank * kMaxRank + 2 * kMaxRank +
+                                                            kRowThreads * (kMaxRank + 1)))));
+      attr = true;
+    }
+    const unsigned grid = grid_cap(ceil_div(n, kRowThreads), 8);
+    k_lev_rows_tpr<FT><<<grid, kRowThreads, smem, st>>>(A, n, r, f, lev, q, info, A_out);
+  } else {
+    const size_t smem = sizeof(FT) * ((size_t)r * r + 2 * r);
+    const unsigned grid = grid_cap(ceil_div(n, kRowThreads / 32), 16);
+    k_lev_rows<FT><<<grid, kRowThreads, smem, st>>>(A, n, r, f, lev, q, info, A_out);
+  }
   CPA_LAUNCH_CHECK();
   return CPA_OK;
 }
+template int lev_rows<double>(const double*, int64_t, int, const SmallFactor*, double*, uint64_t*,
+                              DistInfo*, double*, cudaStream_t);
+template int lev_rows<float>(const float*, int64_t, int, const SmallFactor*, double*, uint64_t*,
+                             DistInfo*, float*, cudaStream_t);
 
-int solve_rows(const double* M, int64_t n, int r, const SmallFactor* f, double* A,
-               cudaStream_t st) {
+template <class FT>
+int solve_rows(const FT* M, int64_t n, int r, const SmallFactor* f, FT* A, cudaStream_t st) {
   if (r < 1 || r > kMaxRank) return CPA_ERR_ARG;
   if (n <= 0) return CPA_OK;
-  const size_t smem = sizeof(double) * (size_t)r * r;
+  const size_t smem = sizeof(FT) * (size_t)r * r;
   const unsigned grid = grid_cap(ceil_div(n * r, kRowThreads), 16);
-  k_solve_rows<<<grid, kRowThreads, smem, st>>>(M, n, r, f, A);
+  k_solve_rows<FT><<<grid, kRowThreads, smem, st>>>(M, n, r, f, A);
   CPA_LAUNCH_CHECK();
   return CPA_OK;
 }
+template int solve_rows<double>(const double*, int64_t, int, const SmallFactor*, double*, cudaStream_t);
+template int solve_rows<float>(const float*, int64_t, int, const SmallFactor*, float*, cudaStream_t);
 
-int scale_columns(double* A, int64_t n, int r, const double* lambda, cudaStream_t st) {
+template <class FT>
+int scale_columns(FT* A, int64_t n, int r, const double* lambda, cudaStream_t st) {
   if (n <= 0) return CPA_OK;
-  k_scale_columns<<<grid_cap(ceil_div(n * r, 256), 8), 256, 0, st>>>(A, n, r, lambda);
+  k_scale_columns<FT><<<grid_cap(ceil_div(n * r, 256), 8), 256, 0, st>>>(A, n, r, lambda);
   CPA_LAUNCH_CHECK();
   return CPA_OK;
 }
+template int scale_columns<double>(double*, int64_t, int, const double*, cudaStream_t);
+template int scale_columns<float>(float*, int64_t, int, const double*, cudaStream_t);
 
 int cdf_from_q(uint64_t* q, uint64_t* C, int64_t n, DistInfo* info, void* scan_scratch,
                cudaStream_t st) {

@@ -33,8 +33,10 @@ struct DistInfo {
   int64_t pad;
 };
 
-// G += A^T A for a row-major n x r FP64 matrix (G must be zeroed by the caller).
-int gram_rows(const double* A, int64_t n, int r, double* G, cudaStream_t st);
+// G += A^T A for a row-major n x r matrix of FT (float or double); partial sums
+// over 32-row tiles in FT, tiles added in FP64 (G zeroed by the caller).
+template <class FT>
+int gram_rows(const FT* A, int64_t n, int r, double* G, cudaStream_t st);
 
 // Factor G (see SmallFactor).  rel_tol: a Cholesky pivot must exceed rel_tol times
 // the largest diagonal entry.  pivot = 0: plain Cholesky; if a pivot fails, the
@@ -49,16 +51,18 @@ int factor_spd(const double* G, int r, int normalize, int pivot, double rel_tol,
 // (kind 1); q_i = round-half-even(2^62 lev_i / r) written to q (if non-null),
 // DistInfo maxq/nnzq accumulated (zeroed by the caller); rows divided by lambda
 // (columns with lambda = 0 untouched) and written to A_out if non-null (may be A).
-int lev_rows(const double* A, int64_t n, int r, const SmallFactor* f, double* lev,
-             uint64_t* q, DistInfo* info, double* A_out, cudaStream_t st);
+template <class FT>
+int lev_rows(const FT* A, int64_t n, int r, const SmallFactor* f, double* lev,
+             uint64_t* q, DistInfo* info, FT* A_out, cudaStream_t st);
 
 // A = M G^{-1} row by row with the factor of G (kind 0: two triangular solves;
 // kind 1: A = M F).
-int solve_rows(const double* M, int64_t n, int r, const SmallFactor* f, double* A,
-               cudaStream_t st);
+template <class FT>
+int solve_rows(const FT* M, int64_t n, int r, const SmallFactor* f, FT* A, cudaStream_t st);
 
 // A(:, c) /= lambda_c for lambda_c > 0.
-int scale_columns(double* A, int64_t n, int r, const double* lambda, cudaStream_t st);
+template <class FT>
+int scale_columns(FT* A, int64_t n, int r, const double* lambda, cudaStream_t st);
 
 // C = inclusive prefix sum of q (in place allowed); info->T = total.
 int cdf_from_q(uint64_t* q, uint64_t* C, int64_t n, DistInfo* info, void* scan_scratch,

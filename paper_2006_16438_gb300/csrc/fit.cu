@@ -13,41 +13,42 @@ namespace {
 
 constexpr int kThreads = 256;
 
-template <class VT, int CPL>
+template <class FT, class VT, int CPL>
 __global__ void __launch_bounds__(kThreads) k_fit_inner(FibreIndex<VT> X, KeyLayout L, FactorPtrs F,
                                                         int kf, const double* __restrict__ lambda,
                                                         int r, double* __restrict__ out) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
-  const double* Ak = F.A[kf];
+  const FT* Ak = static_cast<const FT*>(F.A[kf]);
   double part = 0.0;
   for (int64_t f = gw; f < X.nfib; f += nwarps) {
     const uint64_t key = X.keys[f];
-    double z[CPL], acc[CPL];
+    FT z[CPL], acc[CPL];
 #pragma unroll
     for (int q = 0; q < CPL; ++q) {
       const int c = lane + 32 * q;
-      double v = 0.0;
+      FT v = FT(0);
       if (c < r) {
-        v = lambda[c];
-        for (int t = 0; t < L.d; ++t) v *= F.A[L.mode[t]][(int64_t)L.get(key, t) * r + c];
+        v = (FT)lambda[c];
+        for (int t = 0; t < L.d; ++t)
+          v *= static_cast<const FT*>(F.A[L.mode[t]])[(int64_t)L.get(key, t) * r + c];
       }
       z[q] = v;
-      acc[q] = 0.0;
+      acc[q] = FT(0);
     }
     const uint64_t b = X.off[f], e = X.off[f + 1];
     for (uint64_t p0 = b; p0 < e; p0 += 32) {
       int32_t ik_l = 0;
-      double v_l = 0.0;
+      FT v_l = FT(0);
       if (p0 + lane < e) {
         ik_l = X.ik[p0 + lane];
-        v_l = (double)X.val[p0 + lane];
+        v_l = (FT)X.val[p0 + lane];
       }
       const int nb = (int)(e - p0 < 32 ? e - p0 : 32);
       for (int q2 = 0; q2 < nb; ++q2) {
         const int32_t ik = __shfl_sync(0xffffffffu, ik_l, q2);
-        const double v = __shfl_sync(0xffffffffu, v_l, q2);
+        const FT v = __shfl_sync(0xffffffffu, v_l, q2);
 #pragma unroll
         for (int q = 0; q < CPL; ++q) {
           const int c = lane + 32 * q;
@@ -56,7 +57,7 @@ __global__ void __launch_bounds__(kThreads) k_fit_inner(FibreIndex<VT> X, KeyLay
       }
     }
 #pragma unroll
-    for (int q = 0; q < CPL; ++q) part = fma(z[q], acc[q], part);
+    for (int q = 0; q < CPL; ++q) part += (double)(z[q] * acc[q]);
   }
   for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
   if (lane == 0 && part != 0.0) atomicAdd(out, part);
@@ -89,13 +90,15 @@ __global__ void k_fit_final(const double* __restrict__ grams, int D, const doubl
 
 size_t fit_buffers_bytes(int D, int r) { return sizeof(double) * ((size_t)D * r * r + 8) + 512; }
 
+template <class FT>
 int fit_enqueue(const cpa_index* X, const FactorPtrs& F, const double* lambda, int r, double* scratch,
                 double* fit_dev, cudaStream_t st) {
   const int D = X->order;
   double* grams = scratch;
   double* inner = scratch + (size_t)D * r * r;
   CPA_CUDA_TRY(cudaMemsetAsync(scratch, 0, sizeof(double) * ((size_t)D * r * r + 1), st));
-  for (int m = 0; m < D; ++m) CPA_TRY(gram_rows(F.A[m], X->dims[m], r, grams + (size_t)m * r * r, st));
+  for (int m = 0; m < D; ++m)
+    CPA_TRY(gram_rows<FT>(static_cast<const FT*>(F.A[m]), X->dims[m], r, grams + (size_t)m * r * r, st));
   int kf = 0;
   for (int m = 1; m < D; ++m)
     if (X->mode[m].nfib < X->mode[kf].nfib) kf = m;
@@ -104,16 +107,20 @@ int fit_enqueue(const cpa_index* X, const FactorPtrs& F, const double* lambda, i
   const unsigned grid = (unsigned)(want < sms * 8 ? (want > 0 ? want : 1) : sms * 8);
   if (X->val_dtype == CPA_F32) {
     const FibreIndex<float> fx = fibre_view<float>(X, kf);
-    if (r <= 32) k_fit_inner<float, 1><<<grid, kThreads, 0, st>>>(fx, X->mode[kf].L, F, kf, lambda, r, inner);
-    else k_fit_inner<float, 2><<<grid, kThreads, 0, st>>>(fx, X->mode[kf].L, F, kf, lambda, r, inner);
+    if (r <= 32) k_fit_inner<FT, float, 1><<<grid, kThreads, 0, st>>>(fx, X->mode[kf].L, F, kf, lambda, r, inner);
+    else k_fit_inner<FT, float, 2><<<grid, kThreads, 0, st>>>(fx, X->mode[kf].L, F, kf, lambda, r, inner);
   } else {
     const FibreIndex<double> fx = fibre_view<double>(X, kf);
-    if (r <= 32) k_fit_inner<double, 1><<<grid, kThreads, 0, st>>>(fx, X->mode[kf].L, F, kf, lambda, r, inner);
-    else k_fit_inner<double, 2><<<grid, kThreads, 0, st>>>(fx, X->mode[kf].L, F, kf, lambda, r, inner);
+    if (r <= 32) k_fit_inner<FT, double, 1><<<grid, kThreads, 0, st>>>(fx, X->mode[kf].L, F, kf, lambda, r, inner);
+    else k_fit_inner<FT, double, 2><<<grid, kThreads, 0, st>>>(fx, X->mode[kf].L, F, kf, lambda, r, inner);
   }
   k_fit_final<<<1, 256, 0, st>>>(grams, D, lambda, r, inner, X->norm_x2, fit_dev);
   CPA_LAUNCH_CHECK();
   return CPA_OK;
 }
+template int fit_enqueue<double>(const cpa_index*, const FactorPtrs&, const double*, int, double*, double*,
+                                 cudaStream_t);
+template int fit_enqueue<float>(const cpa_index*, const FactorPtrs&, const double*, int, double*, double*,
+                                cudaStream_t);
 
 }  // namespace cpa

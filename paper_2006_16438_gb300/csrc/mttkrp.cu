@@ -43,15 +43,16 @@ __global__ void k_probe(FibreIndex<VT> X, const uint64_t* __restrict__ idx, DevC
   }
 }
 
-template <int PMAX>
+template <class FT, int PMAX>
 __global__ void __launch_bounds__(kThreads) k_krp_gram(FactorPtrs F, KeyLayout L, int r,
                                                        const uint64_t* __restrict__ idx,
                                                        const double* __restrict__ wgt,
-                                                       DevCount sbar, double* __restrict__ Y,
+                                                       DevCount sbar, FT* __restrict__ Y,
                                                        double* __restrict__ G) {
-  extern __shared__ double tile[];  // kTileRows * r
+  extern __shared__ __align__(16) unsigned char krp_smem[];
+  FT* tile = reinterpret_cast<FT*>(krp_smem);  // kTileRows * r
   __shared__ uint32_t rows[kTileRows][kMaxOrder];
-  __shared__ double wsh[kTileRows];
+  __shared__ FT wsh[kTileRows];
   const int np = r * (r + 1) / 2;
   int pa[PMAX], pb[PMAX];
   double acc[PMAX];
@@ -68,15 +69,16 @@ __global__ void __launch_bounds__(kThreads) k_krp_gram(FactorPtrs F, KeyLayout L
     if (threadIdx.x < cnt) {
       const uint64_t key = idx[t0 + threadIdx.x];
       for (int t = 0; t < L.d; ++t) rows[threadIdx.x][t] = L.get(key, t);
-      wsh[threadIdx.x] = wgt[t0 + threadIdx.x];
+      wsh[threadIdx.x] = (FT)wgt[t0 + threadIdx.x];
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kTileRows * r; i += kThreads) {
       const int sl = i / r, c = i - sl * r;
-      double v = 0.0;
+      FT v = FT(0);
       if (sl < cnt) {
         v = wsh[sl];
-        for (int t = 0; t < L.d; ++t) v *= F.A[L.mode[t]][(int64_t)rows[sl][t] * r + c];
+        for (int t = 0; t < L.d; ++t)
+          v *= static_cast<const FT*>(F.A[L.mode[t]])[(int64_t)rows[sl][t] * r + c];
         Y[(t0 + sl) * r + c] = v;
       }
       tile[i] = v;
@@ -86,9 +88,9 @@ __global__ void __launch_bounds__(kThreads) k_krp_gram(FactorPtrs F, KeyLayout L
     for (int q = 0; q < PMAX; ++q) {
       const int p = threadIdx.x + q * kThreads;
       if (p < np) {
-        double s = 0.0;
+        FT s = FT(0);
         for (int i = 0; i < cnt; ++i) s = fma(tile[i * r + pa[q]], tile[i * r + pb[q]], s);
-        acc[q] += s;
+        acc[q] += (double)s;
       }
     }
   }
@@ -119,16 +121,17 @@ __device__ __forceinline__ int64_t sample_of(const uint64_t* __restrict__ pos, i
 // Lane-parallel gather: a warp takes 32 consecutive sampled nonzeros; each lane
 // resolves its own (sample, fibre offset, i_k, wgt_j * x) with independent loads, then
 // the warp walks the 32 nonzeros and lane c adds coef * y_j(c) into row i_k of M.
-template <class VT, int CPL, bool kShared>
-__global__ void __launch_bounds__(kThreads) k_mttkrp(FibreIndex<VT> X, const double* __restrict__ Y,
+template <class FT, class VT, int CPL, bool kShared>
+__global__ void __launch_bounds__(kThreads) k_mttkrp(FibreIndex<VT> X, const FT* __restrict__ Y,
                                                      const double* __restrict__ wgt,
                                                      const uint64_t* __restrict__ lo,
                                                      const uint64_t* __restrict__ pos, DevCount sbar,
                                                      const uint64_t* __restrict__ d_total, int r,
-                                                     int64_t nk, double* __restrict__ M) {
-  extern __shared__ double Ms[];
+                                                     int64_t nk, FT* __restrict__ M) {
+  extern __shared__ __align__(16) unsigned char mk_smem[];
+  FT* Ms = reinterpret_cast<FT*>(mk_smem);
   if (kShared) {
-    for (int64_t i = threadIdx.x; i < nk * r; i += kThreads) Ms[i] = 0.0;
+    for (int64_t i = threadIdx.x; i < nk * r; i += kThreads) Ms[i] = FT(0);
     __syncthreads();
   }
   const int64_t n = sbar.get();
@@ -140,23 +143,23 @@ __global__ void __launch_bounds__(kThreads) k_mttkrp(FibreIndex<VT> X, const dou
     const uint64_t e = base + lane;
     int64_t j = 0;
     int32_t ik = 0;
-    double coef = 0.0;
+    FT coef = FT(0);
     if (e < total) {
       j = sample_of(pos, n, e);
       const uint64_t off = lo[j] + (e - pos[j]);
       ik = X.ik[off];
-      coef = wgt[j] * (double)X.val[off];
+      coef = (FT)wgt[j] * (FT)X.val[off];
     }
     const int nb = total - base < 32 ? (int)(total - base) : 32;
     for (int q = 0; q < nb; ++q) {
       const int64_t jq = __shfl_sync(0xffffffffu, j, q);
       const int32_t iq = __shfl_sync(0xffffffffu, ik, q);
-      const double cq = __shfl_sync(0xffffffffu, coef, q);
+      const FT cq = __shfl_sync(0xffffffffu, coef, q);
 #pragma unroll
       for (int u = 0; u < CPL; ++u) {
         const int c = lane + 32 * u;
         if (c < r) {
-          const double v = cq * Y[jq * r + c];
+          const FT v = cq * Y[jq * r + c];
           if (kShared) atomicAdd(&Ms[(int64_t)iq * r + c], v);
           else atomicAdd(&M[(int64_t)iq * r + c], v);
         }
@@ -166,48 +169,49 @@ __global__ void __launch_bounds__(kThreads) k_mttkrp(FibreIndex<VT> X, const dou
   if (kShared) {
     __syncthreads();
     for (int64_t i = threadIdx.x; i < nk * r; i += kThreads)
-      if (Ms[i] != 0.0) atomicAdd(&M[i], Ms[i]);
+      if (Ms[i] != FT(0)) atomicAdd(&M[i], Ms[i]);
   }
 }
 
-template <class VT>
+template <class FT, class VT>
 int run(const cpa_index* X, int k, const FactorPtrs& F, int r, const uint64_t* idx, const double* wgt,
-        DevCount sbar, double* M, double* G, MttkrpBuffers& B, cudaStream_t st, cudaEvent_t mid) {
+        DevCount sbar, FT* M, double* G, MttkrpBuffers& B, cudaStream_t st, cudaEvent_t mid) {
   const auto& mode = X->mode[k];
   const FibreIndex<VT> fx = fibre_view<VT>(X, k);
   const int64_t s = sbar.max;
   const int sms = num_sms();
+  FT* Y = static_cast<FT*>(B.Y);
   int64_t pb = ceil_div(s, kThreads);
   k_probe<VT><<<(unsigned)(pb < sms * 16 ? pb : sms * 16), kThreads, 0, st>>>(fx, idx, sbar, B.lo,
                                                                              B.len);
   const int np = r * (r + 1) / 2;
   int64_t tb = ceil_div(s, kTileRows);
   const unsigned tgrid = (unsigned)(tb < sms * 2 ? tb : sms * 2);
-  const size_t tsm = sizeof(double) * kTileRows * r;
+  const size_t tsm = sizeof(FT) * kTileRows * r;
   if (np <= kThreads)
-    k_krp_gram<1><<<tgrid, kThreads, tsm, st>>>(F, mode.L, r, idx, wgt, sbar, B.Y, G);
+    k_krp_gram<FT, 1><<<tgrid, kThreads, tsm, st>>>(F, mode.L, r, idx, wgt, sbar, Y, G);
   else if (np <= 4 * kThreads)
-    k_krp_gram<4><<<tgrid, kThreads, tsm, st>>>(F, mode.L, r, idx, wgt, sbar, B.Y, G);
+    k_krp_gram<FT, 4><<<tgrid, kThreads, tsm, st>>>(F, mode.L, r, idx, wgt, sbar, Y, G);
   else
-    k_krp_gram<9><<<tgrid, kThreads, tsm, st>>>(F, mode.L, r, idx, wgt, sbar, B.Y, G);
+    k_krp_gram<FT, 9><<<tgrid, kThreads, tsm, st>>>(F, mode.L, r, idx, wgt, sbar, Y, G);
   CPA_LAUNCH_CHECK();
   CPA_TRY(scan_u64<uint32_t>(B.len, B.pos, sbar, false, B.total, B.scratch, st));
   k_pos_end<<<1, 1, 0, st>>>(sbar, B.total, B.pos);
   if (mid) CPA_CUDA_TRY(record_event(mid, st));
   const int64_t nk = X->dims[k];
-  const bool shared = nk * r * sizeof(double) <= 48 * 1024;
-  const size_t msm = shared ? sizeof(double) * nk * r : 0;
+  const bool shared = nk * r * sizeof(FT) <= 48 * 1024;
+  const size_t msm = shared ? sizeof(FT) * nk * r : 0;
   const unsigned mgrid = (unsigned)(shared ? sms : sms * 4);
   if (r <= 32) {
     if (shared)
-      k_mttkrp<VT, 1, true><<<mgrid, kThreads, msm, st>>>(fx, B.Y, wgt, B.lo, B.pos, sbar, B.total, r, nk, M);
+      k_mttkrp<FT, VT, 1, true><<<mgrid, kThreads, msm, st>>>(fx, Y, wgt, B.lo, B.pos, sbar, B.total, r, nk, M);
     else
-      k_mttkrp<VT, 1, false><<<mgrid, kThreads, 0, st>>>(fx, B.Y, wgt, B.lo, B.pos, sbar, B.total, r, nk, M);
+      k_mttkrp<FT, VT, 1, false><<<mgrid, kThreads, 0, st>>>(fx, Y, wgt, B.lo, B.pos, sbar, B.total, r, nk, M);
   } else {
     if (shared)
-      k_mttkrp<VT, 2, true><<<mgrid, kThreads, msm, st>>>(fx, B.Y, wgt, B.lo, B.pos, sbar, B.total, r, nk, M);
+      k_mttkrp<FT, VT, 2, true><<<mgrid, kThreads, msm, st>>>(fx, Y, wgt, B.lo, B.pos, sbar, B.total, r, nk, M);
     else
-      k_mttkrp<VT, 2, false><<<mgrid, kThreads, 0, st>>>(fx, B.Y, wgt, B.lo, B.pos, sbar, B.total, r, nk, M);
+      k_mttkrp<FT, VT, 2, false><<<mgrid, kThreads, 0, st>>>(fx, Y, wgt, B.lo, B.pos, sbar, B.total, r, nk, M);
   }
   CPA_LAUNCH_CHECK();
   return CPA_OK;
@@ -215,15 +219,15 @@ int run(const cpa_index* X, int k, const FactorPtrs& F, int r, const uint64_t* i
 
 }  // namespace
 
-size_t mttkrp_buffers_bytes(int64_t s, int r) {
+size_t mttkrp_buffers_bytes(int64_t s, int r, int ft_bytes) {
   Arena a;
   MttkrpBuffers B;
-  mttkrp_buffers_carve(a, s, r, &B);
+  mttkrp_buffers_carve(a, s, r, ft_bytes, &B);
   return a.used + 256;
 }
 
-void mttkrp_buffers_carve(Arena& a, int64_t s, int r, MttkrpBuffers* B) {
-  B->Y = a.take<double>((size_t)s * r);
+void mttkrp_buffers_carve(Arena& a, int64_t s, int r, int ft_bytes, MttkrpBuffers* B) {
+  B->Y = a.take<char>((size_t)s * r * ft_bytes);
   B->lo = a.take<uint64_t>(s);
   B->len = a.take<uint32_t>(s);
   B->pos = a.take<uint64_t>(s + 1);
@@ -231,14 +235,21 @@ void mttkrp_buffers_carve(Arena& a, int64_t s, int r, MttkrpBuffers* B) {
   B->scratch = a.take<char>(scan_workspace(s));
 }
 
+template <class FT>
 int sampled_mttkrp(const cpa_index* X, int k, const FactorPtrs& F, int r, const uint64_t* idx_packed,
-                   const double* wgt, DevCount sbar, double* M, double* G, MttkrpBuffers& B,
+                   const double* wgt, DevCount sbar, FT* M, double* G, MttkrpBuffers& B,
                    cudaStream_t st, cudaEvent_t mid) {
   if (r < 1 || r > kMaxRank) return CPA_ERR_ARG;
   if (sbar.max <= 0) return CPA_OK;
   if (X->val_dtype == CPA_F32)
-    return run<float>(X, k, F, r, idx_packed, wgt, sbar, M, G, B, st, mid);
-  return run<double>(X, k, F, r, idx_packed, wgt, sbar, M, G, B, st, mid);
+    return run<FT, float>(X, k, F, r, idx_packed, wgt, sbar, M, G, B, st, mid);
+  return run<FT, double>(X, k, F, r, idx_packed, wgt, sbar, M, G, B, st, mid);
 }
+template int sampled_mttkrp<double>(const cpa_index*, int, const FactorPtrs&, int, const uint64_t*,
+                                    const double*, DevCount, double*, double*, MttkrpBuffers&,
+                                    cudaStream_t, cudaEvent_t);
+template int sampled_mttkrp<float>(const cpa_index*, int, const FactorPtrs&, int, const uint64_t*,
+                                   const double*, DevCount, float*, double*, MttkrpBuffers&,
+                                   cudaStream_t, cudaEvent_t);
 
 }  // namespace cpa

@@ -5,13 +5,14 @@
 
 namespace cpa {
 
+// Factor matrices indexed by mode, of the element type of the run (float or double).
 struct FactorPtrs {
-  const double* A[kMaxOrder];  // indexed by mode
+  const void* A[kMaxOrder];
 };
 
 // Buffers of one sampled MTTKRP (device), sized for s samples.
 struct MttkrpBuffers {
-  double* Y;          // s x r: y_j = wgt_j * z_j
+  void* Y;            // s x r (factor type): y_j = wgt_j * z_j
   uint64_t* lo;       // s: first nonzero of the fibre of sample j in the mode-k stream
   uint32_t* len;      // s: fibre length
   uint64_t* pos;      // s + 1: exclusive prefix of len; pos[sbar] = nnz of the sample
@@ -19,16 +20,18 @@ struct MttkrpBuffers {
   char* scratch;      // scan workspace for s items
 };
 
-size_t mttkrp_buffers_bytes(int64_t s, int r);
-void mttkrp_buffers_carve(Arena& a, int64_t s, int r, MttkrpBuffers* B);
+size_t mttkrp_buffers_bytes(int64_t s, int r, int ft_bytes);
+void mttkrp_buffers_carve(Arena& a, int64_t s, int r, int ft_bytes, MttkrpBuffers* B);
 
 // G += sum_j y_j y_j^T and M += sum_j wgt_j x(:, key_j) y_j^T over the sbar samples
 // (packed keys), with y_j = wgt_j prod_t A_{m_t}(i_t, :).  G and M must be zeroed
 // by the caller.  sbar: device count (max s).
 // If mid_event is non-null it is recorded on `st` right before the
 // gather-scale-accumulate kernel (after probe, KRP/Gram and the scan).
+// FT: element type of the factors, Y and M (double: FP64 path; float: mixed).
+template <class FT>
 int sampled_mttkrp(const cpa_index* X, int k, const FactorPtrs& F, int r,
-                   const uint64_t* idx_packed, const double* wgt, DevCount sbar, double* M,
+                   const uint64_t* idx_packed, const double* wgt, DevCount sbar, FT* M,
                    double* G, MttkrpBuffers& B, cudaStream_t st, cudaEvent_t mid_event = nullptr);
 
 }  // namespace cpa

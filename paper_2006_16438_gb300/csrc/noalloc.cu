@@ -66,9 +66,9 @@ extern "C" int cpa_leverage_noalloc(const double* A, int64_t n, int32_t r, doubl
   // the array keeps the previous call's contents: clear what accumulates
   CPA_CUDA_TRY(cudaMemsetAsync(G, 0, sizeof(double) * r * r, st));
   CPA_CUDA_TRY(cudaMemsetAsync(warn, 0, sizeof(int), st));
-  CPA_TRY(cpa::gram_rows(A, n, r, G, st));
+  CPA_TRY(cpa::gram_rows<double>(A, n, r, G, st));
   CPA_TRY(cpa::factor_spd(G, r, 1, 1, 1e-12, f, warn, CPA_WARN_RANK_DEFICIENT_LEV, st));
-  CPA_TRY(cpa::lev_rows(A, n, r, f, lev, nullptr, nullptr, nullptr, st));
+  CPA_TRY(cpa::lev_rows<double>(A, n, r, f, lev, nullptr, nullptr, (double*)nullptr, st));
   int hwarn = 0;
   CPA_CUDA_TRY(cudaMemcpyAsync(&hwarn, warn, sizeof(int), cudaMemcpyDeviceToHost, st));
   CPA_CUDA_TRY(cudaStreamSynchronize(st));

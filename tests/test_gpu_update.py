@@ -1,0 +1,106 @@
+"""One mode update through cpa_mode_update, FP64 and mixed precision.
+
+FP64: the rows and counts equal the oracle's bit for bit; the weights agree to
+1e-13 relative (they are bit-exact only when both sides start from the same leverage
+vectors, which the stage tests check: here the GPU's Cholesky leverage and the
+oracle's QR leverage differ in the last bits); the new factor matches within 1e-10
+relative.  Mixed precision (FP32 products, FP64 factorisations):
+the leverage scores come from FP32 Grams, so the rows may differ from the FP64
+oracle's; the check feeds the GPU's own rows to the oracle's FP64 sampled MTTKRP and
+solve and requires the factor within 2e-4 relative, the tolerance stated for the
+mixed path.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2006_16438_gb300 as cpa  # noqa: E402
+from paper_2006_16438_gb300 import binding  # noqa: E402
+
+
+def relerr(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(b).max(), 1e-300))
+
+
+CASES = [
+    ((60, 50, 40), 4000, 4, 1024, 1.0 / 1024),
+    ((37, 29, 41, 13), 20000, 6, 3000, 1.0),
+    ((183, 24, 1140, 1717), 200000, 25, 2 ** 14, 2.0 ** -14),
+]
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_mode_update_fp64_matches_oracle(case):
+    dims, nnz, r, s, tau = CASES[case]
+    coo = synth.random_sparse_tensor(dims, nnz, seed=case + 1)
+    facs = synth.gaussian_factors(dims, r, seed=case + 2)
+    gi = cpa.cpa_index_build(coo)
+    oi = oracle.Index(coo)
+    for k in range(len(dims)):
+        fs = [torch.from_numpy(a).cuda() for a in facs]
+        got = cpa.cpa_mode_update(gi, fs, k, rank=r, samples=s, tau=tau, seed=7, it=3)
+        ref = oracle.mode_update(oi, facs, k, rank=r, samples=s, tau=tau, seed=7, it=3)
+        assert got["sbar"] == ref["sbar"] and got["sdet"] == ref["sdet"]
+        assert abs(got["pdet"] - ref["pdet"]) <= 1e-13 * max(ref["pdet"], 1e-300)
+        np.testing.assert_array_equal(got["idx"].cpu().numpy().astype(np.uint64), ref["idx"])
+        np.testing.assert_array_equal(got["cnt"].cpu().numpy().astype(np.uint32), ref["cnt"])
+        assert relerr(got["wgt"].cpu().numpy(), ref["wgt"]) < 1e-13
+        assert relerr(fs[k].cpu().numpy(), ref["A"]) < 1e-10
+        assert relerr(got["lam"].cpu().numpy(), ref["lam"]) < 1e-10
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_mode_update_mixed_within_2e4(case):
+    dims, nnz, r, s, tau = CASES[case]
+    coo = synth.random_sparse_tensor(dims, nnz, seed=case + 1)
+    facs = synth.gaussian_factors(dims, r, seed=case + 2)
+    gi = cpa.cpa_index_build(coo)
+    oi = oracle.Index(coo)
+    for k in range(len(dims)):
+        fs = [torch.from_numpy(a).cuda() for a in facs]
+        got = cpa.cpa_mode_update(gi, fs, k, rank=r, samples=s, tau=tau, seed=7, it=3,
+                                  precision=binding.MIXED)
+        idx = got["idx"].cpu().numpy().astype(np.uint64)
+        wgt = got["wgt"].cpu().numpy()
+        M, G, _ = oracle.sampled_mttkrp(oi, k, facs, idx, wgt)
+        A, _ = oracle.solve(G, M)
+        An, lam = oracle.normalize(A)
+        assert relerr(fs[k].cpu().numpy(), An) < 2e-4
+        assert relerr(got["lam"].cpu().numpy(), lam) < 2e-4
+        # the sampled rows are valid: same count of rows as weights, positive weights
+        assert got["sbar"] == idx.size and np.all(wgt > 0)
+
+
+def test_mixed_run_reaches_planted_fit():
+    """Exact low-rank tensor: the mixed path converges like the FP64 path.  Its fit is
+    evaluated as ||X||^2 - 2<X,M> + ||M||^2 with FP32 products, so near fit = 1 it
+    resolves only about sqrt(2^-24) ~ 3e-4 (the FP64 floor is 1.5e-8)."""
+    coo, lam0, f0 = synth.exact_lowrank_tensor((30, 25, 20), 3, seed=4, density=0.6)
+    init = synth.gaussian_factors(coo.dims, 3, seed=1)
+    gi = cpa.cpa_index_build(coo)
+    f64 = cpa.cp_arls_lev(gi, [torch.from_numpy(a).cuda() for a in init], rank=3, samples=500, tau=1.0,
+                          iters=150, seed=2)
+    mix = cpa.cp_arls_lev(gi, [torch.from_numpy(a).cuda() for a in init], rank=3, samples=500, tau=1.0,
+                          iters=150, seed=2, precision=binding.MIXED)
+    assert f64.fit > 1 - 1e-6
+    assert mix.fit > 1 - 1e-3
+    assert abs(mix.fit - f64.fit) < 1e-3
+
+
+def test_mixed_small_planted_fit_close_to_fp64():
+    coo = synth.small_planted_tensor(0)
+    init = synth.gaussian_factors(coo.dims, 4, seed=0)
+    gi = cpa.cpa_index_build(coo)
+    f64 = cpa.cp_arls_lev(gi, [torch.from_numpy(a).cuda() for a in init], rank=4, samples=1024, tau=1.0,
+                          iters=10, seed=0)
+    mix = cpa.cp_arls_lev(gi, [torch.from_numpy(a).cuda() for a in init], rank=4, samples=1024, tau=1.0,
+                          iters=10, seed=0, precision=binding.MIXED)
+    assert abs(mix.fit - f64.fit) < 1e-2
