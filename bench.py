@@ -47,8 +47,6 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision series")
-    p.add_argument("--no-launch-count", action="store_true",
-                   help="skip counting kernels with the torch profiler (use under ncu)")
     p.add_argument("--cpu-sample-updates", type=int, default=4,
                    help="mode updates the CPU baseline times (bounded sample)")
     return p.parse_args()
@@ -130,12 +128,30 @@ def make_workload():
     return coo, init
 
 
-def mttkrp_bytes(stats, d, b_val=8):
+def mttkrp_bytes(stats, d, b_val=8, b_f=8):
     """Algorithmic bytes of the gather-scale-accumulate kernel summed over updates:
     per sample its fibre position, start and weight (24 B) and its KRP row y_j
-    (8r B); per sampled nonzero its mode index and value (4 + b_val B); M is counted
-    once per update as written (n_k r 8 B, added by the caller)."""
-    return stats["sbar_total"] * (24 + 8 * RANK) + stats["nnz_sampled_total"] * (4 + b_val)
+    (b_f r B); per sampled nonzero its mode index and value (4 + b_val B); M is
+    counted once per update as written (n_k r b_f B, added by the caller)."""
+    return stats["sbar_total"] * (24 + b_f * RANK) + stats["nnz_sampled_total"] * (4 + b_val)
+
+
+def krp_gram_flops(stats, d):
+    """Algorithmic floating-point operations of the sampled-KRP + sampled-Gram kernel
+    summed over updates: per kept sample, the D-1 multiplications of each of the r
+    entries of y_j = w_j * prod of D-1 factor rows, and the upper triangle of
+    y_j y_j^T accumulated into G (r(r+1)/2 fused multiply-adds = r(r+1) flops)."""
+    return stats["sbar_total"] * (RANK * (RANK + 1) + RANK * (d - 1))
+
+
+# FP64 and FP32 peaks of one GB300 from unit counts and the maximum SM clock:
+# 152 SMs x 2 FP64 FMA/clk (resp. 128 FP32 FMA/clk) x 2 flops x 2.07 GHz.
+SMS, SM_MAX_GHZ = 152, 2.07
+FP64_PEAK_TFLOPS = SMS * 2 * 2 * SM_MAX_GHZ / 1000.0
+FP32_PEAK_TFLOPS = SMS * 128 * 2 * SM_MAX_GHZ / 1000.0
+
+STAGES = ["sample", "probe", "krp_gram", "scan", "mttkrp", "solve", "leverage", "fit"]
+WHOLE = 8
 
 
 def run_reference(args, rank):
@@ -192,23 +208,6 @@ def cpu_baseline(coo, init, n_updates):
             "sample": f"{n_updates} mode updates of the same workload (index built untimed)"}
 
 
-def count_launches(run_once):
-    """Kernels of libcpa launched by one step, counted with the torch profiler."""
-    try:
-        import torch
-        from torch.profiler import ProfilerActivity, profile
-        with profile(activities=[ProfilerActivity.CUDA]) as prof:
-            run_once()
-            torch.cuda.synchronize()
-        n = 0
-        for e in prof.events():
-            if e.device_type.name == "CUDA" and ("cpa::" in e.name or e.name.startswith("_ZN3cpa")):
-                n += 1
-        return n
-    except Exception:
-        return None
-
-
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -227,7 +226,7 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def series(precision, count_launch=False):
+    def series(precision):
         """W untimed + K timed epochs from the same initial factors."""
         fs = [torch.from_numpy(a).cuda() for a in init]
         lam = torch.empty(RANK, dtype=torch.float64, device="cuda")
@@ -244,9 +243,8 @@ def main():
         for _ in range(args.warmup):
             step()
         torch.cuda.synchronize()
-        launches = count_launches(lambda: step()) if count_launch else None
-        times, stages, fits, last = [], np.zeros(8), [], {}
-        acc = {"sbar_total": 0, "nnz_sampled_total": 0}
+        times, stages, fits, last = [], np.zeros(12), [], {}
+        acc = {"sbar_total": 0, "nnz_sampled_total": 0, "kernel_launches": 0}
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
@@ -263,6 +261,10 @@ def main():
             stages += np.array(st["stage_ms"])
             acc["sbar_total"] += st["sbar_total"]
             acc["nnz_sampled_total"] += st["nnz_sampled_total"]
+            if acc["kernel_launches"] is not None and st["kernel_launches"] >= 0:
+                acc["kernel_launches"] += st["kernel_launches"]
+            else:
+                acc["kernel_launches"] = None
             fits.append(res.fit)
             last = st
         total_ms = sum(times)
@@ -270,11 +272,11 @@ def main():
             t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             total_ms = float(t.item())
-        return dict(total_ms=total_ms, stages=stages, acc=acc, fit=fits[-1], last=last, launches=launches)
+        return dict(total_ms=total_ms, stages=stages, acc=acc, fit=fits[-1], last=last)
 
     clocks = ClockSampler(local)
     clocks.start()
-    f64 = series(cpa.binding.FP64, count_launch=not args.no_launch_count)
+    f64 = series(cpa.binding.FP64)
     clk = clocks.stop()
     mixed = None if args.no_mixed else series(cpa.binding.MIXED)
     updates = args.steps * ETA * len(coo.dims)
@@ -282,14 +284,17 @@ def main():
     peaks, peak_src = load_peaks()
     n_updates = updates
     stages, stat_acc, last_stats = f64["stages"], f64["acc"], f64["last"]
-    launches_per_step = f64["launches"]
-    # roofline of the gather-scale-accumulate MTTKRP kernel (stage 2)
-    mk_ms = stages[2]
-    mk_bytes = mttkrp_bytes(stat_acc, len(coo.dims) - 1) + sum(
-        n * RANK * 8 for n in coo.dims) * (n_updates // len(coo.dims))
+    d = len(coo.dims)
+    nk_bytes = sum(n * RANK * 8 for n in coo.dims) * (n_updates // d)
+    # the sampled MTTKRP's HBM figure (the gather-scale-accumulate kernel, stage 4)
+    mk_ms = stages[4]
+    mk_bytes = mttkrp_bytes(stat_acc, d - 1) + nk_bytes
     mk_gbs = mk_bytes / (mk_ms / 1000.0) / 1e9 if mk_ms > 0 else None
-    stage_names = ["sample", "probe_krp_gram", "mttkrp", "solve", "leverage", "fit"]
-    stage_share = {nm: round(float(stages[i] / max(stages[6], 1e-9)), 4) for i, nm in enumerate(stage_names)}
+    # the dominant kernel: sampled KRP rows + sampled Gram (stage 2), FP64-ALU bound
+    kg_ms = stages[2]
+    kg_flops = krp_gram_flops(stat_acc, d)
+    kg_tflops = kg_flops / (kg_ms / 1000.0) / 1e12 if kg_ms > 0 else None
+    stage_share = {nm: round(float(stages[i] / max(stages[WHOLE], 1e-9)), 4) for i, nm in enumerate(STAGES)}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": f64["total_ms"] / args.steps, "higher_is_better": True,
@@ -297,12 +302,17 @@ def main():
         "config": {"workload": WORKLOAD, "step": "1 epoch = 5 outer iterations x 4 mode updates + exact fit",
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": f"{world} independent replicas" if world > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "kernel": "k_mttkrp (gather-scale-accumulate)",
-                     "achieved": mk_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": (mk_gbs / peaks["hbm_gbs"]) if mk_gbs else None, "traffic": None,
-                     "peak_source": peak_src,
-                     "bytes_per_update": mk_bytes / n_updates, "ms_per_update": mk_ms / n_updates},
-        "stages_ms_per_update": {nm: float(stages[i] / n_updates) for i, nm in enumerate(stage_names)},
+        "roofline": {"bound": "alu", "kernel": "k_krp_gram (sampled KRP rows + sampled Gram, FP64)",
+                     "achieved": kg_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": (kg_tflops / FP64_PEAK_TFLOPS) if kg_tflops else None, "traffic": None,
+                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz",
+                     "flops_per_update": kg_flops / n_updates, "ms_per_update": kg_ms / n_updates},
+        "mttkrp_hbm": {"bound": "hbm", "kernel": "k_mttkrp (gather-scale-accumulate)",
+                       "achieved": mk_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                       "frac": (mk_gbs / peaks["hbm_gbs"]) if mk_gbs else None,
+                       "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+                       "bytes_per_update": mk_bytes / n_updates, "ms_per_update": mk_ms / n_updates},
+        "stages_ms_per_update": {nm: float(stages[i] / n_updates) for i, nm in enumerate(STAGES)},
         "stage_share": stage_share,
         "nnz_sampled_per_update": stat_acc["nnz_sampled_total"] / n_updates,
         "last_update": {k: last_stats.get(k) for k in ("sdet_last", "pdet_last", "attempts_last", "sbar_last",
@@ -310,14 +320,14 @@ def main():
         "sbar_per_update": stat_acc["sbar_total"] / n_updates,
         "fit": f64["fit"],
         "clocks": clk,
-        "gpu_launches": (launches_per_step * args.steps) if launches_per_step else None,
+        "gpu_launches": stat_acc["kernel_launches"],
     }
     if mixed is not None:
         mv = updates * world / (mixed["total_ms"] / 1000.0)
         line["mixed_precision"] = {
             "value": mv, "unit": UNIT, "speedup_vs_fp64": mv / value, "fit": mixed["fit"],
             "fit_fp64": f64["fit"], "fit_diff": mixed["fit"] - f64["fit"],
-            "stages_ms_per_update": {nm: float(mixed["stages"][i] / n_updates) for i, nm in enumerate(stage_names)},
+            "stages_ms_per_update": {nm: float(mixed["stages"][i] / n_updates) for i, nm in enumerate(STAGES)},
             "note": "same init and epochs; FP32 factors/Grams/products, FP64 factorisations"}
     if rank == 0 and not args.no_e2e:
         line["e2e"] = e2e(cpa, coo, init, args)

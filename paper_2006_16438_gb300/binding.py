@@ -69,8 +69,8 @@ class Stats(C.Structure):
                 ("epochs", C.c_int32), ("sdet_last", C.c_int64), ("sbar_last", C.c_int64),
                 ("nnz_sampled_last", C.c_int64), ("attempts_last", C.c_int64),
                 ("pdet_last", C.c_double), ("nnz_sampled_total", C.c_int64),
-                ("sbar_total", C.c_int64), ("stage_ms", C.c_double * 8),
-                ("stage_launches", C.c_int64 * 8)]
+                ("sbar_total", C.c_int64), ("stage_ms", C.c_double * 12),
+                ("stage_launches", C.c_int64 * 12), ("kernel_launches", C.c_int64)]
 
     def as_dict(self):
         out = {}

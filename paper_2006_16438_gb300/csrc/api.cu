@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "fit.cuh"
 #include "sample.cuh"
@@ -25,19 +26,24 @@ struct DevStats {
   int pad;
 };
 
-__global__ void k_stats(DevStats* ds, const SampleState* S, const uint64_t* nnz, const int* warn) {
-  ds->sdet_last = S->sdet;
-  ds->sbar_last = S->sbar;
-  ds->nnz_last = (int64_t)*nnz;
-  ds->attempts_last = (int64_t)S->attempts;
-  ds->pdet_last = S->pdet;
-  ds->nnz_total += (int64_t)*nnz;
-  ds->sbar_total += S->sbar;
-  ds->warnings = *warn;
-}
-
 __global__ void k_copy_lambda(const SmallFactor* f, int r, double* lambda) {
   if (threadIdx.x < r) lambda[threadIdx.x] = f->lambda[threadIdx.x];
+}
+
+// end of one mode update: lambda of the solved mode and the statistics
+__global__ void k_finish_update(const SmallFactor* f, int r, double* lambda, DevStats* ds,
+                                const SampleState* S, const uint64_t* nnz, const int* warn) {
+  if (threadIdx.x < r) lambda[threadIdx.x] = f->lambda[threadIdx.x];
+  if (threadIdx.x == 0) {
+    ds->sdet_last = S->sdet;
+    ds->sbar_last = S->sbar;
+    ds->nnz_last = (int64_t)*nnz;
+    ds->attempts_last = (int64_t)S->attempts;
+    ds->pdet_last = S->pdet;
+    ds->nnz_total += (int64_t)*nnz;
+    ds->sbar_total += S->sbar;
+    ds->warnings = *warn;
+  }
 }
 
 __global__ void k_q_from_lev(const double* __restrict__ lev, int64_t n, int r, uint64_t* __restrict__ q,
@@ -127,17 +133,16 @@ struct DevBuf {
 
 // Leverage distribution of one factor: lev (optional), CDF C, info; A normalised in
 // place when `normalize_out` (the update path), untouched otherwise.
+// gram_zeroed: GA was already cleared by the previous kernel (the solve).
 template <class FT>
 int refresh_distribution(FT* A, int64_t n, int r, uint64_t* C, DistInfo* info, double* Pm,
                          double* GA, SmallFactor* fac, int* warn, void* scan_scratch, bool normalize_out,
-                         double* lev_out, cudaStream_t st) {
-  CPA_CUDA_TRY(cudaMemsetAsync(GA, 0, sizeof(double) * r * r, st));
+                         double* lev_out, cudaStream_t st, bool gram_zeroed = false) {
+  if (!gram_zeroed) CPA_CUDA_TRY(cudaMemsetAsync(GA, 0, sizeof(double) * r * r, st));
   CPA_TRY(gram_rows<FT>(A, n, r, GA, st));
-  CPA_TRY(factor_spd(GA, r, 1, 1, 1e-12, fac, warn, CPA_WARN_RANK_DEFICIENT_LEV, st));
-  CPA_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(DistInfo), st));
+  CPA_TRY(factor_spd(GA, r, 1, 1, 1e-12, fac, warn, CPA_WARN_RANK_DEFICIENT_LEV, st, info));
   CPA_TRY(lev_rows<FT>(A, n, r, fac, lev_out, C, info, normalize_out ? A : nullptr, st));
-  CPA_TRY(cdf_from_q(C, C, n, info, scan_scratch, st));
-  CPA_TRY(phat_from_cdf(C, n, info, Pm, st));
+  CPA_TRY(cdf_from_q(C, C, n, info, Pm, scan_scratch, st));
   return CPA_OK;
 }
 
@@ -223,6 +228,13 @@ namespace cpa {
 
 __global__ void k_advance_iter(uint64_t* it) { *it += 1; }
 
+// Per-call state: lambda = 1, fit = NaN, iteration counter = the caller's offset.
+__global__ void k_run_init(double* lam, double* fitd, uint64_t* it, uint64_t it0) {
+  for (int i = threadIdx.x; i < kMaxRank; i += blockDim.x) lam[i] = 1.0;
+  if (threadIdx.x < 4) fitd[threadIdx.x] = NAN;
+  if (threadIdx.x == 0) *it = it0;
+}
+
 struct Plan {
   // key
   int r = 0, D = 0, reject_cap = 0, profile = 0, prec = CPA_FP64, ftb = 8;
@@ -247,7 +259,10 @@ struct Plan {
   MttkrpBuffers MB;
   // graph of one outer iteration
   bool use_graph = false;
-  cudaGraphExec_t exec = nullptr;
+  cudaGraphExec_t exec = nullptr;       // one outer iteration
+  cudaGraphExec_t init_exec = nullptr;  // initial leverage distributions
+  cudaGraphExec_t fit_exec = nullptr;   // exact fit
+  int64_t k_iter = 0, k_init = 0, k_fit = 0;  // kernel nodes of each graph
   cudaStream_t cap_stream = nullptr;
   Profiler gprof;  // event nodes captured into the graph (profile = 1)
 
@@ -320,6 +335,9 @@ struct Plan {
       for (int t = L.d; t < kMaxOrder; ++t) SB[k].cand_off[t] = off;
     }
     CPA_CUDA_TRY(cudaMemsetAsync(SB[0].state, 0, sizeof(SampleState), st));
+    // the combine table starts empty; each pass's compaction empties it again
+    CPA_CUDA_TRY(cudaMemsetAsync(SB[0].hkeys, 0xff, sizeof(uint64_t) << SB[0].hbits, st));
+    CPA_CUDA_TRY(cudaMemsetAsync(SB[0].hcnt, 0, sizeof(uint32_t) << SB[0].hbits, st));
     return CPA_OK;
   }
 
@@ -357,49 +375,89 @@ struct Plan {
       const int64_t nk = X->dims[k];
       FT* Mt = static_cast<FT*>(M);
       FT* Fk = static_cast<FT*>(Fm[k]);
-      CPA_CUDA_TRY(cudaMemsetAsync(Mt, 0, sizeof(FT) * nk * r, st));
-      CPA_CUDA_TRY(cudaMemsetAsync(Gs, 0, sizeof(double) * r * r, st));
-      cudaEvent_t mid = prof.pending(1);
+      cudaEvent_t evs[3] = {prof.pending(1), prof.pending(2), prof.pending(3)};
       CPA_TRY(sampled_mttkrp<FT>(X, k, F, r, SB[k].idx_packed, SB[k].wgt, DevCount{&SB[k].state->sbar, s},
-                                 Mt, Gs, MB, st, mid));
-      CPA_TRY(prof.mark(2));
-      CPA_TRY(factor_spd(Gs, r, 0, 0, 1e-13, fsolve, warn, CPA_WARN_SINGULAR_GRAM, st));
-      CPA_TRY(solve_rows<FT>(Mt, nk, r, fsolve, Fk, st));
-      CPA_TRY(prof.mark(3));
-      CPA_TRY(refresh_distribution<FT>(Fk, nk, r, Cm[k], info + k, Pm[k], GA, flev, warn, scan_ws, true,
-                                       nullptr, st));
-      k_copy_lambda<<<1, 64, 0, st>>>(flev, r, lam);
-      k_stats<<<1, 1, 0, st>>>(dstats, SB[k].state, MB.total, warn);
-      CPA_LAUNCH_CHECK();
+                                 Mt, Gs, MB, st, prof.on ? evs : nullptr));
       CPA_TRY(prof.mark(4));
+      CPA_TRY(factor_spd(Gs, r, 0, 0, 1e-13, fsolve, warn, CPA_WARN_SINGULAR_GRAM, st));
+      CPA_TRY(solve_rows<FT>(Mt, nk, r, fsolve, Fk, st, GA));
+      CPA_TRY(prof.mark(5));
+      CPA_TRY(refresh_distribution<FT>(Fk, nk, r, Cm[k], info + k, Pm[k], GA, flev, warn, scan_ws, true,
+                                       nullptr, st, true));
+      k_finish_update<<<1, 64, 0, st>>>(flev, r, lam, dstats, SB[k].state, MB.total, warn);
+      CPA_LAUNCH_CHECK();
+      CPA_TRY(prof.mark(6));
     }
     k_advance_iter<<<1, 1, 0, st>>>(iter_dev);
     CPA_LAUNCH_CHECK();
     return CPA_OK;
   }
 
-  // Captured on a private stream (the legacy default stream cannot be captured);
-  // the graph is then launched on the caller's stream.
-  int capture(const cpa_index* X) {
+  // Graphs are captured on a private stream (the legacy default stream cannot be
+  // captured) and launched on the caller's stream.  *nk receives the number of
+  // kernel nodes of the graph.
+  template <class Fn>
+  int capture_graph(Fn&& fn, cudaGraphExec_t* out, int64_t* nk) {
     cudaGraph_t g = nullptr;
     if (!cap_stream) CPA_CUDA_TRY(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
-    gprof.on = profile != 0;
-    gprof.st = cap_stream;
-    if (gprof.on) gprof.reserve(6 * D);
     CPA_CUDA_TRY(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
-    const int rc = enqueue_iteration(X, gprof, cap_stream);
+    const int rc = fn(cap_stream);
     const cudaError_t ec = cudaStreamEndCapture(cap_stream, &g);
     if (rc < 0 || ec != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
       return rc < 0 ? rc : CPA_ERR_CUDA;
     }
-    const cudaError_t ei = cudaGraphInstantiate(&exec, g, 0);
+    size_t n = 0;
+    int64_t kernels = 0;
+    if (cudaGraphGetNodes(g, nullptr, &n) == cudaSuccess && n > 0) {
+      std::vector<cudaGraphNode_t> nodes(n);
+      if (cudaGraphGetNodes(g, nodes.data(), &n) == cudaSuccess)
+        for (size_t i = 0; i < n; ++i) {
+          cudaGraphNodeType t;
+          if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+        }
+    }
+    *nk = kernels;
+    const cudaError_t ei = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
     if (ei != cudaSuccess) {
-      exec = nullptr;
+      *out = nullptr;
       return CPA_ERR_CUDA;
     }
     return CPA_OK;
+  }
+
+  // One outer iteration (all D updates), replayed per iteration.
+  int capture(const cpa_index* X) {
+    gprof.on = profile != 0;
+    gprof.st = nullptr;
+    if (gprof.on) gprof.reserve(8 * D);
+    return capture_graph(
+        [&](cudaStream_t cs) {
+          gprof.st = cs;
+          return enqueue_iteration(X, gprof, cs);
+        },
+        &exec, &k_iter);
+  }
+
+  // Leverage distributions of the initial factors (Alg. 3 starts from l(A_k)/r).
+  int enqueue_init(const cpa_index* X, cudaStream_t st) {
+    for (int m = 0; m < D; ++m) {
+      if (prec == CPA_MIXED)
+        CPA_TRY(refresh_distribution<float>(static_cast<float*>(Fm[m]), X->dims[m], r, Cm[m], info + m,
+                                            Pm[m], GA, flev, warn, scan_ws, false, nullptr, st));
+      else
+        CPA_TRY(refresh_distribution<double>(static_cast<double*>(Fm[m]), X->dims[m], r, Cm[m], info + m,
+                                             Pm[m], GA, flev, warn, scan_ws, false, nullptr, st));
+    }
+    return CPA_OK;
+  }
+
+  int enqueue_fit(const cpa_index* X, cudaStream_t st) {
+    FactorPtrs F;
+    for (int m = 0; m < D; ++m) F.A[m] = Fm[m];
+    return prec == CPA_MIXED ? fit_enqueue<float>(X, F, lam, r, fit_ws, fitd, st)
+                             : fit_enqueue<double>(X, F, lam, r, fit_ws, fitd, st);
   }
 
   int run(const cpa_index* X, const cpa_options* opt, double* lambda, double* const* factors,
@@ -433,8 +491,6 @@ struct Plan {
     const int64_t nk = X->dims[k];
     FT* Mt = static_cast<FT*>(M);
     FT* Fk = static_cast<FT*>(Fm[k]);
-    CPA_CUDA_TRY(cudaMemsetAsync(Mt, 0, sizeof(FT) * nk * r, st));
-    CPA_CUDA_TRY(cudaMemsetAsync(Gs, 0, sizeof(double) * r * r, st));
     CPA_TRY(sampled_mttkrp<FT>(X, k, F, r, B.idx_packed, B.wgt, DevCount{&B.state->sbar, s}, Mt, Gs, MB,
                                st));
     CPA_TRY(factor_spd(Gs, r, 0, 0, 1e-13, fsolve, warn, CPA_WARN_SINGULAR_GRAM, st));
@@ -448,6 +504,8 @@ struct Plan {
 
   ~Plan() {
     if (exec) cudaGraphExecDestroy(exec);
+    if (init_exec) cudaGraphExecDestroy(init_exec);
+    if (fit_exec) cudaGraphExecDestroy(fit_exec);
     if (cap_stream) cudaStreamDestroy(cap_stream);
     if (base) {
       cudaDeviceSynchronize();
@@ -460,6 +518,7 @@ void plan_free(Plan* p) { delete p; }
 
 int Plan::run(const cpa_index* X, const cpa_options* opt, double* lambda, double* const* factors,
               int32_t io_on_device, double* fit, cpa_stats* stats, cudaStream_t st) {
+  int64_t kernels = 0;  // launched by this call
   CPA_CUDA_TRY(cudaMemsetAsync(warn, 0, sizeof(int) * 4, st));
   CPA_CUDA_TRY(cudaMemsetAsync(dstats, 0, sizeof(DevStats), st));
   CPA_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(DistInfo) * kMaxOrder, st));
@@ -471,37 +530,41 @@ int Plan::run(const cpa_index* X, const cpa_options* opt, double* lambda, double
       CPA_CUDA_TRY(cudaMemcpyAsync(stage64, factors[m], sizeof(double) * cnt, kin, st));
       k_convert<float, double><<<blocks(cnt), 256, 0, st>>>(stage64, cnt, static_cast<float*>(Fm[m]));
       CPA_LAUNCH_CHECK();
+      ++kernels;
     } else {
       CPA_CUDA_TRY(cudaMemcpyAsync(Fm[m], factors[m], sizeof(double) * cnt, kin, st));
     }
   }
-  {
-    std::vector<double> ones(kMaxRank, 1.0);
-    const double nan4[4] = {NAN, NAN, NAN, NAN};
-    const uint64_t it0 = opt->iter_offset;
-    CPA_CUDA_TRY(cudaMemcpyAsync(lam, ones.data(), sizeof(double) * kMaxRank, cudaMemcpyHostToDevice, st));
-    CPA_CUDA_TRY(cudaMemcpyAsync(fitd, nan4, sizeof(nan4), cudaMemcpyHostToDevice, st));
-    CPA_CUDA_TRY(cudaMemcpyAsync(iter_dev, &it0, sizeof(it0), cudaMemcpyHostToDevice, st));
-    CPA_CUDA_TRY(cudaStreamSynchronize(st));
-  }
+  k_run_init<<<1, 64, 0, st>>>(lam, fitd, iter_dev, opt->iter_offset);
+  CPA_LAUNCH_CHECK();
+  ++kernels;
   cudaEvent_t call0 = nullptr, call1 = nullptr;
   if (profile) {
     cudaEventCreate(&call0);
     cudaEventCreate(&call1);
     cudaEventRecord(call0, st);
   }
-  // initial leverage distributions (Alg. 3: p_k <- l(A_k)/r for the initial guess)
-  for (int m = 0; m < D; ++m) {
-    if (prec == CPA_MIXED)
-      CPA_TRY(refresh_distribution<float>(static_cast<float*>(Fm[m]), X->dims[m], r, Cm[m], info + m, Pm[m],
-                                          GA, flev, warn, scan_ws, false, nullptr, st));
-    else
-      CPA_TRY(refresh_distribution<double>(static_cast<double*>(Fm[m]), X->dims[m], r, Cm[m], info + m,
-                                           Pm[m], GA, flev, warn, scan_ws, false, nullptr, st));
+  if (use_graph) {
+    if (!init_exec) CPA_TRY(capture_graph([&](cudaStream_t cs) { return enqueue_init(X, cs); }, &init_exec, &k_init));
+    if (!exec) CPA_TRY(capture(X));
+    if (!fit_exec) CPA_TRY(capture_graph([&](cudaStream_t cs) { return enqueue_fit(X, cs); }, &fit_exec, &k_fit));
+    CPA_CUDA_TRY(cudaGraphLaunch(init_exec, st));
+    kernels += k_init;
+  } else {
+    CPA_TRY(enqueue_init(X, st));
+    kernels = -1;
   }
-  if (use_graph && !exec) CPA_TRY(capture(X));
-  FactorPtrs F;
-  for (int m = 0; m < D; ++m) F.A[m] = Fm[m];
+  // the fit, as a graph where the updates run as one
+  auto fit_now = [&](Profiler& pr) -> int {
+    CPA_TRY(pr.mark(-1));
+    if (use_graph) {
+      CPA_CUDA_TRY(cudaGraphLaunch(fit_exec, st));
+      if (kernels >= 0) kernels += k_fit;
+    } else {
+      CPA_TRY(enqueue_fit(X, st));
+    }
+    return pr.mark(7);
+  };
   Profiler eprof;  // eager path
   eprof.on = profile != 0;
   eprof.st = st;
@@ -516,6 +579,7 @@ int Plan::run(const cpa_index* X, const cpa_options* opt, double* lambda, double
     for (int l = 0; l < eta && it < opt->iters; ++l, ++it) {
       if (use_graph) {
         CPA_CUDA_TRY(cudaGraphLaunch(exec, st));
+        kernels += k_iter;
         if (profile) {  // the captured events hold this replay's timestamps
           CPA_CUDA_TRY(cudaStreamSynchronize(st));
           gprof.collect_add(&acc);
@@ -526,10 +590,7 @@ int Plan::run(const cpa_index* X, const cpa_options* opt, double* lambda, double
     }
     iters_done = it;
     if (opt->tol > 0.0 && opt->fit_mode == CPA_FIT_EXACT) {
-      CPA_TRY(eprof.mark(-1));
-      CPA_TRY(prec == CPA_MIXED ? fit_enqueue<float>(X, F, lam, r, fit_ws, fitd, st)
-                                : fit_enqueue<double>(X, F, lam, r, fit_ws, fitd, st));
-      CPA_TRY(eprof.mark(5));
+      CPA_TRY(fit_now(eprof));
       double f = 0.0;
       int status = 0;
       CPA_CUDA_TRY(cudaMemcpyAsync(&f, fitd, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -547,10 +608,7 @@ int Plan::run(const cpa_index* X, const cpa_options* opt, double* lambda, double
     }
   }
   if (!(opt->tol > 0.0) && opt->fit_mode == CPA_FIT_EXACT) {
-    CPA_TRY(eprof.mark(-1));
-    CPA_TRY(prec == CPA_MIXED ? fit_enqueue<float>(X, F, lam, r, fit_ws, fitd, st)
-                              : fit_enqueue<double>(X, F, lam, r, fit_ws, fitd, st));
-    CPA_TRY(eprof.mark(5));
+    CPA_TRY(fit_now(eprof));
     CPA_CUDA_TRY(cudaMemcpyAsync(&fit_val, fitd, sizeof(double), cudaMemcpyDeviceToHost, st));
   }
   if (profile) cudaEventRecord(call1, st);
@@ -568,6 +626,7 @@ int Plan::run(const cpa_index* X, const cpa_options* opt, double* lambda, double
     if (prec == CPA_MIXED) {
       k_convert<double, float><<<blocks(cnt), 256, 0, st>>>(static_cast<const float*>(Fm[m]), cnt, stage64);
       CPA_LAUNCH_CHECK();
+      if (kernels >= 0) ++kernels;
       CPA_CUDA_TRY(cudaMemcpyAsync(factors[m], stage64, sizeof(double) * cnt, kout, st));
       CPA_CUDA_TRY(cudaStreamSynchronize(st));  // stage64 is reused by the next mode
     } else {
@@ -591,15 +650,16 @@ int Plan::run(const cpa_index* X, const cpa_options* opt, double* lambda, double
     stats->pdet_last = hs.pdet_last;
     stats->nnz_sampled_total = hs.nnz_total;
     stats->sbar_total = hs.sbar_total;
+    stats->kernel_launches = kernels;
     if (profile) {
       eprof.collect_add(stats);
-      for (int i = 0; i < 6; ++i) {
+      for (int i = 0; i < 8; ++i) {
         stats->stage_ms[i] += acc.stage_ms[i];
         stats->stage_launches[i] += acc.stage_launches[i];
       }
       float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, call0, call1) == cudaSuccess) stats->stage_ms[6] = ms;
-      stats->stage_launches[6] = 1;
+      if (cudaEventElapsedTime(&ms, call0, call1) == cudaSuccess) stats->stage_ms[8] = ms;
+      stats->stage_launches[8] = 1;
     }
   }
   if (call0) cudaEventDestroy(call0);
@@ -723,7 +783,7 @@ int cpa_cdf(const double* lev, int64_t n, int32_t r, uint64_t* C, uint64_t* info
   CPA_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(DistInfo), st));
   k_q_from_lev<<<blocks(n), 256, 0, st>>>(lev, n, r, C, info);
   CPA_LAUNCH_CHECK();
-  CPA_TRY(cdf_from_q(C, C, n, info, scratch, st));
+  CPA_TRY(cdf_from_q(C, C, n, info, nullptr, scratch, st));
   DistInfo h;
   CPA_CUDA_TRY(cudaMemcpyAsync(&h, info, sizeof(h), cudaMemcpyDeviceToHost, st));
   CPA_CUDA_TRY(cudaStreamSynchronize(st));
@@ -780,8 +840,7 @@ int cpa_skrp_lev(int32_t d, const int64_t* dims, const double* const* lev, int32
   for (int t = 0; t < d; ++t) {
     k_q_from_lev<<<blocks(dims[t]), 256, 0, st>>>(lev[t], dims[t], r, Cs[t], info + t);
     CPA_LAUNCH_CHECK();
-    CPA_TRY(cdf_from_q(Cs[t], Cs[t], dims[t], info + t, scan_ws, st));
-    CPA_TRY(phat_from_cdf(Cs[t], dims[t], info + t, Ps[t], st));
+    CPA_TRY(cdf_from_q(Cs[t], Cs[t], dims[t], info + t, Ps[t], scan_ws, st));
   }
   SampleParams P;
   memset(&P, 0, sizeof(P));
@@ -830,9 +889,9 @@ int cpa_sampled_mttkrp(const cpa_index* X, int32_t mode_k, const double* const* 
     F.A[m] = factors[m];
     if (m != mode_k && !factors[m]) return CPA_ERR_ARG;
   }
-  CPA_CUDA_TRY(cudaMemsetAsync(M, 0, sizeof(double) * X->dims[mode_k] * r, st));
-  CPA_CUDA_TRY(cudaMemsetAsync(G, 0, sizeof(double) * r * r, st));
   if (sbar == 0) {
+    CPA_CUDA_TRY(cudaMemsetAsync(M, 0, sizeof(double) * X->dims[mode_k] * r, st));
+    CPA_CUDA_TRY(cudaMemsetAsync(G, 0, sizeof(double) * r * r, st));
     if (nnz_sampled) *nnz_sampled = 0;
     CPA_CUDA_TRY(cudaStreamSynchronize(st));
     return CPA_OK;

@@ -186,11 +186,18 @@ struct DevCount {
 // size their *_workspace function returns for the largest count they will see.
 // ---------------------------------------------------------------------------
 size_t scan_workspace(int64_t n_max);
+// Optional extra outputs of a scan, written by the scan's own kernels:
+//   end:   out[count] = total (an exclusive scan with its closing entry);
+//   ratio: ratio[i] = in[i] / total as IEEE doubles (a probability vector).
+struct ScanExtras {
+  bool end = false;
+  double* ratio = nullptr;
+};
 // out[i] = sum_{j<i} in[j] (exclusive) or sum_{j<=i} in[j] (inclusive) for
 // i < count; *total (device, may be null) = sum of all.  in may equal out.
 template <class T>
 int scan_u64(const T* in, uint64_t* out, DevCount count, bool inclusive, uint64_t* total,
-             void* scratch, cudaStream_t st);
+             void* scratch, cudaStream_t st, ScanExtras extras = ScanExtras());
 
 size_t sort_workspace(int64_t n_max);
 // Stable LSD radix sort (8-bit digits) of keys, and values if vals != null, on key

@@ -135,7 +135,8 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor_spd(const double* __r
                                                                int r, int normalize, int pivot,
                                                                double rel_tol,
                                                                SmallFactor* __restrict__ out,
-                                                               int* warn, int warn_bit) {
+                                                               int* warn, int warn_bit,
+                                                               DistInfo* zero_info) {
   extern __shared__ double sm[];
   double* S = sm;              // r x r working matrix (L in its lower triangle)
   double* X = sm + r * r;      // r x r inverse / eigenvectors
@@ -145,6 +146,10 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor_spd(const double* __r
   __shared__ int perm[kMaxRank];
   __shared__ double dmax, dcur;
   const int tid = threadIdx.x, nt = blockDim.x;
+  if (zero_info && tid == 0) {
+    zero_info->maxq = 0;
+    zero_info->nnzq = 0;
+  }
   for (int c = tid; c < r; c += nt) {
     const double g = G[c * r + c];
     const double lam = g > 0.0 ? sqrt(g) : 0.0;
@@ -405,9 +410,11 @@ template <class FT>
 __global__ void __launch_bounds__(kRowThreads) k_solve_rows(const FT* __restrict__ M,
                                                             int64_t n, int r,
                                                             const SmallFactor* __restrict__ f,
-                                                            FT* __restrict__ A) {
+                                                            FT* __restrict__ A, double* zero_gram) {
   extern __shared__ __align__(16) unsigned char solve_smem[];
   FT* F = reinterpret_cast<FT*>(solve_smem);  // r * r
+  if (zero_gram && blockIdx.x == 0)
+    for (int i = threadIdx.x; i < r * r; i += blockDim.x) zero_gram[i] = 0.0;
   for (int i = threadIdx.x; i < r * r; i += blockDim.x) F[i] = (FT)f->F[i];
   __syncthreads();
   const int64_t total = n * r;
@@ -532,7 +539,7 @@ template int gram_rows<double>(const double*, int64_t, int, double*, cudaStream_
 template int gram_rows<float>(const float*, int64_t, int, double*, cudaStream_t);
 
 int factor_spd(const double* G, int r, int normalize, int pivot, double rel_tol, SmallFactor* out,
-               int* warn, int warn_bit, cudaStream_t st) {
+               int* warn, int warn_bit, cudaStream_t st, DistInfo* zero_info) {
   if (r < 1 || r > kMaxRank) return CPA_ERR_ARG;
   const size_t smem = sizeof(double) * (2 * r * r + 2 * r);
   static bool attr_done = false;
@@ -541,7 +548,8 @@ int factor_spd(const double* G, int r, int normalize, int pivot, double rel_tol,
                                       (int)(sizeof(double) * (2 * kMaxRank * kMaxRank + 2 * kMaxRank))));
     attr_done = true;
   }
-  k_factor_spd<<<1, kFactorThreads, smem, st>>>(G, r, normalize, pivot, rel_tol, out, warn, warn_bit);
+  k_factor_spd<<<1, kFactorThreads, smem, st>>>(G, r, normalize, pivot, rel_tol, out, warn, warn_bit,
+                                                zero_info);
   CPA_LAUNCH_CHECK();
   return CPA_OK;
 }
@@ -576,17 +584,20 @@ template int lev_rows<float>(const float*, int64_t, int, const SmallFactor*, dou
                              DistInfo*, float*, cudaStream_t);
 
 template <class FT>
-int solve_rows(const FT* M, int64_t n, int r, const SmallFactor* f, FT* A, cudaStream_t st) {
+int solve_rows(const FT* M, int64_t n, int r, const SmallFactor* f, FT* A, cudaStream_t st,
+               double* zero_gram) {
   if (r < 1 || r > kMaxRank) return CPA_ERR_ARG;
   if (n <= 0) return CPA_OK;
   const size_t smem = sizeof(FT) * (size_t)r * r;
   const unsigned grid = grid_cap(ceil_div(n * r, kRowThreads), 16);
-  k_solve_rows<FT><<<grid, kRowThreads, smem, st>>>(M, n, r, f, A);
+  k_solve_rows<FT><<<grid, kRowThreads, smem, st>>>(M, n, r, f, A, zero_gram);
   CPA_LAUNCH_CHECK();
   return CPA_OK;
 }
-template int solve_rows<double>(const double*, int64_t, int, const SmallFactor*, double*, cudaStream_t);
-template int solve_rows<float>(const float*, int64_t, int, const SmallFactor*, float*, cudaStream_t);
+template int solve_rows<double>(const double*, int64_t, int, const SmallFactor*, double*, cudaStream_t,
+                                double*);
+template int solve_rows<float>(const float*, int64_t, int, const SmallFactor*, float*, cudaStream_t,
+                               double*);
 
 template <class FT>
 int scale_columns(FT* A, int64_t n, int r, const double* lambda, cudaStream_t st) {
@@ -598,9 +609,11 @@ int scale_columns(FT* A, int64_t n, int r, const double* lambda, cudaStream_t st
 template int scale_columns<double>(double*, int64_t, int, const double*, cudaStream_t);
 template int scale_columns<float>(float*, int64_t, int, const double*, cudaStream_t);
 
-int cdf_from_q(uint64_t* q, uint64_t* C, int64_t n, DistInfo* info, void* scan_scratch,
+int cdf_from_q(uint64_t* q, uint64_t* C, int64_t n, DistInfo* info, double* p, void* scan_scratch,
                cudaStream_t st) {
-  CPA_TRY(scan_u64<uint64_t>(q, C, DevCount{nullptr, n}, true, &info->T, scan_scratch, st));
+  ScanExtras ex;
+  ex.ratio = p;
+  CPA_TRY(scan_u64<uint64_t>(q, C, DevCount{nullptr, n}, true, &info->T, scan_scratch, st, ex));
   return CPA_OK;
 }
 

@@ -44,8 +44,10 @@ int gram_rows(const FT* A, int64_t n, int r, double* G, cudaStream_t st);
 // diagonal pivoting (largest remaining diagonal first) stops at the numerical rank,
 // which is exact for leverage scores of rank-deficient matrices.  Either way a
 // singular G OR-s `warn_bit` into *warn.
+// zero_info (may be null) has its maxq/nnzq cleared for the lev_rows that follows.
 int factor_spd(const double* G, int r, int normalize, int pivot, double rel_tol,
-               SmallFactor* out, int* warn, int warn_bit, cudaStream_t st);
+               SmallFactor* out, int* warn, int warn_bit, cudaStream_t st,
+               DistInfo* zero_info = nullptr);
 
 // For every row a_i of A: lev_i = || L^{-1} S a_i ||^2 (kind 0) or a_i^T S F S a_i
 // (kind 1); q_i = round-half-even(2^62 lev_i / r) written to q (if non-null),
@@ -57,15 +59,18 @@ int lev_rows(const FT* A, int64_t n, int r, const SmallFactor* f, double* lev,
 
 // A = M G^{-1} row by row with the factor of G (kind 0: two triangular solves;
 // kind 1: A = M F).
+// zero_gram (may be null): an r x r FP64 matrix cleared for the Gram that follows.
 template <class FT>
-int solve_rows(const FT* M, int64_t n, int r, const SmallFactor* f, FT* A, cudaStream_t st);
+int solve_rows(const FT* M, int64_t n, int r, const SmallFactor* f, FT* A, cudaStream_t st,
+               double* zero_gram = nullptr);
 
 // A(:, c) /= lambda_c for lambda_c > 0.
 template <class FT>
 int scale_columns(FT* A, int64_t n, int r, const double* lambda, cudaStream_t st);
 
-// C = inclusive prefix sum of q (in place allowed); info->T = total.
-int cdf_from_q(uint64_t* q, uint64_t* C, int64_t n, DistInfo* info, void* scan_scratch,
+// C = inclusive prefix sum of q (in place allowed); info->T = total; if p is
+// non-null, p[i] = q_i / T (IEEE division), the per-row sampling probabilities.
+int cdf_from_q(uint64_t* q, uint64_t* C, int64_t n, DistInfo* info, double* p, void* scan_scratch,
                cudaStream_t st);
 
 inline unsigned grid_cap(int64_t blocks, int per_sm = 8) {

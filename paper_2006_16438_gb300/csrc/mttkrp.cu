@@ -1,7 +1,8 @@
 // KrpSamp + TnsrSamp + sampled normal equations (Section 5.2, Section 5.3).
 //
 // 1. probe:    one thread per sample finds its fibre [lo, lo + len) in the mode-k
-//              stream through the bucket directory and a short binary search.
+//              stream through the bucket directory and a short binary search (the
+//              same kernel clears M and G).
 // 2. krp_gram: samples in tiles of 32: y_j = wgt_j * prod_t A_{m_t}(i_t, :) is formed
 //              (row gathers of the other factors), stored for step 4, and
 //              G += y_j y_j^T is accumulated per thread over upper-triangle pairs.
@@ -30,9 +31,16 @@ __device__ __forceinline__ void pair_of(int p, int r, int* a, int* b) {
   *b = row + (p - start);
 }
 
-template <class VT>
+// also clears M (mz elements) and G (r*r) for the kernels that accumulate into them
+template <class VT, class FT>
 __global__ void k_probe(FibreIndex<VT> X, const uint64_t* __restrict__ idx, DevCount sbar,
-                        uint64_t* __restrict__ lo, uint32_t* __restrict__ len) {
+                        uint64_t* __restrict__ lo, uint32_t* __restrict__ len, FT* __restrict__ M,
+                        int64_t mz, double* __restrict__ G, int gz) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < mz;
+       i += (int64_t)gridDim.x * blockDim.x)
+    M[i] = FT(0);
+  if (blockIdx.x == 0)
+    for (int i = threadIdx.x; i < gz; i += blockDim.x) G[i] = 0.0;
   const int64_t n = sbar.get();
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
        j += (int64_t)gridDim.x * blockDim.x) {
@@ -104,10 +112,6 @@ __global__ void __launch_bounds__(kThreads) k_krp_gram(FactorPtrs F, KeyLayout L
   }
 }
 
-__global__ void k_pos_end(DevCount sbar, const uint64_t* __restrict__ total, uint64_t* pos) {
-  pos[sbar.get()] = *total;
-}
-
 // last j in [0, n) with pos[j] <= e (pos ascending, pos[0] = 0 <= e)
 __device__ __forceinline__ int64_t sample_of(const uint64_t* __restrict__ pos, int64_t n, uint64_t e) {
   int64_t a = 0, b = n - 1;
@@ -175,15 +179,16 @@ __global__ void __launch_bounds__(kThreads) k_mttkrp(FibreIndex<VT> X, const FT*
 
 template <class FT, class VT>
 int run(const cpa_index* X, int k, const FactorPtrs& F, int r, const uint64_t* idx, const double* wgt,
-        DevCount sbar, FT* M, double* G, MttkrpBuffers& B, cudaStream_t st, cudaEvent_t mid) {
+        DevCount sbar, FT* M, double* G, MttkrpBuffers& B, cudaStream_t st, cudaEvent_t* ev) {
   const auto& mode = X->mode[k];
   const FibreIndex<VT> fx = fibre_view<VT>(X, k);
   const int64_t s = sbar.max;
   const int sms = num_sms();
   FT* Y = static_cast<FT*>(B.Y);
   int64_t pb = ceil_div(s, kThreads);
-  k_probe<VT><<<(unsigned)(pb < sms * 16 ? pb : sms * 16), kThreads, 0, st>>>(fx, idx, sbar, B.lo,
-                                                                             B.len);
+  k_probe<VT, FT><<<(unsigned)(pb < sms * 16 ? pb : sms * 16), kThreads, 0, st>>>(
+      fx, idx, sbar, B.lo, B.len, M, X->dims[k] * r, G, r * r);
+  if (ev && ev[0]) CPA_CUDA_TRY(record_event(ev[0], st));
   const int np = r * (r + 1) / 2;
   int64_t tb = ceil_div(s, kTileRows);
   const unsigned tgrid = (unsigned)(tb < sms * 2 ? tb : sms * 2);
@@ -195,9 +200,11 @@ int run(const cpa_index* X, int k, const FactorPtrs& F, int r, const uint64_t* i
   else
     k_krp_gram<FT, 9><<<tgrid, kThreads, tsm, st>>>(F, mode.L, r, idx, wgt, sbar, Y, G);
   CPA_LAUNCH_CHECK();
-  CPA_TRY(scan_u64<uint32_t>(B.len, B.pos, sbar, false, B.total, B.scratch, st));
-  k_pos_end<<<1, 1, 0, st>>>(sbar, B.total, B.pos);
-  if (mid) CPA_CUDA_TRY(record_event(mid, st));
+  if (ev && ev[1]) CPA_CUDA_TRY(record_event(ev[1], st));
+  ScanExtras ex;
+  ex.end = true;  // pos[sbar] = nnz of the sampled right-hand side
+  CPA_TRY(scan_u64<uint32_t>(B.len, B.pos, sbar, false, B.total, B.scratch, st, ex));
+  if (ev && ev[2]) CPA_CUDA_TRY(record_event(ev[2], st));
   const int64_t nk = X->dims[k];
   const bool shared = nk * r * sizeof(FT) <= 48 * 1024;
   const size_t msm = shared ? sizeof(FT) * nk * r : 0;
@@ -238,18 +245,18 @@ void mttkrp_buffers_carve(Arena& a, int64_t s, int r, int ft_bytes, MttkrpBuffer
 template <class FT>
 int sampled_mttkrp(const cpa_index* X, int k, const FactorPtrs& F, int r, const uint64_t* idx_packed,
                    const double* wgt, DevCount sbar, FT* M, double* G, MttkrpBuffers& B,
-                   cudaStream_t st, cudaEvent_t mid) {
+                   cudaStream_t st, cudaEvent_t* ev) {
   if (r < 1 || r > kMaxRank) return CPA_ERR_ARG;
   if (sbar.max <= 0) return CPA_OK;
   if (X->val_dtype == CPA_F32)
-    return run<FT, float>(X, k, F, r, idx_packed, wgt, sbar, M, G, B, st, mid);
-  return run<FT, double>(X, k, F, r, idx_packed, wgt, sbar, M, G, B, st, mid);
+    return run<FT, float>(X, k, F, r, idx_packed, wgt, sbar, M, G, B, st, ev);
+  return run<FT, double>(X, k, F, r, idx_packed, wgt, sbar, M, G, B, st, ev);
 }
 template int sampled_mttkrp<double>(const cpa_index*, int, const FactorPtrs&, int, const uint64_t*,
                                     const double*, DevCount, double*, double*, MttkrpBuffers&,
-                                    cudaStream_t, cudaEvent_t);
+                                    cudaStream_t, cudaEvent_t*);
 template int sampled_mttkrp<float>(const cpa_index*, int, const FactorPtrs&, int, const uint64_t*,
                                    const double*, DevCount, float*, double*, MttkrpBuffers&,
-                                   cudaStream_t, cudaEvent_t);
+                                   cudaStream_t, cudaEvent_t*);
 
 }  // namespace cpa

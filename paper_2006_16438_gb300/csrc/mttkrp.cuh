@@ -23,15 +23,15 @@ struct MttkrpBuffers {
 size_t mttkrp_buffers_bytes(int64_t s, int r, int ft_bytes);
 void mttkrp_buffers_carve(Arena& a, int64_t s, int r, int ft_bytes, MttkrpBuffers* B);
 
-// G += sum_j y_j y_j^T and M += sum_j wgt_j x(:, key_j) y_j^T over the sbar samples
-// (packed keys), with y_j = wgt_j prod_t A_{m_t}(i_t, :).  G and M must be zeroed
-// by the caller.  sbar: device count (max s).
-// If mid_event is non-null it is recorded on `st` right before the
-// gather-scale-accumulate kernel (after probe, KRP/Gram and the scan).
+// G = sum_j y_j y_j^T and M = sum_j wgt_j x(:, key_j) y_j^T over the sbar samples
+// (packed keys), with y_j = wgt_j prod_t A_{m_t}(i_t, :); M and G are cleared here.
+// sbar: device count (max s).
+// ev (may be null): three timing events recorded on `st` after the probe, after
+// the KRP/Gram kernel and after the scan (i.e. before the gather-scale-accumulate).
 // FT: element type of the factors, Y and M (double: FP64 path; float: mixed).
 template <class FT>
 int sampled_mttkrp(const cpa_index* X, int k, const FactorPtrs& F, int r,
                    const uint64_t* idx_packed, const double* wgt, DevCount sbar, FT* M,
-                   double* G, MttkrpBuffers& B, cudaStream_t st, cudaEvent_t mid_event = nullptr);
+                   double* G, MttkrpBuffers& B, cudaStream_t st, cudaEvent_t* ev = nullptr);
 
 }  // namespace cpa

@@ -74,8 +74,32 @@ __device__ __forceinline__ void xs_add(uint64_t* bins, double v) {
   if (hi) atomicAdd((unsigned long long*)&bins[limb + 2], (unsigned long long)hi);
 }
 
+// bits [pos, pos + 64) of the little-endian limb array (missing bits read 0)
+__device__ __forceinline__ uint64_t bits64(const uint32_t* w, int nlimbs, int pos) {
+  uint64_t v = 0;
+  for (int k = 0; k < 3; ++k) {  // the window touches at most three limbs
+    const int lb = pos >= 0 ? (pos >> 5) + k : -((-pos + 31) >> 5) + k;
+    if (lb < 0 || lb >= nlimbs) continue;
+    const int shift = lb * 32 - pos;  // position of limb lb inside the window
+    const uint64_t limb = w[lb];
+    if (shift >= 64 || shift <= -32) continue;
+    v |= shift >= 0 ? (limb << shift) : (limb >> -shift);
+  }
+  return v;
+}
+
+// any bit set below position pos
+__device__ __forceinline__ bool any_below(const uint32_t* w, int pos) {
+  if (pos <= 0) return false;
+  const int full = pos >> 5, rem = pos & 31;
+  for (int i = 0; i < full; ++i)
+    if (w[i]) return true;
+  return rem ? (w[full] & ((1u << rem) - 1u)) != 0 : false;
+}
+
 __device__ double xs_round(const uint64_t* bins_in) {
-  uint32_t w[kXsLimbs + 2];
+  constexpr int kL = kXsLimbs + 2;
+  uint32_t w[kL];
   uint64_t carry = 0;
   for (int i = 0; i < kXsLimbs; ++i) {
     const uint64_t v = bins_in[i] + carry;
@@ -85,23 +109,20 @@ __device__ double xs_round(const uint64_t* bins_in) {
   w[kXsLimbs] = (uint32_t)carry;
   w[kXsLimbs + 1] = (uint32_t)(carry >> 32);
   int top = -1;
-  for (int i = kXsLimbs + 1; i >= 0; --i)
+  for (int i = kL - 1; i >= 0; --i)
     if (w[i]) {
       top = i * 32 + 31 - __clz(w[i]);
       break;
     }
   if (top < 0) return 0.0;
-  auto bit = [&](int pos) -> uint32_t { return pos < 0 ? 0u : (w[pos >> 5] >> (pos & 31)) & 1u; };
   if (top < 53) {  // below 2^-1021: the integer itself is the IEEE bit pattern
-    uint64_t m = 0;
-    for (int b = top; b >= 0; --b) m = (m << 1) | bit(b);
-    return __longlong_as_double((long long)m);
+    return __longlong_as_double((long long)bits64(w, kL, 0));
   }
-  uint64_t m = 0;
-  for (int b = top; b > top - 53; --b) m = (m << 1) | bit(b);
-  const uint32_t round_bit = bit(top - 54 + 1);
-  uint32_t sticky = 0;
-  for (int b = top - 54; b >= 0 && !sticky; --b) sticky |= bit(b);
+  // 64-bit window whose top bit is `top`: 53 kept bits, the round bit, 10 more
+  const uint64_t win = bits64(w, kL, top - 63);
+  uint64_t m = win >> 11;
+  const bool round_bit = (win >> 10) & 1ull;
+  const bool sticky = (win & 0x3ffull) != 0 || any_below(w, top - 63);
   if (round_bit && (sticky || (m & 1ull))) ++m;
   uint64_t bexp = (uint64_t)(top - 51);
   if (m == (1ull << 53)) {
@@ -209,20 +230,6 @@ __global__ void k_det_filter(SampleParams P, SampleState* S, uint32_t* __restric
   }
 }
 
-__global__ void k_det_count(SampleParams P, SampleState* S) {
-  if (threadIdx.x != 0 || blockIdx.x != 0 || S->no_det) return;
-  double prod = 1.0;
-  for (int t = 0; t < P.L.d; ++t) prod *= (double)S->ncand[t];
-  if (prod > (double)P.det_cap) {
-    set_status(&S->status, CPA_ERR_DET_CAP);
-    S->no_det = 1;
-    return;
-  }
-  uint64_t total = 1;
-  for (int t = 0; t < P.L.d; ++t) total *= (uint64_t)S->ncand[t];
-  S->cand_total = total;
-}
-
 // enumerate the candidate product; keep p > tau
 __global__ void k_det_enum(SampleParams P, SampleState* S, const uint32_t* __restrict__ cand,
                            int64_t off1, int64_t off2, int64_t off3, int64_t off4, int64_t off5,
@@ -230,13 +237,24 @@ __global__ void k_det_enum(SampleParams P, SampleState* S, const uint32_t* __res
   __shared__ uint64_t bins[kXsLimbs];
   __shared__ int any;
   if (S->no_det) return;
+  // size of the candidate product (every block computes it; block 0 records it)
+  int64_t nc[kMaxOrder];
+  double prod = 1.0;
+  uint64_t total = 1;
+  for (int t = 0; t < P.L.d; ++t) {
+    nc[t] = S->ncand[t];
+    prod *= (double)nc[t];
+    total *= (uint64_t)nc[t];
+  }
+  if (prod > (double)P.det_cap) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) set_status(&S->status, CPA_ERR_DET_CAP);
+    return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) S->cand_total = total;
   for (int i = threadIdx.x; i < kXsLimbs; i += blockDim.x) bins[i] = 0;
   if (threadIdx.x == 0) any = 0;
   __syncthreads();
   const int64_t offs[kMaxOrder] = {0, off1, off2, off3, off4, off5, off6, 0};
-  const uint64_t total = S->cand_total;
-  int64_t nc[kMaxOrder];
-  for (int t = 0; t < P.L.d; ++t) nc[t] = S->ncand[t];
   for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < total;
        e += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t rest = e, packed = 0;
@@ -265,47 +283,86 @@ __global__ void k_det_enum(SampleParams P, SampleState* S, const uint32_t* __res
       if (bins[i]) atomicAdd((unsigned long long*)&S->xs[i], (unsigned long long)bins[i]);
 }
 
-__global__ void k_det_finish(SampleParams P, SampleState* S) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// s_det, s_rnd and p_det once the deterministic enumeration is done
+struct DetSummary {
+  int64_t sdet, srnd;
+  double pdet;
+  int topk, bad;
+};
+
+__device__ DetSummary det_summary(const SampleParams& P, const SampleState* S) {
+  DetSummary r;
+  r.topk = 0;
+  r.bad = 0;
+  r.pdet = 0.0;
   int64_t sdet = (int64_t)S->det_count;
   if (sdet > P.det_buf) {
     // only reachable when tau * s >= 1 by rounding at the threshold: refuse
-    set_status(&S->status, CPA_ERR_DET_CAP);
+    r.bad = 1;
     sdet = 0;
   } else if (sdet > P.s) {
-    S->need_topk = 1;  // the host runs the top-s selection
+    r.topk = 1;  // the host runs the top-s selection
     sdet = P.s;
   } else {
-    S->pdet = xs_round(S->xs);
+    r.pdet = xs_round(S->xs);
   }
-  S->sdet = sdet;
+  r.sdet = sdet;
   // all rows of nonzero probability already deterministic: nothing left to draw
   double support = 1.0;
   for (int t = 0; t < P.L.d; ++t) support *= (double)P.D.info[t]->nnzq;
-  int64_t srnd = P.s - sdet;
-  if ((double)sdet >= support) srnd = 0;
-  S->srnd = srnd;
-  S->nsort = sdet + srnd;
+  r.srnd = (double)sdet >= support ? 0 : P.s - sdet;
+  return r;
 }
 
-__global__ void k_insert_det(SampleState* S, const uint64_t* __restrict__ det_keys,
-                             uint64_t* __restrict__ hkeys, uint32_t* __restrict__ hcnt, int hbits) {
-  const int64_t sdet = S->sdet;
-  if (S->need_topk) return;
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < sdet;
-       j += (int64_t)gridDim.x * blockDim.x)
-    if (!table_add(hkeys, hcnt, hbits, det_keys[j])) set_status(&S->status, CPA_ERR_UNSUPPORTED);
+__device__ void det_store(SampleState* S, const DetSummary& d) {
+  if (d.bad) set_status(&S->status, CPA_ERR_DET_CAP);
+  S->need_topk = d.topk;
+  S->sdet = d.sdet;
+  S->srnd = d.srnd;
+  if (!d.topk) S->pdet = d.pdet;
+  S->nsort = d.sdet + d.srnd;
+}
+
+__global__ void k_det_finish(SampleParams P, SampleState* S) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  det_store(S, det_summary(P, S));
 }
 
 // Alg. 2 with one Philox counter per (slot, attempt)
+// finish = 1: the deterministic summary is computed here (thread 0 of each block,
+// block 0 stores it); finish = 0: k_det_finish (and the host top-s step) did it.
+// Deterministic rows are entered into the combine table first (slot j < s_det),
+// then slot j < s_rnd draws its random row.
 __global__ void __launch_bounds__(kThreads) k_rnd(SampleParams P, SampleState* S,
                                                   uint64_t* __restrict__ hkeys,
                                                   uint32_t* __restrict__ hcnt, int hbits,
+                                                  const uint64_t* __restrict__ det_keys, int finish,
                                                   uint64_t* __restrict__ raw_key,
                                                   double* __restrict__ raw_w) {
-  const int64_t srnd = S->srnd;
-  const double pdet = S->pdet;
+  __shared__ int64_t sh_sdet, sh_srnd;
+  __shared__ double sh_pdet;
+  __shared__ int sh_topk;
+  if (threadIdx.x == 0) {
+    if (finish) {
+      const DetSummary d = det_summary(P, S);
+      if (blockIdx.x == 0) det_store(S, d);
+      sh_sdet = d.sdet;
+      sh_srnd = d.srnd;
+      sh_pdet = d.pdet;
+      sh_topk = d.topk;
+    } else {
+      sh_sdet = S->sdet;
+      sh_srnd = S->srnd;
+      sh_pdet = S->pdet;
+      sh_topk = S->need_topk;
+    }
+  }
+  __syncthreads();
+  const int64_t srnd = sh_srnd;
+  const double pdet = sh_pdet;
   const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (!sh_topk && j < sh_sdet && !table_add(hkeys, hcnt, hbits, det_keys[j]))
+    set_status(&S->status, CPA_ERR_UNSUPPORTED);
   const uint64_t iter = P.iter_ptr ? *P.iter_ptr : P.iter;
   uint64_t tries = 0;
   if (j < srnd) {
@@ -349,8 +406,8 @@ __global__ void __launch_bounds__(kThreads) k_rnd(SampleParams P, SampleState* S
 }
 
 // occupied table slots -> output rows, unordered (warp-aggregated append)
-__global__ void k_table_compact(SampleParams P, SampleState* S, const uint64_t* __restrict__ hkeys,
-                                const uint32_t* __restrict__ hcnt, int hbits,
+__global__ void k_table_compact(SampleParams P, SampleState* S, uint64_t* __restrict__ hkeys,
+                                uint32_t* __restrict__ hcnt, int hbits,
                                 uint64_t* __restrict__ idx_packed, uint32_t* __restrict__ cnt,
                                 double* __restrict__ wgt) {
   const int64_t H = 1ll << hbits;
@@ -374,6 +431,8 @@ __global__ void k_table_compact(SampleParams P, SampleState* S, const uint64_t* 
       idx_packed[u] = packed;
       cnt[u] = c;
       wgt[u] = row_weight(P, packed, det, c, one_minus_pdet, srnd);
+      hkeys[h] = kEmptyKey;  // leave the table empty for the next pass
+      hcnt[h] = 0;
     }
   }
 }
@@ -523,21 +582,23 @@ int skrp_lev(const SampleParams& P, SampleBuffers& B, cudaStream_t st, bool sort
   const int64_t* co = B.cand_off;
   int64_t total_cand = 0;
   for (int t = 0; t < P.L.d; ++t) total_cand += P.L.n[t];
-  CPA_CUDA_TRY(cudaMemsetAsync(B.hkeys, 0xff, sizeof(uint64_t) << B.hbits, st));
-  CPA_CUDA_TRY(cudaMemsetAsync(B.hcnt, 0, sizeof(uint32_t) << B.hbits, st));
+  if (sorted_output) {  // the compacting path leaves the table empty itself
+    CPA_CUDA_TRY(cudaMemsetAsync(B.hkeys, 0xff, sizeof(uint64_t) << B.hbits, st));
+    CPA_CUDA_TRY(cudaMemsetAsync(B.hcnt, 0, sizeof(uint32_t) << B.hbits, st));
+  }
   k_prepare<<<1, 32, 0, st>>>(P, S);
   const bool may_det = P.tau < 1.0;
   if (may_det) {
     k_det_filter<<<blocks_for(total_cand), kThreads, 0, st>>>(
         P, S, B.cand, co[1], co[2], co[3], co[4], co[5], co[6], total_cand);
-    k_det_count<<<1, 32, 0, st>>>(P, S);
     k_det_enum<<<(unsigned)num_sms() * 4, kThreads, 0, st>>>(P, S, B.cand, co[1], co[2], co[3],
                                                               co[4], co[5], co[6], B.det_keys,
                                                               B.det_p);
   }
-  k_det_finish<<<1, 32, 0, st>>>(P, S);
+  const bool host_topk = may_det && P.tau * (double)P.s < 1.0;
+  if (host_topk) k_det_finish<<<1, 32, 0, st>>>(P, S);
   CPA_LAUNCH_CHECK();
-  if (may_det && P.tau * (double)P.s < 1.0) {
+  if (host_topk) {
     // the deterministic set may hold more than s rows: keep the s most probable
     SampleState h;
     CPA_CUDA_TRY(cudaMemcpyAsync(&h, S, sizeof(SampleState), cudaMemcpyDeviceToHost, st));
@@ -581,9 +642,8 @@ int skrp_lev(const SampleParams& P, SampleBuffers& B, cudaStream_t st, bool sort
       CPA_CUDA_TRY(cudaFreeAsync(ka, st));
     }
   }
-  k_insert_det<<<blocks_for(P.s), kThreads, 0, st>>>(S, B.det_keys, B.hkeys, B.hcnt, B.hbits);
-  k_rnd<<<(unsigned)ceil_div(P.s, kThreads), kThreads, 0, st>>>(P, S, B.hkeys, B.hcnt, B.hbits, B.raw_key,
-                                                                B.raw_w);
+  k_rnd<<<(unsigned)ceil_div(P.s, kThreads), kThreads, 0, st>>>(P, S, B.hkeys, B.hcnt, B.hbits, B.det_keys,
+                                                                host_topk ? 0 : 1, B.raw_key, B.raw_w);
   CPA_LAUNCH_CHECK();
   const int64_t H = 1ll << B.hbits;
   if (!sorted_output) {

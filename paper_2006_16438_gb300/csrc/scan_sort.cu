@@ -92,31 +92,45 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tile_offsets(uint64_t* ti
 constexpr int kFusedTiles = 64;  // up to this many tiles a tile sums its predecessors itself
 
 // fused = 1: tile_off holds raw tile sums and each block adds up the ones before it
+// fused = 1: tile_off holds raw tile sums; each block sums its predecessors' (and,
+// when the total is needed, all) itself.  fused = 0: tile_off holds offsets and
+// *total_out the total, both from k_scan_tile_offsets.
 template <class T>
 __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const T* in, uint64_t* out,
                                                              DevCount count,
                                                              const uint64_t* __restrict__ tile_off,
                                                              int inclusive, int fused,
-                                                             uint64_t* total_out) {
+                                                             uint64_t* total_out, int write_end,
+                                                             double* __restrict__ ratio) {
   __shared__ uint64_t sm[32];
-  __shared__ uint64_t base_off;
+  __shared__ uint64_t base_off, grand;
   const int64_t n = count.get();
   const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  const bool need_total = ratio != nullptr || write_end;
   if (fused) {
     if (threadIdx.x < 32) {
-      uint64_t acc = 0;
-      for (int t = threadIdx.x; t < (int)blockIdx.x; t += 32) acc += tile_off[t];
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (threadIdx.x == 0) base_off = acc;
-      if (blockIdx.x == gridDim.x - 1 && total_out) {
-        uint64_t tot = 0;
-        for (int t = threadIdx.x; t < (int)gridDim.x; t += 32) tot += tile_off[t];
-        for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
-        if (threadIdx.x == 0) *total_out = tot;
+      uint64_t acc = 0, tot = 0;
+      for (int t = threadIdx.x; t < (int)gridDim.x; t += 32) {
+        const uint64_t v = tile_off[t];
+        if (t < (int)blockIdx.x) acc += v;
+        tot += v;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        tot += __shfl_xor_sync(0xffffffffu, tot, o);
+      }
+      if (threadIdx.x == 0) {
+        base_off = acc;
+        grand = tot;
+        if (blockIdx.x == gridDim.x - 1 && total_out) *total_out = tot;
       }
     }
     __syncthreads();
+  } else if (need_total) {
+    if (threadIdx.x == 0) grand = *total_out;
+    __syncthreads();
   }
+  if (write_end && blockIdx.x == 0 && threadIdx.x == 0) out[n] = grand;
   if (base >= n) return;  // uniform over the block
   const int64_t g0 = base + (int64_t)threadIdx.x * kScanItems;
   uint64_t v[kScanItems];
@@ -129,9 +143,11 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const T* in, uint64
   uint64_t bt;
   const uint64_t inc = block_inclusive_scan(local, sm, &bt);
   uint64_t run = (fused ? base_off : tile_off[blockIdx.x]) + inc - local;
+  const double Td = ratio ? __ull2double_rn(grand) : 1.0;
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
     if (g0 + i < n) {
+      if (ratio) ratio[g0 + i] = __ddiv_rn(__ull2double_rn(v[i]), Td);
       if (inclusive) {
         run += v[i];
         out[g0 + i] = run;
@@ -265,32 +281,36 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
 
 size_t scan_workspace(int64_t n_max) {
   const int64_t ntiles = ceil_div(n_max > 0 ? n_max : 1, kScanTile);
-  return (size_t)ntiles * sizeof(uint64_t) + 256;
+  return (size_t)(ntiles + 1) * sizeof(uint64_t) + 256;
 }
 
 template <class T>
 int scan_u64(const T* in, uint64_t* out, DevCount count, bool inclusive, uint64_t* total,
-             void* scratch, cudaStream_t st) {
+             void* scratch, cudaStream_t st, ScanExtras ex) {
   const int64_t ntiles = ceil_div(count.max > 0 ? count.max : 1, kScanTile);
   uint64_t* tile_sums = reinterpret_cast<uint64_t*>(scratch);
+  // the non-fused path keeps the total in scratch when the caller gives none
+  uint64_t* tot = total ? total : tile_sums + ntiles;
   k_scan_tile_sums<T><<<(unsigned)ntiles, kScanThreads, 0, st>>>(in, count, tile_sums);
   if (ntiles <= kFusedTiles) {
     // the tile kernel sums its predecessors' totals itself (and writes the total)
     k_scan_tiles<T><<<(unsigned)ntiles, kScanThreads, 0, st>>>(in, out, count, tile_sums,
-                                                                inclusive ? 1 : 0, 1, total);
+                                                                inclusive ? 1 : 0, 1, total,
+                                                                ex.end ? 1 : 0, ex.ratio);
   } else {
-    k_scan_tile_offsets<<<1, kScanThreads, 0, st>>>(tile_sums, ntiles, total);
+    k_scan_tile_offsets<<<1, kScanThreads, 0, st>>>(tile_sums, ntiles, tot);
     k_scan_tiles<T><<<(unsigned)ntiles, kScanThreads, 0, st>>>(in, out, count, tile_sums,
-                                                                inclusive ? 1 : 0, 0, nullptr);
+                                                                inclusive ? 1 : 0, 0, tot,
+                                                                ex.end ? 1 : 0, ex.ratio);
   }
   CPA_LAUNCH_CHECK();
   return CPA_OK;
 }
 
 template int scan_u64<uint64_t>(const uint64_t*, uint64_t*, DevCount, bool, uint64_t*, void*,
-                                 cudaStream_t);
+                                 cudaStream_t, ScanExtras);
 template int scan_u64<uint32_t>(const uint32_t*, uint64_t*, DevCount, bool, uint64_t*, void*,
-                                 cudaStream_t);
+                                 cudaStream_t, ScanExtras);
 
 size_t sort_workspace(int64_t n_max) {
   const int64_t ntiles = ceil_div(n_max > 0 ? n_max : 1, kSortTile);
