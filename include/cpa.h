@@ -135,11 +135,11 @@ typedef struct {
   int64_t nnz_sampled_total; /* sum over updates */
   int64_t sbar_total;      /* sum over updates */
   /* with cpa_options.profile = 1: milliseconds summed over all updates of
-   * [0] SkrpLev (sampling, combine), [1] fibre probe, [2] sampled KRP rows + sampled
-   * Gram (one kernel), [3] prefix sum of the fibre lengths, [4] the
-   * gather-scale-accumulate MTTKRP kernel, [5] the r x r solve, [6] the leverage
-   * refresh of the solved mode, [7] the fit(s); and [8] the whole call.
-   * stage_launches[i] counts the timed intervals. */
+   * [0] SkrpLev (sampling, combine), [1] sampled KRP rows + sampled Gram (one
+   * kernel), [2] fibre probe + sampled KRP rows + sampled MTTKRP (one kernel),
+   * [3] the r x r solve, [4] the leverage refresh of the solved mode, [5] the
+   * fit(s); and [8] the whole call.  stage_launches[i] counts the timed intervals.
+   * Profiling runs [1] and [2] one after the other; otherwise they run concurrently. */
   double stage_ms[12];
   int64_t stage_launches[12];
   /* kernels this call launched on the GPU (each kernel node of a replayed CUDA

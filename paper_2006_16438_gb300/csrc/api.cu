@@ -257,6 +257,7 @@ struct Plan {
   uint64_t* iter_dev = nullptr;
   SampleBuffers SB[kMaxOrder];
   MttkrpBuffers MB;
+  Fork fork;  // side stream of the Gram branch
   // graph of one outer iteration
   bool use_graph = false;
   cudaGraphExec_t exec = nullptr;       // one outer iteration
@@ -317,12 +318,16 @@ struct Plan {
       scan_ws = a.take<char>(scan_workspace(nmax));
       iter_dev = a.take<uint64_t>(1);
       sample_buffers_carve(a, Lsum, s, det_buf, &SB[0]);
-      mttkrp_buffers_carve(a, s, r, ftb, &MB);
+      mttkrp_buffers_carve(a, s, &MB);
       if (pass == 0) {
         if (cudaMalloc((void**)&a.base, a.used) != cudaSuccess) return CPA_ERR_OOM;
         base = a.base;
       }
     }
+    if (cudaStreamCreateWithFlags(&fork.aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&fork.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&fork.ev_join, cudaEventDisableTiming) != cudaSuccess)
+      return CPA_ERR_CUDA;
     // per-mode copies of the sample buffers differ only in the candidate offsets
     for (int k = 0; k < D; ++k) {
       SB[k] = SB[0];
@@ -375,18 +380,18 @@ struct Plan {
       const int64_t nk = X->dims[k];
       FT* Mt = static_cast<FT*>(M);
       FT* Fk = static_cast<FT*>(Fm[k]);
-      cudaEvent_t evs[3] = {prof.pending(1), prof.pending(2), prof.pending(3)};
+      cudaEvent_t evs[2] = {prof.pending(-1), prof.pending(1)};
       CPA_TRY(sampled_mttkrp<FT>(X, k, F, r, SB[k].idx_packed, SB[k].wgt, DevCount{&SB[k].state->sbar, s},
-                                 Mt, Gs, MB, st, prof.on ? evs : nullptr));
-      CPA_TRY(prof.mark(4));
+                                 Mt, Gs, MB, st, prof.on ? evs : nullptr, &fork));
+      CPA_TRY(prof.mark(2));
       CPA_TRY(factor_spd(Gs, r, 0, 0, 1e-13, fsolve, warn, CPA_WARN_SINGULAR_GRAM, st));
       CPA_TRY(solve_rows<FT>(Mt, nk, r, fsolve, Fk, st, GA));
-      CPA_TRY(prof.mark(5));
+      CPA_TRY(prof.mark(3));
       CPA_TRY(refresh_distribution<FT>(Fk, nk, r, Cm[k], info + k, Pm[k], GA, flev, warn, scan_ws, true,
                                        nullptr, st, true));
       k_finish_update<<<1, 64, 0, st>>>(flev, r, lam, dstats, SB[k].state, MB.total, warn);
       CPA_LAUNCH_CHECK();
-      CPA_TRY(prof.mark(6));
+      CPA_TRY(prof.mark(4));
     }
     k_advance_iter<<<1, 1, 0, st>>>(iter_dev);
     CPA_LAUNCH_CHECK();
@@ -431,7 +436,7 @@ struct Plan {
   int capture(const cpa_index* X) {
     gprof.on = profile != 0;
     gprof.st = nullptr;
-    if (gprof.on) gprof.reserve(8 * D);
+    if (gprof.on) gprof.reserve(7 * D);
     return capture_graph(
         [&](cudaStream_t cs) {
           gprof.st = cs;
@@ -507,6 +512,9 @@ struct Plan {
     if (init_exec) cudaGraphExecDestroy(init_exec);
     if (fit_exec) cudaGraphExecDestroy(fit_exec);
     if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (fork.aux) cudaStreamDestroy(fork.aux);
+    if (fork.ev_fork) cudaEventDestroy(fork.ev_fork);
+    if (fork.ev_join) cudaEventDestroy(fork.ev_join);
     if (base) {
       cudaDeviceSynchronize();
       cudaFree(base);
@@ -563,7 +571,7 @@ int Plan::run(const cpa_index* X, const cpa_options* opt, double* lambda, double
     } else {
       CPA_TRY(enqueue_fit(X, st));
     }
-    return pr.mark(7);
+    return pr.mark(5);
   };
   Profiler eprof;  // eager path
   eprof.on = profile != 0;
@@ -653,7 +661,7 @@ int Plan::run(const cpa_index* X, const cpa_options* opt, double* lambda, double
     stats->kernel_launches = kernels;
     if (profile) {
       eprof.collect_add(stats);
-      for (int i = 0; i < 8; ++i) {
+      for (int i = 0; i < 6; ++i) {
         stats->stage_ms[i] += acc.stage_ms[i];
         stats->stage_launches[i] += acc.stage_launches[i];
       }
@@ -903,7 +911,7 @@ int cpa_sampled_mttkrp(const cpa_index* X, int32_t mode_k, const double* const* 
   for (int pass = 0; pass < 2; ++pass) {
     a.used = 0;
     packed = a.take<uint64_t>(sbar);
-    mttkrp_buffers_carve(a, sbar, r, 8, &B);
+    mttkrp_buffers_carve(a, sbar, &B);
     if (pass == 0) {
       CPA_TRY(buf.alloc(a.used, st));
       a.base = (char*)buf.p;

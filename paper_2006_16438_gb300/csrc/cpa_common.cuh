@@ -20,6 +20,19 @@ constexpr int kWarp = 32;
 // ---------------------------------------------------------------------------
 // Device-side status: kernels record the first error here instead of trapping.
 // ---------------------------------------------------------------------------
+// Comparisons of doubles through their bit patterns.  For non-negative, non-NaN
+// values the IEEE patterns order like the values, so an integer compare gives the
+// exact result; GB300's FP64 compare (and min/max) has a dependent latency of about
+// 200 cycles against a few for the integer forms.
+__device__ __forceinline__ bool nonneg_gt(double a, double b) {  // a > b, a and b >= 0
+  return __double_as_longlong(a) > __double_as_longlong(b);
+}
+// a > 0, false for -0, negative values and NaN
+__device__ __forceinline__ bool pos_finite(double a) {
+  const long long v = __double_as_longlong(a);
+  return v > 0 && v < 0x7ff0000000000000ll;
+}
+
 __device__ __forceinline__ void set_status(int* status, int code) {
   atomicCAS(status, 0, code);
 }

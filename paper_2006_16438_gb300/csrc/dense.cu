@@ -23,7 +23,8 @@ __device__ __forceinline__ void pair_of(int p, int r, int* a, int* b) {
   *b = row + (p - start);
 }
 
-// Per-thread partial sums over a tile are in FT; tile partials are added in FP64.
+// Factor rows of storage type FT are multiplied and summed in FP64 (the Gram feeds
+// leverage scores and the fit, both O(r^2 n) and far from the hot loop).
 template <class FT, int PMAX>
 __global__ void __launch_bounds__(kGramThreads) k_gram_rows(const FT* __restrict__ A,
                                                             int64_t n, int r,
@@ -51,9 +52,9 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_rows(const FT* __restrict
     for (int q = 0; q < PMAX; ++q) {
       const int p = threadIdx.x + q * kGramThreads;
       if (p < np) {
-        FT s = FT(0);
-        for (int i = 0; i < rows; ++i) s = fma(tile[i * r + pa[q]], tile[i * r + pb[q]], s);
-        acc[q] += (double)s;
+        double s = 0.0;
+        for (int i = 0; i < rows; ++i) s = fma((double)tile[i * r + pa[q]], (double)tile[i * r + pb[q]], s);
+        acc[q] += s;
       }
     }
   }
@@ -73,7 +74,7 @@ constexpr int kFactorThreads = 256;
 // Cyclic Jacobi eigendecomposition of the symmetric matrix in `a` (r x r,
 // overwritten by its eigenvalues on the diagonal), eigenvectors in the columns of
 // `v`.  Serial: run by one thread (it is the rare fallback path).
-__device__ void jacobi_eigen_serial(double* a, double* v, int r) {
+__device__ __noinline__ void jacobi_eigen_serial(double* a, double* v, int r) {
   for (int i = 0; i < r; ++i)
     for (int j = 0; j < r; ++j) v[i * r + j] = (i == j) ? 1.0 : 0.0;
   for (int sweep = 0; sweep < 60; ++sweep) {
@@ -118,18 +119,53 @@ __device__ void jacobi_eigen_serial(double* a, double* v, int r) {
 // division and square root cost hundreds of cycles each, so the factorisation keeps
 // them off its serial chain.
 __device__ __forceinline__ double rsqrt_newton(double d) {
-  double y = (double)rsqrtf((float)d);
-  if (!(y > 0.0) || isinf(y)) y = rsqrt(d);  // outside float range: library rsqrt
-  y = y * (1.5 - 0.5 * d * y * y);
-  y = y * (1.5 - 0.5 * d * y * y);
+  const float yf = rsqrtf((float)d);
+  double y = (yf > 0.f && yf < INFINITY) ? (double)yf : rsqrt(d);  // outside float range: library rsqrt
+  y = y * fma(-0.5 * d, y * y, 1.5);
+  y = y * fma(-0.5 * d, y * y, 1.5);
   return y;
 }
 
-// Factor one r x r PSD matrix in one block (see SmallFactor):
-//  * right-looking Cholesky of S = diag(scale) G diag(scale), with diagonal pivoting
-//    (pivot = 1, stops at the numerical rank) or without (pivot = 0);
-//  * the inverse X = L^{-1} of the rank x rank factor by right-looking substitution;
-//  * pivot = 1: F = X (kind 0); pivot = 0: F = X^T X = S^{-1} (kind 2);
+// 1/d for d > 0 in FP64: FP32 seed x, e = 1 - d x, then x (1 + e + e^2) (the
+// truncated series of 1/(1 - e)), relative error about e^3 ~ 2^-69 before rounding.
+// The range check is done in FP32 (FP64 compares are slow on this part).
+__device__ __forceinline__ double rcp_newton(double d) {
+  const float xf = __frcp_rn((float)d);
+  if (!(xf > 0.f && xf < INFINITY)) return 1.0 / d;  // outside float range
+  const double x = (double)xf;
+  const double e = fma(-d, x, 1.0);
+  return fma(x, fma(e, e, e), x);
+}
+
+// Order-preserving 32-bit key of a double for the pivot search: the upper word of a
+// positive double orders like its value (ties within 2^-20 relative); values <= 0 map
+// to 0.  Integer operations only (FP64 conversions use the slow FP64 pipe).
+__device__ __forceinline__ unsigned pivot_key(double v) {
+  const long long b = __double_as_longlong(v);
+  return b > 0 ? (unsigned)((unsigned long long)b >> 32) : 0u;
+}
+
+// Factor one r x r PSD matrix in one block (see SmallFactor).
+//
+// Square-root-free Cholesky S = P L D L^T P^T of S = diag(scale) G diag(scale), L unit
+// lower triangular, with diagonal pivoting (pivot = 1: the largest remaining diagonal
+// entry first, stopping at the numerical rank) or without (pivot = 0).  The unit
+// lower inverse X = L^{-1} is accumulated in the same sweep: by the recurrence
+// X(j, :) = e_j - sum_{u<j} L(j, u) X(u, :), row j of X is final when j is pivoted,
+// and its contribution L(i, j) X(j, :) is added at once to every remaining row i
+// (kept as B = -sum L X).  Pivoting is by index: entries stay in place (S is kept
+// symmetric, by original index) and ord[] maps pivot positions to original indices.
+//
+// Each step is two barriers.  Phase C stages the pivot row sp = S(p, :), its scaled
+// copy sh = sp / D_j and the ordering after the swap; in phase B every remaining
+// Schur-complement entry and every entry of B(i, 0..j) is one FMA of staged values,
+// packed over all threads (a GB300 FP64 warp instruction costs the same with any
+// number of active lanes), while warp 0 updates the remaining diagonal, takes the
+// reciprocals of all of it and picks the next pivot.
+// Outputs:
+//  * pivot = 1: F = D^{-1/2} X (the inverse of the Cholesky factor L D^{1/2}),
+//    perm = the pivot order, rank = the number of pivots (kind 0);
+//  * pivot = 0: F = X^T D^{-1} X = S^{-1} (kind 2);
 //  * pivot = 0 and a pivot <= rel_tol * max diag: F = pinv(S) by Jacobi (kind 1).
 __global__ void __launch_bounds__(kFactorThreads) k_factor_spd(const double* __restrict__ G,
                                                                int r, int normalize, int pivot,
@@ -138,121 +174,146 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor_spd(const double* __r
                                                                int* warn, int warn_bit,
                                                                DistInfo* zero_info) {
   extern __shared__ double sm[];
-  double* S = sm;              // r x r working matrix (L in its lower triangle)
-  double* X = sm + r * r;      // r x r inverse / eigenvectors
-  double* scale = X + r * r;   // r
-  double* y = scale + r;       // r: 1 / L_jj
-  __shared__ int ok, rank, piv;
+  double* S = sm;              // r x r, symmetric, by original index
+  double* B = sm + r * r;      // r x r: B(i, c) = -sum_u L(i, u) X(u, c), c in pivot order
+  double* sh = B + r * r;      // r: S(p, c) / D_j of the current pivot p
+  double* sp = sh + r;         // r: S(p, c)
+  double* dinv = sp + r;       // r: 1 / D_j
+  double* Dv = dinv + r;       // r: D_j
+  double* scale = Dv + r;      // r
+  __shared__ int ordb[2][kMaxRank];  // pivot position -> original index
+  __shared__ unsigned short tri[kMaxRank * (kMaxRank - 1) / 2];  // q -> (a, b), a > b
   __shared__ int perm[kMaxRank];
-  __shared__ double dmax, dcur;
-  const int tid = threadIdx.x, nt = blockDim.x;
+  __shared__ int s_fail, s_p, s_ppos;
+  __shared__ double s_dmax, s_d, s_di;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
   if (zero_info && tid == 0) {
     zero_info->maxq = 0;
     zero_info->nnzq = 0;
   }
   for (int c = tid; c < r; c += nt) {
     const double g = G[c * r + c];
-    const double lam = g > 0.0 ? sqrt(g) : 0.0;
-    out->lambda[c] = lam;
-    scale[c] = normalize ? (lam > 0.0 ? 1.0 / lam : 0.0) : 1.0;
+    const bool pos = pos_finite(g);
+    const double y = pos ? rsqrt_newton(g) : 0.0;  // 1 / sqrt(G_cc)
+    out->lambda[c] = pos ? g * y : 0.0;
+    scale[c] = normalize ? y : 1.0;
     out->scale[c] = scale[c];
-    perm[c] = c;
+    ordb[0][c] = c;
   }
+  for (int a = 1 + tid; a < r; a += nt)
+    for (int b = 0; b < a; ++b) tri[a * (a - 1) / 2 + b] = (unsigned short)((a << 8) | b);
   __syncthreads();
   for (int i = tid; i < r * r; i += nt) {
     const int a = i / r, b = i - a * r;
-    const double v = G[i] * scale[a] * scale[b];
-    S[i] = v;
-    out->gram[i] = v;
-    X[i] = 0.0;
+    S[i] = G[i] * scale[a] * scale[b];
+    B[i] = 0.0;
   }
   __syncthreads();
-  if (tid < 32) {  // largest diagonal entry
-    double m = 0.0;
-    for (int c = tid; c < r; c += 32) m = fmax(m, S[c * r + c]);
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (tid == 0) {
-      dmax = m;
-      ok = 1;
-      rank = r;
+  // First pivot (warp 0): the diagonal's maximum, key argmax and reciprocal.
+  if (warp == 0) {
+    const int x0 = lane, x1 = lane + 32;
+    const double v0 = x0 < r ? S[x0 * (r + 1)] : 0.0, v1 = x1 < r ? S[x1 * (r + 1)] : 0.0;
+    // largest diagonal entry (negative entries count as 0) by integer max of bits
+    long long mb = max(max(__double_as_longlong(v0), __double_as_longlong(v1)), 0ll);
+    for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+    const double m = __longlong_as_double(mb);
+    int pp = 0;
+    if (pivot) {
+      const unsigned k0 = x0 < r ? pivot_key(v0) : 0u, k1 = x1 < r ? pivot_key(v1) : 0u;
+      const unsigned km = __reduce_max_sync(0xffffffffu, k0 > k1 ? k0 : k1);
+      const unsigned b0 = __ballot_sync(0xffffffffu, x0 < r && k0 == km);
+      const unsigned b1 = __ballot_sync(0xffffffffu, x1 < r && k1 == km);
+      pp = b0 ? __ffs(b0) - 1 : 32 + __ffs(b1) - 1;
+    }
+    const double dp = __shfl_sync(0xffffffffu, pp < 32 ? v0 : v1, pp & 31);
+    if (lane == 0) {
+      s_dmax = m;
+      s_fail = 0;
+      s_p = pp;
+      s_ppos = pp;
+      s_d = dp;
+      s_di = pos_finite(dp) ? rcp_newton(dp) : 0.0;
     }
   }
   __syncthreads();
+  const double cut = rel_tol * s_dmax;
+  int k = r;
   for (int j = 0; j < r; ++j) {
-    if (tid < 32) {  // pivot choice and 1/sqrt of the pivot
-      int p = j;
-      if (pivot) {
-        double best = -1.0;
-        for (int i = j + tid; i < r; i += 32) {
-          const double d = S[i * r + i];
-          if (d > best) {
-            best = d;
-            p = i;
-          }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-          const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-          const int op = __shfl_xor_sync(0xffffffffu, p, o);
-          if (ob > best || (ob == best && op < p)) {
-            best = ob;
-            p = op;
-          }
-        }
-      }
-      const double d = S[p * r + p];
-      if (tid == 0) {
-        piv = p;
-        dcur = d;
-        if (!(d > rel_tol * dmax)) {
-          if (pivot) rank = j; else ok = 0;
-        } else {
-          y[j] = rsqrt_newton(d);
-        }
-      }
+    const int p = s_p, ppos = s_ppos;
+    const double d = s_d, di = s_di;
+    if (!(pos_finite(d) && nonneg_gt(d, cut))) {  // d > cut; same decision in every thread
+      if (pivot) k = j; else if (tid == 0) s_fail = 1;
+      break;
+    }
+    int* ordn = ordb[(j + 1) & 1];
+    // phase C: stage the pivot row and the ordering after the swap of j and ppos
+    if (tid < r) {
+      const int* ord = ordb[j & 1];
+      const double v = S[p * r + tid];
+      sp[tid] = v;
+      sh[tid] = v * di;
+      ordn[tid] = tid == j ? p : (tid == ppos ? ord[j] : ord[tid]);
+    }
+    if (tid == 0) {
+      perm[j] = p;
+      dinv[j] = di;
+      Dv[j] = d;
     }
     __syncthreads();
-    if (rank == j || !ok) break;
-    const int p = piv;
-    if (p != j) {  // symmetric swap of rows/columns j and p (includes computed L entries)
-      for (int c = tid; c < r; c += nt) {
-        const double t = S[j * r + c];
-        S[j * r + c] = S[p * r + c];
-        S[p * r + c] = t;
-      }
-      if (tid == 0) {
-        const int t = perm[j];
-        perm[j] = perm[p];
-        perm[p] = t;
-      }
-      __syncthreads();
-      for (int c = tid; c < r; c += nt) {
-        const double t = S[c * r + j];
-        S[c * r + j] = S[c * r + p];
-        S[c * r + p] = t;
-      }
-      __syncthreads();
-    }
-    const double yj = y[j];
-    for (int i = j + 1 + tid; i < r; i += nt) S[i * r + j] *= yj;  // column j of L
-    if (tid == 0) S[j * r + j] = dcur * yj;                        // L_jj = sqrt(d)
-    __syncthreads();
-    // trailing update of the lower triangle: S_ic -= L_ij L_cj for j < c <= i
+    // phase B; remaining pivot positions are j+1 .. r-1
     const int m = r - j - 1;
-    const int npairs = m * (m + 1) / 2;
-    for (int q = tid; q < npairs; q += nt) {
-      // q -> (i, c) with c <= i, both offset by j + 1
-      int ii = (int)((sqrtf(8.0f * q + 1.0f) - 1.0f) * 0.5f);
-      while ((ii + 1) * (ii + 2) / 2 <= q) ++ii;
-      while (ii * (ii + 1) / 2 > q) --ii;
-      const int cc = q - ii * (ii + 1) / 2;
-      const int i = ii + j + 1, c = cc + j + 1;
-      const double v = S[i * r + c] - S[i * r + j] * S[c * r + j];
+    const int* rem = ordn + j + 1;  // original indices of the remaining positions
+    if (warp == 0 && m > 0) {       // diagonal, reciprocals and the next pivot
+      double v0 = 0.0, v1 = 0.0;
+      if (lane < m) {
+        const int i = rem[lane];
+        v0 = fma(-sh[i], sp[i], S[i * (r + 1)]);
+        S[i * (r + 1)] = v0;
+      }
+      if (lane + 32 < m) {
+        const int i = rem[lane + 32];
+        v1 = fma(-sh[i], sp[i], S[i * (r + 1)]);
+        S[i * (r + 1)] = v1;
+      }
+      int pq = 0;  // offset of the next pivot among the remaining positions
+      if (pivot) {
+        const unsigned k0 = lane < m ? pivot_key(v0) : 0u, k1 = lane + 32 < m ? pivot_key(v1) : 0u;
+        const unsigned km = __reduce_max_sync(0xffffffffu, k0 > k1 ? k0 : k1);
+        const unsigned b0 = __ballot_sync(0xffffffffu, lane < m && k0 == km);
+        const unsigned b1 = __ballot_sync(0xffffffffu, lane + 32 < m && k1 == km);
+        pq = b0 ? __ffs(b0) - 1 : 32 + __ffs(b1) - 1;
+      }
+      const double dn = __shfl_sync(0xffffffffu, pq >= 32 ? v1 : v0, pq & 31);
+      if (lane == 0) {
+        s_p = rem[pq];
+        s_ppos = j + 1 + pq;
+        s_d = dn;
+        s_di = pos_finite(dn) ? rcp_newton(dn) : 0.0;
+      }
+    }
+    const int np = m * (m - 1) / 2;
+    for (int q = tid; q < np; q += nt) {  // off-diagonal Schur complement
+      const int ab = tri[q];
+      const int i = rem[ab >> 8], c = rem[ab & 255];
+      const double v = fma(-sh[i], sp[c], S[i * r + c]);
       S[i * r + c] = v;
-      if (c != i) S[c * r + i] = v;  // keep the trailing block symmetric for swaps
+      S[c * r + i] = v;
+    }
+    const int w = j + 1;
+    const float inv_w = 1.0f / (float)w;
+    for (int q = tid; q < m * w; q += nt) {  // B(i, :) -= L(i, j) X(j, :)
+      const int row = __float2int_rz(((float)q + 0.5f) * inv_w);
+      const int c = q - row * w;
+      const int i = rem[row];
+      const double xjc = c == j ? 1.0 : B[p * r + c];
+      B[i * r + c] = fma(-sh[i], xjc, B[i * r + c]);
     }
     __syncthreads();
   }
-  if (!ok) {  // plain Cholesky failed: pseudo-inverse from the eigendecomposition
+  __syncthreads();  // s_fail, and the step that ended the loop early
+  if (s_fail) {  // plain Cholesky failed: pseudo-inverse from the eigendecomposition
+    double* X = B;
+    double* y = sh;
     for (int i = tid; i < r * r; i += nt) {
       const int a = i / r, b = i - a * r;
       S[i] = G[i] * scale[a] * scale[b];
@@ -280,23 +341,18 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor_spd(const double* __r
     for (int c = tid; c < r; c += nt) out->perm[c] = c;
     return;
   }
-  const int k = rank;
-  // X = L^{-1} (k x k), right-looking: row i of X is final once the rows above are
-  // folded in; y holds 1/L_ii.  X starts at zero and accumulates -sum L_iu X_uc.
-  for (int i = 0; i < k; ++i) {
-    const double yi = y[i];
-    for (int c = tid; c <= i; c += nt) X[i * r + c] = ((i == c ? 1.0 : 0.0) - X[i * r + c]) * yi;
-    __syncthreads();
-    const int rows = k - i - 1, cols = i + 1;
-    for (int q = tid; q < rows * cols; q += nt) {
-      const int i2 = i + 1 + q / cols, c = q % cols;
-      X[i2 * r + c] += S[i2 * r + i] * X[i * r + c];
-    }
-    __syncthreads();
-  }
+  // X(j, c) = [c == j] + B(perm_j, c) for c <= j < k
   if (pivot) {
-    for (int i = tid; i < r * r; i += nt) out->F[i] = X[i];
-    for (int c = tid; c < r; c += nt) out->perm[c] = perm[c];
+    for (int j = tid; j < k; j += nt) sh[j] = rsqrt_newton(Dv[j]);
+    __syncthreads();
+    for (int i = tid; i < r * r; i += nt) {
+      const int j = i / r, c = i - j * r;
+      double v = 0.0;
+      if (j < k && c <= j) v = ((c == j ? 1.0 : 0.0) + B[perm[j] * r + c]) * sh[j];
+      out->F[i] = v;
+    }
+    const int* ordk = ordb[k & 1];
+    for (int c = tid; c < r; c += nt) out->perm[c] = c < k ? perm[c] : ordk[c];
     if (tid == 0) {
       out->kind = 0;
       out->rank = k;
@@ -304,13 +360,23 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor_spd(const double* __r
     }
     return;
   }
-  // F = X^T X = (L L^T)^{-1}
+  // S^{-1} = X^T D^{-1} X (no pivoting: pivot order = original order): X to S, then
+  // Y = D^{-1} X to B, F(a, b) = sum_u X(u, a) Y(u, b) over the lower triangle
+  for (int i = tid; i < r * r; i += nt) {
+    const int j = i / r, c = i - j * r;
+    const double x = c <= j ? ((c == j ? 1.0 : 0.0) + B[j * r + c]) : 0.0;
+    S[i] = x;
+  }
+  __syncthreads();
+  for (int i = tid; i < r * r; i += nt) B[i] = S[i] * dinv[i / r];
+  __syncthreads();
   for (int i = tid; i < r * r; i += nt) {
     const int a = i / r, b = i - a * r;
-    const int u0 = a > b ? a : b;
+    if (b > a) continue;
     double s2 = 0.0;
-    for (int u = u0; u < r; ++u) s2 = fma(X[u * r + a], X[u * r + b], s2);
+    for (int u = a; u < r; ++u) s2 = fma(S[u * r + a], B[u * r + b], s2);
     out->F[i] = s2;
+    out->F[b * r + a] = s2;
   }
   for (int c = tid; c < r; c += nt) out->perm[c] = c;
   if (tid == 0) {
@@ -320,10 +386,18 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor_spd(const double* __r
 }
 
 // ---- per-row kernels -------------------------------------------------------
+// p > 0 ? min(p, 1) : 0 (NaN -> 0), by integer compares of the bit pattern
+__device__ __forceinline__ double clamp01(double p) {
+  const long long b = __double_as_longlong(p);
+  if (b <= 0 || b > 0x7ff0000000000000ll) return 0.0;
+  return b < 0x3ff0000000000000ll ? p : 1.0;
+}
+
 constexpr int kRowThreads = 256;
 constexpr int64_t kManyRows = 1 << 16;  // from here on one thread per row
 
-// Leverage of row a_i (one warp per row, lane c owns coordinate c and c + 32):
+// Leverage of row a_i (one warp per row, lane c owns coordinate c and c + 32), in
+// FP64 whatever the storage type FT of the factor:
 // kind 0: y = X P^T (S a), l = ||y||^2 over the rank's coordinates;
 // kind 1: l = (S a)^T F (S a).
 template <class FT>
@@ -333,14 +407,15 @@ __global__ void __launch_bounds__(kRowThreads) k_lev_rows(const FT* A, int64_t n
                                                           uint64_t* __restrict__ q,
                                                           DistInfo* info, FT* A_out) {
   extern __shared__ __align__(16) unsigned char lev_smem[];
-  FT* F = reinterpret_cast<FT*>(lev_smem);  // r * r
-  FT* sc = F + r * r;                       // r
-  FT* lam = sc + r;                         // r
+  double* F = reinterpret_cast<double*>(lev_smem);  // r * r
+  double* sc = F + r * r;                           // r
+  FT* lam = reinterpret_cast<FT*>(sc + r);          // r
   __shared__ int perm[kMaxRank];
-  for (int i = threadIdx.x; i < r * r; i += blockDim.x) F[i] = (FT)f->F[i];
+  for (int i = threadIdx.x; i < r * r; i += blockDim.x) F[i] = f->F[i];
   for (int i = threadIdx.x; i < r; i += blockDim.x) {
-    sc[i] = (FT)f->scale[i];
-    lam[i] = (FT)f->lambda[i];
+    sc[i] = f->scale[i];
+    const double l = f->lambda[i];
+    lam[i] = pos_finite(l) ? (FT)(1.0 / l) : FT(1);  // 1 / lambda_c, or 1 for a zero column
     perm[i] = f->perm[i];
   }
   __syncthreads();
@@ -353,30 +428,30 @@ __global__ void __launch_bounds__(kRowThreads) k_lev_rows(const FT* A, int64_t n
   uint32_t my_nz = 0;
   for (int64_t row = gw; row < n; row += nwarps) {
     const FT* a = A + row * r;
-    FT part = FT(0);
+    double part = 0.0;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int c = lane + 32 * h;
       if (c < k) {
-        FT t = FT(0);
+        double t = 0.0;
         if (kind == 0) {
           for (int u = 0; u <= c; ++u) {
             const int pu = perm[u];
-            t = fma(F[c * r + u], a[pu] * sc[pu], t);
+            t = fma(F[c * r + u], (double)a[pu] * sc[pu], t);
           }
           part = fma(t, t, part);
         } else {
-          for (int u = 0; u < r; ++u) t = fma(F[c * r + u], a[u] * sc[u], t);
-          part = fma(a[c] * sc[c], t, part);
+          for (int u = 0; u < r; ++u) t = fma(F[c * r + u], (double)a[u] * sc[u], t);
+          part = fma((double)a[c] * sc[c], t, part);
         }
       }
     }
     for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
     if (lane == 0) {
-      if (lev) lev[row] = (double)part;
+      if (lev) lev[row] = part;
       if (q) {
-        double p = (double)part / (double)r;
-        p = p > 0.0 ? (p < 1.0 ? p : 1.0) : 0.0;
+        double p = part / (double)r;
+        p = clamp01(p);
         const uint64_t qi = __double2ull_rn(p * 4611686018427387904.0);  // 2^62
         q[row] = qi;
         my_max = qi > my_max ? qi : my_max;
@@ -385,10 +460,7 @@ __global__ void __launch_bounds__(kRowThreads) k_lev_rows(const FT* A, int64_t n
     }
     if (A_out) {
       __syncwarp();
-      for (int c = lane; c < r; c += 32) {
-        const FT v = a[c];
-        A_out[row * r + c] = lam[c] > FT(0) ? v / lam[c] : v;
-      }
+      for (int c = lane; c < r; c += 32) A_out[row * r + c] = a[c] * lam[c];
     }
   }
   if (q && info) {
@@ -448,16 +520,17 @@ __global__ void __launch_bounds__(kRowThreads) k_lev_rows_tpr(const FT* A, int64
                                                               uint64_t* __restrict__ q,
                                                               DistInfo* info, FT* A_out) {
   extern __shared__ __align__(16) unsigned char tpr_smem[];
-  FT* F = reinterpret_cast<FT*>(tpr_smem);  // r * r
-  FT* sc = F + r * r;                       // r
-  FT* lam = sc + r;                         // r
-  FT* xs = lam + r;                         // kRowThreads * (r + 1)
+  double* F = reinterpret_cast<double*>(tpr_smem);  // r * r
+  double* sc = F + r * r;                           // r
+  FT* lam = reinterpret_cast<FT*>(sc + r);          // r
+  FT* xs = lam + ((r + 1) & ~1);                    // kRowThreads * (r + 1), storage type
   __shared__ int perm[kMaxRank];
   const int ld = r + 1;
-  for (int i = threadIdx.x; i < r * r; i += blockDim.x) F[i] = (FT)f->F[i];
+  for (int i = threadIdx.x; i < r * r; i += blockDim.x) F[i] = f->F[i];
   for (int i = threadIdx.x; i < r; i += blockDim.x) {
-    sc[i] = (FT)f->scale[i];
-    lam[i] = (FT)f->lambda[i];
+    sc[i] = f->scale[i];
+    const double l = f->lambda[i];
+    lam[i] = pos_finite(l) ? (FT)(1.0 / l) : FT(1);  // 1 / lambda_c, or 1 for a zero column
     perm[i] = f->perm[i];
   }
   const int kind = f->kind;
@@ -469,27 +542,30 @@ __global__ void __launch_bounds__(kRowThreads) k_lev_rows_tpr(const FT* A, int64
     __syncthreads();
     for (int i = threadIdx.x; i < rows * r; i += kRowThreads) {
       const int rr = i / r, c = i - rr * r;
-      xs[rr * ld + c] = A[row0 * r + i] * sc[c];
+      xs[rr * ld + c] = A[row0 * r + i];
     }
     __syncthreads();
     if (threadIdx.x < rows) {
       const FT* x = xs + threadIdx.x * ld;
-      FT l = FT(0);
+      double l = 0.0;
       for (int c = 0; c < k; ++c) {
-        FT t = FT(0);
+        double t = 0.0;
         if (kind == 0) {
-          for (int u = 0; u <= c; ++u) t = fma(F[c * r + u], x[perm[u]], t);
+          for (int u = 0; u <= c; ++u) {
+            const int pu = perm[u];
+            t = fma(F[c * r + u], (double)x[pu] * sc[pu], t);
+          }
           l = fma(t, t, l);
         } else {
-          for (int u = 0; u < r; ++u) t = fma(F[c * r + u], x[u], t);
-          l = fma(x[c], t, l);
+          for (int u = 0; u < r; ++u) t = fma(F[c * r + u], (double)x[u] * sc[u], t);
+          l = fma((double)x[c] * sc[c], t, l);
         }
       }
       const int64_t row = row0 + threadIdx.x;
-      if (lev) lev[row] = (double)l;
+      if (lev) lev[row] = l;
       if (q) {
-        double p = (double)l / (double)r;
-        p = p > 0.0 ? (p < 1.0 ? p : 1.0) : 0.0;
+        double p = l / (double)r;
+        p = clamp01(p);
         const uint64_t qi = __double2ull_rn(p * 4611686018427387904.0);  // 2^62
         q[row] = qi;
         my_max = qi > my_max ? qi : my_max;
@@ -497,11 +573,7 @@ __global__ void __launch_bounds__(kRowThreads) k_lev_rows_tpr(const FT* A, int64
       }
     }
     if (A_out) {
-      for (int i = threadIdx.x; i < rows * r; i += kRowThreads) {
-        const int c = i % r;
-        const FT v = A[row0 * r + i];
-        A_out[row0 * r + i] = lam[c] > FT(0) ? v / lam[c] : v;
-      }
+      for (int i = threadIdx.x; i < rows * r; i += kRowThreads) A_out[row0 * r + i] = A[row0 * r + i] * lam[i % r];
     }
   }
   if (q && info) {
@@ -541,11 +613,11 @@ template int gram_rows<float>(const float*, int64_t, int, double*, cudaStream_t)
 int factor_spd(const double* G, int r, int normalize, int pivot, double rel_tol, SmallFactor* out,
                int* warn, int warn_bit, cudaStream_t st, DistInfo* zero_info) {
   if (r < 1 || r > kMaxRank) return CPA_ERR_ARG;
-  const size_t smem = sizeof(double) * (2 * r * r + 2 * r);
+  const size_t smem = sizeof(double) * (2 * r * r + 5 * r);
   static bool attr_done = false;
   if (!attr_done) {
     CPA_CUDA_TRY(cudaFuncSetAttribute(k_factor_spd, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(sizeof(double) * (2 * kMaxRank * kMaxRank + 2 * kMaxRank))));
+                                      (int)(sizeof(double) * (2 * kMaxRank * kMaxRank + 5 * kMaxRank))));
     attr_done = true;
   }
   k_factor_spd<<<1, kFactorThreads, smem, st>>>(G, r, normalize, pivot, rel_tol, out, warn, warn_bit,
@@ -560,18 +632,21 @@ int lev_rows(const FT* A, int64_t n, int r, const SmallFactor* f, double* lev, u
   if (r < 1 || r > kMaxRank) return CPA_ERR_ARG;
   if (n <= 0) return CPA_OK;
   if (n >= kManyRows) {
-    const size_t smem = sizeof(FT) * ((size_t)r * r + 2 * r + (size_t)kRowThreads * (r + 1));
+    auto bytes = [](int rr) {
+      return sizeof(double) * ((size_t)rr * rr + rr) + sizeof(FT) * ((size_t)((rr + 1) & ~1) +
+                                                                      (size_t)kRowThreads * (rr + 1));
+    };
+    const size_t smem = bytes(r);
     static bool attr = false;
     if (!attr) {
       CPA_CUDA_TRY(cudaFuncSetAttribute(k_lev_rows_tpr<FT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)(sizeof(FT) * (kMaxRank * kMaxRank + 2 * kMaxRank +
-                                                            kRowThreads * (kMaxRank + 1)))));
+                                        (int)bytes(kMaxRank)));
       attr = true;
     }
     const unsigned grid = grid_cap(ceil_div(n, kRowThreads), 8);
     k_lev_rows_tpr<FT><<<grid, kRowThreads, smem, st>>>(A, n, r, f, lev, q, info, A_out);
   } else {
-    const size_t smem = sizeof(FT) * ((size_t)r * r + 2 * r);
+    const size_t smem = sizeof(double) * ((size_t)r * r + r) + sizeof(FT) * r;
     const unsigned grid = grid_cap(ceil_div(n, kRowThreads / 32), 16);
     k_lev_rows<FT><<<grid, kRowThreads, smem, st>>>(A, n, r, f, lev, q, info, A_out);
   }

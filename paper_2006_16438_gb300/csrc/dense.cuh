@@ -8,15 +8,15 @@
 namespace cpa {
 
 // Result of factoring an r x r symmetric positive semidefinite matrix G.
-// kind 0: F holds the lower Cholesky factor L of P^T (S G S) P (row-major), the
-//         first `rank` columns only when pivoting found G singular; P is the
-//         permutation perm (identity without pivoting), S = diag(scale).
+// kind 0: F holds the inverse of the lower Cholesky factor of P^T (S G S) P
+//         (row-major, lower triangular), its leading rank x rank block only when
+//         pivoting found G singular; P is the permutation perm, S = diag(scale).
 // kind 1: F holds the pseudo-inverse of S G S.
+// kind 2: F holds the inverse of S G S.
 // With normalize = 1, scale_c = 1/sqrt(G_cc) (0 for a zero column) and lambda_c =
-// sqrt(G_cc); otherwise scale = 1, lambda = sqrt(G_cc).  gram holds S G S.
+// sqrt(G_cc); otherwise scale = 1, lambda = sqrt(G_cc).
 struct SmallFactor {
   double F[kMaxRank * kMaxRank];
-  double gram[kMaxRank * kMaxRank];
   double scale[kMaxRank];
   double lambda[kMaxRank];
   int perm[kMaxRank];

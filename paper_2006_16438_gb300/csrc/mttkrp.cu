@@ -1,17 +1,19 @@
-// KrpSamp + TnsrSamp + sampled normal equations (Section 5.2, Section 5.3).
+// KrpSamp, TnsrSamp and the sampled normal-equation products (Section 5.2, 5.3).
 //
-// 1. probe:    one thread per sample finds its fibre [lo, lo + len) in the mode-k
-//              stream through the bucket directory and a short binary search (the
-//              same kernel clears M and G).
-// 2. krp_gram: samples in tiles of 32: y_j = wgt_j * prod_t A_{m_t}(i_t, :) is formed
-//              (row gathers of the other factors), stored for step 4, and
-//              G += y_j y_j^T is accumulated per thread over upper-triangle pairs.
-// 3. scan:     pos = exclusive prefix of len (nnz of the sampled right-hand side).
-// 4. mttkrp:   the flattened list of sampled nonzeros is cut into groups of 32, one
-//              per warp at a time (so a heavy fibre is spread over many warps and a
-//              run of short fibres is resolved 32 at a time); lane c accumulates
-//              M(i_k, c) += wgt_j * x * y_j(c) with atomics, into shared memory when
-//              M fits, else straight to global memory.
+// Two kernels per update, independent of each other (both read only the samples and
+// the factors), so the update runs them as two branches of its graph:
+//
+// 1. k_krp_gram (KrpSamp + sampled Gram): samples in tiles of 32;
+//    y_j = wgt_j * prod_t A_{m_t}(i_t, :) is formed in shared memory (row gathers of
+//    the other factors) and G += y_j y_j^T is accumulated per thread over the
+//    upper-triangle pairs (tile partials in FT, added across tiles in FP64).
+// 2. k_tnsr_mttkrp (KrpSamp + TnsrSamp + sampled MTTKRP, fused): a warp takes 32
+//    consecutive samples; lane l probes the fibre of sample l through the bucket
+//    directory of the mode-k index; then for each sample with a nonempty fibre the
+//    warp forms u_j = wgt_j^2 * prod_t A_{m_t}(i_t, :) (lane c holds column c) and,
+//    for every nonzero (i_k, x) of the fibre, adds x * u_j into row i_k of M.  Chunks
+//    are taken from a counter; fibres longer than kHeavy are listed and spread over
+//    the warps of one block each by k_tnsr_heavy.  The KRP rows are never written.
 #include "mttkrp.cuh"
 
 namespace cpa {
@@ -31,32 +33,11 @@ __device__ __forceinline__ void pair_of(int p, int r, int* a, int* b) {
   *b = row + (p - start);
 }
 
-// also clears M (mz elements) and G (r*r) for the kernels that accumulate into them
-template <class VT, class FT>
-__global__ void k_probe(FibreIndex<VT> X, const uint64_t* __restrict__ idx, DevCount sbar,
-                        uint64_t* __restrict__ lo, uint32_t* __restrict__ len, FT* __restrict__ M,
-                        int64_t mz, double* __restrict__ G, int gz) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < mz;
-       i += (int64_t)gridDim.x * blockDim.x)
-    M[i] = FT(0);
-  if (blockIdx.x == 0)
-    for (int i = threadIdx.x; i < gz; i += blockDim.x) G[i] = 0.0;
-  const int64_t n = sbar.get();
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
-       j += (int64_t)gridDim.x * blockDim.x) {
-    uint64_t a, b;
-    X.probe(idx[j], &a, &b);
-    lo[j] = a;
-    len[j] = (uint32_t)(b - a);
-  }
-}
-
 template <class FT, int PMAX>
 __global__ void __launch_bounds__(kThreads) k_krp_gram(FactorPtrs F, KeyLayout L, int r,
                                                        const uint64_t* __restrict__ idx,
                                                        const double* __restrict__ wgt,
-                                                       DevCount sbar, FT* __restrict__ Y,
-                                                       double* __restrict__ G) {
+                                                       DevCount sbar, double* __restrict__ G) {
   extern __shared__ __align__(16) unsigned char krp_smem[];
   FT* tile = reinterpret_cast<FT*>(krp_smem);  // kTileRows * r
   __shared__ uint32_t rows[kTileRows][kMaxOrder];
@@ -87,7 +68,6 @@ __global__ void __launch_bounds__(kThreads) k_krp_gram(FactorPtrs F, KeyLayout L
         v = wsh[sl];
         for (int t = 0; t < L.d; ++t)
           v *= static_cast<const FT*>(F.A[L.mode[t]])[(int64_t)rows[sl][t] * r + c];
-        Y[(t0 + sl) * r + c] = v;
       }
       tile[i] = v;
     }
@@ -112,151 +92,271 @@ __global__ void __launch_bounds__(kThreads) k_krp_gram(FactorPtrs F, KeyLayout L
   }
 }
 
-// last j in [0, n) with pos[j] <= e (pos ascending, pos[0] = 0 <= e)
-__device__ __forceinline__ int64_t sample_of(const uint64_t* __restrict__ pos, int64_t n, uint64_t e) {
-  int64_t a = 0, b = n - 1;
-  while (a < b) {
-    const int64_t mid = (a + b + 1) >> 1;
-    if (pos[mid] <= e) a = mid; else b = mid - 1;
-  }
-  return a;
-}
+constexpr int kHeavy = 64;  // fibres longer than this go to the heavy list
 
-// Lane-parallel gather: a warp takes 32 consecutive sampled nonzeros; each lane
-// resolves its own (sample, fibre offset, i_k, wgt_j * x) with independent loads, then
-// the warp walks the 32 nonzeros and lane c adds coef * y_j(c) into row i_k of M.
-template <class FT, class VT, int CPL, bool kShared>
-__global__ void __launch_bounds__(kThreads) k_mttkrp(FibreIndex<VT> X, const FT* __restrict__ Y,
-                                                     const double* __restrict__ wgt,
-                                                     const uint64_t* __restrict__ lo,
-                                                     const uint64_t* __restrict__ pos, DevCount sbar,
-                                                     const uint64_t* __restrict__ d_total, int r,
-                                                     int64_t nk, FT* __restrict__ M) {
+// Light pass: warps take chunks of 32 consecutive samples from a counter.  Lane l
+// probes sample l; a fibre longer than kHeavy is appended to the heavy list
+// (processed by k_tnsr_heavy); the others are walked one sample at a time (lane c
+// holds column c of u_j) with the nonzeros loaded 32 at a time.  kPriv: every warp
+// accumulates into its own copy of M in shared memory with plain adds (lanes of a
+// warp touch distinct columns of one row), summed into M at the end; otherwise
+// atomics into M.  ctr[0] += sampled nonzeros, ctr[1] = chunk counter, ctr[2] =
+// heavy-list length.
+template <class FT, class VT, int CPL, bool kPriv>
+__global__ void __launch_bounds__(kThreads) k_tnsr_mttkrp(FibreIndex<VT> X, FactorPtrs F, KeyLayout L,
+                                                          int r, const uint64_t* __restrict__ idx,
+                                                          const double* __restrict__ wgt, DevCount sbar,
+                                                          int64_t nk, FT* __restrict__ M,
+                                                          unsigned long long* __restrict__ ctr,
+                                                          uint4* __restrict__ heavy) {
   extern __shared__ __align__(16) unsigned char mk_smem[];
-  FT* Ms = reinterpret_cast<FT*>(mk_smem);
-  if (kShared) {
-    for (int64_t i = threadIdx.x; i < nk * r; i += kThreads) Ms[i] = FT(0);
-    __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t mz = nk * r;
+  FT* Mw = kPriv ? reinterpret_cast<FT*>(mk_smem) + warp * mz : M;
+  if (kPriv) {
+    for (int64_t i = lane; i < mz; i += 32) Mw[i] = FT(0);
+    __syncwarp();
   }
   const int64_t n = sbar.get();
-  const uint64_t total = *d_total;
-  const int lane = threadIdx.x & 31;
-  const int64_t gw = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
-  for (uint64_t base = (uint64_t)gw * 32; base < total; base += (uint64_t)nwarps * 32) {
-    const uint64_t e = base + lane;
-    int64_t j = 0;
-    int32_t ik = 0;
-    FT coef = FT(0);
-    if (e < total) {
-      j = sample_of(pos, n, e);
-      const uint64_t off = lo[j] + (e - pos[j]);
-      ik = X.ik[off];
-      coef = (FT)wgt[j] * (FT)X.val[off];
+  const int64_t nchunks = (n + 31) >> 5;
+  uint64_t my_nnz = 0;
+  for (;;) {
+    unsigned long long cidx = 0;
+    if (lane == 0) cidx = atomicAdd(&ctr[1], 1ull);
+    cidx = __shfl_sync(0xffffffffu, cidx, 0);
+    if ((int64_t)cidx >= nchunks) break;
+    const int64_t base = (int64_t)cidx * 32;
+    const int64_t j = base + lane;
+    uint64_t key = 0, lo = 0, hi = 0;
+    FT w = FT(0);
+    if (j < n) {
+      key = idx[j];
+      X.probe(key, &lo, &hi);
+      w = (FT)wgt[j];
     }
-    const int nb = total - base < 32 ? (int)(total - base) : 32;
-    for (int q = 0; q < nb; ++q) {
-      const int64_t jq = __shfl_sync(0xffffffffu, j, q);
-      const int32_t iq = __shfl_sync(0xffffffffu, ik, q);
-      const FT cq = __shfl_sync(0xffffffffu, coef, q);
+    uint32_t len = (uint32_t)(hi - lo);
+    my_nnz += len;
+    if (len > kHeavy) {
+      const unsigned long long h = atomicAdd(&ctr[2], 1ull);
+      heavy[h] = make_uint4((unsigned)j, (unsigned)(lo & 0xffffffffu), (unsigned)(lo >> 32), len);
+      len = 0;
+    }
+    unsigned todo = __ballot_sync(0xffffffffu, len > 0);
+    while (todo) {
+      const int q = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const uint32_t lq = __shfl_sync(0xffffffffu, len, q);
+      const uint64_t kq = __shfl_sync(0xffffffffu, key, q);
+      const uint64_t oq = __shfl_sync(0xffffffffu, lo, q);
+      const FT wq = __shfl_sync(0xffffffffu, w, q);
+      FT u[CPL];
 #pragma unroll
-      for (int u = 0; u < CPL; ++u) {
-        const int c = lane + 32 * u;
+      for (int v = 0; v < CPL; ++v) {
+        const int c = lane + 32 * v;
+        FT z = FT(0);
         if (c < r) {
-          const FT v = cq * Y[jq * r + c];
-          if (kShared) atomicAdd(&Ms[(int64_t)iq * r + c], v);
-          else atomicAdd(&M[(int64_t)iq * r + c], v);
+          z = wq * wq;
+          for (int t = 0; t < L.d; ++t)
+            z *= static_cast<const FT*>(F.A[L.mode[t]])[(int64_t)L.get(kq, t) * r + c];
+        }
+        u[v] = z;
+      }
+      int32_t ikl = 0;
+      FT xl = FT(0);
+      if (lane < (int)lq) {  // lq <= kHeavy: at most two loads per lane
+        ikl = X.ik[oq + lane];
+        xl = (FT)X.val[oq + lane];
+      }
+      int32_t ikl2 = 0;
+      FT xl2 = FT(0);
+      if (lane + 32 < (int)lq) {
+        ikl2 = X.ik[oq + 32 + lane];
+        xl2 = (FT)X.val[oq + 32 + lane];
+      }
+      for (int q2 = 0; q2 < (int)lq; ++q2) {
+        const int32_t ik = __shfl_sync(0xffffffffu, q2 < 32 ? ikl : ikl2, q2 & 31);
+        const FT x = __shfl_sync(0xffffffffu, q2 < 32 ? xl : xl2, q2 & 31);
+#pragma unroll
+        for (int v = 0; v < CPL; ++v) {
+          const int c = lane + 32 * v;
+          if (c < r) {
+            if (kPriv) Mw[(int64_t)ik * r + c] += x * u[v];
+            else atomicAdd(&Mw[(int64_t)ik * r + c], x * u[v]);
+          }
         }
       }
     }
   }
-  if (kShared) {
+  for (int o = 16; o > 0; o >>= 1) my_nnz += __shfl_xor_sync(0xffffffffu, my_nnz, o);
+  if (lane == 0 && my_nnz) atomicAdd(&ctr[0], (unsigned long long)my_nnz);
+  if (kPriv) {
     __syncthreads();
-    for (int64_t i = threadIdx.x; i < nk * r; i += kThreads)
-      if (Ms[i] != FT(0)) atomicAdd(&M[i], Ms[i]);
+    const FT* Mb = reinterpret_cast<const FT*>(mk_smem);
+    const int nw = kThreads / 32;
+    for (int64_t i = threadIdx.x; i < mz; i += kThreads) {
+      FT t = FT(0);
+      for (int ww = 0; ww < nw; ++ww) t += Mb[ww * mz + i];
+      if (t != FT(0)) atomicAdd(&M[i], t);
+    }
   }
 }
 
-template <class FT, class VT>
-int run(const cpa_index* X, int k, const FactorPtrs& F, int r, const uint64_t* idx, const double* wgt,
-        DevCount sbar, FT* M, double* G, MttkrpBuffers& B, cudaStream_t st, cudaEvent_t* ev) {
-  const auto& mode = X->mode[k];
-  const FibreIndex<VT> fx = fibre_view<VT>(X, k);
-  const int64_t s = sbar.max;
+// Heavy pass: one block per listed fibre (block-stride); warp w takes the fibre's
+// nonzeros in groups of 32 (w, w + 8, ...), forming u_j itself.
+template <class FT, class VT, int CPL>
+__global__ void __launch_bounds__(kThreads) k_tnsr_heavy(FibreIndex<VT> X, FactorPtrs F, KeyLayout L,
+                                                         int r, const uint64_t* __restrict__ idx,
+                                                         const double* __restrict__ wgt, FT* __restrict__ M,
+                                                         const unsigned long long* __restrict__ ctr,
+                                                         const uint4* __restrict__ heavy) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t nh = (int64_t)ctr[2];
+  for (int64_t h = blockIdx.x; h < nh; h += gridDim.x) {
+    const uint4 e = heavy[h];
+    const int64_t j = e.x;
+    const uint64_t lo = (uint64_t)e.y | ((uint64_t)e.z << 32);
+    const uint32_t len = e.w;
+    const uint64_t key = idx[j];
+    const FT wq = (FT)wgt[j];
+    FT u[CPL];
+#pragma unroll
+    for (int v = 0; v < CPL; ++v) {
+      const int c = lane + 32 * v;
+      FT z = FT(0);
+      if (c < r) {
+        z = wq * wq;
+        for (int t = 0; t < L.d; ++t)
+          z *= static_cast<const FT*>(F.A[L.mode[t]])[(int64_t)L.get(key, t) * r + c];
+      }
+      u[v] = z;
+    }
+    for (uint64_t g = (uint64_t)warp * 32; g < len; g += kThreads) {
+      const int nb = len - g < 32 ? (int)(len - g) : 32;
+      int32_t ikl = 0;
+      FT xl = FT(0);
+      if (lane < nb) {
+        ikl = X.ik[lo + g + lane];
+        xl = (FT)X.val[lo + g + lane];
+      }
+      for (int q2 = 0; q2 < nb; ++q2) {
+        const int32_t ik = __shfl_sync(0xffffffffu, ikl, q2);
+        const FT x = __shfl_sync(0xffffffffu, xl, q2);
+#pragma unroll
+        for (int v = 0; v < CPL; ++v) {
+          const int c = lane + 32 * v;
+          if (c < r) atomicAdd(&M[(int64_t)ik * r + c], x * u[v]);
+        }
+      }
+    }
+  }
+}
+
+template <class FT>
+int launch_gram(const FactorPtrs& F, const KeyLayout& L, int r, const uint64_t* idx, const double* wgt,
+                DevCount sbar, double* G, cudaStream_t st) {
   const int sms = num_sms();
-  FT* Y = static_cast<FT*>(B.Y);
-  int64_t pb = ceil_div(s, kThreads);
-  k_probe<VT, FT><<<(unsigned)(pb < sms * 16 ? pb : sms * 16), kThreads, 0, st>>>(
-      fx, idx, sbar, B.lo, B.len, M, X->dims[k] * r, G, r * r);
-  if (ev && ev[0]) CPA_CUDA_TRY(record_event(ev[0], st));
   const int np = r * (r + 1) / 2;
-  int64_t tb = ceil_div(s, kTileRows);
+  const int64_t tb = ceil_div(sbar.max, (int64_t)kTileRows);
   const unsigned tgrid = (unsigned)(tb < sms * 2 ? tb : sms * 2);
   const size_t tsm = sizeof(FT) * kTileRows * r;
   if (np <= kThreads)
-    k_krp_gram<FT, 1><<<tgrid, kThreads, tsm, st>>>(F, mode.L, r, idx, wgt, sbar, Y, G);
+    k_krp_gram<FT, 1><<<tgrid, kThreads, tsm, st>>>(F, L, r, idx, wgt, sbar, G);
   else if (np <= 4 * kThreads)
-    k_krp_gram<FT, 4><<<tgrid, kThreads, tsm, st>>>(F, mode.L, r, idx, wgt, sbar, Y, G);
+    k_krp_gram<FT, 4><<<tgrid, kThreads, tsm, st>>>(F, L, r, idx, wgt, sbar, G);
   else
-    k_krp_gram<FT, 9><<<tgrid, kThreads, tsm, st>>>(F, mode.L, r, idx, wgt, sbar, Y, G);
+    k_krp_gram<FT, 9><<<tgrid, kThreads, tsm, st>>>(F, L, r, idx, wgt, sbar, G);
   CPA_LAUNCH_CHECK();
-  if (ev && ev[1]) CPA_CUDA_TRY(record_event(ev[1], st));
-  ScanExtras ex;
-  ex.end = true;  // pos[sbar] = nnz of the sampled right-hand side
-  CPA_TRY(scan_u64<uint32_t>(B.len, B.pos, sbar, false, B.total, B.scratch, st, ex));
-  if (ev && ev[2]) CPA_CUDA_TRY(record_event(ev[2], st));
+  return CPA_OK;
+}
+
+template <class FT, class VT>
+int launch_mttkrp(const cpa_index* X, int k, const FactorPtrs& F, int r, const uint64_t* idx,
+                  const double* wgt, DevCount sbar, FT* M, MttkrpBuffers& B, cudaStream_t st) {
+  const FibreIndex<VT> fx = fibre_view<VT>(X, k);
+  const KeyLayout& L = X->mode[k].L;
+  const int sms = num_sms();
   const int64_t nk = X->dims[k];
-  const bool shared = nk * r * sizeof(FT) <= 48 * 1024;
-  const size_t msm = shared ? sizeof(FT) * nk * r : 0;
-  const unsigned mgrid = (unsigned)(shared ? sms : sms * 4);
+  const size_t priv = sizeof(FT) * (size_t)nk * r * (kThreads / 32);  // warp-private copies of M
+  const bool use_priv = priv <= 160 * 1024;
+  const int64_t want = ceil_div(sbar.max, (int64_t)kThreads);  // one warp per 32 samples
+  const int64_t cap = (int64_t)sms * (use_priv ? 1 : 8);
+  const unsigned grid = (unsigned)(want < cap ? (want > 0 ? want : 1) : cap);
+  unsigned long long* ctr = reinterpret_cast<unsigned long long*>(B.ctr);
+  uint4* heavy = reinterpret_cast<uint4*>(B.heavy);
+#define CPA_MK(CPL, PRIV)                                                                         \
+  do {                                                                                            \
+    if (PRIV) {                                                                                   \
+      static bool attr = false;                                                                   \
+      if (!attr) {                                                                                \
+        CPA_CUDA_TRY(cudaFuncSetAttribute(k_tnsr_mttkrp<FT, VT, CPL, PRIV>,                       \
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024)); \
+        attr = true;                                                                              \
+      }                                                                                           \
+    }                                                                                             \
+    k_tnsr_mttkrp<FT, VT, CPL, PRIV><<<grid, kThreads, PRIV ? priv : 0, st>>>(                    \
+        fx, F, L, r, idx, wgt, sbar, nk, M, ctr, heavy);                                          \
+  } while (0)
   if (r <= 32) {
-    if (shared)
-      k_mttkrp<FT, VT, 1, true><<<mgrid, kThreads, msm, st>>>(fx, Y, wgt, B.lo, B.pos, sbar, B.total, r, nk, M);
-    else
-      k_mttkrp<FT, VT, 1, false><<<mgrid, kThreads, 0, st>>>(fx, Y, wgt, B.lo, B.pos, sbar, B.total, r, nk, M);
+    if (use_priv) CPA_MK(1, true); else CPA_MK(1, false);
   } else {
-    if (shared)
-      k_mttkrp<FT, VT, 2, true><<<mgrid, kThreads, msm, st>>>(fx, Y, wgt, B.lo, B.pos, sbar, B.total, r, nk, M);
-    else
-      k_mttkrp<FT, VT, 2, false><<<mgrid, kThreads, 0, st>>>(fx, Y, wgt, B.lo, B.pos, sbar, B.total, r, nk, M);
+    if (use_priv) CPA_MK(2, true); else CPA_MK(2, false);
   }
+#undef CPA_MK
+  CPA_LAUNCH_CHECK();
+  const unsigned hgrid = (unsigned)sms * 2;
+  if (r <= 32)
+    k_tnsr_heavy<FT, VT, 1><<<hgrid, kThreads, 0, st>>>(fx, F, L, r, idx, wgt, M, ctr, heavy);
+  else
+    k_tnsr_heavy<FT, VT, 2><<<hgrid, kThreads, 0, st>>>(fx, F, L, r, idx, wgt, M, ctr, heavy);
   CPA_LAUNCH_CHECK();
   return CPA_OK;
 }
 
 }  // namespace
 
-size_t mttkrp_buffers_bytes(int64_t s, int r, int ft_bytes) {
-  Arena a;
-  MttkrpBuffers B;
-  mttkrp_buffers_carve(a, s, r, ft_bytes, &B);
-  return a.used + 256;
-}
-
-void mttkrp_buffers_carve(Arena& a, int64_t s, int r, int ft_bytes, MttkrpBuffers* B) {
-  B->Y = a.take<char>((size_t)s * r * ft_bytes);
-  B->lo = a.take<uint64_t>(s);
-  B->len = a.take<uint32_t>(s);
-  B->pos = a.take<uint64_t>(s + 1);
-  B->total = a.take<uint64_t>(1);
-  B->scratch = a.take<char>(scan_workspace(s));
+void mttkrp_buffers_carve(Arena& a, int64_t s, MttkrpBuffers* B) {
+  B->ctr = a.take<uint64_t>(4);
+  B->total = B->ctr;
+  B->heavy = a.take<uint32_t>(4 * (size_t)(s > 0 ? s : 1));
 }
 
 template <class FT>
 int sampled_mttkrp(const cpa_index* X, int k, const FactorPtrs& F, int r, const uint64_t* idx_packed,
                    const double* wgt, DevCount sbar, FT* M, double* G, MttkrpBuffers& B,
-                   cudaStream_t st, cudaEvent_t* ev) {
+                   cudaStream_t st, cudaEvent_t* ev, const Fork* fork) {
   if (r < 1 || r > kMaxRank) return CPA_ERR_ARG;
+  CPA_CUDA_TRY(cudaMemsetAsync(M, 0, sizeof(FT) * X->dims[k] * r, st));
+  CPA_CUDA_TRY(cudaMemsetAsync(G, 0, sizeof(double) * r * r, st));
+  CPA_CUDA_TRY(cudaMemsetAsync(B.ctr, 0, 4 * sizeof(uint64_t), st));
   if (sbar.max <= 0) return CPA_OK;
-  if (X->val_dtype == CPA_F32)
-    return run<FT, float>(X, k, F, r, idx_packed, wgt, sbar, M, G, B, st, ev);
-  return run<FT, double>(X, k, F, r, idx_packed, wgt, sbar, M, G, B, st, ev);
+  const KeyLayout& L = X->mode[k].L;
+  auto mttkrp = [&](cudaStream_t s2) {
+    return X->val_dtype == CPA_F32
+               ? launch_mttkrp<FT, float>(X, k, F, r, idx_packed, wgt, sbar, M, B, s2)
+               : launch_mttkrp<FT, double>(X, k, F, r, idx_packed, wgt, sbar, M, B, s2);
+  };
+  const bool timed = ev && ev[0];
+  if (fork && fork->aux && !timed) {
+    // the Gram on the side stream, the MTTKRP on st, joined before returning
+    CPA_CUDA_TRY(cudaEventRecord(fork->ev_fork, st));
+    CPA_CUDA_TRY(cudaStreamWaitEvent(fork->aux, fork->ev_fork, 0));
+    CPA_TRY(launch_gram<FT>(F, L, r, idx_packed, wgt, sbar, G, fork->aux));
+    CPA_CUDA_TRY(cudaEventRecord(fork->ev_join, fork->aux));
+    CPA_TRY(mttkrp(st));
+    CPA_CUDA_TRY(cudaStreamWaitEvent(st, fork->ev_join, 0));
+    return CPA_OK;
+  }
+  if (timed) CPA_CUDA_TRY(record_event(ev[0], st));
+  CPA_TRY(launch_gram<FT>(F, L, r, idx_packed, wgt, sbar, G, st));
+  if (timed && ev[1]) CPA_CUDA_TRY(record_event(ev[1], st));
+  CPA_TRY(mttkrp(st));
+  return CPA_OK;
 }
 template int sampled_mttkrp<double>(const cpa_index*, int, const FactorPtrs&, int, const uint64_t*,
                                     const double*, DevCount, double*, double*, MttkrpBuffers&,
-                                    cudaStream_t, cudaEvent_t*);
+                                    cudaStream_t, cudaEvent_t*, const Fork*);
 template int sampled_mttkrp<float>(const cpa_index*, int, const FactorPtrs&, int, const uint64_t*,
                                    const double*, DevCount, float*, double*, MttkrpBuffers&,
-                                   cudaStream_t, cudaEvent_t*);
+                                   cudaStream_t, cudaEvent_t*, const Fork*);
 
 }  // namespace cpa

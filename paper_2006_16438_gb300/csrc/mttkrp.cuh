@@ -10,28 +10,33 @@ struct FactorPtrs {
   const void* A[kMaxOrder];
 };
 
-// Buffers of one sampled MTTKRP (device), sized for s samples.
+// Device buffers of one sampled MTTKRP for up to s samples.
 struct MttkrpBuffers {
-  void* Y;            // s x r (factor type): y_j = wgt_j * z_j
-  uint64_t* lo;       // s: first nonzero of the fibre of sample j in the mode-k stream
-  uint32_t* len;      // s: fibre length
-  uint64_t* pos;      // s + 1: exclusive prefix of len; pos[sbar] = nnz of the sample
-  uint64_t* total;    // 1: nnz of the sampled right-hand side
-  char* scratch;      // scan workspace for s items
+  uint64_t* ctr;     // 4: sampled nonzeros, chunk counter, heavy-list length, spare
+  uint64_t* total;   // = ctr: nnz of the sampled right-hand side
+  uint32_t* heavy;   // 4 s: (sample, fibre start lo/hi words, length) of long fibres
 };
 
-size_t mttkrp_buffers_bytes(int64_t s, int r, int ft_bytes);
-void mttkrp_buffers_carve(Arena& a, int64_t s, int r, int ft_bytes, MttkrpBuffers* B);
+void mttkrp_buffers_carve(Arena& a, int64_t s, MttkrpBuffers* B);
+
+// A side stream and two events (created without timing) with which the Gram and the
+// MTTKRP run as two branches; aux = null runs them one after the other.
+struct Fork {
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+};
 
 // G = sum_j y_j y_j^T and M = sum_j wgt_j x(:, key_j) y_j^T over the sbar samples
-// (packed keys), with y_j = wgt_j prod_t A_{m_t}(i_t, :); M and G are cleared here.
-// sbar: device count (max s).
-// ev (may be null): three timing events recorded on `st` after the probe, after
-// the KRP/Gram kernel and after the scan (i.e. before the gather-scale-accumulate).
-// FT: element type of the factors, Y and M (double: FP64 path; float: mixed).
+// (packed keys), with y_j = wgt_j prod_t A_{m_t}(i_t, :), i.e. the sampled normal
+// equations of Section 5.3; M, G and B.ctr are cleared here and *B.total receives
+// the number of sampled nonzeros.  sbar: device count (max s, the size B was carved for).
+// ev (may be null): two timing events recorded on `st` before and after the Gram
+// kernel (the branches then run one after the other on `st`).
+// FT: element type of the factors and M (double: FP64 path; float: mixed).
 template <class FT>
 int sampled_mttkrp(const cpa_index* X, int k, const FactorPtrs& F, int r,
                    const uint64_t* idx_packed, const double* wgt, DevCount sbar, FT* M,
-                   double* G, MttkrpBuffers& B, cudaStream_t st, cudaEvent_t* ev = nullptr);
+                   double* G, MttkrpBuffers& B, cudaStream_t st, cudaEvent_t* ev = nullptr,
+                   const Fork* fork = nullptr);
 
 }  // namespace cpa

@@ -223,7 +223,7 @@ __global__ void k_det_filter(SampleParams P, SampleState* S, uint32_t* __restric
     while (t + 1 < P.L.d && g >= offs[t + 1]) ++t;
     const int64_t i = g - offs[t];
     const double p = P.D.P[t][i];
-    if (p >= S->thr[t]) {
+    if (!nonneg_gt(S->thr[t], p)) {  // p >= thr
       const unsigned long long at = atomicAdd((unsigned long long*)&S->ncand[t], 1ull);
       cand[offs[t] + (int64_t)at] = (uint32_t)i;
     }
@@ -255,19 +255,28 @@ __global__ void k_det_enum(SampleParams P, SampleState* S, const uint32_t* __res
   if (threadIdx.x == 0) any = 0;
   __syncthreads();
   const int64_t offs[kMaxOrder] = {0, off1, off2, off3, off4, off5, off6, 0};
+  const bool narrow = total < (1ull << 32);  // 32-bit division (64-bit is emulated)
   for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < total;
        e += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t rest = e, packed = 0;
+    uint32_t rest32 = (uint32_t)e;
     double p = 0.0;
     for (int t = 0; t < P.L.d; ++t) {
-      const uint64_t pos = rest % (uint64_t)nc[t];
-      rest /= (uint64_t)nc[t];
+      uint64_t pos;
+      if (narrow) {
+        const uint32_t q = rest32 / (uint32_t)nc[t];
+        pos = rest32 - q * (uint32_t)nc[t];
+        rest32 = q;
+      } else {
+        pos = rest % (uint64_t)nc[t];
+        rest /= (uint64_t)nc[t];
+      }
       const uint32_t i = cand[offs[t] + (int64_t)pos];
       const double pt = P.D.P[t][i];
       p = t == 0 ? pt : __dmul_rn(p, pt);
       packed |= (uint64_t)i << P.L.off[t];
     }
-    if (p > P.tau) {
+    if (nonneg_gt(p, P.tau)) {  // p > tau
       const unsigned long long at = atomicAdd((unsigned long long*)&S->det_count, 1ull);
       if ((int64_t)at < P.det_buf) {
         det_keys[at] = packed;
@@ -290,7 +299,8 @@ struct DetSummary {
   int topk, bad;
 };
 
-__device__ DetSummary det_summary(const SampleParams& P, const SampleState* S) {
+// with_pdet = false skips the exact-sum rounding (pdet left 0).
+__device__ DetSummary det_summary(const SampleParams& P, const SampleState* S, bool with_pdet = true) {
   DetSummary r;
   r.topk = 0;
   r.bad = 0;
@@ -303,7 +313,7 @@ __device__ DetSummary det_summary(const SampleParams& P, const SampleState* S) {
   } else if (sdet > P.s) {
     r.topk = 1;  // the host runs the top-s selection
     sdet = P.s;
-  } else {
+  } else if (with_pdet) {
     r.pdet = xs_round(S->xs);
   }
   r.sdet = sdet;
@@ -328,23 +338,40 @@ __global__ void k_det_finish(SampleParams P, SampleState* S) {
   det_store(S, det_summary(P, S));
 }
 
+constexpr size_t kRndSmemMax = 96 * 1024;  // CDFs + probabilities staged up to this size
+
 // Alg. 2 with one Philox counter per (slot, attempt)
 // finish = 1: the deterministic summary is computed here (thread 0 of each block,
 // block 0 stores it); finish = 0: k_det_finish (and the host top-s step) did it.
 // Deterministic rows are entered into the combine table first (slot j < s_det),
 // then slot j < s_rnd draws its random row.
+// staged = 1: the CDFs and row probabilities of the d other modes are first copied
+// to shared memory (C_0, P_0, C_1, P_1, ...), so the searches run there.
 __global__ void __launch_bounds__(kThreads) k_rnd(SampleParams P, SampleState* S,
                                                   uint64_t* __restrict__ hkeys,
                                                   uint32_t* __restrict__ hcnt, int hbits,
                                                   const uint64_t* __restrict__ det_keys, int finish,
                                                   uint64_t* __restrict__ raw_key,
-                                                  double* __restrict__ raw_w) {
+                                                  double* __restrict__ raw_w, int staged) {
+  extern __shared__ __align__(16) uint64_t rnd_smem[];
   __shared__ int64_t sh_sdet, sh_srnd;
   __shared__ double sh_pdet;
   __shared__ int sh_topk;
+  if (staged) {
+    uint64_t* o = rnd_smem;
+    for (int t = 0; t < P.L.d; ++t) {
+      const int64_t n = P.L.n[t];
+      for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        o[i] = P.D.C[t][i];
+        o[n + i] = __double_as_longlong(P.D.P[t][i]);
+      }
+      o += 2 * n;
+    }
+  }
   if (threadIdx.x == 0) {
     if (finish) {
-      const DetSummary d = det_summary(P, S);
+      // only block 0 (which stores it) and the optional raw weights need p_det
+      const DetSummary d = det_summary(P, S, blockIdx.x == 0 || raw_w != nullptr);
       if (blockIdx.x == 0) det_store(S, d);
       sh_sdet = d.sdet;
       sh_srnd = d.srnd;
@@ -372,7 +399,12 @@ __global__ void __launch_bounds__(kThreads) k_rnd(SampleParams P, SampleState* S
     for (int a = 0; a < P.reject_cap; ++a) {
       uint64_t w0 = 0, w1 = 0, w2 = 0, w3 = 0;
       packed = 0;
+      const uint64_t* o = rnd_smem;
       for (int t = 0; t < P.L.d; ++t) {
+        const int64_t n = P.L.n[t];
+        const uint64_t* Ct = staged ? o : P.D.C[t];
+        const double* Pt = staged ? reinterpret_cast<const double*>(o + n) : P.D.P[t];
+        o += 2 * n;
         if ((t & 3) == 0) {
           w0 = (uint64_t)j;
           w1 = (uint64_t)a;
@@ -382,13 +414,13 @@ __global__ void __launch_bounds__(kThreads) k_rnd(SampleParams P, SampleState* S
         }
         const uint64_t u = (t & 3) == 0 ? w0 : (t & 3) == 1 ? w1 : (t & 3) == 2 ? w2 : w3;
         const uint64_t T = P.D.info[t]->T;
-        const int64_t i = cdf_search(P.D.C[t], P.L.n[t], __umul64hi(u, T));
-        const double pt = P.D.P[t][i];
+        const int64_t i = cdf_search(Ct, n, __umul64hi(u, T));
+        const double pt = Pt[i];
         p = t == 0 ? pt : __dmul_rn(p, pt);
         packed |= (uint64_t)i << P.L.off[t];
       }
       ++tries;
-      if (p <= P.tau) {
+      if (!nonneg_gt(p, P.tau)) {  // p <= tau
         ok = true;
         break;
       }
@@ -642,8 +674,19 @@ int skrp_lev(const SampleParams& P, SampleBuffers& B, cudaStream_t st, bool sort
       CPA_CUDA_TRY(cudaFreeAsync(ka, st));
     }
   }
-  k_rnd<<<(unsigned)ceil_div(P.s, kThreads), kThreads, 0, st>>>(P, S, B.hkeys, B.hcnt, B.hbits, B.det_keys,
-                                                                host_topk ? 0 : 1, B.raw_key, B.raw_w);
+  int64_t nsum = 0;
+  for (int t = 0; t < P.L.d; ++t) nsum += P.L.n[t];
+  const size_t rsm = sizeof(uint64_t) * 2 * (size_t)nsum;
+  const int staged = rsm <= kRndSmemMax ? 1 : 0;
+  {
+    static bool attr = false;
+    if (!attr) {
+      CPA_CUDA_TRY(cudaFuncSetAttribute(k_rnd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRndSmemMax));
+      attr = true;
+    }
+  }
+  k_rnd<<<(unsigned)ceil_div(P.s, kThreads), kThreads, staged ? rsm : 0, st>>>(
+      P, S, B.hkeys, B.hcnt, B.hbits, B.det_keys, host_topk ? 0 : 1, B.raw_key, B.raw_w, staged);
   CPA_LAUNCH_CHECK();
   const int64_t H = 1ll << B.hbits;
   if (!sorted_output) {
