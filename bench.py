@@ -41,8 +41,8 @@ WORKLOAD = "uber-shaped 183x24x1140x1717 planted counts, ~3.31M nnz, r=25, s=2^1
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
-    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -275,7 +275,8 @@ def main():
             t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             total_ms = float(t.item())
-        return dict(total_ms=total_ms, stages=stages, acc=acc, fit=fits[-1], last=last)
+        return dict(total_ms=total_ms, stages=stages, acc=acc, fit=fits[-1], last=last,
+                    step_ms={"min": min(times), "median": statistics.median(times), "max": max(times)})
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -338,7 +339,8 @@ def main():
         "sbar_per_update": stat_acc["sbar_total"] / n_updates,
         "fit": f64["fit"],
         "clocks": clk,
-        "gpu_launches": stat_acc["kernel_launches"],
+        "step_ms": f64["step_ms"],
+        "gpu_launches": f64["acc"]["kernel_launches"],
     }
     if mixed is not None:
         mv = updates * world / (mixed["total_ms"] / 1000.0)

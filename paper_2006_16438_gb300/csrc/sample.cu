@@ -74,6 +74,64 @@ __device__ __forceinline__ void xs_add(uint64_t* bins, double v) {
   if (hi) atomicAdd((unsigned long long*)&bins[limb + 2], (unsigned long long)hi);
 }
 
+// The three 32-bit chunks of v (as in xs_add) and the limb of the first one.
+__device__ __forceinline__ int xs_parts(double v, uint64_t* c0, uint64_t* c1, uint64_t* c2) {
+  const uint64_t bits = (uint64_t)__double_as_longlong(v);
+  const int bexp = (int)((bits >> 52) & 0x7ff);
+  uint64_t mant = bits & ((1ull << 52) - 1ull);
+  int shift = 0;
+  if (bexp != 0) {
+    mant |= 1ull << 52;
+    shift = bexp - 1;
+  }
+  const int off = shift & 31;
+  const uint64_t lo = mant << off;
+  *c0 = lo & 0xffffffffull;
+  *c1 = lo >> 32;
+  *c2 = off ? (mant >> (64 - off)) : 0ull;
+  return shift >> 5;
+}
+
+// Per-thread accumulation of exact-sum chunks in a three-limb window at the limb of
+// the thread's first term (terms elsewhere go straight to the bins), merged across
+// the warp before touching the shared bins: lanes with the same window reduce each
+// chunk sum in 16-bit pieces (exact), and one lane adds the result.
+struct XsWindow {
+  int base = -1;
+  uint64_t w0 = 0, w1 = 0, w2 = 0;
+  __device__ __forceinline__ void add(uint64_t* bins, double v) {
+    uint64_t c0, c1, c2;
+    const int limb = xs_parts(v, &c0, &c1, &c2);
+    if (base < 0) base = limb;
+    if (limb == base) {
+      w0 += c0;
+      w1 += c1;
+      w2 += c2;
+    } else {
+      atomicAdd((unsigned long long*)&bins[limb], (unsigned long long)c0);
+      atomicAdd((unsigned long long*)&bins[limb + 1], (unsigned long long)c1);
+      if (c2) atomicAdd((unsigned long long*)&bins[limb + 2], (unsigned long long)c2);
+    }
+  }
+  // all 32 lanes call this
+  __device__ __forceinline__ void flush(uint64_t* bins) {
+    const unsigned grp = __match_any_sync(0xffffffffu, base);
+    const int lane = threadIdx.x & 31;
+    const uint64_t wv[3] = {w0, w1, w2};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint64_t tot = 0;
+#pragma unroll
+      for (int piece = 0; piece < 4; ++piece) {
+        const unsigned part = (unsigned)((wv[k] >> (16 * piece)) & 0xffffu);
+        tot += (uint64_t)__reduce_add_sync(grp, part) << (16 * piece);
+      }
+      if (base >= 0 && lane == __ffs(grp) - 1 && tot)
+        atomicAdd((unsigned long long*)&bins[base + k], (unsigned long long)tot);
+    }
+  }
+};
+
 // bits [pos, pos + 64) of the little-endian limb array (missing bits read 0)
 __device__ __forceinline__ uint64_t bits64(const uint32_t* w, int nlimbs, int pos) {
   uint64_t v = 0;
@@ -97,12 +155,14 @@ __device__ __forceinline__ bool any_below(const uint32_t* w, int pos) {
   return rem ? (w[full] & ((1u << rem) - 1u)) != 0 : false;
 }
 
+// bins_in: kXsRep replicas of kXsLimbs bins, added limb by limb (integer, exact)
 __device__ double xs_round(const uint64_t* bins_in) {
   constexpr int kL = kXsLimbs + 2;
   uint32_t w[kL];
   uint64_t carry = 0;
   for (int i = 0; i < kXsLimbs; ++i) {
-    const uint64_t v = bins_in[i] + carry;
+    uint64_t v = carry;
+    for (int rr = 0; rr < kXsRep; ++rr) v += bins_in[rr * kXsLimbs + i];
     w[i] = (uint32_t)v;
     carry = v >> 32;
   }
@@ -182,33 +242,42 @@ __device__ __forceinline__ double row_weight(const SampleParams& P, uint64_t pac
 }
 
 // ---- kernels ----------------------------------------------------------
+// One warp: scalars cleared, alpha_t = max_i p_t(i) for every other mode t (lane t),
+// alpha_* = their product in mode order, candidate thresholds
+// thr_t = (tau alpha_t / alpha_*) (1 - 2^-40).
 __global__ void k_prepare(SampleParams P, SampleState* S) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  // S->status is sticky across passes: the caller zeroes it once
-  S->need_topk = 0;
-  S->cand_total = 0;
-  S->det_count = 0;
-  S->sdet = 0;
-  S->srnd = 0;
-  S->nsort = 0;
-  S->sbar = 0;
-  S->nuniq = 0;
-  S->attempts = 0;
-  S->pdet = 0.0;
-  for (int i = 0; i < kXsLimbs; ++i) S->xs[i] = 0;
-  double astar = 0.0;
-  double alpha[kMaxOrder];
-  for (int t = 0; t < P.L.d; ++t) {
-    S->ncand[t] = 0;
+  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+  const int t = threadIdx.x;
+  for (int i = t; i < kXsRep * kXsLimbs; i += 32) S->xs[i] = 0;
+  if (t < kMaxOrder) S->ncand[t] = 0;
+  double alpha = 1.0;
+  if (t < P.L.d) {
     const DistInfo* I = P.D.info[t];
-    alpha[t] = __ddiv_rn(__ull2double_rn(I->maxq), __ull2double_rn(I->T));
-    astar = t == 0 ? alpha[t] : __dmul_rn(astar, alpha[t]);
+    alpha = __ddiv_rn(__ull2double_rn(I->maxq), __ull2double_rn(I->T));
   }
-  S->alpha_star = astar;
-  S->no_det = !(astar > P.tau);
+  double astar = 0.0;
+  for (int u = 0; u < P.L.d; ++u) {
+    const double au = __shfl_sync(0xffffffffu, alpha, u);
+    astar = u == 0 ? au : __dmul_rn(astar, au);
+  }
   const double slack = 1.0 - 0x1p-40;
-  for (int t = 0; t < P.L.d; ++t)
-    S->thr[t] = __dmul_rn(__ddiv_rn(__dmul_rn(P.tau, alpha[t]), astar), slack);
+  if (t < P.L.d) S->thr[t] = __dmul_rn(__ddiv_rn(__dmul_rn(P.tau, alpha), astar), slack);
+  if (t == 0) {
+    // S->status is sticky across passes: the caller zeroes it once
+    S->need_topk = 0;
+    S->cand_total = 0;
+    S->det_count = 0;
+    S->sdet = 0;
+    S->srnd = 0;
+    S->nsort = 0;
+    S->sbar = 0;
+    S->nuniq = 0;
+    S->attempts = 0;
+    S->slot_ctr = 0;
+    S->pdet = 0.0;
+    S->alpha_star = astar;
+    S->no_det = !(pos_finite(astar) && nonneg_gt(astar, P.tau));
+  }
 }
 
 // candidates of every other mode: p_t(i) >= thr_t (unordered)
@@ -256,6 +325,7 @@ __global__ void k_det_enum(SampleParams P, SampleState* S, const uint32_t* __res
   __syncthreads();
   const int64_t offs[kMaxOrder] = {0, off1, off2, off3, off4, off5, off6, 0};
   const bool narrow = total < (1ull << 32);  // 32-bit division (64-bit is emulated)
+  XsWindow win;
   for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < total;
        e += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t rest = e, packed = 0;
@@ -282,14 +352,17 @@ __global__ void k_det_enum(SampleParams P, SampleState* S, const uint32_t* __res
         det_keys[at] = packed;
         det_p[at] = p;
       }
-      xs_add(bins, p);
+      win.add(bins, p);
       any = 1;
     }
   }
+  win.flush(bins);
   __syncthreads();
-  if (any)
+  if (any) {
+    uint64_t* rep = S->xs + (blockIdx.x % kXsRep) * kXsLimbs;
     for (int i = threadIdx.x; i < kXsLimbs; i += blockDim.x)
-      if (bins[i]) atomicAdd((unsigned long long*)&S->xs[i], (unsigned long long)bins[i]);
+      if (bins[i]) atomicAdd((unsigned long long*)&rep[i], (unsigned long long)bins[i]);
+  }
 }
 
 // s_det, s_rnd and p_det once the deterministic enumeration is done
@@ -339,24 +412,31 @@ __global__ void k_det_finish(SampleParams P, SampleState* S) {
 }
 
 constexpr size_t kRndSmemMax = 96 * 1024;  // CDFs + probabilities staged up to this size
+constexpr int kGuideBits = 9;              // guide-table buckets per staged CDF
+constexpr int kGuide = 1 << kGuideBits;
 
 // Alg. 2 with one Philox counter per (slot, attempt)
 // finish = 1: the deterministic summary is computed here (thread 0 of each block,
 // block 0 stores it); finish = 0: k_det_finish (and the host top-s step) did it.
-// Deterministic rows are entered into the combine table first (slot j < s_det),
-// then slot j < s_rnd draws its random row.
+// Slot j < s_rnd draws its random row, stored in rkeys[j]; k_table_insert then
+// enters the deterministic and random rows into the combine table.
 // staged = 1: the CDFs and row probabilities of the d other modes are first copied
 // to shared memory (C_0, P_0, C_1, P_1, ...), so the searches run there.
 __global__ void __launch_bounds__(kThreads) k_rnd(SampleParams P, SampleState* S,
-                                                  uint64_t* __restrict__ hkeys,
-                                                  uint32_t* __restrict__ hcnt, int hbits,
-                                                  const uint64_t* __restrict__ det_keys, int finish,
+                                                  uint64_t* __restrict__ rkeys, int finish,
                                                   uint64_t* __restrict__ raw_key,
-                                                  double* __restrict__ raw_w, int staged) {
+                                                  double* __restrict__ raw_w, int staged,
+                                                  int64_t nsum_smem) {
   extern __shared__ __align__(16) uint64_t rnd_smem[];
   __shared__ int64_t sh_sdet, sh_srnd;
   __shared__ double sh_pdet;
   __shared__ int sh_topk;
+  // guide[t][b] (b <= kGuide) = first index i with C_t[i] > mulhi(b << (64 - kGuideBits), T_t),
+  // kGuide buckets by the top bits of the draw u; the answer for u lies in
+  // [guide[b], guide[b + 1]] with b = u >> (64 - kGuideBits).
+  uint32_t* guide = reinterpret_cast<uint32_t*>(rnd_smem + 2 * (staged ? nsum_smem : 0));
+  __shared__ int sh_span;  // widest guide bucket over the staged CDFs
+  if (threadIdx.x == 0) sh_span = 1;
   if (staged) {
     uint64_t* o = rnd_smem;
     for (int t = 0; t < P.L.d; ++t) {
@@ -366,6 +446,29 @@ __global__ void __launch_bounds__(kThreads) k_rnd(SampleParams P, SampleState* S
         o[n + i] = __double_as_longlong(P.D.P[t][i]);
       }
       o += 2 * n;
+    }
+    if (P.L.d <= 4) {
+      __syncthreads();
+      const uint64_t* c = rnd_smem;
+      for (int t = 0; t < P.L.d; ++t) {
+        const int64_t n = P.L.n[t];
+        const uint64_t T = P.D.info[t]->T;
+        for (int b = threadIdx.x; b <= kGuide; b += blockDim.x) {
+          uint32_t g = (uint32_t)(n - 1);
+          if (b < kGuide) g = (uint32_t)cdf_search(c, n, __umul64hi((uint64_t)b << (64 - kGuideBits), T));
+          guide[t * (kGuide + 1) + b] = g;
+        }
+        c += 2 * n;
+      }
+      __syncthreads();
+      int span = 1;
+      for (int t = 0; t < P.L.d; ++t)
+        for (int b = threadIdx.x; b < kGuide; b += blockDim.x) {
+          const int w = (int)(guide[t * (kGuide + 1) + b + 1] - guide[t * (kGuide + 1) + b]) + 1;
+          span = w > span ? w : span;
+        }
+      span = (int)__reduce_max_sync(0xffffffffu, (unsigned)span);
+      if ((threadIdx.x & 31) == 0) atomicMax(&sh_span, span);
     }
   }
   if (threadIdx.x == 0) {
@@ -387,18 +490,91 @@ __global__ void __launch_bounds__(kThreads) k_rnd(SampleParams P, SampleState* S
   __syncthreads();
   const int64_t srnd = sh_srnd;
   const double pdet = sh_pdet;
-  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (!sh_topk && j < sh_sdet && !table_add(hkeys, hcnt, hbits, det_keys[j]))
-    set_status(&S->status, CPA_ERR_UNSUPPORTED);
   const uint64_t iter = P.iter_ptr ? *P.iter_ptr : P.iter;
   uint64_t tries = 0;
-  if (j < srnd) {
+  // Random slots come from a queue: a lane whose slot is accepted (or gives up)
+  // takes the next unclaimed slot, so the lanes of a warp stay busy whatever the
+  // number of attempts of each slot.  Attempt a of slot j always uses the Philox
+  // counter (j, a, ...), so the draws do not depend on the schedule.
+  const int lane = threadIdx.x & 31;
+  const bool narrow = P.L.d <= 4;
+  const uint64_t* Cb[4];
+  const double* Pb[4];
+  const uint32_t* Gb[4];
+  uint64_t Tb[4];
+  int steps = 0;  // bisection steps that always suffice (whole CDF, or one guide bucket)
+  if (narrow) {
+    const uint64_t* o = rnd_smem;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const bool on = t < P.L.d;
+      const int64_t n = on ? P.L.n[t] : 1;
+      Cb[t] = on ? (staged ? o : P.D.C[t]) : nullptr;
+      Pb[t] = on ? (staged ? reinterpret_cast<const double*>(o + n) : P.D.P[t]) : nullptr;
+      Gb[t] = staged ? guide + t * (kGuide + 1) : nullptr;
+      Tb[t] = on ? P.D.info[t]->T : 0;
+      if (on) o += 2 * n;
+      const int64_t span = staged ? (int64_t)sh_span : n;
+      int lg = 0;
+      while ((1ll << lg) < span) ++lg;
+      steps = lg > steps ? lg : steps;
+    }
+  }
+  int64_t jj = -1;  // current slot (-1: take one; >= srnd: done)
+  int a = 0;
+  for (;;) {
+    const unsigned want = __ballot_sync(0xffffffffu, jj < 0);
+    if (want) {
+      unsigned long long base = 0;
+      if (lane == __ffs(want) - 1)
+        base = atomicAdd((unsigned long long*)&S->slot_ctr, (unsigned long long)__popc(want));
+      base = __shfl_sync(0xffffffffu, base, __ffs(want) - 1);
+      if (jj < 0) {
+        jj = (int64_t)base + __popc(want & ((1u << lane) - 1u));
+        a = 0;
+      }
+    }
+    const bool active = jj < srnd;
+    if (!__any_sync(0xffffffffu, active)) break;
+    if (!active) continue;
     uint64_t packed = 0;
     double p = 0.0;
-    bool ok = false;
-    for (int a = 0; a < P.reject_cap; ++a) {
+    if (narrow) {
+      uint64_t w[4] = {(uint64_t)jj, (uint64_t)a, (uint64_t)(uint32_t)P.mode_k | kDomainSample, iter};
+      Philox4x64::block(w[0], w[1], w[2], w[3], P.seed, 0ull);
+      uint32_t lo[4], hi[4];
+      uint64_t tg[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        tg[t] = __umul64hi(w[t], Tb[t]);
+        if (staged) {
+          const uint32_t b = (uint32_t)(w[t] >> (64 - kGuideBits));
+          lo[t] = t < P.L.d ? Gb[t][b] : 0u;
+          hi[t] = t < P.L.d ? Gb[t][b + 1] : 0u;
+        } else {
+          lo[t] = 0;
+          hi[t] = t < P.L.d ? (uint32_t)(P.L.n[t] - 1) : 0u;
+        }
+      }
+      for (int it = 0; it < steps; ++it) {  // first index with C > target, as cdf_search
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          if (lo[t] < hi[t]) {
+            const uint32_t mid = lo[t] + ((hi[t] - lo[t]) >> 1);
+            if (Cb[t][mid] > tg[t]) hi[t] = mid; else lo[t] = mid + 1;
+          }
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        if (t < P.L.d) {
+          const double pt = Pb[t][lo[t]];
+          p = t == 0 ? pt : __dmul_rn(p, pt);
+          packed |= (uint64_t)lo[t] << P.L.off[t];
+        }
+      }
+    } else {
       uint64_t w0 = 0, w1 = 0, w2 = 0, w3 = 0;
-      packed = 0;
       const uint64_t* o = rnd_smem;
       for (int t = 0; t < P.L.d; ++t) {
         const int64_t n = P.L.n[t];
@@ -406,7 +582,7 @@ __global__ void __launch_bounds__(kThreads) k_rnd(SampleParams P, SampleState* S
         const double* Pt = staged ? reinterpret_cast<const double*>(o + n) : P.D.P[t];
         o += 2 * n;
         if ((t & 3) == 0) {
-          w0 = (uint64_t)j;
+          w0 = (uint64_t)jj;
           w1 = (uint64_t)a;
           w2 = (uint64_t)(uint32_t)P.mode_k | ((uint64_t)(t >> 2) << 16) | kDomainSample;
           w3 = iter;
@@ -419,57 +595,102 @@ __global__ void __launch_bounds__(kThreads) k_rnd(SampleParams P, SampleState* S
         p = t == 0 ? pt : __dmul_rn(p, pt);
         packed |= (uint64_t)i << P.L.off[t];
       }
-      ++tries;
-      if (!nonneg_gt(p, P.tau)) {  // p <= tau
-        ok = true;
-        break;
-      }
     }
-    if (!ok) set_status(&S->status, CPA_ERR_REJECT_LIMIT);
-    if (!table_add(hkeys, hcnt, hbits, (1ull << P.L.total_bits) | packed))
-      set_status(&S->status, CPA_ERR_UNSUPPORTED);
-    if (raw_key) raw_key[j] = P.L.linear(packed);
-    if (raw_w)
-      raw_w[j] = __dsqrt_rn(__ddiv_rn(__dsub_rn(1.0, pdet), __dmul_rn(p, __ll2double_rn(srnd))));
+    ++tries;
+    ++a;
+    const bool ok = !nonneg_gt(p, P.tau);  // p <= tau
+    if (ok || a >= P.reject_cap) {
+      if (!ok) set_status(&S->status, CPA_ERR_REJECT_LIMIT);
+      rkeys[jj] = packed;  // entered into the combine table by k_table_insert
+      if (raw_key) raw_key[jj] = P.L.linear(packed);
+      if (raw_w)
+        raw_w[jj] = __dsqrt_rn(__ddiv_rn(__dsub_rn(1.0, pdet), __dmul_rn(p, __ll2double_rn(srnd))));
+      jj = -1;
+    }
   }
   for (int o = 16; o > 0; o >>= 1) tries += __shfl_xor_sync(0xffffffffu, tries, o);
   if ((threadIdx.x & 31) == 0 && tries)
     atomicAdd((unsigned long long*)&S->attempts, (unsigned long long)tries);
 }
 
-// occupied table slots -> output rows, unordered (warp-aggregated append)
-__global__ void k_table_compact(SampleParams P, SampleState* S, uint64_t* __restrict__ hkeys,
-                                uint32_t* __restrict__ hcnt, int hbits,
-                                uint64_t* __restrict__ idx_packed, uint32_t* __restrict__ cnt,
-                                double* __restrict__ wgt) {
+// CombineRepeats input: the s_det deterministic keys (unless the top-s path entered
+// them) and the s_rnd random keys, the latter with the flag bit, into the table.
+__global__ void k_table_insert(SampleParams P, SampleState* S, uint64_t* __restrict__ hkeys,
+                               uint32_t* __restrict__ hcnt, int hbits,
+                               const uint64_t* __restrict__ det_keys,
+                               const uint64_t* __restrict__ rkeys) {
+  const int64_t sdet = S->need_topk ? 0 : S->sdet, srnd = S->srnd;
+  const uint64_t flag = 1ull << P.L.total_bits;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < sdet + srnd;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t key = g < sdet ? det_keys[g] : (flag | rkeys[g - sdet]);
+    if (!table_add(hkeys, hcnt, hbits, key)) set_status(&S->status, CPA_ERR_UNSUPPORTED);
+  }
+}
+
+// occupied table slots -> output rows, unordered; each block takes kCompactPer
+// consecutive slots per thread and claims its output range with one atomic
+constexpr int kCompactPer = 4;
+__global__ void __launch_bounds__(kThreads) k_table_compact(SampleParams P, SampleState* S,
+                                                            uint64_t* __restrict__ hkeys,
+                                                            uint32_t* __restrict__ hcnt, int hbits,
+                                                            uint64_t* __restrict__ idx_packed,
+                                                            uint32_t* __restrict__ cnt,
+                                                            double* __restrict__ wgt) {
+  __shared__ unsigned wsum[kThreads / 32];
+  __shared__ unsigned long long bbase;
   const int64_t H = 1ll << hbits;
   const int64_t srnd = S->srnd;
   const double one_minus_pdet = __dsub_rn(1.0, S->pdet);
   const uint64_t flag_bit = 1ull << P.L.total_bits;
-  const int lane = threadIdx.x & 31;
-  for (int64_t h0 = blockIdx.x * (int64_t)blockDim.x; h0 < H; h0 += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t h = h0 + threadIdx.x;
-    const uint64_t v = h < H ? hkeys[h] : kEmptyKey;
-    const bool occ = v != kEmptyKey;
-    const unsigned bal = __ballot_sync(0xffffffffu, occ);
-    unsigned long long base = 0;
-    if (lane == 0 && bal) base = atomicAdd((unsigned long long*)&S->sbar, (unsigned long long)__popc(bal));
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (occ) {
-      const int64_t u = (int64_t)base + __popc(bal & ((1u << lane) - 1u));
-      const uint64_t packed = v & (flag_bit - 1ull);
-      const bool det = !(v & flag_bit);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t span = (int64_t)kThreads * kCompactPer;
+  for (int64_t b0 = blockIdx.x * span; b0 < H; b0 += (int64_t)gridDim.x * span) {
+    uint64_t v[kCompactPer];
+    unsigned mine = 0;
+#pragma unroll
+    for (int u = 0; u < kCompactPer; ++u) {
+      const int64_t h = b0 + (int64_t)u * kThreads + threadIdx.x;
+      v[u] = h < H ? hkeys[h] : kEmptyKey;
+      mine += v[u] != kEmptyKey;
+    }
+    // block-exclusive prefix of the per-thread counts
+    unsigned incl = mine;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned tot = 0;
+      for (int w = 0; w < kThreads / 32; ++w) {
+        const unsigned c = wsum[w];
+        wsum[w] = tot;
+        tot += c;
+      }
+      bbase = tot ? atomicAdd((unsigned long long*)&S->sbar, (unsigned long long)tot) : 0ull;
+    }
+    __syncthreads();
+    int64_t u_out = (int64_t)bbase + wsum[warp] + (incl - mine);
+#pragma unroll
+    for (int u = 0; u < kCompactPer; ++u) {
+      if (v[u] == kEmptyKey) continue;
+      const int64_t h = b0 + (int64_t)u * kThreads + threadIdx.x;
+      const uint64_t packed = v[u] & (flag_bit - 1ull);
+      const bool det = !(v[u] & flag_bit);
       const uint32_t c = det ? 1u : hcnt[h];
-      idx_packed[u] = packed;
-      cnt[u] = c;
-      wgt[u] = row_weight(P, packed, det, c, one_minus_pdet, srnd);
+      idx_packed[u_out] = packed;
+      cnt[u_out] = c;
+      wgt[u_out] = row_weight(P, packed, det, c, one_minus_pdet, srnd);
       hkeys[h] = kEmptyKey;  // leave the table empty for the next pass
       hcnt[h] = 0;
+      ++u_out;
     }
+    __syncthreads();  // wsum and bbase are reused by the next span
   }
 }
 
-// occupied table slots -> flagged keys (unordered), for the sorted output
 __global__ void k_table_collect(SampleState* S, const uint64_t* __restrict__ hkeys, int hbits,
                                 uint64_t* __restrict__ out) {
   const int64_t H = 1ll << hbits;
@@ -528,8 +749,9 @@ __global__ void k_topk_take(SampleParams P, SampleState* S, const uint64_t* __re
     xs_add(bins, key_prob(P, packed));
   }
   __syncthreads();
+  uint64_t* rep = S->xs + (blockIdx.x % kXsRep) * kXsLimbs;
   for (int i = threadIdx.x; i < kXsLimbs; i += blockDim.x)
-    if (bins[i]) atomicAdd((unsigned long long*)&S->xs[i], (unsigned long long)bins[i]);
+    if (bins[i]) atomicAdd((unsigned long long*)&rep[i], (unsigned long long)bins[i]);
 }
 
 __global__ void k_topk_finish(SampleState* S) {
@@ -537,7 +759,7 @@ __global__ void k_topk_finish(SampleState* S) {
 }
 
 __global__ void k_zero_bins(SampleState* S) {
-  if (threadIdx.x < kXsLimbs) S->xs[threadIdx.x] = 0;
+  for (int i = threadIdx.x; i < kXsRep * kXsLimbs; i += blockDim.x) S->xs[i] = 0;
 }
 
 inline unsigned blocks_for(int64_t n);
@@ -676,8 +898,8 @@ int skrp_lev(const SampleParams& P, SampleBuffers& B, cudaStream_t st, bool sort
   }
   int64_t nsum = 0;
   for (int t = 0; t < P.L.d; ++t) nsum += P.L.n[t];
-  const size_t rsm = sizeof(uint64_t) * 2 * (size_t)nsum;
-  const int staged = rsm <= kRndSmemMax ? 1 : 0;
+  const size_t rsm = sizeof(uint64_t) * 2 * (size_t)nsum + sizeof(uint32_t) * 4 * (kGuide + 1);
+  const int staged = rsm <= kRndSmemMax && nsum < (1ll << 31) ? 1 : 0;
   {
     static bool attr = false;
     if (!attr) {
@@ -685,13 +907,19 @@ int skrp_lev(const SampleParams& P, SampleBuffers& B, cudaStream_t st, bool sort
       attr = true;
     }
   }
-  k_rnd<<<(unsigned)ceil_div(P.s, kThreads), kThreads, staged ? rsm : 0, st>>>(
-      P, S, B.hkeys, B.hcnt, B.hbits, B.det_keys, host_topk ? 0 : 1, B.raw_key, B.raw_w, staged);
+  // a few warps per SM: the random slots come from a queue, and a warp's last slots
+  // (one sequence of attempts each) set its length
+  const int64_t rblocks = ceil_div(P.s, kThreads);
+  const int64_t rcap = (int64_t)num_sms() * 2;
+  k_rnd<<<(unsigned)(rblocks < rcap ? rblocks : rcap), kThreads, staged ? rsm : 0, st>>>(
+      P, S, B.sortA, host_topk ? 0 : 1, B.raw_key, B.raw_w, staged, nsum);
+  CPA_LAUNCH_CHECK();
+  k_table_insert<<<blocks_for(2 * P.s), kThreads, 0, st>>>(P, S, B.hkeys, B.hcnt, B.hbits, B.det_keys, B.sortA);
   CPA_LAUNCH_CHECK();
   const int64_t H = 1ll << B.hbits;
   if (!sorted_output) {
-    k_table_compact<<<blocks_for(H), kThreads, 0, st>>>(P, S, B.hkeys, B.hcnt, B.hbits, B.idx_packed,
-                                                        B.cnt, B.wgt);
+    k_table_compact<<<blocks_for(ceil_div(H, kCompactPer)), kThreads, 0, st>>>(P, S, B.hkeys, B.hcnt, B.hbits,
+                                                                              B.idx_packed, B.cnt, B.wgt);
     CPA_LAUNCH_CHECK();
     return CPA_OK;
   }

@@ -7,6 +7,7 @@
 namespace cpa {
 
 constexpr int kXsLimbs = 36;  // exact-sum accumulator: 36 x 32 bits from 2^-1074 up
+constexpr int kXsRep = 8;     // replicas of the accumulator (blocks spread their atomics)
 
 // Device scalars of one sampling pass.
 struct SampleState {
@@ -23,10 +24,11 @@ struct SampleState {
   int64_t sbar;         // rows after combining
   int64_t nuniq;        // distinct keys in the sorted buffer
   uint64_t attempts;
+  uint64_t slot_ctr;    // next random slot to hand out (work queue of the draws)
   double pdet;
   double alpha_star;
   double thr[kMaxOrder];
-  uint64_t xs[kXsLimbs];  // exact-sum bins of p_det
+  uint64_t xs[kXsRep * kXsLimbs];  // exact-sum bins of p_det; the sum is over the replicas
 };
 
 // Per-mode distributions of the d other modes (device pointers): the inclusive
@@ -61,7 +63,7 @@ struct SampleBuffers {
   int64_t cand_off[kMaxOrder];
   uint64_t* det_keys;   // det_cap packed keys
   double* det_p;        // det_cap probabilities
-  uint64_t* sortA;      // s
+  uint64_t* sortA;      // s: per-slot random keys of the draws, then the sort input
   uint64_t* sortB;      // s
   uint64_t* hkeys;      // 2^hbits combine-table keys
   uint32_t* hcnt;       // 2^hbits repeat counts
