@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision series")
+    p.add_argument("--no-equal-fit", action="store_true", help="skip the equal-fit comparison")
+    p.add_argument("--equal-fit-epochs", type=int, default=30)
     p.add_argument("--cpu-sample-updates", type=int, default=4,
                    help="mode updates the CPU baseline times (bounded sample)")
     return p.parse_args()
@@ -113,6 +115,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x, world, device):
+    """The largest value of x over the ranks (the job's time is the slowest rank's)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(updates_per_rank, world, max_ms):
+    """Whole-job mode updates per second: the updates of all ranks over the slowest
+    rank's time."""
+    return updates_per_rank * world / (max_ms / 1000.0)
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -152,6 +170,21 @@ FP64_PEAK_TFLOPS = SMS * 2 * 2 * SM_MAX_GHZ / 1000.0
 FP32_PEAK_TFLOPS = SMS * 128 * 2 * SM_MAX_GHZ / 1000.0
 
 STAGES = ["sample", "krp_gram", "mttkrp", "solve", "leverage", "fit"]
+
+
+def captured_traffic(kernel, source):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary
+    (profiles/traffic.json), or None when the kernel's source changed since."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)[kernel]
+        with open(os.path.join(ROOT, source), "rb") as f:
+            if hashlib.sha1(f.read()).hexdigest() != rec["source_sha1"]:
+                return None
+        return rec["dram_bytes_per_launch"]
+    except Exception:
+        return None
 WHOLE = 8
 
 
@@ -270,11 +303,7 @@ def main():
                 acc["kernel_launches"] = None
             fits.append(res.fit)
             last = st
-        total_ms = sum(times)
-        if world > 1:
-            t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = max_over_ranks(sum(times), world, "cuda")
         return dict(total_ms=total_ms, stages=stages, acc=acc, fit=fits[-1], last=last,
                     step_ms={"min": min(times), "median": statistics.median(times), "max": max(times)})
 
@@ -288,7 +317,7 @@ def main():
         mixed = series(cpa.binding.MIXED, 0)
         mixedp = series(cpa.binding.MIXED, 1)
     updates = args.steps * ETA * len(coo.dims)
-    value = updates * world / (f64["total_ms"] / 1000.0)
+    value = job_throughput(updates, world, f64["total_ms"])
     peaks, peak_src = load_peaks()
     n_updates = updates
     stages, stat_acc, last_stats = f64p["stages"], f64p["acc"], f64["last"]
@@ -312,7 +341,9 @@ def main():
         pk = FP64_PEAK_TFLOPS if b_f == 8 else FP32_PEAK_TFLOPS
         kg = {"bound": "alu", "kernel": f"k_krp_gram (sampled KRP rows + sampled Gram, {'FP64' if b_f == 8 else 'FP32'})",
               "achieved": kg_tf, "peak": pk, "unit": "TFLOP/s", "frac": (kg_tf / pk) if kg_tf else None,
-              "traffic": None,
+              "traffic": captured_traffic("k_krp_gram<double,4>", "paper_2006_16438_gb300/csrc/mttkrp.cu")
+              if b_f == 8 else None,
+              "traffic_unit": "DRAM bytes per launch (ncu, profiles/traffic.json)",
               "peak_source": f"derived: 152 SMs x {2 if b_f == 8 else 128} {'FP64' if b_f == 8 else 'FP32'} "
                              "FMA/clk x 2 flops x 2.07 GHz",
               "flops_per_update": kg_flops / n_updates, "ms_per_update": kg_ms / n_updates}
@@ -351,6 +382,8 @@ def main():
             "stages_ms_per_update": {nm: float(mixedp["stages"][i] / n_updates) for i, nm in enumerate(STAGES)},
             "krp_gram": kg32, "mttkrp_hbm": mk32,
             "note": "same init and epochs; FP32 factors/Grams/products, FP64 factorisations"}
+    if mixed is not None and not args.no_equal_fit:
+        line["mixed_precision"]["equal_fit"] = equal_fit(cpa, index, init, seed, stream, args.equal_fit_epochs)
     if rank == 0 and not args.no_e2e:
         line["e2e"] = e2e(cpa, coo, init, args)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
@@ -360,6 +393,58 @@ def main():
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def equal_fit(cpa, index, init, seed, stream, epochs):
+    """Mixed precision against FP64 at equal fit: FP64 runs `epochs` epochs from the
+    initial factors; the target is its final fit minus 1e-4; both paths are then timed
+    (CUDA events, epoch by epoch) until they first reach the target, mixed precision
+    for at most twice as many epochs."""
+    import torch
+    s, tau = SAMPLES, 2.0 ** -TAU_EXP
+
+    def run(precision, max_epochs, target=None):
+        fs = [torch.from_numpy(a).cuda() for a in init]
+        lam = torch.empty(RANK, dtype=torch.float64, device="cuda")
+        fitd = torch.empty(1, dtype=torch.float64, device="cuda")
+        fits, ms = [], []
+        for ep in range(max_epochs):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = cpa.cp_arls_lev(index, None, rank=RANK, samples=s, tau=tau, iters=ETA, seed=seed,
+                                  iter_offset=ETA * ep, out=(fs, lam, fitd), precision=precision)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            fits.append(res.fit)
+            ms.append(e0.elapsed_time(e1))
+            if target is not None and res.fit >= target:
+                break
+        return fits, ms
+
+    f64_fits, f64_ms = run(cpa.binding.FP64, epochs)
+    target = f64_fits[-1] - 1e-4
+    fix_fits, fix_ms = run(cpa.binding.MIXED, epochs)  # same number of epochs
+    mx_fits, mx_ms = run(cpa.binding.MIXED, 2 * epochs, target)
+
+    def reach(fits, ms):
+        for i, f in enumerate(fits):
+            if f >= target:
+                return i + 1, sum(ms[:i + 1])
+        return None, None
+
+    e64, t64 = reach(f64_fits, f64_ms)
+    emx, tmx = reach(mx_fits, mx_ms)
+    return {"same_epochs": {"epochs": epochs, "fp64_fit": f64_fits[-1], "mixed_fit": fix_fits[-1],
+                            "fit_diff": fix_fits[-1] - f64_fits[-1],
+                            "fp64_ms": sum(f64_ms), "mixed_ms": sum(fix_ms),
+                            "throughput_ratio": sum(f64_ms) / sum(fix_ms)},
+            "target_fit": target, "fp64_final_fit": f64_fits[-1], "mixed_best_fit": max(mx_fits),
+            "fp64_epochs": e64, "fp64_ms": t64, "mixed_epochs": emx, "mixed_ms": tmx,
+            "speedup_at_equal_fit": (t64 / tmx) if (t64 and tmx) else None,
+            "note": f"target = FP64 fit after {epochs} epochs - 1e-4; epochs of {ETA} outer iterations; "
+                    "the randomized fits fluctuate by about 1e-4 near convergence, so the epoch at which a "
+                    "path first reaches the target is noisy"}
 
 
 def e2e(cpa, coo, init, args):
