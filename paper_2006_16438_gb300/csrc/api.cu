@@ -235,6 +235,8 @@ __global__ void k_run_init(double* lam, double* fitd, uint64_t* it, uint64_t it0
   if (threadIdx.x == 0) *it = it0;
 }
 
+constexpr int kEpochGraphMax = 256;  // longest fixed-length call run as one graph
+
 struct Plan {
   // key
   int r = 0, D = 0, reject_cap = 0, profile = 0, prec = CPA_FP64, ftb = 8;
@@ -264,6 +266,10 @@ struct Plan {
   cudaGraphExec_t init_exec = nullptr;  // initial leverage distributions
   cudaGraphExec_t fit_exec = nullptr;   // exact fit
   int64_t k_iter = 0, k_init = 0, k_fit = 0;  // kernel nodes of each graph
+  cudaGraph_t g_iter = nullptr, g_init = nullptr, g_fit = nullptr;  // kept to compose the epoch
+  cudaGraphExec_t epoch_exec = nullptr;  // init + epoch_iters iterations + fit, one launch
+  int epoch_iters = -1;
+  int64_t k_epoch = 0;
   cudaStream_t cap_stream = nullptr;
   Profiler gprof;  // event nodes captured into the graph (profile = 1)
 
@@ -402,7 +408,7 @@ struct Plan {
   // captured) and launched on the caller's stream.  *nk receives the number of
   // kernel nodes of the graph.
   template <class Fn>
-  int capture_graph(Fn&& fn, cudaGraphExec_t* out, int64_t* nk) {
+  int capture_graph(Fn&& fn, cudaGraphExec_t* out, int64_t* nk, cudaGraph_t* keep = nullptr) {
     cudaGraph_t g = nullptr;
     if (!cap_stream) CPA_CUDA_TRY(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
     CPA_CUDA_TRY(cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -424,7 +430,7 @@ struct Plan {
     }
     *nk = kernels;
     const cudaError_t ei = cudaGraphInstantiate(out, g, 0);
-    cudaGraphDestroy(g);
+    if (keep) *keep = g; else cudaGraphDestroy(g);
     if (ei != cudaSuccess) {
       *out = nullptr;
       return CPA_ERR_CUDA;
@@ -442,7 +448,7 @@ struct Plan {
           gprof.st = cs;
           return enqueue_iteration(X, gprof, cs);
         },
-        &exec, &k_iter);
+        &exec, &k_iter, &g_iter);
   }
 
   // Leverage distributions of the initial factors (Alg. 3 starts from l(A_k)/r).
@@ -507,7 +513,44 @@ struct Plan {
     return CPA_OK;
   }
 
+  // One graph for a whole fixed-length call: the initial leverage, `iters` replays of
+  // the outer iteration and the fit, as child graphs in a chain.  A single launch
+  // per call leaves the GPU queue full whatever the host does meanwhile.
+  int build_epoch(int iters, bool with_fit) {
+    if (epoch_exec && epoch_iters == iters) return CPA_OK;
+    if (epoch_exec) {
+      cudaGraphExecDestroy(epoch_exec);
+      epoch_exec = nullptr;
+    }
+    cudaGraph_t eg = nullptr;
+    CPA_CUDA_TRY(cudaGraphCreate(&eg, 0));
+    cudaGraphNode_t prev = nullptr, node = nullptr;
+    int rc = CPA_OK;
+    auto add = [&](cudaGraph_t child) {
+      if (rc < 0) return;
+      if (cudaGraphAddChildGraphNode(&node, eg, prev ? &prev : nullptr, prev ? 1 : 0, child) != cudaSuccess)
+        rc = CPA_ERR_CUDA;
+      prev = node;
+    };
+    add(g_init);
+    for (int i = 0; i < iters; ++i) add(g_iter);
+    if (with_fit) add(g_fit);
+    if (rc == CPA_OK && cudaGraphInstantiate(&epoch_exec, eg, 0) != cudaSuccess) {
+      epoch_exec = nullptr;
+      rc = CPA_ERR_CUDA;
+    }
+    cudaGraphDestroy(eg);
+    if (rc < 0) return rc;
+    epoch_iters = iters;
+    k_epoch = k_init + (int64_t)iters * k_iter + (with_fit ? k_fit : 0);
+    return CPA_OK;
+  }
+
   ~Plan() {
+    if (epoch_exec) cudaGraphExecDestroy(epoch_exec);
+    if (g_iter) cudaGraphDestroy(g_iter);
+    if (g_init) cudaGraphDestroy(g_init);
+    if (g_fit) cudaGraphDestroy(g_fit);
     if (exec) cudaGraphExecDestroy(exec);
     if (init_exec) cudaGraphExecDestroy(init_exec);
     if (fit_exec) cudaGraphExecDestroy(fit_exec);
@@ -552,12 +595,22 @@ int Plan::run(const cpa_index* X, const cpa_options* opt, double* lambda, double
     cudaEventCreate(&call1);
     cudaEventRecord(call0, st);
   }
+  // fixed-length call without stage events: the whole call is one graph launch
+  const bool one_graph = use_graph && !profile && !(opt->tol > 0.0) && opt->iters <= kEpochGraphMax;
   if (use_graph) {
-    if (!init_exec) CPA_TRY(capture_graph([&](cudaStream_t cs) { return enqueue_init(X, cs); }, &init_exec, &k_init));
+    if (!init_exec)
+      CPA_TRY(capture_graph([&](cudaStream_t cs) { return enqueue_init(X, cs); }, &init_exec, &k_init, &g_init));
     if (!exec) CPA_TRY(capture(X));
-    if (!fit_exec) CPA_TRY(capture_graph([&](cudaStream_t cs) { return enqueue_fit(X, cs); }, &fit_exec, &k_fit));
-    CPA_CUDA_TRY(cudaGraphLaunch(init_exec, st));
-    kernels += k_init;
+    if (!fit_exec)
+      CPA_TRY(capture_graph([&](cudaStream_t cs) { return enqueue_fit(X, cs); }, &fit_exec, &k_fit, &g_fit));
+    if (one_graph) {
+      CPA_TRY(build_epoch(opt->iters, opt->fit_mode == CPA_FIT_EXACT));
+      CPA_CUDA_TRY(cudaGraphLaunch(epoch_exec, st));
+      kernels += k_epoch;
+    } else {
+      CPA_CUDA_TRY(cudaGraphLaunch(init_exec, st));
+      kernels += k_init;
+    }
   } else {
     CPA_TRY(enqueue_init(X, st));
     kernels = -1;
@@ -583,6 +636,8 @@ int Plan::run(const cpa_index* X, const cpa_options* opt, double* lambda, double
   double best = -INFINITY, fit_val = NAN;
   const int eta = opt->epoch_len > 0 ? opt->epoch_len : 1;
   int it = 0;
+  if (one_graph) it = opt->iters;  // done by the graph launched above
+  iters_done = it;
   while (it < opt->iters) {
     for (int l = 0; l < eta && it < opt->iters; ++l, ++it) {
       if (use_graph) {
@@ -616,7 +671,7 @@ int Plan::run(const cpa_index* X, const cpa_options* opt, double* lambda, double
     }
   }
   if (!(opt->tol > 0.0) && opt->fit_mode == CPA_FIT_EXACT) {
-    CPA_TRY(fit_now(eprof));
+    if (!one_graph) CPA_TRY(fit_now(eprof));
     CPA_CUDA_TRY(cudaMemcpyAsync(&fit_val, fitd, sizeof(double), cudaMemcpyDeviceToHost, st));
   }
   if (profile) cudaEventRecord(call1, st);

@@ -33,6 +33,14 @@ __device__ __forceinline__ bool pos_finite(double a) {
   return v > 0 && v < 0x7ff0000000000000ll;
 }
 
+// Asynchronous 8-byte global -> shared copy (cp.async, no register round trip) and
+// the wait for all of this thread's outstanding ones.
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 __device__ __forceinline__ void set_status(int* status, int code) {
   atomicCAS(status, 0, code);
 }

@@ -3,7 +3,7 @@
 // Two kernels per update, independent of each other (both read only the samples and
 // the factors), so the update runs them as two branches of its graph:
 //
-// 1. k_krp_gram (KrpSamp + sampled Gram): samples in tiles of 32;
+// 1. k_krp_gram (KrpSamp + sampled Gram): samples in tiles of 64;
 //    y_j = wgt_j * prod_t A_{m_t}(i_t, :) is formed in shared memory (row gathers of
 //    the other factors) and G += y_j y_j^T is accumulated per thread over the
 //    upper-triangle pairs (tile partials in FT, added across tiles in FP64).
@@ -20,8 +20,9 @@ namespace cpa {
 
 namespace {
 
-constexpr int kTileRows = 32;
+constexpr int kTileRows = 64;        // samples per k_krp_gram tile
 constexpr int kThreads = 256;
+constexpr int kGramMaxThreads = 1024;
 
 __device__ __forceinline__ void pair_of(int p, int r, int* a, int* b) {
   int row = 0, start = 0;
@@ -33,21 +34,24 @@ __device__ __forceinline__ void pair_of(int p, int r, int* a, int* b) {
   *b = row + (p - start);
 }
 
+// blockDim.x threads, each owning up to PMAX upper-triangle pairs (a, b) of G; the
+// block size is chosen so that the pairs split evenly (one pair per thread at r = 25).
 template <class FT, int PMAX>
-__global__ void __launch_bounds__(kThreads) k_krp_gram(FactorPtrs F, KeyLayout L, int r,
-                                                       const uint64_t* __restrict__ idx,
-                                                       const double* __restrict__ wgt,
-                                                       DevCount sbar, double* __restrict__ G) {
+__global__ void __launch_bounds__(kGramMaxThreads) k_krp_gram(FactorPtrs F, KeyLayout L, int r,
+                                                              const uint64_t* __restrict__ idx,
+                                                              const double* __restrict__ wgt,
+                                                              DevCount sbar, double* __restrict__ G) {
   extern __shared__ __align__(16) unsigned char krp_smem[];
   FT* tile = reinterpret_cast<FT*>(krp_smem);  // kTileRows * r
   __shared__ uint32_t rows[kTileRows][kMaxOrder];
   __shared__ FT wsh[kTileRows];
   const int np = r * (r + 1) / 2;
+  const int nt = blockDim.x;
   int pa[PMAX], pb[PMAX];
   double acc[PMAX];
 #pragma unroll
   for (int q = 0; q < PMAX; ++q) {
-    const int p = threadIdx.x + q * kThreads;
+    const int p = threadIdx.x + q * nt;
     if (p < np) pair_of(p, r, &pa[q], &pb[q]); else pa[q] = pb[q] = 0;
     acc[q] = 0.0;
   }
@@ -55,13 +59,13 @@ __global__ void __launch_bounds__(kThreads) k_krp_gram(FactorPtrs F, KeyLayout L
   for (int64_t t0 = (int64_t)blockIdx.x * kTileRows; t0 < n; t0 += (int64_t)gridDim.x * kTileRows) {
     const int cnt = (int)((n - t0) < kTileRows ? (n - t0) : kTileRows);
     __syncthreads();
-    if (threadIdx.x < cnt) {
-      const uint64_t key = idx[t0 + threadIdx.x];
-      for (int t = 0; t < L.d; ++t) rows[threadIdx.x][t] = L.get(key, t);
-      wsh[threadIdx.x] = (FT)wgt[t0 + threadIdx.x];
+    for (int sl = threadIdx.x; sl < cnt; sl += nt) {  // nt may be below the tile size
+      const uint64_t key = idx[t0 + sl];
+      for (int t = 0; t < L.d; ++t) rows[sl][t] = L.get(key, t);
+      wsh[sl] = (FT)wgt[t0 + sl];
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < kTileRows * r; i += kThreads) {
+    for (int i = threadIdx.x; i < kTileRows * r; i += nt) {
       const int sl = i / r, c = i - sl * r;
       FT v = FT(0);
       if (sl < cnt) {
@@ -74,17 +78,22 @@ __global__ void __launch_bounds__(kThreads) k_krp_gram(FactorPtrs F, KeyLayout L
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < PMAX; ++q) {
-      const int p = threadIdx.x + q * kThreads;
+      const int p = threadIdx.x + q * nt;
       if (p < np) {
-        FT s = FT(0);
-        for (int i = 0; i < cnt; ++i) s = fma(tile[i * r + pa[q]], tile[i * r + pb[q]], s);
-        acc[q] += (double)s;
+        FT s0 = FT(0), s1 = FT(0);  // two chains for the FMA latency
+        int i = 0;
+        for (; i + 1 < cnt; i += 2) {
+          s0 = fma(tile[i * r + pa[q]], tile[i * r + pb[q]], s0);
+          s1 = fma(tile[(i + 1) * r + pa[q]], tile[(i + 1) * r + pb[q]], s1);
+        }
+        if (i < cnt) s0 = fma(tile[i * r + pa[q]], tile[i * r + pb[q]], s0);
+        acc[q] += (double)s0 + (double)s1;
       }
     }
   }
 #pragma unroll
   for (int q = 0; q < PMAX; ++q) {
-    const int p = threadIdx.x + q * kThreads;
+    const int p = threadIdx.x + q * nt;
     if (p < np && acc[q] != 0.0) {
       atomicAdd(&G[pa[q] * r + pb[q]], acc[q]);
       if (pa[q] != pb[q]) atomicAdd(&G[pb[q] * r + pa[q]], acc[q]);
@@ -256,15 +265,17 @@ int launch_gram(const FactorPtrs& F, const KeyLayout& L, int r, const uint64_t* 
                 DevCount sbar, double* G, cudaStream_t st) {
   const int sms = num_sms();
   const int np = r * (r + 1) / 2;
+  // threads: the pair count rounded up to whole warps, at most 1024 (r > 44: 2-3 pairs each)
+  const int nt = np <= kGramMaxThreads ? ((np + 31) / 32) * 32 : kGramMaxThreads;
+  const int per = (np + nt - 1) / nt;
   const int64_t tb = ceil_div(sbar.max, (int64_t)kTileRows);
-  const unsigned tgrid = (unsigned)(tb < sms * 2 ? tb : sms * 2);
+  const int64_t cap = (int64_t)sms * (nt <= 512 ? 2 : 1);
+  const unsigned tgrid = (unsigned)(tb < cap ? tb : cap);
   const size_t tsm = sizeof(FT) * kTileRows * r;
-  if (np <= kThreads)
-    k_krp_gram<FT, 1><<<tgrid, kThreads, tsm, st>>>(F, L, r, idx, wgt, sbar, G);
-  else if (np <= 4 * kThreads)
-    k_krp_gram<FT, 4><<<tgrid, kThreads, tsm, st>>>(F, L, r, idx, wgt, sbar, G);
+  if (per <= 1)
+    k_krp_gram<FT, 1><<<tgrid, nt, tsm, st>>>(F, L, r, idx, wgt, sbar, G);
   else
-    k_krp_gram<FT, 9><<<tgrid, kThreads, tsm, st>>>(F, L, r, idx, wgt, sbar, G);
+    k_krp_gram<FT, 3><<<tgrid, nt, tsm, st>>>(F, L, r, idx, wgt, sbar, G);
   CPA_LAUNCH_CHECK();
   return CPA_OK;
 }

@@ -439,14 +439,15 @@ __global__ void __launch_bounds__(kThreads) k_rnd(SampleParams P, SampleState* S
   if (threadIdx.x == 0) sh_span = 1;
   if (staged) {
     uint64_t* o = rnd_smem;
-    for (int t = 0; t < P.L.d; ++t) {
+    for (int t = 0; t < P.L.d; ++t) {  // all copies in flight at once
       const int64_t n = P.L.n[t];
       for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-        o[i] = P.D.C[t][i];
-        o[n + i] = __double_as_longlong(P.D.P[t][i]);
+        cp_async8(o + i, P.D.C[t] + i);
+        cp_async8(o + n + i, P.D.P[t] + i);
       }
       o += 2 * n;
     }
+    cp_async_wait_all();
     if (P.L.d <= 4) {
       __syncthreads();
       const uint64_t* c = rnd_smem;
