@@ -201,6 +201,18 @@ int cpa_index_export(const cpa_index* index, int32_t mode, uint64_t* keys, uint6
 int cp_arls_lev(const cpa_index* index, const cpa_options* opt, double* lambda,
                 double* const* factors, int32_t io_on_device, double* fit, cpa_stats* stats);
 
+/* Full CP-ALS (Sec. 2, Eq. 2.3: the exact least-squares update that Alg. 3
+ * randomizes), for comparison and for the tau = 0 reduction at scale: per mode,
+ * M = X_(k) times the Khatri-Rao product of the other factors (exact MTTKRP over the
+ * mode-k fibre index), G = Hadamard product of the other factors' Grams, A_k =
+ * M G^{-1} (FP64 factorisation, pseudo-inverse fallback), columns normalised into
+ * lambda.  Runs exactly opt->iters outer iterations; uses opt->rank, iters,
+ * precision (CPA_FP64 or CPA_MIXED: FP32 factors and MTTKRP), fit_mode, stream;
+ * samples, tau, seed and the epoch rule are ignored.  Arguments, ownership and
+ * errors as cp_arls_lev (stats: iters_done, mode_updates, warnings only). */
+int cp_als(const cpa_index* index, const cpa_options* opt, double* lambda, double* const* factors,
+           int32_t io_on_device, double* fit, cpa_stats* stats);
+
 /* The same from a COO tensor: builds the index, runs cp_arls_lev and frees the
  * index.  Arguments as for cpa_index_build and cp_arls_lev. */
 int cp_arls_lev_coo(const cpa_coo* coo, const cpa_options* opt, double* lambda,

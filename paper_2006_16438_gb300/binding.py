@@ -40,7 +40,7 @@ EXPORTED = [
     "cpa_options_default", "cpa_strerror", "cpa_index_build", "cpa_index_free", "cpa_index_info",
     "cpa_index_export", "cp_arls_lev", "cp_arls_lev_coo", "cpa_philox4x64", "cpa_leverage",
     "cpa_cdf", "cpa_skrp_lev", "cpa_sampled_mttkrp", "cpa_solve", "cpa_fit", "cpa_leverage_noalloc",
-    "cpa_mode_update",
+    "cpa_mode_update", "cp_als",
 ]
 
 
@@ -115,6 +115,7 @@ def _declare(lib):
         "cpa_index_export": ([P, I32, P, P, P, P, P], I32),
         "cp_arls_lev": ([P, P, P, P, I32, P, P], I32),
         "cp_arls_lev_coo": ([P, P, P, P, I32, P, P], I32),
+        "cp_als": ([P, P, P, P, I32, P, P], I32),
         "cpa_mode_update": ([P, P, I32, U64, P, P, P, P, P, P, P], I32),
         "cpa_philox4x64": ([P, P, I64, P, P], I32),
         "cpa_leverage": ([P, I64, I32, P, P], I32),
@@ -297,6 +298,22 @@ def cp_arls_lev(index: Index, factors, *, rank, samples, tau=1.0, iters=10, epoc
                             0, C.byref(fit), C.byref(stats))
     _check(rc, "cp_arls_lev")
     return Result(lam, fs, fit.value, stats.as_dict(), rc)
+
+
+def cp_als(index: Index, factors, *, rank, iters=10, fit_mode=FIT_EXACT, precision=FP64) -> Result:
+    """Full CP-ALS on the GPU (exact MTTKRP).  ``factors``: CUDA float64 tensors
+    (n_k x rank); returns a Result with new factor copies."""
+    torch = _torch()
+    o = default_options(rank=rank, iters=int(iters), fit_mode=int(fit_mode), precision=int(precision))
+    o.stream = _stream()
+    stats = Stats()
+    fs = [f.detach().to(device="cuda", dtype=torch.float64).contiguous().clone() for f in factors]
+    lam = torch.empty(rank, dtype=torch.float64, device="cuda")
+    fit_d = torch.empty(1, dtype=torch.float64, device="cuda")
+    rc = _lib().cp_als(index.h, C.byref(o), _ptr(lam), _ptr_array([f.data_ptr() for f in fs]), 1,
+                       _ptr(fit_d), C.byref(stats))
+    _check(rc, "cp_als")
+    return Result(lam, fs, float(fit_d.item()), stats.as_dict(), rc)
 
 
 def cp_arls_lev_coo(coo, factors, *, rank, samples, tau=1.0, iters=10, seed=0, fit_mode=FIT_EXACT,

@@ -27,6 +27,9 @@ struct cpa_index {
     uint64_t* dir = nullptr;    // (1 << dbits) + 1 bucket starts over the top key bits
     int dbits = 0;
     int dshift = 0;
+    // open-addressing table of (key, lo << 24 | len), 2^hbits slots (null: directory only)
+    ulonglong2* htab = nullptr;
+    int hbits = 0;
   } mode[cpa::kMaxOrder];
   std::vector<void*> allocations;
   // cached workspace + CUDA graph of one outer iteration (see api.cu)
@@ -35,6 +38,13 @@ struct cpa_index {
 };
 
 namespace cpa {
+
+// Empty slot of the fibre hash table (a packed key uses at most 63 bits).
+constexpr uint64_t kNoFibre = ~0ull;
+// Slot of a packed key in a table of 2^hbits slots (multiplicative hashing).
+__host__ __device__ __forceinline__ uint64_t fibre_slot(uint64_t key, int hbits) {
+  return (key * 0x9E3779B97F4A7C15ull) >> (64 - hbits);
+}
 
 // Device view of one mode of the index, passed by value to kernels.
 template <class VT>
@@ -47,9 +57,29 @@ struct FibreIndex {
   int64_t nfib;
   int dshift;
   int dbits;
+  const ulonglong2* htab;  // null: probe through the directory
+  int hbits;
 
   // Fibre [*lo, *hi) of a packed key; empty range if the key has no nonzeros.
+  // With the hash table a probe is one 16-byte record (key, lo << 24 | len) per slot
+  // visited (load <= 1/2); otherwise the directory bucket and a bisection of keys.
   __device__ __forceinline__ void probe(uint64_t key, uint64_t* lo, uint64_t* hi) const {
+    if (htab) {
+      const uint64_t mask = (1ull << hbits) - 1ull;
+      uint64_t h = fibre_slot(key, hbits);
+      for (uint64_t step = 0; step <= mask; ++step) {
+        const ulonglong2 rec = htab[h];
+        if (rec.x == key) {
+          *lo = rec.y >> 24;
+          *hi = *lo + (rec.y & 0xffffffull);
+          return;
+        }
+        if (rec.x == kNoFibre) break;
+        h = (h + 1) & mask;
+      }
+      *lo = *hi = 0;
+      return;
+    }
     const uint64_t b = dshift >= 64 ? 0 : (key >> dshift);
     int64_t a = (int64_t)dir[b], z = (int64_t)dir[b + 1];
     while (a < z) {  // lower bound in keys[a, z)
@@ -69,7 +99,7 @@ template <class VT>
 inline FibreIndex<VT> fibre_view(const cpa_index* X, int k) {
   const auto& M = X->mode[k];
   return FibreIndex<VT>{M.keys, M.off, M.ik, reinterpret_cast<const VT*>(M.val), M.dir,
-                        M.nfib, M.dshift, M.dbits};
+                        M.nfib, M.dshift, M.dbits, M.htab, M.hbits};
 }
 
 // index.cu

@@ -97,14 +97,44 @@ __global__ void k_write_fibres(const uint64_t* __restrict__ skeys, int compose, 
 
 __global__ void k_finish_off(uint64_t* off, int64_t nfib, int64_t nnz) { off[nfib] = (uint64_t)nnz; }
 
-// dir[b] = first fibre whose key has top bits >= b, for b in [0, 2^dbits].
+constexpr size_t kFibreHashBudget = size_t(4) << 30;  // bytes of fibre hash table per mode
+
+// dir[b] = first fibre whose key has top bits >= b, for b in [0, 2^dbits]: one
+// bisection of the sorted keys per bucket (balanced whatever the key skew).
 __global__ void k_directory(const uint64_t* __restrict__ keys, int64_t nfib, int dshift,
                             int64_t nbuckets, uint64_t* __restrict__ dir) {
-  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f <= nfib;
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b <= nbuckets;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    int64_t lo = 0, hi = nfib;
+    if (b < nbuckets) {
+      while (lo < hi) {
+        const int64_t mid = lo + ((hi - lo) >> 1);
+        if ((int64_t)(keys[mid] >> dshift) < b) lo = mid + 1; else hi = mid;
+      }
+    } else {
+      lo = nfib;
+    }
+    dir[b] = (uint64_t)lo;
+  }
+}
+
+// Fibre f into the open-addressing table (slots preset to kNoFibre; keys distinct).
+__global__ void k_hash_fibres(const uint64_t* __restrict__ keys, const uint64_t* __restrict__ off,
+                              int64_t nfib, int hbits, ulonglong2* __restrict__ htab) {
+  const uint64_t mask = (1ull << hbits) - 1ull;
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nfib;
        f += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t bf = f < nfib ? (int64_t)(keys[f] >> dshift) : nbuckets;
-    const int64_t bp = f > 0 ? (int64_t)(keys[f - 1] >> dshift) : -1;
-    for (int64_t b = bp + 1; b <= bf; ++b) dir[b] = (uint64_t)f;
+    const uint64_t key = keys[f], lo = off[f], len = off[f + 1] - lo;
+    uint64_t h = fibre_slot(key, hbits);
+    for (;;) {  // at most nfib < 2^hbits occupied slots: a free one exists
+      const unsigned long long prev = atomicCAS(reinterpret_cast<unsigned long long*>(&htab[h].x),
+                                                (unsigned long long)kNoFibre, (unsigned long long)key);
+      if (prev == kNoFibre) {
+        htab[h].y = (lo << 24) | len;
+        break;
+      }
+      h = (h + 1) & mask;
+    }
   }
 }
 
@@ -222,8 +252,23 @@ int build_modes(cpa_index* X, const CooPtrs& coo, const VT* vals, int* d_status,
       const int64_t nb = 1ll << dbits;
       CPA_CUDA_TRY(cudaMallocAsync(&M.dir, sizeof(uint64_t) * (nb + 1), st));
       X->allocations.push_back(M.dir);
-      k_directory<<<grid_for(M.nfib + 1), 256, 0, st>>>(M.keys, M.nfib, M.dshift, nb, M.dir);
+      k_directory<<<grid_for(nb + 1), 256, 0, st>>>(M.keys, M.nfib, M.dshift, nb, M.dir);
       CPA_LAUNCH_CHECK();
+      // hash table of the fibres (load <= 1/2) when it fits the budget and the record
+      // encoding (fibre start < 2^40, length < 2^24)
+      int hb = 4;
+      while ((1ll << hb) < 2 * M.nfib) ++hb;
+      const size_t hbytes = sizeof(ulonglong2) * ((size_t)1 << hb);
+      size_t longest = 0;  // host bound: a fibre is at most dims[k] long
+      longest = (size_t)X->dims[k];
+      if (M.nfib > 0 && hbytes <= kFibreHashBudget && longest < (1ull << 24) && nnz < (1ll << 40)) {
+        M.hbits = hb;
+        CPA_CUDA_TRY(cudaMallocAsync(&M.htab, hbytes, st));
+        X->allocations.push_back(M.htab);
+        CPA_CUDA_TRY(cudaMemsetAsync(M.htab, 0xff, hbytes, st));
+        k_hash_fibres<<<grid_for(M.nfib), 256, 0, st>>>(M.keys, M.off, M.nfib, hb, M.htab);
+        CPA_LAUNCH_CHECK();
+      }
     }
   }
   CPA_CUDA_TRY(cudaFreeAsync(a.base, st));
