@@ -213,6 +213,39 @@ int cp_arls_lev(const cpa_index* index, const cpa_options* opt, double* lambda,
 int cp_als(const cpa_index* index, const cpa_options* opt, double* lambda, double* const* factors,
            int32_t io_on_device, double* fit, cpa_stats* stats);
 
+/* Batched decompositions (no counterpart in the paper; the serving pattern of many
+ * independent CP-ARLS-LEV runs, e.g. random restarts or ranks, sharing the GPU).
+ * A batch holds nprob fixed-length cp_arls_lev calls on DEVICE buffers; each run
+ * replays all of them as the independent branches of one CUDA graph (one launch),
+ * each call continuing its decomposition where the previous run stopped (the
+ * Philox iteration offset advances by opts[i].iters per run).
+ *   indices   nprob tensor indices (may repeat)
+ *   opts      nprob options: tol must be 0, profile 0, iters <= 256, and the draws
+ *             graph-replayable (not tau < 1 with tau * samples < 1), else
+ *             CPA_ERR_UNSUPPORTED
+ *   lambdas   nprob device pointers to r_i doubles (out)
+ *   factors   nprob host arrays of order_i device pointers (in/out, as cp_arls_lev)
+ *   fits      nprob device pointers to one double (out), or NULL
+ *   autotune  1: time the batch graph with its kernels sized for all, 1/2, 1/4 and
+ *             1/8 of the SMs (two runs each from the same factors, which are then
+ *             restored) and keep the fastest; 0: all SMs
+ * The buffers must stay valid for the batch's lifetime; cpa_batch_free releases it.
+ * Errors as cp_arls_lev; CPA_ERR_UNSUPPORTED as above. */
+typedef struct cpa_batch cpa_batch;
+int cpa_batch_create(int32_t nprob, const cpa_index* const* indices, const cpa_options* opts,
+                     double* const* lambdas, double* const* const* factors, double* const* fits,
+                     int32_t autotune, void* stream, cpa_batch** out);
+/* Runs every call of the batch once (one graph launch, then one synchronisation).
+ * stats (nprob entries, may be NULL): iters_done, mode_updates, warnings, sampled
+ * counters; kernel_launches of the whole launch in stats[0]. Returns the first
+ * negative status of a call, else the OR of the warnings. */
+int cpa_batch_run(cpa_batch* batch, void* stream, cpa_stats* stats);
+/* The SM budget chosen, the four candidate budgets and their timed milliseconds
+ * (zeros without autotuning) and the kernel nodes of one run; outputs may be NULL. */
+int cpa_batch_info(const cpa_batch* batch, int32_t* sm_budget, int32_t* cand_budgets, double* cand_ms,
+                   int64_t* kernels);
+int cpa_batch_free(cpa_batch* batch);
+
 /* The same from a COO tensor: builds the index, runs cp_arls_lev and frees the
  * index.  Arguments as for cpa_index_build and cp_arls_lev. */
 int cp_arls_lev_coo(const cpa_coo* coo, const cpa_options* opt, double* lambda,

@@ -40,7 +40,7 @@ EXPORTED = [
     "cpa_options_default", "cpa_strerror", "cpa_index_build", "cpa_index_free", "cpa_index_info",
     "cpa_index_export", "cp_arls_lev", "cp_arls_lev_coo", "cpa_philox4x64", "cpa_leverage",
     "cpa_cdf", "cpa_skrp_lev", "cpa_sampled_mttkrp", "cpa_solve", "cpa_fit", "cpa_leverage_noalloc",
-    "cpa_mode_update", "cp_als",
+    "cpa_mode_update", "cp_als", "cpa_batch_create", "cpa_batch_run", "cpa_batch_info", "cpa_batch_free",
 ]
 
 
@@ -116,6 +116,10 @@ def _declare(lib):
         "cp_arls_lev": ([P, P, P, P, I32, P, P], I32),
         "cp_arls_lev_coo": ([P, P, P, P, I32, P, P], I32),
         "cp_als": ([P, P, P, P, I32, P, P], I32),
+        "cpa_batch_create": ([I32, P, P, P, P, P, I32, P, P], I32),
+        "cpa_batch_run": ([P, P, P], I32),
+        "cpa_batch_info": ([P, P, P, P, P], I32),
+        "cpa_batch_free": ([P], I32),
         "cpa_mode_update": ([P, P, I32, U64, P, P, P, P, P, P, P], I32),
         "cpa_philox4x64": ([P, P, I64, P, P], I32),
         "cpa_leverage": ([P, I64, I32, P, P], I32),
@@ -314,6 +318,66 @@ def cp_als(index: Index, factors, *, rank, iters=10, fit_mode=FIT_EXACT, precisi
                        _ptr(fit_d), C.byref(stats))
     _check(rc, "cp_als")
     return Result(lam, fs, float(fit_d.item()), stats.as_dict(), rc)
+
+
+class Batch:
+    """Many fixed-length cp_arls_lev calls replayed as one CUDA graph (cpa_batch_*).
+    problems: list of dicts with keys index, factors (CUDA float64 tensors), rank,
+    samples, tau, iters, seed and optionally precision, iter_offset.  The factors are
+    updated in place by every run()."""
+
+    def __init__(self, problems, autotune=True):
+        torch = _torch()
+        self.problems = problems
+        n = len(problems)
+        self.lams = [torch.empty(p["rank"], dtype=torch.float64, device="cuda") for p in problems]
+        self.fits_d = [torch.empty(1, dtype=torch.float64, device="cuda") for p in problems]
+        self.factors = [p["factors"] for p in problems]
+        opts = (Options * n)()
+        for i, p in enumerate(problems):
+            opts[i] = default_options(rank=p["rank"], samples=int(p["samples"]), tau=float(p["tau"]),
+                                      iters=int(p["iters"]), seed=int(p.get("seed", 0)),
+                                      iter_offset=int(p.get("iter_offset", 0)),
+                                      precision=int(p.get("precision", FP64)), stream=_stream())
+        self._fac_arrays = [_ptr_array([f.data_ptr() for f in fs]) for fs in self.factors]
+        fac_ptrs = (C.c_void_p * n)(*[C.cast(a, C.c_void_p) for a in self._fac_arrays])
+        idx = (C.c_void_p * n)(*[p["index"].h.value for p in problems])
+        lam_ptrs = (C.c_void_p * n)(*[t.data_ptr() for t in self.lams])
+        fit_ptrs = (C.c_void_p * n)(*[t.data_ptr() for t in self.fits_d])
+        h = C.c_void_p()
+        rc = _lib().cpa_batch_create(n, idx, opts, lam_ptrs, fac_ptrs, fit_ptrs, int(autotune), _stream(),
+                                     C.byref(h))
+        _check(rc, "cpa_batch_create")
+        self.h = h
+        self.n = n
+
+    def run(self):
+        stats = (Stats * self.n)()
+        rc = _lib().cpa_batch_run(self.h, _stream(), stats)
+        _check(rc, "cpa_batch_run")
+        return [s.as_dict() for s in stats]
+
+    def fits(self):
+        return [float(t.item()) for t in self.fits_d]
+
+    def info(self):
+        b = C.c_int32(0)
+        cb = (C.c_int32 * 4)()
+        cm = (C.c_double * 4)()
+        k = C.c_int64(0)
+        _check(_lib().cpa_batch_info(self.h, C.byref(b), cb, cm, C.byref(k)), "cpa_batch_info")
+        return {"sm_budget": b.value, "candidates": list(cb), "candidate_ms": list(cm), "kernels": k.value}
+
+    def free(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            _lib().cpa_batch_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 def cp_arls_lev_coo(coo, factors, *, rank, samples, tau=1.0, iters=10, seed=0, fit_mode=FIT_EXACT,

@@ -8,6 +8,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <memory>
 #include <mutex>
 #include <vector>
 
@@ -233,6 +234,32 @@ __global__ void k_run_init(double* lam, double* fitd, uint64_t* it, uint64_t it0
   for (int i = threadIdx.x; i < kMaxRank; i += blockDim.x) lam[i] = 1.0;
   if (threadIdx.x < 4) fitd[threadIdx.x] = NAN;
   if (threadIdx.x == 0) *it = it0;
+}
+
+// As k_run_init with the iteration offset read from, and advanced in, device memory
+// (a captured call continues where the previous replay stopped).
+__global__ void k_run_init_dev(double* lam, double* fitd, uint64_t* it, uint64_t* it0, uint64_t advance) {
+  for (int i = threadIdx.x; i < kMaxRank; i += blockDim.x) lam[i] = 1.0;
+  if (threadIdx.x < 4) fitd[threadIdx.x] = NAN;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *it = *it0;
+    *it0 += advance;
+  }
+}
+
+// Status of a captured call: the sticky status word, the warnings and the counters.
+struct CallOut {
+  int status;
+  int warnings;
+  int64_t nnz_total;
+  int64_t sbar_total;
+};
+__global__ void k_call_out(const int* status, const int* warn, const DevStats* ds, CallOut* out) {
+  out->status = *status;
+  out->warnings = *warn;
+  out->nnz_total = ds->nnz_total;
+  out->sbar_total = ds->sbar_total;
 }
 
 constexpr int kEpochGraphMax = 256;  // longest fixed-length call run as one graph
@@ -510,6 +537,63 @@ struct Plan {
                                      nullptr, st));
     k_copy_lambda<<<1, 64, 0, st>>>(flev, r, lam);
     CPA_LAUNCH_CHECK();
+    return CPA_OK;
+  }
+
+  // A whole fixed-length call on device buffers as one graph (batched entry point):
+  // state reset, copy-in, initial leverage, `iters` outer iterations, fit, copy-out
+  // and the call's status into *out.  The iteration offset lives in *it0_dev and is
+  // advanced by `iters` per replay.  Grid sizes follow num_sms() at capture time.
+  int capture_call(const cpa_index* X, int iters, bool with_fit, double* lambda, double* const* factors,
+                   double* fit_dev, uint64_t* it0_dev, CallOut* out, cudaGraph_t* g_out) {
+    if (!cap_stream) CPA_CUDA_TRY(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
+    cudaStream_t cs = cap_stream;
+    Profiler off;
+    cudaGraph_t g = nullptr;
+    CPA_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    auto body = [&]() -> int {
+      CPA_CUDA_TRY(cudaMemsetAsync(warn, 0, sizeof(int) * 4, cs));
+      CPA_CUDA_TRY(cudaMemsetAsync(dstats, 0, sizeof(DevStats), cs));
+      CPA_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(DistInfo) * kMaxOrder, cs));
+      CPA_CUDA_TRY(cudaMemsetAsync(&SB[0].state->status, 0, sizeof(int), cs));
+      for (int m = 0; m < D; ++m) {
+        const int64_t cnt = X->dims[m] * r;
+        if (prec == CPA_MIXED) {
+          CPA_CUDA_TRY(cudaMemcpyAsync(stage64, factors[m], sizeof(double) * cnt, cudaMemcpyDeviceToDevice, cs));
+          k_convert<float, double><<<blocks(cnt), 256, 0, cs>>>(stage64, cnt, static_cast<float*>(Fm[m]));
+          CPA_LAUNCH_CHECK();
+        } else {
+          CPA_CUDA_TRY(cudaMemcpyAsync(Fm[m], factors[m], sizeof(double) * cnt, cudaMemcpyDeviceToDevice, cs));
+        }
+      }
+      k_run_init_dev<<<1, 64, 0, cs>>>(lam, fitd, iter_dev, it0_dev, (uint64_t)iters);
+      CPA_LAUNCH_CHECK();
+      CPA_TRY(enqueue_init(X, cs));
+      for (int i = 0; i < iters; ++i) CPA_TRY(enqueue_iteration(X, off, cs));
+      if (with_fit) CPA_TRY(enqueue_fit(X, cs));
+      for (int m = 0; m < D; ++m) {
+        const int64_t cnt = X->dims[m] * r;
+        if (prec == CPA_MIXED) {
+          k_convert<double, float><<<blocks(cnt), 256, 0, cs>>>(static_cast<const float*>(Fm[m]), cnt, stage64);
+          CPA_LAUNCH_CHECK();
+          CPA_CUDA_TRY(cudaMemcpyAsync(factors[m], stage64, sizeof(double) * cnt, cudaMemcpyDeviceToDevice, cs));
+        } else {
+          CPA_CUDA_TRY(cudaMemcpyAsync(factors[m], Fm[m], sizeof(double) * cnt, cudaMemcpyDeviceToDevice, cs));
+        }
+      }
+      CPA_CUDA_TRY(cudaMemcpyAsync(lambda, lam, sizeof(double) * r, cudaMemcpyDeviceToDevice, cs));
+      if (fit_dev) CPA_CUDA_TRY(cudaMemcpyAsync(fit_dev, fitd, sizeof(double), cudaMemcpyDeviceToDevice, cs));
+      k_call_out<<<1, 1, 0, cs>>>(&SB[0].state->status, warn, dstats, out);
+      CPA_LAUNCH_CHECK();
+      return CPA_OK;
+    };
+    const int rc = body();
+    const cudaError_t ec = cudaStreamEndCapture(cs, &g);
+    if (rc < 0 || ec != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return rc < 0 ? rc : CPA_ERR_CUDA;
+    }
+    *g_out = g;
     return CPA_OK;
   }
 
@@ -1139,6 +1223,225 @@ int cp_arls_lev_coo(const cpa_coo* coo, const cpa_options* opt, double* lambda, 
   const int rc = cp_arls_lev(X, opt, lambda, factors, io_on_device, fit, stats);
   cpa_index_free(X);
   return rc;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched decompositions: many independent fixed-length cp_arls_lev calls as the
+// branches of one CUDA graph (one launch), with the SM budget their kernels are sized
+// for chosen by timing the candidate graphs.
+// ---------------------------------------------------------------------------
+struct cpa_batch {
+  int n = 0;
+  std::vector<cpa::Plan*> plans;
+  std::vector<const cpa_index*> idx;
+  std::vector<cpa_options> opts;
+  std::vector<double*> lambdas, fits;
+  std::vector<std::vector<double*>> factors;
+  char* dev = nullptr;
+  cpa::CallOut* outs = nullptr;
+  uint64_t* it0 = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int budget = 0;
+  int64_t kernels = 0;
+  double tune_ms[4] = {0, 0, 0, 0};
+  int tune_budget[4] = {0, 0, 0, 0};
+
+  ~cpa_batch() {
+    if (exec) cudaGraphExecDestroy(exec);
+    for (auto* p : plans) cpa::plan_free(p);
+    if (dev) {
+      cudaDeviceSynchronize();
+      cudaFree(dev);
+    }
+  }
+
+  // capture every problem's call with grids sized for `sms` SMs and compose them
+  int build(int sms) {
+    using namespace cpa;
+    if (exec) {
+      cudaGraphExecDestroy(exec);
+      exec = nullptr;
+    }
+    cudaGraph_t bg = nullptr;
+    CPA_CUDA_TRY(cudaGraphCreate(&bg, 0));
+    int rc = CPA_OK;
+    int64_t kern = 0;
+    sm_budget_override() = sms;
+    for (int i = 0; i < n && rc == CPA_OK; ++i) {
+      cudaGraph_t g = nullptr;
+      rc = plans[i]->capture_call(idx[i], opts[i].iters, opts[i].fit_mode == CPA_FIT_EXACT, lambdas[i],
+                                  factors[i].data(), fits[i], it0 + i, outs + i, &g);
+      if (rc < 0) break;
+      size_t nn = 0;
+      if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess && nn > 0) {
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess)
+          for (size_t q = 0; q < nn; ++q) {
+            cudaGraphNodeType t;
+            if (cudaGraphNodeGetType(nodes[q], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kern;
+          }
+      }
+      cudaGraphNode_t node = nullptr;
+      if (cudaGraphAddChildGraphNode(&node, bg, nullptr, 0, g) != cudaSuccess) rc = CPA_ERR_CUDA;
+      cudaGraphDestroy(g);
+    }
+    sm_budget_override() = 0;
+    if (rc == CPA_OK && cudaGraphInstantiate(&exec, bg, 0) != cudaSuccess) {
+      exec = nullptr;
+      rc = CPA_ERR_CUDA;
+    }
+    cudaGraphDestroy(bg);
+    if (rc < 0) return rc;
+    budget = sms;
+    kernels = kern;
+    return CPA_OK;
+  }
+};
+
+extern "C" {
+
+int cpa_batch_create(int32_t nprob, const cpa_index* const* indices, const cpa_options* opts,
+                     double* const* lambdas, double* const* const* factors, double* const* fits,
+                     int32_t autotune, void* stream, cpa_batch** out) {
+  using namespace cpa;
+  if (!out || nprob < 1 || !indices || !opts || !lambdas || !factors) return CPA_ERR_ARG;
+  *out = nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int i = 0; i < nprob; ++i) {
+    const cpa_options& o = opts[i];
+    CPA_TRY(check_options(&o));
+    if (!indices[i] || !lambdas[i] || !factors[i]) return CPA_ERR_ARG;
+    for (int m = 0; m < indices[i]->order; ++m)
+      if (!factors[i][m]) return CPA_ERR_ARG;
+    // fixed-length calls only, replayable as a graph
+    if (o.tol > 0.0 || o.profile || o.iters > kEpochGraphMax) return CPA_ERR_UNSUPPORTED;
+    if (o.tau < 1.0 && o.tau * (double)o.samples < 1.0) return CPA_ERR_UNSUPPORTED;
+  }
+  std::unique_ptr<cpa_batch> b(new (std::nothrow) cpa_batch());
+  if (!b) return CPA_ERR_OOM;
+  b->n = nprob;
+  for (int i = 0; i < nprob; ++i) {
+    b->idx.push_back(indices[i]);
+    b->opts.push_back(opts[i]);
+    b->lambdas.push_back(lambdas[i]);
+    b->fits.push_back(fits ? fits[i] : nullptr);
+    b->factors.emplace_back(factors[i], factors[i] + indices[i]->order);
+    Plan* p = new (std::nothrow) Plan();
+    if (!p) return CPA_ERR_OOM;
+    b->plans.push_back(p);
+    CPA_TRY(p->init(indices[i], &opts[i], st));
+  }
+  const size_t outs_bytes = ((sizeof(CallOut) * nprob + 255) / 256) * 256;
+  if (cudaMalloc((void**)&b->dev, outs_bytes + sizeof(uint64_t) * nprob) != cudaSuccess) return CPA_ERR_OOM;
+  b->outs = reinterpret_cast<CallOut*>(b->dev);
+  b->it0 = reinterpret_cast<uint64_t*>(b->dev + outs_bytes);
+  std::vector<uint64_t> it0h(nprob);
+  for (int i = 0; i < nprob; ++i) it0h[i] = opts[i].iter_offset;
+  CPA_CUDA_TRY(cudaMemcpy(b->it0, it0h.data(), sizeof(uint64_t) * nprob, cudaMemcpyHostToDevice));
+  const int sms = num_sms();
+  if (!autotune) {
+    CPA_TRY(b->build(sms));
+    *out = b.release();
+    return CPA_OK;
+  }
+  // autotune: run each candidate once untimed and once timed from the same starting
+  // factors and iteration offsets, restoring both afterwards
+  std::vector<std::pair<double*, size_t>> snap;
+  DevBuf sbuf;
+  size_t total = 0;
+  for (int i = 0; i < nprob; ++i)
+    for (int m = 0; m < indices[i]->order; ++m) total += sizeof(double) * indices[i]->dims[m] * opts[i].rank;
+  CPA_TRY(sbuf.alloc(total, st));
+  auto copy_all = [&](bool save) -> int {
+    char* q = (char*)sbuf.p;
+    for (int i = 0; i < nprob; ++i)
+      for (int m = 0; m < indices[i]->order; ++m) {
+        const size_t nb = sizeof(double) * indices[i]->dims[m] * opts[i].rank;
+        CPA_CUDA_TRY(cudaMemcpyAsync(save ? (void*)q : (void*)factors[i][m], save ? (void*)factors[i][m] : (void*)q,
+                                     nb, cudaMemcpyDeviceToDevice, st));
+        q += nb;
+      }
+    CPA_CUDA_TRY(cudaMemcpyAsync(b->it0, it0h.data(), sizeof(uint64_t) * nprob, cudaMemcpyHostToDevice, st));
+    CPA_CUDA_TRY(cudaStreamSynchronize(st));
+    return CPA_OK;
+  };
+  CPA_TRY(copy_all(true));
+  const int cand[4] = {sms, (sms + 1) / 2, (sms + 3) / 4, (sms + 7) / 8};
+  cudaEvent_t e0, e1;
+  CPA_CUDA_TRY(cudaEventCreate(&e0));
+  CPA_CUDA_TRY(cudaEventCreate(&e1));
+  int best = -1;
+  double best_ms = 0.0;
+  int rc = CPA_OK;
+  for (int c = 0; c < 4 && rc == CPA_OK; ++c) {
+    rc = b->build(cand[c]);
+    if (rc < 0) break;
+    for (int rep = 0; rep < 2 && rc == CPA_OK; ++rep) {
+      if (cudaEventRecord(e0, st) != cudaSuccess || cudaGraphLaunch(b->exec, st) != cudaSuccess ||
+          cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+        rc = CPA_ERR_CUDA;
+    }
+    float ms = 0.f;
+    if (rc == CPA_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = CPA_ERR_CUDA;
+    if (rc == CPA_OK) rc = copy_all(false);
+    b->tune_budget[c] = cand[c];
+    b->tune_ms[c] = ms;
+    if (rc == CPA_OK && (best < 0 || ms < best_ms)) {
+      best = c;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc < 0) return rc;
+  if (b->budget != cand[best]) CPA_TRY(b->build(cand[best]));
+  *out = b.release();
+  return CPA_OK;
+}
+
+int cpa_batch_run(cpa_batch* b, void* stream, cpa_stats* stats) {
+  using namespace cpa;
+  if (!b || !b->exec) return CPA_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  CPA_CUDA_TRY(cudaGraphLaunch(b->exec, st));
+  std::vector<CallOut> h(b->n);
+  CPA_CUDA_TRY(cudaMemcpyAsync(h.data(), b->outs, sizeof(CallOut) * b->n, cudaMemcpyDeviceToHost, st));
+  CPA_CUDA_TRY(cudaStreamSynchronize(st));
+  int warn = 0;
+  for (int i = 0; i < b->n; ++i) {
+    if (h[i].status < 0) return h[i].status;
+    warn |= h[i].warnings;
+    if (stats) {
+      cpa_stats& s = stats[i];
+      memset(&s, 0, sizeof(s));
+      s.iters_done = b->opts[i].iters;
+      s.mode_updates = b->opts[i].iters * b->idx[i]->order;
+      s.warnings = h[i].warnings;
+      s.nnz_sampled_total = h[i].nnz_total;
+      s.sbar_total = h[i].sbar_total;
+      s.kernel_launches = i == 0 ? b->kernels : 0;  // the whole batch is counted once
+    }
+  }
+  return warn;
+}
+
+int cpa_batch_info(const cpa_batch* b, int32_t* sm_budget, int32_t* cand_budgets, double* cand_ms,
+                   int64_t* kernels) {
+  if (!b) return CPA_ERR_ARG;
+  if (sm_budget) *sm_budget = b->budget;
+  for (int c = 0; c < 4; ++c) {
+    if (cand_budgets) cand_budgets[c] = b->tune_budget[c];
+    if (cand_ms) cand_ms[c] = b->tune_ms[c];
+  }
+  if (kernels) *kernels = b->kernels;
+  return CPA_OK;
+}
+
+int cpa_batch_free(cpa_batch* b) {
+  delete b;
+  return CPA_OK;
 }
 
 }  // extern "C"

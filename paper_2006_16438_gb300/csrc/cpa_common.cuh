@@ -168,7 +168,15 @@ struct Arena {
 
 #define CPA_LAUNCH_CHECK() CPA_CUDA_TRY(cudaGetLastError())
 
+// SMs that grid sizes are computed for: the device's count, or a smaller budget set
+// by the caller (per host thread) while it captures work that shares the GPU with
+// other concurrent work (the batched entry point).
+inline int& sm_budget_override() {
+  static thread_local int v = 0;
+  return v;
+}
 inline int num_sms() {
+  if (sm_budget_override() > 0) return sm_budget_override();
   static int sms = 0;
   if (!sms) {
     int dev = 0;

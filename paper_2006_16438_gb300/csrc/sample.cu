@@ -254,6 +254,9 @@ __global__ void k_prepare(SampleParams P, SampleState* S) {
   if (t < P.L.d) {
     const DistInfo* I = P.D.info[t];
     alpha = __ddiv_rn(__ull2double_rn(I->maxq), __ull2double_rn(I->T));
+    // a distribution without mass (all-zero factor) cannot be drawn from: fail now
+    // rather than after reject_cap attempts of every slot
+    if (I->T == 0) set_status(&S->status, CPA_ERR_REJECT_LIMIT);
   }
   double astar = 0.0;
   for (int u = 0; u < P.L.d; ++u) {
@@ -430,7 +433,7 @@ __global__ void __launch_bounds__(kThreads) k_rnd(SampleParams P, SampleState* S
   extern __shared__ __align__(16) uint64_t rnd_smem[];
   __shared__ int64_t sh_sdet, sh_srnd;
   __shared__ double sh_pdet;
-  __shared__ int sh_topk;
+  __shared__ int sh_topk, sh_failed;
   // guide[t][b] (b <= kGuide) = first index i with C_t[i] > mulhi(b << (64 - kGuideBits), T_t),
   // kGuide buckets by the top bits of the draw u; the answer for u lies in
   // [guide[b], guide[b + 1]] with b = u >> (64 - kGuideBits).
@@ -473,6 +476,7 @@ __global__ void __launch_bounds__(kThreads) k_rnd(SampleParams P, SampleState* S
     }
   }
   if (threadIdx.x == 0) {
+    sh_failed = *(volatile int*)&S->status < 0;
     if (finish) {
       // only block 0 (which stores it) and the optional raw weights need p_det
       const DetSummary d = det_summary(P, S, blockIdx.x == 0 || raw_w != nullptr);
@@ -493,6 +497,7 @@ __global__ void __launch_bounds__(kThreads) k_rnd(SampleParams P, SampleState* S
   const double pdet = sh_pdet;
   const uint64_t iter = P.iter_ptr ? *P.iter_ptr : P.iter;
   uint64_t tries = 0;
+  if (sh_failed) return;  // an earlier step failed (e.g. no mass); block-uniform
   // Random slots come from a queue: a lane whose slot is accepted (or gives up)
   // takes the next unclaimed slot, so the lanes of a warp stay busy whatever the
   // number of attempts of each slot.  Attempt a of slot j always uses the Philox

@@ -248,3 +248,46 @@ def exact_lowrank_tensor(dims, rank, seed=0, density=0.5) -> tuple:
 CONFIG_SMALL = dict(name="planted-60x50x40-r4", rank=4, samples=1024, tau=1.0, iters=10, seed=0)
 CONFIG_UBER = dict(name="uber-like-183x24x1140x1717-r25", rank=25, samples=2 ** 17,
                    tau=2.0 ** -17, seed=0)
+
+
+def batch_problems(nprob: int = 64, seed0: int = 0, max_nnz: int = 10 ** 6) -> list:
+    """The batched workload: independent 3- and 4-way planted count tensors of uneven
+    size.  Problem i (seed seed0 + i): order 3 or 4; mode sizes log-uniform in
+    [10^2, 10^5] (redrawn while their product reaches 2^60, or while no nonzero count
+    fits the bounds below); nnz log-uniform in [10^4, max_nnz], at most a tenth of the
+    cells and at least 50 N_k / s for every mode k (N_k = Khatri-Rao rows), so that
+    the sampled right-hand sides are not empty; Zipf(alpha) popularity with alpha
+    uniform in [1.0, 1.3]; CP rank uniform in 5..50; s = 2^u, u uniform in 14..17,
+    lowered to a power of two at most 1/128 of the fewest Khatri-Rao rows of any mode
+    (the method's regime s << N_k: with s near N_k and skewed leverage almost all of the
+    mass is deterministic and the rejection loop of Alg. 2 rarely finds a row below
+    tau) and at least 16 r (mode sizes redrawn otherwise); tau = 1/s.  Returns dicts with coo, rank, samples, tau, zipf_alpha, seed."""
+    out = []
+    for i in range(nprob):
+        g = _rng(seed0 + i, 31)
+        order = int(g.integers(3, 5))
+        alpha = float(g.uniform(1.0, 1.3))
+        rank = int(g.integers(5, 51))
+        u = int(g.integers(14, 18))
+        lg_nnz = g.uniform(4.0, np.log10(max_nnz))
+        while True:
+            dims = tuple(int(round(10 ** g.uniform(2.0, 5.0))) for _ in range(order))
+            cells = float(np.prod([float(n) for n in dims]))
+            if cells >= 2.0 ** 60:
+                continue
+            fewest = min(cells / n for n in dims)
+            s = 2 ** u
+            while s > fewest / 128 and s > 32:
+                s //= 2
+            if s < 16 * rank:  # far more sampled rows than unknowns per row of A_k
+                continue
+            # at least ~50 sampled nonzeros expected in every mode (s nnz / N_k >= 50)
+            most = max(cells / n for n in dims)
+            lo = max(1e4, 50.0 * most / s)
+            hi = min(float(max_nnz), 0.1 * cells)
+            if lo <= hi:
+                break
+        nnz = int(round(min(max(10 ** lg_nnz, lo), hi)))
+        coo = planted_cp_tensor(dims, rank, target_nnz=nnz, seed=seed0 + i, zipf_alpha=alpha)
+        out.append(dict(coo=coo, rank=rank, samples=s, tau=1.0 / s, zipf_alpha=alpha, seed=seed0 + i))
+    return out
