@@ -296,6 +296,7 @@ struct Plan {
   cudaGraph_t g_iter = nullptr, g_init = nullptr, g_fit = nullptr;  // kept to compose the epoch
   cudaGraphExec_t epoch_exec = nullptr;  // init + epoch_iters iterations + fit, one launch
   int epoch_iters = -1;
+  bool epoch_fit = false;
   int64_t k_epoch = 0;
   cudaStream_t cap_stream = nullptr;
   Profiler gprof;  // event nodes captured into the graph (profile = 1)
@@ -601,7 +602,7 @@ struct Plan {
   // the outer iteration and the fit, as child graphs in a chain.  A single launch
   // per call leaves the GPU queue full whatever the host does meanwhile.
   int build_epoch(int iters, bool with_fit) {
-    if (epoch_exec && epoch_iters == iters) return CPA_OK;
+    if (epoch_exec && epoch_iters == iters && epoch_fit == with_fit) return CPA_OK;
     if (epoch_exec) {
       cudaGraphExecDestroy(epoch_exec);
       epoch_exec = nullptr;
@@ -626,6 +627,7 @@ struct Plan {
     cudaGraphDestroy(eg);
     if (rc < 0) return rc;
     epoch_iters = iters;
+    epoch_fit = with_fit;
     k_epoch = k_init + (int64_t)iters * k_iter + (with_fit ? k_fit : 0);
     return CPA_OK;
   }

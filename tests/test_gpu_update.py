@@ -104,3 +104,19 @@ def test_mixed_small_planted_fit_close_to_fp64():
     mix = cpa.cp_arls_lev(gi, [torch.from_numpy(a).cuda() for a in init], rank=4, samples=1024, tau=1.0,
                           iters=10, seed=0, precision=binding.MIXED)
     assert abs(mix.fit - f64.fit) < 1e-2
+
+
+def test_epoch_graph_keyed_by_fit_mode():
+    """The one-graph call is cached per (iterations, fit): a call with the fit after
+    one without it (same index, same options otherwise) still computes the fit."""
+    coo = synth.small_planted_tensor(0)
+    init = synth.gaussian_factors(coo.dims, 4, seed=0)
+    gi = cpa.cpa_index_build(coo)
+    a = cpa.cp_arls_lev(gi, [torch.from_numpy(x).cuda() for x in init], rank=4, samples=1024, tau=1.0, iters=2,
+                        seed=0, fit_mode=binding.FIT_NONE)
+    assert np.isnan(a.fit)
+    b = cpa.cp_arls_lev(gi, [torch.from_numpy(x).cuda() for x in init], rank=4, samples=1024, tau=1.0, iters=2,
+                        seed=0, fit_mode=binding.FIT_EXACT)
+    c = cpa.cp_arls_lev(cpa.cpa_index_build(coo), [torch.from_numpy(x).cuda() for x in init], rank=4,
+                        samples=1024, tau=1.0, iters=2, seed=0)
+    assert np.isfinite(b.fit) and abs(b.fit - c.fit) < 1e-12
