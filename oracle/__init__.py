@@ -115,6 +115,10 @@ def _declare(lib):
     lib.orc_mode_update_once.restype = I32
     lib.orc_cp_als.argtypes = [P, I32, I32, P, P, P]
     lib.orc_cp_als.restype = I32
+    lib.orc_fit_sample.argtypes = [P, I64, C.c_double, U64, I32, P, P, P, P]
+    lib.orc_fit_sample.restype = I32
+    lib.orc_fit_estimate.argtypes = [P, P, P, P, P, I64, P, P, I32, P]
+    lib.orc_fit_estimate.restype = C.c_double
 
 
 def _ptr(a):
@@ -335,6 +339,44 @@ def fit(index: Index, factors, lam):
     fs, fp = _factor_ptrs(factors)
     lam = _c(lam, np.float64)
     return float(_lib().orc_fit(index.h, C.cast(fp, C.c_void_p), _ptr(lam), lam.shape[0]))
+
+
+class FitSample:
+    """Stratified element sample of the estimated fit (Section 5.4): coords
+    (order x S int32), xs (S values, nonzero samples first), s_nz, s_z, zero attempts
+    and the weights phi = (nnz / s_nz, (prod n - nnz) / s_z)."""
+
+    def __init__(self, coords, xs, counts, phi):
+        self.coords, self.xs = coords, xs
+        self.s_nz, self.s_z, self.attempts = (int(c) for c in counts)
+        self.phi = phi
+
+
+def fit_sample(index: Index, s_fit, alpha=0.5, seed=0, reject_cap=4096) -> FitSample:
+    coords = np.zeros((index.order, int(s_fit)), dtype=np.int32)
+    xs = np.zeros(int(s_fit))
+    counts = np.zeros(3, dtype=np.int64)
+    phi = np.zeros(2)
+    rc = _lib().orc_fit_sample(index.h, int(s_fit), float(alpha), int(seed), int(reject_cap), _ptr(coords),
+                               _ptr(xs), _ptr(counts), _ptr(phi))
+    if rc < 0:
+        raise OracleError(rc, "fit_sample")
+    S = int(counts[0] + counts[1])
+    return FitSample(coords[:, :S].copy(), xs[:S].copy(), counts, phi)
+
+
+def fit_estimate(index: Index, sample: FitSample, factors, lam):
+    """(estimated fit 1 - sqrt(F_hat) / ||X||, F_hat) of Section 5.4."""
+    fs, fp = _factor_ptrs(factors)
+    lam = _c(lam, np.float64)
+    coords = _c(sample.coords, np.int32)
+    xs = _c(sample.xs, np.float64)
+    counts = np.array([sample.s_nz, sample.s_z, sample.attempts], dtype=np.int64)
+    phi = _c(sample.phi, np.float64)
+    F = C.c_double(0.0)
+    f = _lib().orc_fit_estimate(index.h, _ptr(coords), _ptr(xs), _ptr(counts), _ptr(phi), coords.shape[1],
+                                C.cast(fp, C.c_void_p), _ptr(lam), lam.shape[0], C.byref(F))
+    return float(f), F.value
 
 
 def cp_arls_lev(index: Index, factors, *, rank, samples, tau=1.0, iters=10, epoch_len=5,

@@ -750,6 +750,130 @@ double orc_fit(const orc_index* X, const double* const* factors, const double* l
 }
 
 /* ------------------------------------------------------------------------ */
+/* Estimated fit (Section 5.4): a stratified sample of tensor elements,      */
+/* ceil(alpha s_fit) nonzeros and the rest zeros, each uniform over its      */
+/* stratum; the zeros by rejection of uniform coordinates.  The squared      */
+/* residual of each sampled element is weighted by the stratum's size over   */
+/* its sample count.                                                        */
+/* ------------------------------------------------------------------------ */
+static const orc_index* g_lin_X; /* comparator context (the oracle is single-threaded) */
+
+/* compare two coordinates by the linear index of Eq. 2.2 over all modes (mode 0
+ * fastest): the last mode is the most significant digit */
+static int cmp_coord(const int32_t* a, const int32_t* b, int order) {
+  for (int m = order - 1; m >= 0; --m)
+    if (a[m] != b[m]) return a[m] < b[m] ? -1 : 1;
+  return 0;
+}
+
+static int cmp_nz_linear(const void* pa, const void* pb) {
+  const int64_t ea = *(const int64_t*)pa, eb = *(const int64_t*)pb;
+  int32_t a[16], b[16];
+  for (int m = 0; m < g_lin_X->order; ++m) {
+    a[m] = g_lin_X->coo_idx[m][ea];
+    b[m] = g_lin_X->coo_idx[m][eb];
+  }
+  return cmp_coord(a, b, g_lin_X->order);
+}
+
+/* floor(u * n / 2^64) */
+static int64_t scale_u64(uint64_t u, int64_t n) {
+  return (int64_t)(((unsigned __int128)u * (uint64_t)n) >> 64);
+}
+
+int orc_fit_sample(const orc_index* X, int64_t s_fit, double alpha, uint64_t seed, int reject_cap,
+                   int32_t* coords, double* xs, int64_t* counts, double* phi) {
+  const int order = X->order;
+  const int64_t nnz = X->nnz;
+  if (s_fit < 1 || !(alpha > 0.0 && alpha <= 1.0) || nnz < 1) return ORC_ERR_ARG;
+  /* number of elements, prod n (rounded in FP64 when above 2^53) */
+  double cells = 1.0;
+  for (int m = 0; m < order; ++m) cells *= (double)X->dims[m];
+  const int has_zeros = cells > (double)nnz;
+  int64_t s_nz = (int64_t)ceil(alpha * (double)s_fit);
+  if (s_nz > s_fit) s_nz = s_fit;
+  const int64_t s_z = has_zeros ? s_fit - s_nz : 0;
+  /* the nonzeros in ascending linear-index order */
+  int64_t* order_e = (int64_t*)malloc(sizeof(int64_t) * (size_t)nnz);
+  if (!order_e) return ORC_ERR_OOM;
+  for (int64_t e = 0; e < nnz; ++e) order_e[e] = e;
+  g_lin_X = X;
+  qsort(order_e, (size_t)nnz, sizeof(int64_t), cmp_nz_linear);
+  const uint64_t key[2] = {seed, 0};
+  for (int64_t j = 0; j < s_nz; ++j) {
+    const uint64_t ctr[4] = {(uint64_t)j, 0, 2ull << 32, 0};
+    uint64_t out[4];
+    orc_philox4x64_10(ctr, key, out);
+    const int64_t e = order_e[scale_u64(out[0], nnz)];
+    for (int m = 0; m < order; ++m) coords[(size_t)m * s_fit + j] = X->coo_idx[m][e];
+    xs[j] = X->coo_val[e];
+  }
+  int64_t attempts = 0;
+  for (int64_t j = 0; j < s_z; ++j) {
+    int accepted = 0;
+    for (int a = 0; a < reject_cap && !accepted; ++a) {
+      int32_t c[16];
+      for (int m = 0; m < order; ++m) {
+        const uint64_t ctr[4] = {(uint64_t)j, (uint64_t)a, (2ull << 32) | 1ull | ((uint64_t)(m / 4) << 16), 0};
+        uint64_t out[4];
+        orc_philox4x64_10(ctr, key, out);
+        c[m] = (int32_t)scale_u64(out[m % 4], X->dims[m]);
+      }
+      ++attempts;
+      /* is c a nonzero?  bisection over the sorted nonzeros */
+      int64_t lo = 0, hi = nnz;
+      int hit = 0;
+      while (lo < hi) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        int32_t b[16];
+        for (int m = 0; m < order; ++m) b[m] = X->coo_idx[m][order_e[mid]];
+        const int cmp = cmp_coord(b, c, order);
+        if (cmp == 0) { hit = 1; break; }
+        if (cmp < 0) lo = mid + 1; else hi = mid;
+      }
+      if (!hit) {
+        for (int m = 0; m < order; ++m) coords[(size_t)m * s_fit + s_nz + j] = c[m];
+        xs[s_nz + j] = 0.0;
+        accepted = 1;
+      }
+    }
+    if (!accepted) {
+      free(order_e);
+      return ORC_ERR_REJECT_LIMIT;
+    }
+  }
+  free(order_e);
+  counts[0] = s_nz;
+  counts[1] = s_z;
+  counts[2] = attempts;
+  phi[0] = s_nz > 0 ? (double)nnz / (double)s_nz : 0.0;
+  phi[1] = s_z > 0 ? (cells - (double)nnz) / (double)s_z : 0.0;
+  return ORC_OK;
+}
+
+double orc_fit_estimate(const orc_index* X, const int32_t* coords, const double* xs,
+                        const int64_t* counts, const double* phi, int64_t stride,
+                        const double* const* factors, const double* lambda, int r, double* F_hat_out) {
+  const int order = X->order;
+  double nx2 = 0.0;
+  for (int64_t e = 0; e < X->nnz; ++e) nx2 += X->coo_val[e] * X->coo_val[e];
+  const int64_t S = counts[0] + counts[1];
+  double F = 0.0;
+  for (int64_t j = 0; j < S; ++j) {
+    double mval = 0.0;
+    for (int c = 0; c < r; ++c) {
+      double v = lambda[c];
+      for (int m = 0; m < order; ++m) v *= factors[m][(size_t)coords[(size_t)m * stride + j] * r + c];
+      mval += v;
+    }
+    const double res = mval - xs[j];
+    F += (j < counts[0] ? phi[0] : phi[1]) * res * res;
+  }
+  if (F_hat_out) *F_hat_out = F;
+  return nx2 > 0.0 ? 1.0 - sqrt(F) / sqrt(nx2) : 0.0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Alg. 3                                                                   */
 /* ------------------------------------------------------------------------ */
 static int refresh_mode(orc_state* st, int m, const double* A) {

@@ -157,6 +157,31 @@ int orc_mode_update_once(const orc_index* X, int r, int k, double* const* factor
                          int64_t det_cap, int reject_cap, uint64_t* idx, uint32_t* cnt,
                          double* wgt, int64_t* stats, double* pdet);
 
+/* Estimated fit (Section 5.4).  orc_fit_sample draws the stratified sample once:
+ * s_nz = ceil(alpha * s_fit) nonzeros and s_z = s_fit - s_nz zero elements (the
+ * paper's floor((1 - alpha) s_fit) in exact arithmetic), each uniform over its
+ * stratum, with replacement; s_z = 0 when the tensor has no zero element.
+ *   nonzero slot j: u = word 0 of Philox(ctr = (j, 0, 2<<32, 0), key = (seed, 0));
+ *     the element is the nonzero at position floor(u nnz / 2^64) in ascending order
+ *     of the linear index of Eq. 2.2 over all modes (mode 0 fastest);
+ *   zero slot j, attempt a: i_m = floor(u_m n_m / 2^64), u_m = word m%4 of
+ *     Philox(ctr = (j, a, 2<<32 | 1 | (m/4)<<16, 0), key = (seed, 0)); the attempt is
+ *     rejected if (i_0..i_{D-1}) is a nonzero; more than reject_cap attempts is
+ *     ORC_ERR_REJECT_LIMIT.
+ * Outputs: coords (order x s_fit int32, row m at coords + m*s_fit), xs (s_fit values,
+ * 0 for zero samples; nonzero samples first), counts = {s_nz, s_z, zero attempts},
+ * phi = {nnz / s_nz, (prod n - nnz) / s_z} (0 for an empty stratum).
+ * 0 < alpha <= 1, s_fit >= 1 and nnz >= 1, else ORC_ERR_ARG. */
+int orc_fit_sample(const orc_index* X, int64_t s_fit, double alpha, uint64_t seed, int reject_cap,
+                   int32_t* coords, double* xs, int64_t* counts, double* phi);
+
+/* F_hat = sum_j phi_j (m_j - x_j)^2 over the sample (m_j the model's entry,
+ * sum_c lambda_c prod_m A_m(i_m, c)); returns 1 - sqrt(F_hat) / ||X||.  *F_hat_out
+ * (may be NULL) receives F_hat. */
+double orc_fit_estimate(const orc_index* X, const int32_t* coords, const double* xs,
+                        const int64_t* counts, const double* phi, int64_t stride,
+                        const double* const* factors, const double* lambda, int r, double* F_hat_out);
+
 /* Standard CP-ALS (exact MTTKRP) with a fixed iteration count. */
 int orc_cp_als(const orc_index* X, int r, int iters, double* const* factors, double* lambda,
                double* fit);

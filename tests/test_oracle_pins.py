@@ -489,3 +489,136 @@ def test_theorem_5_2_bound_holds(orc):
         B = (res["A"] * res["lam"]).T
         ok += np.linalg.norm(Z @ B - Y) ** 2 <= (1 + eps) * ropt
     assert ok >= (1 - delta) * trials
+
+
+# --------------------------------------------------------------------------- estimated fit (Section 5.4)
+def _brute_F(coo, factors, lam):
+    """||X - M||^2 summed over every cell of the dense tensor."""
+    M = np.zeros(coo.dims)
+    for j in range(lam.shape[0]):
+        T = lam[j]
+        for A in factors:
+            T = np.multiply.outer(T, A[:, j])
+        M += T
+    return float(((coo.dense() - M) ** 2).sum())
+
+
+def test_fit_sample_draws_follow_their_definition(orc):
+    """Every draw recomputed from numpy's Philox: nonzero slot j takes the nonzero at
+    floor(u nnz / 2^64) in ascending linear-index order (np.lexsort, last mode most
+    significant); zero slot j takes the first attempt whose uniform coordinates
+    (floor(u_m n_m / 2^64)) miss every nonzero."""
+    coo = synth.random_sparse_tensor((5, 7, 3, 4), 150, seed=4)
+    X = orc.Index(coo)
+    s_fit, alpha, seed = 301, 0.3, 77
+    fs = orc.fit_sample(X, s_fit, alpha=alpha, seed=seed)
+    cells = math.prod(coo.dims)
+    s_nz = math.ceil(alpha * s_fit)
+    assert (fs.s_nz, fs.s_z) == (s_nz, s_fit - s_nz)
+    assert fs.phi[0] == coo.nnz / s_nz and fs.phi[1] == (cells - coo.nnz) / (s_fit - s_nz)
+    order = np.lexsort(tuple(coo.idx))
+    nz_set = set(zip(*(i.tolist() for i in coo.idx)))
+    for j in range(s_nz):
+        u = int(_ref.numpy_philox_block([j, 0, 2 << 32, 0], [seed, 0])[0])
+        e = order[(u * coo.nnz) >> 64]
+        assert tuple(int(c) for c in fs.coords[:, j]) == tuple(int(i[e]) for i in coo.idx)
+        assert fs.xs[j] == coo.vals[e]
+    attempts = 0
+    for j in range(s_fit - s_nz):
+        for a in range(4096):
+            c = []
+            for m, n in enumerate(coo.dims):
+                u = int(_ref.numpy_philox_block([j, a, (2 << 32) | 1 | ((m // 4) << 16), 0], [seed, 0])[m % 4])
+                c.append((u * n) >> 64)
+            attempts += 1
+            if tuple(c) not in nz_set:
+                break
+        assert tuple(int(x) for x in fs.coords[:, s_nz + j]) == tuple(c)
+        assert fs.xs[s_nz + j] == 0.0
+    assert fs.attempts == attempts
+
+
+def test_fit_sample_strata_are_uniform(orc):
+    """Chi-square: nonzero draws uniform over the nonzeros, zero draws uniform over
+    the zero cells and never on a nonzero."""
+    from scipy import stats
+    coo = synth.random_sparse_tensor((4, 3, 2), 7, seed=2)
+    X = orc.Index(coo)
+    fs = orc.fit_sample(X, 40000, alpha=0.5, seed=5)
+    lin = lambda c: c[0] + 4 * (c[1] + 3 * c[2])  # noqa: E731
+    nz = {lin(c): e for e, c in enumerate(zip(*(i.tolist() for i in coo.idx)))}
+    cnt_nz = np.zeros(coo.nnz)
+    for j in range(fs.s_nz):
+        e = nz[lin(fs.coords[:, j].tolist())]
+        cnt_nz[e] += 1
+        assert fs.xs[j] == coo.vals[e]
+    zeros = [c for c in range(24) if c not in nz]
+    cnt_z = np.zeros(24)
+    for j in range(fs.s_nz, fs.s_nz + fs.s_z):
+        cnt_z[lin(fs.coords[:, j].tolist())] += 1
+    assert cnt_z[list(nz)].sum() == 0
+    assert stats.chisquare(cnt_nz).pvalue > 1e-4
+    assert stats.chisquare(cnt_z[zeros]).pvalue > 1e-4
+
+
+def test_fit_estimate_exact_lowrank_is_one(orc):
+    """A sparse tensor that is exactly its CP model: every sampled residual is zero
+    (up to rounding) in both strata, so the estimated fit is 1."""
+    coo, lam, facs = synth.exact_lowrank_tensor((9, 8, 7), 3, seed=1, density=0.4)
+    X = orc.Index(coo)
+    fs = orc.fit_sample(X, 5000, alpha=0.5, seed=3)
+    assert fs.s_z > 0 and fs.s_nz > 0
+    fit, F = orc.fit_estimate(X, fs, facs, lam)
+    assert F <= 1e-24 * float((coo.vals ** 2).sum()) and fit > 1 - 1e-12
+    # a model with one factor's rows permuted is far from X in both strata
+    bad = [facs[0], facs[1][::-1].copy(), facs[2]]
+    fit_bad, _ = orc.fit_estimate(X, fs, bad, lam)
+    assert fit_bad < 0.9
+
+
+def test_fit_estimate_is_unbiased(orc):
+    """E[F_hat] = ||X - M||^2 (Section 5.4's weights make each stratum's sum
+    unbiased): the mean over 400 independent samples is within 5 standard errors of
+    the brute-force value, and the estimate with the zero-stratum weight
+    prod(n) / s_z (instead of (prod(n) - nnz) / s_z) is not."""
+    coo = synth.random_sparse_tensor((6, 5, 4), 40, seed=9)
+    X = orc.Index(coo)
+    g = np.random.default_rng(0)
+    facs = [g.uniform(0.0, 1.0, size=(n, 2)) for n in coo.dims]
+    lam = np.array([1.0, 0.5])
+    F_true = _brute_F(coo, facs, lam)
+    Fs, Fs_wrong = [], []
+    cells = math.prod(coo.dims)
+    for seed in range(400):
+        fs = orc.fit_sample(X, 64, alpha=0.5, seed=seed)
+        Fs.append(orc.fit_estimate(X, fs, facs, lam)[1])
+        fs.phi = np.array([fs.phi[0], cells / fs.s_z])
+        Fs_wrong.append(orc.fit_estimate(X, fs, facs, lam)[1])
+    Fs, Fs_wrong = np.array(Fs), np.array(Fs_wrong)
+    se = Fs.std(ddof=1) / math.sqrt(Fs.size)
+    assert abs(Fs.mean() - F_true) < 5 * se
+    assert abs(Fs_wrong.mean() - F_true) > 5 * se
+
+
+def test_fit_sample_edge_cases(orc):
+    # a tensor with no zero cell: the zero stratum is empty and the estimate exact
+    # in expectation from the nonzeros alone
+    dims = (3, 2, 2)
+    full = np.stack(np.unravel_index(np.arange(12), dims, order="F"))
+    coo = synth.Coo(dims, [c.astype(np.int32) for c in full], np.arange(1.0, 13.0))
+    X = orc.Index(coo)
+    fs = orc.fit_sample(X, 10, alpha=0.5, seed=1)
+    assert (fs.s_nz, fs.s_z) == (5, 0) and fs.phi[1] == 0.0
+    # alpha = 1: nonzeros only; alpha outside (0, 1] and s_fit < 1 are errors
+    coo2 = synth.random_sparse_tensor((5, 4, 3), 10, seed=3)
+    X2 = orc.Index(coo2)
+    fs = orc.fit_sample(X2, 17, alpha=1.0, seed=2)
+    assert (fs.s_nz, fs.s_z) == (17, 0)
+    for bad in (dict(s_fit=0, alpha=0.5), dict(s_fit=8, alpha=0.0), dict(s_fit=8, alpha=1.5)):
+        with pytest.raises(orc.OracleError):
+            orc.fit_sample(X2, bad["s_fit"], alpha=bad["alpha"], seed=0)
+    # a nearly full tensor with a rejection cap of 1 hits the limit
+    coo3 = synth.random_sparse_tensor((4, 4, 4), 63, seed=1)
+    with pytest.raises(orc.OracleError) as ei:
+        orc.fit_sample(orc.Index(coo3), 200, alpha=0.5, seed=0, reject_cap=1)
+    assert ei.value.code == orc.ERR_REJECT_LIMIT
