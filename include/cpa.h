@@ -60,6 +60,8 @@ extern "C" {
                            probabilities and lambda in FP64 */
 #define CPA_FIT_NONE 0  /* no fit computed (fit output set to NaN) */
 #define CPA_FIT_EXACT 1 /* exact fit of Eq. 5.1 after the run (and per epoch if tol > 0) */
+#define CPA_FIT_ESTIMATED 2 /* estimated fit of Section 5.4 from a stratified sample of
+                               fit_samples elements (fraction fit_alpha nonzeros) */
 
 /* Sparse tensor in coordinate format (Section 5.3: (d+2) nnz storage).
  *   order      number of modes D = d + 1, 2 <= D <= 8
@@ -97,7 +99,12 @@ typedef struct {
  *   iter_offset added to the outer iteration number in the Philox counter, so a run
  *               can be resumed with the same stream of draws
  *   precision   CPA_FP64 or CPA_MIXED
- *   fit_mode    CPA_FIT_EXACT or CPA_FIT_NONE
+ *   fit_mode    CPA_FIT_EXACT, CPA_FIT_ESTIMATED or CPA_FIT_NONE
+ *   fit_samples s_fit, elements in the sample of the estimated fit (>= 1; default
+ *               2^27, the paper's Section 6 setting); used with CPA_FIT_ESTIMATED
+ *   fit_alpha   fraction alpha in (0, 1] of the sample taken from the nonzeros
+ *               (0.5); the sample is drawn once per (index, seed, fit_samples,
+ *               fit_alpha, reject_cap) and reused by later calls
  *   det_cap     largest candidate product the deterministic search may enumerate
  *   reject_cap  largest number of draws of one random slot
  *   profile     1: time the stages of every update with CUDA events on `stream`
@@ -115,6 +122,8 @@ typedef struct {
   uint64_t iter_offset;
   int32_t precision;
   int32_t fit_mode;
+  int64_t fit_samples;
+  double fit_alpha;
   int64_t det_cap;
   int32_t reject_cap;
   int32_t profile;
@@ -151,8 +160,8 @@ typedef struct {
 typedef struct cpa_index cpa_index; /* opaque; owns device memory */
 
 /* Fills *opt with: rank 10, samples 2^17, tau 2^-17, iters 10, epoch_len 5,
- * patience 3, tol 0, seed 0, iter_offset 0, CPA_FP64, CPA_FIT_EXACT,
- * det_cap 2^24, reject_cap 4096, stream NULL. */
+ * patience 3, tol 0, seed 0, iter_offset 0, CPA_FP64, CPA_FIT_EXACT, fit_samples
+ * 2^27, fit_alpha 0.5, det_cap 2^24, reject_cap 4096, stream NULL. */
 void cpa_options_default(cpa_options* opt);
 
 /* Human-readable text of a status code (static string). */
@@ -194,7 +203,10 @@ int cpa_index_export(const cpa_index* index, int32_t mode, uint64_t* keys, uint6
  *   factors   array (host) of `order` pointers to n_k x r row-major doubles; in:
  *             initial guess, out: factors with unit-norm columns
  *   io_on_device  1 if lambda, fit and factors[k] are device pointers, 0 if host
- *   fit       out: fit of Eq. 5.1 (NaN if fit_mode is CPA_FIT_NONE); may be NULL
+ *   fit       out: fit of Eq. 5.1, or its estimate (Section 5.4) with
+ *             CPA_FIT_ESTIMATED (the element sample of cpa_fit_sample with the
+ *             run's seed, drawn at the first call and reused while the options
+ *             keep it); NaN if fit_mode is CPA_FIT_NONE; may be NULL
  *   stats     out: statistics; may be NULL
  * Errors: CPA_ERR_ARG, CPA_ERR_REJECT_LIMIT, CPA_ERR_DET_CAP, CPA_ERR_OOM,
  * CPA_ERR_CUDA.  Warnings: CPA_WARN_SINGULAR_GRAM, CPA_WARN_RANK_DEFICIENT_LEV. */
@@ -207,7 +219,8 @@ int cp_arls_lev(const cpa_index* index, const cpa_options* opt, double* lambda,
  * mode-k fibre index), G = Hadamard product of the other factors' Grams, A_k =
  * M G^{-1} (FP64 factorisation, pseudo-inverse fallback), columns normalised into
  * lambda.  Runs exactly opt->iters outer iterations; uses opt->rank, iters,
- * precision (CPA_FP64 or CPA_MIXED: FP32 factors and MTTKRP), fit_mode, stream;
+ * precision (CPA_FP64 or CPA_MIXED: FP32 factors and MTTKRP), fit_mode
+ * (CPA_FIT_NONE or CPA_FIT_EXACT; CPA_FIT_ESTIMATED is CPA_ERR_ARG), stream;
  * samples, tau, seed and the epoch rule are ignored.  Arguments, ownership and
  * errors as cp_arls_lev (stats: iters_done, mode_updates, warnings only). */
 int cp_als(const cpa_index* index, const cpa_options* opt, double* lambda, double* const* factors,
@@ -265,6 +278,45 @@ int cp_arls_lev_coo(const cpa_coo* coo, const cpa_options* opt, double* lambda,
 int cpa_mode_update(const cpa_index* index, const cpa_options* opt, int32_t mode_k, uint64_t iter,
                     double* const* factors, double* lambda, uint64_t* idx, uint32_t* cnt, double* wgt,
                     int64_t* counts, double* pdet);
+
+/* ---- estimated fit (Section 5.4) ------------------------------------------------ */
+
+/* Draws the stratified element sample of the estimated fit: s_nz = ceil(alpha *
+ * fit_samples) nonzeros and s_z = fit_samples - s_nz zero cells (the paper's
+ * floor((1 - alpha) s_fit) in exact arithmetic; 0 if the tensor has no zero cell),
+ * each uniform over its stratum, with replacement.
+ *   nonzero slot j: u = word 0 of Philox4x64-10(counter (j, 0, 2<<32, 0), key
+ *     (seed, 0)); the nonzero at position floor(u nnz / 2^64) in ascending order of
+ *     the linear index of Eq. 2.2 over all modes (mode 0 fastest)
+ *   zero slot j, attempt a: i_m = floor(u_m n_m / 2^64) with u_m word m % 4 of
+ *     Philox(counter (j, a, 2<<32 | 1 | (m/4)<<16, 0), key (seed, 0)); the attempt
+ *     is rejected if the cell is a nonzero
+ *   coords  device, order x fit_samples int32 (row m at coords + m * fit_samples)
+ *   xs      device, fit_samples doubles: the values (nonzero samples first, then
+ *           zeros with value 0)
+ *   counts  host out: {s_nz, s_z, zero-cell attempts}
+ *   phi     host out: {nnz / s_nz, (prod n - nnz) / s_z} (0 for an empty stratum)
+ * Errors: CPA_ERR_ARG (fit_samples < 1, alpha outside (0, 1], nnz = 0,
+ * reject_cap < 1), CPA_ERR_REJECT_LIMIT (a zero slot drew reject_cap nonzeros in a
+ * row), CPA_ERR_OOM, CPA_ERR_CUDA. */
+int cpa_fit_sample(const cpa_index* index, int64_t fit_samples, double fit_alpha, uint64_t seed,
+                   int32_t reject_cap, int32_t* coords, double* xs, int64_t* counts, double* phi,
+                   void* stream);
+
+/* Estimated fit of a model [[lambda; A_0..A_{D-1}]] on a sample from cpa_fit_sample:
+ * F_hat = sum_j phi_j (m_j - x_j)^2, m_j = sum_c lambda_c prod_m A_m(i_m, c), and
+ * *fit = 1 - sqrt(F_hat) / ||X||.
+ *   coords, xs  device, as cpa_fit_sample wrote them (row stride `stride`)
+ *   counts, phi host, as cpa_fit_sample returned them
+ *   lambda      device, r doubles; factors: host array of order device pointers to
+ *               n_m x r row-major doubles
+ *   precision   CPA_FP64 (every product in FP64) or CPA_MIXED (the factors rounded
+ *               to FP32 and each model value formed in FP32; residuals in FP64)
+ *   fit, F_hat  host out (F_hat may be NULL)
+ * Errors: CPA_ERR_ARG, CPA_ERR_OOM, CPA_ERR_CUDA. */
+int cpa_fit_estimate(const cpa_index* index, const int32_t* coords, const double* xs, const int64_t* counts,
+                     const double* phi, int64_t stride, const double* lambda, const double* const* factors,
+                     int32_t r, int32_t precision, double* fit, double* F_hat, void* stream);
 
 /* ---- stage entry points (each one step of the per-mode update) --------------- */
 

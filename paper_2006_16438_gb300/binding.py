@@ -35,12 +35,14 @@ FP64 = 0
 MIXED = 1
 FIT_NONE = 0
 FIT_EXACT = 1
+FIT_ESTIMATED = 2
 
 EXPORTED = [
     "cpa_options_default", "cpa_strerror", "cpa_index_build", "cpa_index_free", "cpa_index_info",
     "cpa_index_export", "cp_arls_lev", "cp_arls_lev_coo", "cpa_philox4x64", "cpa_leverage",
     "cpa_cdf", "cpa_skrp_lev", "cpa_sampled_mttkrp", "cpa_solve", "cpa_fit", "cpa_leverage_noalloc",
     "cpa_mode_update", "cp_als", "cpa_batch_create", "cpa_batch_run", "cpa_batch_info", "cpa_batch_free",
+    "cpa_fit_sample", "cpa_fit_estimate",
 ]
 
 
@@ -60,7 +62,8 @@ class Options(C.Structure):
     _fields_ = [("rank", C.c_int32), ("samples", C.c_int64), ("tau", C.c_double), ("iters", C.c_int32),
                 ("epoch_len", C.c_int32), ("patience", C.c_int32), ("tol", C.c_double),
                 ("seed", C.c_uint64), ("iter_offset", C.c_uint64), ("precision", C.c_int32),
-                ("fit_mode", C.c_int32), ("det_cap", C.c_int64), ("reject_cap", C.c_int32),
+                ("fit_mode", C.c_int32), ("fit_samples", C.c_int64), ("fit_alpha", C.c_double),
+                ("det_cap", C.c_int64), ("reject_cap", C.c_int32),
                 ("profile", C.c_int32), ("stream", C.c_void_p)]
 
 
@@ -129,6 +132,8 @@ def _declare(lib):
         "cpa_sampled_mttkrp": ([P, I32, P, I32, P, P, I64, P, P, P, P], I32),
         "cpa_solve": ([P, P, I64, I32, P, P, P], I32),
         "cpa_fit": ([P, P, P, I32, P, P], I32),
+        "cpa_fit_sample": ([P, I64, D, U64, I32, P, P, P, P, P], I32),
+        "cpa_fit_estimate": ([P, P, P, P, P, I64, P, P, I32, I32, P, P, P], I32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -273,7 +278,8 @@ class Result:
 
 def cp_arls_lev(index: Index, factors, *, rank, samples, tau=1.0, iters=10, epoch_len=5, patience=3,
                 tol=0.0, seed=0, iter_offset=0, fit_mode=FIT_EXACT, det_cap=1 << 24,
-                reject_cap=4096, on_device=True, profile=0, out=None, precision=FP64) -> Result:
+                reject_cap=4096, on_device=True, profile=0, out=None, precision=FP64,
+                fit_samples=1 << 27, fit_alpha=0.5) -> Result:
     """Alg. 3 on the GPU.  ``factors``: list of CUDA float64 tensors (n_k x rank), or
     numpy arrays with on_device=False.  Returns a Result with new factor copies."""
     torch = _torch()
@@ -281,7 +287,7 @@ def cp_arls_lev(index: Index, factors, *, rank, samples, tau=1.0, iters=10, epoc
                         epoch_len=int(epoch_len), patience=int(patience), tol=float(tol),
                         seed=int(seed), iter_offset=int(iter_offset), fit_mode=int(fit_mode),
                         det_cap=int(det_cap), reject_cap=int(reject_cap), profile=int(profile),
-                        precision=int(precision))
+                        precision=int(precision), fit_samples=int(fit_samples), fit_alpha=float(fit_alpha))
     o.stream = _stream()
     stats = Stats()
     fit = C.c_double(0.0)
@@ -338,7 +344,10 @@ class Batch:
             opts[i] = default_options(rank=p["rank"], samples=int(p["samples"]), tau=float(p["tau"]),
                                       iters=int(p["iters"]), seed=int(p.get("seed", 0)),
                                       iter_offset=int(p.get("iter_offset", 0)),
-                                      precision=int(p.get("precision", FP64)), stream=_stream())
+                                      precision=int(p.get("precision", FP64)),
+                                      fit_mode=int(p.get("fit_mode", FIT_EXACT)),
+                                      fit_samples=int(p.get("fit_samples", 1 << 27)),
+                                      fit_alpha=float(p.get("fit_alpha", 0.5)), stream=_stream())
         self._fac_arrays = [_ptr_array([f.data_ptr() for f in fs]) for fs in self.factors]
         fac_ptrs = (C.c_void_p * n)(*[C.cast(a, C.c_void_p) for a in self._fac_arrays])
         idx = (C.c_void_p * n)(*[p["index"].h.value for p in problems])
@@ -522,3 +531,46 @@ def cpa_fit(index: Index, factors, lam):
     _check(_lib().cpa_fit(index.h, _ptr_array([f.data_ptr() for f in fs]), _ptr(lam), lam.shape[0],
                           C.byref(out), _stream()), "cpa_fit")
     return out.value
+
+
+# --------------------------------------------------------------------------- estimated fit
+@dataclass
+class FitSample:
+    """Element sample of the estimated fit (Section 5.4) on the device: coords
+    (order x S int32 CUDA tensor), xs (S float64), s_nz, s_z, zero-cell attempts,
+    phi = (nnz / s_nz, (prod n - nnz) / s_z)."""
+    coords: object
+    xs: object
+    s_nz: int
+    s_z: int
+    attempts: int
+    phi: tuple
+
+
+def cpa_fit_sample(index: Index, fit_samples, alpha=0.5, seed=0, reject_cap=4096) -> FitSample:
+    torch = _torch()
+    coords = torch.empty((index.order, int(fit_samples)), dtype=torch.int32, device="cuda")
+    xs = torch.empty(int(fit_samples), dtype=torch.float64, device="cuda")
+    counts = (C.c_int64 * 3)()
+    phi = (C.c_double * 2)()
+    _check(_lib().cpa_fit_sample(index.h, int(fit_samples), float(alpha), int(seed), int(reject_cap),
+                                 _ptr(coords), _ptr(xs), counts, phi, _stream()), "cpa_fit_sample")
+    n = counts[0] + counts[1]
+    return FitSample(coords[:, :n], xs[:n], counts[0], counts[1], counts[2], (phi[0], phi[1]))
+
+
+def cpa_fit_estimate(index: Index, sample: FitSample, factors, lam, precision=FP64):
+    """(estimated fit, F_hat) of the model [[lam; factors]] on a sample."""
+    torch = _torch()
+    fs = [f.to(device="cuda", dtype=torch.float64).contiguous() for f in factors]
+    lam = lam.to(device="cuda", dtype=torch.float64).contiguous()
+    coords = sample.coords.contiguous()
+    xs = sample.xs.contiguous()
+    counts = (C.c_int64 * 3)(sample.s_nz, sample.s_z, sample.attempts)
+    phi = (C.c_double * 2)(*sample.phi)
+    fit = C.c_double(0)
+    F = C.c_double(0)
+    _check(_lib().cpa_fit_estimate(index.h, _ptr(coords), _ptr(xs), counts, phi, coords.shape[1], _ptr(lam),
+                                   _ptr_array([f.data_ptr() for f in fs]), lam.shape[0], int(precision),
+                                   C.byref(fit), C.byref(F), _stream()), "cpa_fit_estimate")
+    return fit.value, F.value

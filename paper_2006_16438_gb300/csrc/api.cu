@@ -212,7 +212,10 @@ int check_options(const cpa_options* o) {
   if (!(o->tau >= 0.0 && o->tau <= 1.0)) return CPA_ERR_ARG;
   if (o->iters < 0 || o->reject_cap < 1 || o->det_cap < 1) return CPA_ERR_ARG;
   if (o->precision != CPA_FP64 && o->precision != CPA_MIXED) return CPA_ERR_ARG;
-  if (o->fit_mode != CPA_FIT_EXACT && o->fit_mode != CPA_FIT_NONE) return CPA_ERR_ARG;
+  if (o->fit_mode != CPA_FIT_EXACT && o->fit_mode != CPA_FIT_NONE && o->fit_mode != CPA_FIT_ESTIMATED)
+    return CPA_ERR_ARG;
+  if (o->fit_mode == CPA_FIT_ESTIMATED && (o->fit_samples < 1 || !(o->fit_alpha > 0.0 && o->fit_alpha <= 1.0)))
+    return CPA_ERR_ARG;
   if (o->tol < 0.0) return CPA_ERR_ARG;
   return CPA_OK;
 }
@@ -296,7 +299,12 @@ struct Plan {
   cudaGraph_t g_iter = nullptr, g_init = nullptr, g_fit = nullptr;  // kept to compose the epoch
   cudaGraphExec_t epoch_exec = nullptr;  // init + epoch_iters iterations + fit, one launch
   int epoch_iters = -1;
-  bool epoch_fit = false;
+  int epoch_fit = CPA_FIT_NONE;
+  // estimated fit (Section 5.4): the element sample and the graph that evaluates it
+  FitSample est;
+  cudaGraphExec_t est_exec = nullptr;
+  cudaGraph_t g_est = nullptr;
+  int64_t k_est = 0;
   int64_t k_epoch = 0;
   cudaStream_t cap_stream = nullptr;
   Profiler gprof;  // event nodes captured into the graph (profile = 1)
@@ -492,11 +500,39 @@ struct Plan {
     return CPA_OK;
   }
 
-  int enqueue_fit(const cpa_index* X, cudaStream_t st) {
+  // The fit of the current factors into fitd: exact (Eq. 5.1) or estimated from the
+  // drawn element sample (Section 5.4).
+  int enqueue_fit(const cpa_index* X, int kind, cudaStream_t st) {
     FactorPtrs F;
     for (int m = 0; m < D; ++m) F.A[m] = Fm[m];
+    if (kind == CPA_FIT_ESTIMATED)
+      return prec == CPA_MIXED ? fit_estimate_enqueue<float>(X, est, F, lam, r, fitd, st)
+                               : fit_estimate_enqueue<double>(X, est, F, lam, r, fitd, st);
     return prec == CPA_MIXED ? fit_enqueue<float>(X, F, lam, r, fit_ws, fitd, st)
                              : fit_enqueue<double>(X, F, lam, r, fit_ws, fitd, st);
+  }
+
+  // Draws the element sample of the estimated fit unless the one held matches the
+  // options; a new sample invalidates the graphs that read the old one.
+  int ensure_est(const cpa_index* X, const cpa_options* o, cudaStream_t st, int64_t* kernels = nullptr) {
+    if (est.coords && est.s_fit == o->fit_samples && est.alpha == o->fit_alpha && est.seed == o->seed &&
+        est.reject_cap == o->reject_cap)
+      return CPA_OK;
+    if (est_exec) {
+      cudaGraphExecDestroy(est_exec);
+      est_exec = nullptr;
+    }
+    if (g_est) {
+      cudaGraphDestroy(g_est);
+      g_est = nullptr;
+    }
+    if (epoch_exec && epoch_fit == CPA_FIT_ESTIMATED) {
+      cudaGraphExecDestroy(epoch_exec);
+      epoch_exec = nullptr;
+    }
+    CPA_TRY(fit_sample_draw(X, o->fit_samples, o->fit_alpha, o->seed, o->reject_cap, &est, st));
+    if (kernels) *kernels += (est.s_nz > 0) + (est.s_z > 0);
+    return CPA_OK;
   }
 
   int run(const cpa_index* X, const cpa_options* opt, double* lambda, double* const* factors,
@@ -545,7 +581,7 @@ struct Plan {
   // state reset, copy-in, initial leverage, `iters` outer iterations, fit, copy-out
   // and the call's status into *out.  The iteration offset lives in *it0_dev and is
   // advanced by `iters` per replay.  Grid sizes follow num_sms() at capture time.
-  int capture_call(const cpa_index* X, int iters, bool with_fit, double* lambda, double* const* factors,
+  int capture_call(const cpa_index* X, int iters, int fit_kind, double* lambda, double* const* factors,
                    double* fit_dev, uint64_t* it0_dev, CallOut* out, cudaGraph_t* g_out) {
     if (!cap_stream) CPA_CUDA_TRY(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
     cudaStream_t cs = cap_stream;
@@ -571,7 +607,7 @@ struct Plan {
       CPA_LAUNCH_CHECK();
       CPA_TRY(enqueue_init(X, cs));
       for (int i = 0; i < iters; ++i) CPA_TRY(enqueue_iteration(X, off, cs));
-      if (with_fit) CPA_TRY(enqueue_fit(X, cs));
+      if (fit_kind != CPA_FIT_NONE) CPA_TRY(enqueue_fit(X, fit_kind, cs));
       for (int m = 0; m < D; ++m) {
         const int64_t cnt = X->dims[m] * r;
         if (prec == CPA_MIXED) {
@@ -601,8 +637,8 @@ struct Plan {
   // One graph for a whole fixed-length call: the initial leverage, `iters` replays of
   // the outer iteration and the fit, as child graphs in a chain.  A single launch
   // per call leaves the GPU queue full whatever the host does meanwhile.
-  int build_epoch(int iters, bool with_fit) {
-    if (epoch_exec && epoch_iters == iters && epoch_fit == with_fit) return CPA_OK;
+  int build_epoch(int iters, int fit_kind) {
+    if (epoch_exec && epoch_iters == iters && epoch_fit == fit_kind) return CPA_OK;
     if (epoch_exec) {
       cudaGraphExecDestroy(epoch_exec);
       epoch_exec = nullptr;
@@ -619,7 +655,8 @@ struct Plan {
     };
     add(g_init);
     for (int i = 0; i < iters; ++i) add(g_iter);
-    if (with_fit) add(g_fit);
+    if (fit_kind == CPA_FIT_EXACT) add(g_fit);
+    if (fit_kind == CPA_FIT_ESTIMATED) add(g_est);
     if (rc == CPA_OK && cudaGraphInstantiate(&epoch_exec, eg, 0) != cudaSuccess) {
       epoch_exec = nullptr;
       rc = CPA_ERR_CUDA;
@@ -627,8 +664,9 @@ struct Plan {
     cudaGraphDestroy(eg);
     if (rc < 0) return rc;
     epoch_iters = iters;
-    epoch_fit = with_fit;
-    k_epoch = k_init + (int64_t)iters * k_iter + (with_fit ? k_fit : 0);
+    epoch_fit = fit_kind;
+    k_epoch = k_init + (int64_t)iters * k_iter + (fit_kind == CPA_FIT_EXACT ? k_fit : 0) +
+              (fit_kind == CPA_FIT_ESTIMATED ? k_est : 0);
     return CPA_OK;
   }
 
@@ -637,6 +675,8 @@ struct Plan {
     if (g_iter) cudaGraphDestroy(g_iter);
     if (g_init) cudaGraphDestroy(g_init);
     if (g_fit) cudaGraphDestroy(g_fit);
+    if (g_est) cudaGraphDestroy(g_est);
+    if (est_exec) cudaGraphExecDestroy(est_exec);
     if (exec) cudaGraphExecDestroy(exec);
     if (init_exec) cudaGraphExecDestroy(init_exec);
     if (fit_exec) cudaGraphExecDestroy(fit_exec);
@@ -656,6 +696,7 @@ void plan_free(Plan* p) { delete p; }
 int Plan::run(const cpa_index* X, const cpa_options* opt, double* lambda, double* const* factors,
               int32_t io_on_device, double* fit, cpa_stats* stats, cudaStream_t st) {
   int64_t kernels = 0;  // launched by this call
+  if (opt->fit_mode == CPA_FIT_ESTIMATED) CPA_TRY(ensure_est(X, opt, st, &kernels));
   CPA_CUDA_TRY(cudaMemsetAsync(warn, 0, sizeof(int) * 4, st));
   CPA_CUDA_TRY(cudaMemsetAsync(dstats, 0, sizeof(DevStats), st));
   CPA_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(DistInfo) * kMaxOrder, st));
@@ -683,14 +724,19 @@ int Plan::run(const cpa_index* X, const cpa_options* opt, double* lambda, double
   }
   // fixed-length call without stage events: the whole call is one graph launch
   const bool one_graph = use_graph && !profile && !(opt->tol > 0.0) && opt->iters <= kEpochGraphMax;
+  const int fit_kind = opt->fit_mode;
   if (use_graph) {
     if (!init_exec)
       CPA_TRY(capture_graph([&](cudaStream_t cs) { return enqueue_init(X, cs); }, &init_exec, &k_init, &g_init));
     if (!exec) CPA_TRY(capture(X));
     if (!fit_exec)
-      CPA_TRY(capture_graph([&](cudaStream_t cs) { return enqueue_fit(X, cs); }, &fit_exec, &k_fit, &g_fit));
+      CPA_TRY(capture_graph([&](cudaStream_t cs) { return enqueue_fit(X, CPA_FIT_EXACT, cs); }, &fit_exec, &k_fit,
+                            &g_fit));
+    if (fit_kind == CPA_FIT_ESTIMATED && !est_exec)
+      CPA_TRY(capture_graph([&](cudaStream_t cs) { return enqueue_fit(X, CPA_FIT_ESTIMATED, cs); }, &est_exec,
+                            &k_est, &g_est));
     if (one_graph) {
-      CPA_TRY(build_epoch(opt->iters, opt->fit_mode == CPA_FIT_EXACT));
+      CPA_TRY(build_epoch(opt->iters, fit_kind));
       CPA_CUDA_TRY(cudaGraphLaunch(epoch_exec, st));
       kernels += k_epoch;
     } else {
@@ -705,10 +751,10 @@ int Plan::run(const cpa_index* X, const cpa_options* opt, double* lambda, double
   auto fit_now = [&](Profiler& pr) -> int {
     CPA_TRY(pr.mark(-1));
     if (use_graph) {
-      CPA_CUDA_TRY(cudaGraphLaunch(fit_exec, st));
-      if (kernels >= 0) kernels += k_fit;
+      CPA_CUDA_TRY(cudaGraphLaunch(fit_kind == CPA_FIT_ESTIMATED ? est_exec : fit_exec, st));
+      if (kernels >= 0) kernels += fit_kind == CPA_FIT_ESTIMATED ? k_est : k_fit;
     } else {
-      CPA_TRY(enqueue_fit(X, st));
+      CPA_TRY(enqueue_fit(X, fit_kind, st));
     }
     return pr.mark(5);
   };
@@ -738,7 +784,7 @@ int Plan::run(const cpa_index* X, const cpa_options* opt, double* lambda, double
       }
     }
     iters_done = it;
-    if (opt->tol > 0.0 && opt->fit_mode == CPA_FIT_EXACT) {
+    if (opt->tol > 0.0 && fit_kind != CPA_FIT_NONE) {
       CPA_TRY(fit_now(eprof));
       double f = 0.0;
       int status = 0;
@@ -756,7 +802,7 @@ int Plan::run(const cpa_index* X, const cpa_options* opt, double* lambda, double
       }
     }
   }
-  if (!(opt->tol > 0.0) && opt->fit_mode == CPA_FIT_EXACT) {
+  if (!(opt->tol > 0.0) && fit_kind != CPA_FIT_NONE) {
     if (!one_graph) CPA_TRY(fit_now(eprof));
     CPA_CUDA_TRY(cudaMemcpyAsync(&fit_val, fitd, sizeof(double), cudaMemcpyDeviceToHost, st));
   }
@@ -785,7 +831,7 @@ int Plan::run(const cpa_index* X, const cpa_options* opt, double* lambda, double
   CPA_CUDA_TRY(cudaMemcpyAsync(lambda, lam, sizeof(double) * r, kout, st));
   if (fit && io_on_device) CPA_CUDA_TRY(cudaMemcpyAsync(fit, fitd, sizeof(double), cudaMemcpyDeviceToDevice, st));
   CPA_CUDA_TRY(cudaStreamSynchronize(st));
-  if (fit && !io_on_device) *fit = opt->fit_mode == CPA_FIT_EXACT ? fit_val : NAN;
+  if (fit && !io_on_device) *fit = fit_kind != CPA_FIT_NONE ? fit_val : NAN;
   if (stats) {
     memset(stats, 0, sizeof(*stats));
     stats->iters_done = iters_done;
@@ -835,6 +881,8 @@ void cpa_options_default(cpa_options* opt) {
   opt->iter_offset = 0;
   opt->precision = CPA_FP64;
   opt->fit_mode = CPA_FIT_EXACT;
+  opt->fit_samples = 1ll << 27;
+  opt->fit_alpha = 0.5;
   opt->det_cap = 1 << 24;
   opt->reject_cap = 4096;
   opt->stream = nullptr;
@@ -1093,6 +1141,84 @@ int cpa_solve(const double* G, const double* M, int64_t n, int32_t r, double* A,
   return hwarn;
 }
 
+int cpa_fit_sample(const cpa_index* X, int64_t fit_samples, double fit_alpha, uint64_t seed, int32_t reject_cap,
+                   int32_t* coords, double* xs, int64_t* counts, double* phi, void* stream) {
+  if (!X || !coords || !xs || !counts || !phi) return CPA_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  FitSample S;
+  CPA_TRY(fit_sample_draw(X, fit_samples, fit_alpha, seed, reject_cap, &S, st));
+  const int64_t n = S.s_nz + S.s_z;
+  for (int m = 0; m < X->order; ++m)
+    CPA_CUDA_TRY(cudaMemcpyAsync(coords + (size_t)m * fit_samples, S.coords + (size_t)m * S.s_fit,
+                                 sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st));
+  CPA_CUDA_TRY(cudaMemcpyAsync(xs, S.xs, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  CPA_CUDA_TRY(cudaStreamSynchronize(st));
+  counts[0] = S.s_nz;
+  counts[1] = S.s_z;
+  counts[2] = S.attempts;
+  phi[0] = S.phi[0];
+  phi[1] = S.phi[1];
+  return CPA_OK;
+}
+
+int cpa_fit_estimate(const cpa_index* X, const int32_t* coords, const double* xs, const int64_t* counts,
+                     const double* phi, int64_t stride, const double* lambda, const double* const* factors,
+                     int32_t r, int32_t precision, double* fit, double* F_hat, void* stream) {
+  if (!X || !coords || !xs || !counts || !phi || !lambda || !factors || !fit || r < 1 || r > kMaxRank)
+    return CPA_ERR_ARG;
+  if (precision != CPA_FP64 && precision != CPA_MIXED) return CPA_ERR_ARG;
+  if (counts[0] < 0 || counts[1] < 0 || counts[0] + counts[1] > stride) return CPA_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int D = X->order;
+  int64_t conv = 0;
+  for (int m = 0; m < D; ++m) {
+    if (!factors[m]) return CPA_ERR_ARG;
+    conv += X->dims[m] * r;
+  }
+  DevBuf buf;
+  const size_t partial_bytes = sizeof(double) * ((size_t)device_sms() * 8 + 8);
+  CPA_TRY(buf.alloc(partial_bytes + 64 + (precision == CPA_MIXED ? sizeof(float) * conv + 256 : 0), st));
+  double* fit_dev = (double*)buf.p;
+  FitSample S;  // a view of the caller's sample: released as a view below
+  S.coords = const_cast<int32_t*>(coords);
+  S.xs = const_cast<double*>(xs);
+  S.partial = fit_dev + 8;
+  S.stride = stride;
+  S.s_nz = counts[0];
+  S.s_z = counts[1];
+  S.phi[0] = phi[0];
+  S.phi[1] = phi[1];
+  FactorPtrs F;
+  int rc = CPA_OK;
+  if (precision == CPA_MIXED) {
+    float* f32 = reinterpret_cast<float*>((char*)buf.p + partial_bytes + 64);
+    for (int m = 0; m < D; ++m) {
+      const int64_t cnt = X->dims[m] * r;
+      k_convert<float, double><<<blocks(cnt), 256, 0, st>>>(factors[m], cnt, f32);
+      F.A[m] = f32;
+      f32 += cnt;
+    }
+    if (cudaGetLastError() != cudaSuccess) rc = CPA_ERR_CUDA;
+    if (rc == CPA_OK) rc = fit_estimate_enqueue<float>(X, S, F, lambda, r, fit_dev, st);
+  } else {
+    for (int m = 0; m < D; ++m) F.A[m] = factors[m];
+    rc = fit_estimate_enqueue<double>(X, S, F, lambda, r, fit_dev, st);
+  }
+  double h[2] = {NAN, NAN};
+  if (rc == CPA_OK) {
+    if (cudaMemcpyAsync(h, fit_dev, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      rc = CPA_ERR_CUDA;
+  }
+  S.coords = nullptr;
+  S.xs = nullptr;
+  S.partial = nullptr;
+  if (rc < 0) return rc;
+  *fit = h[0];
+  if (F_hat) *F_hat = h[1];
+  return CPA_OK;
+}
+
 int cpa_fit(const cpa_index* X, const double* const* factors, const double* lambda, int32_t r,
             double* fit, void* stream) {
   if (!X || !factors || !lambda || !fit || r < 1 || r > kMaxRank) return CPA_ERR_ARG;
@@ -1266,6 +1392,9 @@ struct cpa_batch {
       cudaGraphExecDestroy(exec);
       exec = nullptr;
     }
+    // element samples of estimated fits are drawn before any capture
+    for (int i = 0; i < n; ++i)
+      if (opts[i].fit_mode == CPA_FIT_ESTIMATED) CPA_TRY(plans[i]->ensure_est(idx[i], &opts[i], nullptr));
     cudaGraph_t bg = nullptr;
     CPA_CUDA_TRY(cudaGraphCreate(&bg, 0));
     int rc = CPA_OK;
@@ -1273,7 +1402,7 @@ struct cpa_batch {
     sm_budget_override() = sms;
     for (int i = 0; i < n && rc == CPA_OK; ++i) {
       cudaGraph_t g = nullptr;
-      rc = plans[i]->capture_call(idx[i], opts[i].iters, opts[i].fit_mode == CPA_FIT_EXACT, lambdas[i],
+      rc = plans[i]->capture_call(idx[i], opts[i].iters, opts[i].fit_mode, lambdas[i],
                                   factors[i].data(), fits[i], it0 + i, outs + i, &g);
       if (rc < 0) break;
       size_t nn = 0;

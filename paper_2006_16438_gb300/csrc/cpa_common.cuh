@@ -74,8 +74,10 @@ struct Philox4x64 {
   }
 };
 
-// Domain tag of the sampling draws in the third counter word.
+// Domain tags of the draws in the third counter word: Khatri-Rao row sampling and
+// the element sample of the estimated fit.
 constexpr uint64_t kDomainSample = 1ull << 32;
+constexpr uint64_t kDomainFit = 2ull << 32;
 
 // ---------------------------------------------------------------------------
 // Packed multi-index: other mode t occupies bits [off_t, off_t + bits_t) of a
@@ -175,8 +177,8 @@ inline int& sm_budget_override() {
   static thread_local int v = 0;
   return v;
 }
-inline int num_sms() {
-  if (sm_budget_override() > 0) return sm_budget_override();
+// The device's SM count, whatever the budget.
+inline int device_sms() {
   static int sms = 0;
   if (!sms) {
     int dev = 0;
@@ -185,6 +187,10 @@ inline int num_sms() {
     if (sms <= 0) sms = 1;
   }
   return sms;
+}
+inline int num_sms() {
+  if (sm_budget_override() > 0) return sm_budget_override();
+  return device_sms();
 }
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }

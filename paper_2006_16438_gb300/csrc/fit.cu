@@ -1,10 +1,16 @@
-// Fit of Eq. 5.1: fit = 1 - ||X - M|| / ||X|| with
+// Exact fit (Eq. 5.1) and estimated fit (Section 5.4).
+//
+// Exact: fit = 1 - ||X - M|| / ||X|| with
 // ||X - M||^2 = ||X||^2 - 2 <X, M> + ||M||^2,  M = [[lambda; A_1, ..., A_D]].
 //
 // <X, M> is one pass over the fibre index of the mode with the fewest fibres: a
 // warp takes a fibre, forms z = lambda * prod_t A_{m_t}(i_t, :) once, and for each
 // nonzero of the fibre accumulates x * A_k(i_k, :) per lane; the fibre contributes
 // z . acc.  ||M||^2 = lambda^T (Hadamard product of the Grams A_m^T A_m) lambda.
+//
+// Estimated: a stratified sample of elements drawn once (nonzeros uniformly, zero
+// cells uniformly by rejection) and F_hat = sum_j phi_j (m_j - x_j)^2 per evaluation,
+// O(s_fit D r) work instead of O(nnz D r).
 #include "fit.cuh"
 
 namespace cpa {
@@ -122,5 +128,272 @@ template int fit_enqueue<double>(const cpa_index*, const FactorPtrs&, const doub
                                  cudaStream_t);
 template int fit_enqueue<float>(const cpa_index*, const FactorPtrs&, const double*, int, double*, double*,
                                 cudaStream_t);
+
+
+// ---------------------------------------------------------------------------
+// Estimated fit (Section 5.4)
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kEstThreads = 256;
+constexpr int kEstLanes = 8;  // lanes per sample in the evaluation
+constexpr int kDrawThreads = 256;
+
+__device__ __forceinline__ int64_t scale_u64(uint64_t u, int64_t n) {
+  return (int64_t)__umul64hi(u, (uint64_t)n);
+}
+
+// Nonzero slot j: the nonzero at position floor(u nnz / 2^64) of mode 0's index.
+template <class VT>
+__global__ void __launch_bounds__(kDrawThreads) k_fit_draw_nz(FibreIndex<VT> X0, KeyLayout L0, int64_t nnz,
+                                                              int64_t s_nz, uint64_t seed, int32_t* __restrict__ coords,
+                                                              int64_t S, double* __restrict__ xs) {
+  const int64_t j = (int64_t)blockIdx.x * kDrawThreads + threadIdx.x;
+  if (j >= s_nz) return;
+  uint64_t w0 = (uint64_t)j, w1 = 0, w2 = kDomainFit, w3 = 0;
+  Philox4x64::block(w0, w1, w2, w3, seed, 0ull);
+  const uint64_t p = (uint64_t)scale_u64(w0, nnz);
+  // fibre f with off[f] <= p < off[f + 1]
+  int64_t a = 0, z = X0.nfib;  // first offset greater than p is off[a + 1]
+  while (a < z) {
+    const int64_t mid = a + ((z - a) >> 1);
+    if (X0.off[mid + 1] <= p) a = mid + 1; else z = mid;
+  }
+  const uint64_t key = X0.keys[a];
+  coords[j] = X0.ik[p];
+  for (int t = 0; t < L0.d; ++t) coords[(int64_t)L0.mode[t] * S + j] = (int32_t)L0.get(key, t);
+  xs[j] = (double)X0.val[p];
+}
+
+// Zero slot j: uniform cells until one is not a nonzero.
+template <class VT>
+__global__ void __launch_bounds__(kDrawThreads) k_fit_draw_zero(FibreIndex<VT> X0, KeyLayout L0, int D, int64_t n0,
+                                                                int64_t s_nz, int64_t s_z, uint64_t seed,
+                                                                int reject_cap, int32_t* __restrict__ coords,
+                                                                int64_t S, double* __restrict__ xs,
+                                                                int* __restrict__ status,
+                                                                unsigned long long* __restrict__ attempts) {
+  const int64_t j = (int64_t)blockIdx.x * kDrawThreads + threadIdx.x;
+  unsigned long long tried = 0;
+  if (j < s_z) {
+    bool done = false;
+    for (int a = 0; a < reject_cap && !done; ++a) {
+      int32_t c[kMaxOrder];
+      uint64_t w[4];
+      for (int m = 0; m < D; ++m) {
+        if ((m & 3) == 0) {
+          w[0] = (uint64_t)j;
+          w[1] = (uint64_t)a;
+          w[2] = kDomainFit | 1ull | ((uint64_t)(m >> 2) << 16);
+          w[3] = 0;
+          Philox4x64::block(w[0], w[1], w[2], w[3], seed, 0ull);
+        }
+        const int64_t nm = m == 0 ? n0 : L0.n[m - 1];
+        c[m] = (int32_t)scale_u64(w[m & 3], nm);
+      }
+      ++tried;
+      uint64_t key = 0;
+      for (int t = 0; t < L0.d; ++t) key |= (uint64_t)(uint32_t)c[L0.mode[t]] << L0.off[t];
+      uint64_t lo, hi;
+      X0.probe(key, &lo, &hi);
+      uint64_t a0 = lo, b0 = hi;  // first position in the fibre with i_0 >= c_0 (ascending)
+      while (a0 < b0) {
+        const uint64_t mid = a0 + ((b0 - a0) >> 1);
+        if (X0.ik[mid] < c[0]) a0 = mid + 1; else b0 = mid;
+      }
+      const bool is_nz = a0 < hi && X0.ik[a0] == c[0];
+      if (!is_nz) {
+        for (int m = 0; m < D; ++m) coords[(int64_t)m * S + s_nz + j] = c[m];
+        xs[s_nz + j] = 0.0;
+        done = true;
+      }
+    }
+    if (!done) set_status(status, CPA_ERR_REJECT_LIMIT);
+  }
+  for (int o = 16; o > 0; o >>= 1) tried += __shfl_xor_sync(0xffffffffu, tried, o);
+  if ((threadIdx.x & 31) == 0 && tried) atomicAdd(attempts, tried);
+}
+
+// Per block: sum over its samples of phi_j (m_j - x_j)^2, eight lanes per sample
+// (lane g of a group takes columns g, g + 8, ...), model value accumulated in FT.
+template <class FT, int CPL>
+__global__ void __launch_bounds__(kEstThreads) k_fit_est(const int32_t* __restrict__ coords, int64_t stride,
+                                                         const double* __restrict__ xs, int64_t S, int64_t s_nz,
+                                                         double phi_nz, double phi_z, FactorPtrs F,
+                                                         const double* __restrict__ lambda, int r, int D,
+                                                         double* __restrict__ partial) {
+  __shared__ double red[kEstThreads / 32];
+  const int lane = threadIdx.x & 31;
+  const int g = lane & (kEstLanes - 1);
+  // the four groups of a warp take samples base + 0..3; every lane of the warp runs
+  // the same number of iterations (full-mask shuffles)
+  const int64_t base0 = (((int64_t)blockIdx.x * kEstThreads + threadIdx.x) >> 5) * (32 / kEstLanes);
+  const int64_t ngroups = ((int64_t)gridDim.x * kEstThreads) / kEstLanes;
+  const int sub = lane / kEstLanes;
+  FT lam[CPL];
+#pragma unroll
+  for (int q = 0; q < CPL; ++q) {
+    const int c = g + kEstLanes * q;
+    lam[q] = c < r ? (FT)lambda[c] : FT(0);
+  }
+  double acc = 0.0;
+  for (int64_t base = base0; base < S; base += ngroups) {
+    const int64_t j = base + sub;
+    const bool live = j < S;
+    FT v[CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) v[q] = lam[q];
+    if (live) {
+      for (int m = 0; m < D; ++m) {
+        const FT* A = static_cast<const FT*>(F.A[m]) + (int64_t)coords[(int64_t)m * stride + j] * r;
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) {
+          const int c = g + kEstLanes * q;
+          if (c < r) v[q] *= A[c];
+        }
+      }
+    }
+    FT mv = FT(0);
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) mv += v[q];
+    for (int o = kEstLanes / 2; o > 0; o >>= 1) mv += __shfl_xor_sync(0xffffffffu, mv, o);
+    if (live && g == 0) {
+      const double res = (double)mv - xs[j];
+      acc += (j < s_nz ? phi_nz : phi_z) * res * res;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int w = 0; w < kEstThreads / 32; ++w) b += red[w];
+    partial[blockIdx.x] = b;
+  }
+}
+
+// F_hat = the partials summed in a fixed order; fit = 1 - sqrt(F_hat) / ||X||.
+__global__ void k_fit_est_final(const double* __restrict__ partial, int nb, double norm_x2,
+                                double* __restrict__ fit_out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) s += partial[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double F = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) F += red[w];
+    fit_out[0] = norm_x2 > 0.0 ? 1.0 - sqrt(F) / sqrt(norm_x2) : 0.0;
+    fit_out[1] = F;
+  }
+}
+
+int est_blocks(int64_t S) {
+  const int64_t per_block = kEstThreads / kEstLanes;
+  const int64_t want = ceil_div(S > 0 ? S : 1, per_block);
+  const int64_t cap = (int64_t)num_sms() * 8;
+  return (int)(want < cap ? want : cap);
+}
+
+}  // namespace
+
+void FitSample::release() {
+  if (coords) cudaFree(coords);
+  if (xs) cudaFree(xs);
+  if (partial) cudaFree(partial);
+  coords = nullptr;
+  xs = nullptr;
+  partial = nullptr;
+  s_fit = s_nz = s_z = attempts = 0;
+}
+
+int fit_sample_draw(const cpa_index* X, int64_t s_fit, double alpha, uint64_t seed, int reject_cap,
+                    FitSample* S, cudaStream_t st) {
+  if (s_fit < 1 || !(alpha > 0.0 && alpha <= 1.0) || X->nnz < 1 || reject_cap < 1) return CPA_ERR_ARG;
+  const int D = X->order;
+  double cells = 1.0;
+  for (int m = 0; m < D; ++m) cells *= (double)X->dims[m];
+  const bool has_zeros = cells > (double)X->nnz;
+  int64_t s_nz = (int64_t)ceil(alpha * (double)s_fit);
+  if (s_nz > s_fit) s_nz = s_fit;
+  const int64_t s_z = has_zeros ? s_fit - s_nz : 0;
+  S->release();
+  CPA_CUDA_TRY(cudaMalloc((void**)&S->coords, sizeof(int32_t) * (size_t)D * s_fit));
+  CPA_CUDA_TRY(cudaMalloc((void**)&S->xs, sizeof(double) * (size_t)s_fit));
+  CPA_CUDA_TRY(cudaMalloc((void**)&S->partial, sizeof(double) * ((size_t)device_sms() * 8 + 8)));
+  int* d_status = nullptr;
+  CPA_CUDA_TRY(cudaMallocAsync((void**)&d_status, sizeof(int) * 2 + sizeof(unsigned long long), st));
+  unsigned long long* d_att = reinterpret_cast<unsigned long long*>(d_status + 2);
+  CPA_CUDA_TRY(cudaMemsetAsync(d_status, 0, sizeof(int) * 2 + sizeof(unsigned long long), st));
+  const KeyLayout& L0 = X->mode[0].L;
+  auto draw = [&](auto tag) -> int {
+    using VT = decltype(tag);
+    const FibreIndex<VT> x0 = fibre_view<VT>(X, 0);
+    if (s_nz > 0)
+      k_fit_draw_nz<VT><<<(unsigned)ceil_div(s_nz, kDrawThreads), kDrawThreads, 0, st>>>(
+          x0, L0, X->nnz, s_nz, seed, S->coords, s_fit, S->xs);
+    CPA_LAUNCH_CHECK();
+    if (s_z > 0)
+      k_fit_draw_zero<VT><<<(unsigned)ceil_div(s_z, kDrawThreads), kDrawThreads, 0, st>>>(
+          x0, L0, D, X->dims[0], s_nz, s_z, seed, reject_cap, S->coords, s_fit, S->xs, d_status, d_att);
+    CPA_LAUNCH_CHECK();
+    return CPA_OK;
+  };
+  int rc = X->val_dtype == CPA_F32 ? draw(float()) : draw(double());
+  int h_status = 0;
+  unsigned long long h_att = 0;
+  if (rc == CPA_OK) {
+    if (cudaMemcpyAsync(&h_status, d_status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(&h_att, d_att, sizeof(h_att), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      rc = CPA_ERR_CUDA;
+  }
+  cudaFreeAsync(d_status, st);
+  if (rc == CPA_OK && h_status < 0) rc = h_status;
+  if (rc < 0) {
+    S->release();
+    return rc;
+  }
+  S->s_fit = s_fit;
+  S->stride = s_fit;
+  S->s_nz = s_nz;
+  S->s_z = s_z;
+  S->attempts = (int64_t)h_att;
+  S->phi[0] = s_nz > 0 ? (double)X->nnz / (double)s_nz : 0.0;
+  S->phi[1] = s_z > 0 ? (cells - (double)X->nnz) / (double)s_z : 0.0;
+  S->alpha = alpha;
+  S->seed = seed;
+  S->reject_cap = reject_cap;
+  return CPA_OK;
+}
+
+template <class FT>
+int fit_estimate_enqueue(const cpa_index* X, const FitSample& S, const FactorPtrs& F, const double* lambda,
+                         int r, double* fit_dev, cudaStream_t st) {
+  const int64_t n = S.s_nz + S.s_z;
+  const int nb = est_blocks(n);
+  const int D = X->order;
+  if (r <= 8)
+    k_fit_est<FT, 1><<<nb, kEstThreads, 0, st>>>(S.coords, S.stride, S.xs, n, S.s_nz, S.phi[0], S.phi[1], F, lambda, r, D,
+                                                 S.partial);
+  else if (r <= 16)
+    k_fit_est<FT, 2><<<nb, kEstThreads, 0, st>>>(S.coords, S.stride, S.xs, n, S.s_nz, S.phi[0], S.phi[1], F, lambda, r, D,
+                                                 S.partial);
+  else if (r <= 32)
+    k_fit_est<FT, 4><<<nb, kEstThreads, 0, st>>>(S.coords, S.stride, S.xs, n, S.s_nz, S.phi[0], S.phi[1], F, lambda, r, D,
+                                                 S.partial);
+  else
+    k_fit_est<FT, 8><<<nb, kEstThreads, 0, st>>>(S.coords, S.stride, S.xs, n, S.s_nz, S.phi[0], S.phi[1], F, lambda, r, D,
+                                                 S.partial);
+  CPA_LAUNCH_CHECK();
+  k_fit_est_final<<<1, 256, 0, st>>>(S.partial, nb, X->norm_x2, fit_dev);
+  CPA_LAUNCH_CHECK();
+  return CPA_OK;
+}
+template int fit_estimate_enqueue<double>(const cpa_index*, const FitSample&, const FactorPtrs&, const double*,
+                                          int, double*, cudaStream_t);
+template int fit_estimate_enqueue<float>(const cpa_index*, const FitSample&, const FactorPtrs&, const double*,
+                                         int, double*, cudaStream_t);
 
 }  // namespace cpa

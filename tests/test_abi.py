@@ -57,3 +57,4 @@ def test_strerror_without_gpu():
     opt = binding.default_options()
     assert opt.epoch_len == 5 and opt.patience == 3 and opt.reject_cap == 4096
     assert opt.tau == 2.0 ** -17 and opt.samples == 2 ** 17
+    assert opt.fit_mode == binding.FIT_EXACT and opt.fit_samples == 2 ** 27 and opt.fit_alpha == 0.5
