@@ -31,6 +31,9 @@ ERR_COO_DUP = -3
 ERR_OOM = -4
 ERR_REJECT_LIMIT = -5
 ERR_DET_CAP = -6
+DIST_LEVERAGE = 0
+DIST_UNIFORM = 1
+DIST_LENGTH_SQUARED = 2
 WARN_SINGULAR_GRAM = 1
 WARN_RANK_DEFICIENT_LEV = 2
 
@@ -108,13 +111,15 @@ def _declare(lib):
     lib.orc_fit.argtypes = [P, P, P, I32]
     lib.orc_fit.restype = C.c_double
     lib.orc_cp_arls_lev.argtypes = [P, I32, I64, C.c_double, I32, I32, I32, C.c_double, U64, U64,
-                                    I64, I32, P, P, P, P]
+                                    I64, I32, P, P, P, P, I32]
     lib.orc_cp_arls_lev.restype = I32
     lib.orc_mode_update_once.argtypes = [P, I32, I32, P, P, I64, C.c_double, U64, U64, I64, I32,
-                                         P, P, P, P, P]
+                                         P, P, P, P, P, I32]
     lib.orc_mode_update_once.restype = I32
     lib.orc_cp_als.argtypes = [P, I32, I32, P, P, P]
     lib.orc_cp_als.restype = I32
+    lib.orc_scores.argtypes = [P, I64, I32, I32, P, P]
+    lib.orc_scores.restype = I32
     lib.orc_fit_sample.argtypes = [P, I64, C.c_double, U64, I32, P, P, P, P]
     lib.orc_fit_sample.restype = I32
     lib.orc_fit_estimate.argtypes = [P, P, P, P, P, I64, P, P, I32, P]
@@ -379,8 +384,21 @@ def fit_estimate(index: Index, sample: FitSample, factors, lam):
     return float(f), F.value
 
 
+def scores(A, dist=DIST_LEVERAGE):
+    """Row scores (summing to the rank) of the chosen per-factor distribution."""
+    A = _c(A, np.float64)
+    n, r = A.shape
+    out = np.zeros(n)
+    rank = C.c_int(0)
+    rc = _lib().orc_scores(_ptr(A), n, r, int(dist), _ptr(out), C.byref(rank))
+    if rc < 0:
+        raise OracleError(rc, "scores")
+    return out, rank.value
+
+
 def cp_arls_lev(index: Index, factors, *, rank, samples, tau=1.0, iters=10, epoch_len=5,
-                patience=3, tol=0.0, seed=0, iter_offset=0, det_cap=1 << 24, reject_cap=4096):
+                patience=3, tol=0.0, seed=0, iter_offset=0, det_cap=1 << 24, reject_cap=4096,
+                distribution=DIST_LEVERAGE):
     """Alg. 3.  Returns (lambda, factors, fit, iters_done, warnings)."""
     fs = [_c(A, np.float64).copy() for A in factors]
     fp = _ptr_array(fs)
@@ -390,14 +408,14 @@ def cp_arls_lev(index: Index, factors, *, rank, samples, tau=1.0, iters=10, epoc
     rc = _lib().orc_cp_arls_lev(index.h, rank, int(samples), float(tau), int(iters), int(epoch_len),
                                 int(patience), float(tol), int(seed), int(iter_offset),
                                 int(det_cap), int(reject_cap), C.cast(fp, C.c_void_p), _ptr(lam),
-                                C.byref(f), C.byref(done))
+                                C.byref(f), C.byref(done), int(distribution))
     if rc < 0:
         raise OracleError(rc, "cp_arls_lev")
     return lam, fs, f.value, done.value, rc
 
 
 def mode_update(index: Index, factors, k, *, rank, samples, tau=1.0, seed=0, it=0,
-                det_cap=1 << 24, reject_cap=4096):
+                det_cap=1 << 24, reject_cap=4096, distribution=DIST_LEVERAGE):
     """One randomized update of mode k from the given factors (Alg. 3 inner loop).
     Returns dict(A=new factor k (normalised), lam, idx, cnt, wgt, sbar, sdet, pdet,
     nnz_sampled, attempts, warnings)."""
@@ -412,7 +430,8 @@ def mode_update(index: Index, factors, k, *, rank, samples, tau=1.0, seed=0, it=
     pdet = C.c_double(0)
     rc = _lib().orc_mode_update_once(index.h, rank, int(k), C.cast(fp, C.c_void_p), _ptr(lam), s,
                                      float(tau), int(seed), int(it), int(det_cap), int(reject_cap),
-                                     _ptr(idx), _ptr(cnt), _ptr(wgt), _ptr(st), C.byref(pdet))
+                                     _ptr(idx), _ptr(cnt), _ptr(wgt), _ptr(st), C.byref(pdet),
+                                     int(distribution))
     if rc < 0:
         raise OracleError(rc, "mode_update")
     sbar = int(st[0])

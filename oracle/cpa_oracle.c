@@ -876,9 +876,33 @@ double orc_fit_estimate(const orc_index* X, const int32_t* coords, const double*
 /* ------------------------------------------------------------------------ */
 /* Alg. 3                                                                   */
 /* ------------------------------------------------------------------------ */
+/* Row scores of one factor, summing to r, whose ratio to r is the factor's sampling
+ * distribution: leverage scores (Alg. 3), or for the comparison of App. B the
+ * uniform score r / n or the length-squared score r ||a_i||^2 / ||A||_F^2 (of the
+ * factor as given: column-normalised after an update, the caller's initial guess at
+ * the start). */
+int orc_scores(const double* A, int64_t n, int r, int dist, double* s, int* rank) {
+  if (dist == ORC_DIST_LEVERAGE) return orc_leverage(A, n, r, s, rank);
+  *rank = r;
+  if (dist == ORC_DIST_UNIFORM) {
+    for (int64_t i = 0; i < n; ++i) s[i] = (double)r / (double)n;
+    return ORC_OK;
+  }
+  if (dist != ORC_DIST_LENGTH_SQUARED) return ORC_ERR_ARG;
+  double fro = 0.0;
+  for (int64_t i = 0; i < n; ++i)
+    for (int c = 0; c < r; ++c) fro += A[(size_t)i * r + c] * A[(size_t)i * r + c];
+  for (int64_t i = 0; i < n; ++i) {
+    double row = 0.0;
+    for (int c = 0; c < r; ++c) row += A[(size_t)i * r + c] * A[(size_t)i * r + c];
+    s[i] = fro > 0.0 ? (double)r * row / fro : 0.0;
+  }
+  return ORC_OK;
+}
+
 static int refresh_mode(orc_state* st, int m, const double* A) {
   int rank = 0;
-  int rc = orc_leverage(A, st->dims[m], st->r, st->lev[m], &rank);
+  int rc = orc_scores(A, st->dims[m], st->r, st->dist, st->lev[m], &rank);
   if (rc < 0) return rc;
   if (rc & ORC_WARN_RANK_DEFICIENT_LEV) st->warnings |= ORC_WARN_RANK_DEFICIENT_LEV;
   st->T[m] = orc_cdf(st->lev[m], st->dims[m], st->r, st->q[m], st->C[m], &st->maxq[m],
@@ -887,10 +911,11 @@ static int refresh_mode(orc_state* st, int m, const double* A) {
 }
 
 int orc_state_init(orc_state* st, int order, const int64_t* dims, int r,
-                   double* const* factors) {
+                   double* const* factors, int dist) {
   memset(st, 0, sizeof(*st));
   st->order = order;
   st->r = r;
+  st->dist = dist;
   for (int m = 0; m < order; ++m) {
     st->dims[m] = dims[m];
     st->lev[m] = (double*)malloc(sizeof(double) * (size_t)dims[m]);
@@ -951,10 +976,10 @@ int orc_mode_update(const orc_index* X, orc_state* st, int k, double* const* fac
 int orc_cp_arls_lev(const orc_index* X, int r, int64_t s, double tau, int iters, int epoch_len,
                     int patience, double tol, uint64_t seed, uint64_t iter_offset,
                     int64_t det_cap, int reject_cap, double* const* factors, double* lambda,
-                    double* fit, int* iters_done) {
+                    double* fit, int* iters_done, int dist) {
   int order = X->order;
   orc_state st;
-  int rc = orc_state_init(&st, order, X->dims, r, factors);
+  int rc = orc_state_init(&st, order, X->dims, r, factors, dist);
   if (rc < 0) { orc_state_free(&st); return rc; }
   for (int c = 0; c < r; ++c) lambda[c] = 1.0;
   int it = 0, bad = 0;
@@ -1007,9 +1032,9 @@ int orc_mode_update_once(const orc_index* X, int r, int k, double* const* factor
                          double* lambda, int64_t s, double tau, uint64_t seed, uint64_t iter,
                          int64_t det_cap, int reject_cap, uint64_t* idx, uint32_t* cnt,
                          double* wgt, int64_t* stats /* sbar, sdet, nnz_sampled, attempts */,
-                         double* pdet) {
+                         double* pdet, int dist) {
   orc_state st;
-  int rc = orc_state_init(&st, X->order, X->dims, r, factors);
+  int rc = orc_state_init(&st, X->order, X->dims, r, factors, dist);
   if (rc >= 0)
     rc = orc_mode_update(X, &st, k, factors, lambda, s, tau, seed, iter, det_cap, reject_cap,
                          idx, cnt, wgt);

@@ -30,6 +30,11 @@
 #define ORC_ERR_DET_CAP (-6)
 #define ORC_WARN_SINGULAR_GRAM 1
 #define ORC_WARN_RANK_DEFICIENT_LEV 2
+/* per-factor row distributions (leverage: the method; uniform and length-squared:
+ * the comparison of App. B) */
+#define ORC_DIST_LEVERAGE 0
+#define ORC_DIST_UNIFORM 1
+#define ORC_DIST_LENGTH_SQUARED 2
 
 /* Philox4x64-10 block function. */
 void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]);
@@ -123,6 +128,7 @@ double orc_fit(const orc_index* X, const double* const* factors, const double* l
  * in an orc_state. */
 typedef struct {
   int order, r;
+  int dist;               /* ORC_DIST_* */
   int64_t dims[16];
   double* lev[16];
   uint64_t* q[16];
@@ -136,7 +142,11 @@ typedef struct {
 } orc_state;
 
 int orc_state_init(orc_state* st, int order, const int64_t* dims, int r,
-                   double* const* factors);
+                   double* const* factors, int dist);
+
+/* Row scores of a factor summing to r (p_i = score_i / r): leverage scores
+ * (orc_leverage), r / n (uniform) or r ||a_i||^2 / ||A||_F^2 (length-squared). */
+int orc_scores(const double* A, int64_t n, int r, int dist, double* s, int* rank);
 void orc_state_free(orc_state* st);
 int orc_mode_update(const orc_index* X, orc_state* st, int k, double* const* factors,
                     double* lambda, int64_t s, double tau, uint64_t seed, uint64_t iter,
@@ -148,14 +158,14 @@ int orc_mode_update(const orc_index* X, orc_state* st, int k, double* const* fac
 int orc_cp_arls_lev(const orc_index* X, int r, int64_t s, double tau, int iters, int epoch_len,
                     int patience, double tol, uint64_t seed, uint64_t iter_offset,
                     int64_t det_cap, int reject_cap, double* const* factors, double* lambda,
-                    double* fit, int* iters_done);
+                    double* fit, int* iters_done, int dist);
 
 /* One mode update from the given factors (leverage of all modes recomputed first).
  * stats = {sbar, sdet, nnz_sampled, attempts}. */
 int orc_mode_update_once(const orc_index* X, int r, int k, double* const* factors,
                          double* lambda, int64_t s, double tau, uint64_t seed, uint64_t iter,
                          int64_t det_cap, int reject_cap, uint64_t* idx, uint32_t* cnt,
-                         double* wgt, int64_t* stats, double* pdet);
+                         double* wgt, int64_t* stats, double* pdet, int dist);
 
 /* Estimated fit (Section 5.4).  orc_fit_sample draws the stratified sample once:
  * s_nz = ceil(alpha * s_fit) nonzeros and s_z = s_fit - s_nz zero elements (the

@@ -622,3 +622,80 @@ def test_fit_sample_edge_cases(orc):
     with pytest.raises(orc.OracleError) as ei:
         orc.fit_sample(orc.Index(coo3), 200, alpha=0.5, seed=0, reject_cap=1)
     assert ei.value.code == orc.ERR_REJECT_LIMIT
+
+
+# --------------------------------------------------------------------------- App. B distributions
+def test_uniform_and_length_squared_scores(orc):
+    """Uniform scores are r/n; length-squared scores are r times each row's share of
+    ||A||_F^2; both sum to r, so p = score / r is a distribution.  The product of the
+    length-squared factor distributions is the normalised bound of App. B,
+    ||Z(i,:)||^2 <= prod_k ||A_k(i_k,:)||^2, checked on the explicit Khatri-Rao product."""
+    g = np.random.default_rng(5)
+    A = g.standard_normal((13, 4)) * np.array([1.0, 3.0, 0.2, 7.0])
+    su, ru = orc.scores(A, orc.DIST_UNIFORM)
+    assert ru == 4 and np.all(su == 4 / 13)
+    sl, _ = orc.scores(A, orc.DIST_LENGTH_SQUARED)
+    rows = np.linalg.norm(A, axis=1) ** 2
+    np.testing.assert_allclose(sl, 4 * rows / np.linalg.norm(A) ** 2, rtol=1e-14)
+    assert abs(sl.sum() - 4) < 1e-12
+    mats = [g.standard_normal((n, 3)) for n in (5, 4, 6)]
+    Z = _ref.khatri_rao(mats)
+    bound = _ref.product_probs([np.linalg.norm(M, axis=1) ** 2 for M in mats])
+    assert np.all((Z ** 2).sum(axis=1) <= bound * (1 + 1e-12))
+    ps = [orc.scores(M, orc.DIST_LENGTH_SQUARED)[0] / 3 for M in mats]
+    np.testing.assert_allclose(_ref.product_probs(ps), bound / bound.sum(), rtol=1e-12)
+
+
+@pytest.mark.parametrize("dist", [1, 2])
+def test_sampling_distribution_app_b(orc, dist):
+    """Chi-square of random-only draws against the product of the per-factor uniform
+    or length-squared distributions (the implicit product sampling of Lemma 5.3
+    applies to any product distribution)."""
+    g = np.random.default_rng(40 + dist)
+    mats = [g.standard_normal((n, 2)) * np.exp(2 * g.standard_normal((n, 1))) for n in (6, 5, 4)]
+    ds = [orc.ModeDist(orc.scores(M, dist)[0], 2) for M in mats]
+    s = 60000
+    irnd, _, _ = orc.rnd_skrp(ds, s, 1.0, 0.0, 321, 0, 0)
+    pfull = _ref.product_probs([d.p for d in ds])
+    if dist == 1:
+        np.testing.assert_allclose(pfull, 1.0 / pfull.size, rtol=1e-12)
+    obs = np.bincount(irnd.astype(np.int64), minlength=pfull.size)
+    exp = pfull * s
+    keep = exp > 0
+    chi2 = float(((obs[keep] - exp[keep]) ** 2 / exp[keep]).sum())
+    dof = int(keep.sum()) - 1
+    assert chi2 < dof + 5 * math.sqrt(2 * dof)
+
+
+@pytest.mark.parametrize("dist", [1, 2])
+def test_unbiased_sketch_app_b(orc, dist):
+    """Lemma 3.3's unbiasedness E||Omega x||^2 = ||x||^2 holds for any sampling
+    distribution positive where x is nonzero: uniform and length-squared, hybrid."""
+    g = np.random.default_rng(50 + dist)
+    mats = [g.standard_normal((n, 2)) * np.exp(g.standard_normal((n, 1))) for n in (10, 8)]
+    ds = [orc.ModeDist(orc.scores(M, dist)[0], 2) for M in mats]
+    tau = 2.0 ** -6
+    x = g.standard_normal(80)
+    vals = []
+    for it in range(3000):
+        res = orc.skrp_lev(ds, 40, tau, 19, it, 0)
+        vals.append(math.fsum((res["wgt"] * x[res["idx"].astype(np.int64)]) ** 2))
+    vals = np.array(vals)
+    mean, sem = vals.mean(), vals.std() / math.sqrt(vals.size)
+    assert abs(mean - x @ x) < 4 * sem + 1e-12
+
+
+def test_app_b_all_rows_is_cp_als(orc):
+    """With tau = 0 every row of positive probability is deterministic (weight 1), so
+    an update under any of the three distributions is the exact CP-ALS update when
+    all probabilities are positive."""
+    coo = synth.random_sparse_tensor((6, 5, 4), 60, seed=8)
+    X = orc.Index(coo)
+    facs = synth.gaussian_factors(coo.dims, 3, seed=9)
+    outs = [orc.mode_update(X, facs, 1, rank=3, samples=24, tau=0.0, distribution=dist) for dist in (0, 1, 2)]
+    M, G = orc.exact_mttkrp(X, 1, facs)
+    A, _ = orc.solve(G, M)
+    An, _ = orc.normalize(A)
+    for o in outs:
+        assert o["sdet"] == 24
+        np.testing.assert_allclose(o["A"], An, rtol=1e-10, atol=1e-12)
