@@ -48,7 +48,9 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision series")
     p.add_argument("--no-equal-fit", action="store_true", help="skip the equal-fit comparison")
-    p.add_argument("--equal-fit-epochs", type=int, default=30)
+    p.add_argument("--equal-fit-restarts", type=int, default=16)
+    p.add_argument("--equal-fit-max-epochs", type=int, default=40)
+    p.add_argument("--equal-fit-fixed-epochs", type=int, default=30)
     p.add_argument("--no-batched", action="store_true", help="skip the 64-problem batched comparison")
     p.add_argument("--batched-problems", type=int, default=64)
     p.add_argument("--cpu-sample-updates", type=int, default=4,
@@ -343,7 +345,7 @@ def main():
         pk = FP64_PEAK_TFLOPS if b_f == 8 else FP32_PEAK_TFLOPS
         kg = {"bound": "alu", "kernel": f"k_krp_gram (sampled KRP rows + sampled Gram, {'FP64' if b_f == 8 else 'FP32'})",
               "achieved": kg_tf, "peak": pk, "unit": "TFLOP/s", "frac": (kg_tf / pk) if kg_tf else None,
-              "traffic": captured_traffic("k_krp_gram<double,4>", "paper_2006_16438_gb300/csrc/mttkrp.cu")
+              "traffic": captured_traffic("k_krp_gram<double,1>", "paper_2006_16438_gb300/csrc/mttkrp.cu")
               if b_f == 8 else None,
               "traffic_unit": "DRAM bytes per launch (ncu, profiles/traffic.json)",
               "peak_source": f"derived: 152 SMs x {2 if b_f == 8 else 128} {'FP64' if b_f == 8 else 'FP32'} "
@@ -387,7 +389,9 @@ def main():
     if not args.no_batched and rank == 0:
         line["batched"] = batched(cpa, args, stream)
     if mixed is not None and not args.no_equal_fit:
-        line["mixed_precision"]["equal_fit"] = equal_fit(cpa, index, init, seed, stream, args.equal_fit_epochs)
+        line["mixed_precision"]["equal_fit"] = equal_fit(cpa, coo, seed, stream,
+                                                             args.equal_fit_restarts, args.equal_fit_max_epochs,
+                                                             args.equal_fit_fixed_epochs)
     if rank == 0 and not args.no_e2e:
         line["e2e"] = e2e(cpa, coo, init, args)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
@@ -413,7 +417,7 @@ def batched(cpa, args, stream):
         p["index"] = cpa.cpa_index_build(p["coo"])
         p["init"] = synth.gaussian_factors(p["coo"].dims, p["rank"], seed=p["seed"])
     updates = sum(ETA * len(p["coo"].dims) for p in probs)
-    reps = max(1, min(args.steps, 5))
+    reps = max(3, min(args.steps, 7))
 
     def timed(fn):
         torch.cuda.synchronize()
@@ -436,9 +440,10 @@ def batched(cpa, args, stream):
                                     out=(state[i], outs[i][0], outs[i][1])).fit for i, p in enumerate(probs)]
 
         sequential(0)  # warm-up: plans and graphs
+        sequential(ETA)
         seq_ms, seq_fits = [], None
         for r in range(reps):
-            ms, seq_fits = timed(lambda: sequential(ETA * (r + 1)))
+            ms, seq_fits = timed(lambda: sequential(ETA * (r + 2)))
             seq_ms.append(ms)
         bprobs = [dict(index=p["index"], factors=[torch.from_numpy(a).cuda() for a in p["init"]], rank=p["rank"],
                        samples=p["samples"], tau=p["tau"], iters=ETA, seed=p["seed"], precision=precision)
@@ -446,17 +451,25 @@ def batched(cpa, args, stream):
         t1 = time.perf_counter()
         batch = cpa.Batch(bprobs, autotune=1)
         tune_s = time.perf_counter() - t1
-        batch.run()  # warm-up (the same first epoch as the sequential warm-up)
-        b_ms = []
+        batch.run()  # warm-up (the same first two epochs as the sequential warm-up)
+        batch.run()
+        b_ms, b_att, b_pdet = [], [], []
         for r in range(reps):
-            ms, _ = timed(batch.run)
+            ms, st = timed(batch.run)
             b_ms.append(ms)
+            worst = max(range(len(st)), key=lambda i: st[i]["attempts_last"])
+            b_att.append([worst, st[worst]["attempts_last"], probs[worst]["samples"]])
+            b_pdet.append(max(x["pdet_last"] for x in st))
         diffs = sorted(abs(a - b) for a, b in zip(seq_fits, batch.fits()))
-        seq_v = updates * reps / (sum(seq_ms) / 1000.0)
-        b_v = updates * reps / (sum(b_ms) / 1000.0)
-        res = {"sequential": {"value": seq_v, "unit": UNIT, "ms_per_pass": seq_ms},
-               "batched": {"value": b_v, "unit": UNIT, "ms_per_pass": b_ms},
+        seq_v = updates / (statistics.median(seq_ms) / 1000.0)
+        b_v = updates / (statistics.median(b_ms) / 1000.0)
+        res = {"sequential": {"value": seq_v, "unit": UNIT, "ms_per_pass": seq_ms,
+                              "value_mean": updates * reps / (sum(seq_ms) / 1000.0)},
+               "batched": {"value": b_v, "unit": UNIT, "ms_per_pass": b_ms,
+                           "value_mean": updates * reps / (sum(b_ms) / 1000.0),
+                           "most_attempts_per_pass": b_att, "max_pdet_per_pass": b_pdet},
                "speedup": b_v / seq_v,
+               "timing": "value = updates per pass / median pass time; value_mean = over the sum",
                "fit_diff_median": diffs[len(diffs) // 2], "fit_diff_max": diffs[-1],
                "autotune": batch.info(), "tune_s": tune_s}
         batch.free()
@@ -474,56 +487,80 @@ def batched(cpa, args, stream):
                         "one pass = one epoch (5 outer iterations + exact fit) of every problem"}
 
 
-def equal_fit(cpa, index, init, seed, stream, epochs):
-    """Mixed precision against FP64 at equal fit: FP64 runs `epochs` epochs from the
-    initial factors; the target is its final fit minus 1e-4; both paths are then timed
-    (CUDA events, epoch by epoch) until they first reach the target, mixed precision
-    for at most twice as many epochs."""
+def equal_fit(cpa, coo, seed, stream, restarts, max_epochs, fixed_epochs):
+    """Mixed precision against FP64 at equal fit, over `restarts` random initial
+    factors (Gaussian, Section 6), paired by restart:
+      - converged: each run to the stopping rule of Alg. 3 (exact fit after every
+        epoch of eta = 5 outer iterations; stop once the fit has not improved by more
+        than tol = 1e-4 for pi = 3 epochs), in FP64, in FP64 once more (the spread that
+        the order of floating-point atomics alone causes: the sampled rows of later
+        iterations depend on every bit of the factors) and in mixed precision;
+      - fixed: `fixed_epochs` epochs in each precision.
+    Times are CUDA events around each whole call; each precision runs on its own
+    index (so each keeps its cached workspace and graphs), warmed up first.  A change
+    of precision moves a randomized trajectory as a change of seed does, so fits are
+    compared as paired differences (mean and standard error over restarts)."""
     import torch
+    import synth
     s, tau = SAMPLES, 2.0 ** -TAU_EXP
+    dims = coo.dims
+    indices = {cpa.binding.FP64: cpa.cpa_index_build(coo), cpa.binding.MIXED: cpa.cpa_index_build(coo)}
 
-    def run(precision, max_epochs, target=None):
+    def run(init, precision, epochs, tol):
+        index = indices[precision]
         fs = [torch.from_numpy(a).cuda() for a in init]
         lam = torch.empty(RANK, dtype=torch.float64, device="cuda")
         fitd = torch.empty(1, dtype=torch.float64, device="cuda")
-        fits, ms = [], []
-        for ep in range(max_epochs):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            res = cpa.cp_arls_lev(index, None, rank=RANK, samples=s, tau=tau, iters=ETA, seed=seed,
-                                  iter_offset=ETA * ep, out=(fs, lam, fitd), precision=precision)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            fits.append(res.fit)
-            ms.append(e0.elapsed_time(e1))
-            if target is not None and res.fit >= target:
-                break
-        return fits, ms
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = cpa.cp_arls_lev(index, None, rank=RANK, samples=s, tau=tau, iters=ETA * epochs, seed=seed,
+                              tol=tol, patience=3, epoch_len=ETA, out=(fs, lam, fitd), precision=precision)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ep = res.stats["epochs"] if tol > 0 else epochs
+        return {"fit": res.fit, "epochs": ep, "ms": e0.elapsed_time(e1)}
 
-    f64_fits, f64_ms = run(cpa.binding.FP64, epochs)
-    target = f64_fits[-1] - 1e-4
-    fix_fits, fix_ms = run(cpa.binding.MIXED, epochs)  # same number of epochs
-    mx_fits, mx_ms = run(cpa.binding.MIXED, 2 * epochs, target)
+    keys = ("fp64", "fp64_rerun", "mixed", "fp64_fixed", "mixed_fixed")
+    runs = {k: [] for k in keys}
+    warm = synth.gaussian_factors(dims, RANK, seed=999)
+    for prec in indices:  # workspace and graphs of both call shapes
+        run(warm, prec, 2, 1e-4)
+        run(warm, prec, 2, 0.0)
+    for rs in range(restarts):
+        init = synth.gaussian_factors(dims, RANK, seed=1000 + rs)
+        runs["fp64"].append(run(init, cpa.binding.FP64, max_epochs, 1e-4))
+        runs["fp64_rerun"].append(run(init, cpa.binding.FP64, max_epochs, 1e-4))
+        runs["mixed"].append(run(init, cpa.binding.MIXED, max_epochs, 1e-4))
+        runs["fp64_fixed"].append(run(init, cpa.binding.FP64, fixed_epochs, 0.0))
+        runs["mixed_fixed"].append(run(init, cpa.binding.MIXED, fixed_epochs, 0.0))
 
-    def reach(fits, ms):
-        for i, f in enumerate(fits):
-            if f >= target:
-                return i + 1, sum(ms[:i + 1])
-        return None, None
+    def summary(rs):
+        f = np.array([r["fit"] for r in rs])
+        return {"fit_mean": float(f.mean()), "fit_sd": float(f.std(ddof=1)) if f.size > 1 else 0.0,
+                "fit_median": float(np.median(f)), "epochs_mean": float(np.mean([r["epochs"] for r in rs])),
+                "ms_total": sum(r["ms"] for r in rs),
+                "ms_per_epoch": sum(r["ms"] for r in rs) / sum(r["epochs"] for r in rs),
+                "fits": [round(r["fit"], 6) for r in rs], "epochs": [r["epochs"] for r in rs]}
 
-    e64, t64 = reach(f64_fits, f64_ms)
-    emx, tmx = reach(mx_fits, mx_ms)
-    return {"same_epochs": {"epochs": epochs, "fp64_fit": f64_fits[-1], "mixed_fit": fix_fits[-1],
-                            "fit_diff": fix_fits[-1] - f64_fits[-1],
-                            "fp64_ms": sum(f64_ms), "mixed_ms": sum(fix_ms),
-                            "throughput_ratio": sum(f64_ms) / sum(fix_ms)},
-            "target_fit": target, "fp64_final_fit": f64_fits[-1], "mixed_best_fit": max(mx_fits),
-            "fp64_epochs": e64, "fp64_ms": t64, "mixed_epochs": emx, "mixed_ms": tmx,
-            "speedup_at_equal_fit": (t64 / tmx) if (t64 and tmx) else None,
-            "note": f"target = FP64 fit after {epochs} epochs - 1e-4; epochs of {ETA} outer iterations; "
-                    "the randomized fits fluctuate by about 1e-4 near convergence, so the epoch at which a "
-                    "path first reaches the target is noisy"}
+    def paired(a, b):
+        d = np.array([x["fit"] - y["fit"] for x, y in zip(runs[a], runs[b])])
+        se = float(d.std(ddof=1) / math.sqrt(d.size)) if d.size > 1 else 0.0
+        return {"mean": float(d.mean()), "se": se, "abs_median": float(np.median(np.abs(d))),
+                "identical": int(np.sum(np.abs(d) < 1e-12))}
+
+    out = {k: summary(v) for k, v in runs.items()}
+    out.update({
+        "restarts": restarts, "max_epochs": max_epochs, "fixed_epochs": fixed_epochs, "tol": 1e-4, "patience": 3,
+        "fit_diff_converged": paired("mixed", "fp64"),
+        "fit_diff_fp64_rerun": paired("fp64_rerun", "fp64"),
+        "fit_diff_fixed": paired("mixed_fixed", "fp64_fixed"),
+        "speedup_at_convergence": out["fp64"]["ms_total"] / out["mixed"]["ms_total"],
+        "per_epoch_speedup": out["fp64_fixed"]["ms_per_epoch"] / out["mixed_fixed"]["ms_per_epoch"],
+        "note": "fit_diff_* = mixed - FP64 per restart (mean, standard error, median |diff|, count of "
+                "identical fits); fit_diff_fp64_rerun compares two FP64 runs of the same restart"})
+    return out
 
 
 def e2e(cpa, coo, init, args):

@@ -58,6 +58,9 @@ extern "C" {
 #define CPA_MIXED 1     /* factors, Grams, sampled products and row solves in FP32 (FP64
                            accumulation across tiles); r x r factorisations, sampling
                            probabilities and lambda in FP64 */
+#define CPA_DIST_LEVERAGE 0       /* row sampling by leverage scores (Lemma 5.3) */
+#define CPA_DIST_UNIFORM 1        /* uniform rows of every factor (App. B comparison) */
+#define CPA_DIST_LENGTH_SQUARED 2 /* squared row norms of every factor (App. B comparison) */
 #define CPA_FIT_NONE 0  /* no fit computed (fit output set to NaN) */
 #define CPA_FIT_EXACT 1 /* exact fit of Eq. 5.1 after the run (and per epoch if tol > 0) */
 #define CPA_FIT_ESTIMATED 2 /* estimated fit of Section 5.4 from a stratified sample of
@@ -99,6 +102,13 @@ typedef struct {
  *   iter_offset added to the outer iteration number in the Philox counter, so a run
  *               can be resumed with the same stream of draws
  *   precision   CPA_FP64 or CPA_MIXED
+ *   distribution  per-factor row distribution whose product is sampled:
+ *               CPA_DIST_LEVERAGE (the method), or for comparison (App. B)
+ *               CPA_DIST_UNIFORM (p_m(i) = 1/n_m) or CPA_DIST_LENGTH_SQUARED
+ *               (p_m(i) = ||A_m(i,:)||^2 / ||A_m||_F^2 of the factor as the next
+ *               Khatri-Rao product uses it: column-normalised after an update, as
+ *               given at the start); the threshold, weights and combining are the
+ *               same for all three
  *   fit_mode    CPA_FIT_EXACT, CPA_FIT_ESTIMATED or CPA_FIT_NONE
  *   fit_samples s_fit, elements in the sample of the estimated fit (>= 1; default
  *               2^27, the paper's Section 6 setting); used with CPA_FIT_ESTIMATED
@@ -121,6 +131,7 @@ typedef struct {
   uint64_t seed;
   uint64_t iter_offset;
   int32_t precision;
+  int32_t distribution;
   int32_t fit_mode;
   int64_t fit_samples;
   double fit_alpha;
@@ -160,7 +171,7 @@ typedef struct {
 typedef struct cpa_index cpa_index; /* opaque; owns device memory */
 
 /* Fills *opt with: rank 10, samples 2^17, tau 2^-17, iters 10, epoch_len 5,
- * patience 3, tol 0, seed 0, iter_offset 0, CPA_FP64, CPA_FIT_EXACT, fit_samples
+ * patience 3, tol 0, seed 0, iter_offset 0, CPA_FP64, CPA_DIST_LEVERAGE, CPA_FIT_EXACT, fit_samples
  * 2^27, fit_alpha 0.5, det_cap 2^24, reject_cap 4096, stream NULL. */
 void cpa_options_default(cpa_options* opt);
 
@@ -249,8 +260,9 @@ int cpa_batch_create(int32_t nprob, const cpa_index* const* indices, const cpa_o
                      double* const* lambdas, double* const* const* factors, double* const* fits,
                      int32_t autotune, void* stream, cpa_batch** out);
 /* Runs every call of the batch once (one graph launch, then one synchronisation).
- * stats (nprob entries, may be NULL): iters_done, mode_updates, warnings, sampled
- * counters; kernel_launches of the whole launch in stats[0]. Returns the first
+ * stats (nprob entries, may be NULL): iters_done, mode_updates, warnings, the
+ * sampled-row totals and the last update's counters (sdet, sbar, nnz_sampled,
+ * attempts, pdet); kernel_launches of the whole launch in stats[0]. Returns the first
  * negative status of a call, else the OR of the warnings. */
 int cpa_batch_run(cpa_batch* batch, void* stream, cpa_stats* stats);
 /* The SM budget chosen, the four candidate budgets and their timed milliseconds
@@ -278,6 +290,22 @@ int cp_arls_lev_coo(const cpa_coo* coo, const cpa_options* opt, double* lambda,
 int cpa_mode_update(const cpa_index* index, const cpa_options* opt, int32_t mode_k, uint64_t iter,
                     double* const* factors, double* lambda, uint64_t* idx, uint32_t* cnt, double* wgt,
                     int64_t* counts, double* pdet);
+
+/* ---- randomized range finder initialisation (App. F) ----------------------------- */
+
+/* Initial factor of mode `mode` as a random linear combination of the tensor's
+ * mode-k fibres (the columns of the unfolding X_(k)): A = X_(k)(:, S) Omega, S =
+ * s_init fibres drawn uniformly with replacement from the F_k nonzero fibres.  Draw j
+ * takes the fibre at position floor(u F_k / 2^64) in ascending order of the fibre's
+ * linear key (Eq. 2.2), u = word 0 of Philox4x64-10(counter (j, 0, 3<<32 | mode, 0),
+ * key (seed, 0)).
+ *   omega   device, s_init x r row-major doubles: the Gaussian combination weights,
+ *           drawn by the caller
+ *   A       device, n_mode x r row-major doubles out (overwritten)
+ * The sums are FP64 atomic additions (order not fixed).  Errors: CPA_ERR_ARG (mode
+ * out of range, s_init < 1, r outside [1, 64], empty tensor), CPA_ERR_CUDA. */
+int cpa_rrf_init(const cpa_index* index, int32_t mode, int64_t s_init, uint64_t seed, const double* omega,
+                 int32_t r, double* A, void* stream);
 
 /* ---- estimated fit (Section 5.4) ------------------------------------------------ */
 

@@ -118,6 +118,8 @@ def _declare(lib):
     lib.orc_mode_update_once.restype = I32
     lib.orc_cp_als.argtypes = [P, I32, I32, P, P, P]
     lib.orc_cp_als.restype = I32
+    lib.orc_rrf_init.argtypes = [P, I32, I64, U64, P, I32, P]
+    lib.orc_rrf_init.restype = I32
     lib.orc_scores.argtypes = [P, I64, I32, I32, P, P]
     lib.orc_scores.restype = I32
     lib.orc_fit_sample.argtypes = [P, I64, C.c_double, U64, I32, P, P, P, P]
@@ -382,6 +384,17 @@ def fit_estimate(index: Index, sample: FitSample, factors, lam):
     f = _lib().orc_fit_estimate(index.h, _ptr(coords), _ptr(xs), _ptr(counts), _ptr(phi), coords.shape[1],
                                 C.cast(fp, C.c_void_p), _ptr(lam), lam.shape[0], C.byref(F))
     return float(f), F.value
+
+
+def rrf_init(index: Index, k, omega, seed=0):
+    """Randomized range finder initial factor of mode k (App. F): X_(k)(:, S) omega."""
+    omega = _c(omega, np.float64)
+    s_init, r = omega.shape
+    A = np.zeros((index.dims[k], r))
+    rc = _lib().orc_rrf_init(index.h, int(k), int(s_init), int(seed), _ptr(omega), int(r), _ptr(A))
+    if rc < 0:
+        raise OracleError(rc, "rrf_init")
+    return A
 
 
 def scores(A, dist=DIST_LEVERAGE):

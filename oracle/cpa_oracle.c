@@ -874,6 +874,32 @@ double orc_fit_estimate(const orc_index* X, const int32_t* coords, const double*
 }
 
 /* ------------------------------------------------------------------------ */
+/* Randomized range finder initialisation (App. F): a random linear         */
+/* combination of s_init mode-k fibres (columns of the unfolding X_(k))     */
+/* drawn uniformly, with replacement, from the nonzero fibres.              */
+/* ------------------------------------------------------------------------ */
+int orc_rrf_init(const orc_index* X, int k, int64_t s_init, uint64_t seed, const double* omega, int r,
+                 double* A) {
+  if (k < 0 || k >= X->order || s_init < 1 || r < 1 || X->nnz < 1) return ORC_ERR_ARG;
+  const int64_t F = X->nfib[k];
+  memset(A, 0, sizeof(double) * (size_t)X->dims[k] * r);
+  const uint64_t key[2] = {seed, 0};
+  for (int64_t j = 0; j < s_init; ++j) {
+    const uint64_t ctr[4] = {(uint64_t)j, 0, (3ull << 32) | (uint64_t)k, 0};
+    uint64_t out[4];
+    orc_philox4x64_10(ctr, key, out);
+    /* the f-th nonzero fibre in ascending order of its linear key (Eq. 2.2) */
+    const int64_t f = scale_u64(out[0], F);
+    for (int64_t e = X->off[k][f]; e < X->off[k][f + 1]; ++e) {
+      const double x = X->val[k][e];
+      double* row = A + (size_t)X->ik[k][e] * r;
+      for (int c = 0; c < r; ++c) row[c] += x * omega[(size_t)j * r + c];
+    }
+  }
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Alg. 3                                                                   */
 /* ------------------------------------------------------------------------ */
 /* Row scores of one factor, summing to r, whose ratio to r is the factor's sampling

@@ -192,6 +192,15 @@ double orc_fit_estimate(const orc_index* X, const int32_t* coords, const double*
                         const int64_t* counts, const double* phi, int64_t stride,
                         const double* const* factors, const double* lambda, int r, double* F_hat_out);
 
+/* Randomized range finder initialisation of factor k (App. F):
+ * A = X_(k)(:, S) * Omega, S = s_init fibres drawn uniformly with replacement from the
+ * F_k nonzero mode-k fibres: draw j takes the fibre at position
+ * floor(u F_k / 2^64) in ascending order of the fibre's linear key (Eq. 2.2),
+ * u = word 0 of Philox(counter (j, 0, 3<<32 | k, 0), key (seed, 0)).  omega: s_init x r
+ * (the Gaussian draws, supplied by the caller), A: n_k x r out. */
+int orc_rrf_init(const orc_index* X, int k, int64_t s_init, uint64_t seed, const double* omega, int r,
+                 double* A);
+
 /* Standard CP-ALS (exact MTTKRP) with a fixed iteration count. */
 int orc_cp_als(const orc_index* X, int r, int iters, double* const* factors, double* lambda,
                double* fit);

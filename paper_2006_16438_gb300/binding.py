@@ -33,6 +33,9 @@ F32 = 1
 F64 = 2
 FP64 = 0
 MIXED = 1
+DIST_LEVERAGE = 0
+DIST_UNIFORM = 1
+DIST_LENGTH_SQUARED = 2
 FIT_NONE = 0
 FIT_EXACT = 1
 FIT_ESTIMATED = 2
@@ -42,7 +45,7 @@ EXPORTED = [
     "cpa_index_export", "cp_arls_lev", "cp_arls_lev_coo", "cpa_philox4x64", "cpa_leverage",
     "cpa_cdf", "cpa_skrp_lev", "cpa_sampled_mttkrp", "cpa_solve", "cpa_fit", "cpa_leverage_noalloc",
     "cpa_mode_update", "cp_als", "cpa_batch_create", "cpa_batch_run", "cpa_batch_info", "cpa_batch_free",
-    "cpa_fit_sample", "cpa_fit_estimate",
+    "cpa_fit_sample", "cpa_fit_estimate", "cpa_rrf_init",
 ]
 
 
@@ -62,7 +65,7 @@ class Options(C.Structure):
     _fields_ = [("rank", C.c_int32), ("samples", C.c_int64), ("tau", C.c_double), ("iters", C.c_int32),
                 ("epoch_len", C.c_int32), ("patience", C.c_int32), ("tol", C.c_double),
                 ("seed", C.c_uint64), ("iter_offset", C.c_uint64), ("precision", C.c_int32),
-                ("fit_mode", C.c_int32), ("fit_samples", C.c_int64), ("fit_alpha", C.c_double),
+                ("distribution", C.c_int32), ("fit_mode", C.c_int32), ("fit_samples", C.c_int64), ("fit_alpha", C.c_double),
                 ("det_cap", C.c_int64), ("reject_cap", C.c_int32),
                 ("profile", C.c_int32), ("stream", C.c_void_p)]
 
@@ -133,6 +136,7 @@ def _declare(lib):
         "cpa_solve": ([P, P, I64, I32, P, P, P], I32),
         "cpa_fit": ([P, P, P, I32, P, P], I32),
         "cpa_fit_sample": ([P, I64, D, U64, I32, P, P, P, P, P], I32),
+        "cpa_rrf_init": ([P, I32, I64, U64, P, I32, P, P], I32),
         "cpa_fit_estimate": ([P, P, P, P, P, I64, P, P, I32, I32, P, P, P], I32),
     }
     for name, (args, res) in sig.items():
@@ -279,7 +283,7 @@ class Result:
 def cp_arls_lev(index: Index, factors, *, rank, samples, tau=1.0, iters=10, epoch_len=5, patience=3,
                 tol=0.0, seed=0, iter_offset=0, fit_mode=FIT_EXACT, det_cap=1 << 24,
                 reject_cap=4096, on_device=True, profile=0, out=None, precision=FP64,
-                fit_samples=1 << 27, fit_alpha=0.5) -> Result:
+                fit_samples=1 << 27, fit_alpha=0.5, distribution=DIST_LEVERAGE) -> Result:
     """Alg. 3 on the GPU.  ``factors``: list of CUDA float64 tensors (n_k x rank), or
     numpy arrays with on_device=False.  Returns a Result with new factor copies."""
     torch = _torch()
@@ -287,7 +291,8 @@ def cp_arls_lev(index: Index, factors, *, rank, samples, tau=1.0, iters=10, epoc
                         epoch_len=int(epoch_len), patience=int(patience), tol=float(tol),
                         seed=int(seed), iter_offset=int(iter_offset), fit_mode=int(fit_mode),
                         det_cap=int(det_cap), reject_cap=int(reject_cap), profile=int(profile),
-                        precision=int(precision), fit_samples=int(fit_samples), fit_alpha=float(fit_alpha))
+                        precision=int(precision), fit_samples=int(fit_samples), fit_alpha=float(fit_alpha),
+                        distribution=int(distribution))
     o.stream = _stream()
     stats = Stats()
     fit = C.c_double(0.0)
@@ -346,6 +351,7 @@ class Batch:
                                       iter_offset=int(p.get("iter_offset", 0)),
                                       precision=int(p.get("precision", FP64)),
                                       fit_mode=int(p.get("fit_mode", FIT_EXACT)),
+                                      distribution=int(p.get("distribution", DIST_LEVERAGE)),
                                       fit_samples=int(p.get("fit_samples", 1 << 27)),
                                       fit_alpha=float(p.get("fit_alpha", 0.5)), stream=_stream())
         self._fac_arrays = [_ptr_array([f.data_ptr() for f in fs]) for fs in self.factors]
@@ -408,12 +414,13 @@ def cp_arls_lev_coo(coo, factors, *, rank, samples, tau=1.0, iters=10, seed=0, f
 
 
 def cpa_mode_update(index: Index, factors, k, *, rank, samples, tau=1.0, seed=0, it=0, precision=FP64,
-                    det_cap=1 << 24, reject_cap=4096):
+                    det_cap=1 << 24, reject_cap=4096, distribution=DIST_LEVERAGE):
     """One update of mode k.  factors: CUDA float64 tensors (factor k is replaced in
     place).  Returns dict(lam, idx, cnt, wgt, sbar, sdet, attempts, pdet, warnings)."""
     torch = _torch()
     o = default_options(rank=rank, samples=int(samples), tau=float(tau), seed=int(seed),
-                        precision=int(precision), det_cap=int(det_cap), reject_cap=int(reject_cap))
+                        precision=int(precision), det_cap=int(det_cap), reject_cap=int(reject_cap),
+                        distribution=int(distribution))
     o.stream = _stream()
     s = int(samples)
     lam = torch.empty(rank, dtype=torch.float64, device="cuda")
@@ -574,3 +581,17 @@ def cpa_fit_estimate(index: Index, sample: FitSample, factors, lam, precision=FP
                                    _ptr_array([f.data_ptr() for f in fs]), lam.shape[0], int(precision),
                                    C.byref(fit), C.byref(F), _stream()), "cpa_fit_estimate")
     return fit.value, F.value
+
+
+# --------------------------------------------------------------------------- range-finder init
+def cpa_rrf_init(index: Index, mode, omega, seed=0):
+    """Initial factor of ``mode`` (App. F): X_(k)(:, S) omega for s_init fibres drawn
+    uniformly; omega: s_init x r (CUDA or CPU float64).  Returns a CUDA tensor."""
+    torch = _torch()
+    om = omega.to(device="cuda", dtype=torch.float64).contiguous()
+    s_init, r = om.shape
+    n = index.dims[mode] if 0 <= mode < index.order else 1  # an invalid mode is the library's to reject
+    A = torch.empty((n, max(r, 1)), dtype=torch.float64, device="cuda")
+    _check(_lib().cpa_rrf_init(index.h, int(mode), int(s_init), int(seed), _ptr(om), int(r), _ptr(A), _stream()),
+           "cpa_rrf_init")
+    return A

@@ -135,14 +135,18 @@ struct DevBuf {
 // Leverage distribution of one factor: lev (optional), CDF C, info; A normalised in
 // place when `normalize_out` (the update path), untouched otherwise.
 // gram_zeroed: GA was already cleared by the previous kernel (the solve).
+// dist: the row distribution (leverage, or uniform / length-squared for comparison);
+// the Gram and its factor are formed in every case (lambda, normalisation).
 template <class FT>
 int refresh_distribution(FT* A, int64_t n, int r, uint64_t* C, DistInfo* info, double* Pm,
                          double* GA, SmallFactor* fac, int* warn, void* scan_scratch, bool normalize_out,
-                         double* lev_out, cudaStream_t st, bool gram_zeroed = false) {
+                         double* lev_out, cudaStream_t st, bool gram_zeroed = false, int dist = CPA_DIST_LEVERAGE) {
   if (!gram_zeroed) CPA_CUDA_TRY(cudaMemsetAsync(GA, 0, sizeof(double) * r * r, st));
   CPA_TRY(gram_rows<FT>(A, n, r, GA, st));
-  CPA_TRY(factor_spd(GA, r, 1, 1, 1e-12, fac, warn, CPA_WARN_RANK_DEFICIENT_LEV, st, info));
-  CPA_TRY(lev_rows<FT>(A, n, r, fac, lev_out, C, info, normalize_out ? A : nullptr, st));
+  // a rank-deficient factor matters only to leverage scores (warning bit 0: no warning)
+  CPA_TRY(factor_spd(GA, r, 1, 1, 1e-12, fac, warn, dist == CPA_DIST_LEVERAGE ? CPA_WARN_RANK_DEFICIENT_LEV : 0,
+                     st, info));
+  CPA_TRY(lev_rows<FT>(A, n, r, fac, lev_out, C, info, normalize_out ? A : nullptr, st, dist));
   CPA_TRY(cdf_from_q(C, C, n, info, Pm, scan_scratch, st));
   return CPA_OK;
 }
@@ -212,6 +216,9 @@ int check_options(const cpa_options* o) {
   if (!(o->tau >= 0.0 && o->tau <= 1.0)) return CPA_ERR_ARG;
   if (o->iters < 0 || o->reject_cap < 1 || o->det_cap < 1) return CPA_ERR_ARG;
   if (o->precision != CPA_FP64 && o->precision != CPA_MIXED) return CPA_ERR_ARG;
+  if (o->distribution != CPA_DIST_LEVERAGE && o->distribution != CPA_DIST_UNIFORM &&
+      o->distribution != CPA_DIST_LENGTH_SQUARED)
+    return CPA_ERR_ARG;
   if (o->fit_mode != CPA_FIT_EXACT && o->fit_mode != CPA_FIT_NONE && o->fit_mode != CPA_FIT_ESTIMATED)
     return CPA_ERR_ARG;
   if (o->fit_mode == CPA_FIT_ESTIMATED && (o->fit_samples < 1 || !(o->fit_alpha > 0.0 && o->fit_alpha <= 1.0)))
@@ -257,19 +264,26 @@ struct CallOut {
   int warnings;
   int64_t nnz_total;
   int64_t sbar_total;
+  int64_t sdet_last, sbar_last, nnz_last, attempts_last;
+  double pdet_last;
 };
 __global__ void k_call_out(const int* status, const int* warn, const DevStats* ds, CallOut* out) {
   out->status = *status;
   out->warnings = *warn;
   out->nnz_total = ds->nnz_total;
   out->sbar_total = ds->sbar_total;
+  out->sdet_last = ds->sdet_last;
+  out->sbar_last = ds->sbar_last;
+  out->nnz_last = ds->nnz_last;
+  out->attempts_last = ds->attempts_last;
+  out->pdet_last = ds->pdet_last;
 }
 
 constexpr int kEpochGraphMax = 256;  // longest fixed-length call run as one graph
 
 struct Plan {
   // key
-  int r = 0, D = 0, reject_cap = 0, profile = 0, prec = CPA_FP64, ftb = 8;
+  int r = 0, D = 0, reject_cap = 0, profile = 0, prec = CPA_FP64, ftb = 8, dist = CPA_DIST_LEVERAGE;
   int64_t s = 0, det_cap = 0, det_buf = 0;
   double tau = 0.0;
   uint64_t seed = 0;
@@ -312,7 +326,7 @@ struct Plan {
   bool matches(const cpa_options* o) const {
     return o->rank == r && o->samples == s && o->tau == tau && o->seed == seed &&
            o->reject_cap == reject_cap && o->det_cap == det_cap && (o->profile != 0) == (profile != 0) &&
-           o->precision == prec;
+           o->precision == prec && o->distribution == dist;
   }
 
   int init(const cpa_index* X, const cpa_options* o, cudaStream_t st) {
@@ -325,13 +339,16 @@ struct Plan {
     det_cap = o->det_cap;
     profile = o->profile != 0;
     prec = o->precision;
+    dist = o->distribution;
     ftb = prec == CPA_MIXED ? 4 : 8;
     det_buf = det_buffer_capacity(s, tau, det_cap);
     use_graph = !(tau < 1.0 && tau * (double)s < 1.0);  // no top-s host sync possible
     int64_t nmax = 1, nsum = 0;
+    bool slabs = false;  // some mode's M is accumulated slab by slab
     for (int m = 0; m < D; ++m) {
       nmax = std::max<int64_t>(nmax, X->dims[m]);
       nsum += X->dims[m];
+      slabs = slabs || mttkrp_slabs(X->dims[m], r, ftb) > 1;
     }
     KeyLayout Lsum;
     memset(&Lsum, 0, sizeof(Lsum));
@@ -360,7 +377,7 @@ struct Plan {
       scan_ws = a.take<char>(scan_workspace(nmax));
       iter_dev = a.take<uint64_t>(1);
       sample_buffers_carve(a, Lsum, s, det_buf, &SB[0]);
-      mttkrp_buffers_carve(a, s, &MB);
+      mttkrp_buffers_carve(a, s, r, ftb, slabs, &MB);
       if (pass == 0) {
         if (cudaMalloc((void**)&a.base, a.used) != cudaSuccess) return CPA_ERR_OOM;
         base = a.base;
@@ -430,7 +447,7 @@ struct Plan {
       CPA_TRY(solve_rows<FT>(Mt, nk, r, fsolve, Fk, st, GA));
       CPA_TRY(prof.mark(3));
       CPA_TRY(refresh_distribution<FT>(Fk, nk, r, Cm[k], info + k, Pm[k], GA, flev, warn, scan_ws, true,
-                                       nullptr, st, true));
+                                       nullptr, st, true, dist));
       k_finish_update<<<1, 64, 0, st>>>(flev, r, lam, dstats, SB[k].state, MB.total, warn);
       CPA_LAUNCH_CHECK();
       CPA_TRY(prof.mark(4));
@@ -492,10 +509,10 @@ struct Plan {
     for (int m = 0; m < D; ++m) {
       if (prec == CPA_MIXED)
         CPA_TRY(refresh_distribution<float>(static_cast<float*>(Fm[m]), X->dims[m], r, Cm[m], info + m,
-                                            Pm[m], GA, flev, warn, scan_ws, false, nullptr, st));
+                                            Pm[m], GA, flev, warn, scan_ws, false, nullptr, st, false, dist));
       else
         CPA_TRY(refresh_distribution<double>(static_cast<double*>(Fm[m]), X->dims[m], r, Cm[m], info + m,
-                                             Pm[m], GA, flev, warn, scan_ws, false, nullptr, st));
+                                             Pm[m], GA, flev, warn, scan_ws, false, nullptr, st, false, dist));
     }
     return CPA_OK;
   }
@@ -571,7 +588,7 @@ struct Plan {
     CPA_TRY(factor_spd(Gs, r, 0, 0, 1e-13, fsolve, warn, CPA_WARN_SINGULAR_GRAM, st));
     CPA_TRY(solve_rows<FT>(Mt, nk, r, fsolve, Fk, st));
     CPA_TRY(refresh_distribution<FT>(Fk, nk, r, Cm[k], info + k, Pm[k], GA, flev, warn, scan_ws, true,
-                                     nullptr, st));
+                                     nullptr, st, false, dist));
     k_copy_lambda<<<1, 64, 0, st>>>(flev, r, lam);
     CPA_LAUNCH_CHECK();
     return CPA_OK;
@@ -1100,7 +1117,7 @@ int cpa_sampled_mttkrp(const cpa_index* X, int32_t mode_k, const double* const* 
   for (int pass = 0; pass < 2; ++pass) {
     a.used = 0;
     packed = a.take<uint64_t>(sbar);
-    mttkrp_buffers_carve(a, sbar, &B);
+    mttkrp_buffers_carve(a, sbar, r, (int)sizeof(double), mttkrp_slabs(X->dims[mode_k], r, 8) > 1, &B);
     if (pass == 0) {
       CPA_TRY(buf.alloc(a.used, st));
       a.base = (char*)buf.p;
@@ -1139,6 +1156,15 @@ int cpa_solve(const double* G, const double* M, int64_t n, int32_t r, double* A,
   CPA_CUDA_TRY(cudaMemcpyAsync(&hwarn, warn, sizeof(int), cudaMemcpyDeviceToHost, st));
   CPA_CUDA_TRY(cudaStreamSynchronize(st));
   return hwarn;
+}
+
+int cpa_rrf_init(const cpa_index* X, int32_t mode, int64_t s_init, uint64_t seed, const double* omega, int32_t r,
+                 double* A, void* stream) {
+  if (!X) return CPA_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  CPA_TRY(rrf_enqueue(X, mode, s_init, seed, omega, r, A, st));
+  CPA_CUDA_TRY(cudaStreamSynchronize(st));
+  return CPA_OK;
 }
 
 int cpa_fit_sample(const cpa_index* X, int64_t fit_samples, double fit_alpha, uint64_t seed, int32_t reject_cap,
@@ -1307,12 +1333,13 @@ int cpa_mode_update(const cpa_index* X, const cpa_options* opt, int32_t mode_k, 
       k_convert<float, double><<<blocks(c), 256, 0, st>>>(factors[m], c, static_cast<float*>(P->Fm[m]));
       CPA_LAUNCH_CHECK();
       CPA_TRY(refresh_distribution<float>(static_cast<float*>(P->Fm[m]), X->dims[m], r, P->Cm[m], P->info + m,
-                                          P->Pm[m], P->GA, P->flev, P->warn, P->scan_ws, false, nullptr, st));
+                                          P->Pm[m], P->GA, P->flev, P->warn, P->scan_ws, false, nullptr, st, false,
+                                          P->dist));
     } else {
       CPA_CUDA_TRY(cudaMemcpyAsync(P->Fm[m], factors[m], sizeof(double) * c, cudaMemcpyDeviceToDevice, st));
       CPA_TRY(refresh_distribution<double>(static_cast<double*>(P->Fm[m]), X->dims[m], r, P->Cm[m],
                                            P->info + m, P->Pm[m], P->GA, P->flev, P->warn, P->scan_ws, false,
-                                           nullptr, st));
+                                           nullptr, st, false, P->dist));
     }
   }
   if (P->prec == CPA_MIXED) CPA_TRY(P->update_once<float>(X, mode_k, iter, idx, st));
@@ -1552,6 +1579,11 @@ int cpa_batch_run(cpa_batch* b, void* stream, cpa_stats* stats) {
       s.warnings = h[i].warnings;
       s.nnz_sampled_total = h[i].nnz_total;
       s.sbar_total = h[i].sbar_total;
+      s.sdet_last = h[i].sdet_last;
+      s.sbar_last = h[i].sbar_last;
+      s.nnz_sampled_last = h[i].nnz_last;
+      s.attempts_last = h[i].attempts_last;
+      s.pdet_last = h[i].pdet_last;
       s.kernel_launches = i == 0 ? b->kernels : 0;  // the whole batch is counted once
     }
   }

@@ -74,10 +74,12 @@ struct Philox4x64 {
   }
 };
 
-// Domain tags of the draws in the third counter word: Khatri-Rao row sampling and
-// the element sample of the estimated fit.
+// Domain tags of the draws in the third counter word: Khatri-Rao row sampling, the
+// element sample of the estimated fit and the fibre draws of the range-finder
+// initialisation.
 constexpr uint64_t kDomainSample = 1ull << 32;
 constexpr uint64_t kDomainFit = 2ull << 32;
+constexpr uint64_t kDomainRrf = 3ull << 32;
 
 // ---------------------------------------------------------------------------
 // Packed multi-index: other mode t occupies bits [off_t, off_t + bits_t) of a

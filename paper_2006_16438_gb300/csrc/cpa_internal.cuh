@@ -107,5 +107,11 @@ int index_build(const cpa_coo* coo, cudaStream_t st, cpa_index** out);
 void index_free(cpa_index* X);
 int index_export(const cpa_index* X, int k, uint64_t* keys, uint64_t* off, int32_t* ik,
                  void* val, cudaStream_t st);
+// Range-finder initial factor of mode k (App. F): A (n_k x r, zeroed here) =
+// X_(k)(:, S) omega with S = s_init fibres of mode k drawn uniformly (Philox domain
+// kDomainRrf | k, word 0 of counter (j, 0, ., 0), position floor(u F_k / 2^64) in key
+// order).  omega: s_init x r device doubles.
+int rrf_enqueue(const cpa_index* X, int k, int64_t s_init, uint64_t seed, const double* omega, int r,
+                double* A, cudaStream_t st);
 
 }  // namespace cpa

@@ -24,13 +24,14 @@ __device__ __forceinline__ void pair_of(int p, int r, int* a, int* b) {
 }
 
 // Factor rows of storage type FT are multiplied and summed in FP64 (the Gram feeds
-// leverage scores and the fit, both O(r^2 n) and far from the hot loop).
+// leverage scores and the fit).  The tile is converted to FP64 once when staged: on
+// GB300 a conversion issues on the FP64 pipe like a multiply-add.
 template <class FT, int PMAX>
 __global__ void __launch_bounds__(kGramThreads) k_gram_rows(const FT* __restrict__ A,
                                                             int64_t n, int r,
                                                             double* __restrict__ G) {
   extern __shared__ __align__(16) unsigned char gram_smem[];
-  FT* tile = reinterpret_cast<FT*>(gram_smem);  // kGramRows * r
+  double* tile = reinterpret_cast<double*>(gram_smem);  // kGramRows * r
   const int np = r * (r + 1) / 2;
   int pa[PMAX], pb[PMAX];
   double acc[PMAX];
@@ -46,14 +47,14 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_rows(const FT* __restrict
     __syncthreads();
     const FT* src = A + row0 * r;
     for (int i = threadIdx.x; i < kGramRows * r; i += kGramThreads)
-      tile[i] = i < rows * r ? src[i] : FT(0);
+      tile[i] = i < rows * r ? (double)src[i] : 0.0;
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < PMAX; ++q) {
       const int p = threadIdx.x + q * kGramThreads;
       if (p < np) {
         double s = 0.0;
-        for (int i = 0; i < rows; ++i) s = fma((double)tile[i * r + pa[q]], (double)tile[i * r + pb[q]], s);
+        for (int i = 0; i < rows; ++i) s = fma(tile[i * r + pa[q]], tile[i * r + pb[q]], s);
         acc[q] += s;
       }
     }
@@ -400,17 +401,29 @@ constexpr int64_t kManyRows = 1 << 16;  // from here on one thread per row
 // FP64 whatever the storage type FT of the factor:
 // kind 0: y = X P^T (S a), l = ||y||^2 over the rank's coordinates;
 // kind 1: l = (S a)^T F (S a).
+// Denominator of the length-squared score: ||B||_F^2 with B the column-normalised
+// factor (the number of nonzero columns) or the factor itself (sum of lambda_c^2).
+__device__ __forceinline__ double lensq_den(const SmallFactor* f, int r, bool normalised) {
+  double den = 0.0;
+  for (int c = 0; c < r; ++c) {
+    const double l = f->lambda[c];
+    den += normalised ? (pos_finite(l) ? 1.0 : 0.0) : l * l;
+  }
+  return den;
+}
+
 template <class FT>
 __global__ void __launch_bounds__(kRowThreads) k_lev_rows(const FT* A, int64_t n, int r,
                                                           const SmallFactor* __restrict__ f,
                                                           double* __restrict__ lev,
                                                           uint64_t* __restrict__ q,
-                                                          DistInfo* info, FT* A_out) {
+                                                          DistInfo* info, FT* A_out, int dist) {
   extern __shared__ __align__(16) unsigned char lev_smem[];
   double* F = reinterpret_cast<double*>(lev_smem);  // r * r
   double* sc = F + r * r;                           // r
   FT* lam = reinterpret_cast<FT*>(sc + r);          // r
   __shared__ int perm[kMaxRank];
+  __shared__ double brow[kRowThreads / 32][kMaxRank];  // each warp's row, scaled, FP64
   for (int i = threadIdx.x; i < r * r; i += blockDim.x) F[i] = f->F[i];
   for (int i = threadIdx.x; i < r; i += blockDim.x) {
     sc[i] = f->scale[i];
@@ -424,29 +437,42 @@ __global__ void __launch_bounds__(kRowThreads) k_lev_rows(const FT* A, int64_t n
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * kRowThreads + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * kRowThreads) >> 5;
+  const bool normalised = A_out != nullptr;
+  const double den = dist == CPA_DIST_LENGTH_SQUARED ? lensq_den(f, r, normalised) : 1.0;
   uint64_t my_max = 0;
   uint32_t my_nz = 0;
+  double* b = brow[threadIdx.x >> 5];
   for (int64_t row = gw; row < n; row += nwarps) {
     const FT* a = A + row * r;
     double part = 0.0;
+    if (dist == CPA_DIST_LEVERAGE) {
+      // S a_i converted and scaled once (one FP64-pipe operation each), not per use
+      __syncwarp();
+      for (int c = lane; c < r; c += 32) b[c] = (double)a[c] * sc[c];
+      __syncwarp();
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int c = lane + 32 * h;
-      if (c < k) {
-        double t = 0.0;
-        if (kind == 0) {
-          for (int u = 0; u <= c; ++u) {
-            const int pu = perm[u];
-            t = fma(F[c * r + u], (double)a[pu] * sc[pu], t);
+      for (int h = 0; h < 2; ++h) {
+        const int c = lane + 32 * h;
+        if (c < k) {
+          double t = 0.0;
+          if (kind == 0) {
+            for (int u = 0; u <= c; ++u) t = fma(F[c * r + u], b[perm[u]], t);
+            part = fma(t, t, part);
+          } else {
+            for (int u = 0; u < r; ++u) t = fma(F[c * r + u], b[u], t);
+            part = fma(b[c], t, part);
           }
-          part = fma(t, t, part);
-        } else {
-          for (int u = 0; u < r; ++u) t = fma(F[c * r + u], (double)a[u] * sc[u], t);
-          part = fma((double)a[c] * sc[c], t, part);
         }
+      }
+    } else if (dist == CPA_DIST_LENGTH_SQUARED) {
+      for (int c = lane; c < r; c += 32) {
+        const double b = normalised ? (double)a[c] * (double)lam[c] : (double)a[c];
+        part = fma(b, b, part);
       }
     }
     for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (dist == CPA_DIST_UNIFORM) part = (double)r / (double)n;
+    else if (dist == CPA_DIST_LENGTH_SQUARED) part = den > 0.0 ? (double)r * part / den : 0.0;
     if (lane == 0) {
       if (lev) lev[row] = part;
       if (q) {
@@ -518,14 +544,16 @@ __global__ void __launch_bounds__(kRowThreads) k_lev_rows_tpr(const FT* A, int64
                                                               const SmallFactor* __restrict__ f,
                                                               double* __restrict__ lev,
                                                               uint64_t* __restrict__ q,
-                                                              DistInfo* info, FT* A_out) {
+                                                              DistInfo* info, FT* A_out, int dist) {
   extern __shared__ __align__(16) unsigned char tpr_smem[];
   double* F = reinterpret_cast<double*>(tpr_smem);  // r * r
   double* sc = F + r * r;                           // r
   FT* lam = reinterpret_cast<FT*>(sc + r);          // r
-  FT* xs = lam + ((r + 1) & ~1);                    // kRowThreads * (r + 1), storage type
+  // rows staged as S a_i in FP64 (converted and scaled once each); an odd row stride
+  // in doubles keeps a half-warp's reads of one column in distinct banks
+  double* xs = reinterpret_cast<double*>(lam + ((r + 1) & ~1));  // kRowThreads * ld
   __shared__ int perm[kMaxRank];
-  const int ld = r + 1;
+  const int ld = r | 1;
   for (int i = threadIdx.x; i < r * r; i += blockDim.x) F[i] = f->F[i];
   for (int i = threadIdx.x; i < r; i += blockDim.x) {
     sc[i] = f->scale[i];
@@ -535,33 +563,44 @@ __global__ void __launch_bounds__(kRowThreads) k_lev_rows_tpr(const FT* A, int64
   }
   const int kind = f->kind;
   const int k = kind == 0 ? f->rank : r;
+  const bool normalised = A_out != nullptr;
+  const double den = dist == CPA_DIST_LENGTH_SQUARED ? lensq_den(f, r, normalised) : 1.0;
   uint64_t my_max = 0;
   uint32_t my_nz = 0;
   for (int64_t row0 = (int64_t)blockIdx.x * kRowThreads; row0 < n; row0 += (int64_t)gridDim.x * kRowThreads) {
     const int rows = (int)(n - row0 < kRowThreads ? n - row0 : kRowThreads);
     __syncthreads();
-    for (int i = threadIdx.x; i < rows * r; i += kRowThreads) {
-      const int rr = i / r, c = i - rr * r;
-      xs[rr * ld + c] = A[row0 * r + i];
-    }
+    if (dist == CPA_DIST_LEVERAGE)
+      for (int i = threadIdx.x; i < rows * r; i += kRowThreads) {
+        const int rr = i / r, c = i - rr * r;
+        xs[rr * ld + c] = (double)A[row0 * r + i] * sc[c];
+      }
     __syncthreads();
     if (threadIdx.x < rows) {
-      const FT* x = xs + threadIdx.x * ld;
-      double l = 0.0;
-      for (int c = 0; c < k; ++c) {
-        double t = 0.0;
-        if (kind == 0) {
-          for (int u = 0; u <= c; ++u) {
-            const int pu = perm[u];
-            t = fma(F[c * r + u], (double)x[pu] * sc[pu], t);
-          }
-          l = fma(t, t, l);
-        } else {
-          for (int u = 0; u < r; ++u) t = fma(F[c * r + u], (double)x[u] * sc[u], t);
-          l = fma((double)x[c] * sc[c], t, l);
-        }
-      }
+      const double* x = xs + threadIdx.x * ld;
       const int64_t row = row0 + threadIdx.x;
+      double l = 0.0;
+      if (dist == CPA_DIST_LEVERAGE) {
+        for (int c = 0; c < k; ++c) {
+          double t = 0.0;
+          if (kind == 0) {
+            for (int u = 0; u <= c; ++u) t = fma(F[c * r + u], x[perm[u]], t);
+            l = fma(t, t, l);
+          } else {
+            for (int u = 0; u < r; ++u) t = fma(F[c * r + u], x[u], t);
+            l = fma(x[c], t, l);
+          }
+        }
+      } else if (dist == CPA_DIST_UNIFORM) {
+        l = (double)r / (double)n;
+      } else {  // comparison distribution: read the row directly
+        const FT* a = A + row * r;
+        for (int c = 0; c < r; ++c) {
+          const double b = normalised ? (double)a[c] * (double)lam[c] : (double)a[c];
+          l = fma(b, b, l);
+        }
+        l = den > 0.0 ? (double)r * l / den : 0.0;
+      }
       if (lev) lev[row] = l;
       if (q) {
         double p = l / (double)r;
@@ -597,7 +636,7 @@ int gram_rows(const FT* A, int64_t n, int r, double* G, cudaStream_t st) {
   if (n <= 0) return CPA_OK;
   const int np = r * (r + 1) / 2;
   const unsigned grid = grid_cap(ceil_div(n, kGramRows), 4);
-  const size_t smem = sizeof(FT) * kGramRows * r;
+  const size_t smem = sizeof(double) * kGramRows * r;
   if (np <= kGramThreads)
     k_gram_rows<FT, 1><<<grid, kGramThreads, smem, st>>>(A, n, r, G);
   else if (np <= 4 * kGramThreads)
@@ -628,13 +667,15 @@ int factor_spd(const double* G, int r, int normalize, int pivot, double rel_tol,
 
 template <class FT>
 int lev_rows(const FT* A, int64_t n, int r, const SmallFactor* f, double* lev, uint64_t* q,
-             DistInfo* info, FT* A_out, cudaStream_t st) {
+             DistInfo* info, FT* A_out, cudaStream_t st, int dist) {
+  if (dist != CPA_DIST_LEVERAGE && dist != CPA_DIST_UNIFORM && dist != CPA_DIST_LENGTH_SQUARED)
+    return CPA_ERR_ARG;
   if (r < 1 || r > kMaxRank) return CPA_ERR_ARG;
   if (n <= 0) return CPA_OK;
   if (n >= kManyRows) {
     auto bytes = [](int rr) {
-      return sizeof(double) * ((size_t)rr * rr + rr) + sizeof(FT) * ((size_t)((rr + 1) & ~1) +
-                                                                      (size_t)kRowThreads * (rr + 1));
+      return sizeof(double) * ((size_t)rr * rr + rr) + sizeof(FT) * (size_t)((rr + 1) & ~1) +
+             sizeof(double) * (size_t)kRowThreads * (rr | 1);
     };
     const size_t smem = bytes(r);
     static bool attr = false;
@@ -644,19 +685,19 @@ int lev_rows(const FT* A, int64_t n, int r, const SmallFactor* f, double* lev, u
       attr = true;
     }
     const unsigned grid = grid_cap(ceil_div(n, kRowThreads), 8);
-    k_lev_rows_tpr<FT><<<grid, kRowThreads, smem, st>>>(A, n, r, f, lev, q, info, A_out);
+    k_lev_rows_tpr<FT><<<grid, kRowThreads, smem, st>>>(A, n, r, f, lev, q, info, A_out, dist);
   } else {
     const size_t smem = sizeof(double) * ((size_t)r * r + r) + sizeof(FT) * r;
     const unsigned grid = grid_cap(ceil_div(n, kRowThreads / 32), 16);
-    k_lev_rows<FT><<<grid, kRowThreads, smem, st>>>(A, n, r, f, lev, q, info, A_out);
+    k_lev_rows<FT><<<grid, kRowThreads, smem, st>>>(A, n, r, f, lev, q, info, A_out, dist);
   }
   CPA_LAUNCH_CHECK();
   return CPA_OK;
 }
 template int lev_rows<double>(const double*, int64_t, int, const SmallFactor*, double*, uint64_t*,
-                              DistInfo*, double*, cudaStream_t);
+                              DistInfo*, double*, cudaStream_t, int);
 template int lev_rows<float>(const float*, int64_t, int, const SmallFactor*, double*, uint64_t*,
-                             DistInfo*, float*, cudaStream_t);
+                             DistInfo*, float*, cudaStream_t, int);
 
 template <class FT>
 int solve_rows(const FT* M, int64_t n, int r, const SmallFactor* f, FT* A, cudaStream_t st,

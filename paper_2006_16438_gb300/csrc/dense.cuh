@@ -49,13 +49,19 @@ int factor_spd(const double* G, int r, int normalize, int pivot, double rel_tol,
                SmallFactor* out, int* warn, int warn_bit, cudaStream_t st,
                DistInfo* zero_info = nullptr);
 
-// For every row a_i of A: lev_i = || L^{-1} S a_i ||^2 (kind 0) or a_i^T S F S a_i
-// (kind 1); q_i = round-half-even(2^62 lev_i / r) written to q (if non-null),
-// DistInfo maxq/nnzq accumulated (zeroed by the caller); rows divided by lambda
-// (columns with lambda = 0 untouched) and written to A_out if non-null (may be A).
+// For every row a_i of A a sampling score s_i (sum over rows r):
+//   dist = CPA_DIST_LEVERAGE: s_i = || L^{-1} S a_i ||^2 (kind 0) or a_i^T S F S a_i
+//     (kind 1), the leverage score;
+//   dist = CPA_DIST_UNIFORM: s_i = r / n;
+//   dist = CPA_DIST_LENGTH_SQUARED: s_i = r ||b_i||^2 / ||B||_F^2 with B = A with its
+//     columns divided by lambda (zero columns dropped) if A_out is non-null (the
+//     factor the next Khatri-Rao product uses), else B = A;
+// q_i = round-half-even(2^62 s_i / r) written to q (if non-null), s_i to lev (if
+// non-null), DistInfo maxq/nnzq accumulated (zeroed by the caller); rows divided by
+// lambda (columns with lambda = 0 untouched) and written to A_out if non-null (may be A).
 template <class FT>
 int lev_rows(const FT* A, int64_t n, int r, const SmallFactor* f, double* lev,
-             uint64_t* q, DistInfo* info, FT* A_out, cudaStream_t st);
+             uint64_t* q, DistInfo* info, FT* A_out, cudaStream_t st, int dist = CPA_DIST_LEVERAGE);
 
 // A = M G^{-1} row by row with the factor of G (kind 0: two triangular solves;
 // kind 1: A = M F).

@@ -417,4 +417,49 @@ int index_export(const cpa_index* X, int k, uint64_t* keys, uint64_t* off, int32
   return CPA_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Range-finder initialisation (App. F): one warp per drawn fibre; lane c adds
+// x * omega(j, c) (and column c + 32) into row i of A for every nonzero (i, x) of the
+// fibre (FP64 atomics: rows are shared between fibres).
+// ---------------------------------------------------------------------------
+namespace {
+
+template <class VT>
+__global__ void __launch_bounds__(256) k_rrf(FibreIndex<VT> Xk, int k, int64_t s_init, uint64_t seed,
+                                             const double* __restrict__ omega, int r, double* __restrict__ A) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < s_init; j += nw) {
+    uint64_t w0 = (uint64_t)j, w1 = 0, w2 = kDomainRrf | (uint64_t)(uint32_t)k, w3 = 0;
+    Philox4x64::block(w0, w1, w2, w3, seed, 0ull);
+    const int64_t f = (int64_t)__umul64hi(w0, (uint64_t)Xk.nfib);
+    const double o0 = lane < r ? omega[j * r + lane] : 0.0;
+    const double o1 = lane + 32 < r ? omega[j * r + lane + 32] : 0.0;
+    for (uint64_t e = Xk.off[f]; e < Xk.off[f + 1]; ++e) {
+      const double x = (double)Xk.val[e];
+      double* row = A + (int64_t)Xk.ik[e] * r;
+      if (lane < r) atomicAdd(row + lane, x * o0);
+      if (lane + 32 < r) atomicAdd(row + lane + 32, x * o1);
+    }
+  }
+}
+
+}  // namespace
+
+int rrf_enqueue(const cpa_index* X, int k, int64_t s_init, uint64_t seed, const double* omega, int r,
+                double* A, cudaStream_t st) {
+  if (k < 0 || k >= X->order || s_init < 1 || r < 1 || r > kMaxRank || X->nnz < 1 || !omega || !A)
+    return CPA_ERR_ARG;
+  CPA_CUDA_TRY(cudaMemsetAsync(A, 0, sizeof(double) * (size_t)X->dims[k] * r, st));
+  const int64_t want = ceil_div(s_init, 8);
+  const unsigned grid = (unsigned)(want < (int64_t)num_sms() * 16 ? want : (int64_t)num_sms() * 16);
+  if (X->val_dtype == CPA_F32)
+    k_rrf<float><<<grid, 256, 0, st>>>(fibre_view<float>(X, k), k, s_init, seed, omega, r, A);
+  else
+    k_rrf<double><<<grid, 256, 0, st>>>(fibre_view<double>(X, k), k, s_init, seed, omega, r, A);
+  CPA_LAUNCH_CHECK();
+  return CPA_OK;
+}
+
 }  // namespace cpa

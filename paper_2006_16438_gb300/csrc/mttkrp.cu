@@ -14,6 +14,15 @@
 //    for every nonzero (i_k, x) of the fibre, adds x * u_j into row i_k of M.  Chunks
 //    are taken from a counter; fibres longer than kHeavy are listed and spread over
 //    the warps of one block each by k_tnsr_heavy.  The KRP rows are never written.
+//
+// When M does not fit in L2 (billions of nonzeros: n_k in the millions), its rows are
+// split into P slabs.  k_slab_prep probes every sample's fibre once, stores u_j and,
+// since the nonzeros of a fibre are sorted by i_k, where each slab's rows start in the
+// fibre; then for p = 0..P-1, k_slab_light and k_slab_heavy add the nonzeros of slab p
+// only.  Every nonzero is read once; the additions of one pass hit one slab of M,
+// small enough to stay in L2, instead of scattering over the whole of it in DRAM.
+#include <stdlib.h>
+
 #include "mttkrp.cuh"
 
 namespace cpa {
@@ -260,6 +269,215 @@ __global__ void __launch_bounds__(kThreads) k_tnsr_heavy(FibreIndex<VT> X, Facto
   }
 }
 
+// ---- row-slab path ----------------------------------------------------------
+constexpr int kSlabHeavy = 256;  // slab ranges longer than this go to the pass's heavy list
+
+// Per sample (a warp takes 32 consecutive samples): probe the fibre, store u_j and the
+// start of each slab's rows in the fibre (ballots over the loaded i_k for fibres of at
+// most 32 nonzeros, one bisection per slab boundary otherwise).
+template <class FT, class VT, int CPL>
+__global__ void __launch_bounds__(kThreads) k_slab_prep(FibreIndex<VT> X, FactorPtrs F, KeyLayout L, int r,
+                                                        const uint64_t* __restrict__ idx,
+                                                        const double* __restrict__ wgt, DevCount sbar,
+                                                        int64_t slab_rows, int P, FT* __restrict__ U,
+                                                        uint64_t* __restrict__ los, uint32_t* __restrict__ bnd,
+                                                        unsigned long long* __restrict__ ctr) {
+  const int lane = threadIdx.x & 31;
+  const int64_t n = sbar.get();
+  const int64_t gw = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * kThreads) >> 5;
+  uint64_t my_nnz = 0;
+  for (int64_t base = gw * 32; base < n; base += nw * 32) {
+    const int64_t j = base + lane;
+    uint64_t key = 0, lo = 0, hi = 0;
+    FT w = FT(0);
+    if (j < n) {
+      key = idx[j];
+      X.probe(key, &lo, &hi);
+      w = (FT)wgt[j];
+      los[j] = lo;
+    }
+    const uint32_t len = (uint32_t)(hi - lo);
+    my_nnz += len;
+    const int cnt = (int)(n - base < 32 ? n - base : 32);
+    for (int q = 0; q < cnt; ++q) {
+      const int64_t jq = base + q;
+      const uint32_t lq = __shfl_sync(0xffffffffu, len, q);
+      const uint64_t kq = __shfl_sync(0xffffffffu, key, q);
+      const uint64_t oq = __shfl_sync(0xffffffffu, lo, q);
+      const FT wq = __shfl_sync(0xffffffffu, w, q);
+#pragma unroll
+      for (int v = 0; v < CPL; ++v) {
+        const int c = lane + 32 * v;
+        if (c < r) {
+          FT z = wq * wq;
+          for (int t = 0; t < L.d; ++t)
+            z *= static_cast<const FT*>(F.A[L.mode[t]])[(int64_t)L.get(kq, t) * r + c];
+          U[jq * r + c] = z;
+        }
+      }
+      uint32_t b = 0;
+      if (lq <= 32) {
+        const int32_t ik = lane < (int)lq ? X.ik[oq + lane] : INT32_MAX;
+        for (int p2 = 1; p2 < P; ++p2) {
+          const uint32_t below = __popc(__ballot_sync(0xffffffffu, (int64_t)ik < (int64_t)p2 * slab_rows));
+          if (lane == p2) b = below;
+        }
+      } else if (lane > 0 && lane < P) {
+        const int64_t target = (int64_t)lane * slab_rows;
+        uint64_t a = 0, z = lq;
+        while (a < z) {
+          const uint64_t mid = a + ((z - a) >> 1);
+          if ((int64_t)X.ik[oq + mid] < target) a = mid + 1; else z = mid;
+        }
+        b = (uint32_t)a;
+      }
+      if (lane == P) b = lq;
+      if (lane <= P) bnd[jq * 32 + lane] = b;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) my_nnz += __shfl_xor_sync(0xffffffffu, my_nnz, o);
+  if (lane == 0 && my_nnz) atomicAdd(&ctr[0], (unsigned long long)my_nnz);
+}
+
+// Pass p, light part: warps take chunks of 32 samples; a sample's range of slab p
+// longer than kSlabHeavy is listed for k_slab_heavy, the others are walked as in
+// k_tnsr_mttkrp with u_j read back (the nonzero stream is read once: streaming loads).
+template <class FT, class VT, int CPL>
+__global__ void __launch_bounds__(kThreads) k_slab_light(FibreIndex<VT> X, int r, DevCount sbar, int p,
+                                                         const FT* __restrict__ U,
+                                                         const uint64_t* __restrict__ los,
+                                                         const uint32_t* __restrict__ bnd, FT* __restrict__ M,
+                                                         unsigned long long* __restrict__ pctr,
+                                                         uint4* __restrict__ heavy) {
+  const int lane = threadIdx.x & 31;
+  const int64_t n = sbar.get();
+  const int64_t nchunks = (n + 31) >> 5;
+  for (;;) {
+    unsigned long long cidx = 0;
+    if (lane == 0) cidx = atomicAdd(&pctr[0], 1ull);
+    cidx = __shfl_sync(0xffffffffu, cidx, 0);
+    if ((int64_t)cidx >= nchunks) break;
+    const int64_t j = (int64_t)cidx * 32 + lane;
+    uint64_t start = 0;
+    uint32_t len = 0;
+    if (j < n) {
+      const uint32_t a = bnd[j * 32 + p], b = bnd[j * 32 + p + 1];
+      len = b - a;
+      start = los[j] + a;
+    }
+    if (len > kSlabHeavy) {
+      const unsigned long long h = atomicAdd(&pctr[1], 1ull);
+      heavy[h] = make_uint4((unsigned)j, (unsigned)(start & 0xffffffffu), (unsigned)(start >> 32), len);
+      len = 0;
+    }
+    unsigned todo = __ballot_sync(0xffffffffu, len > 0);
+    while (todo) {
+      const int q = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const uint32_t lq = __shfl_sync(0xffffffffu, len, q);
+      const uint64_t sq = __shfl_sync(0xffffffffu, start, q);
+      const int64_t jq = (int64_t)cidx * 32 + q;
+      FT u[CPL];
+#pragma unroll
+      for (int v = 0; v < CPL; ++v) {
+        const int c = lane + 32 * v;
+        u[v] = c < r ? U[jq * r + c] : FT(0);
+      }
+      for (uint32_t g = 0; g < lq; g += 32) {
+        const int nb = lq - g < 32 ? (int)(lq - g) : 32;
+        int32_t ikl = 0;
+        FT xl = FT(0);
+        if (lane < nb) {
+          ikl = __ldcs(X.ik + sq + g + lane);
+          xl = (FT)__ldcs(X.val + sq + g + lane);
+        }
+        for (int q2 = 0; q2 < nb; ++q2) {
+          const int32_t ik = __shfl_sync(0xffffffffu, ikl, q2);
+          const FT x = __shfl_sync(0xffffffffu, xl, q2);
+#pragma unroll
+          for (int v = 0; v < CPL; ++v) {
+            const int c = lane + 32 * v;
+            if (c < r) atomicAdd(&M[(int64_t)ik * r + c], x * u[v]);
+          }
+        }
+      }
+    }
+  }
+}
+
+// Pass p, heavy part: one block per listed range, its warps taking groups of 32.
+template <class FT, class VT, int CPL>
+__global__ void __launch_bounds__(kThreads) k_slab_heavy(FibreIndex<VT> X, int r, const FT* __restrict__ U,
+                                                         FT* __restrict__ M,
+                                                         const unsigned long long* __restrict__ pctr,
+                                                         const uint4* __restrict__ heavy) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t nh = (int64_t)pctr[1];
+  for (int64_t h = blockIdx.x; h < nh; h += gridDim.x) {
+    const uint4 e = heavy[h];
+    const int64_t j = e.x;
+    const uint64_t start = (uint64_t)e.y | ((uint64_t)e.z << 32);
+    const uint32_t len = e.w;
+    FT u[CPL];
+#pragma unroll
+    for (int v = 0; v < CPL; ++v) {
+      const int c = lane + 32 * v;
+      u[v] = c < r ? U[j * r + c] : FT(0);
+    }
+    for (uint64_t g = (uint64_t)warp * 32; g < len; g += kThreads) {
+      const int nb = len - g < 32 ? (int)(len - g) : 32;
+      int32_t ikl = 0;
+      FT xl = FT(0);
+      if (lane < nb) {
+        ikl = __ldcs(X.ik + start + g + lane);
+        xl = (FT)__ldcs(X.val + start + g + lane);
+      }
+      for (int q2 = 0; q2 < nb; ++q2) {
+        const int32_t ik = __shfl_sync(0xffffffffu, ikl, q2);
+        const FT x = __shfl_sync(0xffffffffu, xl, q2);
+#pragma unroll
+        for (int v = 0; v < CPL; ++v) {
+          const int c = lane + 32 * v;
+          if (c < r) atomicAdd(&M[(int64_t)ik * r + c], x * u[v]);
+        }
+      }
+    }
+  }
+}
+
+template <class FT, class VT>
+int launch_mttkrp_slabs(const cpa_index* X, int k, const FactorPtrs& F, int r, const uint64_t* idx,
+                        const double* wgt, DevCount sbar, FT* M, MttkrpBuffers& B, int P, cudaStream_t st) {
+  const FibreIndex<VT> fx = fibre_view<VT>(X, k);
+  const KeyLayout& L = X->mode[k].L;
+  const int sms = num_sms();
+  const int64_t nk = X->dims[k];
+  const int64_t slab_rows = ceil_div(nk, P);
+  unsigned long long* ctr = reinterpret_cast<unsigned long long*>(B.ctr);
+  uint4* heavy = reinterpret_cast<uint4*>(B.heavy);
+  FT* U = static_cast<FT*>(B.U);
+  const int64_t want = ceil_div(sbar.max, (int64_t)kThreads);
+  const unsigned grid = (unsigned)(want < (int64_t)sms * 8 ? (want > 0 ? want : 1) : (int64_t)sms * 8);
+  if (r <= 32)
+    k_slab_prep<FT, VT, 1><<<grid, kThreads, 0, st>>>(fx, F, L, r, idx, wgt, sbar, slab_rows, P, U, B.los, B.bnd, ctr);
+  else
+    k_slab_prep<FT, VT, 2><<<grid, kThreads, 0, st>>>(fx, F, L, r, idx, wgt, sbar, slab_rows, P, U, B.los, B.bnd, ctr);
+  CPA_LAUNCH_CHECK();
+  for (int p = 0; p < P; ++p) {
+    unsigned long long* pctr = ctr + 4 + 2 * p;
+    if (r <= 32) {
+      k_slab_light<FT, VT, 1><<<grid, kThreads, 0, st>>>(fx, r, sbar, p, U, B.los, B.bnd, M, pctr, heavy);
+      k_slab_heavy<FT, VT, 1><<<(unsigned)sms * 2, kThreads, 0, st>>>(fx, r, U, M, pctr, heavy);
+    } else {
+      k_slab_light<FT, VT, 2><<<grid, kThreads, 0, st>>>(fx, r, sbar, p, U, B.los, B.bnd, M, pctr, heavy);
+      k_slab_heavy<FT, VT, 2><<<(unsigned)sms * 2, kThreads, 0, st>>>(fx, r, U, M, pctr, heavy);
+    }
+    CPA_LAUNCH_CHECK();
+  }
+  return CPA_OK;
+}
+
 template <class FT>
 int launch_gram(const FactorPtrs& F, const KeyLayout& L, int r, const uint64_t* idx, const double* wgt,
                 DevCount sbar, double* G, cudaStream_t st) {
@@ -325,10 +543,39 @@ int launch_mttkrp(const cpa_index* X, int k, const FactorPtrs& F, int r, const u
 
 }  // namespace
 
-void mttkrp_buffers_carve(Arena& a, int64_t s, MttkrpBuffers* B) {
-  B->ctr = a.take<uint64_t>(4);
+size_t mttkrp_slab_bytes() {
+  const char* e = getenv("CPA_MTTKRP_SLAB_BYTES");
+  if (e) {
+    const long long v = atoll(e);
+    if (v > 0) return (size_t)v;
+  }
+  return size_t(32) << 20;
+}
+
+int mttkrp_slabs(int64_t nk, int r, int ftb) {
+  const size_t bytes = (size_t)nk * r * ftb;
+  const size_t slab = mttkrp_slab_bytes();
+  if (bytes <= slab || nk < 2) return 1;
+  int64_t P = (int64_t)((bytes + slab - 1) / slab);
+  if (P > kSlabMax) P = kSlabMax;
+  if (P > nk) P = nk;
+  return (int)P;
+}
+
+void mttkrp_buffers_carve(Arena& a, int64_t s, int r, int ftb, bool slabs, MttkrpBuffers* B) {
+  const size_t ss = (size_t)(s > 0 ? s : 1);
+  B->ctr = a.take<uint64_t>(kMttkrpCounters);
   B->total = B->ctr;
-  B->heavy = a.take<uint32_t>(4 * (size_t)(s > 0 ? s : 1));
+  B->heavy = a.take<uint32_t>(4 * ss);
+  if (slabs) {
+    B->U = a.take<char>(ss * r * ftb);
+    B->los = a.take<uint64_t>(ss);
+    B->bnd = a.take<uint32_t>(32 * ss);
+  } else {
+    B->U = nullptr;
+    B->los = nullptr;
+    B->bnd = nullptr;
+  }
 }
 
 template <class FT>
@@ -338,10 +585,15 @@ int sampled_mttkrp(const cpa_index* X, int k, const FactorPtrs& F, int r, const 
   if (r < 1 || r > kMaxRank) return CPA_ERR_ARG;
   CPA_CUDA_TRY(cudaMemsetAsync(M, 0, sizeof(FT) * X->dims[k] * r, st));
   CPA_CUDA_TRY(cudaMemsetAsync(G, 0, sizeof(double) * r * r, st));
-  CPA_CUDA_TRY(cudaMemsetAsync(B.ctr, 0, 4 * sizeof(uint64_t), st));
+  CPA_CUDA_TRY(cudaMemsetAsync(B.ctr, 0, kMttkrpCounters * sizeof(uint64_t), st));
   if (sbar.max <= 0) return CPA_OK;
   const KeyLayout& L = X->mode[k].L;
+  const int P = B.U ? mttkrp_slabs(X->dims[k], r, (int)sizeof(FT)) : 1;
   auto mttkrp = [&](cudaStream_t s2) {
+    if (P > 1)
+      return X->val_dtype == CPA_F32
+                 ? launch_mttkrp_slabs<FT, float>(X, k, F, r, idx_packed, wgt, sbar, M, B, P, s2)
+                 : launch_mttkrp_slabs<FT, double>(X, k, F, r, idx_packed, wgt, sbar, M, B, P, s2);
     return X->val_dtype == CPA_F32
                ? launch_mttkrp<FT, float>(X, k, F, r, idx_packed, wgt, sbar, M, B, s2)
                : launch_mttkrp<FT, double>(X, k, F, r, idx_packed, wgt, sbar, M, B, s2);

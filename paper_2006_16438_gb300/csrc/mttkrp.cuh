@@ -12,12 +12,27 @@ struct FactorPtrs {
 
 // Device buffers of one sampled MTTKRP for up to s samples.
 struct MttkrpBuffers {
-  uint64_t* ctr;     // 4: sampled nonzeros, chunk counter, heavy-list length, spare
+  uint64_t* ctr;     // kMttkrpCounters: sampled nonzeros, chunk counter, heavy-list
+                     // length, spare, then per row slab its chunk counter and heavy length
   uint64_t* total;   // = ctr: nnz of the sampled right-hand side
   uint32_t* heavy;   // 4 s: (sample, fibre start lo/hi words, length) of long fibres
+  // row-slab path (null when no mode's M exceeds one slab): per sample u_j
+  // (s x r, run element type), fibre start, and the start of each slab's rows
+  // within the fibre (s x 32 u32, slab p at column p, the fibre length at column P)
+  void* U = nullptr;
+  uint64_t* los = nullptr;
+  uint32_t* bnd = nullptr;
 };
+constexpr int kMttkrpCounters = 4 + 2 * 32;
+constexpr int kSlabMax = 31;  // most row slabs of one M
 
-void mttkrp_buffers_carve(Arena& a, int64_t s, MttkrpBuffers* B);
+// Bytes of M per row slab: M larger than this is accumulated slab by slab so that
+// the scattered additions of a pass stay in L2 (CPA_MTTKRP_SLAB_BYTES overrides).
+size_t mttkrp_slab_bytes();
+// Number of row slabs of an n_k x r M of ftb-byte elements (1: no slabs).
+int mttkrp_slabs(int64_t nk, int r, int ftb);
+
+void mttkrp_buffers_carve(Arena& a, int64_t s, int r, int ftb, bool slabs, MttkrpBuffers* B);
 
 // A side stream and two events (created without timing) with which the Gram and the
 // MTTKRP run as two branches; aux = null runs them one after the other.

@@ -20,6 +20,7 @@ if not torch.cuda.is_available():  # collected on CPU machines, skipped there
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
 import paper_2006_16438_gb300 as cpa  # noqa: E402
+from paper_2006_16438_gb300 import binding  # noqa: E402
 
 
 def relerr(a, b):
@@ -234,6 +235,43 @@ def test_sampled_mttkrp_empty_fibres_and_heavy_fibre():
     assert relerr(M.cpu().numpy(), Mr) < 1e-12 and relerr(G.cpu().numpy(), Gr) < 1e-12
 
 
+@pytest.mark.parametrize("slab_bytes", [64, 4096])
+@pytest.mark.parametrize("dims,nnz,r,s,tau", [
+    ((300, 20, 25), 30000, 5, 2000, 1.0),
+    ((3000, 4, 5), 20000, 25, 500, 1.0),      # fibres of about 1000 nonzeros: heavy slab ranges
+    ((183, 24, 1140, 1717), 200000, 25, 2 ** 14, 2.0 ** -14),
+    ((500, 40, 30), 20000, 40, 5000, 1.0),    # r > 32: two columns per lane
+])
+def test_sampled_mttkrp_row_slabs_vs_oracle(monkeypatch, slab_bytes, dims, nnz, r, s, tau):
+    """The row-slab path (M accumulated one slab of rows at a time, every fibre cut at
+    the slab boundaries of its sorted i_k), forced at these sizes by a small slab."""
+    monkeypatch.setenv("CPA_MTTKRP_SLAB_BYTES", str(slab_bytes))
+    coo = synth.random_sparse_tensor(dims, nnz, seed=9)
+    facs = synth.gaussian_factors(dims, r, seed=2)
+    gi = cpa.cpa_index_build(coo)
+    oi = oracle.Index(coo)
+    for k in range(len(dims)):
+        smp = _sample_for(coo, facs, k, r, s, tau)
+        M, G, nz = cpa.cpa_sampled_mttkrp(gi, k, [cu(f) for f in facs], cu(smp["idx"]), cu(smp["wgt"]))
+        Mr, Gr, nzr = oracle.sampled_mttkrp(oi, k, facs, smp["idx"], smp["wgt"])
+        assert nz == nzr
+        assert relerr(M.cpu().numpy(), Mr) < 1e-12
+        assert relerr(G.cpu().numpy(), Gr) < 1e-12
+
+
+def test_whole_run_row_slabs(monkeypatch):
+    """Alg. 3 with every mode's M in row slabs (FP64: factors within 1e-10 of the
+    oracle; mixed precision runs)."""
+    monkeypatch.setenv("CPA_MTTKRP_SLAB_BYTES", "256")
+    coo = synth.small_planted_tensor(0)
+    _compare_run(coo, 4, 1024, 1.0 / 1024, 5)
+    gi = cpa.cpa_index_build(coo)
+    init = synth.gaussian_factors(coo.dims, 4, seed=0)
+    res = cpa.cp_arls_lev(gi, [cu(a) for a in init], rank=4, samples=1024, tau=1.0 / 1024, iters=5,
+                          precision=binding.MIXED)
+    assert np.isfinite(res.fit)
+
+
 def test_solve_vs_oracle():
     g = np.random.default_rng(7)
     for n, r in [(1, 1), (183, 25), (5000, 25), (77, 64)]:
@@ -269,13 +307,14 @@ def test_fit_vs_oracle():
 
 
 # --------------------------------------------------------------------------- whole runs
-def _compare_run(coo, r, s, tau, iters, seed=0, init_seed=0, tol_f=1e-10):
+def _compare_run(coo, r, s, tau, iters, seed=0, init_seed=0, tol_f=1e-10, dist=0):
     init = synth.gaussian_factors(coo.dims, r, seed=init_seed)
     gi = cpa.cpa_index_build(coo)
-    res = cpa.cp_arls_lev(gi, [cu(a) for a in init], rank=r, samples=s, tau=tau, iters=iters, seed=seed)
+    res = cpa.cp_arls_lev(gi, [cu(a) for a in init], rank=r, samples=s, tau=tau, iters=iters, seed=seed,
+                          distribution=dist)
     oi = oracle.Index(coo)
     lam, fs, fit, done, warn = oracle.cp_arls_lev(oi, init, rank=r, samples=s, tau=tau, iters=iters,
-                                                  seed=seed)
+                                                  seed=seed, distribution=dist)
     errs = [relerr(a.cpu().numpy(), b) for a, b in zip(res.factors, fs)]
     assert max(errs) < tol_f, errs
     assert relerr(res.lam.cpu().numpy(), lam) < tol_f
@@ -294,6 +333,15 @@ def test_small_planted_hybrid():
     coo = synth.small_planted_tensor(0)
     res, fit = _compare_run(coo, 4, 1024, 1.0 / 1024, 5)
     assert res.stats["sdet_last"] > 0
+
+
+@pytest.mark.parametrize("dist", [oracle.DIST_UNIFORM, oracle.DIST_LENGTH_SQUARED])
+@pytest.mark.parametrize("tau", [1.0, 1.0 / 1024])
+def test_app_b_distributions_whole_run(dist, tau):
+    """Uniform and length-squared sampling (App. B) through the whole of Alg. 3, random
+    and hybrid, on the small planted tensor and a ragged 4-way tensor."""
+    _compare_run(synth.small_planted_tensor(0), 4, 1024, tau, 6, dist=dist)
+    _compare_run(synth.random_sparse_tensor((37, 29, 41, 13), 20000, seed=3), 6, 3000, tau, 3, dist=dist)
 
 
 @pytest.mark.parametrize("dims,nnz,r,s", [((37, 29, 41, 13), 20000, 6, 3000), ((40, 30, 20), 8000, 3, 500),

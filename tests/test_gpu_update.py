@@ -57,6 +57,28 @@ def test_mode_update_fp64_matches_oracle(case):
         assert relerr(got["lam"].cpu().numpy(), ref["lam"]) < 1e-10
 
 
+@pytest.mark.parametrize("dist", [binding.DIST_UNIFORM, binding.DIST_LENGTH_SQUARED])
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_mode_update_app_b_matches_oracle(case, dist):
+    """Uniform and length-squared sampling (App. B): rows and counts bit-exact (the
+    uniform scores are the same two IEEE operations on both sides; length-squared
+    scores agree to the last bits), weights to 1e-13, the new factor to 1e-10."""
+    dims, nnz, r, s, tau = CASES[case]
+    coo = synth.random_sparse_tensor(dims, nnz, seed=case + 1)
+    facs = synth.gaussian_factors(dims, r, seed=case + 2)
+    gi = cpa.cpa_index_build(coo)
+    oi = oracle.Index(coo)
+    for k in range(len(dims)):
+        fs = [torch.from_numpy(a).cuda() for a in facs]
+        got = cpa.cpa_mode_update(gi, fs, k, rank=r, samples=s, tau=tau, seed=7, it=3, distribution=dist)
+        ref = oracle.mode_update(oi, facs, k, rank=r, samples=s, tau=tau, seed=7, it=3, distribution=dist)
+        assert got["sbar"] == ref["sbar"] and got["sdet"] == ref["sdet"]
+        np.testing.assert_array_equal(got["idx"].cpu().numpy().astype(np.uint64), ref["idx"])
+        np.testing.assert_array_equal(got["cnt"].cpu().numpy().astype(np.uint32), ref["cnt"])
+        assert relerr(got["wgt"].cpu().numpy(), ref["wgt"]) < 1e-13
+        assert relerr(fs[k].cpu().numpy(), ref["A"]) < 1e-10
+
+
 @pytest.mark.parametrize("case", range(len(CASES)))
 def test_mode_update_mixed_within_2e4(case):
     dims, nnz, r, s, tau = CASES[case]

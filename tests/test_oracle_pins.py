@@ -699,3 +699,30 @@ def test_app_b_all_rows_is_cp_als(orc):
     for o in outs:
         assert o["sdet"] == 24
         np.testing.assert_allclose(o["A"], An, rtol=1e-10, atol=1e-12)
+
+
+# --------------------------------------------------------------------------- RRF initialisation (App. F)
+def test_rrf_init_is_sampled_unfolding_times_omega(orc):
+    """A = X_(k)(:, S) Omega from the dense mode-k unfolding (columns ordered by the
+    linear key of Eq. 2.2 over the other modes, first fastest), S recomputed from
+    numpy's Philox over the nonzero columns; every mode of a 4-way tensor."""
+    coo = synth.random_sparse_tensor((5, 7, 3, 4), 90, seed=6)
+    X = orc.Index(coo)
+    Xd = coo.dense()
+    g = np.random.default_rng(2)
+    s_init, r, seed = 37, 3, 11
+    for k in range(4):
+        # columns of the unfolding: key = sum_t i_t prod_{u<t} n_u, first other mode fastest
+        Xk = np.moveaxis(Xd, k, 0).reshape(coo.dims[k], -1, order="F")
+        nzcols = np.nonzero(np.abs(Xk).sum(axis=0))[0]
+        assert nzcols.size == X.nfib(k)
+        omega = g.standard_normal((s_init, r))
+        cols = []
+        for j in range(s_init):
+            u = int(_ref.numpy_philox_block([j, 0, (3 << 32) | k, 0], [seed, 0])[0])
+            cols.append(nzcols[(u * nzcols.size) >> 64])
+        want = Xk[:, cols] @ omega
+        got = orc.rrf_init(X, k, omega, seed=seed)
+        np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-12)
+    with pytest.raises(orc.OracleError):
+        orc.rrf_init(X, 0, np.zeros((0, 2)))  # s_init = 0
