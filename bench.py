@@ -495,71 +495,107 @@ def equal_fit(cpa, coo, seed, stream, restarts, max_epochs, fixed_epochs):
         than tol = 1e-4 for pi = 3 epochs), in FP64, in FP64 once more (the spread that
         the order of floating-point atomics alone causes: the sampled rows of later
         iterations depend on every bit of the factors) and in mixed precision;
-      - fixed: `fixed_epochs` epochs in each precision.
-    Times are CUDA events around each whole call; each precision runs on its own
-    index (so each keeps its cached workspace and graphs), warmed up first.  A change
-    of precision moves a randomized trajectory as a change of seed does, so fits are
-    compared as paired differences (mean and standard error over restarts)."""
+      - traces: `fixed_epochs` epochs in each precision, one call (one graph launch)
+        per epoch with the exact fit after it; the restart's target is the lower of the
+        two best fits minus 1e-4, a fit both precisions reach, and the time each takes
+        to first reach it gives the speedup at equal fit.
+    Times are CUDA events; each precision runs on its own index (so each keeps its
+    cached workspace and graphs), warmed up first.  A change of precision moves a
+    randomized trajectory as a change of seed does, so fits are compared as paired
+    differences (mean and standard error over restarts)."""
     import torch
     import synth
     s, tau = SAMPLES, 2.0 ** -TAU_EXP
     dims = coo.dims
     indices = {cpa.binding.FP64: cpa.cpa_index_build(coo), cpa.binding.MIXED: cpa.cpa_index_build(coo)}
 
-    def run(init, precision, epochs, tol):
-        index = indices[precision]
-        fs = [torch.from_numpy(a).cuda() for a in init]
-        lam = torch.empty(RANK, dtype=torch.float64, device="cuda")
-        fitd = torch.empty(1, dtype=torch.float64, device="cuda")
-        torch.cuda.synchronize()
+    def call(fs, lam, fitd, precision, iters, tol, offset):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        res = cpa.cp_arls_lev(index, None, rank=RANK, samples=s, tau=tau, iters=ETA * epochs, seed=seed,
-                              tol=tol, patience=3, epoch_len=ETA, out=(fs, lam, fitd), precision=precision)
+        res = cpa.cp_arls_lev(indices[precision], None, rank=RANK, samples=s, tau=tau, iters=iters, seed=seed,
+                              tol=tol, patience=3, epoch_len=ETA, iter_offset=offset, out=(fs, lam, fitd),
+                              precision=precision)
         e1.record(stream)
         torch.cuda.synchronize()
-        ep = res.stats["epochs"] if tol > 0 else epochs
-        return {"fit": res.fit, "epochs": ep, "ms": e0.elapsed_time(e1)}
+        return res, e0.elapsed_time(e1)
 
-    keys = ("fp64", "fp64_rerun", "mixed", "fp64_fixed", "mixed_fixed")
-    runs = {k: [] for k in keys}
+    def buffers(init):
+        fs = [torch.from_numpy(a).cuda() for a in init]
+        return fs, torch.empty(RANK, dtype=torch.float64, device="cuda"), torch.empty(1, dtype=torch.float64,
+                                                                                      device="cuda")
+
+    def converged(init, precision):
+        fs, lam, fitd = buffers(init)
+        res, ms = call(fs, lam, fitd, precision, ETA * max_epochs, 1e-4, 0)
+        return {"fit": res.fit, "epochs": res.stats["epochs"], "ms": ms}
+
+    def trace(init, precision):
+        fs, lam, fitd = buffers(init)
+        fits, ms = [], []
+        for ep in range(fixed_epochs):
+            res, t = call(fs, lam, fitd, precision, ETA, 0.0, ETA * ep)
+            fits.append(res.fit)
+            ms.append(t)
+        return fits, ms
+
     warm = synth.gaussian_factors(dims, RANK, seed=999)
     for prec in indices:  # workspace and graphs of both call shapes
-        run(warm, prec, 2, 1e-4)
-        run(warm, prec, 2, 0.0)
+        converged(warm, prec)
+        trace(warm, prec)
+    runs = {"fp64": [], "fp64_rerun": [], "mixed": []}
+    tr = []
     for rs in range(restarts):
         init = synth.gaussian_factors(dims, RANK, seed=1000 + rs)
-        runs["fp64"].append(run(init, cpa.binding.FP64, max_epochs, 1e-4))
-        runs["fp64_rerun"].append(run(init, cpa.binding.FP64, max_epochs, 1e-4))
-        runs["mixed"].append(run(init, cpa.binding.MIXED, max_epochs, 1e-4))
-        runs["fp64_fixed"].append(run(init, cpa.binding.FP64, fixed_epochs, 0.0))
-        runs["mixed_fixed"].append(run(init, cpa.binding.MIXED, fixed_epochs, 0.0))
+        runs["fp64"].append(converged(init, cpa.binding.FP64))
+        runs["fp64_rerun"].append(converged(init, cpa.binding.FP64))
+        runs["mixed"].append(converged(init, cpa.binding.MIXED))
+        f64, m64 = trace(init, cpa.binding.FP64)
+        fmx, mmx = trace(init, cpa.binding.MIXED)
+        target = min(max(f64), max(fmx)) - 1e-4
+
+        def reach(fits, ms):
+            for i, f in enumerate(fits):
+                if f >= target:
+                    return i + 1, sum(ms[:i + 1])
+            return None, None
+
+        e64, t64 = reach(f64, m64)
+        emx, tmx = reach(fmx, mmx)
+        tr.append({"target": target, "best_fp64": max(f64), "best_mixed": max(fmx), "final_fp64": f64[-1],
+                   "final_mixed": fmx[-1], "epochs_fp64": e64, "epochs_mixed": emx, "ms_fp64": t64, "ms_mixed": tmx,
+                   "ms_per_epoch_fp64": sum(m64) / len(m64), "ms_per_epoch_mixed": sum(mmx) / len(mmx)})
 
     def summary(rs):
         f = np.array([r["fit"] for r in rs])
         return {"fit_mean": float(f.mean()), "fit_sd": float(f.std(ddof=1)) if f.size > 1 else 0.0,
-                "fit_median": float(np.median(f)), "epochs_mean": float(np.mean([r["epochs"] for r in rs])),
-                "ms_total": sum(r["ms"] for r in rs),
+                "epochs_mean": float(np.mean([r["epochs"] for r in rs])), "ms_total": sum(r["ms"] for r in rs),
                 "ms_per_epoch": sum(r["ms"] for r in rs) / sum(r["epochs"] for r in rs),
                 "fits": [round(r["fit"], 6) for r in rs], "epochs": [r["epochs"] for r in rs]}
 
-    def paired(a, b):
-        d = np.array([x["fit"] - y["fit"] for x, y in zip(runs[a], runs[b])])
+    def paired(xs, ys):
+        d = np.array([x - y for x, y in zip(xs, ys)])
         se = float(d.std(ddof=1) / math.sqrt(d.size)) if d.size > 1 else 0.0
         return {"mean": float(d.mean()), "se": se, "abs_median": float(np.median(np.abs(d))),
                 "identical": int(np.sum(np.abs(d) < 1e-12))}
 
     out = {k: summary(v) for k, v in runs.items()}
+    ratios = np.array([t["ms_fp64"] / t["ms_mixed"] for t in tr])
     out.update({
-        "restarts": restarts, "max_epochs": max_epochs, "fixed_epochs": fixed_epochs, "tol": 1e-4, "patience": 3,
-        "fit_diff_converged": paired("mixed", "fp64"),
-        "fit_diff_fp64_rerun": paired("fp64_rerun", "fp64"),
-        "fit_diff_fixed": paired("mixed_fixed", "fp64_fixed"),
-        "speedup_at_convergence": out["fp64"]["ms_total"] / out["mixed"]["ms_total"],
-        "per_epoch_speedup": out["fp64_fixed"]["ms_per_epoch"] / out["mixed_fixed"]["ms_per_epoch"],
-        "note": "fit_diff_* = mixed - FP64 per restart (mean, standard error, median |diff|, count of "
-                "identical fits); fit_diff_fp64_rerun compares two FP64 runs of the same restart"})
+        "restarts": restarts, "max_epochs": max_epochs, "trace_epochs": fixed_epochs, "tol": 1e-4, "patience": 3,
+        "fit_diff_converged": paired([r["fit"] for r in runs["mixed"]], [r["fit"] for r in runs["fp64"]]),
+        "fit_diff_fp64_rerun": paired([r["fit"] for r in runs["fp64_rerun"]], [r["fit"] for r in runs["fp64"]]),
+        "fit_diff_best_in_trace": paired([t["best_mixed"] for t in tr], [t["best_fp64"] for t in tr]),
+        "speedup_at_equal_fit": {"median": float(np.median(ratios)),
+                                 "geomean": float(np.exp(np.mean(np.log(ratios)))),
+                                 "per_restart": [round(float(x), 3) for x in ratios]},
+        "per_epoch_speedup": float(np.mean([t["ms_per_epoch_fp64"] for t in tr]) /
+                                   np.mean([t["ms_per_epoch_mixed"] for t in tr])),
+        "mixed_reaches_fp64_best": int(sum(t["best_mixed"] >= t["best_fp64"] - 1e-4 for t in tr)),
+        "traces": tr,
+        "note": "fit_diff_* = mixed - FP64 per restart (mean, standard error, median |diff|, count of identical "
+                "fits); speedup_at_equal_fit = FP64 time / mixed time to the restart's common target (the lower "
+                "best fit minus 1e-4), epoch-by-epoch calls with the exact fit"})
     return out
 
 

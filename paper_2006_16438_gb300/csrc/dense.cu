@@ -72,45 +72,111 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_rows(const FT* __restrict
 // ---- r x r factorisation in one block -------------------------------------
 constexpr int kFactorThreads = 256;
 
-// Cyclic Jacobi eigendecomposition of the symmetric matrix in `a` (r x r,
-// overwritten by its eigenvalues on the diagonal), eigenvectors in the columns of
-// `v`.  Serial: run by one thread (it is the rare fallback path).
-__device__ __noinline__ void jacobi_eigen_serial(double* a, double* v, int r) {
-  for (int i = 0; i < r; ++i)
-    for (int j = 0; j < r; ++j) v[i * r + j] = (i == j) ? 1.0 : 0.0;
+// Cyclic Jacobi eigendecomposition of the symmetric matrix in `a` (r x r in shared
+// memory, overwritten by its eigenvalues on the diagonal), eigenvectors in the
+// columns of `v`, by all threads of the block (every thread must call it).  Each
+// round applies r/2 disjoint rotations (round-robin pairing: index m - 1 fixed, the
+// others rotating; m = r rounded up to even, pairs with the padding index skipped):
+// the angles from the round's a_pp, a_qq, a_pq (Rutishauser's formulas), then the
+// column phase a <- a J, v <- v J and the row phase a <- J^T a, exact because the
+// rotations of a round touch disjoint index pairs.  A sweep is m - 1 rounds; sweeps
+// stop when the off-diagonal mass falls below 1e-30 of the total (at most 60).
+__device__ __noinline__ void jacobi_eigen_block(double* a, double* v, int r, int tid, int nt) {
+  __shared__ double rc[kMaxRank / 2], rs[kMaxRank / 2];
+  __shared__ int rp[kMaxRank / 2], rq[kMaxRank / 2];
+  __shared__ double red[kFactorThreads / 32];
+  __shared__ int done;
+  const int m = (r + 1) & ~1;
+  const int half = m / 2;
+  for (int i = tid; i < r * r; i += nt) v[i] = (i / r == i % r) ? 1.0 : 0.0;
+  __syncthreads();
   for (int sweep = 0; sweep < 60; ++sweep) {
+    // convergence: off = 2 sum_{i<j} a_ij^2 against diag = sum a_ii^2
     double off = 0.0, diag = 0.0;
-    for (int i = 0; i < r; ++i) {
-      diag += a[i * r + i] * a[i * r + i];
-      for (int j = i + 1; j < r; ++j) off += 2.0 * a[i * r + j] * a[i * r + j];
+    for (int i = tid; i < r * r; i += nt) {
+      const int row = i / r, col = i - row * r;
+      const double x = a[i];
+      if (row == col) diag += x * x; else off += x * x;
     }
-    if (off == 0.0 || off <= 1e-30 * (off + diag)) break;
-    for (int p = 0; p < r - 1; ++p) {
-      for (int q = p + 1; q < r; ++q) {
-        const double apq = a[p * r + q];
-        if (apq == 0.0) continue;
-        const double app = a[p * r + p], aqq = a[q * r + q];
-        // rotation angle that zeroes a_pq (Rutishauser's formulas)
-        const double zeta = (aqq - app) / (2.0 * apq);
-        const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        const double c = rsqrt(1.0 + t * t);
-        const double s = t * c;
-        for (int k = 0; k < r; ++k) {
-          const double akp = a[k * r + p], akq = a[k * r + q];
-          a[k * r + p] = c * akp - s * akq;
-          a[k * r + q] = s * akp + c * akq;
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      diag += __shfl_xor_sync(0xffffffffu, diag, o);
+    }
+    if ((tid & 31) == 0) red[tid >> 5] = off;
+    __syncthreads();
+    if (tid == 0) {
+      double o_sum = 0.0;
+      for (int w = 0; w < (nt >> 5); ++w) o_sum += red[w];
+      red[0] = o_sum;
+    }
+    __syncthreads();
+    const double off_all = red[0];
+    __syncthreads();
+    if ((tid & 31) == 0) red[tid >> 5] = diag;
+    __syncthreads();
+    if (tid == 0) {
+      double d_sum = 0.0;
+      for (int w = 0; w < (nt >> 5); ++w) d_sum += red[w];
+      done = (off_all == 0.0 || off_all <= 1e-30 * (off_all + d_sum)) ? 1 : 0;
+    }
+    __syncthreads();
+    if (done) break;
+    for (int round = 0; round < m - 1; ++round) {
+      if (tid < half) {
+        int p, q;
+        if (tid == 0) {
+          p = m - 1;
+          q = round;
+        } else {
+          p = (round + tid) % (m - 1);
+          q = (round - tid + (m - 1)) % (m - 1);
         }
-        for (int k = 0; k < r; ++k) {
-          const double apk = a[p * r + k], aqk = a[q * r + k];
-          a[p * r + k] = c * apk - s * aqk;
-          a[q * r + k] = s * apk + c * aqk;
+        if (p > q) {
+          const int t2 = p;
+          p = q;
+          q = t2;
         }
-        for (int k = 0; k < r; ++k) {
-          const double vkp = v[k * r + p], vkq = v[k * r + q];
-          v[k * r + p] = c * vkp - s * vkq;
-          v[k * r + q] = s * vkp + c * vkq;
+        double c = 1.0, sn = 0.0;
+        if (q < r) {
+          const double apq = a[p * r + q];
+          if (apq != 0.0) {
+            const double zeta = (a[q * r + q] - a[p * r + p]) / (2.0 * apq);
+            const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            c = rsqrt(1.0 + t * t);
+            sn = t * c;
+          }
+        } else {
+          p = q = -1;  // pairs with the padding index do nothing
         }
+        rc[tid] = c;
+        rs[tid] = sn;
+        rp[tid] = p;
+        rq[tid] = q;
       }
+      __syncthreads();
+      for (int w = tid; w < half * r; w += nt) {  // a <- a J, v <- v J (columns p, q)
+        const int k = w / r, i = w - k * r;
+        const int p = rp[k], q = rq[k];
+        if (p < 0) continue;
+        const double c = rc[k], sn = rs[k];
+        const double aip = a[i * r + p], aiq = a[i * r + q];
+        a[i * r + p] = c * aip - sn * aiq;
+        a[i * r + q] = sn * aip + c * aiq;
+        const double vip = v[i * r + p], viq = v[i * r + q];
+        v[i * r + p] = c * vip - sn * viq;
+        v[i * r + q] = sn * vip + c * viq;
+      }
+      __syncthreads();
+      for (int w = tid; w < half * r; w += nt) {  // a <- J^T a (rows p, q)
+        const int k = w / r, j = w - k * r;
+        const int p = rp[k], q = rq[k];
+        if (p < 0) continue;
+        const double c = rc[k], sn = rs[k];
+        const double apj = a[p * r + j], aqj = a[q * r + j];
+        a[p * r + j] = c * apj - sn * aqj;
+        a[q * r + j] = sn * apj + c * aqj;
+      }
+      __syncthreads();
     }
   }
 }
@@ -320,8 +386,8 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor_spd(const double* __r
       S[i] = G[i] * scale[a] * scale[b];
     }
     __syncthreads();
+    jacobi_eigen_block(S, X, r, tid, nt);
     if (tid == 0) {
-      jacobi_eigen_serial(S, X, r);
       double emax = 0.0;
       for (int c = 0; c < r; ++c) emax = fmax(emax, fabs(S[c * r + c]));
       for (int c = 0; c < r; ++c) {

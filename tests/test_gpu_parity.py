@@ -294,6 +294,23 @@ def test_solve_vs_oracle():
     assert relerr(A.cpu().numpy(), An) < 1e-9
 
 
+@pytest.mark.parametrize("r,deficit", [(2, 1), (7, 3), (25, 5), (50, 2), (64, 9)])
+def test_singular_solve_pinv_vs_oracle(r, deficit):
+    """A rank-deficient sampled Gram takes the pseudo-inverse path (block-parallel
+    Jacobi on the GPU, serial Jacobi in the oracle): the same pinv solution and the
+    singular-Gram warning on both sides."""
+    g = np.random.default_rng(100 + r)
+    B = g.standard_normal((r, r - deficit)) * np.exp(g.standard_normal(r - deficit))
+    G = B @ B.T
+    M = g.standard_normal((40, r)) @ (G + np.eye(r) * 0.0)  # right-hand sides in range(G)
+    A, lam, warn = cpa.cpa_solve(cu(G), cu(M))
+    Ar, rc = oracle.solve(G, M)
+    An, lamr = oracle.normalize(Ar)
+    assert warn & 1 and rc & 1
+    assert relerr(A.cpu().numpy(), An) < 1e-9
+    assert relerr(lam.cpu().numpy(), lamr) < 1e-9
+
+
 def test_fit_vs_oracle():
     for dims, nnz in [((30, 20, 25), 3000), ((183, 24, 114, 171), 50000)]:
         coo = synth.random_sparse_tensor(dims, nnz, seed=11)
