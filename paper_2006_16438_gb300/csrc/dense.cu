@@ -69,6 +69,62 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_rows(const FT* __restrict
   }
 }
 
+// FP32 factors: the same Gram on the FP32 pipe.  Each float product is split
+// exactly into its rounded value p and error e = fma(a, b, -p); p is added to a
+// float pair (hi, lo) by TwoSum (Knuth) and e into lo, so a 64-row tile is summed to
+// about 2^-44 relative before the tile is added in FP64.  The _rn intrinsics keep the
+// compiler from fusing the error-free steps.
+constexpr int kGramRowsFF = 64;
+
+template <int PMAX>
+__global__ void __launch_bounds__(kGramThreads) k_gram_rows_ff(const float* __restrict__ A, int64_t n, int r,
+                                                               double* __restrict__ G) {
+  extern __shared__ __align__(16) unsigned char gram_smem[];
+  float* tile = reinterpret_cast<float*>(gram_smem);  // kGramRowsFF * r
+  const int np = r * (r + 1) / 2;
+  int pa[PMAX], pb[PMAX];
+  double acc[PMAX];
+#pragma unroll
+  for (int q = 0; q < PMAX; ++q) {
+    const int p = threadIdx.x + q * kGramThreads;
+    if (p < np) pair_of(p, r, &pa[q], &pb[q]); else pa[q] = pb[q] = 0;
+    acc[q] = 0.0;
+  }
+  for (int64_t row0 = (int64_t)blockIdx.x * kGramRowsFF; row0 < n; row0 += (int64_t)gridDim.x * kGramRowsFF) {
+    const int rows = (int)((n - row0) < kGramRowsFF ? (n - row0) : kGramRowsFF);
+    __syncthreads();
+    const float* src = A + row0 * r;
+    for (int i = threadIdx.x; i < kGramRowsFF * r; i += kGramThreads) tile[i] = i < rows * r ? src[i] : 0.f;
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < PMAX; ++q) {
+      const int p = threadIdx.x + q * kGramThreads;
+      if (p < np) {
+        float hi = 0.f, lo = 0.f;
+        for (int i = 0; i < rows; ++i) {
+          const float a = tile[i * r + pa[q]], b = tile[i * r + pb[q]];
+          const float pr = __fmul_rn(a, b);
+          const float e = __fmaf_rn(a, b, -pr);
+          const float t = __fadd_rn(hi, pr);
+          const float z = __fsub_rn(t, hi);
+          const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, z)), __fsub_rn(pr, z));
+          hi = t;
+          lo = __fadd_rn(lo, __fadd_rn(err, e));
+        }
+        acc[q] += (double)hi + (double)lo;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < PMAX; ++q) {
+    const int p = threadIdx.x + q * kGramThreads;
+    if (p < np) {
+      atomicAdd(&G[pa[q] * r + pb[q]], acc[q]);
+      if (pa[q] != pb[q]) atomicAdd(&G[pb[q] * r + pa[q]], acc[q]);
+    }
+  }
+}
+
 // ---- r x r factorisation in one block -------------------------------------
 constexpr int kFactorThreads = 256;
 
@@ -694,6 +750,126 @@ __global__ void __launch_bounds__(kRowThreads) k_lev_rows_tpr(const FT* A, int64
   }
 }
 
+// ---- leverage of many FP32 rows on the FP32 pipe ---------------------------
+// Float-pair ("double-float") arithmetic: a value is hi + lo with |lo| <= ulp(hi)/2.
+// TwoSum gives the exact error of a float addition; fma(a, b, -ab) that of a product.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float z = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+// (hi, lo) += (ah + al) (bh + bl), the product's al*bl term dropped (below 2^-46).
+__device__ __forceinline__ void ff_fma(float ah, float al, float bh, float bl, float& hi, float& lo) {
+  const float p = __fmul_rn(ah, bh);
+  const float e = __fmaf_rn(ah, bh, -p);
+  const float cross = __fmaf_rn(ah, bl, __fmul_rn(al, bh));
+  float s, t;
+  two_sum(hi, p, s, t);
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(t, __fadd_rn(e, cross)));
+}
+
+// Leverage scores (kind 0 factors: l = ||L^{-1} P^T (S a)||^2) of FP32 rows, one
+// thread per row, in float-pair arithmetic (about 2^-44 relative): F and the column
+// scales are split into float pairs once per block, S a is formed as a float pair
+// when the row is staged.  A kind 1 (pseudo-inverse) factor takes the FP64 loop.
+// Outputs as k_lev_rows_tpr.
+__global__ void __launch_bounds__(kRowThreads) k_lev_rows_ff(const float* A, int64_t n, int r,
+                                                             const SmallFactor* __restrict__ f,
+                                                             double* __restrict__ lev, uint64_t* __restrict__ q,
+                                                             DistInfo* info, float* A_out) {
+  extern __shared__ __align__(16) unsigned char ff_smem[];
+  float* Fh = reinterpret_cast<float*>(ff_smem);  // r * r
+  float* Fl = Fh + r * r;                         // r * r
+  float* sch = Fl + r * r;                        // r
+  float* scl = sch + r;                           // r
+  float* lam = scl + r;                           // r
+  float2* xs = reinterpret_cast<float2*>(lam + ((r + 1) & ~1));  // kRowThreads * ld (S a as float pairs)
+  __shared__ int perm[kMaxRank];
+  const int ld = r | 1;
+  const int kind = f->kind;
+  const int k = kind == 0 ? f->rank : r;
+  for (int i = threadIdx.x; i < r * r; i += blockDim.x) {
+    const double v = f->F[i];
+    const float h = (float)v;
+    Fh[i] = h;
+    Fl[i] = (float)(v - (double)h);
+  }
+  for (int i = threadIdx.x; i < r; i += blockDim.x) {
+    const double sc = f->scale[i];
+    const float h = (float)sc;
+    sch[i] = h;
+    scl[i] = (float)(sc - (double)h);
+    const double l = f->lambda[i];
+    lam[i] = pos_finite(l) ? (float)(1.0 / l) : 1.f;
+    perm[i] = f->perm[i];
+  }
+  uint64_t my_max = 0;
+  uint32_t my_nz = 0;
+  for (int64_t row0 = (int64_t)blockIdx.x * kRowThreads; row0 < n; row0 += (int64_t)gridDim.x * kRowThreads) {
+    const int rows = (int)(n - row0 < kRowThreads ? n - row0 : kRowThreads);
+    __syncthreads();
+    for (int i = threadIdx.x; i < rows * r; i += kRowThreads) {
+      const int rr = i / r, c = i - rr * r;
+      const float x = A[row0 * r + i];
+      const float p = __fmul_rn(x, sch[c]);
+      const float rest = __fmaf_rn(x, scl[c], __fmaf_rn(x, sch[c], -p));
+      const float h = __fadd_rn(p, rest);
+      xs[rr * ld + c] = make_float2(h, __fsub_rn(rest, __fsub_rn(h, p)));
+    }
+    __syncthreads();
+    if (threadIdx.x < rows) {
+      const float2* b = xs + threadIdx.x * ld;
+      const int64_t row = row0 + threadIdx.x;
+      double l = 0.0;
+      if (kind == 0) {
+        float lh = 0.f, ll = 0.f;
+        for (int c = 0; c < k; ++c) {
+          float th = 0.f, tl = 0.f;
+          for (int u = 0; u <= c; ++u) {
+            const float2 bu = b[perm[u]];
+            ff_fma(Fh[c * r + u], Fl[c * r + u], bu.x, bu.y, th, tl);
+          }
+          float s, e;
+          two_sum(th, tl, s, e);
+          ff_fma(s, e, s, e, lh, ll);
+        }
+        l = (double)lh + (double)ll;
+      } else {
+        for (int c = 0; c < r; ++c) {
+          double t = 0.0;
+          for (int u = 0; u < r; ++u)
+            t = fma((double)Fh[c * r + u] + (double)Fl[c * r + u], (double)b[u].x + (double)b[u].y, t);
+          l = fma((double)b[c].x + (double)b[c].y, t, l);
+        }
+      }
+      if (lev) lev[row] = l;
+      if (q) {
+        double pr = l / (double)r;
+        pr = clamp01(pr);
+        const uint64_t qi = __double2ull_rn(pr * 4611686018427387904.0);  // 2^62
+        q[row] = qi;
+        my_max = qi > my_max ? qi : my_max;
+        my_nz += qi > 0;
+      }
+    }
+    if (A_out) {
+      for (int i = threadIdx.x; i < rows * r; i += kRowThreads) A_out[row0 * r + i] = A[row0 * r + i] * lam[i % r];
+    }
+  }
+  if (q && info) {
+    for (int o = 16; o > 0; o >>= 1) {
+      const uint64_t om = __shfl_xor_sync(0xffffffffu, my_max, o);
+      my_max = om > my_max ? om : my_max;
+      my_nz += __shfl_xor_sync(0xffffffffu, my_nz, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicMax((unsigned long long*)&info->maxq, (unsigned long long)my_max);
+      atomicAdd((unsigned long long*)&info->nnzq, (unsigned long long)my_nz);
+    }
+  }
+}
+
 }  // namespace
 
 template <class FT>
@@ -701,6 +877,18 @@ int gram_rows(const FT* A, int64_t n, int r, double* G, cudaStream_t st) {
   if (r < 1 || r > kMaxRank) return CPA_ERR_ARG;
   if (n <= 0) return CPA_OK;
   const int np = r * (r + 1) / 2;
+  if constexpr (sizeof(FT) == 4) {
+    const unsigned grid = grid_cap(ceil_div(n, kGramRowsFF), 4);
+    const size_t smem = sizeof(float) * kGramRowsFF * r;
+    if (np <= kGramThreads)
+      k_gram_rows_ff<1><<<grid, kGramThreads, smem, st>>>(A, n, r, G);
+    else if (np <= 4 * kGramThreads)
+      k_gram_rows_ff<4><<<grid, kGramThreads, smem, st>>>(A, n, r, G);
+    else
+      k_gram_rows_ff<9><<<grid, kGramThreads, smem, st>>>(A, n, r, G);
+    CPA_LAUNCH_CHECK();
+    return CPA_OK;
+  }
   const unsigned grid = grid_cap(ceil_div(n, kGramRows), 4);
   const size_t smem = sizeof(double) * kGramRows * r;
   if (np <= kGramThreads)
@@ -738,6 +926,24 @@ int lev_rows(const FT* A, int64_t n, int r, const SmallFactor* f, double* lev, u
     return CPA_ERR_ARG;
   if (r < 1 || r > kMaxRank) return CPA_ERR_ARG;
   if (n <= 0) return CPA_OK;
+  if constexpr (sizeof(FT) == 4) {
+    if (n >= kManyRows && dist == CPA_DIST_LEVERAGE) {
+      auto bytes = [](int rr) {
+        return sizeof(float) * ((size_t)2 * rr * rr + 3 * rr + 1) + sizeof(float2) * (size_t)kRowThreads * (rr | 1) +
+               16;
+      };
+      static bool attr = false;
+      if (!attr) {
+        CPA_CUDA_TRY(cudaFuncSetAttribute(k_lev_rows_ff, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)bytes(kMaxRank)));
+        attr = true;
+      }
+      const unsigned grid = grid_cap(ceil_div(n, kRowThreads), 8);
+      k_lev_rows_ff<<<grid, kRowThreads, bytes(r), st>>>(A, n, r, f, lev, q, info, A_out);
+      CPA_LAUNCH_CHECK();
+      return CPA_OK;
+    }
+  }
   if (n >= kManyRows) {
     auto bytes = [](int rr) {
       return sizeof(double) * ((size_t)rr * rr + rr) + sizeof(FT) * (size_t)((rr + 1) & ~1) +

@@ -270,7 +270,9 @@ __global__ void __launch_bounds__(kThreads) k_tnsr_heavy(FibreIndex<VT> X, Facto
 }
 
 // ---- row-slab path ----------------------------------------------------------
-constexpr int kSlabHeavy = 256;  // slab ranges longer than this go to the pass's heavy list
+constexpr int kSlabHeavy = 256;    // slab ranges longer than this go to the pass's heavy list
+constexpr int kSlabPiece = 4096;   // heavy ranges are listed in pieces of at most this length
+constexpr int kHeavyPerSample = 4; // heavy-list entries per sample of the buffer
 
 // Per sample (a warp takes 32 consecutive samples): probe the fibre, store u_j and the
 // start of each slab's rows in the fibre (ballots over the loaded i_k for fibres of at
@@ -349,7 +351,7 @@ __global__ void __launch_bounds__(kThreads) k_slab_light(FibreIndex<VT> X, int r
                                                          const uint64_t* __restrict__ los,
                                                          const uint32_t* __restrict__ bnd, FT* __restrict__ M,
                                                          unsigned long long* __restrict__ pctr,
-                                                         uint4* __restrict__ heavy) {
+                                                         uint4* __restrict__ heavy, int64_t heavy_cap) {
   const int lane = threadIdx.x & 31;
   const int64_t n = sbar.get();
   const int64_t nchunks = (n + 31) >> 5;
@@ -366,10 +368,20 @@ __global__ void __launch_bounds__(kThreads) k_slab_light(FibreIndex<VT> X, int r
       len = b - a;
       start = los[j] + a;
     }
-    if (len > kSlabHeavy) {
-      const unsigned long long h = atomicAdd(&pctr[1], 1ull);
-      heavy[h] = make_uint4((unsigned)j, (unsigned)(start & 0xffffffffu), (unsigned)(start >> 32), len);
-      len = 0;
+    if (len > kSlabHeavy) {  // listed in pieces, each taken whole by one block
+      const uint32_t np = (len + kSlabPiece - 1) / kSlabPiece;
+      const unsigned long long h = atomicAdd(&pctr[1], (unsigned long long)np);
+      if (h + np <= (unsigned long long)heavy_cap) {
+        for (uint32_t q = 0; q < np; ++q) {
+          const uint64_t ps = start + (uint64_t)q * kSlabPiece;
+          const uint32_t pl = len - q * kSlabPiece < (uint32_t)kSlabPiece ? len - q * kSlabPiece : kSlabPiece;
+          heavy[h + q] = make_uint4((unsigned)j, (unsigned)(ps & 0xffffffffu), (unsigned)(ps >> 32), pl);
+        }
+        len = 0;
+      } else {  // list full: empty the slots reserved below the capacity, walk the range here
+        for (unsigned long long q = h; q < h + np && q < (unsigned long long)heavy_cap; ++q)
+          heavy[q] = make_uint4((unsigned)j, 0u, 0u, 0u);
+      }
     }
     unsigned todo = __ballot_sync(0xffffffffu, len > 0);
     while (todo) {
@@ -406,15 +418,22 @@ __global__ void __launch_bounds__(kThreads) k_slab_light(FibreIndex<VT> X, int r
   }
 }
 
-// Pass p, heavy part: one block per listed range, its warps taking groups of 32.
+// Pass p, heavy part: blocks take listed pieces from a counter (pctr[2]); the warps of
+// a block take the piece's nonzeros in groups of 32 (w, w + 8, ...), the next group's
+// loads issued before the current group is added.
 template <class FT, class VT, int CPL>
 __global__ void __launch_bounds__(kThreads) k_slab_heavy(FibreIndex<VT> X, int r, const FT* __restrict__ U,
-                                                         FT* __restrict__ M,
-                                                         const unsigned long long* __restrict__ pctr,
-                                                         const uint4* __restrict__ heavy) {
+                                                         FT* __restrict__ M, unsigned long long* __restrict__ pctr,
+                                                         const uint4* __restrict__ heavy, int64_t heavy_cap) {
+  __shared__ long long item;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t nh = (int64_t)pctr[1];
-  for (int64_t h = blockIdx.x; h < nh; h += gridDim.x) {
+  const long long nh = (long long)(pctr[1] < (unsigned long long)heavy_cap ? pctr[1] : heavy_cap);
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) item = (long long)atomicAdd(&pctr[2], 1ull);
+    __syncthreads();
+    const long long h = item;
+    if (h >= nh) break;
     const uint4 e = heavy[h];
     const int64_t j = e.x;
     const uint64_t start = (uint64_t)e.y | ((uint64_t)e.z << 32);
@@ -425,13 +444,21 @@ __global__ void __launch_bounds__(kThreads) k_slab_heavy(FibreIndex<VT> X, int r
       const int c = lane + 32 * v;
       u[v] = c < r ? U[j * r + c] : FT(0);
     }
-    for (uint64_t g = (uint64_t)warp * 32; g < len; g += kThreads) {
+    uint64_t g = (uint64_t)warp * 32;
+    int32_t ikl = 0;
+    FT xl = FT(0);
+    if (g + lane < len) {
+      ikl = __ldcs(X.ik + start + g + lane);
+      xl = (FT)__ldcs(X.val + start + g + lane);
+    }
+    for (; g < len; g += kThreads) {
       const int nb = len - g < 32 ? (int)(len - g) : 32;
-      int32_t ikl = 0;
-      FT xl = FT(0);
-      if (lane < nb) {
-        ikl = __ldcs(X.ik + start + g + lane);
-        xl = (FT)__ldcs(X.val + start + g + lane);
+      const uint64_t gn = g + kThreads;  // prefetch of this warp's next group
+      int32_t ikn = 0;
+      FT xn = FT(0);
+      if (gn + lane < len) {
+        ikn = __ldcs(X.ik + start + gn + lane);
+        xn = (FT)__ldcs(X.val + start + gn + lane);
       }
       for (int q2 = 0; q2 < nb; ++q2) {
         const int32_t ik = __shfl_sync(0xffffffffu, ikl, q2);
@@ -442,6 +469,8 @@ __global__ void __launch_bounds__(kThreads) k_slab_heavy(FibreIndex<VT> X, int r
           if (c < r) atomicAdd(&M[(int64_t)ik * r + c], x * u[v]);
         }
       }
+      ikl = ikn;
+      xl = xn;
     }
   }
 }
@@ -464,14 +493,15 @@ int launch_mttkrp_slabs(const cpa_index* X, int k, const FactorPtrs& F, int r, c
   else
     k_slab_prep<FT, VT, 2><<<grid, kThreads, 0, st>>>(fx, F, L, r, idx, wgt, sbar, slab_rows, P, U, B.los, B.bnd, ctr);
   CPA_LAUNCH_CHECK();
+  const int64_t cap = (int64_t)kHeavyPerSample * (sbar.max > 0 ? sbar.max : 1);
   for (int p = 0; p < P; ++p) {
-    unsigned long long* pctr = ctr + 4 + 2 * p;
+    unsigned long long* pctr = ctr + 4 + 3 * p;
     if (r <= 32) {
-      k_slab_light<FT, VT, 1><<<grid, kThreads, 0, st>>>(fx, r, sbar, p, U, B.los, B.bnd, M, pctr, heavy);
-      k_slab_heavy<FT, VT, 1><<<(unsigned)sms * 2, kThreads, 0, st>>>(fx, r, U, M, pctr, heavy);
+      k_slab_light<FT, VT, 1><<<grid, kThreads, 0, st>>>(fx, r, sbar, p, U, B.los, B.bnd, M, pctr, heavy, cap);
+      k_slab_heavy<FT, VT, 1><<<(unsigned)sms * 2, kThreads, 0, st>>>(fx, r, U, M, pctr, heavy, cap);
     } else {
-      k_slab_light<FT, VT, 2><<<grid, kThreads, 0, st>>>(fx, r, sbar, p, U, B.los, B.bnd, M, pctr, heavy);
-      k_slab_heavy<FT, VT, 2><<<(unsigned)sms * 2, kThreads, 0, st>>>(fx, r, U, M, pctr, heavy);
+      k_slab_light<FT, VT, 2><<<grid, kThreads, 0, st>>>(fx, r, sbar, p, U, B.los, B.bnd, M, pctr, heavy, cap);
+      k_slab_heavy<FT, VT, 2><<<(unsigned)sms * 2, kThreads, 0, st>>>(fx, r, U, M, pctr, heavy, cap);
     }
     CPA_LAUNCH_CHECK();
   }
@@ -566,7 +596,7 @@ void mttkrp_buffers_carve(Arena& a, int64_t s, int r, int ftb, bool slabs, Mttkr
   const size_t ss = (size_t)(s > 0 ? s : 1);
   B->ctr = a.take<uint64_t>(kMttkrpCounters);
   B->total = B->ctr;
-  B->heavy = a.take<uint32_t>(4 * ss);
+  B->heavy = a.take<uint32_t>(4 * ss * (slabs ? kHeavyPerSample : 1));
   if (slabs) {
     B->U = a.take<char>(ss * r * ftb);
     B->los = a.take<uint64_t>(ss);

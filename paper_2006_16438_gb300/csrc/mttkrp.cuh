@@ -13,9 +13,11 @@ struct FactorPtrs {
 // Device buffers of one sampled MTTKRP for up to s samples.
 struct MttkrpBuffers {
   uint64_t* ctr;     // kMttkrpCounters: sampled nonzeros, chunk counter, heavy-list
-                     // length, spare, then per row slab its chunk counter and heavy length
+                     // length, spare, then per row slab its chunk counter, heavy-list
+                     // length and heavy-piece counter
   uint64_t* total;   // = ctr: nnz of the sampled right-hand side
-  uint32_t* heavy;   // 4 s: (sample, fibre start lo/hi words, length) of long fibres
+  uint32_t* heavy;   // 4 s (16 s with row slabs): (sample, start lo/hi words, length) of
+                     // long fibres (row slabs: pieces of long slab ranges)
   // row-slab path (null when no mode's M exceeds one slab): per sample u_j
   // (s x r, run element type), fibre start, and the start of each slab's rows
   // within the fibre (s x 32 u32, slab p at column p, the fibre length at column P)
@@ -23,7 +25,7 @@ struct MttkrpBuffers {
   uint64_t* los = nullptr;
   uint32_t* bnd = nullptr;
 };
-constexpr int kMttkrpCounters = 4 + 2 * 32;
+constexpr int kMttkrpCounters = 4 + 3 * 32;
 constexpr int kSlabMax = 31;  // most row slabs of one M
 
 // Bytes of M per row slab: M larger than this is accumulated slab by slab so that

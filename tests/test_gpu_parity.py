@@ -241,6 +241,7 @@ def test_sampled_mttkrp_empty_fibres_and_heavy_fibre():
     ((3000, 4, 5), 20000, 25, 500, 1.0),      # fibres of about 1000 nonzeros: heavy slab ranges
     ((183, 24, 1140, 1717), 200000, 25, 2 ** 14, 2.0 ** -14),
     ((500, 40, 30), 20000, 40, 5000, 1.0),    # r > 32: two columns per lane
+    ((20000, 30, 40), 200000, 25, 4000, 1.0),
 ])
 def test_sampled_mttkrp_row_slabs_vs_oracle(monkeypatch, slab_bytes, dims, nnz, r, s, tau):
     """The row-slab path (M accumulated one slab of rows at a time, every fibre cut at
@@ -257,6 +258,25 @@ def test_sampled_mttkrp_row_slabs_vs_oracle(monkeypatch, slab_bytes, dims, nnz, 
         assert nz == nzr
         assert relerr(M.cpu().numpy(), Mr) < 1e-12
         assert relerr(G.cpu().numpy(), Gr) < 1e-12
+
+
+def test_row_slabs_skewed(monkeypatch):
+    """A Zipf-skewed planted tensor whose first mode has 30,000 rows, its M in row
+    slabs: long fibres are cut into pieces shared by the blocks; FP64 products equal
+    the oracle's, and a mixed-precision run works."""
+    monkeypatch.setenv("CPA_MTTKRP_SLAB_BYTES", "100000")
+    coo = synth.planted_cp_tensor((30000, 60, 50), 5, events=300000, seed=3, zipf_alpha=1.1)
+    facs = synth.gaussian_factors(coo.dims, 5, seed=4)
+    gi = cpa.cpa_index_build(coo)
+    oi = oracle.Index(coo)
+    smp = _sample_for(coo, facs, 0, 5, 2000, 1.0 / 2000)
+    M, G, nz = cpa.cpa_sampled_mttkrp(gi, 0, [cu(f) for f in facs], cu(smp["idx"]), cu(smp["wgt"]))
+    Mr, Gr, nzr = oracle.sampled_mttkrp(oi, 0, facs, smp["idx"], smp["wgt"])
+    assert nz == nzr and nz > 0
+    assert relerr(M.cpu().numpy(), Mr) < 1e-12
+    res = cpa.cp_arls_lev(gi, [cu(a) for a in facs], rank=5, samples=2000, tau=1.0 / 2000, iters=3,
+                          precision=binding.MIXED)
+    assert np.isfinite(res.fit)
 
 
 def test_whole_run_row_slabs(monkeypatch):

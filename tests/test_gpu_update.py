@@ -142,3 +142,26 @@ def test_epoch_graph_keyed_by_fit_mode():
     c = cpa.cp_arls_lev(cpa.cpa_index_build(coo), [torch.from_numpy(x).cuda() for x in init], rank=4,
                         samples=1024, tau=1.0, iters=2, seed=0)
     assert np.isfinite(b.fit) and abs(b.fit - c.fit) < 1e-12
+
+
+@pytest.mark.parametrize("r", [8, 25])
+def test_mixed_float_pair_leverage_matches_fp64_rows(r):
+    """Mixed precision with factors that are exact in FP32 and a first mode of 70,000
+    rows: the factor Gram (k_gram_rows_ff) and the leverage rows (k_lev_rows_ff) of
+    the FP32 factors run in float-pair arithmetic (about 2^-44), so the leverage
+    distributions, and with them the sampled rows and counts, equal the FP64
+    oracle's; weights to 1e-12."""
+    dims = (70000, 40, 30)
+    coo = synth.random_sparse_tensor(dims, 300000, seed=11)
+    facs = [a.astype(np.float32).astype(np.float64) for a in synth.gaussian_factors(dims, r, seed=12)]
+    gi = cpa.cpa_index_build(coo)
+    oi = oracle.Index(coo)
+    for k in (1, 2):
+        fs = [torch.from_numpy(a).cuda() for a in facs]
+        got = cpa.cpa_mode_update(gi, fs, k, rank=r, samples=4000, tau=1.0 / 4000, seed=5, it=1,
+                                  precision=binding.MIXED)
+        ref = oracle.mode_update(oi, facs, k, rank=r, samples=4000, tau=1.0 / 4000, seed=5, it=1)
+        assert got["sbar"] == ref["sbar"] and got["sdet"] == ref["sdet"]
+        np.testing.assert_array_equal(got["idx"].cpu().numpy().astype(np.uint64), ref["idx"])
+        np.testing.assert_array_equal(got["cnt"].cpu().numpy().astype(np.uint32), ref["cnt"])
+        assert relerr(got["wgt"].cpu().numpy(), ref["wgt"]) < 1e-12
