@@ -370,12 +370,12 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor_spd(const double* __r
     }
     int* ordn = ordb[(j + 1) & 1];
     // phase C: stage the pivot row and the ordering after the swap of j and ppos
-    if (tid < r) {
+    for (int c = tid; c < r; c += nt) {
       const int* ord = ordb[j & 1];
-      const double v = S[p * r + tid];
-      sp[tid] = v;
-      sh[tid] = v * di;
-      ordn[tid] = tid == j ? p : (tid == ppos ? ord[j] : ord[tid]);
+      const double v = S[p * r + c];
+      sp[c] = v;
+      sh[c] = v * di;
+      ordn[c] = c == j ? p : (c == ppos ? ord[j] : ord[c]);
     }
     if (tid == 0) {
       perm[j] = p;
@@ -903,6 +903,20 @@ int gram_rows(const FT* A, int64_t n, int r, double* G, cudaStream_t st) {
 template int gram_rows<double>(const double*, int64_t, int, double*, cudaStream_t);
 template int gram_rows<float>(const float*, int64_t, int, double*, cudaStream_t);
 
+// Threads of the r x r factorisation block: a multiple of 32 in [32, 256]
+// (CPA_FACTOR_THREADS overrides the default, for tuning).
+static int factor_threads() {
+  static int nt = 0;
+  if (!nt) {
+    nt = kFactorThreads;
+    if (const char* e = getenv("CPA_FACTOR_THREADS")) {
+      const int v = atoi(e);
+      if (v >= 32 && v <= kFactorThreads && v % 32 == 0) nt = v;
+    }
+  }
+  return nt;
+}
+
 int factor_spd(const double* G, int r, int normalize, int pivot, double rel_tol, SmallFactor* out,
                int* warn, int warn_bit, cudaStream_t st, DistInfo* zero_info) {
   if (r < 1 || r > kMaxRank) return CPA_ERR_ARG;
@@ -913,7 +927,7 @@ int factor_spd(const double* G, int r, int normalize, int pivot, double rel_tol,
                                       (int)(sizeof(double) * (2 * kMaxRank * kMaxRank + 5 * kMaxRank))));
     attr_done = true;
   }
-  k_factor_spd<<<1, kFactorThreads, smem, st>>>(G, r, normalize, pivot, rel_tol, out, warn, warn_bit,
+  k_factor_spd<<<1, factor_threads(), smem, st>>>(G, r, normalize, pivot, rel_tol, out, warn, warn_bit,
                                                 zero_info);
   CPA_LAUNCH_CHECK();
   return CPA_OK;
