@@ -164,7 +164,9 @@ typedef struct {
   int64_t stage_launches[12];
   /* kernels this call launched on the GPU (each kernel node of a replayed CUDA
    * graph counted once per replay); -1 where the updates ran outside a graph
-   * (the top-s path with tau * samples < 1), where the count is not kept. */
+   * (the top-s path with tau * samples < 1), where the count is not kept.  The
+   * one-time drawing and ordering of the estimated fit's element sample (first
+   * call with new fit options) is not counted. */
   int64_t kernel_launches;
 } cpa_stats;
 

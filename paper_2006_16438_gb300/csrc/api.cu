@@ -548,7 +548,8 @@ struct Plan {
       epoch_exec = nullptr;
     }
     CPA_TRY(fit_sample_draw(X, o->fit_samples, o->fit_alpha, o->seed, o->reject_cap, &est, st));
-    if (kernels) *kernels += (est.s_nz > 0) + (est.s_z > 0);
+    CPA_TRY(fit_sample_sort(X, &est, st));
+    (void)kernels;  // one-time work, not counted (see cpa_stats.kernel_launches)
     return CPA_OK;
   }
 

@@ -11,6 +11,8 @@
 // Estimated: a stratified sample of elements drawn once (nonzeros uniformly, zero
 // cells uniformly by rejection) and F_hat = sum_j phi_j (m_j - x_j)^2 per evaluation,
 // O(s_fit D r) work instead of O(nnz D r).
+#include <algorithm>
+
 #include "fit.cuh"
 
 namespace cpa {
@@ -365,6 +367,73 @@ int fit_sample_draw(const cpa_index* X, int64_t s_fit, double alpha, uint64_t se
   S->alpha = alpha;
   S->seed = seed;
   S->reject_cap = reject_cap;
+  return CPA_OK;
+}
+
+namespace {
+
+// Sort key of sample j: its stratum above the coordinate of the largest mode.
+__global__ void k_fit_sort_keys(const int32_t* __restrict__ coords_m, int64_t n, int64_t s_nz,
+                                uint64_t* __restrict__ keys, uint32_t* __restrict__ pos) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    keys[j] = ((uint64_t)(j >= s_nz) << 32) | (uint32_t)coords_m[j];
+    pos[j] = (uint32_t)j;
+  }
+}
+
+__global__ void k_fit_gather(const int32_t* __restrict__ coords, const double* __restrict__ xs, int64_t stride,
+                             int D, int64_t n, const uint32_t* __restrict__ pos, int32_t* __restrict__ coords_out,
+                             double* __restrict__ xs_out) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t src = pos[j];
+    for (int m = 0; m < D; ++m) coords_out[(int64_t)m * stride + j] = coords[(int64_t)m * stride + src];
+    xs_out[j] = xs[src];
+  }
+}
+
+}  // namespace
+
+int fit_sample_sort(const cpa_index* X, FitSample* S, cudaStream_t st) {
+  const int64_t n = S->s_nz + S->s_z;
+  if (n < 2 || n >= (1ll << 32)) return CPA_OK;
+  const int D = X->order;
+  int mbig = 0;
+  for (int m = 1; m < D; ++m)
+    if (X->dims[m] > X->dims[mbig]) mbig = m;
+  const int bits = 33;  // stratum bit + a 32-bit coordinate
+  const size_t ws = sort_workspace(n);
+  char* buf = nullptr;
+  const size_t need = sizeof(uint64_t) * 2 * n + sizeof(uint32_t) * 2 * n + ws + 1024;
+  CPA_CUDA_TRY(cudaMallocAsync((void**)&buf, need, st));
+  uint64_t* k0 = reinterpret_cast<uint64_t*>(buf);
+  uint64_t* k1 = k0 + n;
+  uint32_t* p0 = reinterpret_cast<uint32_t*>(k1 + n);
+  uint32_t* p1 = p0 + n;
+  char* scratch = reinterpret_cast<char*>(((uintptr_t)(p1 + n) + 255) & ~(uintptr_t)255);
+  const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(n, 256), (int64_t)num_sms() * 8);
+  k_fit_sort_keys<<<grid, 256, 0, st>>>(S->coords + (size_t)mbig * S->stride, n, S->s_nz, k0, p0);
+  CPA_LAUNCH_CHECK();
+  int in_alt = 0;
+  int rc = radix_sort<uint32_t>(k0, k1, p0, p1, DevCount{nullptr, n}, 0, bits, scratch, st, &in_alt);
+  int32_t* coords2 = nullptr;
+  double* xs2 = nullptr;
+  if (rc == CPA_OK && (cudaMalloc((void**)&coords2, sizeof(int32_t) * (size_t)D * S->stride) != cudaSuccess ||
+                       cudaMalloc((void**)&xs2, sizeof(double) * (size_t)S->stride) != cudaSuccess))
+    rc = CPA_ERR_OOM;
+  if (rc == CPA_OK) {
+    k_fit_gather<<<grid, 256, 0, st>>>(S->coords, S->xs, S->stride, D, n, in_alt ? p1 : p0, coords2, xs2);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) rc = CPA_ERR_CUDA;
+  }
+  cudaFreeAsync(buf, st);
+  if (rc < 0) {
+    if (coords2) cudaFree(coords2);
+    if (xs2) cudaFree(xs2);
+    return rc;
+  }
+  cudaFree(S->coords);
+  cudaFree(S->xs);
+  S->coords = coords2;
+  S->xs = xs2;
   return CPA_OK;
 }
 

@@ -42,6 +42,11 @@ struct FitSample {
 int fit_sample_draw(const cpa_index* X, int64_t s_fit, double alpha, uint64_t seed, int reject_cap,
                     FitSample* S, cudaStream_t st);
 
+// Reorders the sample within each stratum by the coordinate of the largest mode, so
+// that the evaluation reads that factor's rows in ascending order (the estimate is a
+// sum: its value does not depend on the order).  Synchronises the stream.
+int fit_sample_sort(const cpa_index* X, FitSample* S, cudaStream_t st);
+
 // Enqueues F_hat = sum_j phi_j (m_j - x_j)^2 over the sample and *fit_dev =
 // 1 - sqrt(F_hat) / ||X|| (fit_dev[1] = F_hat).  Deterministic for a given grid.
 template <class FT>
