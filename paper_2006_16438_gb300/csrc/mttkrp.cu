@@ -15,7 +15,8 @@
 //    are taken from a counter; fibres longer than kHeavy are listed and spread over
 //    the warps of one block each by k_tnsr_heavy.  The KRP rows are never written.
 //
-// When M does not fit in L2 (billions of nonzeros: n_k in the millions), its rows are
+// Optionally (CPA_MTTKRP_SLAB_BYTES = bytes per slab; off by default, since one pass
+// with the piece list measured faster on the 1.75e9-nonzero tensor), M's rows are
 // split into P slabs.  k_slab_prep probes every sample's fibre once, stores u_j and,
 // since the nonzeros of a fibre are sorted by i_k, where each slab's rows start in the
 // fibre; then for p = 0..P-1, k_slab_light and k_slab_heavy add the nonzeros of slab p
@@ -110,7 +111,9 @@ __global__ void __launch_bounds__(kGramMaxThreads) k_krp_gram(FactorPtrs F, KeyL
   }
 }
 
-constexpr int kHeavy = 64;  // fibres longer than this go to the heavy list
+constexpr int kHeavy = 64;          // fibres longer than this go to the heavy list
+constexpr int kPiece = 4096;        // heavy fibres are listed in pieces of at most this length
+constexpr int kHeavyPerSample = 4;  // heavy-list entries per sample of the buffer
 
 // Light pass: warps take chunks of 32 consecutive samples from a counter.  Lane l
 // probes sample l; a fibre longer than kHeavy is appended to the heavy list
@@ -121,12 +124,12 @@ constexpr int kHeavy = 64;  // fibres longer than this go to the heavy list
 // atomics into M.  ctr[0] += sampled nonzeros, ctr[1] = chunk counter, ctr[2] =
 // heavy-list length.
 template <class FT, class VT, int CPL, bool kPriv>
-__global__ void __launch_bounds__(kThreads) k_tnsr_mttkrp(FibreIndex<VT> X, FactorPtrs F, KeyLayout L,
+__global__ void __launch_bounds__(kThreads, 4) k_tnsr_mttkrp(FibreIndex<VT> X, FactorPtrs F, KeyLayout L,
                                                           int r, const uint64_t* __restrict__ idx,
                                                           const double* __restrict__ wgt, DevCount sbar,
                                                           int64_t nk, FT* __restrict__ M,
                                                           unsigned long long* __restrict__ ctr,
-                                                          uint4* __restrict__ heavy) {
+                                                          uint4* __restrict__ heavy, int64_t heavy_cap) {
   extern __shared__ __align__(16) unsigned char mk_smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t mz = nk * r;
@@ -154,10 +157,20 @@ __global__ void __launch_bounds__(kThreads) k_tnsr_mttkrp(FibreIndex<VT> X, Fact
     }
     uint32_t len = (uint32_t)(hi - lo);
     my_nnz += len;
-    if (len > kHeavy) {
-      const unsigned long long h = atomicAdd(&ctr[2], 1ull);
-      heavy[h] = make_uint4((unsigned)j, (unsigned)(lo & 0xffffffffu), (unsigned)(lo >> 32), len);
-      len = 0;
+    if (len > kHeavy) {  // listed in pieces, each taken whole by one block of k_tnsr_heavy
+      const uint32_t np = (len + kPiece - 1) / kPiece;
+      const unsigned long long h = atomicAdd(&ctr[2], (unsigned long long)np);
+      if (h + np <= (unsigned long long)heavy_cap) {
+        for (uint32_t q = 0; q < np; ++q) {
+          const uint64_t ps = lo + (uint64_t)q * kPiece;
+          const uint32_t pl = len - q * kPiece < (uint32_t)kPiece ? len - q * kPiece : kPiece;
+          heavy[h + q] = make_uint4((unsigned)j, (unsigned)(ps & 0xffffffffu), (unsigned)(ps >> 32), pl);
+        }
+        len = 0;
+      } else {  // list full: empty the slots reserved below the capacity, walk the fibre here
+        for (unsigned long long q = h; q < h + np && q < (unsigned long long)heavy_cap; ++q)
+          heavy[q] = make_uint4((unsigned)j, 0u, 0u, 0u);
+      }
     }
     unsigned todo = __ballot_sync(0xffffffffu, len > 0);
     while (todo) {
@@ -179,27 +192,24 @@ __global__ void __launch_bounds__(kThreads) k_tnsr_mttkrp(FibreIndex<VT> X, Fact
         }
         u[v] = z;
       }
-      int32_t ikl = 0;
-      FT xl = FT(0);
-      if (lane < (int)lq) {  // lq <= kHeavy: at most two loads per lane
-        ikl = X.ik[oq + lane];
-        xl = (FT)X.val[oq + lane];
-      }
-      int32_t ikl2 = 0;
-      FT xl2 = FT(0);
-      if (lane + 32 < (int)lq) {
-        ikl2 = X.ik[oq + 32 + lane];
-        xl2 = (FT)X.val[oq + 32 + lane];
-      }
-      for (int q2 = 0; q2 < (int)lq; ++q2) {
-        const int32_t ik = __shfl_sync(0xffffffffu, q2 < 32 ? ikl : ikl2, q2 & 31);
-        const FT x = __shfl_sync(0xffffffffu, q2 < 32 ? xl : xl2, q2 & 31);
+      for (uint32_t g = 0; g < lq; g += 32) {  // nonzeros 32 at a time
+        const int nb = lq - g < 32 ? (int)(lq - g) : 32;
+        int32_t ikl = 0;
+        FT xl = FT(0);
+        if (lane < nb) {
+          ikl = X.ik[oq + g + lane];
+          xl = (FT)X.val[oq + g + lane];
+        }
+        for (int q2 = 0; q2 < nb; ++q2) {
+          const int32_t ik = __shfl_sync(0xffffffffu, ikl, q2);
+          const FT x = __shfl_sync(0xffffffffu, xl, q2);
 #pragma unroll
-        for (int v = 0; v < CPL; ++v) {
-          const int c = lane + 32 * v;
-          if (c < r) {
-            if (kPriv) Mw[(int64_t)ik * r + c] += x * u[v];
-            else atomicAdd(&Mw[(int64_t)ik * r + c], x * u[v]);
+          for (int v = 0; v < CPL; ++v) {
+            const int c = lane + 32 * v;
+            if (c < r) {
+              if (kPriv) Mw[(int64_t)ik * r + c] += x * u[v];
+              else atomicAdd(&Mw[(int64_t)ik * r + c], x * u[v]);
+            }
           }
         }
       }
@@ -219,21 +229,29 @@ __global__ void __launch_bounds__(kThreads) k_tnsr_mttkrp(FibreIndex<VT> X, Fact
   }
 }
 
-// Heavy pass: one block per listed fibre (block-stride); warp w takes the fibre's
-// nonzeros in groups of 32 (w, w + 8, ...), forming u_j itself.
+// Heavy pass: blocks take listed pieces from a counter (ctr[3]); each forms u_j of its
+// sample and its warps take the piece's nonzeros in groups of 32 (w, w + 8, ...), the
+// next group's loads issued before the current group is added.
 template <class FT, class VT, int CPL>
 __global__ void __launch_bounds__(kThreads) k_tnsr_heavy(FibreIndex<VT> X, FactorPtrs F, KeyLayout L,
                                                          int r, const uint64_t* __restrict__ idx,
                                                          const double* __restrict__ wgt, FT* __restrict__ M,
-                                                         const unsigned long long* __restrict__ ctr,
-                                                         const uint4* __restrict__ heavy) {
+                                                         unsigned long long* __restrict__ ctr,
+                                                         const uint4* __restrict__ heavy, int64_t heavy_cap) {
+  __shared__ long long item;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t nh = (int64_t)ctr[2];
-  for (int64_t h = blockIdx.x; h < nh; h += gridDim.x) {
+  const long long nh = (long long)(ctr[2] < (unsigned long long)heavy_cap ? ctr[2] : heavy_cap);
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) item = (long long)atomicAdd(&ctr[3], 1ull);
+    __syncthreads();
+    const long long h = item;
+    if (h >= nh) break;
     const uint4 e = heavy[h];
     const int64_t j = e.x;
     const uint64_t lo = (uint64_t)e.y | ((uint64_t)e.z << 32);
     const uint32_t len = e.w;
+    if (len == 0) continue;
     const uint64_t key = idx[j];
     const FT wq = (FT)wgt[j];
     FT u[CPL];
@@ -248,13 +266,21 @@ __global__ void __launch_bounds__(kThreads) k_tnsr_heavy(FibreIndex<VT> X, Facto
       }
       u[v] = z;
     }
-    for (uint64_t g = (uint64_t)warp * 32; g < len; g += kThreads) {
+    uint64_t g = (uint64_t)warp * 32;
+    int32_t ikl = 0;
+    FT xl = FT(0);
+    if (g + lane < len) {
+      ikl = X.ik[lo + g + lane];
+      xl = (FT)X.val[lo + g + lane];
+    }
+    for (; g < len; g += kThreads) {
       const int nb = len - g < 32 ? (int)(len - g) : 32;
-      int32_t ikl = 0;
-      FT xl = FT(0);
-      if (lane < nb) {
-        ikl = X.ik[lo + g + lane];
-        xl = (FT)X.val[lo + g + lane];
+      const uint64_t gn = g + kThreads;
+      int32_t ikn = 0;
+      FT xn = FT(0);
+      if (gn + lane < len) {
+        ikn = X.ik[lo + gn + lane];
+        xn = (FT)X.val[lo + gn + lane];
       }
       for (int q2 = 0; q2 < nb; ++q2) {
         const int32_t ik = __shfl_sync(0xffffffffu, ikl, q2);
@@ -265,14 +291,15 @@ __global__ void __launch_bounds__(kThreads) k_tnsr_heavy(FibreIndex<VT> X, Facto
           if (c < r) atomicAdd(&M[(int64_t)ik * r + c], x * u[v]);
         }
       }
+      ikl = ikn;
+      xl = xn;
     }
   }
 }
 
 // ---- row-slab path ----------------------------------------------------------
 constexpr int kSlabHeavy = 256;    // slab ranges longer than this go to the pass's heavy list
-constexpr int kSlabPiece = 4096;   // heavy ranges are listed in pieces of at most this length
-constexpr int kHeavyPerSample = 4; // heavy-list entries per sample of the buffer
+constexpr int kSlabPiece = kPiece;  // heavy slab ranges are listed in pieces of this length
 
 // Per sample (a warp takes 32 consecutive samples): probe the fibre, store u_j and the
 // start of each slab's rows in the fibre (ballots over the loaded i_k for fibres of at
@@ -542,6 +569,7 @@ int launch_mttkrp(const cpa_index* X, int k, const FactorPtrs& F, int r, const u
   const unsigned grid = (unsigned)(want < cap ? (want > 0 ? want : 1) : cap);
   unsigned long long* ctr = reinterpret_cast<unsigned long long*>(B.ctr);
   uint4* heavy = reinterpret_cast<uint4*>(B.heavy);
+  const int64_t hcap = (int64_t)kHeavyPerSample * (sbar.max > 0 ? sbar.max : 1);
 #define CPA_MK(CPL, PRIV)                                                                         \
   do {                                                                                            \
     if (PRIV) {                                                                                   \
@@ -553,7 +581,7 @@ int launch_mttkrp(const cpa_index* X, int k, const FactorPtrs& F, int r, const u
       }                                                                                           \
     }                                                                                             \
     k_tnsr_mttkrp<FT, VT, CPL, PRIV><<<grid, kThreads, PRIV ? priv : 0, st>>>(                    \
-        fx, F, L, r, idx, wgt, sbar, nk, M, ctr, heavy);                                          \
+        fx, F, L, r, idx, wgt, sbar, nk, M, ctr, heavy, hcap);                                    \
   } while (0)
   if (r <= 32) {
     if (use_priv) CPA_MK(1, true); else CPA_MK(1, false);
@@ -564,9 +592,9 @@ int launch_mttkrp(const cpa_index* X, int k, const FactorPtrs& F, int r, const u
   CPA_LAUNCH_CHECK();
   const unsigned hgrid = (unsigned)sms * 2;
   if (r <= 32)
-    k_tnsr_heavy<FT, VT, 1><<<hgrid, kThreads, 0, st>>>(fx, F, L, r, idx, wgt, M, ctr, heavy);
+    k_tnsr_heavy<FT, VT, 1><<<hgrid, kThreads, 0, st>>>(fx, F, L, r, idx, wgt, M, ctr, heavy, hcap);
   else
-    k_tnsr_heavy<FT, VT, 2><<<hgrid, kThreads, 0, st>>>(fx, F, L, r, idx, wgt, M, ctr, heavy);
+    k_tnsr_heavy<FT, VT, 2><<<hgrid, kThreads, 0, st>>>(fx, F, L, r, idx, wgt, M, ctr, heavy, hcap);
   CPA_LAUNCH_CHECK();
   return CPA_OK;
 }
@@ -579,13 +607,13 @@ size_t mttkrp_slab_bytes() {
     const long long v = atoll(e);
     if (v > 0) return (size_t)v;
   }
-  return size_t(32) << 20;
+  return 0;  // off: at 1.75e9 nonzeros one pass with the piece list is faster (1.30 vs 1.66 ms per update)
 }
 
 int mttkrp_slabs(int64_t nk, int r, int ftb) {
   const size_t bytes = (size_t)nk * r * ftb;
   const size_t slab = mttkrp_slab_bytes();
-  if (bytes <= slab || nk < 2) return 1;
+  if (slab == 0 || bytes <= slab || nk < 2) return 1;
   int64_t P = (int64_t)((bytes + slab - 1) / slab);
   if (P > kSlabMax) P = kSlabMax;
   if (P > nk) P = nk;
@@ -596,7 +624,7 @@ void mttkrp_buffers_carve(Arena& a, int64_t s, int r, int ftb, bool slabs, Mttkr
   const size_t ss = (size_t)(s > 0 ? s : 1);
   B->ctr = a.take<uint64_t>(kMttkrpCounters);
   B->total = B->ctr;
-  B->heavy = a.take<uint32_t>(4 * ss * (slabs ? kHeavyPerSample : 1));
+  B->heavy = a.take<uint32_t>(4 * ss * kHeavyPerSample);
   if (slabs) {
     B->U = a.take<char>(ss * r * ftb);
     B->los = a.take<uint64_t>(ss);

@@ -28,8 +28,9 @@ struct MttkrpBuffers {
 constexpr int kMttkrpCounters = 4 + 3 * 32;
 constexpr int kSlabMax = 31;  // most row slabs of one M
 
-// Bytes of M per row slab: M larger than this is accumulated slab by slab so that
-// the scattered additions of a pass stay in L2 (CPA_MTTKRP_SLAB_BYTES overrides).
+// Bytes of M per row slab (CPA_MTTKRP_SLAB_BYTES; 0 = no slabs, the default): M
+// larger than this is accumulated slab by slab, the additions of a pass confined to
+// one slab of rows.
 size_t mttkrp_slab_bytes();
 // Number of row slabs of an n_k x r M of ftb-byte elements (1: no slabs).
 int mttkrp_slabs(int64_t nk, int r, int ftb);
