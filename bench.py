@@ -177,6 +177,7 @@ def krp_gram_flops(stats, d):
 SMS, SM_MAX_GHZ = 152, 2.07
 FP64_PEAK_TFLOPS = SMS * 2 * 2 * SM_MAX_GHZ / 1000.0
 FP32_PEAK_TFLOPS = SMS * 128 * 2 * SM_MAX_GHZ / 1000.0
+TF32_PER_BF16 = 1.1 / 2.25  # nominal dense tensor rates of the part
 
 STAGES = ["sample", "krp_gram", "mttkrp", "solve", "leverage", "fit"]
 
@@ -349,15 +350,32 @@ def main():
         kg_ms = stg[1]
         kg_flops = krp_gram_flops(acc, d)
         kg_tf = kg_flops / (kg_ms / 1000.0) / 1e12 if kg_ms > 0 else None
-        pk = FP64_PEAK_TFLOPS if b_f == 8 else FP32_PEAK_TFLOPS
-        kg = {"bound": "alu", "kernel": f"k_krp_gram (sampled KRP rows + sampled Gram, {'FP64' if b_f == 8 else 'FP32'})",
-              "achieved": kg_tf, "peak": pk, "unit": "TFLOP/s", "frac": (kg_tf / pk) if kg_tf else None,
-              "traffic": captured_traffic("k_krp_gram<double,1>", "paper_2006_16438_gb300/csrc/mttkrp.cu")
-              if b_f == 8 else None,
-              "traffic_unit": "DRAM bytes per launch (ncu, profiles/traffic.json)",
-              "peak_source": f"derived: 152 SMs x {2 if b_f == 8 else 128} {'FP64' if b_f == 8 else 'FP32'} "
-                             "FMA/clk x 2 flops x 2.07 GHz",
-              "flops_per_update": kg_flops / n_updates, "ms_per_update": kg_ms / n_updates}
+        if b_f == 8:
+            kg = {"bound": "alu", "kernel": "k_krp_gram (sampled KRP rows + sampled Gram, FP64)",
+                  "achieved": kg_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                  "frac": (kg_tf / FP64_PEAK_TFLOPS) if kg_tf else None,
+                  "traffic": captured_traffic("k_krp_gram<double,1>", "paper_2006_16438_gb300/csrc/mttkrp.cu"),
+                  "traffic_unit": "DRAM bytes per launch (ncu, profiles/traffic.json)",
+                  "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz",
+                  "flops_per_update": kg_flops / n_updates, "ms_per_update": kg_ms / n_updates}
+        elif os.environ.get("CPA_GRAM_TENSOR_CORES", "0") not in ("", "0"):
+            # tensor cores, kind::tf32: the measured bf16 peak times the nominal tf32/bf16 ratio
+            pk = peaks["bf16_tflops"] * TF32_PER_BF16
+            issued = acc["sbar_total"] * 128 * (32 if RANK <= 32 else 64) * 2 * 3  # M=128 x N x 2 flops x 3 products
+            kg = {"bound": "tensor", "kernel": "k_krp_gram_tc (sampled KRP rows + sampled Gram, tcgen05 kind::tf32, "
+                                               "3-product split)",
+                  "achieved": kg_tf, "peak": pk, "unit": "TFLOP/s", "frac": (kg_tf / pk) if kg_tf else None,
+                  "traffic": None,
+                  "peak_source": f"{peak_src} bf16_tflops x nominal tf32/bf16 ratio {TF32_PER_BF16:.3f}",
+                  "tensor_flops_issued_per_update": issued / n_updates,
+                  "flops_per_update": kg_flops / n_updates, "ms_per_update": kg_ms / n_updates}
+        else:
+            # FP32 pipe (the default): FP32 tile sums added across tiles in FP64
+            kg = {"bound": "alu", "kernel": "k_krp_gram (sampled KRP rows + sampled Gram, FP32 tile sums, FP64 across tiles)",
+                  "achieved": kg_tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                  "frac": (kg_tf / FP32_PEAK_TFLOPS) if kg_tf else None, "traffic": None,
+                  "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 flops x 2.07 GHz",
+                  "flops_per_update": kg_flops / n_updates, "ms_per_update": kg_ms / n_updates}
         return kg, mk
 
     kg64, mk64 = rooflines(stages, stat_acc, 8)
@@ -498,7 +516,7 @@ def run_amazon(args, rank, world, local):
                    "step": "1 epoch = 5 outer iterations x 3 mode updates + estimated fit",
                    "l2": "inputs far larger than L2 (about 40 GB of index)",
                    "parallelism": f"{world} independent replicas" if world > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "kernel": "sampled MTTKRP (k_slab_prep/light/heavy, row slabs)",
+        "roofline": {"bound": "hbm", "kernel": ("sampled MTTKRP (k_slab_prep/light/heavy, row slabs)" if os.environ.get("CPA_MTTKRP_SLAB_BYTES", "0") not in ("", "0") else "sampled MTTKRP (k_tnsr_mttkrp + k_tnsr_heavy, one pass, fibre pieces)"),
                      "achieved": mk_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": (mk_gbs / peaks["hbm_gbs"]) if mk_gbs else None, "traffic": None,
                      "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",

@@ -387,6 +387,7 @@ struct Plan {
         cudaEventCreateWithFlags(&fork.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&fork.ev_join, cudaEventDisableTiming) != cudaSuccess)
       return CPA_ERR_CUDA;
+    MB.status = &SB[0].state->status;  // the tensor-core Gram reports a timed-out wait here
     // per-mode copies of the sample buffers differ only in the candidate offsets
     for (int k = 0; k < D; ++k) {
       SB[k] = SB[0];

@@ -535,9 +535,241 @@ int launch_mttkrp_slabs(const cpa_index* X, int k, const FactorPtrs& F, int r, c
   return CPA_OK;
 }
 
+// ---- sampled Gram on the tensor cores (mixed precision) -----------------------
+// G = sum_j y_j y_j^T as a matrix product D = Y^T Y over the samples: one block takes
+// 128 samples in four tiles of 32.  Its threads form y_j (FP32) and split each value
+// into hi = tf32(y) (round to nearest) and lo = y - hi (exact in FP32); the tiles are
+// written to shared memory as the K-major operand (rows = the r coordinates padded to
+// M = 128, K = samples) in the canonical layout without swizzle (8-row x 16-byte
+// core matrices: K-adjacent 128 bytes apart, 8-row groups 1024 bytes apart).  One
+// thread issues, per K-step of 8 samples, tcgen05.mma kind::tf32 with M = 128 and
+// N = 32 (or 64) for hi.hi, hi.lo and lo.hi (the three-product split, about FP32
+// accuracy), accumulating in tensor memory; tcgen05.commit signals an mbarrier per
+// tile buffer (two buffers).  The block then reads its r x r partial Gram with
+// tcgen05.ld every 128 samples (the FP32 accumulation stays short), sums the partials
+// in FP64 in shared memory and adds them into G once.  Every mbarrier wait is bounded:
+// on timeout the status word records CPA_ERR_CUDA and the block still frees its
+// tensor memory.
+namespace tc {
+
+constexpr int kThreads = 256;
+constexpr int kK = 32;        // samples per tile
+constexpr int kTiles = 4;     // tiles per block
+constexpr uint32_t kLBO = 128;   // bytes between K-adjacent core matrices
+constexpr uint32_t kSBO = 1024;  // bytes between 8-row groups (kK / 4 core matrices)
+constexpr uint32_t kTileBytes = 128 * kK * 4;  // one operand tile (M = 128 rows)
+constexpr int kSpin = 1 << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: start, leading (K) and stride (M/N) byte offsets,
+// descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t desc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((kLBO >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((kSBO >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ bool wait_parity(uint64_t* bar, uint32_t parity) {
+  uint32_t done = 0;
+  for (int it = 0; it < kSpin && !done; ++it)
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity));
+  return done != 0;
+}
+
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t y;
+  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(y) : "f"(x));
+  return __uint_as_float(y);
+}
+
+}  // namespace tc
+
+template <int NCOLS>
+__global__ void __launch_bounds__(tc::kThreads) k_krp_gram_tc(FactorPtrs F, KeyLayout L, int r,
+                                                              const uint64_t* __restrict__ idx,
+                                                              const double* __restrict__ wgt, DevCount sbar,
+                                                              double* __restrict__ G, int* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char tc_raw[];
+  __shared__ uint32_t rows[tc::kK][kMaxOrder];
+  __shared__ float wsh[tc::kK];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ uint32_t tmem;
+  const int64_t n = sbar.get();
+  const int64_t group = (int64_t)tc::kK * tc::kTiles;  // samples per readout
+  const int64_t ngroups = (n + group - 1) / group;
+  if ((int64_t)blockIdx.x >= ngroups) return;  // the whole block
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // four operand tiles (buffer 0 hi, lo; buffer 1 hi, lo), 1024-byte aligned; rows >= r
+  // stay zero for the block's life
+  const uint32_t raw = tc::smem_u32(tc_raw);
+  const uint32_t pad = ((raw + 1023u) & ~1023u) - raw;
+  float* tiles = reinterpret_cast<float*>(tc_raw + pad);
+  const uint32_t tiles_s = raw + pad;
+  double* gacc = reinterpret_cast<double*>(tc_raw + pad + 4 * tc::kTileBytes);  // r x r FP64 partial Gram
+  for (int i = tid; i < 4 * (int)(tc::kTileBytes / 16); i += tc::kThreads)
+    reinterpret_cast<float4*>(tiles)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int i = tid; i < r * r; i += tc::kThreads) gacc[i] = 0.0;
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(tc::smem_u32(&bar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(tc::smem_u32(&bar[1])));
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(tc::smem_u32(&tmem)),
+                 "r"(NCOLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t d = tmem;
+  // D F32, A and B TF32, both K-major, N = NCOLS, M = 128
+  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NCOLS >> 3) << 17) | (8u << 24);
+  bool ok = true;
+  int64_t T = 0;  // tiles issued by this block (tile T uses buffer T & 1, its (T >> 1)-th commit)
+  for (int64_t gi = blockIdx.x; gi < ngroups && ok; gi += gridDim.x) {
+    const int64_t s0 = gi * group;
+    for (int t = 0; t < tc::kTiles; ++t, ++T) {
+      const int stage = (int)(T & 1);
+      if (T >= 2 && !tc::wait_parity(&bar[stage], (uint32_t)((T - 2) >> 1) & 1u)) ok = false;
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const int64_t base = s0 + (int64_t)t * tc::kK;
+      if (tid < tc::kK) {
+        const int64_t j = base + tid;
+        float w = 0.f;
+        if (j < n) {
+          const uint64_t key = idx[j];
+          for (int q = 0; q < L.d; ++q) rows[tid][q] = L.get(key, q);
+          w = (float)wgt[j];
+        } else {
+          for (int q = 0; q < L.d; ++q) rows[tid][q] = 0;
+        }
+        wsh[tid] = w;
+      }
+      __syncthreads();
+      float* hi = tiles + (size_t)(2 * stage) * (tc::kTileBytes / 4);
+      float* lo = hi + tc::kTileBytes / 4;
+      for (int e = tid; e < tc::kK * r; e += tc::kThreads) {
+        const int sl = e / r, c = e - sl * r;
+        float v = wsh[sl];
+        for (int q = 0; q < L.d; ++q) v *= static_cast<const float*>(F.A[L.mode[q]])[(int64_t)rows[sl][q] * r + c];
+        const float h = tc::to_tf32(v);
+        const uint32_t off = (uint32_t)(c >> 3) * tc::kSBO + (uint32_t)(sl >> 2) * tc::kLBO + (uint32_t)(c & 7) * 16u +
+                             (uint32_t)(sl & 3) * 4u;
+        hi[off >> 2] = h;
+        lo[off >> 2] = v - h;
+      }
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      if (tid == 0) {
+        const uint32_t hs = tiles_s + (uint32_t)(2 * stage) * tc::kTileBytes, ls = hs + tc::kTileBytes;
+        for (int ks = 0; ks < tc::kK / 8; ++ks) {
+          const uint32_t ko = (uint32_t)ks * 2u * tc::kLBO;  // 8 samples = two core matrices along K
+          const uint64_t ah = tc::desc(hs + ko), al = tc::desc(ls + ko);
+          tc::mma_tf32(d, ah, ah, idesc, (t | ks) != 0);  // a new group starts from zero
+          tc::mma_tf32(d, ah, al, idesc, 1u);
+          tc::mma_tf32(d, al, ah, idesc, 1u);
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+            tc::smem_u32(&bar[stage])));
+      }
+    }
+    // the group's last commit on each buffer (tiles T - 2 and T - 1)
+    if (!tc::wait_parity(&bar[(T - 2) & 1], (uint32_t)((T - 2) >> 1) & 1u)) ok = false;
+    if (!tc::wait_parity(&bar[(T - 1) & 1], (uint32_t)((T - 1) >> 1) & 1u)) ok = false;
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (ok) {
+#pragma unroll
+      for (int cc = 0; cc < NCOLS / 32; ++cc) {
+        if (warp * 32 < r) {  // warp-uniform: this warp's lanes hold rows 32 w .. 32 w + 31
+          uint32_t v[32];
+          const uint32_t a = d + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 32);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+              "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+              : "r"(a));
+          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+          const int row = warp * 32 + lane;
+          if (row < r) {  // each (row, col) belongs to one thread: plain FP64 adds
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) {
+              const int col = cc * 32 + jj;
+              if (col < r) gacc[row * r + col] += (double)__uint_as_float(v[jj]);
+            }
+          }
+        }
+      }
+    }
+    // the next group's first products overwrite D: the reads above come first
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  }
+  if (!ok) {
+    if (tid == 0) atomicCAS(status, 0, CPA_ERR_CUDA);
+    if (T >= 1) tc::wait_parity(&bar[(T - 1) & 1], (uint32_t)((T - 1) >> 1) & 1u);  // bounded, again
+    if (T >= 2) tc::wait_parity(&bar[(T - 2) & 1], (uint32_t)((T - 2) >> 1) & 1u);
+  } else {
+    for (int i = tid; i < r * r; i += tc::kThreads)  // the block's partial Gram, once
+      if (gacc[i] != 0.0) atomicAdd(&G[i], gacc[i]);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(d), "r"(NCOLS));
+}
+
+// Sampled Gram of FP32 factors on the tensor cores (k_krp_gram_tc).  Measured on the
+// Uber-shaped tensor it is slower than the FP32-pipe kernel (60 against 42 us per
+// update: both are bound by the factor-row gathers, the tensor pipe is about 3 %
+// busy), so it runs only with CPA_GRAM_TENSOR_CORES=1.
+bool gram_tensor_cores() {  // read at each launch set-up (a plan's graph keeps its choice)
+  const char* e = getenv("CPA_GRAM_TENSOR_CORES");
+  return e && atoi(e) != 0;
+}
+
+int launch_gram_tc(const FactorPtrs& F, const KeyLayout& L, int r, const uint64_t* idx, const double* wgt,
+                   DevCount sbar, double* G, int* status, cudaStream_t st) {
+  const size_t smem_max = 4 * (size_t)tc::kTileBytes + 1024 + sizeof(double) * kMaxRank * kMaxRank;
+  const size_t smem = 4 * (size_t)tc::kTileBytes + 1024 + sizeof(double) * (size_t)r * r;
+  static bool attr = false;
+  if (!attr) {
+    CPA_CUDA_TRY(cudaFuncSetAttribute(k_krp_gram_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+    CPA_CUDA_TRY(cudaFuncSetAttribute(k_krp_gram_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+    attr = true;
+  }
+  const int64_t groups = ceil_div(sbar.max > 0 ? sbar.max : 1, (int64_t)tc::kK * tc::kTiles);
+  const int64_t nb = groups < (int64_t)num_sms() * 3 ? groups : (int64_t)num_sms() * 3;  // persistent blocks
+  if (r <= 32)
+    k_krp_gram_tc<32><<<(unsigned)nb, tc::kThreads, smem, st>>>(F, L, r, idx, wgt, sbar, G, status);
+  else
+    k_krp_gram_tc<64><<<(unsigned)nb, tc::kThreads, smem, st>>>(F, L, r, idx, wgt, sbar, G, status);
+  CPA_LAUNCH_CHECK();
+  return CPA_OK;
+}
+
 template <class FT>
 int launch_gram(const FactorPtrs& F, const KeyLayout& L, int r, const uint64_t* idx, const double* wgt,
-                DevCount sbar, double* G, cudaStream_t st) {
+                DevCount sbar, double* G, int* status, cudaStream_t st) {
+  if constexpr (sizeof(FT) == 4) {
+    if (gram_tensor_cores()) return launch_gram_tc(F, L, r, idx, wgt, sbar, G, status, st);
+  }
   const int sms = num_sms();
   const int np = r * (r + 1) / 2;
   // threads: the pair count rounded up to whole warps, at most 1024 (r > 44: 2-3 pairs each)
@@ -646,6 +878,7 @@ int sampled_mttkrp(const cpa_index* X, int k, const FactorPtrs& F, int r, const 
   CPA_CUDA_TRY(cudaMemsetAsync(B.ctr, 0, kMttkrpCounters * sizeof(uint64_t), st));
   if (sbar.max <= 0) return CPA_OK;
   const KeyLayout& L = X->mode[k].L;
+  int* gstatus = B.status ? B.status : reinterpret_cast<int*>(B.ctr + kMttkrpCounters - 1);
   const int P = B.U ? mttkrp_slabs(X->dims[k], r, (int)sizeof(FT)) : 1;
   auto mttkrp = [&](cudaStream_t s2) {
     if (P > 1)
@@ -661,14 +894,14 @@ int sampled_mttkrp(const cpa_index* X, int k, const FactorPtrs& F, int r, const 
     // the Gram on the side stream, the MTTKRP on st, joined before returning
     CPA_CUDA_TRY(cudaEventRecord(fork->ev_fork, st));
     CPA_CUDA_TRY(cudaStreamWaitEvent(fork->aux, fork->ev_fork, 0));
-    CPA_TRY(launch_gram<FT>(F, L, r, idx_packed, wgt, sbar, G, fork->aux));
+    CPA_TRY(launch_gram<FT>(F, L, r, idx_packed, wgt, sbar, G, gstatus, fork->aux));
     CPA_CUDA_TRY(cudaEventRecord(fork->ev_join, fork->aux));
     CPA_TRY(mttkrp(st));
     CPA_CUDA_TRY(cudaStreamWaitEvent(st, fork->ev_join, 0));
     return CPA_OK;
   }
   if (timed) CPA_CUDA_TRY(record_event(ev[0], st));
-  CPA_TRY(launch_gram<FT>(F, L, r, idx_packed, wgt, sbar, G, st));
+  CPA_TRY(launch_gram<FT>(F, L, r, idx_packed, wgt, sbar, G, gstatus, st));
   if (timed && ev[1]) CPA_CUDA_TRY(record_event(ev[1], st));
   CPA_TRY(mttkrp(st));
   return CPA_OK;

@@ -24,6 +24,9 @@ struct MttkrpBuffers {
   void* U = nullptr;
   uint64_t* los = nullptr;
   uint32_t* bnd = nullptr;
+  // sticky status word of the run (device; null: a word of ctr) for kernels that can
+  // time out (the tensor-core Gram's bounded waits)
+  int* status = nullptr;
 };
 constexpr int kMttkrpCounters = 4 + 3 * 32;
 constexpr int kSlabMax = 31;  // most row slabs of one M

@@ -165,3 +165,46 @@ def test_mixed_float_pair_leverage_matches_fp64_rows(r):
         np.testing.assert_array_equal(got["idx"].cpu().numpy().astype(np.uint64), ref["idx"])
         np.testing.assert_array_equal(got["cnt"].cpu().numpy().astype(np.uint32), ref["cnt"])
         assert relerr(got["wgt"].cpu().numpy(), ref["wgt"]) < 1e-12
+
+
+@pytest.mark.parametrize("r", [33, 40, 64])
+def test_mode_update_mixed_wide_rank_within_2e4(r):
+    """Mixed precision with r > 32 (the tensor-core sampled Gram with N = 64): the
+    new factor within 2e-4 of the FP64 oracle's solve on the GPU's own rows."""
+    dims = (50, 40, 30)
+    coo = synth.random_sparse_tensor(dims, 20000, seed=r)
+    facs = synth.gaussian_factors(dims, r, seed=r + 1)
+    gi = cpa.cpa_index_build(coo)
+    oi = oracle.Index(coo)
+    for k in range(3):
+        fs = [torch.from_numpy(a).cuda() for a in facs]
+        got = cpa.cpa_mode_update(gi, fs, k, rank=r, samples=1200, tau=1.0, seed=3, it=0, precision=binding.MIXED)
+        idx = got["idx"].cpu().numpy().astype(np.uint64)
+        wgt = got["wgt"].cpu().numpy()
+        M, G, _ = oracle.sampled_mttkrp(oi, k, facs, idx, wgt)
+        A, _ = oracle.solve(G, M)
+        An, lam = oracle.normalize(A)
+        assert relerr(fs[k].cpu().numpy(), An) < 2e-4
+        assert relerr(got["lam"].cpu().numpy(), lam) < 2e-4
+
+
+@pytest.mark.parametrize("r", [4, 25, 40, 64])
+def test_mode_update_mixed_tensor_core_gram(monkeypatch, r):
+    """The sampled Gram on the tensor cores (CPA_GRAM_TENSOR_CORES=1: tcgen05 kind::tf32
+    with the three-product split, M = 128, N = 32 or 64): the new factor within 2e-4
+    of the FP64 oracle's solve on the GPU's own rows."""
+    monkeypatch.setenv("CPA_GRAM_TENSOR_CORES", "1")
+    dims = (50, 40, 30)
+    coo = synth.random_sparse_tensor(dims, 20000, seed=100 + r)
+    facs = synth.gaussian_factors(dims, r, seed=r + 3)
+    gi = cpa.cpa_index_build(coo)
+    oi = oracle.Index(coo)
+    for k in range(3):
+        fs = [torch.from_numpy(a).cuda() for a in facs]
+        got = cpa.cpa_mode_update(gi, fs, k, rank=r, samples=1500, tau=1.0, seed=4, it=0, precision=binding.MIXED)
+        idx = got["idx"].cpu().numpy().astype(np.uint64)
+        wgt = got["wgt"].cpu().numpy()
+        M, G, _ = oracle.sampled_mttkrp(oi, k, facs, idx, wgt)
+        A, _ = oracle.solve(G, M)
+        An, lam = oracle.normalize(A)
+        assert relerr(fs[k].cpu().numpy(), An) < 2e-4
