@@ -55,11 +55,11 @@ def parse():
     p.add_argument("--batched-problems", type=int, default=64)
     p.add_argument("--cpu-sample-updates", type=int, default=4,
                    help="mode updates the CPU baseline times (bounded sample)")
-    p.add_argument("--workload", default="uber", choices=["uber", "amazon"],
+    p.add_argument("--workload", default="uber", choices=["uber", "amazon", "reddit"],
                    help="uber: the default line; amazon: the 4.8M x 1.8M x 1.8M, 1.7e9-nonzero tensor "
                         "(mixed precision, generated on the GPU)")
     p.add_argument("--amazon-fraction", type=float, default=1.0,
-                   help="fraction of the amazon-shaped tensor's events (dims kept)")
+                   help="fraction of the amazon- or reddit-shaped tensor's events (dims kept)")
     return p.parse_args()
 
 
@@ -257,8 +257,8 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank)
-    if args.workload == "amazon":
-        return run_amazon(args, rank, world, local)
+    if args.workload in LARGE:
+        return run_large(args, LARGE[args.workload], rank, world, local)
     import torch
     import paper_2006_16438_gb300 as cpa
     torch.cuda.set_device(local)
@@ -431,17 +431,29 @@ def main():
 AMAZON_DIMS = (4_821_207, 1_774_269, 1_805_187)
 AMAZON_NNZ = 1_740_000_000
 AMAZON_EVENTS_PER_NNZ = 1.43  # Poisson events per distinct nonzero of this planted model
+# The billion-nonzero workloads: shape, target nonzeros, Poisson events per distinct
+# nonzero of the planted model at that size, Zipf exponent, values.
+LARGE = {
+    "amazon": {"name": "amazon-shaped", "dims": AMAZON_DIMS, "nnz": AMAZON_NNZ,
+               "events_per_nnz": AMAZON_EVENTS_PER_NNZ, "zipf": 1.1, "log_counts": False,
+               "values": "counts"},
+    "reddit": {"name": "reddit-shaped", "dims": (8_211_298, 176_962, 8_116_559), "nnz": 4_690_000_000,
+               "events_per_nnz": 2.9, "zipf": 1.2, "log_counts": True, "values": "log(1 + count)"},
+}
 
 
-def run_amazon(args, rank, world, local):
-    """The 4,821,207 x 1,774,269 x 1,805,187 planted count tensor (Zipf(1.1)
-    popularity, about 1.74e9 nonzeros, int32 COO and FP32 values, generated on the
-    GPU), r = 25, s = 2^17, tau = 2^-17, mixed precision, the paper's setting for this
-    size: range-finder start (App. F, s_init = 1e5) and the estimated fit (Sec. 5.4,
-    2^27 stratified samples).  One step = one epoch: eta = 5 outer iterations (15 mode
-    updates) and the estimated fit, one cp_arls_lev call continuing the run.  A
-    second series with stage events gives the stage times and the sampled MTTKRP's
-    algorithmic bytes per second."""
+def run_large(args, spec, rank, world, local):
+    """A billion-nonzero planted tensor generated on the GPU (int32 COO, FP32 values):
+    the 4,821,207 x 1,774,269 x 1,805,187 counts with Zipf(1.1) popularity (about
+    1.74e9 nonzeros) or the 8,211,298 x 176,962 x 8,116,559 log(1 + count) values with
+    Zipf(1.2) popularity (about 4.69e9 nonzeros); r = 25, s = 2^17, tau = 2^-17, mixed
+    precision, the paper's setting for these sizes: range-finder start (App. F, s_init
+    = 1e5) and the estimated fit (Sec. 5.4, 2^27 stratified samples).  One step = one
+    epoch: eta = 5 outer iterations (15 mode updates) and the estimated fit, one
+    cp_arls_lev call continuing the run.  A second series with stage events gives the
+    stage times and the sampled MTTKRP's algorithmic bytes per second.  The COO is
+    dropped once the index is built; the device memory in use during the runs is
+    reported."""
     import torch
     import paper_2006_16438_gb300 as cpa
     from synth import gpu as sgpu
@@ -451,13 +463,17 @@ def run_amazon(args, rank, world, local):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     stream = torch.cuda.current_stream()
     frac = args.amazon_fraction
+    dims = spec["dims"]
     t0 = time.perf_counter()
-    idx, vals = sgpu.planted_cp_tensor_gpu(AMAZON_DIMS, RANK, events=int(AMAZON_EVENTS_PER_NNZ * AMAZON_NNZ * frac),
-                                           seed=rank, zipf_alpha=1.1)
+    idx, vals = sgpu.planted_cp_tensor_gpu(dims, RANK, events=int(spec["events_per_nnz"] * spec["nnz"] * frac),
+                                           seed=rank, zipf_alpha=spec["zipf"], log_counts=spec["log_counts"])
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     gen_s = time.perf_counter() - t0
-    index = cpa.cpa_index_build(AMAZON_DIMS, device_tensors=(idx, vals))
+    t0 = time.perf_counter()
+    index = cpa.cpa_index_build(dims, device_tensors=(idx, vals))
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
     nnz = int(vals.numel())
     del idx, vals
     torch.cuda.synchronize()
@@ -480,6 +496,8 @@ def run_amazon(args, rank, world, local):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    free_b, total_b = torch.cuda.mem_get_info()
     clocks = ClockSampler(local)
     clocks.start()
     if world > 1:
@@ -504,19 +522,24 @@ def run_amazon(args, rank, world, local):
     # fused probe + KRP + MTTKRP bytes (b_f = 4, values FP32): per kept sample its key,
     # weight and probe (32 B) and d = 2 factor rows; per sampled nonzero i_k and value
     mk_bytes = st["sbar_total"] * (32 + 2 * RANK * 4) + st["nnz_sampled_total"] * 8 + \
-        sum(AMAZON_DIMS) * RANK * 4 * ETA
+        sum(dims) * RANK * 4 * ETA
     mk_ms = st["stage_ms"][2]
     mk_gbs = mk_bytes / (mk_ms / 1000.0) / 1e9 if mk_ms > 0 else None
+    nfib = [index.nfib(k) for k in range(3)]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 (factors, Grams, sampled products; FP64 factorisations)", "data": "synthetic",
-        "config": {"workload": f"amazon-shaped 4821207x1774269x1805187 planted counts, {nnz} nnz, r=25, s=2^17, "
-                               "tau=2^-17, mixed precision, range-finder start, estimated fit 2^27",
+        "config": {"workload": f"{spec['name']} {'x'.join(str(n) for n in dims)} planted {spec['values']}, "
+                               f"{nnz} nnz, r=25, s=2^17, tau=2^-17, mixed precision, range-finder start, "
+                               "estimated fit 2^27",
                    "step": "1 epoch = 5 outer iterations x 3 mode updates + estimated fit",
-                   "l2": "inputs far larger than L2 (about 40 GB of index)",
+                   "l2": f"inputs far larger than L2 ({index.device_bytes() / 1e9:.0f} GB of index)",
                    "parallelism": f"{world} independent replicas" if world > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "kernel": ("sampled MTTKRP (k_slab_prep/light/heavy, row slabs)" if os.environ.get("CPA_MTTKRP_SLAB_BYTES", "0") not in ("", "0") else "sampled MTTKRP (k_tnsr_mttkrp + k_tnsr_heavy, one pass, fibre pieces)"),
+        "roofline": {"bound": "hbm", "kernel": ("sampled MTTKRP (k_slab_prep/light/heavy, row slabs)"
+                                                if os.environ.get("CPA_MTTKRP_SLAB_BYTES", "0") not in ("", "0")
+                                                else "sampled MTTKRP (k_tnsr_mttkrp + k_tnsr_heavy, one pass, "
+                                                     "fibre pieces)"),
                      "achieved": mk_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": (mk_gbs / peaks["hbm_gbs"]) if mk_gbs else None, "traffic": None,
                      "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
@@ -524,7 +547,9 @@ def run_amazon(args, rank, world, local):
         "stages_ms_per_update": {nm: float(st["stage_ms"][i] / n_up) for i, nm in enumerate(STAGES)},
         "nnz_sampled_per_update": st["nnz_sampled_total"] / n_up,
         "estimated_fit": prof.fit,
-        "generate_s": gen_s,
+        "memory": {"index_bytes": index.device_bytes(), "fibres_per_mode": nfib,
+                   "device_bytes_in_use": total_b - free_b, "device_bytes_total": total_b},
+        "generate_s": gen_s, "index_build_s": build_s,
         "clocks": clk,
         "gpu_launches": launches,
         "e2e": None, "cpu_baseline": None,

@@ -69,7 +69,7 @@ extern "C" {
 /* Sparse tensor in coordinate format (Section 5.3: (d+2) nnz storage).
  *   order      number of modes D = d + 1, 2 <= D <= 8
  *   dims       host array of D mode sizes, each in [1, 2^31 - 1]
- *   nnz        number of stored nonzeros, 0 <= nnz < 2^40
+ *   nnz        number of stored nonzeros, 0 <= nnz < 2^35
  *   idx        host array of D pointers; idx[m][e] (int32) is the mode-m index of
  *              nonzero e.  The pointed-to arrays are device memory if on_device,
  *              host memory otherwise.
@@ -184,7 +184,12 @@ const char* cpa_strerror(int code);
  * linearized indices ... for every mode", D extra words per nonzero) on the GPU:
  * for every mode k the nonzeros are sorted by (other-mode multi-index, i_k), so the
  * fibre X(:, key) of every key is one contiguous run that a sampled key finds by
- * one probe.  Values are stored in the COO's dtype.
+ * one probe.  Values are stored in the COO's dtype, fibre offsets as 32-bit words
+ * (with the few fibres where the offsets pass a multiple of 2^32 kept aside).  The
+ * build works in segments of at most 2^29 nonzeros by default (ranges of the
+ * other mode of highest number; CPA_INDEX_SEGMENT_NNZ in the environment sets the
+ * size), so its scratch is about 44 bytes per nonzero of a segment on top of the
+ * index itself (about 8 bytes per nonzero and 12 per fibre, per mode).
  *   coo    input tensor (host or device, see cpa_coo)
  *   stream cudaStream_t
  *   out    receives the new index (host pointer to an opaque handle)
@@ -199,6 +204,10 @@ int cpa_index_free(cpa_index* index);
  * NULL), nnz, and the number of distinct fibres F_k of mode `mode` (may be NULL). */
 int cpa_index_info(const cpa_index* index, int32_t mode, int32_t* order, int64_t* dims,
                    int64_t* nnz, int64_t* nfib);
+
+/* Device memory held by an index, in bytes (all modes: permuted streams, fibre
+ * tables, directories, hash tables). */
+int cpa_index_device_bytes(const cpa_index* index, int64_t* bytes);
 
 /* Copies the fibre index of one mode to DEVICE buffers: keys[F_k] (linear keys of
  * Eq. 2.2, ascending), off[F_k + 1] (start of each fibre), ik[nnz] (mode index of

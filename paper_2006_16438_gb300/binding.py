@@ -45,7 +45,7 @@ EXPORTED = [
     "cpa_index_export", "cp_arls_lev", "cp_arls_lev_coo", "cpa_philox4x64", "cpa_leverage",
     "cpa_cdf", "cpa_skrp_lev", "cpa_sampled_mttkrp", "cpa_solve", "cpa_fit", "cpa_leverage_noalloc",
     "cpa_mode_update", "cp_als", "cpa_batch_create", "cpa_batch_run", "cpa_batch_info", "cpa_batch_free",
-    "cpa_fit_sample", "cpa_fit_estimate", "cpa_rrf_init",
+    "cpa_fit_sample", "cpa_fit_estimate", "cpa_rrf_init", "cpa_index_device_bytes",
 ]
 
 
@@ -118,6 +118,7 @@ def _declare(lib):
         "cpa_index_build": ([P, P, P], I32),
         "cpa_index_free": ([P], I32),
         "cpa_index_info": ([P, I32, P, P, P, P], I32),
+        "cpa_index_device_bytes": ([P, P], I32),
         "cpa_index_export": ([P, I32, P, P, P, P, P], I32),
         "cp_arls_lev": ([P, P, P, P, I32, P, P], I32),
         "cp_arls_lev_coo": ([P, P, P, P, I32, P, P], I32),
@@ -198,6 +199,12 @@ class Index:
     def nfib(self, k):
         n = C.c_int64(0)
         _check(_lib().cpa_index_info(self.h, k, None, None, None, C.byref(n)), "cpa_index_info")
+        return n.value
+
+    def device_bytes(self):
+        """Device memory the index holds (bytes)."""
+        n = C.c_int64(0)
+        _check(_lib().cpa_index_device_bytes(self.h, C.byref(n)), "cpa_index_device_bytes")
         return n.value
 
     def free(self):

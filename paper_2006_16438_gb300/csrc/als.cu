@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(kThreads) k_exact_mttkrp(FibreIndex<VT> X, Key
       FT v_l = FT(0);
       if (p0 + lane < e) {
         ik_l = X.ik[p0 + lane];
-        v_l = (FT)X.val[p0 + lane];
+        v_l = (FT)X.value(p0 + lane);
       }
       const int nb = (int)(e - p0 < 32 ? e - p0 : 32);
       for (int q2 = 0; q2 < nb; ++q2) {
@@ -107,15 +107,13 @@ int exact_mttkrp(const cpa_index* X, int k, const FactorPtrs& F, int r, FT* M, c
   const auto& mode = X->mode[k];
   if (mode.nfib <= 0) return CPA_OK;
   const unsigned grid = grid_of(mode.nfib * 32);
-  if (X->val_dtype == CPA_F32) {
-    const FibreIndex<float> fx = fibre_view<float>(X, k);
-    if (r <= 32) k_exact_mttkrp<FT, float, 1><<<grid, kThreads, 0, st>>>(fx, mode.L, F, r, M);
-    else k_exact_mttkrp<FT, float, 2><<<grid, kThreads, 0, st>>>(fx, mode.L, F, r, M);
-  } else {
-    const FibreIndex<double> fx = fibre_view<double>(X, k);
-    if (r <= 32) k_exact_mttkrp<FT, double, 1><<<grid, kThreads, 0, st>>>(fx, mode.L, F, r, M);
-    else k_exact_mttkrp<FT, double, 2><<<grid, kThreads, 0, st>>>(fx, mode.L, F, r, M);
-  }
+  with_value_type(X, [&](auto tag) {
+    using VT = decltype(tag);
+    const FibreIndex<VT> fx = fibre_view<VT>(X, k);
+    if (r <= 32) k_exact_mttkrp<FT, VT, 1><<<grid, kThreads, 0, st>>>(fx, mode.L, F, r, M);
+    else k_exact_mttkrp<FT, VT, 2><<<grid, kThreads, 0, st>>>(fx, mode.L, F, r, M);
+    return 0;
+  });
   CPA_LAUNCH_CHECK();
   return CPA_OK;
 }

@@ -947,6 +947,12 @@ int cpa_index_info(const cpa_index* X, int32_t mode, int32_t* order, int64_t* di
   return CPA_OK;
 }
 
+int cpa_index_device_bytes(const cpa_index* X, int64_t* bytes) {
+  if (!X || !bytes) return CPA_ERR_ARG;
+  *bytes = (int64_t)X->device_bytes;
+  return CPA_OK;
+}
+
 int cpa_index_export(const cpa_index* X, int32_t mode, uint64_t* keys, uint64_t* off, int32_t* ik,
                      void* val, void* stream) {
   return index_export(X, mode, keys, off, ik, val, (cudaStream_t)stream);

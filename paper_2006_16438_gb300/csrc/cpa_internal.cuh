@@ -2,12 +2,34 @@
 #pragma once
 
 #include <mutex>
+#include <type_traits>
 
 #include "cpa_common.cuh"
 
 namespace cpa {
 struct Plan;
 void plan_free(Plan* p);
+}  // namespace cpa
+
+namespace cpa {
+// Fibre offsets stored as their low `shift` bits (32 unless a test asks for fewer).
+// Offsets ascend with the fibre number, so the high part of off[f] is the number of
+// multiples of 2^shift that the offsets have passed by fibre f: wrap[w] is the first
+// fibre whose offset is >= (w + 1) 2^shift.  The builder accepts nnz < 8 * 2^shift,
+// so there are at most seven.
+constexpr int kMaxWraps = 7;
+struct OffView {
+  const uint32_t* lo = nullptr;  // F_k + 1 entries
+  int shift = 32;
+  int nwrap = 0;
+  int64_t wrap[kMaxWraps] = {};
+  __host__ __device__ __forceinline__ uint64_t operator[](int64_t f) const {
+    uint64_t hi = 0;
+#pragma unroll
+    for (int w = 0; w < kMaxWraps; ++w) hi += (w < nwrap && f >= wrap[w]) ? 1ull : 0ull;  // static indices
+    return (hi << shift) | (uint64_t)lo[f];
+  }
+};
 }  // namespace cpa
 
 // Opaque index of the C ABI (Section 5.3 fibre index, one per mode).
@@ -21,7 +43,10 @@ struct cpa_index {
     cpa::KeyLayout L;           // packed layout of the other modes
     int64_t nfib = 0;           // F_k
     uint64_t* keys = nullptr;   // F_k packed keys, ascending
-    uint64_t* off = nullptr;    // F_k + 1 offsets into ik/val
+    uint32_t* off = nullptr;    // F_k + 1 offsets into ik/val, low off_shift bits
+    int off_shift = 32;
+    int nwrap = 0;              // high parts: see cpa::OffView
+    int64_t wrap[cpa::kMaxWraps] = {};
     int32_t* ik = nullptr;      // nnz mode-k indices, fibre order (ascending within a fibre)
     void* val = nullptr;        // nnz values (float or double)
     uint64_t* dir = nullptr;    // (1 << dbits) + 1 bucket starts over the top key bits
@@ -31,7 +56,12 @@ struct cpa_index {
     ulonglong2* htab = nullptr;
     int hbits = 0;
   } mode[cpa::kMaxOrder];
+  // FP32 values stored as 16-bit codes into vtab (ascending distinct values, nvtab <=
+  // 65,536) instead of floats; null: values in val_dtype
+  float* vtab = nullptr;
+  int nvtab = 0;
   std::vector<void*> allocations;
+  size_t device_bytes = 0;  // sum of the sizes of `allocations`
   // cached workspace + CUDA graph of one outer iteration (see api.cu)
   cpa::Plan* plan = nullptr;
   std::mutex plan_mu;
@@ -46,11 +76,23 @@ __host__ __device__ __forceinline__ uint64_t fibre_slot(uint64_t key, int hbits)
   return (key * 0x9E3779B97F4A7C15ull) >> (64 - hbits);
 }
 
-// Device view of one mode of the index, passed by value to kernels.
+// Arithmetic type of a stored value: the value itself, or the float a 16-bit code
+// stands for.
+template <class VT>
+struct ValueOf {
+  using type = VT;
+};
+template <>
+struct ValueOf<uint16_t> {
+  using type = float;
+};
+
+// Device view of one mode of the index, passed by value to kernels.  VT is the
+// stored value type: float, double, or uint16_t (codes into vtab).
 template <class VT>
 struct FibreIndex {
   const uint64_t* keys;
-  const uint64_t* off;
+  OffView off;  // off[f], f <= nfib, as 64-bit offsets
   const int32_t* ik;
   const VT* val;
   const uint64_t* dir;
@@ -59,6 +101,18 @@ struct FibreIndex {
   int dbits;
   const ulonglong2* htab;  // null: probe through the directory
   int hbits;
+  const float* vtab;  // values of the codes (VT = uint16_t)
+
+  // Value of the nonzero at stream position e.
+  __device__ __forceinline__ typename ValueOf<VT>::type value(uint64_t e) const {
+    if constexpr (std::is_same<VT, uint16_t>::value) return vtab[val[e]];
+    else return val[e];
+  }
+  // The same with a streaming (evict-first) load of the stored value.
+  __device__ __forceinline__ typename ValueOf<VT>::type value_stream(uint64_t e) const {
+    if constexpr (std::is_same<VT, uint16_t>::value) return vtab[__ldcs(val + e)];
+    else return __ldcs(val + e);
+  }
 
   // Fibre [*lo, *hi) of a packed key; empty range if the key has no nonzeros.
   // With the hash table a probe is one 16-byte record (key, lo << 24 | len) per slot
@@ -95,11 +149,29 @@ struct FibreIndex {
   }
 };
 
+inline OffView off_view(const cpa_index* X, int k) {
+  const auto& M = X->mode[k];
+  OffView o;
+  o.lo = M.off;
+  o.shift = M.off_shift;
+  o.nwrap = M.nwrap;
+  for (int w = 0; w < kMaxWraps; ++w) o.wrap[w] = M.wrap[w];
+  return o;
+}
+
 template <class VT>
 inline FibreIndex<VT> fibre_view(const cpa_index* X, int k) {
   const auto& M = X->mode[k];
-  return FibreIndex<VT>{M.keys, M.off, M.ik, reinterpret_cast<const VT*>(M.val), M.dir,
-                        M.nfib, M.dshift, M.dbits, M.htab, M.hbits};
+  return FibreIndex<VT>{M.keys, off_view(X, k), M.ik, reinterpret_cast<const VT*>(M.val), M.dir,
+                        M.nfib, M.dshift, M.dbits, M.htab, M.hbits, X->vtab};
+}
+
+// Calls fn with a value of the index's stored value type (uint16_t for coded values).
+template <class Fn>
+inline int with_value_type(const cpa_index* X, Fn&& fn) {
+  if (X->vtab) return fn(uint16_t());
+  if (X->val_dtype == CPA_F32) return fn(float());
+  return fn(double());
 }
 
 // index.cu

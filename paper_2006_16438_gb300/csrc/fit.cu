@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(kThreads) k_fit_inner(FibreIndex<VT> X, KeyLay
       FT v_l = FT(0);
       if (p0 + lane < e) {
         ik_l = X.ik[p0 + lane];
-        v_l = (FT)X.val[p0 + lane];
+        v_l = (FT)X.value(p0 + lane);
       }
       const int nb = (int)(e - p0 < 32 ? e - p0 : 32);
       for (int q2 = 0; q2 < nb; ++q2) {
@@ -113,15 +113,13 @@ int fit_enqueue(const cpa_index* X, const FactorPtrs& F, const double* lambda, i
   const int sms = num_sms();
   const int64_t want = ceil_div(X->mode[kf].nfib, kThreads / 32);
   const unsigned grid = (unsigned)(want < sms * 8 ? (want > 0 ? want : 1) : sms * 8);
-  if (X->val_dtype == CPA_F32) {
-    const FibreIndex<float> fx = fibre_view<float>(X, kf);
-    if (r <= 32) k_fit_inner<FT, float, 1><<<grid, kThreads, 0, st>>>(fx, X->mode[kf].L, F, kf, lambda, r, inner);
-    else k_fit_inner<FT, float, 2><<<grid, kThreads, 0, st>>>(fx, X->mode[kf].L, F, kf, lambda, r, inner);
-  } else {
-    const FibreIndex<double> fx = fibre_view<double>(X, kf);
-    if (r <= 32) k_fit_inner<FT, double, 1><<<grid, kThreads, 0, st>>>(fx, X->mode[kf].L, F, kf, lambda, r, inner);
-    else k_fit_inner<FT, double, 2><<<grid, kThreads, 0, st>>>(fx, X->mode[kf].L, F, kf, lambda, r, inner);
-  }
+  with_value_type(X, [&](auto tag) {
+    using VT = decltype(tag);
+    const FibreIndex<VT> fx = fibre_view<VT>(X, kf);
+    if (r <= 32) k_fit_inner<FT, VT, 1><<<grid, kThreads, 0, st>>>(fx, X->mode[kf].L, F, kf, lambda, r, inner);
+    else k_fit_inner<FT, VT, 2><<<grid, kThreads, 0, st>>>(fx, X->mode[kf].L, F, kf, lambda, r, inner);
+    return 0;
+  });
   k_fit_final<<<1, 256, 0, st>>>(grams, D, lambda, r, inner, X->norm_x2, fit_dev);
   CPA_LAUNCH_CHECK();
   return CPA_OK;
@@ -164,7 +162,7 @@ __global__ void __launch_bounds__(kDrawThreads) k_fit_draw_nz(FibreIndex<VT> X0,
   const uint64_t key = X0.keys[a];
   coords[j] = X0.ik[p];
   for (int t = 0; t < L0.d; ++t) coords[(int64_t)L0.mode[t] * S + j] = (int32_t)L0.get(key, t);
-  xs[j] = (double)X0.val[p];
+  xs[j] = (double)X0.value(p);
 }
 
 // Zero slot j: uniform cells until one is not a nonzero.
@@ -342,7 +340,7 @@ int fit_sample_draw(const cpa_index* X, int64_t s_fit, double alpha, uint64_t se
     CPA_LAUNCH_CHECK();
     return CPA_OK;
   };
-  int rc = X->val_dtype == CPA_F32 ? draw(float()) : draw(double());
+  int rc = with_value_type(X, draw);
   int h_status = 0;
   unsigned long long h_att = 0;
   if (rc == CPA_OK) {

@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_tnsr_mttkrp(FibreIndex<VT> X, F
         FT xl = FT(0);
         if (lane < nb) {
           ikl = X.ik[oq + g + lane];
-          xl = (FT)X.val[oq + g + lane];
+          xl = (FT)X.value(oq + g + lane);
         }
         for (int q2 = 0; q2 < nb; ++q2) {
           const int32_t ik = __shfl_sync(0xffffffffu, ikl, q2);
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(kThreads) k_tnsr_heavy(FibreIndex<VT> X, Facto
     FT xl = FT(0);
     if (g + lane < len) {
       ikl = X.ik[lo + g + lane];
-      xl = (FT)X.val[lo + g + lane];
+      xl = (FT)X.value(lo + g + lane);
     }
     for (; g < len; g += kThreads) {
       const int nb = len - g < 32 ? (int)(len - g) : 32;
@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(kThreads) k_tnsr_heavy(FibreIndex<VT> X, Facto
       FT xn = FT(0);
       if (gn + lane < len) {
         ikn = X.ik[lo + gn + lane];
-        xn = (FT)X.val[lo + gn + lane];
+        xn = (FT)X.value(lo + gn + lane);
       }
       for (int q2 = 0; q2 < nb; ++q2) {
         const int32_t ik = __shfl_sync(0xffffffffu, ikl, q2);
@@ -429,7 +429,7 @@ __global__ void __launch_bounds__(kThreads) k_slab_light(FibreIndex<VT> X, int r
         FT xl = FT(0);
         if (lane < nb) {
           ikl = __ldcs(X.ik + sq + g + lane);
-          xl = (FT)__ldcs(X.val + sq + g + lane);
+          xl = (FT)X.value_stream(sq + g + lane);
         }
         for (int q2 = 0; q2 < nb; ++q2) {
           const int32_t ik = __shfl_sync(0xffffffffu, ikl, q2);
@@ -476,7 +476,7 @@ __global__ void __launch_bounds__(kThreads) k_slab_heavy(FibreIndex<VT> X, int r
     FT xl = FT(0);
     if (g + lane < len) {
       ikl = __ldcs(X.ik + start + g + lane);
-      xl = (FT)__ldcs(X.val + start + g + lane);
+      xl = (FT)X.value_stream(start + g + lane);
     }
     for (; g < len; g += kThreads) {
       const int nb = len - g < 32 ? (int)(len - g) : 32;
@@ -485,7 +485,7 @@ __global__ void __launch_bounds__(kThreads) k_slab_heavy(FibreIndex<VT> X, int r
       FT xn = FT(0);
       if (gn + lane < len) {
         ikn = __ldcs(X.ik + start + gn + lane);
-        xn = (FT)__ldcs(X.val + start + gn + lane);
+        xn = (FT)X.value_stream(start + gn + lane);
       }
       for (int q2 = 0; q2 < nb; ++q2) {
         const int32_t ik = __shfl_sync(0xffffffffu, ikl, q2);
@@ -881,13 +881,11 @@ int sampled_mttkrp(const cpa_index* X, int k, const FactorPtrs& F, int r, const 
   int* gstatus = B.status ? B.status : reinterpret_cast<int*>(B.ctr + kMttkrpCounters - 1);
   const int P = B.U ? mttkrp_slabs(X->dims[k], r, (int)sizeof(FT)) : 1;
   auto mttkrp = [&](cudaStream_t s2) {
-    if (P > 1)
-      return X->val_dtype == CPA_F32
-                 ? launch_mttkrp_slabs<FT, float>(X, k, F, r, idx_packed, wgt, sbar, M, B, P, s2)
-                 : launch_mttkrp_slabs<FT, double>(X, k, F, r, idx_packed, wgt, sbar, M, B, P, s2);
-    return X->val_dtype == CPA_F32
-               ? launch_mttkrp<FT, float>(X, k, F, r, idx_packed, wgt, sbar, M, B, s2)
-               : launch_mttkrp<FT, double>(X, k, F, r, idx_packed, wgt, sbar, M, B, s2);
+    return with_value_type(X, [&](auto tag) {
+      using VT = decltype(tag);
+      if (P > 1) return launch_mttkrp_slabs<FT, VT>(X, k, F, r, idx_packed, wgt, sbar, M, B, P, s2);
+      return launch_mttkrp<FT, VT>(X, k, F, r, idx_packed, wgt, sbar, M, B, s2);
+    });
   };
   const bool timed = ev && ev[0];
   if (fork && fork->aux && !timed) {

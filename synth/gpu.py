@@ -35,14 +35,22 @@ def _columns_gpu(torch, gen, n, rank, alpha, device):
     return C
 
 
-def _draw_by_component(torch, gen, W, comp, device):
-    """Index per event from column comp[e] of the weight matrix W (rows x rank):
-    inverse CDF on the per-column cumulative sums placed at offsets j (column j's CDF
-    occupies [j, j + 1]), one search for all events."""
+def _flat_cdf(torch, W, device):
+    """Per-column cumulative sums of W (rows x rank) placed at offsets j (column j's
+    CDF occupies [j, j + 1]), as one ascending vector."""
     rows, rank = W.shape
     cdf = torch.cumsum(W, dim=0)
     cdf = cdf / cdf[-1:, :].clamp_min(1e-300)
-    flat = (cdf + torch.arange(rank, device=device, dtype=torch.float64)[None, :]).t().contiguous().view(-1)
+    return (cdf + torch.arange(rank, device=device, dtype=torch.float64)[None, :]).t().contiguous().view(-1)
+
+
+def _draw_by_component(torch, gen, W, comp, device, flat=None):
+    """Index per event from column comp[e] of the weight matrix W (rows x rank):
+    inverse CDF on the flat per-column CDF (computed here unless given), one search
+    for all events."""
+    rows, rank = W.shape
+    if flat is None:
+        flat = _flat_cdf(torch, W, device)
     u = torch.rand(comp.shape[0], device=device, dtype=torch.float64, generator=gen)
     pos = torch.searchsorted(flat, comp.to(torch.float64) + u, right=True)
     idx = pos - comp * rows
@@ -79,6 +87,7 @@ def planted_cp_tensor_gpu(dims, rank, *, events, seed=0, zipf_alpha=1.1, log_cou
     lo = torch.where(starts[:, None] > 0, csum[(starts - 1).clamp_min(0)], torch.zeros_like(hi))
     mass = (hi - lo) * w[None, :]  # nslices x rank
     per_slice = g_host.multinomial(int(events), (mass.sum(dim=1) / mass.sum()).cpu().numpy())
+    flats = [None] + [_flat_cdf(torch, cols[m], device) for m in range(1, d)]  # same for every slice
     out_idx = [[] for _ in range(d)]
     out_val = []
     for sl in range(nslices):
@@ -94,7 +103,7 @@ def planted_cp_tensor_gpu(dims, rank, *, events, seed=0, zipf_alpha=1.1, log_cou
         key = i0 - a
         rest = []
         for m in range(1, d):
-            im = _draw_by_component(torch, gen, cols[m], comp, device)
+            im = _draw_by_component(torch, gen, cols[m], comp, device, flats[m])
             key = key * dims[m] + im
             rest.append(im)
         uniq, cnt = torch.unique(key, sorted=True, return_counts=True)
@@ -111,6 +120,11 @@ def planted_cp_tensor_gpu(dims, rank, *, events, seed=0, zipf_alpha=1.1, log_cou
         v = cnt.to(torch.float32)
         out_val.append(torch.log1p(v) if log_counts else v)
         del comp, i0, key, rest, uniq, cnt
-    idx = [torch.cat(c) for c in out_idx]
+    del flats
+    idx = []
+    for m in range(d):  # one mode at a time, dropping its slices: peak about 1 + 1/(d + 1) tensors
+        idx.append(torch.cat(out_idx[m]))
+        out_idx[m] = None
     vals = torch.cat(out_val)
+    del out_val
     return idx, vals
