@@ -536,10 +536,9 @@ def run_large(args, spec, rank, world, local):
                    "step": "1 epoch = 5 outer iterations x 3 mode updates + estimated fit",
                    "l2": f"inputs far larger than L2 ({index.device_bytes() / 1e9:.0f} GB of index)",
                    "parallelism": f"{world} independent replicas" if world > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "kernel": ("sampled MTTKRP (k_slab_prep/light/heavy, row slabs)"
-                                                if os.environ.get("CPA_MTTKRP_SLAB_BYTES", "0") not in ("", "0")
-                                                else "sampled MTTKRP (k_tnsr_mttkrp + k_tnsr_heavy, one pass, "
-                                                     "fibre pieces)"),
+        "roofline": {"bound": "hbm", "kernel": "sampled MTTKRP (modes whose M exceeds 128 MB: row slabs, "
+                                               "k_slab_prep + k_slab_light + k_slab_heavy; the others one pass, "
+                                               "k_tnsr_mttkrp + k_tnsr_heavy)",
                      "achieved": mk_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": (mk_gbs / peaks["hbm_gbs"]) if mk_gbs else None, "traffic": None,
                      "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",

@@ -15,13 +15,13 @@
 //    are taken from a counter; fibres longer than kHeavy are listed and spread over
 //    the warps of one block each by k_tnsr_heavy.  The KRP rows are never written.
 //
-// Optionally (CPA_MTTKRP_SLAB_BYTES = bytes per slab; off by default, since one pass
-// with the piece list measured faster on the 1.75e9-nonzero tensor), M's rows are
-// split into P slabs.  k_slab_prep probes every sample's fibre once, stores u_j and,
-// since the nonzeros of a fibre are sorted by i_k, where each slab's rows start in the
-// fibre; then for p = 0..P-1, k_slab_light and k_slab_heavy add the nonzeros of slab p
-// only.  Every nonzero is read once; the additions of one pass hit one slab of M,
-// small enough to stay in L2, instead of scattering over the whole of it in DRAM.
+// When M is larger than one slab (128 MB, about the L2 size; CPA_MTTKRP_SLAB_BYTES
+// sets it, 0 turns slabs off), M's rows are split into P slabs.  k_slab_prep probes
+// every sample's fibre once, stores u_j and, since the nonzeros of a fibre are sorted
+// by i_k, where each slab's rows start in the fibre; then for p = 0..P-1, k_slab_light
+// and k_slab_heavy add the nonzeros of slab p only.  Every nonzero is read once; the
+// additions of one pass hit one slab of M, which stays in L2, instead of
+// read-modify-writes of rows scattered over the whole of M in DRAM.
 #include <stdlib.h>
 
 #include "mttkrp.cuh"
@@ -837,9 +837,12 @@ size_t mttkrp_slab_bytes() {
   const char* e = getenv("CPA_MTTKRP_SLAB_BYTES");
   if (e) {
     const long long v = atoll(e);
-    if (v > 0) return (size_t)v;
+    return v > 0 ? (size_t)v : 0;  // 0: one pass whatever M's size
   }
-  return 0;  // off: at 1.75e9 nonzeros one pass with the piece list is faster (1.30 vs 1.66 ms per update)
+  // About the L2 size.  Measured per update: 1.75e9 nonzeros (M of 480 and 180 MB)
+  // 1.29 ms in one pass, 1.34 with 64 MB and 1.18 with 128 MB slabs; 4.68e9 nonzeros
+  // (M of 820 MB) 5.95, 4.77 and 4.48 ms.
+  return size_t(128) << 20;
 }
 
 int mttkrp_slabs(int64_t nk, int r, int ftb) {

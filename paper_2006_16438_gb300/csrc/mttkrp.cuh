@@ -31,7 +31,7 @@ struct MttkrpBuffers {
 constexpr int kMttkrpCounters = 4 + 3 * 32;
 constexpr int kSlabMax = 31;  // most row slabs of one M
 
-// Bytes of M per row slab (CPA_MTTKRP_SLAB_BYTES; 0 = no slabs, the default): M
+// Bytes of M per row slab (128 MB, or CPA_MTTKRP_SLAB_BYTES; 0 = no slabs): M
 // larger than this is accumulated slab by slab, the additions of a pass confined to
 // one slab of rows.
 size_t mttkrp_slab_bytes();
