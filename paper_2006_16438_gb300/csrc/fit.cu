@@ -216,7 +216,8 @@ __global__ void __launch_bounds__(kDrawThreads) k_fit_draw_zero(FibreIndex<VT> X
 
 // Per block: sum over its samples of phi_j (m_j - x_j)^2, eight lanes per sample
 // (lane g of a group takes columns g, g + 8, ...), model value accumulated in FT.
-template <class FT, int CPL>
+// MD >= D bounds the unrolled per-mode loops (registers for 2 MD coordinates).
+template <class FT, int CPL, int MD>
 __global__ void __launch_bounds__(kEstThreads) k_fit_est(const int32_t* __restrict__ coords, int64_t stride,
                                                          const double* __restrict__ xs, int64_t S, int64_t s_nz,
                                                          double phi_nz, double phi_z, FactorPtrs F,
@@ -237,29 +238,52 @@ __global__ void __launch_bounds__(kEstThreads) k_fit_est(const int32_t* __restri
     lam[q] = c < r ? (FT)lambda[c] : FT(0);
   }
   double acc = 0.0;
-  for (int64_t base = base0; base < S; base += ngroups) {
-    const int64_t j = base + sub;
-    const bool live = j < S;
-    FT v[CPL];
+  // two samples per group and iteration (j and j + ngroups), all coordinate loads
+  // issued before the row loads; each lane still adds its samples in ascending j
+  for (int64_t base = base0; base < S; base += 2 * ngroups) {
+    const int64_t jj[2] = {base + sub, base + ngroups + sub};
+    const bool lv[2] = {jj[0] < S, jj[1] < S};
+    int32_t ci[2][MD];
 #pragma unroll
-    for (int q = 0; q < CPL; ++q) v[q] = lam[q];
-    if (live) {
-      for (int m = 0; m < D; ++m) {
-        const FT* A = static_cast<const FT*>(F.A[m]) + (int64_t)coords[(int64_t)m * stride + j] * r;
+    for (int m = 0; m < MD; ++m) {
+      if (m < D) {
 #pragma unroll
-        for (int q = 0; q < CPL; ++q) {
-          const int c = g + kEstLanes * q;
-          if (c < r) v[q] *= A[c];
+        for (int h = 0; h < 2; ++h) ci[h][m] = lv[h] ? __ldg(coords + (int64_t)m * stride + jj[h]) : 0;
+      }
+    }
+    double xv[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) xv[h] = (lv[h] && g == 0) ? xs[jj[h]] : 0.0;
+    FT v[2][CPL];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) v[h][q] = lam[q];
+#pragma unroll
+    for (int m = 0; m < MD; ++m) {
+      if (m < D) {
+        const FT* Am = static_cast<const FT*>(F.A[m]);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const FT* A = Am + (int64_t)ci[h][m] * r;  // row 0 for a sample past the end (result unused)
+#pragma unroll
+          for (int q = 0; q < CPL; ++q) {
+            const int c = g + kEstLanes * q;
+            if (c < r) v[h][q] *= A[c];
+          }
         }
       }
     }
-    FT mv = FT(0);
 #pragma unroll
-    for (int q = 0; q < CPL; ++q) mv += v[q];
-    for (int o = kEstLanes / 2; o > 0; o >>= 1) mv += __shfl_xor_sync(0xffffffffu, mv, o);
-    if (live && g == 0) {
-      const double res = (double)mv - xs[j];
-      acc += (j < s_nz ? phi_nz : phi_z) * res * res;
+    for (int h = 0; h < 2; ++h) {
+      FT mv = FT(0);
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) mv += v[h][q];
+      for (int o = kEstLanes / 2; o > 0; o >>= 1) mv += __shfl_xor_sync(0xffffffffu, mv, o);
+      if (lv[h] && g == 0) {
+        const double res = (double)mv - xv[h];
+        acc += (jj[h] < s_nz ? phi_nz : phi_z) * res * res;
+      }
     }
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -441,18 +465,22 @@ int fit_estimate_enqueue(const cpa_index* X, const FitSample& S, const FactorPtr
   const int64_t n = S.s_nz + S.s_z;
   const int nb = est_blocks(n);
   const int D = X->order;
-  if (r <= 8)
-    k_fit_est<FT, 1><<<nb, kEstThreads, 0, st>>>(S.coords, S.stride, S.xs, n, S.s_nz, S.phi[0], S.phi[1], F, lambda, r, D,
-                                                 S.partial);
-  else if (r <= 16)
-    k_fit_est<FT, 2><<<nb, kEstThreads, 0, st>>>(S.coords, S.stride, S.xs, n, S.s_nz, S.phi[0], S.phi[1], F, lambda, r, D,
-                                                 S.partial);
-  else if (r <= 32)
-    k_fit_est<FT, 4><<<nb, kEstThreads, 0, st>>>(S.coords, S.stride, S.xs, n, S.s_nz, S.phi[0], S.phi[1], F, lambda, r, D,
-                                                 S.partial);
-  else
-    k_fit_est<FT, 8><<<nb, kEstThreads, 0, st>>>(S.coords, S.stride, S.xs, n, S.s_nz, S.phi[0], S.phi[1], F, lambda, r, D,
-                                                 S.partial);
+  auto launch = [&](auto cpl_tag) {
+    constexpr int CPL = decltype(cpl_tag)::value;
+    if (D <= 3)
+      k_fit_est<FT, CPL, 3><<<nb, kEstThreads, 0, st>>>(S.coords, S.stride, S.xs, n, S.s_nz, S.phi[0], S.phi[1], F,
+                                                        lambda, r, D, S.partial);
+    else if (D == 4)
+      k_fit_est<FT, CPL, 4><<<nb, kEstThreads, 0, st>>>(S.coords, S.stride, S.xs, n, S.s_nz, S.phi[0], S.phi[1], F,
+                                                        lambda, r, D, S.partial);
+    else
+      k_fit_est<FT, CPL, kMaxOrder><<<nb, kEstThreads, 0, st>>>(S.coords, S.stride, S.xs, n, S.s_nz, S.phi[0],
+                                                                S.phi[1], F, lambda, r, D, S.partial);
+  };
+  if (r <= 8) launch(std::integral_constant<int, 1>());
+  else if (r <= 16) launch(std::integral_constant<int, 2>());
+  else if (r <= 32) launch(std::integral_constant<int, 4>());
+  else launch(std::integral_constant<int, 8>());
   CPA_LAUNCH_CHECK();
   k_fit_est_final<<<1, 256, 0, st>>>(S.partial, nb, X->norm_x2, fit_dev);
   CPA_LAUNCH_CHECK();
