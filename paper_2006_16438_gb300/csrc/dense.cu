@@ -624,6 +624,70 @@ __global__ void __launch_bounds__(kRowThreads) k_lev_rows(const FT* A, int64_t n
   }
 }
 
+// FP32 rows (mixed precision, many rows): one thread per row.  The rows of a tile are
+// staged through shared memory (coalesced loads and stores), each thread holds its
+// row and its r sums in registers and reads F four columns per shared-memory load
+// (every thread the same address: a broadcast).  Each sum takes the products in the
+// order u = 0..r-1 with fused multiply-adds, as k_solve_rows does, so the results are
+// the same bit for bit.
+template <int RB>
+__global__ void __launch_bounds__(kRowThreads) k_solve_rows_f32(const float* __restrict__ M, int64_t n, int r,
+                                                                const SmallFactor* __restrict__ f,
+                                                                float* __restrict__ A, double* zero_gram) {
+  extern __shared__ __align__(16) unsigned char solve_smem[];
+  const int rp = (r + 3) & ~3;
+  const int ld = r | 1;
+  float* F = reinterpret_cast<float*>(solve_smem);  // r x rp, zero padded
+  float* T = F + r * rp;                            // kRowThreads x ld tile of rows
+  if (zero_gram && blockIdx.x == 0)
+    for (int i = threadIdx.x; i < r * r; i += blockDim.x) zero_gram[i] = 0.0;
+  for (int i = threadIdx.x; i < r * rp; i += blockDim.x) {
+    const int u = i / rp, c = i - u * rp;
+    F[i] = c < r ? (float)f->F[u * r + c] : 0.f;
+  }
+  for (int64_t row0 = (int64_t)blockIdx.x * kRowThreads; row0 < n; row0 += (int64_t)gridDim.x * kRowThreads) {
+    const int rows = (int)(n - row0 < kRowThreads ? n - row0 : kRowThreads);
+    __syncthreads();
+    for (int i = threadIdx.x; i < rows * r; i += kRowThreads) {
+      const int rr = i / r, c = i - rr * r;
+      T[rr * ld + c] = M[row0 * r + i];
+    }
+    __syncthreads();
+    if (threadIdx.x < rows) {
+      float x[RB], t[RB];
+#pragma unroll
+      for (int u = 0; u < RB; ++u) {
+        x[u] = u < r ? T[threadIdx.x * ld + u] : 0.f;
+        t[u] = 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < RB; ++u) {
+        if (u < r) {
+          const float4* Fu = reinterpret_cast<const float4*>(F + u * rp);
+#pragma unroll
+          for (int c4 = 0; c4 < RB / 4; ++c4) {
+            if (4 * c4 < r) {
+              const float4 w = Fu[c4];
+              t[4 * c4 + 0] = fmaf(x[u], w.x, t[4 * c4 + 0]);
+              t[4 * c4 + 1] = fmaf(x[u], w.y, t[4 * c4 + 1]);
+              t[4 * c4 + 2] = fmaf(x[u], w.z, t[4 * c4 + 2]);
+              t[4 * c4 + 3] = fmaf(x[u], w.w, t[4 * c4 + 3]);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < RB; ++c)  // the thread's own row of the tile
+        if (c < r) T[threadIdx.x * ld + c] = t[c];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < rows * r; i += kRowThreads) {
+      const int rr = i / r, c = i - rr * r;
+      A[row0 * r + i] = T[rr * ld + c];
+    }
+  }
+}
+
 // A = M F with F the explicit inverse (kind 2) or pseudo-inverse (kind 1) of G:
 // one thread per output element.
 template <class FT>
@@ -990,6 +1054,28 @@ int solve_rows(const FT* M, int64_t n, int r, const SmallFactor* f, FT* A, cudaS
                double* zero_gram) {
   if (r < 1 || r > kMaxRank) return CPA_ERR_ARG;
   if (n <= 0) return CPA_OK;
+  if constexpr (sizeof(FT) == 4) {
+    if (n >= kManyRows) {
+      auto bytes = [](int rr) {
+        return sizeof(float) * ((size_t)rr * ((rr + 3) & ~3) + (size_t)kRowThreads * (rr | 1));
+      };
+      static bool attr = false;
+      if (!attr) {
+        CPA_CUDA_TRY(cudaFuncSetAttribute(k_solve_rows_f32<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)bytes(kMaxRank)));
+        CPA_CUDA_TRY(cudaFuncSetAttribute(k_solve_rows_f32<kMaxRank>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)bytes(kMaxRank)));
+        attr = true;
+      }
+      const unsigned grid = grid_cap(ceil_div(n, kRowThreads), 8);
+      if (r <= 32)
+        k_solve_rows_f32<32><<<grid, kRowThreads, bytes(r), st>>>(M, n, r, f, A, zero_gram);
+      else
+        k_solve_rows_f32<kMaxRank><<<grid, kRowThreads, bytes(r), st>>>(M, n, r, f, A, zero_gram);
+      CPA_LAUNCH_CHECK();
+      return CPA_OK;
+    }
+  }
   const size_t smem = sizeof(FT) * (size_t)r * r;
   const unsigned grid = grid_cap(ceil_div(n * r, kRowThreads), 16);
   k_solve_rows<FT><<<grid, kRowThreads, smem, st>>>(M, n, r, f, A, zero_gram);

@@ -208,3 +208,24 @@ def test_mode_update_mixed_tensor_core_gram(monkeypatch, r):
         A, _ = oracle.solve(G, M)
         An, lam = oracle.normalize(A)
         assert relerr(fs[k].cpu().numpy(), An) < 2e-4
+
+
+@pytest.mark.parametrize("r", [8, 25, 40, 64])
+def test_mode_update_mixed_many_rows_within_2e4(r):
+    """Mixed precision on a mode of 70,000 rows: the solve A = M G^-1 runs one
+    thread per row (k_solve_rows_f32, the row and its sums in registers); the new
+    factor within 2e-4 of the FP64 oracle's solve on the GPU's own rows."""
+    dims = (70000, 40, 30)
+    coo = synth.random_sparse_tensor(dims, 300000, seed=20 + r)
+    facs = synth.gaussian_factors(dims, r, seed=r + 5)
+    gi = cpa.cpa_index_build(coo)
+    oi = oracle.Index(coo)
+    fs = [torch.from_numpy(a).cuda() for a in facs]
+    got = cpa.cpa_mode_update(gi, fs, 0, rank=r, samples=3000, tau=1.0, seed=6, it=0, precision=binding.MIXED)
+    idx = got["idx"].cpu().numpy().astype(np.uint64)
+    wgt = got["wgt"].cpu().numpy()
+    M, G, _ = oracle.sampled_mttkrp(oi, 0, facs, idx, wgt)
+    A, _ = oracle.solve(G, M)
+    An, lam = oracle.normalize(A)
+    assert relerr(fs[0].cpu().numpy(), An) < 2e-4
+    assert relerr(got["lam"].cpu().numpy(), lam) < 2e-4
