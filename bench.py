@@ -758,28 +758,38 @@ def equal_fit(cpa, coo, seed, stream, restarts, max_epochs, fixed_epochs):
 
 
 def e2e(cpa, coo, init, args):
-    """Same metric through cp_arls_lev_coo with HOST buffers: each step copies the
-    COO tensor and the factors in, builds the index, runs one epoch and copies the
-    factors, lambda and fit back."""
+    """Same metric through cp_arls_lev_coo with HOST buffers in pinned memory (filled
+    once, outside the timed region): each step copies the COO tensor and the factors
+    in, builds the index, runs one epoch and copies the factors, lambda and fit back
+    (the factors into the same pinned arrays)."""
     import torch
-    idx_bytes = sum(i.nbytes for i in coo.idx) + coo.vals.astype(np.float64).nbytes
-    fac_bytes = sum(a.nbytes for a in init)
+    import synth
+    keep = []
+
+    def pinned(a):
+        t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        keep.append(t)
+        return t.numpy()
+
+    pcoo = synth.Coo(coo.dims, [pinned(np.asarray(i, dtype=np.int32)) for i in coo.idx],
+                     pinned(np.asarray(coo.vals, dtype=np.float64)))
+    fs = [pinned(np.asarray(a, dtype=np.float64)) for a in init]
+    idx_bytes = sum(i.nbytes for i in pcoo.idx) + pcoo.vals.nbytes
+    fac_bytes = sum(a.nbytes for a in fs)
     times = []
-    fs = [a.copy() for a in init]
     for i in range(max(1, min(3, args.steps)) + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        res = cpa.cp_arls_lev_coo(coo, fs, rank=RANK, samples=SAMPLES, tau=2.0 ** -TAU_EXP, iters=ETA,
-                                  seed=0, iter_offset=ETA * i)
+        cpa.cp_arls_lev_coo(pcoo, fs, rank=RANK, samples=SAMPLES, tau=2.0 ** -TAU_EXP, iters=ETA,
+                            seed=0, iter_offset=ETA * i, inplace=True)
         t1 = time.perf_counter()
-        fs = res.factors
         if i > 0:
             times.append(t1 - t0)
     per = sum(times) / len(times)
     return {"value": ETA * len(coo.dims) / per, "unit": UNIT,
             "h2d_bytes_per_step": int(idx_bytes + fac_bytes),
             "d2h_bytes_per_step": int(fac_bytes + 8 * RANK + 8),
-            "note": "index build included in every step"}
+            "note": "index build included in every step; inputs and factors in pinned host memory"}
 
 
 if __name__ == "__main__":

@@ -403,14 +403,21 @@ class Batch:
 
 
 def cp_arls_lev_coo(coo, factors, *, rank, samples, tau=1.0, iters=10, seed=0, fit_mode=FIT_EXACT,
-                    dtype=np.float64, **kw) -> Result:
-    """Host COO + host factors in, host results out (index built and freed inside)."""
+                    dtype=np.float64, inplace=False, **kw) -> Result:
+    """Host COO + host factors in, host results out (index built and freed inside).
+    inplace=True updates the caller's factor arrays (C-contiguous float64, e.g. views
+    of pinned memory) instead of copies."""
     _torch()
     s = coo_from_host(coo, dtype)
     o = default_options(rank=rank, samples=int(samples), tau=float(tau), iters=int(iters), seed=int(seed),
                         fit_mode=int(fit_mode), **kw)
     o.stream = _stream()
-    fs = [np.ascontiguousarray(f, dtype=np.float64).copy() for f in factors]
+    if inplace:
+        fs = list(factors)
+        if not all(isinstance(f, np.ndarray) and f.dtype == np.float64 and f.flags.c_contiguous for f in fs):
+            raise ValueError("inplace factors must be C-contiguous float64 numpy arrays")
+    else:
+        fs = [np.ascontiguousarray(f, dtype=np.float64).copy() for f in factors]
     lam = np.zeros(rank)
     fit = C.c_double(0.0)
     stats = Stats()
