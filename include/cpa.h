@@ -180,8 +180,8 @@ void cpa_options_default(cpa_options* opt);
 /* Human-readable text of a status code (static string). */
 const char* cpa_strerror(int code);
 
-/* Builds the per-mode fibre index of Section 5.3 ("precompute and store the
- * linearized indices ... for every mode", D extra words per nonzero) on the GPU:
+/* Builds the per-mode fibre index of Section 5.3 (every mode's linear indices
+ * computed once and kept, D extra words per nonzero) on the GPU:
  * for every mode k the nonzeros are sorted by (other-mode multi-index, i_k), so the
  * fibre X(:, key) of every key is one contiguous run that a sampled key finds by
  * one probe.  Values are stored in the COO's dtype, fibre offsets as 32-bit words

@@ -1,5 +1,5 @@
-// Per-mode fibre index (Section 5.3, "precompute and store the linearized indices
-// ... for every mode"), built once per tensor on the GPU.
+// Per-mode fibre index (Section 5.3: the linear indices of every mode are computed
+// once and kept), built once per tensor on the GPU.
 //
 // For mode k every nonzero gets its packed other-mode multi-index (a 64-bit key
 // whose order is the order of the linear index of Eq. 2.2).  Nonzeros are sorted by
