@@ -48,28 +48,55 @@ __global__ void k_top_hist(const int32_t* __restrict__ itop, int64_t nnz, int sh
 }
 
 // Positions of the nonzeros whose top coordinate lies in [lo, hi), in any order (the
-// sort that follows orders them by their unique (key, i_k)).  One atomic per warp.
-__global__ void k_seg_select(const int32_t* __restrict__ itop, int64_t nnz, int64_t lo, int64_t hi,
-                             uint64_t* __restrict__ pos, int64_t cap, unsigned long long* __restrict__ cnt,
-                             int* status) {
-  const int lane = threadIdx.x & 31;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;  // a multiple of 32
-  for (int64_t e0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); e0 < nnz; e0 += stride) {
-    const int64_t e = e0 + lane;
-    bool m = false;
-    if (e < nnz) {
-      const int64_t v = itop[e];
-      m = v >= lo && v < hi;
+// sort that follows orders them by their unique (key, i_k)).  A block takes tiles of
+// kSelItems coalesced items per thread, counts the tile's matches with warp ballots,
+// and reserves the tile's output range with one atomic (one per warp contended on the
+// single counter at billions of nonzeros).
+constexpr int kSelItems = 8;
+__global__ void __launch_bounds__(256) k_seg_select(const int32_t* __restrict__ itop, int64_t nnz, int64_t lo,
+                                                    int64_t hi, uint64_t* __restrict__ pos, int64_t cap,
+                                                    unsigned long long* __restrict__ cnt, int* status) {
+  __shared__ unsigned wsum[32];
+  __shared__ unsigned long long bbase;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int64_t tile = (int64_t)blockDim.x * kSelItems;
+  for (int64_t t0 = (int64_t)blockIdx.x * tile; t0 < nnz; t0 += (int64_t)gridDim.x * tile) {  // block-uniform
+    unsigned bal[kSelItems];
+    unsigned mine = 0;
+#pragma unroll
+    for (int i = 0; i < kSelItems; ++i) {
+      const int64_t e = t0 + (int64_t)i * blockDim.x + threadIdx.x;
+      bool m = false;
+      if (e < nnz) {
+        const int64_t v = itop[e];
+        m = v >= lo && v < hi;
+      }
+      bal[i] = __ballot_sync(0xffffffffu, m);
+      mine += __popc(bal[i]);
     }
-    const unsigned bal = __ballot_sync(0xffffffffu, m);
-    if (!bal) continue;
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(cnt, (unsigned long long)__popc(bal));
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (m) {
-      const int64_t at = (int64_t)base + __popc(bal & ((1u << lane) - 1u));
-      if (at < cap) pos[at] = (uint64_t)e; else set_status(status, CPA_ERR_CUDA);
+    if (lane == 0) wsum[warp] = mine;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned run = 0;
+      for (int w = 0; w < nwarps; ++w) {
+        const unsigned c = wsum[w];
+        wsum[w] = run;
+        run += c;
+      }
+      bbase = run ? atomicAdd(cnt, (unsigned long long)run) : 0ull;
     }
+    __syncthreads();
+    unsigned long long at = bbase + wsum[warp];
+#pragma unroll
+    for (int i = 0; i < kSelItems; ++i) {
+      if ((bal[i] >> lane) & 1u) {
+        const unsigned long long p = at + __popc(bal[i] & ((1u << lane) - 1u));
+        if ((int64_t)p < cap) pos[p] = (uint64_t)(t0 + (int64_t)i * blockDim.x + threadIdx.x);
+        else set_status(status, CPA_ERR_CUDA);
+      }
+      at += __popc(bal[i]);
+    }
+    __syncthreads();  // wsum and bbase are rewritten for the next tile
   }
 }
 
