@@ -58,6 +58,8 @@ def parse():
     p.add_argument("--workload", default="uber", choices=["uber", "amazon", "reddit"],
                    help="uber: the default line; amazon: the 4.8M x 1.8M x 1.8M, 1.7e9-nonzero tensor "
                         "(mixed precision, generated on the GPU)")
+    p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
+                   help="arithmetic of the billion-nonzero workloads")
     p.add_argument("--amazon-fraction", type=float, default=1.0,
                    help="fraction of the amazon- or reddit-shaped tensor's events (dims kept)")
     return p.parse_args()
@@ -485,10 +487,11 @@ def run_large(args, spec, rank, world, local):
     lam = torch.empty(RANK, dtype=torch.float64, device="cuda")
     fitd = torch.empty(1, dtype=torch.float64, device="cuda")
     s, tau, it = SAMPLES, 2.0 ** -TAU_EXP, [0]
+    prec = cpa.binding.FP64 if args.precision == "fp64" else cpa.binding.MIXED
 
     def step(profile=0):
         res = cpa.cp_arls_lev(index, None, rank=RANK, samples=s, tau=tau, iters=ETA, seed=rank, iter_offset=it[0],
-                              out=(fs, lam, fitd), precision=cpa.binding.MIXED, fit_mode=cpa.binding.FIT_ESTIMATED,
+                              out=(fs, lam, fitd), precision=prec, fit_mode=cpa.binding.FIT_ESTIMATED,
                               fit_samples=1 << 27, profile=profile)
         it[0] += ETA
         return res

@@ -378,12 +378,13 @@ int cpa_leverage(const double* A, int64_t n, int32_t r, double* lev, void* strea
  * cudaMalloc/cudaFree would synchronise the device): they pass only A and lev.
  *   A (device) n x r row-major doubles; lev (device) n doubles out;
  *   1 <= r <= 64 (r > 64 returns CPA_ERR_UNSUPPORTED: the scratch holds r <= 64).
- * Its scratch (the r x r Gram, its factorisation, a warning word) is a 128 KiB
- * device array in the library, present on every GPU that loads the library until
- * the process exits.  The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress); make that first call before any stream capture.
- * All calls share the array: calls whose work overlaps on a GPU race on it.
- * Same results, warnings and errors as cpa_leverage otherwise. */
+ * Its scratch (the r x r Gram with its per-block partial sums, its factorisation, a
+ * warning word) is a 1 MiB device array in the library, present on every GPU that
+ * loads the library until the process exits.  The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  All calls share the array: calls whose work overlaps on a
+ * GPU race on it.  Same warnings and errors as cpa_leverage; the same scores up to
+ * rounding (the Gram may be summed over fewer blocks; reproducible call to call). */
 int cpa_leverage_noalloc(const double* A, int64_t n, int32_t r, double* lev, void* stream);
 
 /* Fixed-point sampling distribution of one mode (Lemma 5.3 draws

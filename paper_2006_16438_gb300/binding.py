@@ -473,12 +473,23 @@ def cpa_leverage(A):
 
 def cpa_leverage_noalloc(A, lev=None):
     """cpa_leverage without any device allocation inside the library (the caller
-    supplies the output ``lev``; the library's scratch is a fixed device array)."""
+    supplies the output ``lev``; the library's scratch is a fixed device array).
+    A supplied ``lev`` must be a contiguous float64 tensor of n elements on A's
+    device: the library writes n doubles through its pointer."""
     torch = _torch()
     A = A.to(device="cuda", dtype=torch.float64).contiguous()
     n, r = A.shape
     if lev is None:
-        lev = torch.empty(n, dtype=torch.float64, device="cuda")
+        lev = torch.empty(n, dtype=torch.float64, device=A.device)
+    else:
+        if not isinstance(lev, torch.Tensor):
+            raise TypeError("lev must be a torch tensor")
+        if lev.dtype != torch.float64:
+            raise TypeError(f"lev must be float64, not {lev.dtype}")
+        if lev.device != A.device:
+            raise ValueError(f"lev is on {lev.device}, A on {A.device}")
+        if lev.numel() != n or not lev.is_contiguous():
+            raise ValueError(f"lev must be a contiguous tensor of {n} elements")
     rc = _check(_lib().cpa_leverage_noalloc(_ptr(A), n, r, _ptr(lev), _stream()), "cpa_leverage_noalloc")
     return lev, rc
 

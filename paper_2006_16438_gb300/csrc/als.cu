@@ -132,6 +132,7 @@ int run_als(const cpa_index* X, const cpa_options* opt, double* lambda, double* 
   FT* M = nullptr;
   SmallFactor* fs = nullptr;
   int* warn = nullptr;
+  BlockSums sums;
   for (int pass = 0; pass < 2; ++pass) {
     a.used = 0;
     for (int m = 0; m < D; ++m) Fm[m] = a.take<FT>((size_t)X->dims[m] * r);
@@ -144,6 +145,7 @@ int run_als(const cpa_index* X, const cpa_options* opt, double* lambda, double* 
     fit_ws = a.take<double>(fit_buffers_bytes(D, r) / sizeof(double) + 1);
     fs = a.take<SmallFactor>(1);
     warn = a.take<int>(4);
+    sums = a.take_sums(kSumMaxBlocks, gram_sums_width(r));
     if (pass == 0 && cudaMalloc((void**)&a.base, a.used) != cudaSuccess) return CPA_ERR_OOM;
   }
   struct Free {
@@ -157,13 +159,13 @@ int run_als(const cpa_index* X, const cpa_options* opt, double* lambda, double* 
   } guard{a.base};
   const cudaMemcpyKind kin = io_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   CPA_CUDA_TRY(cudaMemsetAsync(warn, 0, sizeof(int) * 4, st));
+  CPA_CUDA_TRY(cudaMemsetAsync(sums.ticket, 0, sizeof(unsigned), st));
   for (int m = 0; m < D; ++m) {
     const int64_t cnt = X->dims[m] * r;
     CPA_CUDA_TRY(cudaMemcpyAsync(stage, factors[m], sizeof(double) * cnt, kin, st));
     k_conv<FT, double><<<grid_of(cnt), kThreads, 0, st>>>(stage, cnt, Fm[m]);
     CPA_LAUNCH_CHECK();
-    CPA_CUDA_TRY(cudaMemsetAsync(grams + (size_t)m * r * r, 0, sizeof(double) * r * r, st));
-    CPA_TRY(gram_rows<FT>(Fm[m], X->dims[m], r, grams + (size_t)m * r * r, st));
+    CPA_TRY(gram_rows<FT>(Fm[m], X->dims[m], r, grams + (size_t)m * r * r, sums, st));
   }
   FactorPtrs F;
   for (int m = 0; m < D; ++m) F.A[m] = Fm[m];
@@ -181,7 +183,7 @@ int run_als(const cpa_index* X, const cpa_options* opt, double* lambda, double* 
       CPA_TRY(exact_mttkrp<FT>(X, k, F, r, M, st));
       CPA_TRY(factor_spd(G, r, 0, 0, 1e-13, fs, warn, CPA_WARN_SINGULAR_GRAM, st));
       CPA_TRY(solve_rows<FT>(M, nk, r, fs, Fm[k], st, gk));  // also clears gk
-      CPA_TRY(gram_rows<FT>(Fm[k], nk, r, gk, st));
+      CPA_TRY(gram_rows<FT>(Fm[k], nk, r, gk, sums, st));
       k_lambda_from_gram<<<1, 256, 0, st>>>(gk, r, lam);
       CPA_LAUNCH_CHECK();
       k_scale_cols<FT><<<grid_of(nk * r), kThreads, 0, st>>>(Fm[k], nk, r, lam);
@@ -190,7 +192,7 @@ int run_als(const cpa_index* X, const cpa_options* opt, double* lambda, double* 
   }
   double fv = NAN;
   if (opt->fit_mode == CPA_FIT_EXACT) {
-    CPA_TRY(fit_enqueue<FT>(X, F, lam, r, fit_ws, fitd, st));
+    CPA_TRY(fit_enqueue<FT>(X, F, lam, r, fit_ws, sums, fitd, st));
     CPA_CUDA_TRY(cudaMemcpyAsync(&fv, fitd, sizeof(double), cudaMemcpyDeviceToHost, st));
   }
   const cudaMemcpyKind kout = io_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;

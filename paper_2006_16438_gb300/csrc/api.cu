@@ -133,20 +133,25 @@ struct DevBuf {
 };
 
 // Leverage distribution of one factor: lev (optional), CDF C, info; A normalised in
-// place when `normalize_out` (the update path), untouched otherwise.
-// gram_zeroed: GA was already cleared by the previous kernel (the solve).
+// place when `normalize_out` (the update path), untouched otherwise.  GA receives the
+// factor's Gram (block-ordered sums in S).
 // dist: the row distribution (leverage, or uniform / length-squared for comparison);
 // the Gram and its factor are formed in every case (lambda, normalisation).
+// src (optional, row stride lda): the rows are read from src and the normalised
+// rows written to A (the update with the solve folded into the sampled MTTKRP, whose
+// output src holds the unnormalised new factor).
 template <class FT>
 int refresh_distribution(FT* A, int64_t n, int r, uint64_t* C, DistInfo* info, double* Pm,
-                         double* GA, SmallFactor* fac, int* warn, void* scan_scratch, bool normalize_out,
-                         double* lev_out, cudaStream_t st, bool gram_zeroed = false, int dist = CPA_DIST_LEVERAGE) {
-  if (!gram_zeroed) CPA_CUDA_TRY(cudaMemsetAsync(GA, 0, sizeof(double) * r * r, st));
-  CPA_TRY(gram_rows<FT>(A, n, r, GA, st));
+                         double* GA, const BlockSums& S, SmallFactor* fac, int* warn, void* scan_scratch,
+                         bool normalize_out, double* lev_out, cudaStream_t st, int dist = CPA_DIST_LEVERAGE,
+                         const FT* src = nullptr, int lda = 0) {
+  const FT* in = src ? src : A;
+  CPA_TRY(gram_rows<FT>(in, n, r, GA, S, st, src ? lda : r));
   // a rank-deficient factor matters only to leverage scores (warning bit 0: no warning)
   CPA_TRY(factor_spd(GA, r, 1, 1, 1e-12, fac, warn, dist == CPA_DIST_LEVERAGE ? CPA_WARN_RANK_DEFICIENT_LEV : 0,
                      st, info));
-  CPA_TRY(lev_rows<FT>(A, n, r, fac, lev_out, C, info, normalize_out ? A : nullptr, st, dist));
+  CPA_TRY(lev_rows<FT>(in, n, r, fac, lev_out, C, info, normalize_out || src ? A : nullptr, st, dist,
+                       src ? lda : r));
   CPA_TRY(cdf_from_q(C, C, n, info, Pm, scan_scratch, st));
   return CPA_OK;
 }
@@ -285,6 +290,7 @@ struct Plan {
   // key
   int r = 0, D = 0, reject_cap = 0, profile = 0, prec = CPA_FP64, ftb = 8, dist = CPA_DIST_LEVERAGE;
   int64_t s = 0, det_cap = 0, det_buf = 0;
+  int64_t fold_min = 0;  // modes of at least this many rows take the folded update
   double tau = 0.0;
   uint64_t seed = 0;
   // workspace
@@ -297,6 +303,8 @@ struct Plan {
   void* M = nullptr;
   double *Gs = nullptr, *GA = nullptr, *lam = nullptr, *fitd = nullptr, *fit_ws = nullptr;
   SmallFactor *fsolve = nullptr, *flev = nullptr;
+  BlockSums sums_lev;   // block-ordered sums of the factor Grams and the fit (main stream)
+  BlockSums sums_gram;  // of the sampled Gram (its own branch)
   int* warn = nullptr;
   DevStats* dstats = nullptr;
   char* scan_ws = nullptr;
@@ -344,11 +352,12 @@ struct Plan {
     det_buf = det_buffer_capacity(s, tau, det_cap);
     use_graph = !(tau < 1.0 && tau * (double)s < 1.0);  // no top-s host sync possible
     int64_t nmax = 1, nsum = 0;
-    bool slabs = false;  // some mode's M is accumulated slab by slab
+    bool slabs = false;  // some mode's M is accumulated slab by slab, or its update folded
+    fold_min = fold_rows();
     for (int m = 0; m < D; ++m) {
       nmax = std::max<int64_t>(nmax, X->dims[m]);
       nsum += X->dims[m];
-      slabs = slabs || mttkrp_slabs(X->dims[m], r, ftb) > 1;
+      slabs = slabs || mttkrp_slabs(X->dims[m], r, ftb) > 1 || X->dims[m] >= fold_min;
     }
     KeyLayout Lsum;
     memset(&Lsum, 0, sizeof(Lsum));
@@ -364,7 +373,7 @@ struct Plan {
       }
       stage64 = prec == CPA_MIXED ? a.take<double>((size_t)nmax * r) : nullptr;
       info = a.take<DistInfo>(kMaxOrder);
-      M = a.take<char>((size_t)nmax * r * ftb);
+      M = a.take<char>((size_t)nmax * fold_ldm(r, ftb) * ftb);
       Gs = a.take<double>(r * r);
       GA = a.take<double>(r * r);
       lam = a.take<double>(kMaxRank);
@@ -372,12 +381,14 @@ struct Plan {
       fit_ws = a.take<double>(fit_buffers_bytes(D, r) / sizeof(double) + 1);
       fsolve = a.take<SmallFactor>(1);
       flev = a.take<SmallFactor>(1);
+      sums_lev = a.take_sums(kSumMaxBlocks, gram_sums_width(r));
+      sums_gram = a.take_sums(kSumMaxBlocks, gram_sums_width(r));
       warn = a.take<int>(4);
       dstats = a.take<DevStats>(1);
       scan_ws = a.take<char>(scan_workspace(nmax));
       iter_dev = a.take<uint64_t>(1);
       sample_buffers_carve(a, Lsum, s, det_buf, &SB[0]);
-      mttkrp_buffers_carve(a, s, r, ftb, slabs, &MB);
+      mttkrp_buffers_carve(a, s, r, ftb, slabs, &MB, det_capacity(X, prec));
       if (pass == 0) {
         if (cudaMalloc((void**)&a.base, a.used) != cudaSuccess) return CPA_ERR_OOM;
         base = a.base;
@@ -400,6 +411,8 @@ struct Plan {
       for (int t = L.d; t < kMaxOrder; ++t) SB[k].cand_off[t] = off;
     }
     CPA_CUDA_TRY(cudaMemsetAsync(SB[0].state, 0, sizeof(SampleState), st));
+    CPA_CUDA_TRY(cudaMemsetAsync(sums_lev.ticket, 0, sizeof(unsigned), st));
+    CPA_CUDA_TRY(cudaMemsetAsync(sums_gram.ticket, 0, sizeof(unsigned), st));
     // the combine table starts empty; each pass's compaction empties it again
     CPA_CUDA_TRY(cudaMemsetAsync(SB[0].hkeys, 0xff, sizeof(uint64_t) << SB[0].hbits, st));
     CPA_CUDA_TRY(cudaMemsetAsync(SB[0].hcnt, 0, sizeof(uint32_t) << SB[0].hbits, st));
@@ -435,20 +448,34 @@ struct Plan {
       Ps.det_cap = tau < 1.0 ? det_cap : 1;
       Ps.det_buf = det_buf;
       CPA_TRY(prof.mark(-1));
-      CPA_TRY(skrp_lev(Ps, SB[k], st, false));
+      // FP64: the sampled rows in ascending key order, so that every later sum over
+      // them (Gram, MTTKRP) runs in one order and the run is reproducible
+      CPA_TRY(skrp_lev(Ps, SB[k], st, prec == CPA_FP64));
       CPA_TRY(prof.mark(0));
       const int64_t nk = X->dims[k];
       FT* Mt = static_cast<FT*>(M);
       FT* Fk = static_cast<FT*>(Fm[k]);
       cudaEvent_t evs[2] = {prof.pending(-1), prof.pending(1)};
-      CPA_TRY(sampled_mttkrp<FT>(X, k, F, r, SB[k].idx_packed, SB[k].wgt, DevCount{&SB[k].state->sbar, s},
-                                 Mt, Gs, MB, st, prof.on ? evs : nullptr, &fork));
-      CPA_TRY(prof.mark(2));
-      CPA_TRY(factor_spd(Gs, r, 0, 0, 1e-13, fsolve, warn, CPA_WARN_SINGULAR_GRAM, st));
-      CPA_TRY(solve_rows<FT>(Mt, nk, r, fsolve, Fk, st, GA));
-      CPA_TRY(prof.mark(3));
-      CPA_TRY(refresh_distribution<FT>(Fk, nk, r, Cm[k], info + k, Pm[k], GA, flev, warn, scan_ws, true,
-                                       nullptr, st, true, dist));
+      if (nk >= fold_min) {
+        // the solve folded into the sampled MTTKRP: Mt holds the unnormalised new
+        // factor, which the leverage refresh normalises into Fk
+        const int ldm = fold_ldm(r, ftb);
+        CPA_TRY(sampled_mttkrp_fold<FT>(X, k, F, r, SB[k].idx_packed, SB[k].wgt, DevCount{&SB[k].state->sbar, s},
+                                        Mt, ldm, Gs, fsolve, warn, MB, st, prof.on ? evs : nullptr));
+        CPA_TRY(prof.mark(2));
+        CPA_TRY(prof.mark(3));
+        CPA_TRY(refresh_distribution<FT>(Fk, nk, r, Cm[k], info + k, Pm[k], GA, sums_lev, flev, warn, scan_ws,
+                                         true, nullptr, st, dist, Mt, ldm));
+      } else {
+        CPA_TRY(sampled_mttkrp<FT>(X, k, F, r, SB[k].idx_packed, SB[k].wgt, DevCount{&SB[k].state->sbar, s},
+                                   Mt, Gs, MB, st, prof.on ? evs : nullptr, &fork));
+        CPA_TRY(prof.mark(2));
+        CPA_TRY(factor_spd(Gs, r, 0, 0, 1e-13, fsolve, warn, CPA_WARN_SINGULAR_GRAM, st));
+        CPA_TRY(solve_rows<FT>(Mt, nk, r, fsolve, Fk, st, GA));
+        CPA_TRY(prof.mark(3));
+        CPA_TRY(refresh_distribution<FT>(Fk, nk, r, Cm[k], info + k, Pm[k], GA, sums_lev, flev, warn, scan_ws,
+                                         true, nullptr, st, dist));
+      }
       k_finish_update<<<1, 64, 0, st>>>(flev, r, lam, dstats, SB[k].state, MB.total, warn);
       CPA_LAUNCH_CHECK();
       CPA_TRY(prof.mark(4));
@@ -510,10 +537,10 @@ struct Plan {
     for (int m = 0; m < D; ++m) {
       if (prec == CPA_MIXED)
         CPA_TRY(refresh_distribution<float>(static_cast<float*>(Fm[m]), X->dims[m], r, Cm[m], info + m,
-                                            Pm[m], GA, flev, warn, scan_ws, false, nullptr, st, false, dist));
+                                            Pm[m], GA, sums_lev, flev, warn, scan_ws, false, nullptr, st, dist));
       else
         CPA_TRY(refresh_distribution<double>(static_cast<double*>(Fm[m]), X->dims[m], r, Cm[m], info + m,
-                                             Pm[m], GA, flev, warn, scan_ws, false, nullptr, st, false, dist));
+                                             Pm[m], GA, sums_lev, flev, warn, scan_ws, false, nullptr, st, dist));
     }
     return CPA_OK;
   }
@@ -526,8 +553,8 @@ struct Plan {
     if (kind == CPA_FIT_ESTIMATED)
       return prec == CPA_MIXED ? fit_estimate_enqueue<float>(X, est, F, lam, r, fitd, st)
                                : fit_estimate_enqueue<double>(X, est, F, lam, r, fitd, st);
-    return prec == CPA_MIXED ? fit_enqueue<float>(X, F, lam, r, fit_ws, fitd, st)
-                             : fit_enqueue<double>(X, F, lam, r, fit_ws, fitd, st);
+    return prec == CPA_MIXED ? fit_enqueue<float>(X, F, lam, r, fit_ws, sums_lev, fitd, st)
+                             : fit_enqueue<double>(X, F, lam, r, fit_ws, sums_lev, fitd, st);
   }
 
   // Draws the element sample of the estimated fit unless the one held matches the
@@ -585,12 +612,20 @@ struct Plan {
     const int64_t nk = X->dims[k];
     FT* Mt = static_cast<FT*>(M);
     FT* Fk = static_cast<FT*>(Fm[k]);
-    CPA_TRY(sampled_mttkrp<FT>(X, k, F, r, B.idx_packed, B.wgt, DevCount{&B.state->sbar, s}, Mt, Gs, MB,
-                               st));
-    CPA_TRY(factor_spd(Gs, r, 0, 0, 1e-13, fsolve, warn, CPA_WARN_SINGULAR_GRAM, st));
-    CPA_TRY(solve_rows<FT>(Mt, nk, r, fsolve, Fk, st));
-    CPA_TRY(refresh_distribution<FT>(Fk, nk, r, Cm[k], info + k, Pm[k], GA, flev, warn, scan_ws, true,
-                                     nullptr, st, false, dist));
+    if (nk >= fold_min) {
+      const int ldm = fold_ldm(r, ftb);
+      CPA_TRY(sampled_mttkrp_fold<FT>(X, k, F, r, B.idx_packed, B.wgt, DevCount{&B.state->sbar, s}, Mt, ldm, Gs,
+                                      fsolve, warn, MB, st));
+      CPA_TRY(refresh_distribution<FT>(Fk, nk, r, Cm[k], info + k, Pm[k], GA, sums_lev, flev, warn, scan_ws, true,
+                                       nullptr, st, dist, Mt, ldm));
+    } else {
+      CPA_TRY(sampled_mttkrp<FT>(X, k, F, r, B.idx_packed, B.wgt, DevCount{&B.state->sbar, s}, Mt, Gs, MB,
+                                 st));
+      CPA_TRY(factor_spd(Gs, r, 0, 0, 1e-13, fsolve, warn, CPA_WARN_SINGULAR_GRAM, st));
+      CPA_TRY(solve_rows<FT>(Mt, nk, r, fsolve, Fk, st));
+      CPA_TRY(refresh_distribution<FT>(Fk, nk, r, Cm[k], info + k, Pm[k], GA, sums_lev, flev, warn, scan_ws, true,
+                                       nullptr, st, dist));
+    }
     k_copy_lambda<<<1, 64, 0, st>>>(flev, r, lam);
     CPA_LAUNCH_CHECK();
     return CPA_OK;
@@ -977,14 +1012,15 @@ int cpa_leverage(const double* A, int64_t n, int32_t r, double* lev, void* strea
     double* G = a.take<double>(r * r);
     SmallFactor* f = a.take<SmallFactor>(1);
     int* warn = a.take<int>(1);
+    BlockSums sums = a.take_sums(kSumMaxBlocks, gram_sums_width(r));
     if (pass == 0) {
       CPA_TRY(buf.alloc(a.used, st));
       a.base = (char*)buf.p;
       continue;
     }
-    CPA_CUDA_TRY(cudaMemsetAsync(G, 0, sizeof(double) * r * r, st));
     CPA_CUDA_TRY(cudaMemsetAsync(warn, 0, sizeof(int), st));
-    CPA_TRY(gram_rows<double>(A, n, r, G, st));
+    CPA_CUDA_TRY(cudaMemsetAsync(sums.ticket, 0, sizeof(unsigned), st));
+    CPA_TRY(gram_rows<double>(A, n, r, G, sums, st));
     CPA_TRY(factor_spd(G, r, 1, 1, 1e-12, f, warn, CPA_WARN_RANK_DEFICIENT_LEV, st));
     CPA_TRY(lev_rows<double>(A, n, r, f, lev, nullptr, nullptr, (double*)nullptr, st));
     int hwarn = 0;
@@ -1125,7 +1161,8 @@ int cpa_sampled_mttkrp(const cpa_index* X, int32_t mode_k, const double* const* 
   for (int pass = 0; pass < 2; ++pass) {
     a.used = 0;
     packed = a.take<uint64_t>(sbar);
-    mttkrp_buffers_carve(a, sbar, r, (int)sizeof(double), mttkrp_slabs(X->dims[mode_k], r, 8) > 1, &B);
+    mttkrp_buffers_carve(a, sbar, r, (int)sizeof(double), mttkrp_slabs(X->dims[mode_k], r, 8) > 1, &B,
+                         det_capacity(X, CPA_FP64));
     if (pass == 0) {
       CPA_TRY(buf.alloc(a.used, st));
       a.base = (char*)buf.p;
@@ -1146,16 +1183,18 @@ int cpa_solve(const double* G, const double* M, int64_t n, int32_t r, double* A,
   if (!G || !M || !A || !lambda || n < 1 || r < 1 || r > kMaxRank || A == M) return CPA_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   DevBuf buf;
-  CPA_TRY(buf.alloc(sizeof(SmallFactor) * 2 + sizeof(double) * r * r + 1024, st));
+  const size_t sums_bytes = block_sums_bytes(kSumMaxBlocks, gram_sums_width(r));
+  CPA_TRY(buf.alloc(sizeof(SmallFactor) * 2 + sizeof(double) * r * r + 1024 + sums_bytes, st));
   SmallFactor* fs = (SmallFactor*)buf.p;
   SmallFactor* fl = fs + 1;
   double* GA = (double*)(fl + 1);
   int* warn = (int*)(GA + r * r);
+  BlockSums sums = block_sums_at((char*)buf.p + sizeof(SmallFactor) * 2 + sizeof(double) * r * r + 1024, kSumMaxBlocks);
   CPA_CUDA_TRY(cudaMemsetAsync(warn, 0, sizeof(int), st));
+  CPA_CUDA_TRY(cudaMemsetAsync(sums.ticket, 0, sizeof(unsigned), st));
   CPA_TRY(factor_spd(G, r, 0, 0, 1e-13, fs, warn, CPA_WARN_SINGULAR_GRAM, st));
   CPA_TRY(solve_rows<double>(M, n, r, fs, A, st));
-  CPA_CUDA_TRY(cudaMemsetAsync(GA, 0, sizeof(double) * r * r, st));
-  CPA_TRY(gram_rows<double>(A, n, r, GA, st));
+  CPA_TRY(gram_rows<double>(A, n, r, GA, sums, st));
   int dummy_warn_bit = 0;
   CPA_TRY(factor_spd(GA, r, 1, 1, 1e-12, fl, warn, dummy_warn_bit, st));
   k_copy_lambda<<<1, 64, 0, st>>>(fl, r, lambda);
@@ -1263,10 +1302,13 @@ int cpa_fit(const cpa_index* X, const double* const* factors, const double* lamb
     F.A[m] = factors[m];
   }
   DevBuf buf;
-  CPA_TRY(buf.alloc(fit_buffers_bytes(X->order, r) + 256, st));
+  const size_t fb = (fit_buffers_bytes(X->order, r) + 256 + 255) & ~size_t(255);
+  CPA_TRY(buf.alloc(fb + block_sums_bytes(kSumMaxBlocks, gram_sums_width(r)), st));
   double* fit_dev = (double*)buf.p;
   double* scratch = fit_dev + 32;
-  CPA_TRY(fit_enqueue<double>(X, F, lambda, r, scratch, fit_dev, st));
+  BlockSums sums = block_sums_at((char*)buf.p + fb, kSumMaxBlocks);
+  CPA_CUDA_TRY(cudaMemsetAsync(sums.ticket, 0, sizeof(unsigned), st));
+  CPA_TRY(fit_enqueue<double>(X, F, lambda, r, scratch, sums, fit_dev, st));
   CPA_CUDA_TRY(cudaMemcpyAsync(fit, fit_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
   CPA_CUDA_TRY(cudaStreamSynchronize(st));
   return CPA_OK;
@@ -1341,13 +1383,13 @@ int cpa_mode_update(const cpa_index* X, const cpa_options* opt, int32_t mode_k, 
       k_convert<float, double><<<blocks(c), 256, 0, st>>>(factors[m], c, static_cast<float*>(P->Fm[m]));
       CPA_LAUNCH_CHECK();
       CPA_TRY(refresh_distribution<float>(static_cast<float*>(P->Fm[m]), X->dims[m], r, P->Cm[m], P->info + m,
-                                          P->Pm[m], P->GA, P->flev, P->warn, P->scan_ws, false, nullptr, st, false,
-                                          P->dist));
+                                          P->Pm[m], P->GA, P->sums_lev, P->flev, P->warn, P->scan_ws, false, nullptr,
+                                          st, P->dist));
     } else {
       CPA_CUDA_TRY(cudaMemcpyAsync(P->Fm[m], factors[m], sizeof(double) * c, cudaMemcpyDeviceToDevice, st));
       CPA_TRY(refresh_distribution<double>(static_cast<double*>(P->Fm[m]), X->dims[m], r, P->Cm[m],
-                                           P->info + m, P->Pm[m], P->GA, P->flev, P->warn, P->scan_ws, false,
-                                           nullptr, st, false, P->dist));
+                                           P->info + m, P->Pm[m], P->GA, P->sums_lev, P->flev, P->warn, P->scan_ws,
+                                           false, nullptr, st, P->dist));
     }
   }
   if (P->prec == CPA_MIXED) CPA_TRY(P->update_once<float>(X, mode_k, iter, idx, st));

@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <new>
 #include <vector>
 
@@ -135,6 +136,63 @@ inline bool make_layout(int order, const int64_t* dims, int k, KeyLayout* L) {
 }
 
 // ---------------------------------------------------------------------------
+// Deterministic sums across the blocks of a grid.  Each block stores its partial
+// values (width of them) at part[blockIdx.x * width + i]; the block that arrives
+// last (a ticket counter) adds every block's partials in block order and re-arms
+// the ticket.  The result depends only on the grid size, so kernels that reduce
+// this way take grids that do not depend on the SM count or an SM budget.
+// ---------------------------------------------------------------------------
+constexpr int kSumMaxBlocks = 608;  // largest grid of a block-ordered sum (4 per SM of a GB300)
+
+struct BlockSums {
+  unsigned* ticket = nullptr;  // zero between uses
+  double* part = nullptr;      // max_blocks * width
+  int max_blocks = 0;
+};
+constexpr size_t block_sums_bytes(int max_blocks, int width) {
+  return 256 + sizeof(double) * (size_t)max_blocks * (size_t)(width > 0 ? width : 1);
+}
+// Views a zeroed region of block_sums_bytes(max_blocks, width) bytes at p.
+inline BlockSums block_sums_at(void* p, int max_blocks) {
+  BlockSums s;
+  s.ticket = reinterpret_cast<unsigned*>(p);
+  s.part = reinterpret_cast<double*>(reinterpret_cast<char*>(p) + 256);
+  s.max_blocks = max_blocks;
+  return s;
+}
+
+// Called by every thread of every block once the block's partials are stored;
+// true in the one block that arrives last, which may then read all partials (with
+// ld.global.cg, past the non-coherent L1).
+__device__ __forceinline__ bool last_block_to_arrive(unsigned* ticket) {
+  __shared__ int last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (last) __threadfence();
+  return last != 0;
+}
+// Sum over blocks b = 0..nb-1 of part[b * width + i] in a fixed order (four
+// interleaved chains, then (c0 + c1) + (c2 + c3)), so FP64 add latency overlaps.
+__device__ __forceinline__ double ordered_block_sum(const double* part, int nb, int width, int i) {
+  double c0 = 0.0, c1 = 0.0, c2 = 0.0, c3 = 0.0;
+  int b = 0;
+  for (; b + 3 < nb; b += 4) {
+    c0 += __ldcg(part + (size_t)b * width + i);
+    c1 += __ldcg(part + (size_t)(b + 1) * width + i);
+    c2 += __ldcg(part + (size_t)(b + 2) * width + i);
+    c3 += __ldcg(part + (size_t)(b + 3) * width + i);
+  }
+  for (; b < nb; ++b) c0 += __ldcg(part + (size_t)b * width + i);
+  return (c0 + c1) + (c2 + c3);
+}
+// Re-arms the ticket (by thread 0 of the last block, after its reads).
+__device__ __forceinline__ void rearm_ticket(unsigned* ticket) {
+  if (threadIdx.x == 0) *ticket = 0u;
+}
+
+// ---------------------------------------------------------------------------
 // Device arena: one cudaMallocAsync block carved into aligned pieces.  A first
 // pass with base == nullptr only measures.
 // ---------------------------------------------------------------------------
@@ -148,7 +206,33 @@ struct Arena {
     used = at + count * sizeof(T) + 1;
     return base ? reinterpret_cast<T*>(base + at) : nullptr;
   }
+  // Workspace of a block-ordered sum (its ticket must be zeroed before first use).
+  BlockSums take_sums(int max_blocks, int width) {
+    char* p = take<char>(block_sums_bytes(max_blocks, width));
+    BlockSums s;
+    if (p) s = block_sums_at(p, max_blocks);
+    s.max_blocks = max_blocks;
+    return s;
+  }
 };
+
+// ---------------------------------------------------------------------------
+// Kernel attributes (the opt-in to large dynamic shared memory) belong to each
+// device's context: set_attr_once runs `set` once per device, the current one.
+// `done` holds a bit per device (devices >= 64: set at every call).  Two host threads
+// may both run `set` for a device the first time; the call is idempotent.
+// ---------------------------------------------------------------------------
+template <class Fn>
+inline cudaError_t set_attr_once(std::atomic<unsigned long long>& done, Fn&& set) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = dev >= 0 && dev < 64 ? (1ull << dev) : 0ull;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  e = set();
+  if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
+}
 
 // ---------------------------------------------------------------------------
 // Error plumbing

@@ -23,13 +23,35 @@ __device__ __forceinline__ void pair_of(int p, int r, int* a, int* b) {
   *b = row + (p - start);
 }
 
+// The block's pair sums go to its partials; the last block to finish adds all
+// blocks' partials in block order and writes the symmetric G (so G is the same bit
+// for bit at every run with the same grid).
+template <int PMAX>
+__device__ __forceinline__ void gram_block_finish(const double* acc, int np, int r, double* G, const BlockSums& S) {
+  double* mine = S.part + (size_t)blockIdx.x * np;
+#pragma unroll
+  for (int q = 0; q < PMAX; ++q) {
+    const int p = threadIdx.x + q * kGramThreads;
+    if (p < np) mine[p] = acc[q];
+  }
+  if (!last_block_to_arrive(S.ticket)) return;
+  for (int p = threadIdx.x; p < np; p += blockDim.x) {
+    const double v = ordered_block_sum(S.part, gridDim.x, np, p);
+    int a, b;
+    pair_of(p, r, &a, &b);
+    G[a * r + b] = v;
+    G[b * r + a] = v;
+  }
+  rearm_ticket(S.ticket);
+}
+
 // Factor rows of storage type FT are multiplied and summed in FP64 (the Gram feeds
 // leverage scores and the fit).  The tile is converted to FP64 once when staged: on
 // GB300 a conversion issues on the FP64 pipe like a multiply-add.
 template <class FT, int PMAX>
 __global__ void __launch_bounds__(kGramThreads) k_gram_rows(const FT* __restrict__ A,
-                                                            int64_t n, int r,
-                                                            double* __restrict__ G) {
+                                                            int64_t n, int r, int lda,
+                                                            double* __restrict__ G, BlockSums S) {
   extern __shared__ __align__(16) unsigned char gram_smem[];
   double* tile = reinterpret_cast<double*>(gram_smem);  // kGramRows * r
   const int np = r * (r + 1) / 2;
@@ -45,9 +67,11 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_rows(const FT* __restrict
        row0 += (int64_t)gridDim.x * kGramRows) {
     const int rows = (int)((n - row0) < kGramRows ? (n - row0) : kGramRows);
     __syncthreads();
-    const FT* src = A + row0 * r;
-    for (int i = threadIdx.x; i < kGramRows * r; i += kGramThreads)
-      tile[i] = i < rows * r ? (double)src[i] : 0.0;
+    const FT* src = A + row0 * lda;
+    for (int i = threadIdx.x; i < kGramRows * r; i += kGramThreads) {
+      const int rr = i / r, c = i - rr * r;
+      tile[i] = rr < rows ? (double)src[(int64_t)rr * lda + c] : 0.0;
+    }
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < PMAX; ++q) {
@@ -59,14 +83,7 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_rows(const FT* __restrict
       }
     }
   }
-#pragma unroll
-  for (int q = 0; q < PMAX; ++q) {
-    const int p = threadIdx.x + q * kGramThreads;
-    if (p < np) {
-      atomicAdd(&G[pa[q] * r + pb[q]], acc[q]);
-      if (pa[q] != pb[q]) atomicAdd(&G[pb[q] * r + pa[q]], acc[q]);
-    }
-  }
+  gram_block_finish<PMAX>(acc, np, r, G, S);
 }
 
 // FP32 factors: the same Gram on the FP32 pipe.  Each float product is split
@@ -78,7 +95,7 @@ constexpr int kGramRowsFF = 64;
 
 template <int PMAX>
 __global__ void __launch_bounds__(kGramThreads) k_gram_rows_ff(const float* __restrict__ A, int64_t n, int r,
-                                                               double* __restrict__ G) {
+                                                               int lda, double* __restrict__ G, BlockSums S) {
   extern __shared__ __align__(16) unsigned char gram_smem[];
   float* tile = reinterpret_cast<float*>(gram_smem);  // kGramRowsFF * r
   const int np = r * (r + 1) / 2;
@@ -93,8 +110,11 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_rows_ff(const float* __re
   for (int64_t row0 = (int64_t)blockIdx.x * kGramRowsFF; row0 < n; row0 += (int64_t)gridDim.x * kGramRowsFF) {
     const int rows = (int)((n - row0) < kGramRowsFF ? (n - row0) : kGramRowsFF);
     __syncthreads();
-    const float* src = A + row0 * r;
-    for (int i = threadIdx.x; i < kGramRowsFF * r; i += kGramThreads) tile[i] = i < rows * r ? src[i] : 0.f;
+    const float* src = A + row0 * lda;
+    for (int i = threadIdx.x; i < kGramRowsFF * r; i += kGramThreads) {
+      const int rr = i / r, c = i - rr * r;
+      tile[i] = rr < rows ? src[(int64_t)rr * lda + c] : 0.f;
+    }
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < PMAX; ++q) {
@@ -115,14 +135,7 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_rows_ff(const float* __re
       }
     }
   }
-#pragma unroll
-  for (int q = 0; q < PMAX; ++q) {
-    const int p = threadIdx.x + q * kGramThreads;
-    if (p < np) {
-      atomicAdd(&G[pa[q] * r + pb[q]], acc[q]);
-      if (pa[q] != pb[q]) atomicAdd(&G[pb[q] * r + pa[q]], acc[q]);
-    }
-  }
+  gram_block_finish<PMAX>(acc, np, r, G, S);
 }
 
 // ---- r x r factorisation in one block -------------------------------------
@@ -535,7 +548,7 @@ __device__ __forceinline__ double lensq_den(const SmallFactor* f, int r, bool no
 }
 
 template <class FT>
-__global__ void __launch_bounds__(kRowThreads) k_lev_rows(const FT* A, int64_t n, int r,
+__global__ void __launch_bounds__(kRowThreads) k_lev_rows(const FT* A, int64_t n, int r, int lda,
                                                           const SmallFactor* __restrict__ f,
                                                           double* __restrict__ lev,
                                                           uint64_t* __restrict__ q,
@@ -565,7 +578,7 @@ __global__ void __launch_bounds__(kRowThreads) k_lev_rows(const FT* A, int64_t n
   uint32_t my_nz = 0;
   double* b = brow[threadIdx.x >> 5];
   for (int64_t row = gw; row < n; row += nwarps) {
-    const FT* a = A + row * r;
+    const FT* a = A + row * lda;
     double part = 0.0;
     if (dist == CPA_DIST_LEVERAGE) {
       // S a_i converted and scaled once (one FP64-pipe operation each), not per use
@@ -726,7 +739,7 @@ __global__ void k_scale_columns(FT* A, int64_t n, int r, const double* __restric
 // Leverage for many rows: one thread per row, rows staged through shared memory
 // (coalesced), runtime loops over r (FP32 factors of large modes).
 template <class FT>
-__global__ void __launch_bounds__(kRowThreads) k_lev_rows_tpr(const FT* A, int64_t n, int r,
+__global__ void __launch_bounds__(kRowThreads) k_lev_rows_tpr(const FT* A, int64_t n, int r, int lda,
                                                               const SmallFactor* __restrict__ f,
                                                               double* __restrict__ lev,
                                                               uint64_t* __restrict__ q,
@@ -759,7 +772,7 @@ __global__ void __launch_bounds__(kRowThreads) k_lev_rows_tpr(const FT* A, int64
     if (dist == CPA_DIST_LEVERAGE)
       for (int i = threadIdx.x; i < rows * r; i += kRowThreads) {
         const int rr = i / r, c = i - rr * r;
-        xs[rr * ld + c] = (double)A[row0 * r + i] * sc[c];
+        xs[rr * ld + c] = (double)A[(row0 + rr) * lda + c] * sc[c];
       }
     __syncthreads();
     if (threadIdx.x < rows) {
@@ -780,7 +793,7 @@ __global__ void __launch_bounds__(kRowThreads) k_lev_rows_tpr(const FT* A, int64
       } else if (dist == CPA_DIST_UNIFORM) {
         l = (double)r / (double)n;
       } else {  // comparison distribution: read the row directly
-        const FT* a = A + row * r;
+        const FT* a = A + row * lda;
         for (int c = 0; c < r; ++c) {
           const double b = normalised ? (double)a[c] * (double)lam[c] : (double)a[c];
           l = fma(b, b, l);
@@ -798,7 +811,10 @@ __global__ void __launch_bounds__(kRowThreads) k_lev_rows_tpr(const FT* A, int64
       }
     }
     if (A_out) {
-      for (int i = threadIdx.x; i < rows * r; i += kRowThreads) A_out[row0 * r + i] = A[row0 * r + i] * lam[i % r];
+      for (int i = threadIdx.x; i < rows * r; i += kRowThreads) {
+        const int rr = i / r, c = i - rr * r;
+        A_out[row0 * r + i] = A[(row0 + rr) * lda + c] * lam[c];
+      }
     }
   }
   if (q && info) {
@@ -838,7 +854,7 @@ __device__ __forceinline__ void ff_fma(float ah, float al, float bh, float bl, f
 // scales are split into float pairs once per block, S a is formed as a float pair
 // when the row is staged.  A kind 1 (pseudo-inverse) factor takes the FP64 loop.
 // Outputs as k_lev_rows_tpr.
-__global__ void __launch_bounds__(kRowThreads) k_lev_rows_ff(const float* A, int64_t n, int r,
+__global__ void __launch_bounds__(kRowThreads) k_lev_rows_ff(const float* A, int64_t n, int r, int lda,
                                                              const SmallFactor* __restrict__ f,
                                                              double* __restrict__ lev, uint64_t* __restrict__ q,
                                                              DistInfo* info, float* A_out) {
@@ -875,7 +891,7 @@ __global__ void __launch_bounds__(kRowThreads) k_lev_rows_ff(const float* A, int
     __syncthreads();
     for (int i = threadIdx.x; i < rows * r; i += kRowThreads) {
       const int rr = i / r, c = i - rr * r;
-      const float x = A[row0 * r + i];
+      const float x = A[(row0 + rr) * lda + c];
       const float p = __fmul_rn(x, sch[c]);
       const float rest = __fmaf_rn(x, scl[c], __fmaf_rn(x, sch[c], -p));
       const float h = __fadd_rn(p, rest);
@@ -918,7 +934,10 @@ __global__ void __launch_bounds__(kRowThreads) k_lev_rows_ff(const float* A, int
       }
     }
     if (A_out) {
-      for (int i = threadIdx.x; i < rows * r; i += kRowThreads) A_out[row0 * r + i] = A[row0 * r + i] * lam[i % r];
+      for (int i = threadIdx.x; i < rows * r; i += kRowThreads) {
+        const int rr = i / r, c = i - rr * r;
+        A_out[row0 * r + i] = A[(row0 + rr) * lda + c] * lam[c];
+      }
     }
   }
   if (q && info) {
@@ -937,35 +956,47 @@ __global__ void __launch_bounds__(kRowThreads) k_lev_rows_ff(const float* A, int
 }  // namespace
 
 template <class FT>
-int gram_rows(const FT* A, int64_t n, int r, double* G, cudaStream_t st) {
+int gram_rows(const FT* A, int64_t n, int r, double* G, const BlockSums& S, cudaStream_t st, int lda) {
+  if (lda <= 0) lda = r;
   if (r < 1 || r > kMaxRank) return CPA_ERR_ARG;
-  if (n <= 0) return CPA_OK;
+  if (!S.ticket || S.max_blocks < 1) return CPA_ERR_ARG;
   const int np = r * (r + 1) / 2;
+  if (n <= 0) {
+    CPA_CUDA_TRY(cudaMemsetAsync(G, 0, sizeof(double) * r * r, st));
+    return CPA_OK;
+  }
+  // grid from the sizes only (not the SM count): the block-ordered sum then gives the
+  // same G on every run
+  auto grid_for = [&](int64_t rows_per_block) {
+    int64_t g = ceil_div(n, rows_per_block);
+    const int64_t cap = S.max_blocks < kSumMaxBlocks ? S.max_blocks : kSumMaxBlocks;
+    return (unsigned)(g < cap ? g : cap);
+  };
   if constexpr (sizeof(FT) == 4) {
-    const unsigned grid = grid_cap(ceil_div(n, kGramRowsFF), 4);
+    const unsigned grid = grid_for(kGramRowsFF);
     const size_t smem = sizeof(float) * kGramRowsFF * r;
     if (np <= kGramThreads)
-      k_gram_rows_ff<1><<<grid, kGramThreads, smem, st>>>(A, n, r, G);
+      k_gram_rows_ff<1><<<grid, kGramThreads, smem, st>>>(A, n, r, lda, G, S);
     else if (np <= 4 * kGramThreads)
-      k_gram_rows_ff<4><<<grid, kGramThreads, smem, st>>>(A, n, r, G);
+      k_gram_rows_ff<4><<<grid, kGramThreads, smem, st>>>(A, n, r, lda, G, S);
     else
-      k_gram_rows_ff<9><<<grid, kGramThreads, smem, st>>>(A, n, r, G);
+      k_gram_rows_ff<9><<<grid, kGramThreads, smem, st>>>(A, n, r, lda, G, S);
     CPA_LAUNCH_CHECK();
     return CPA_OK;
   }
-  const unsigned grid = grid_cap(ceil_div(n, kGramRows), 4);
+  const unsigned grid = grid_for(kGramRows);
   const size_t smem = sizeof(double) * kGramRows * r;
   if (np <= kGramThreads)
-    k_gram_rows<FT, 1><<<grid, kGramThreads, smem, st>>>(A, n, r, G);
+    k_gram_rows<FT, 1><<<grid, kGramThreads, smem, st>>>(A, n, r, lda, G, S);
   else if (np <= 4 * kGramThreads)
-    k_gram_rows<FT, 4><<<grid, kGramThreads, smem, st>>>(A, n, r, G);
+    k_gram_rows<FT, 4><<<grid, kGramThreads, smem, st>>>(A, n, r, lda, G, S);
   else
-    k_gram_rows<FT, 9><<<grid, kGramThreads, smem, st>>>(A, n, r, G);
+    k_gram_rows<FT, 9><<<grid, kGramThreads, smem, st>>>(A, n, r, lda, G, S);
   CPA_LAUNCH_CHECK();
   return CPA_OK;
 }
-template int gram_rows<double>(const double*, int64_t, int, double*, cudaStream_t);
-template int gram_rows<float>(const float*, int64_t, int, double*, cudaStream_t);
+template int gram_rows<double>(const double*, int64_t, int, double*, const BlockSums&, cudaStream_t, int);
+template int gram_rows<float>(const float*, int64_t, int, double*, const BlockSums&, cudaStream_t, int);
 
 // Threads of the r x r factorisation block: a multiple of 32 in [32, 256]
 // (CPA_FACTOR_THREADS overrides the default, for tuning).
@@ -985,12 +1016,11 @@ int factor_spd(const double* G, int r, int normalize, int pivot, double rel_tol,
                int* warn, int warn_bit, cudaStream_t st, DistInfo* zero_info) {
   if (r < 1 || r > kMaxRank) return CPA_ERR_ARG;
   const size_t smem = sizeof(double) * (2 * r * r + 5 * r);
-  static bool attr_done = false;
-  if (!attr_done) {
-    CPA_CUDA_TRY(cudaFuncSetAttribute(k_factor_spd, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(sizeof(double) * (2 * kMaxRank * kMaxRank + 5 * kMaxRank))));
-    attr_done = true;
-  }
+  static std::atomic<unsigned long long> attr{0};
+  CPA_CUDA_TRY(set_attr_once(attr, [] {
+    return cudaFuncSetAttribute(k_factor_spd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(sizeof(double) * (2 * kMaxRank * kMaxRank + 5 * kMaxRank)));
+  }));
   k_factor_spd<<<1, factor_threads(), smem, st>>>(G, r, normalize, pivot, rel_tol, out, warn, warn_bit,
                                                 zero_info);
   CPA_LAUNCH_CHECK();
@@ -999,7 +1029,9 @@ int factor_spd(const double* G, int r, int normalize, int pivot, double rel_tol,
 
 template <class FT>
 int lev_rows(const FT* A, int64_t n, int r, const SmallFactor* f, double* lev, uint64_t* q,
-             DistInfo* info, FT* A_out, cudaStream_t st, int dist) {
+             DistInfo* info, FT* A_out, cudaStream_t st, int dist, int lda) {
+  if (lda <= 0) lda = r;
+  if (lda != r && A_out == A) return CPA_ERR_ARG;  // in place only at stride r
   if (dist != CPA_DIST_LEVERAGE && dist != CPA_DIST_UNIFORM && dist != CPA_DIST_LENGTH_SQUARED)
     return CPA_ERR_ARG;
   if (r < 1 || r > kMaxRank) return CPA_ERR_ARG;
@@ -1010,14 +1042,12 @@ int lev_rows(const FT* A, int64_t n, int r, const SmallFactor* f, double* lev, u
         return sizeof(float) * ((size_t)2 * rr * rr + 3 * rr + 1) + sizeof(float2) * (size_t)kRowThreads * (rr | 1) +
                16;
       };
-      static bool attr = false;
-      if (!attr) {
-        CPA_CUDA_TRY(cudaFuncSetAttribute(k_lev_rows_ff, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)bytes(kMaxRank)));
-        attr = true;
-      }
+      static std::atomic<unsigned long long> attr{0};
+      CPA_CUDA_TRY(set_attr_once(attr, [&] {
+        return cudaFuncSetAttribute(k_lev_rows_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes(kMaxRank));
+      }));
       const unsigned grid = grid_cap(ceil_div(n, kRowThreads), 8);
-      k_lev_rows_ff<<<grid, kRowThreads, bytes(r), st>>>(A, n, r, f, lev, q, info, A_out);
+      k_lev_rows_ff<<<grid, kRowThreads, bytes(r), st>>>(A, n, r, lda, f, lev, q, info, A_out);
       CPA_LAUNCH_CHECK();
       return CPA_OK;
     }
@@ -1028,26 +1058,25 @@ int lev_rows(const FT* A, int64_t n, int r, const SmallFactor* f, double* lev, u
              sizeof(double) * (size_t)kRowThreads * (rr | 1);
     };
     const size_t smem = bytes(r);
-    static bool attr = false;
-    if (!attr) {
-      CPA_CUDA_TRY(cudaFuncSetAttribute(k_lev_rows_tpr<FT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)bytes(kMaxRank)));
-      attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    CPA_CUDA_TRY(set_attr_once(attr, [&] {
+      return cudaFuncSetAttribute(k_lev_rows_tpr<FT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)bytes(kMaxRank));
+    }));
     const unsigned grid = grid_cap(ceil_div(n, kRowThreads), 8);
-    k_lev_rows_tpr<FT><<<grid, kRowThreads, smem, st>>>(A, n, r, f, lev, q, info, A_out, dist);
+    k_lev_rows_tpr<FT><<<grid, kRowThreads, smem, st>>>(A, n, r, lda, f, lev, q, info, A_out, dist);
   } else {
     const size_t smem = sizeof(double) * ((size_t)r * r + r) + sizeof(FT) * r;
     const unsigned grid = grid_cap(ceil_div(n, kRowThreads / 32), 16);
-    k_lev_rows<FT><<<grid, kRowThreads, smem, st>>>(A, n, r, f, lev, q, info, A_out, dist);
+    k_lev_rows<FT><<<grid, kRowThreads, smem, st>>>(A, n, r, lda, f, lev, q, info, A_out, dist);
   }
   CPA_LAUNCH_CHECK();
   return CPA_OK;
 }
 template int lev_rows<double>(const double*, int64_t, int, const SmallFactor*, double*, uint64_t*,
-                              DistInfo*, double*, cudaStream_t, int);
+                              DistInfo*, double*, cudaStream_t, int, int);
 template int lev_rows<float>(const float*, int64_t, int, const SmallFactor*, double*, uint64_t*,
-                             DistInfo*, float*, cudaStream_t, int);
+                             DistInfo*, float*, cudaStream_t, int, int);
 
 template <class FT>
 int solve_rows(const FT* M, int64_t n, int r, const SmallFactor* f, FT* A, cudaStream_t st,
@@ -1059,14 +1088,14 @@ int solve_rows(const FT* M, int64_t n, int r, const SmallFactor* f, FT* A, cudaS
       auto bytes = [](int rr) {
         return sizeof(float) * ((size_t)rr * ((rr + 3) & ~3) + (size_t)kRowThreads * (rr | 1));
       };
-      static bool attr = false;
-      if (!attr) {
-        CPA_CUDA_TRY(cudaFuncSetAttribute(k_solve_rows_f32<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)bytes(kMaxRank)));
-        CPA_CUDA_TRY(cudaFuncSetAttribute(k_solve_rows_f32<kMaxRank>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)bytes(kMaxRank)));
-        attr = true;
-      }
+      static std::atomic<unsigned long long> attr{0};
+      CPA_CUDA_TRY(set_attr_once(attr, [&] {
+        cudaError_t e = cudaFuncSetAttribute(k_solve_rows_f32<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)bytes(kMaxRank));
+        if (e != cudaSuccess) return e;
+        return cudaFuncSetAttribute(k_solve_rows_f32<kMaxRank>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)bytes(kMaxRank));
+      }));
       const unsigned grid = grid_cap(ceil_div(n, kRowThreads), 8);
       if (r <= 32)
         k_solve_rows_f32<32><<<grid, kRowThreads, bytes(r), st>>>(M, n, r, f, A, zero_gram);

@@ -33,10 +33,16 @@ struct DistInfo {
   int64_t pad;
 };
 
-// G += A^T A for a row-major n x r matrix of FT (float or double); partial sums
-// over 32-row tiles in FT, tiles added in FP64 (G zeroed by the caller).
+// G = A^T A for a row-major n x r matrix of FT (float or double): FP64 products of
+// FP64 rows; FP32 rows summed per 64-row tile in float-pair arithmetic (2^-44
+// relative); tiles added in FP64.  The blocks' partial sums are added in block order
+// (S: a workspace of block_sums_bytes(max_blocks, r (r + 1) / 2) bytes with its
+// ticket zeroed), so the result is reproducible bit for bit.
+// lda: row stride of A in elements (0: r).
 template <class FT>
-int gram_rows(const FT* A, int64_t n, int r, double* G, cudaStream_t st);
+int gram_rows(const FT* A, int64_t n, int r, double* G, const BlockSums& S, cudaStream_t st, int lda = 0);
+// Width of the block sums of gram_rows for rank r.
+inline int gram_sums_width(int r) { return r * (r + 1) / 2; }
 
 // Factor G (see SmallFactor).  rel_tol: a Cholesky pivot must exceed rel_tol times
 // the largest diagonal entry.  pivot = 0: plain Cholesky; if a pivot fails, the
@@ -59,9 +65,12 @@ int factor_spd(const double* G, int r, int normalize, int pivot, double rel_tol,
 // q_i = round-half-even(2^62 s_i / r) written to q (if non-null), s_i to lev (if
 // non-null), DistInfo maxq/nnzq accumulated (zeroed by the caller); rows divided by
 // lambda (columns with lambda = 0 untouched) and written to A_out if non-null (may be A).
+// lda: row stride of A in elements (0: r; A_out always has stride r, and may be A
+// only when lda = r).
 template <class FT>
 int lev_rows(const FT* A, int64_t n, int r, const SmallFactor* f, double* lev,
-             uint64_t* q, DistInfo* info, FT* A_out, cudaStream_t st, int dist = CPA_DIST_LEVERAGE);
+             uint64_t* q, DistInfo* info, FT* A_out, cudaStream_t st, int dist = CPA_DIST_LEVERAGE,
+             int lda = 0);
 
 // A = M G^{-1} row by row with the factor of G (kind 0: two triangular solves;
 // kind 1: A = M F).

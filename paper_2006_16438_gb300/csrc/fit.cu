@@ -24,7 +24,8 @@ constexpr int kThreads = 256;
 template <class FT, class VT, int CPL>
 __global__ void __launch_bounds__(kThreads) k_fit_inner(FibreIndex<VT> X, KeyLayout L, FactorPtrs F,
                                                         int kf, const double* __restrict__ lambda,
-                                                        int r, double* __restrict__ out) {
+                                                        int r, double* __restrict__ out, BlockSums S) {
+  __shared__ double wsum[kThreads / 32];
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
@@ -68,7 +69,17 @@ __global__ void __launch_bounds__(kThreads) k_fit_inner(FibreIndex<VT> X, KeyLay
     for (int q = 0; q < CPL; ++q) part += (double)(z[q] * acc[q]);
   }
   for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-  if (lane == 0 && part != 0.0) atomicAdd(out, part);
+  // warps in order, then blocks in order (the last block to finish adds them)
+  if (lane == 0) wsum[threadIdx.x >> 5] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) b += wsum[w];
+    S.part[blockIdx.x] = b;
+  }
+  if (!last_block_to_arrive(S.ticket)) return;
+  if (threadIdx.x == 0) *out = ordered_block_sum(S.part, gridDim.x, 1, 0);
+  rearm_ticket(S.ticket);
 }
 
 __global__ void k_fit_final(const double* __restrict__ grams, int D, const double* __restrict__ lambda,
@@ -100,34 +111,36 @@ size_t fit_buffers_bytes(int D, int r) { return sizeof(double) * ((size_t)D * r 
 
 template <class FT>
 int fit_enqueue(const cpa_index* X, const FactorPtrs& F, const double* lambda, int r, double* scratch,
-                double* fit_dev, cudaStream_t st) {
+                const BlockSums& S, double* fit_dev, cudaStream_t st) {
   const int D = X->order;
   double* grams = scratch;
   double* inner = scratch + (size_t)D * r * r;
-  CPA_CUDA_TRY(cudaMemsetAsync(scratch, 0, sizeof(double) * ((size_t)D * r * r + 1), st));
+  CPA_CUDA_TRY(cudaMemsetAsync(inner, 0, sizeof(double), st));  // an empty tensor launches no inner kernel
   for (int m = 0; m < D; ++m)
-    CPA_TRY(gram_rows<FT>(static_cast<const FT*>(F.A[m]), X->dims[m], r, grams + (size_t)m * r * r, st));
+    CPA_TRY(gram_rows<FT>(static_cast<const FT*>(F.A[m]), X->dims[m], r, grams + (size_t)m * r * r, S, st));
   int kf = 0;
   for (int m = 1; m < D; ++m)
     if (X->mode[m].nfib < X->mode[kf].nfib) kf = m;
-  const int sms = num_sms();
+  // grid from the size only: the block-ordered sum is then the same at every run
   const int64_t want = ceil_div(X->mode[kf].nfib, kThreads / 32);
-  const unsigned grid = (unsigned)(want < sms * 8 ? (want > 0 ? want : 1) : sms * 8);
-  with_value_type(X, [&](auto tag) {
-    using VT = decltype(tag);
-    const FibreIndex<VT> fx = fibre_view<VT>(X, kf);
-    if (r <= 32) k_fit_inner<FT, VT, 1><<<grid, kThreads, 0, st>>>(fx, X->mode[kf].L, F, kf, lambda, r, inner);
-    else k_fit_inner<FT, VT, 2><<<grid, kThreads, 0, st>>>(fx, X->mode[kf].L, F, kf, lambda, r, inner);
-    return 0;
-  });
+  const int64_t cap = S.max_blocks < kSumMaxBlocks ? S.max_blocks : kSumMaxBlocks;
+  const unsigned grid = (unsigned)(want < cap ? want : cap);
+  if (X->mode[kf].nfib > 0)
+    with_value_type(X, [&](auto tag) {
+      using VT = decltype(tag);
+      const FibreIndex<VT> fx = fibre_view<VT>(X, kf);
+      if (r <= 32) k_fit_inner<FT, VT, 1><<<grid, kThreads, 0, st>>>(fx, X->mode[kf].L, F, kf, lambda, r, inner, S);
+      else k_fit_inner<FT, VT, 2><<<grid, kThreads, 0, st>>>(fx, X->mode[kf].L, F, kf, lambda, r, inner, S);
+      return 0;
+    });
   k_fit_final<<<1, 256, 0, st>>>(grams, D, lambda, r, inner, X->norm_x2, fit_dev);
   CPA_LAUNCH_CHECK();
   return CPA_OK;
 }
-template int fit_enqueue<double>(const cpa_index*, const FactorPtrs&, const double*, int, double*, double*,
-                                 cudaStream_t);
-template int fit_enqueue<float>(const cpa_index*, const FactorPtrs&, const double*, int, double*, double*,
-                                cudaStream_t);
+template int fit_enqueue<double>(const cpa_index*, const FactorPtrs&, const double*, int, double*,
+                                 const BlockSums&, double*, cudaStream_t);
+template int fit_enqueue<float>(const cpa_index*, const FactorPtrs&, const double*, int, double*,
+                                const BlockSums&, double*, cudaStream_t);
 
 
 // ---------------------------------------------------------------------------
@@ -313,11 +326,13 @@ __global__ void k_fit_est_final(const double* __restrict__ partial, int nb, doub
   }
 }
 
+// Blocks of the estimate: from the sample size only (8 per SM of a GB300 at most),
+// so the fixed-order sum of the block partials is the same whatever the SM budget.
+constexpr int kEstMaxBlocks = 1216;
 int est_blocks(int64_t S) {
   const int64_t per_block = kEstThreads / kEstLanes;
   const int64_t want = ceil_div(S > 0 ? S : 1, per_block);
-  const int64_t cap = (int64_t)num_sms() * 8;
-  return (int)(want < cap ? want : cap);
+  return (int)(want < kEstMaxBlocks ? want : kEstMaxBlocks);
 }
 
 }  // namespace
@@ -345,7 +360,7 @@ int fit_sample_draw(const cpa_index* X, int64_t s_fit, double alpha, uint64_t se
   S->release();
   CPA_CUDA_TRY(cudaMalloc((void**)&S->coords, sizeof(int32_t) * (size_t)D * s_fit));
   CPA_CUDA_TRY(cudaMalloc((void**)&S->xs, sizeof(double) * (size_t)s_fit));
-  CPA_CUDA_TRY(cudaMalloc((void**)&S->partial, sizeof(double) * ((size_t)device_sms() * 8 + 8)));
+  CPA_CUDA_TRY(cudaMalloc((void**)&S->partial, sizeof(double) * ((size_t)kEstMaxBlocks + 8)));
   int* d_status = nullptr;
   CPA_CUDA_TRY(cudaMallocAsync((void**)&d_status, sizeof(int) * 2 + sizeof(unsigned long long), st));
   unsigned long long* d_att = reinterpret_cast<unsigned long long*>(d_status + 2);

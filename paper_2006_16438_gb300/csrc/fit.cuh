@@ -7,10 +7,12 @@ namespace cpa {
 
 size_t fit_buffers_bytes(int D, int r);
 // Enqueue the fit of [[lambda; A_1..A_D]] against X; result in *fit_dev (device).
-// scratch: fit_buffers_bytes(D, r) bytes of device memory.
+// scratch: fit_buffers_bytes(D, r) bytes of device memory; S: block-ordered sums of
+// width >= gram_sums_width(r) (the Grams and the inner product <X, M>, so the fit is
+// the same bit for bit at every run).
 template <class FT>
 int fit_enqueue(const cpa_index* X, const FactorPtrs& F, const double* lambda, int r, double* scratch,
-                double* fit_dev, cudaStream_t st);
+                const BlockSums& S, double* fit_dev, cudaStream_t st);
 
 // Stratified element sample of the estimated fit (Section 5.4), drawn once and kept
 // on the device: coords (D rows of int32, row m at coords + m * stride), xs (values, the

@@ -19,13 +19,24 @@ namespace {
 
 using cpa::SmallFactor;
 
-// Largest scratch this entry point uses: r <= 64 (cpa::kMaxRank).
-constexpr size_t kScratchBytes = 128 * 1024;
+// Largest scratch this entry point uses: r <= 64 (cpa::kMaxRank).  Layout: the r x r
+// Gram, its factorisation, a warning word, then the block partial sums of the Gram
+// (the rest of the array: at least 57 blocks at r = 64, the full grid at r <= 36).
+constexpr size_t kScratchBytes = 1024 * 1024;
 constexpr size_t kGramOff = 0;
 constexpr size_t kFactorOff = 32 * 1024;  // r*r doubles <= 32 KiB before it
 constexpr size_t kWarnOff = kFactorOff + ((sizeof(SmallFactor) + 255) / 256) * 256;
+constexpr size_t kSumsOff = kWarnOff + 256;
 static_assert(sizeof(double) * cpa::kMaxRank * cpa::kMaxRank <= kFactorOff, "Gram does not fit");
-static_assert(kWarnOff + 256 <= kScratchBytes, "scratch layout exceeds the array");
+static_assert(kSumsOff + cpa::block_sums_bytes(32, cpa::kMaxRank * (cpa::kMaxRank + 1) / 2) <= kScratchBytes,
+              "scratch layout exceeds the array");
+
+// Blocks of the Gram whose partial sums fit the rest of the array at rank r.
+int sums_blocks(int r) {
+  const size_t width = (size_t)cpa::gram_sums_width(r);
+  const size_t fit = (kScratchBytes - kSumsOff - 256) / (sizeof(double) * width);
+  return (int)(fit < (size_t)cpa::kSumMaxBlocks ? fit : (size_t)cpa::kSumMaxBlocks);
+}
 
 static __device__ __align__(256) unsigned char g_lev_scratch[kScratchBytes];
 
@@ -63,10 +74,13 @@ extern "C" int cpa_leverage_noalloc(const double* A, int64_t n, int32_t r, doubl
   double* G = reinterpret_cast<double*>(b + kGramOff);
   SmallFactor* f = reinterpret_cast<SmallFactor*>(b + kFactorOff);
   int* warn = reinterpret_cast<int*>(b + kWarnOff);
-  // the array keeps the previous call's contents: clear what accumulates
-  CPA_CUDA_TRY(cudaMemsetAsync(G, 0, sizeof(double) * r * r, st));
+  const cpa::BlockSums sums = cpa::block_sums_at(b + kSumsOff, sums_blocks(r));
+  // the array keeps the previous call's contents: clear the warning word and the
+  // ticket of the block sums (re-armed by every completed Gram, cleared here in case
+  // an earlier launch did not complete)
   CPA_CUDA_TRY(cudaMemsetAsync(warn, 0, sizeof(int), st));
-  CPA_TRY(cpa::gram_rows<double>(A, n, r, G, st));
+  CPA_CUDA_TRY(cudaMemsetAsync(sums.ticket, 0, sizeof(unsigned), st));
+  CPA_TRY(cpa::gram_rows<double>(A, n, r, G, sums, st));
   CPA_TRY(cpa::factor_spd(G, r, 1, 1, 1e-12, f, warn, CPA_WARN_RANK_DEFICIENT_LEV, st));
   CPA_TRY(cpa::lev_rows<double>(A, n, r, f, lev, nullptr, nullptr, (double*)nullptr, st));
   int hwarn = 0;

@@ -907,11 +907,10 @@ int skrp_lev(const SampleParams& P, SampleBuffers& B, cudaStream_t st, bool sort
   const size_t rsm = sizeof(uint64_t) * 2 * (size_t)nsum + sizeof(uint32_t) * 4 * (kGuide + 1);
   const int staged = rsm <= kRndSmemMax && nsum < (1ll << 31) ? 1 : 0;
   {
-    static bool attr = false;
-    if (!attr) {
-      CPA_CUDA_TRY(cudaFuncSetAttribute(k_rnd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRndSmemMax));
-      attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    CPA_CUDA_TRY(set_attr_once(attr, [] {
+      return cudaFuncSetAttribute(k_rnd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRndSmemMax);
+    }));
   }
   // a few warps per SM: the random slots come from a queue, and a warp's last slots
   // (one sequence of attempts each) set its length

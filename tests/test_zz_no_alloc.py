@@ -49,3 +49,43 @@ def test_leverage_noalloc_rejects_rank_above_scratch():
     A = torch.zeros((100, 65), dtype=torch.float64, device="cuda")
     lev = torch.empty(100, dtype=torch.float64, device="cuda")
     assert _call_noalloc(lib, A, lev) == binding.ERR_UNSUPPORTED
+
+
+def test_leverage_noalloc_allocates_no_device_memory():
+    """After a first call on the device (which looks up the array's address), a call
+    leaves the device's free memory unchanged: the library allocated nothing."""
+    lib = binding.load()
+    g = np.random.default_rng(7)
+    A = torch.from_numpy(g.standard_normal((20000, 25))).cuda()
+    lev = torch.empty(20000, dtype=torch.float64, device="cuda")
+    assert _call_noalloc(lib, A, lev) >= 0
+    torch.cuda.synchronize()
+    free_before, _ = torch.cuda.mem_get_info()
+    assert _call_noalloc(lib, A, lev) >= 0
+    torch.cuda.synchronize()
+    free_after, _ = torch.cuda.mem_get_info()
+    assert free_after == free_before
+
+
+def test_leverage_noalloc_binding_checks_and_matches():
+    """The Python wrapper: with and without a supplied output, the same scores as
+    cpa_leverage; a supplied output of the wrong type, length or layout is refused
+    before the library writes through its pointer."""
+    g = np.random.default_rng(11)
+    A = torch.from_numpy(g.standard_normal((3000, 25))).cuda()
+    ref, _ = binding.cpa_leverage(A)
+    lev, rc = binding.cpa_leverage_noalloc(A)
+    assert rc >= 0
+    assert (lev - ref).abs().max().item() / ref.abs().max().item() < 1e-11
+    out = torch.full((3000,), -1.0, dtype=torch.float64, device="cuda")
+    lev2, rc2 = binding.cpa_leverage_noalloc(A, out)
+    assert rc2 >= 0 and lev2.data_ptr() == out.data_ptr()
+    assert (out - ref).abs().max().item() / ref.abs().max().item() < 1e-11
+    with pytest.raises(TypeError):
+        binding.cpa_leverage_noalloc(A, torch.empty(3000, dtype=torch.float32, device="cuda"))
+    with pytest.raises(ValueError):
+        binding.cpa_leverage_noalloc(A, torch.empty(2999, dtype=torch.float64, device="cuda"))
+    with pytest.raises(ValueError):
+        binding.cpa_leverage_noalloc(A, torch.empty(6000, dtype=torch.float64, device="cuda")[::2])
+    with pytest.raises(ValueError):
+        binding.cpa_leverage_noalloc(A, torch.empty(3000, dtype=torch.float64))
