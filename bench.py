@@ -1,18 +1,23 @@
 """Benchmark of the GB300 CP-ARLS-LEV hot path.
 
-Workload (default): the 183 x 24 x 1140 x 1717 planted count tensor with about
-3.31M nonzeros (the shape and nonzero count of the paper's Uber tensor, Table 6.1;
-synthetic, planted rank 25, Zipf(1.1) popularity), CP rank 25, s = 2^17 samples
-per least-squares problem, hybrid threshold tau = 1/s, FP64.
+Workload (default): the 8,211,298 x 176,962 x 8,116,559 planted log(1 + count)
+tensor with about 4.69e9 nonzeros (the shape and nonzero count of the paper's Reddit
+tensor, Table 6.1; synthetic, planted rank 25, Zipf(1.2) popularity, generated on the
+GPU), CP rank 25, s = 2^17 samples per least-squares problem, hybrid threshold
+tau = 1/s, range-finder start and estimated fit as the paper runs this size.
 
-One step = one epoch of Alg. 3: eta = 5 outer iterations, each updating all 4 modes
-(sampling, sampled MTTKRP, solve, leverage refresh), then the exact fit -- i.e. 20
-mode updates through one cp_arls_lev call that continues the decomposition
-(iter_offset advances).  value = mode updates per second over the timed steps,
-inputs resident in HBM; L2 is flushed (a 256 MiB write) between timed steps.
+One step = one epoch of Alg. 3: eta = 5 outer iterations, each updating all 3 modes
+(sampling, sampled Gram and its factorisation, sampled MTTKRP with the solve folded
+in, leverage refresh), then the estimated fit -- 15 mode updates through one
+cp_arls_lev call that continues the decomposition (iter_offset advances).  value =
+FP64 mode updates per second over the timed steps, inputs resident in HBM (the index,
+145 GB, far larger than L2).  The mixed-precision series, the end-to-end series
+through host buffers and the oracle on the host cores are reported beside it.
 
---impl reference times the FP64 CPU oracle (the paper's algorithm written plainly)
-on the same workload and prints the same JSON line with "impl": "reference".
+--workload amazon: the 1.74e9-nonzero Amazon-shaped tensor; --workload uber: the
+183 x 24 x 1140 x 1717 Uber-shaped tensor (3.3M nonzeros, FP64, exact fit) with the
+batched and equal-fit comparisons.  --impl reference times the FP64 CPU oracle and
+prints the same JSON line with "impl": "reference".
 """
 from __future__ import annotations
 
@@ -32,7 +37,7 @@ if ROOT not in sys.path:
 
 import numpy as np  # noqa: E402
 
-METRIC = "CP-ARLS-LEV mode-updates/sec (sampled-MTTKRP HBM GB/s in roofline)"
+METRIC = "CP-ARLS-LEV mode-updates/sec and sampled-MTTKRP HBM GB/s at equal fit vs FP64 GPU path"
 UNIT = "mode-updates/s"
 RANK, SAMPLES, TAU_EXP, ETA = 25, 2 ** 17, 17, 5
 WORKLOAD = "uber-shaped 183x24x1140x1717 planted counts, ~3.31M nnz, r=25, s=2^17, tau=2^-17, FP64"
@@ -48,20 +53,24 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision series")
     p.add_argument("--no-equal-fit", action="store_true", help="skip the equal-fit comparison")
-    p.add_argument("--equal-fit-restarts", type=int, default=16)
-    p.add_argument("--equal-fit-max-epochs", type=int, default=40)
-    p.add_argument("--equal-fit-fixed-epochs", type=int, default=30)
+    p.add_argument("--equal-fit-restarts", type=int, default=32)
+    p.add_argument("--equal-fit-epochs", type=int, default=30)
     p.add_argument("--no-batched", action="store_true", help="skip the 64-problem batched comparison")
     p.add_argument("--batched-problems", type=int, default=64)
     p.add_argument("--cpu-sample-updates", type=int, default=4,
                    help="mode updates the CPU baseline times (bounded sample)")
-    p.add_argument("--workload", default="uber", choices=["uber", "amazon", "reddit"],
-                   help="uber: the default line; amazon: the 4.8M x 1.8M x 1.8M, 1.7e9-nonzero tensor "
-                        "(mixed precision, generated on the GPU)")
-    p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
-                   help="arithmetic of the billion-nonzero workloads")
-    p.add_argument("--amazon-fraction", type=float, default=1.0,
+    p.add_argument("--workload", default="reddit", choices=["uber", "amazon", "reddit"],
+                   help="reddit (default): the 8.2M x 177K x 8.1M, 4.7e9-nonzero tensor; amazon: the "
+                        "4.8M x 1.8M x 1.8M, 1.7e9-nonzero tensor (both generated on the GPU); uber: the "
+                        "183 x 24 x 1140 x 1717, 3.3M-nonzero tensor")
+    p.add_argument("--fit-samples", type=int, default=1 << 27,
+                   help="elements of the estimated fit's sample (billion-nonzero workloads)")
+    p.add_argument("--fraction", "--amazon-fraction", dest="fraction", type=float, default=1.0,
                    help="fraction of the amazon- or reddit-shaped tensor's events (dims kept)")
+    p.add_argument("--cpu-fraction", type=float, default=1.0 / 1024,
+                   help="fraction of the events in the oracle's same-shape tensor (billion-nonzero workloads)")
+    p.add_argument("--cpu-procs", type=int, default=0,
+                   help="oracle processes of the CPU baseline (0: all host cores, as memory allows)")
     return p.parse_args()
 
 
@@ -178,6 +187,7 @@ def krp_gram_flops(stats, d):
 # 152 SMs x 2 FP64 FMA/clk (resp. 128 FP32 FMA/clk) x 2 flops x 2.07 GHz.
 SMS, SM_MAX_GHZ = 152, 2.07
 FP64_PEAK_TFLOPS = SMS * 2 * 2 * SM_MAX_GHZ / 1000.0
+FP64_OPS_PEAK = SMS * 2 * SM_MAX_GHZ / 1000.0  # FP64 instructions (multiply or FMA) per second, x1e12
 FP32_PEAK_TFLOPS = SMS * 128 * 2 * SM_MAX_GHZ / 1000.0
 TF32_PER_BF16 = 1.1 / 2.25  # nominal dense tensor rates of the part
 
@@ -258,6 +268,8 @@ def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
+        if args.workload in LARGE:
+            return run_reference_large(args, LARGE[args.workload], rank)
         return run_reference(args, rank)
     if args.workload in LARGE:
         return run_large(args, LARGE[args.workload], rank, world, local)
@@ -416,9 +428,8 @@ def main():
     if not args.no_batched and rank == 0:
         line["batched"] = batched(cpa, args, stream)
     if mixed is not None and not args.no_equal_fit:
-        line["mixed_precision"]["equal_fit"] = equal_fit(cpa, coo, seed, stream,
-                                                             args.equal_fit_restarts, args.equal_fit_max_epochs,
-                                                             args.equal_fit_fixed_epochs)
+        line["mixed_precision"]["equal_fit"] = equal_fit(cpa, coo, seed, stream, args.equal_fit_restarts,
+                                                         args.equal_fit_epochs)
     if rank == 0 and not args.no_e2e:
         line["e2e"] = e2e(cpa, coo, init, args)
     if rank == 0 and not args.no_cpu_baseline and world == 1:
@@ -442,20 +453,38 @@ LARGE = {
     "reddit": {"name": "reddit-shaped", "dims": (8_211_298, 176_962, 8_116_559), "nnz": 4_690_000_000,
                "events_per_nnz": 2.9, "zipf": 1.2, "log_counts": True, "values": "log(1 + count)"},
 }
+# The oracle's time per mode update on the full shape (Householder QR of two factors
+# of ~8M rows) is about a minute on one core, so the reference arm runs it on the
+# Reddit-shaped model with every dimension divided by this and the events by its cube.
+REF_SHRINK = 16
+
+
+def large_workload_name(spec, nnz, frac):
+    return (f"{spec['name']} {'x'.join(str(n) for n in spec['dims'])} planted {spec['values']}, {nnz} nnz"
+            f"{'' if frac == 1.0 else f' ({frac:g} of the events)'}, r=25, s=2^17, tau=2^-17, range-finder "
+            "start, estimated fit 2^27")
+
+
+def large_mttkrp_bytes(st, dims, b_f):
+    """Algorithmic bytes of the sampled MTTKRP over the updates of `st`: per kept
+    sample its key, weight and probe (32 B) and its d = 2 factor rows (2 r b_f); per
+    sampled nonzero i_k and its FP32 value (8 B); per update the n_k x r output rows."""
+    n_up = st["mode_updates"]
+    per_mode = sum(dims) * RANK * b_f * (n_up // len(dims))
+    return st["sbar_total"] * (32 + 2 * RANK * b_f) + st["nnz_sampled_total"] * 8 + per_mode
 
 
 def run_large(args, spec, rank, world, local):
     """A billion-nonzero planted tensor generated on the GPU (int32 COO, FP32 values):
-    the 4,821,207 x 1,774,269 x 1,805,187 counts with Zipf(1.1) popularity (about
-    1.74e9 nonzeros) or the 8,211,298 x 176,962 x 8,116,559 log(1 + count) values with
-    Zipf(1.2) popularity (about 4.69e9 nonzeros); r = 25, s = 2^17, tau = 2^-17, mixed
-    precision, the paper's setting for these sizes: range-finder start (App. F, s_init
-    = 1e5) and the estimated fit (Sec. 5.4, 2^27 stratified samples).  One step = one
-    epoch: eta = 5 outer iterations (15 mode updates) and the estimated fit, one
-    cp_arls_lev call continuing the run.  A second series with stage events gives the
-    stage times and the sampled MTTKRP's algorithmic bytes per second.  The COO is
-    dropped once the index is built; the device memory in use during the runs is
-    reported."""
+    by default the 8,211,298 x 176,962 x 8,116,559 log(1 + count) tensor with Zipf(1.2)
+    popularity (about 4.69e9 nonzeros), or the 4,821,207 x 1,774,269 x 1,805,187
+    counts with Zipf(1.1) (about 1.74e9); r = 25, s = 2^17, tau = 2^-17, the paper's
+    setting for these sizes: range-finder start (App. F, s_init = 1e5) and the
+    estimated fit (Sec. 5.4, 2^27 stratified samples).  One step = one epoch: eta = 5
+    outer iterations (15 mode updates) and the estimated fit, one cp_arls_lev call
+    continuing the run.  The headline series is FP64; the mixed-precision series
+    starts from the same factors.  One further epoch with stage events gives the stage
+    times and the sampled MTTKRP's rates.  The COO is dropped once the index is built."""
     import torch
     import paper_2006_16438_gb300 as cpa
     from synth import gpu as sgpu
@@ -464,99 +493,168 @@ def run_large(args, spec, rank, world, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     stream = torch.cuda.current_stream()
-    frac = args.amazon_fraction
+    frac = args.fraction
     dims = spec["dims"]
     t0 = time.perf_counter()
     idx, vals = sgpu.planted_cp_tensor_gpu(dims, RANK, events=int(spec["events_per_nnz"] * spec["nnz"] * frac),
                                            seed=rank, zipf_alpha=spec["zipf"], log_counts=spec["log_counts"])
     torch.cuda.synchronize()
-    torch.cuda.empty_cache()
+    torch.cuda.empty_cache()  # the generator's cached blocks: the build needs the room
     gen_s = time.perf_counter() - t0
+    nnz = int(vals.numel())
+    coo_bytes = sum(int(i.numel()) * 4 for i in idx) + nnz * 4
     t0 = time.perf_counter()
     index = cpa.cpa_index_build(dims, device_tensors=(idx, vals))
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
-    nnz = int(vals.numel())
     del idx, vals
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     g = torch.Generator(device="cuda")
     g.manual_seed(1000 + rank)
-    fs = [cpa.cpa_rrf_init(index, k, torch.randn(100000, RANK, dtype=torch.float64, device="cuda", generator=g),
-                           seed=k) for k in range(3)]
-    lam = torch.empty(RANK, dtype=torch.float64, device="cuda")
-    fitd = torch.empty(1, dtype=torch.float64, device="cuda")
-    s, tau, it = SAMPLES, 2.0 ** -TAU_EXP, [0]
-    prec = cpa.binding.FP64 if args.precision == "fp64" else cpa.binding.MIXED
-
-    def step(profile=0):
-        res = cpa.cp_arls_lev(index, None, rank=RANK, samples=s, tau=tau, iters=ETA, seed=rank, iter_offset=it[0],
-                              out=(fs, lam, fitd), precision=prec, fit_mode=cpa.binding.FIT_ESTIMATED,
-                              fit_samples=1 << 27, profile=profile)
-        it[0] += ETA
-        return res
-
-    for _ in range(args.warmup):
-        step()
+    init = [cpa.cpa_rrf_init(index, k, torch.randn(100000, RANK, dtype=torch.float64, device="cuda", generator=g),
+                             seed=k) for k in range(3)]
     torch.cuda.synchronize()
-    torch.cuda.empty_cache()
-    free_b, total_b = torch.cuda.mem_get_info()
-    clocks = ClockSampler(local)
-    clocks.start()
-    if world > 1:
-        torch.distributed.barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    launches = 0
-    e0.record(stream)
-    for _ in range(args.steps):
-        res = step()
-        launches = launches + res.stats["kernel_launches"] if res.stats["kernel_launches"] >= 0 else launches
-    e1.record(stream)
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    total_ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
-    updates = args.steps * ETA * 3
-    value = job_throughput(updates, world, total_ms)
-    prof = step(profile=1)
-    st = prof.stats
+    s, tau = SAMPLES, 2.0 ** -TAU_EXP
     n_up = ETA * 3
+
+    def series(prec):
+        fs = [a.clone() for a in init]
+        lam = torch.empty(RANK, dtype=torch.float64, device="cuda")
+        fitd = torch.empty(1, dtype=torch.float64, device="cuda")
+        it = [0]
+
+        def step(profile=0):
+            res = cpa.cp_arls_lev(index, None, rank=RANK, samples=s, tau=tau, iters=ETA, seed=rank,
+                                  iter_offset=it[0], out=(fs, lam, fitd), precision=prec,
+                                  fit_mode=cpa.binding.FIT_ESTIMATED, fit_samples=args.fit_samples, profile=profile)
+            it[0] += ETA
+            return res
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local)
+        clocks.start()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        launches = 0
+        evs[0].record(stream)
+        est = []
+        tag = "fp64_epoch" if prec == cpa.binding.FP64 else "mixed_epoch"
+        for i in range(args.steps):
+            torch.cuda.nvtx.range_push(tag)  # lets a profiler select the timed epochs
+            res = step()
+            torch.cuda.nvtx.range_pop()
+            evs[i + 1].record(stream)
+            est.append(res.fit)
+            launches = launches + res.stats["kernel_launches"] if res.stats["kernel_launches"] >= 0 else launches
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+        total_ms = max_over_ranks(sum(step_ms), world, "cuda")
+        prof = step(profile=1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        exact = cpa.cpa_fit(index, fs, lam)
+        exact_s = time.perf_counter() - t0
+        out = dict(total_ms=total_ms, step_ms=step_ms, launches=launches, clocks=clk, stats=prof.stats,
+                   est_fit=est[-1] if est else None, exact_fit=exact, exact_fit_s=exact_s,
+                   epochs=args.warmup + args.steps + 1)
+        del fs
+        return out
+
+    f64 = series(cpa.binding.FP64)
+    mixed = None if args.no_mixed else series(cpa.binding.MIXED)
+    updates = args.steps * n_up
+    value = job_throughput(updates, world, f64["total_ms"])
     peaks, peak_src = load_peaks()
-    # fused probe + KRP + MTTKRP bytes (b_f = 4, values FP32): per kept sample its key,
-    # weight and probe (32 B) and d = 2 factor rows; per sampled nonzero i_k and value
-    mk_bytes = st["sbar_total"] * (32 + 2 * RANK * 4) + st["nnz_sampled_total"] * 8 + \
-        sum(dims) * RANK * 4 * ETA
-    mk_ms = st["stage_ms"][2]
-    mk_gbs = mk_bytes / (mk_ms / 1000.0) / 1e9 if mk_ms > 0 else None
+
+    def stage_table(st):
+        return {nm: float(st["stage_ms"][i] / n_up) for i, nm in enumerate(STAGES)}
+
+    def mttkrp_rates(st, b_f):
+        ms = st["stage_ms"][2]
+        byts = large_mttkrp_bytes(st, dims, b_f)
+        gbs = byts / (ms / 1000.0) / 1e9 if ms > 0 else None
+        return {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": gbs / peaks["hbm_gbs"] if gbs else None,
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+                "bytes_per_update": byts / n_up, "ms_per_update": ms / n_up,
+                "sampled_nonzeros_per_update": st["nnz_sampled_total"] / n_up,
+                "row_additions_per_s": st["nnz_sampled_total"] / (ms / 1000.0) if ms > 0 else None}
+
+    st64 = f64["stats"]
+    mk64 = mttkrp_rates(st64, 8)
+    # the headline roofline: the sampled MTTKRP's algorithmic bytes per second against
+    # the measured HBM copy rate (the metric's GB/s).  Its on-chip limits are given
+    # beside: the FP64 multiplies (r per sampled nonzero; 2 r + 1 Khatri-Rao multiplies
+    # and r^2 multiply-adds of the folded solve per sample) against the FP64 pipe
+    # (152 SMs x 2 FP64 instructions per clock per SM x 2.07 GHz), and the row additions
+    # (one FP64 atomic row of r words per sampled nonzero).
+    fp64_ops = st64["nnz_sampled_total"] * RANK + st64["sbar_total"] * (2 * RANK + 1 + RANK * RANK)
+    ms2 = st64["stage_ms"][2]
+    fp64_rate = fp64_ops / (ms2 / 1000.0) / 1e12 if ms2 > 0 else None
+    roof = dict(mk64)
+    roof.update({
+        "kernel": "sampled MTTKRP, FP64 (k_slab_prep: probe + sampled Khatri-Rao rows times the inverse sampled "
+                  "Gram; k_slab_light + k_slab_heavy: FP64 products added into row slabs of A_k)",
+        "traffic": captured_traffic("k_slab_light<double>", "paper_2006_16438_gb300/csrc/mttkrp.cu"),
+        "traffic_unit": "DRAM bytes per launch (ncu, profiles/traffic.json)",
+        "fp64_pipe": {"achieved": fp64_rate, "peak": FP64_OPS_PEAK, "unit": "T FP64 instructions/s",
+                      "frac": fp64_rate / FP64_OPS_PEAK if fp64_rate else None,
+                      "peak_source": "derived: 152 SMs x 2 FP64 lanes/clk x 2.07 GHz"}})
     nfib = [index.nfib(k) for k in range(3)]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 (factors, Grams, sampled products; FP64 factorisations)", "data": "synthetic",
-        "config": {"workload": f"{spec['name']} {'x'.join(str(n) for n in dims)} planted {spec['values']}, "
-                               f"{nnz} nnz, r=25, s=2^17, tau=2^-17, mixed precision, range-finder start, "
-                               "estimated fit 2^27",
+        "ms_per_step": f64["total_ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": large_workload_name(spec, nnz, frac),
                    "step": "1 epoch = 5 outer iterations x 3 mode updates + estimated fit",
                    "l2": f"inputs far larger than L2 ({index.device_bytes() / 1e9:.0f} GB of index)",
                    "parallelism": f"{world} independent replicas" if world > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "kernel": "sampled MTTKRP (modes whose M exceeds 128 MB: row slabs, "
-                                               "k_slab_prep + k_slab_light + k_slab_heavy; the others one pass, "
-                                               "k_tnsr_mttkrp + k_tnsr_heavy)",
-                     "achieved": mk_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": (mk_gbs / peaks["hbm_gbs"]) if mk_gbs else None, "traffic": None,
-                     "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
-                     "bytes_per_update": mk_bytes / n_up, "ms_per_update": mk_ms / n_up},
-        "stages_ms_per_update": {nm: float(st["stage_ms"][i] / n_up) for i, nm in enumerate(STAGES)},
-        "nnz_sampled_per_update": st["nnz_sampled_total"] / n_up,
-        "estimated_fit": prof.fit,
-        "memory": {"index_bytes": index.device_bytes(), "fibres_per_mode": nfib,
-                   "device_bytes_in_use": total_b - free_b, "device_bytes_total": total_b},
+        "roofline": roof,
+        "mttkrp_hbm": mk64,
+        "stages_ms_per_update": stage_table(st64),
+        "fit": {"estimated": f64["est_fit"], "exact": f64["exact_fit"], "epochs": f64["epochs"]},
+        "clocks": f64["clocks"],
+        "step_ms": {"min": min(f64["step_ms"]), "median": statistics.median(f64["step_ms"]),
+                    "max": max(f64["step_ms"])},
+        "gpu_launches": f64["launches"],
+        "memory": {"index_bytes": index.device_bytes(), "fibres_per_mode": nfib},
         "generate_s": gen_s, "index_build_s": build_s,
-        "clocks": clk,
-        "gpu_launches": launches,
-        "e2e": None, "cpu_baseline": None,
-        "note": "e2e and cpu_baseline are given for the default workload; the host oracle cannot hold this tensor",
     }
+    if mixed is not None:
+        stm = mixed["stats"]
+        mv = job_throughput(updates, world, mixed["total_ms"])
+        line["mixed_precision"] = {
+            "value": mv, "unit": UNIT, "speedup_vs_fp64": mv / value,
+            "fit": {"estimated": mixed["est_fit"], "exact": mixed["exact_fit"]},
+            "exact_fit_diff_vs_fp64": mixed["exact_fit"] - f64["exact_fit"],
+            "stages_ms_per_update": stage_table(stm), "mttkrp_hbm": mttkrp_rates(stm, 4),
+            "clocks": mixed["clocks"], "gpu_launches": mixed["launches"],
+            "note": "same range-finder start and epochs as the FP64 series; FP32 factors, Grams and sampled "
+                    "products, FP64 factorisations and leverage; exact fits (Eq. 5.1) after the same epochs"}
+    free_b, total_b = torch.cuda.mem_get_info()
+    line["memory"]["device_bytes_in_use"] = total_b - free_b
+    if rank == 0 and not args.no_e2e:
+        line["e2e"] = e2e_large(cpa, index, init, args, coo_bytes, gen_s, build_s)
+    del init
+    index.free()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline_large(spec, args)
+    if rank == 0 and mixed is not None and not args.no_equal_fit:
+        # equal fit needs many restarts with an exact fit per epoch: measured on the
+        # Uber-shaped tensor, where an epoch takes milliseconds
+        import synth
+        line["mixed_precision"]["equal_fit"] = equal_fit(cpa, synth.uber_like_tensor(0), 0, stream,
+                                                         args.equal_fit_restarts, args.equal_fit_epochs)
+    if rank == 0 and not args.no_batched:
+        line["batched"] = batched(cpa, args, stream)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -564,20 +662,178 @@ def run_large(args, spec, rank, world, local):
     return 0
 
 
-def batched(cpa, args, stream):
+def e2e_large(cpa, index, init, args, coo_bytes, gen_s, build_s):
+    """The FP64 series through cp_arls_lev with HOST factor buffers in pinned memory:
+    every step copies the factors in, runs one epoch on the resident index and copies
+    the factors, lambda and the fit back (the library's own copies, inside the timed
+    region).  The index is the resident form of the tensor, built once (its one-time
+    cost is reported beside)."""
+    import torch
+    keep = [a.cpu().pin_memory() for a in init]
+    fs = [t.numpy() for t in keep]
+    fac_bytes = sum(a.nbytes for a in fs)
+    s, tau = SAMPLES, 2.0 ** -TAU_EXP
+
+    def step(i):
+        return cpa.cp_arls_lev(index, fs, rank=RANK, samples=s, tau=tau, iters=ETA, seed=0, iter_offset=ETA * i,
+                               on_device=False, inplace=True, precision=cpa.binding.FP64,
+                               fit_mode=cpa.binding.FIT_ESTIMATED, fit_samples=args.fit_samples)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        step(args.warmup + i)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"value": ETA * 3 * args.steps / dt, "unit": UNIT, "h2d_bytes_per_step": int(fac_bytes),
+            "d2h_bytes_per_step": int(fac_bytes + 8 * RANK + 8), "steps": args.steps,
+            "note": "cp_arls_lev on host factor buffers (pinned), FP64, every step's copies in the timed region; "
+                    "the tensor is resident as its index",
+            "one_time": {"coo_bytes": coo_bytes, "generate_s": gen_s, "index_build_s": build_s}}
+
+
+def _oracle_update_worker(task):
+    """One mode update of the oracle (in a spawned process): loads the COO saved by the
+    parent, builds the oracle's index and times oracle.mode_update."""
+    path, dims, k, seed = task
+    import oracle
+    import synth
+    z = np.load(path)
+    coo = synth.Coo(tuple(dims), [z[f"i{m}"] for m in range(len(dims))], z["v"])
+    idx = oracle.Index(coo)
+    fs = synth.gaussian_factors(dims, RANK, seed=seed)
+    t0 = time.perf_counter()
+    oracle.mode_update(idx, fs, k, rank=RANK, samples=SAMPLES, tau=2.0 ** -TAU_EXP, seed=seed, it=0)
+    return time.perf_counter() - t0
+
+
+def _mem_available_bytes():
+    try:
+        with open("/proc/meminfo") as f:
+            for ln in f:
+                if ln.startswith("MemAvailable:"):
+                    return int(ln.split()[1]) * 1024
+    except Exception:
+        pass
+    return 0
+
+
+def cpu_baseline_large(spec, args):
+    """The oracle as it stands on the host cores: one mode update per process, all
+    processes at once, on a tensor of the same shape (so the factor matrices and
+    their leverage QRs are the full size) with 1/1024 of the planted model's events
+    (generated on the GPU by the same generator, seed 7)."""
+    import multiprocessing
+    import tempfile
+    import torch
+    from synth import gpu as sgpu
+    dims = spec["dims"]
+    frac = args.cpu_fraction
+    idx, vals = sgpu.planted_cp_tensor_gpu(dims, RANK, events=int(spec["events_per_nnz"] * spec["nnz"] * frac),
+                                           seed=7, zipf_alpha=spec["zipf"], log_counts=spec["log_counts"])
+    arrs = {f"i{m}": idx[m].cpu().numpy() for m in range(len(dims))}
+    arrs["v"] = vals.cpu().numpy().astype(np.float64)
+    nnz = int(vals.numel())
+    del idx, vals
+    torch.cuda.empty_cache()
+    tmp = tempfile.mkdtemp(prefix="cpa_oracle_")
+    path = os.path.join(tmp, "coo.npz")
+    np.savez(path, **arrs)
+    del arrs
+    # per process: the factors (and the oracle's copies of them) and its index
+    per_proc = 4 * sum(dims) * RANK * 8 + nnz * 64 + (1 << 30)
+    cores = os.cpu_count() or 1
+    procs = max(1, min(cores, args.cpu_procs or cores, int(0.6 * _mem_available_bytes() // per_proc)))
+    ctx = multiprocessing.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(procs) as pool:
+        times = pool.map(_oracle_update_worker, [(path, list(dims), p % 3, p) for p in range(procs)])
+    wall = time.perf_counter() - t0
+    try:
+        os.remove(path)
+        os.rmdir(tmp)
+    except OSError:
+        pass
+    return {"value": procs / max(times), "unit": UNIT, "cores": procs, "kind": "oracle",
+            "nproc": cores, "single_process_value": 1.0 / statistics.median(times),
+            "seconds_per_update": {"min": min(times), "median": statistics.median(times), "max": max(times)},
+            "wall_s": wall,
+            "sample": f"{procs} processes at once, one mode update each (modes cycled), FP64 oracle on a "
+                      f"{'x'.join(str(n) for n in dims)} tensor with {nnz} nnz ({frac:g} of the planted model's "
+                      "events), r=25, s=2^17, tau=2^-17; value = updates / slowest process's time"}
+
+
+def run_reference_large(args, spec, rank):
+    """--impl reference for the billion-nonzero workloads: the FP64 oracle on the host,
+    one mode update per step (modes cycled, the decomposition continuing), on the same
+    planted model with every dimension divided by REF_SHRINK and the events by its cube
+    (generated on the host) -- the full shape takes about a minute per update on one
+    core."""
+    import oracle
+    import synth
+    if rank != 0:
+        return 0
+    dims = tuple(max(RANK, n // REF_SHRINK) for n in spec["dims"])
+    events = int(spec["events_per_nnz"] * spec["nnz"] / REF_SHRINK ** 3)
+    coo = synth.planted_cp_tensor(dims, RANK, events=events, seed=0, zipf_alpha=spec["zipf"],
+                                  log_counts=spec["log_counts"])
+    idx = oracle.Index(coo)
+    fs = synth.gaussian_factors(dims, RANK, seed=0)
+    times = []
+    it = 0
+    for step in range(args.warmup + args.steps):
+        k = step % 3
+        t0 = time.perf_counter()
+        res = oracle.mode_update(idx, fs, k, rank=RANK, samples=SAMPLES, tau=2.0 ** -TAU_EXP, seed=0, it=it)
+        dt = time.perf_counter() - t0
+        fs[k] = res["A"]
+        if k == 2:
+            it += 1
+        if step >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = len(times) / total
+    wl = (f"{spec['name']} model with dimensions / {REF_SHRINK} ({'x'.join(str(n) for n in dims)}), "
+          f"{coo.nnz} nnz, r=25, s=2^17, tau=2^-17, FP64")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": wl, "step": "1 mode update"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "nproc": os.cpu_count(),
+                         "sample": f"1 mode update per step of the {wl} tensor (the oracle recomputes the "
+                                   "leverage of the other modes by Householder QR in every update)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def batched(cpa, args, stream, max_nnz=10 ** 7):
     """Many independent decompositions: the same epoch (5 outer iterations + fit) of
     every problem, run as sequential cp_arls_lev calls and as one batch graph
-    (cpa_batch_*, autotuned SM budget), from the same initial factors and offsets, in
-    FP64 and in mixed precision."""
+    (cpa_batch_*, autotuned), from the same initial factors and offsets, in FP64 and
+    in mixed precision.  The 64 problems (synth.batch_specs: 3- and 4-way, dims
+    log-uniform 1e2-1e5, nnz log-uniform 1e4-max_nnz, ranks 5-50) are generated on the
+    GPU."""
     import torch
     import synth
+    from synth import gpu as sgpu
     t0 = time.perf_counter()
-    probs = synth.batch_problems(args.batched_problems)
+    probs = []
+    for sp, idx, vals in sgpu.batch_problems_gpu(args.batched_problems, 0, max_nnz):
+        index = cpa.cpa_index_build(sp["dims"], device_tensors=(idx, vals))
+        nnz = int(vals.numel())
+        del idx, vals
+        probs.append(dict(index=index, dims=sp["dims"], nnz=nnz, rank=sp["rank"], samples=sp["samples"],
+                          tau=sp["tau"], seed=sp["seed"],
+                          init=synth.gaussian_factors(sp["dims"], sp["rank"], seed=sp["seed"])))
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
     gen_s = time.perf_counter() - t0
-    for p in probs:
-        p["index"] = cpa.cpa_index_build(p["coo"])
-        p["init"] = synth.gaussian_factors(p["coo"].dims, p["rank"], seed=p["seed"])
-    updates = sum(ETA * len(p["coo"].dims) for p in probs)
+    updates = sum(ETA * len(p["dims"]) for p in probs)
     reps = max(3, min(args.steps, 7))
 
     def timed(fn):
@@ -636,81 +892,63 @@ def batched(cpa, args, stream):
         batch.free()
         return res
 
-    return {"problems": len(probs), "total_nnz": int(sum(p["coo"].nnz for p in probs)),
-            "mode_updates_per_pass": updates, "passes": reps, "generate_s": gen_s,
-            "fp64": compare(cpa.binding.FP64), "mixed": compare(cpa.binding.MIXED),
-            "note": "fits after the same epochs with the same seeds; the few problems whose randomized "
-                    "iterations are unstable diverge under a different order of floating-point atomics, "
-                    "hence median and max of the fit differences",
-            "workload": "64 planted count tensors, 3-/4-way, dims log-uniform 1e2-1e5, nnz log-uniform "
-                        "1e4-1e6 (<= 10% of cells, >= 50 N_k/s), Zipf alpha U[1.0,1.3], rank 5-50, "
-                        "s = 2^14..2^17 capped at 1/128 of the fewest Khatri-Rao rows and >= 16 r, tau = 1/s; "
-                        "one pass = one epoch (5 outer iterations + exact fit) of every problem"}
+    out = {"problems": len(probs), "total_nnz": int(sum(p["nnz"] for p in probs)),
+           "largest_nnz": int(max(p["nnz"] for p in probs)),
+           "mode_updates_per_pass": updates, "passes": reps, "generate_s": gen_s,
+           "fp64": compare(cpa.binding.FP64), "mixed": compare(cpa.binding.MIXED),
+           "note": "fits after the same epochs with the same seeds (FP64: reproducible sums, so batched and "
+                   "sequential runs agree bit for bit; mixed: FP32 atomics, so a few unstable problems drift)",
+           "workload": f"{len(probs)} planted count tensors, 3-/4-way, dims log-uniform 1e2-1e5, nnz log-uniform "
+                       f"1e4-{max_nnz:.0e} (<= 10% of cells, >= 50 N_k/s), Zipf alpha U[1.0,1.3], rank 5-50, "
+                       "s = 2^14..2^17 capped at 1/128 of the fewest Khatri-Rao rows and >= 16 r, tau = 1/s; "
+                       "one pass = one epoch (5 outer iterations + exact fit) of every problem"}
+    for p in probs:
+        p["index"].free()
+    return out
 
 
-def equal_fit(cpa, coo, seed, stream, restarts, max_epochs, fixed_epochs):
-    """Mixed precision against FP64 at equal fit, over `restarts` random initial
-    factors (Gaussian, Section 6), paired by restart:
-      - converged: each run to the stopping rule of Alg. 3 (exact fit after every
-        epoch of eta = 5 outer iterations; stop once the fit has not improved by more
-        than tol = 1e-4 for pi = 3 epochs), in FP64, in FP64 once more (the spread that
-        the order of floating-point atomics alone causes: the sampled rows of later
-        iterations depend on every bit of the factors) and in mixed precision;
-      - traces: `fixed_epochs` epochs in each precision, one call (one graph launch)
-        per epoch with the exact fit after it; the restart's target is the lower of the
-        two best fits minus 1e-4, a fit both precisions reach, and the time each takes
-        to first reach it gives the speedup at equal fit.
-    Times are CUDA events; each precision runs on its own index (so each keeps its
-    cached workspace and graphs), warmed up first.  A change of precision moves a
-    randomized trajectory as a change of seed does, so fits are compared as paired
-    differences (mean and standard error over restarts)."""
+def equal_fit(cpa, coo, seed, stream, restarts, epochs):
+    """Mixed precision against FP64 at equal fit on `coo` (r = 25, s = 2^17,
+    tau = 2^-17), over `restarts` random initial factors (Gaussian, Section 6), paired
+    by restart.  Per restart both precisions run `epochs` epochs (eta = 5 outer
+    iterations each), one cp_arls_lev call per epoch with the exact fit (Eq. 5.1)
+    after it, timed with CUDA events (fits included).  The restart's target is the
+    lower of the two best fits minus 1e-4, a fit both precisions reach; the time each
+    needs to first reach it gives the restart's speedup at equal fit (FP64 time /
+    mixed time).  A change of precision moves a randomized trajectory as a change of
+    seed does, so the speedup is a distribution over restarts: its median with a
+    bootstrap 95 % interval (4000 resamples of the restarts), its geometric mean, and
+    the per-epoch speedup are reported, with the paired differences of the best and
+    final fits."""
     import torch
     import synth
     s, tau = SAMPLES, 2.0 ** -TAU_EXP
     dims = coo.dims
     indices = {cpa.binding.FP64: cpa.cpa_index_build(coo), cpa.binding.MIXED: cpa.cpa_index_build(coo)}
 
-    def call(fs, lam, fitd, precision, iters, tol, offset):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        res = cpa.cp_arls_lev(indices[precision], None, rank=RANK, samples=s, tau=tau, iters=iters, seed=seed,
-                              tol=tol, patience=3, epoch_len=ETA, iter_offset=offset, out=(fs, lam, fitd),
-                              precision=precision)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        return res, e0.elapsed_time(e1)
-
-    def buffers(init):
-        fs = [torch.from_numpy(a).cuda() for a in init]
-        return fs, torch.empty(RANK, dtype=torch.float64, device="cuda"), torch.empty(1, dtype=torch.float64,
-                                                                                      device="cuda")
-
-    def converged(init, precision):
-        fs, lam, fitd = buffers(init)
-        res, ms = call(fs, lam, fitd, precision, ETA * max_epochs, 1e-4, 0)
-        return {"fit": res.fit, "epochs": res.stats["epochs"], "ms": ms}
-
     def trace(init, precision):
-        fs, lam, fitd = buffers(init)
+        fs = [torch.from_numpy(a).cuda() for a in init]
+        lam = torch.empty(RANK, dtype=torch.float64, device="cuda")
+        fitd = torch.empty(1, dtype=torch.float64, device="cuda")
         fits, ms = [], []
-        for ep in range(fixed_epochs):
-            res, t = call(fs, lam, fitd, precision, ETA, 0.0, ETA * ep)
+        for ep in range(epochs):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = cpa.cp_arls_lev(indices[precision], None, rank=RANK, samples=s, tau=tau, iters=ETA, seed=seed,
+                                  iter_offset=ETA * ep, out=(fs, lam, fitd), precision=precision)
+            e1.record(stream)
+            torch.cuda.synchronize()
             fits.append(res.fit)
-            ms.append(t)
+            ms.append(e0.elapsed_time(e1))
         return fits, ms
 
     warm = synth.gaussian_factors(dims, RANK, seed=999)
-    for prec in indices:  # workspace and graphs of both call shapes
-        converged(warm, prec)
+    for prec in indices:  # workspaces and graphs
         trace(warm, prec)
-    runs = {"fp64": [], "fp64_rerun": [], "mixed": []}
     tr = []
     for rs in range(restarts):
         init = synth.gaussian_factors(dims, RANK, seed=1000 + rs)
-        runs["fp64"].append(converged(init, cpa.binding.FP64))
-        runs["fp64_rerun"].append(converged(init, cpa.binding.FP64))
-        runs["mixed"].append(converged(init, cpa.binding.MIXED))
         f64, m64 = trace(init, cpa.binding.FP64)
         fmx, mmx = trace(init, cpa.binding.MIXED)
         target = min(max(f64), max(fmx)) - 1e-4
@@ -724,40 +962,34 @@ def equal_fit(cpa, coo, seed, stream, restarts, max_epochs, fixed_epochs):
         e64, t64 = reach(f64, m64)
         emx, tmx = reach(fmx, mmx)
         tr.append({"target": target, "best_fp64": max(f64), "best_mixed": max(fmx), "final_fp64": f64[-1],
-                   "final_mixed": fmx[-1], "epochs_fp64": e64, "epochs_mixed": emx, "ms_fp64": t64, "ms_mixed": tmx,
-                   "ms_per_epoch_fp64": sum(m64) / len(m64), "ms_per_epoch_mixed": sum(mmx) / len(mmx)})
-
-    def summary(rs):
-        f = np.array([r["fit"] for r in rs])
-        return {"fit_mean": float(f.mean()), "fit_sd": float(f.std(ddof=1)) if f.size > 1 else 0.0,
-                "epochs_mean": float(np.mean([r["epochs"] for r in rs])), "ms_total": sum(r["ms"] for r in rs),
-                "ms_per_epoch": sum(r["ms"] for r in rs) / sum(r["epochs"] for r in rs),
-                "fits": [round(r["fit"], 6) for r in rs], "epochs": [r["epochs"] for r in rs]}
+                   "final_mixed": fmx[-1], "epochs_fp64": e64, "epochs_mixed": emx, "ms_fp64": t64,
+                   "ms_mixed": tmx, "ms_per_epoch_fp64": sum(m64) / len(m64),
+                   "ms_per_epoch_mixed": sum(mmx) / len(mmx)})
+    for ix in indices.values():
+        ix.free()
+    ratios = np.array([t["ms_fp64"] / t["ms_mixed"] for t in tr])
+    g = np.random.default_rng(0)
+    boot = np.median(ratios[g.integers(0, ratios.size, size=(4000, ratios.size))], axis=1)
 
     def paired(xs, ys):
         d = np.array([x - y for x, y in zip(xs, ys)])
         se = float(d.std(ddof=1) / math.sqrt(d.size)) if d.size > 1 else 0.0
-        return {"mean": float(d.mean()), "se": se, "abs_median": float(np.median(np.abs(d))),
-                "identical": int(np.sum(np.abs(d) < 1e-12))}
+        return {"mean": float(d.mean()), "se": se, "abs_median": float(np.median(np.abs(d)))}
 
-    out = {k: summary(v) for k, v in runs.items()}
-    ratios = np.array([t["ms_fp64"] / t["ms_mixed"] for t in tr])
-    out.update({
-        "restarts": restarts, "max_epochs": max_epochs, "trace_epochs": fixed_epochs, "tol": 1e-4, "patience": 3,
-        "fit_diff_converged": paired([r["fit"] for r in runs["mixed"]], [r["fit"] for r in runs["fp64"]]),
-        "fit_diff_fp64_rerun": paired([r["fit"] for r in runs["fp64_rerun"]], [r["fit"] for r in runs["fp64"]]),
-        "fit_diff_best_in_trace": paired([t["best_mixed"] for t in tr], [t["best_fp64"] for t in tr]),
+    return {
+        "workload": f"{'x'.join(str(n) for n in dims)} planted counts, {coo.nnz} nnz, r=25, s=2^17, tau=2^-17",
+        "restarts": restarts, "epochs": epochs,
         "speedup_at_equal_fit": {"median": float(np.median(ratios)),
+                                 "ci95": [float(np.percentile(boot, 2.5)), float(np.percentile(boot, 97.5))],
                                  "geomean": float(np.exp(np.mean(np.log(ratios)))),
                                  "per_restart": [round(float(x), 3) for x in ratios]},
         "per_epoch_speedup": float(np.mean([t["ms_per_epoch_fp64"] for t in tr]) /
                                    np.mean([t["ms_per_epoch_mixed"] for t in tr])),
+        "fit_diff_best": paired([t["best_mixed"] for t in tr], [t["best_fp64"] for t in tr]),
+        "fit_diff_final": paired([t["final_mixed"] for t in tr], [t["final_fp64"] for t in tr]),
         "mixed_reaches_fp64_best": int(sum(t["best_mixed"] >= t["best_fp64"] - 1e-4 for t in tr)),
-        "traces": tr,
-        "note": "fit_diff_* = mixed - FP64 per restart (mean, standard error, median |diff|, count of identical "
-                "fits); speedup_at_equal_fit = FP64 time / mixed time to the restart's common target (the lower "
-                "best fit minus 1e-4), epoch-by-epoch calls with the exact fit"})
-    return out
+        "note": "fit_diff_* = mixed - FP64 per restart (mean, standard error, median |diff|); the target of a "
+                "restart is a fit both precisions reach (the lower best fit minus 1e-4)"}
 
 
 def e2e(cpa, coo, init, args):

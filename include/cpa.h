@@ -445,6 +445,15 @@ int cpa_solve(const double* G, const double* M, int64_t n, int32_t r, double* A,
 int cpa_fit(const cpa_index* index, const double* const* factors, const double* lambda,
             int32_t r, double* fit, void* stream);
 
+/* The three terms of the fit of Eq. 5.1 for the nonzeros of `index`:
+ * terms[0] = ||X||^2, terms[1] = <X, M>, terms[2] = ||M||^2 (host out, FP64), with
+ * M = [[lambda; A_1, ..., A_D]] (factors: host array of device pointers; lambda:
+ * device).  The first two are sums over the nonzeros, so the terms of tensors that
+ * hold disjoint parts of one tensor's nonzeros (the shards of a sharded run) add up
+ * to the whole tensor's; the third depends on the factors only.  Errors as cpa_fit. */
+int cpa_fit_terms(const cpa_index* index, const double* const* factors, const double* lambda,
+                  int32_t r, double* terms, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -11,6 +11,7 @@ from .binding import (  # noqa: F401
     Index, Result, CpaError, load, library_path, default_options,
     cpa_index_build, cpa_index_export, cp_arls_lev, cp_arls_lev_coo, cpa_mode_update, cp_als, Batch,
     cpa_philox4x64, cpa_leverage, cpa_leverage_noalloc, cpa_cdf, cpa_skrp_lev, cpa_sampled_mttkrp, cpa_solve, cpa_fit,
+    cpa_fit_terms,
     cpa_fit_sample, cpa_fit_estimate, FitSample, cpa_rrf_init,
     EXPORTED,
 )

@@ -45,7 +45,7 @@ EXPORTED = [
     "cpa_index_export", "cp_arls_lev", "cp_arls_lev_coo", "cpa_philox4x64", "cpa_leverage",
     "cpa_cdf", "cpa_skrp_lev", "cpa_sampled_mttkrp", "cpa_solve", "cpa_fit", "cpa_leverage_noalloc",
     "cpa_mode_update", "cp_als", "cpa_batch_create", "cpa_batch_run", "cpa_batch_info", "cpa_batch_free",
-    "cpa_fit_sample", "cpa_fit_estimate", "cpa_rrf_init", "cpa_index_device_bytes",
+    "cpa_fit_sample", "cpa_fit_estimate", "cpa_rrf_init", "cpa_index_device_bytes", "cpa_fit_terms",
 ]
 
 
@@ -136,6 +136,7 @@ def _declare(lib):
         "cpa_sampled_mttkrp": ([P, I32, P, I32, P, P, I64, P, P, P, P], I32),
         "cpa_solve": ([P, P, I64, I32, P, P, P], I32),
         "cpa_fit": ([P, P, P, I32, P, P], I32),
+        "cpa_fit_terms": ([P, P, P, I32, P, P], I32),
         "cpa_fit_sample": ([P, I64, D, U64, I32, P, P, P, P, P], I32),
         "cpa_rrf_init": ([P, I32, I64, U64, P, I32, P, P], I32),
         "cpa_fit_estimate": ([P, P, P, P, P, I64, P, P, I32, I32, P, P, P], I32),
@@ -290,9 +291,12 @@ class Result:
 def cp_arls_lev(index: Index, factors, *, rank, samples, tau=1.0, iters=10, epoch_len=5, patience=3,
                 tol=0.0, seed=0, iter_offset=0, fit_mode=FIT_EXACT, det_cap=1 << 24,
                 reject_cap=4096, on_device=True, profile=0, out=None, precision=FP64,
-                fit_samples=1 << 27, fit_alpha=0.5, distribution=DIST_LEVERAGE) -> Result:
+                fit_samples=1 << 27, fit_alpha=0.5, distribution=DIST_LEVERAGE, inplace=False) -> Result:
     """Alg. 3 on the GPU.  ``factors``: list of CUDA float64 tensors (n_k x rank), or
-    numpy arrays with on_device=False.  Returns a Result with new factor copies."""
+    numpy arrays with on_device=False (host buffers: the library copies them in and
+    the results out).  Returns a Result with new factor copies; with on_device=False
+    and inplace=True the caller's arrays (C-contiguous float64, e.g. views of pinned
+    memory) receive the results instead."""
     torch = _torch()
     o = default_options(rank=rank, samples=int(samples), tau=float(tau), iters=int(iters),
                         epoch_len=int(epoch_len), patience=int(patience), tol=float(tol),
@@ -314,7 +318,12 @@ def cp_arls_lev(index: Index, factors, *, rank, samples, tau=1.0, iters=10, epoc
                                 _ptr(fit_d), C.byref(stats))
         _check(rc, "cp_arls_lev")
         return Result(lam, fs, float(fit_d.item()), stats.as_dict(), rc)
-    fs = [np.ascontiguousarray(f, dtype=np.float64).copy() for f in factors]
+    if inplace:
+        fs = list(factors)
+        if not all(isinstance(f, np.ndarray) and f.dtype == np.float64 and f.flags.c_contiguous for f in fs):
+            raise ValueError("inplace factors must be C-contiguous float64 numpy arrays")
+    else:
+        fs = [np.ascontiguousarray(f, dtype=np.float64).copy() for f in factors]
     lam = np.zeros(rank)
     rc = _lib().cp_arls_lev(index.h, C.byref(o), lam.ctypes.data, _ptr_array([f.ctypes.data for f in fs]),
                             0, C.byref(fit), C.byref(stats))
@@ -563,6 +572,17 @@ def cpa_fit(index: Index, factors, lam):
     _check(_lib().cpa_fit(index.h, _ptr_array([f.data_ptr() for f in fs]), _ptr(lam), lam.shape[0],
                           C.byref(out), _stream()), "cpa_fit")
     return out.value
+
+
+def cpa_fit_terms(index: Index, factors, lam):
+    """(||X||^2, <X, M>, ||M||^2) of Eq. 5.1 over the nonzeros of ``index``."""
+    torch = _torch()
+    fs = [f.to(device="cuda", dtype=torch.float64).contiguous() for f in factors]
+    lam = lam.to(device="cuda", dtype=torch.float64).contiguous()
+    out = (C.c_double * 3)()
+    _check(_lib().cpa_fit_terms(index.h, _ptr_array([f.data_ptr() for f in fs]), _ptr(lam), lam.shape[0], out,
+                                _stream()), "cpa_fit_terms")
+    return float(out[0]), float(out[1]), float(out[2])
 
 
 # --------------------------------------------------------------------------- estimated fit

@@ -1314,6 +1314,28 @@ int cpa_fit(const cpa_index* X, const double* const* factors, const double* lamb
   return CPA_OK;
 }
 
+int cpa_fit_terms(const cpa_index* X, const double* const* factors, const double* lambda, int32_t r,
+                  double* terms, void* stream) {
+  if (!X || !factors || !lambda || !terms || r < 1 || r > kMaxRank) return CPA_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  FactorPtrs F;
+  for (int m = 0; m < X->order; ++m) {
+    if (!factors[m]) return CPA_ERR_ARG;
+    F.A[m] = factors[m];
+  }
+  DevBuf buf;
+  const size_t fb = (fit_buffers_bytes(X->order, r) + 256 + 255) & ~size_t(255);
+  CPA_TRY(buf.alloc(fb + block_sums_bytes(kSumMaxBlocks, gram_sums_width(r)), st));
+  double* fit_dev = (double*)buf.p;  // fit_dev[0]: fit, [1..3]: the terms
+  double* scratch = fit_dev + 32;
+  BlockSums sums = block_sums_at((char*)buf.p + fb, kSumMaxBlocks);
+  CPA_CUDA_TRY(cudaMemsetAsync(sums.ticket, 0, sizeof(unsigned), st));
+  CPA_TRY(fit_enqueue<double>(X, F, lambda, r, scratch, sums, fit_dev, st, fit_dev + 1));
+  CPA_CUDA_TRY(cudaMemcpyAsync(terms, fit_dev + 1, sizeof(double) * 3, cudaMemcpyDeviceToHost, st));
+  CPA_CUDA_TRY(cudaStreamSynchronize(st));
+  return CPA_OK;
+}
+
 int cp_arls_lev(const cpa_index* Xc, const cpa_options* opt, double* lambda, double* const* factors,
                 int32_t io_on_device, double* fit, cpa_stats* stats) {
   if (!Xc || !lambda || !factors) return CPA_ERR_ARG;

@@ -953,6 +953,182 @@ __global__ void __launch_bounds__(kRowThreads) k_lev_rows_ff(const float* A, int
   }
 }
 
+// ---- FP64 rows of many-row factors on the FP32 pipe --------------------------
+// GB300's FP64 pipe runs at 1/64 of the FP32 rate, so the Gram and the leverage
+// quadratic forms of FP64 factors with >= kManyRows rows take float-pair arithmetic:
+// each FP64 value is split once into floats hi + lo (hi = the value with its low 29
+// mantissa bits cleared, exact; lo = the rest rounded, 2^-48 relative), products and
+// sums as in the FP32-row kernels (about 2^-44 relative), tiles added in FP64.
+// The split takes integer operations only (a conversion or an FP64 subtraction would
+// issue on the slow FP64 pipe): hi's bits are the sign, the rebiased exponent and the
+// top 23 stored mantissa bits of v; lo is the remaining 29 mantissa bits, scaled by
+// 2^(E - 1075) and normalised to a float by their leading one (its lowest bits dropped
+// when there are more than 24: 2^-47 relative to v).  Values whose hi or lo falls outside
+// FP32's normal range (zero, magnitudes below about 2^-97 or from 2^128) take the
+// conversions.
+__device__ __forceinline__ float2 split_ff(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned hi32 = (unsigned)(b >> 32);
+  const unsigned sign = hi32 & 0x80000000u;
+  const int E = (int)((hi32 >> 20) & 0x7ffu);
+  const int fe = E - 896;  // FP32 exponent field of hi
+  const unsigned low = (unsigned)b & 0x1fffffffu;  // v - hi = low * 2^(E - 1075)
+  const int top = low ? 31 - __clz(low) : 0;       // position of lo's leading one (0..28)
+  const int le = E - 1075 + top + 127;             // FP32 exponent field of lo
+  if (fe >= 1 && fe <= 254 && (!low || le >= 1)) {
+    const float h = __uint_as_float(sign | ((unsigned)fe << 23) | ((unsigned)(b >> 29) & 0x7fffffu));
+    float l = 0.f;
+    if (low) {
+      const unsigned m = top >= 23 ? (low >> (top - 23)) : (low << (23 - top));
+      l = __uint_as_float(sign | ((unsigned)le << 23) | (m & 0x7fffffu));
+    }
+    return make_float2(h, l);
+  }
+  const double vh = __longlong_as_double((long long)(b & ~((1ull << 29) - 1)));
+  return make_float2((float)vh, (float)(v - vh));
+}
+
+template <int PMAX>
+__global__ void __launch_bounds__(kGramThreads) k_gram_rows_ffd(const double* __restrict__ A, int64_t n, int r,
+                                                                int lda, double* __restrict__ G, BlockSums S) {
+  extern __shared__ __align__(16) unsigned char gram_smem2[];
+  float2* tile = reinterpret_cast<float2*>(gram_smem2);  // kGramRowsFF * r
+  const int np = r * (r + 1) / 2;
+  int pa[PMAX], pb[PMAX];
+  double acc[PMAX];
+#pragma unroll
+  for (int q = 0; q < PMAX; ++q) {
+    const int p = threadIdx.x + q * kGramThreads;
+    if (p < np) pair_of(p, r, &pa[q], &pb[q]); else pa[q] = pb[q] = 0;
+    acc[q] = 0.0;
+  }
+  for (int64_t row0 = (int64_t)blockIdx.x * kGramRowsFF; row0 < n; row0 += (int64_t)gridDim.x * kGramRowsFF) {
+    const int rows = (int)((n - row0) < kGramRowsFF ? (n - row0) : kGramRowsFF);
+    __syncthreads();
+    const double* src = A + row0 * lda;
+    for (int i = threadIdx.x; i < kGramRowsFF * r; i += kGramThreads) {
+      const int rr = i / r, c = i - rr * r;
+      tile[i] = rr < rows ? split_ff(src[(int64_t)rr * lda + c]) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < PMAX; ++q) {
+      const int p = threadIdx.x + q * kGramThreads;
+      if (p < np) {
+        float hi = 0.f, lo = 0.f;
+        for (int i = 0; i < rows; ++i) {
+          const float2 a = tile[i * r + pa[q]], b = tile[i * r + pb[q]];
+          ff_fma(a.x, a.y, b.x, b.y, hi, lo);
+        }
+        acc[q] += (double)hi + (double)lo;
+      }
+    }
+  }
+  gram_block_finish<PMAX>(acc, np, r, G, S);
+}
+
+// Leverage scores of FP64 rows (kind 0 factors), one thread per row, in float-pair
+// arithmetic as k_lev_rows_ff; the rows are written out divided by lambda in FP64.
+__global__ void __launch_bounds__(kRowThreads) k_lev_rows_ffd(const double* A, int64_t n, int r, int lda,
+                                                              const SmallFactor* __restrict__ f,
+                                                              double* __restrict__ lev, uint64_t* __restrict__ q,
+                                                              DistInfo* info, double* A_out) {
+  extern __shared__ __align__(16) unsigned char ffd_smem[];
+  double* ilam = reinterpret_cast<double*>(ffd_smem);  // r: 1 / lambda_c (1 for a zero column)
+  float* Fh = reinterpret_cast<float*>(ilam + r);       // r * r
+  float* Fl = Fh + r * r;                               // r * r
+  float* sch = Fl + r * r;                              // r
+  float* scl = sch + r;                                 // r
+  // 8 r + 4 (2 r^2 + 2 r) bytes before it: 8-byte aligned
+  float2* xs = reinterpret_cast<float2*>(scl + r);  // kRowThreads * ld (S a as float pairs)
+  __shared__ int perm[kMaxRank];
+  const int ld = r | 1;
+  const int kind = f->kind;
+  const int k = kind == 0 ? f->rank : r;
+  for (int i = threadIdx.x; i < r * r; i += blockDim.x) {
+    const double v = f->F[i];
+    const float h = (float)v;
+    Fh[i] = h;
+    Fl[i] = (float)(v - (double)h);
+  }
+  for (int i = threadIdx.x; i < r; i += blockDim.x) {
+    const double sc = f->scale[i];
+    const float h = (float)sc;
+    sch[i] = h;
+    scl[i] = (float)(sc - (double)h);
+    const double l = f->lambda[i];
+    ilam[i] = pos_finite(l) ? 1.0 / l : 1.0;
+    perm[i] = f->perm[i];
+  }
+  uint64_t my_max = 0;
+  uint32_t my_nz = 0;
+  for (int64_t row0 = (int64_t)blockIdx.x * kRowThreads; row0 < n; row0 += (int64_t)gridDim.x * kRowThreads) {
+    const int rows = (int)(n - row0 < kRowThreads ? n - row0 : kRowThreads);
+    __syncthreads();
+    for (int i = threadIdx.x; i < rows * r; i += kRowThreads) {
+      const int rr = i / r, c = i - rr * r;
+      const float2 x = split_ff(A[(row0 + rr) * lda + c]);
+      const float p = __fmul_rn(x.x, sch[c]);
+      const float rest = __fmaf_rn(x.x, scl[c], __fmaf_rn(x.y, sch[c], __fmaf_rn(x.x, sch[c], -p)));
+      const float h = __fadd_rn(p, rest);
+      xs[rr * ld + c] = make_float2(h, __fsub_rn(rest, __fsub_rn(h, p)));
+    }
+    __syncthreads();
+    if (threadIdx.x < rows) {
+      const float2* b = xs + threadIdx.x * ld;
+      const int64_t row = row0 + threadIdx.x;
+      double l = 0.0;
+      if (kind == 0) {
+        float lh = 0.f, ll = 0.f;
+        for (int c = 0; c < k; ++c) {
+          float th = 0.f, tl = 0.f;
+          for (int u = 0; u <= c; ++u) {
+            const float2 bu = b[perm[u]];
+            ff_fma(Fh[c * r + u], Fl[c * r + u], bu.x, bu.y, th, tl);
+          }
+          float s, e;
+          two_sum(th, tl, s, e);
+          ff_fma(s, e, s, e, lh, ll);
+        }
+        l = (double)lh + (double)ll;
+      } else {
+        for (int c = 0; c < r; ++c) {
+          double t = 0.0;
+          for (int u = 0; u < r; ++u)
+            t = fma((double)Fh[c * r + u] + (double)Fl[c * r + u], (double)b[u].x + (double)b[u].y, t);
+          l = fma((double)b[c].x + (double)b[c].y, t, l);
+        }
+      }
+      if (lev) lev[row] = l;
+      if (q) {
+        double pr = l / (double)r;
+        pr = clamp01(pr);
+        const uint64_t qi = __double2ull_rn(pr * 4611686018427387904.0);  // 2^62
+        q[row] = qi;
+        my_max = qi > my_max ? qi : my_max;
+        my_nz += qi > 0;
+      }
+    }
+    if (A_out) {
+      for (int i = threadIdx.x; i < rows * r; i += kRowThreads) {
+        const int rr = i / r, c = i - rr * r;
+        A_out[row0 * r + i] = A[(row0 + rr) * lda + c] * ilam[c];
+      }
+    }
+  }
+  if (q && info) {
+    for (int o = 16; o > 0; o >>= 1) {
+      const uint64_t om = __shfl_xor_sync(0xffffffffu, my_max, o);
+      my_max = om > my_max ? om : my_max;
+      my_nz += __shfl_xor_sync(0xffffffffu, my_nz, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicMax((unsigned long long*)&info->maxq, (unsigned long long)my_max);
+      atomicAdd((unsigned long long*)&info->nnzq, (unsigned long long)my_nz);
+    }
+  }
+}
+
 }  // namespace
 
 template <class FT>
@@ -981,6 +1157,18 @@ int gram_rows(const FT* A, int64_t n, int r, double* G, const BlockSums& S, cuda
       k_gram_rows_ff<4><<<grid, kGramThreads, smem, st>>>(A, n, r, lda, G, S);
     else
       k_gram_rows_ff<9><<<grid, kGramThreads, smem, st>>>(A, n, r, lda, G, S);
+    CPA_LAUNCH_CHECK();
+    return CPA_OK;
+  }
+  if (n >= kManyRows) {  // FP64 rows of a many-row factor: float pairs on the FP32 pipe
+    const unsigned grid = grid_for(kGramRowsFF);
+    const size_t smem = sizeof(float2) * kGramRowsFF * r;
+    if (np <= kGramThreads)
+      k_gram_rows_ffd<1><<<grid, kGramThreads, smem, st>>>(reinterpret_cast<const double*>(A), n, r, lda, G, S);
+    else if (np <= 4 * kGramThreads)
+      k_gram_rows_ffd<4><<<grid, kGramThreads, smem, st>>>(reinterpret_cast<const double*>(A), n, r, lda, G, S);
+    else
+      k_gram_rows_ffd<9><<<grid, kGramThreads, smem, st>>>(reinterpret_cast<const double*>(A), n, r, lda, G, S);
     CPA_LAUNCH_CHECK();
     return CPA_OK;
   }
@@ -1048,6 +1236,24 @@ int lev_rows(const FT* A, int64_t n, int r, const SmallFactor* f, double* lev, u
       }));
       const unsigned grid = grid_cap(ceil_div(n, kRowThreads), 8);
       k_lev_rows_ff<<<grid, kRowThreads, bytes(r), st>>>(A, n, r, lda, f, lev, q, info, A_out);
+      CPA_LAUNCH_CHECK();
+      return CPA_OK;
+    }
+  }
+  if constexpr (sizeof(FT) == 8) {
+    if (n >= kManyRows && dist == CPA_DIST_LEVERAGE) {
+      auto bytes = [](int rr) {
+        return sizeof(double) * (size_t)rr + sizeof(float) * ((size_t)2 * rr * rr + 2 * rr) +
+               sizeof(float2) * (size_t)kRowThreads * (rr | 1);
+      };
+      static std::atomic<unsigned long long> attr{0};
+      CPA_CUDA_TRY(set_attr_once(attr, [&] {
+        return cudaFuncSetAttribute(k_lev_rows_ffd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)bytes(kMaxRank));
+      }));
+      const unsigned grid = grid_cap(ceil_div(n, kRowThreads), 8);
+      k_lev_rows_ffd<<<grid, kRowThreads, bytes(r), st>>>(reinterpret_cast<const double*>(A), n, r, lda, f, lev,
+                                                         q, info, reinterpret_cast<double*>(A_out));
       CPA_LAUNCH_CHECK();
       return CPA_OK;
     }

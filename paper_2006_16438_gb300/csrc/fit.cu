@@ -82,9 +82,10 @@ __global__ void __launch_bounds__(kThreads) k_fit_inner(FibreIndex<VT> X, KeyLay
   rearm_ticket(S.ticket);
 }
 
+// terms (may be null): receives ||X||^2, <X, M> and ||M||^2, the three terms of Eq. 5.1.
 __global__ void k_fit_final(const double* __restrict__ grams, int D, const double* __restrict__ lambda,
                             int r, const double* __restrict__ inner, double norm_x2,
-                            double* __restrict__ fit_out) {
+                            double* __restrict__ fit_out, double* __restrict__ terms) {
   __shared__ double red[32];
   double s = 0.0;
   for (int i = threadIdx.x; i < r * r; i += blockDim.x) {
@@ -102,6 +103,11 @@ __global__ void k_fit_final(const double* __restrict__ grams, int D, const doubl
     double F2 = norm_x2 - 2.0 * (*inner) + nm2;
     if (F2 < 0.0) F2 = 0.0;
     *fit_out = norm_x2 > 0.0 ? 1.0 - sqrt(F2) / sqrt(norm_x2) : 0.0;
+    if (terms) {
+      terms[0] = norm_x2;
+      terms[1] = *inner;
+      terms[2] = nm2;
+    }
   }
 }
 
@@ -111,7 +117,7 @@ size_t fit_buffers_bytes(int D, int r) { return sizeof(double) * ((size_t)D * r 
 
 template <class FT>
 int fit_enqueue(const cpa_index* X, const FactorPtrs& F, const double* lambda, int r, double* scratch,
-                const BlockSums& S, double* fit_dev, cudaStream_t st) {
+                const BlockSums& S, double* fit_dev, cudaStream_t st, double* terms) {
   const int D = X->order;
   double* grams = scratch;
   double* inner = scratch + (size_t)D * r * r;
@@ -133,14 +139,14 @@ int fit_enqueue(const cpa_index* X, const FactorPtrs& F, const double* lambda, i
       else k_fit_inner<FT, VT, 2><<<grid, kThreads, 0, st>>>(fx, X->mode[kf].L, F, kf, lambda, r, inner, S);
       return 0;
     });
-  k_fit_final<<<1, 256, 0, st>>>(grams, D, lambda, r, inner, X->norm_x2, fit_dev);
+  k_fit_final<<<1, 256, 0, st>>>(grams, D, lambda, r, inner, X->norm_x2, fit_dev, terms);
   CPA_LAUNCH_CHECK();
   return CPA_OK;
 }
 template int fit_enqueue<double>(const cpa_index*, const FactorPtrs&, const double*, int, double*,
-                                 const BlockSums&, double*, cudaStream_t);
+                                 const BlockSums&, double*, cudaStream_t, double*);
 template int fit_enqueue<float>(const cpa_index*, const FactorPtrs&, const double*, int, double*,
-                                const BlockSums&, double*, cudaStream_t);
+                                const BlockSums&, double*, cudaStream_t, double*);
 
 
 // ---------------------------------------------------------------------------

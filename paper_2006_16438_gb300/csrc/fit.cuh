@@ -11,8 +11,9 @@ size_t fit_buffers_bytes(int D, int r);
 // width >= gram_sums_width(r) (the Grams and the inner product <X, M>, so the fit is
 // the same bit for bit at every run).
 template <class FT>
+// terms (device, may be null): ||X||^2, <X, M>, ||M||^2 (Eq. 5.1) beside the fit.
 int fit_enqueue(const cpa_index* X, const FactorPtrs& F, const double* lambda, int r, double* scratch,
-                const BlockSums& S, double* fit_dev, cudaStream_t st);
+                const BlockSums& S, double* fit_dev, cudaStream_t st, double* terms = nullptr);
 
 // Stratified element sample of the estimated fit (Section 5.4), drawn once and kept
 // on the device: coords (D rows of int32, row m at coords + m * stride), xs (values, the

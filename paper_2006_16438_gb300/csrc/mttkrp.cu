@@ -415,28 +415,33 @@ __global__ void __launch_bounds__(kThreads) k_slab_prep(FibreIndex<VT> X, Factor
   if (lane == 0 && my_nnz) atomicAdd(&ctr[0], (unsigned long long)my_nnz);
 }
 
-// Pass p, light part: warps take chunks of 32 samples; a sample's range of slab p
-// longer than kSlabHeavy is listed for k_slab_heavy, the others are walked as in
-// k_tnsr_mttkrp with u_j read back (the nonzero stream is read once: streaming loads).
-template <class FT, class VT, int CPL>
-__global__ void __launch_bounds__(kThreads) k_slab_light(FibreIndex<VT> X, int r, DevCount sbar, int p,
-                                                         const FT* __restrict__ U, int ldu,
-                                                         const uint64_t* __restrict__ los,
-                                                         const uint32_t* __restrict__ bnd, FT* __restrict__ M,
-                                                         int ldm, unsigned long long* __restrict__ pctr,
-                                                         uint4* __restrict__ heavy, int64_t heavy_cap) {
+// Light passes: a warp takes a chunk of kLightChunk consecutive samples (lane l < kLightChunk
+// holds sample l's range of slab p; ranges longer than kSlabHeavy are listed for the heavy
+// pass) and walks the remaining (sample, group of 32 nonzeros) items in order, issuing
+// the next item's loads before the current item's additions.  `sample(j)` sets up a
+// sample's row (warp-uniform j), `group(nb, ikl, xl)` adds a group of nb nonzeros
+// (lane l holds i_k and x of nonzero l).
+constexpr int kLightChunk = 8;
+
+template <class VT, class SampleFn, class GroupFn>
+__device__ __forceinline__ void walk_light(const FibreIndex<VT>& X, DevCount sbar, int p,
+                                           const uint64_t* __restrict__ los, const uint32_t* __restrict__ bnd,
+                                           unsigned long long* __restrict__ pctr, uint4* __restrict__ heavy,
+                                           int64_t heavy_cap, SampleFn&& sample, GroupFn&& group) {
+  using XT = typename ValueOf<VT>::type;
   const int lane = threadIdx.x & 31;
   const int64_t n = sbar.get();
-  const int64_t nchunks = (n + 31) >> 5;
+  const int64_t nchunks = (n + kLightChunk - 1) / kLightChunk;
   for (;;) {
     unsigned long long cidx = 0;
     if (lane == 0) cidx = atomicAdd(&pctr[0], 1ull);
     cidx = __shfl_sync(0xffffffffu, cidx, 0);
     if ((int64_t)cidx >= nchunks) break;
-    const int64_t j = (int64_t)cidx * 32 + lane;
+    const int64_t base = (int64_t)cidx * kLightChunk;
+    const int64_t j = base + lane;
     uint64_t start = 0;
     uint32_t len = 0;
-    if (j < n) {
+    if (lane < kLightChunk && j < n) {
       const uint32_t a = bnd[j * 32 + p], b = bnd[j * 32 + p + 1];
       len = b - a;
       start = los[j] + a;
@@ -457,38 +462,88 @@ __global__ void __launch_bounds__(kThreads) k_slab_light(FibreIndex<VT> X, int r
       }
     }
     unsigned todo = __ballot_sync(0xffffffffu, len > 0);
-    while (todo) {
-      const int q = __ffs(todo) - 1;
-      todo &= todo - 1;
-      const uint32_t lq = __shfl_sync(0xffffffffu, len, q);
-      const uint64_t sq = __shfl_sync(0xffffffffu, start, q);
-      const int64_t jq = (int64_t)cidx * 32 + q;
-      FT u[CPL];
-#pragma unroll
-      for (int v = 0; v < CPL; ++v) {
-        const int c = lane + 32 * v;
-        u[v] = c < r ? U[jq * ldu + c] : FT(0);
-      }
-      for (uint32_t g = 0; g < lq; g += 32) {
-        const int nb = lq - g < 32 ? (int)(lq - g) : 32;
-        int32_t ikl = 0;
-        FT xl = FT(0);
-        if (lane < nb) {
-          ikl = __ldcs(X.ik + sq + g + lane);
-          xl = (FT)X.value_stream(sq + g + lane);
+    if (!todo) continue;
+    int q = __ffs(todo) - 1;
+    todo &= todo - 1;
+    uint32_t lq = __shfl_sync(0xffffffffu, len, q);
+    uint64_t sq = __shfl_sync(0xffffffffu, start, q);
+    uint32_t g = 0;
+    sample(base + q);
+    int32_t ikl = 0;
+    XT xl = XT(0);
+    if (lane < (lq < 32u ? (int)lq : 32)) {
+      ikl = __ldcs(X.ik + sq + lane);
+      xl = X.value_stream(sq + lane);
+    }
+    for (;;) {
+      const int nb = lq - g < 32 ? (int)(lq - g) : 32;
+      uint32_t g2 = g + 32, lq2 = lq;
+      uint64_t sq2 = sq;
+      int q2 = q;
+      bool more = true, fresh = false;
+      if (g2 >= lq) {
+        if (todo) {
+          q2 = __ffs(todo) - 1;
+          todo &= todo - 1;
+          lq2 = __shfl_sync(0xffffffffu, len, q2);
+          sq2 = __shfl_sync(0xffffffffu, start, q2);
+          g2 = 0;
+          fresh = true;
+        } else {
+          more = false;
         }
+      }
+      int32_t ikn = 0;
+      XT xn = XT(0);
+      if (more && lane < (lq2 - g2 < 32u ? (int)(lq2 - g2) : 32)) {
+        ikn = __ldcs(X.ik + sq2 + g2 + lane);
+        xn = X.value_stream(sq2 + g2 + lane);
+      }
+      group(nb, ikl, xl);
+      if (!more) break;
+      if (fresh) sample(base + q2);
+      q = q2;
+      lq = lq2;
+      sq = sq2;
+      g = g2;
+      ikl = ikn;
+      xl = xn;
+    }
+  }
+}
+
+// Pass p, light part, scalar atomics (FP64, or FP32 rows not padded to 16 bytes): lane c
+// holds column c of u_j; one row addition per nonzero.
+template <class FT, class VT, int CPL>
+__global__ void __launch_bounds__(kThreads) k_slab_light(FibreIndex<VT> X, int r, DevCount sbar, int p,
+                                                         const FT* __restrict__ U, int ldu,
+                                                         const uint64_t* __restrict__ los,
+                                                         const uint32_t* __restrict__ bnd, FT* __restrict__ M,
+                                                         int ldm, unsigned long long* __restrict__ pctr,
+                                                         uint4* __restrict__ heavy, int64_t heavy_cap) {
+  using XT = typename ValueOf<VT>::type;
+  const int lane = threadIdx.x & 31;
+  FT u[CPL];
+  walk_light(
+      X, sbar, p, los, bnd, pctr, heavy, heavy_cap,
+      [&](int64_t j) {
+#pragma unroll
+        for (int v = 0; v < CPL; ++v) {
+          const int c = lane + 32 * v;
+          u[v] = c < r ? U[j * ldu + c] : FT(0);
+        }
+      },
+      [&](int nb, int32_t ikl, XT xl) {
         for (int q2 = 0; q2 < nb; ++q2) {
           const int32_t ik = __shfl_sync(0xffffffffu, ikl, q2);
-          const FT x = __shfl_sync(0xffffffffu, xl, q2);
+          const FT x = (FT)__shfl_sync(0xffffffffu, xl, q2);
 #pragma unroll
           for (int v = 0; v < CPL; ++v) {
             const int c = lane + 32 * v;
             if (c < r) atomicAdd(&M[(int64_t)ik * ldm + c], x * u[v]);
           }
         }
-      }
-    }
-  }
+      });
 }
 
 // Pass p, heavy part: blocks take listed pieces from a counter (pctr[2]); the warps of
@@ -602,58 +657,11 @@ __global__ void __launch_bounds__(kThreads) k_slab_light_v4(FibreIndex<VT> X, in
                                                             const uint32_t* __restrict__ bnd, float* __restrict__ M,
                                                             unsigned long long* __restrict__ pctr,
                                                             uint4* __restrict__ heavy, int64_t heavy_cap) {
-  const int lane = threadIdx.x & 31;
   const int ldm = 4 * nq;
-  const int64_t n = sbar.get();
-  const int64_t nchunks = (n + 31) >> 5;
-  for (;;) {
-    unsigned long long cidx = 0;
-    if (lane == 0) cidx = atomicAdd(&pctr[0], 1ull);
-    cidx = __shfl_sync(0xffffffffu, cidx, 0);
-    if ((int64_t)cidx >= nchunks) break;
-    const int64_t j = (int64_t)cidx * 32 + lane;
-    uint64_t start = 0;
-    uint32_t len = 0;
-    if (j < n) {
-      const uint32_t a = bnd[j * 32 + p], b = bnd[j * 32 + p + 1];
-      len = b - a;
-      start = los[j] + a;
-    }
-    if (len > kSlabHeavy) {  // listed in pieces, each taken whole by one block
-      const uint32_t np = (len + kSlabPiece - 1) / kSlabPiece;
-      const unsigned long long h = atomicAdd(&pctr[1], (unsigned long long)np);
-      if (h + np <= (unsigned long long)heavy_cap) {
-        for (uint32_t q = 0; q < np; ++q) {
-          const uint64_t ps = start + (uint64_t)q * kSlabPiece;
-          const uint32_t pl = len - q * kSlabPiece < (uint32_t)kSlabPiece ? len - q * kSlabPiece : kSlabPiece;
-          heavy[h + q] = make_uint4((unsigned)j, (unsigned)(ps & 0xffffffffu), (unsigned)(ps >> 32), pl);
-        }
-        len = 0;
-      } else {  // list full: empty the slots reserved below the capacity, walk the range here
-        for (unsigned long long q = h; q < h + np && q < (unsigned long long)heavy_cap; ++q)
-          heavy[q] = make_uint4((unsigned)j, 0u, 0u, 0u);
-      }
-    }
-    unsigned todo = __ballot_sync(0xffffffffu, len > 0);
-    while (todo) {
-      const int q = __ffs(todo) - 1;
-      todo &= todo - 1;
-      const uint32_t lq = __shfl_sync(0xffffffffu, len, q);
-      const uint64_t sq = __shfl_sync(0xffffffffu, start, q);
-      float4 u[Q2];
-      load_u_v4<Q2>(U, (int64_t)cidx * 32 + q, nq, u);
-      for (uint32_t g = 0; g < lq; g += 32) {
-        const int nb = lq - g < 32 ? (int)(lq - g) : 32;
-        int32_t ikl = 0;
-        float xl = 0.f;
-        if (lane < nb) {
-          ikl = __ldcs(X.ik + sq + g + lane);
-          xl = (float)X.value_stream(sq + g + lane);
-        }
-        add_group_v4<Q2>(nb, ikl, xl, u, nq, M, ldm);
-      }
-    }
-  }
+  float4 u[Q2];
+  walk_light(
+      X, sbar, p, los, bnd, pctr, heavy, heavy_cap, [&](int64_t j) { load_u_v4<Q2>(U, j, nq, u); },
+      [&](int nb, int32_t ikl, float xl) { add_group_v4<Q2>(nb, ikl, xl, u, nq, M, ldm); });
 }
 
 // Pass p, heavy part (as k_slab_heavy, with 16-byte atomics).

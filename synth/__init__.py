@@ -250,18 +250,9 @@ CONFIG_UBER = dict(name="uber-like-183x24x1140x1717-r25", rank=25, samples=2 ** 
                    tau=2.0 ** -17, seed=0)
 
 
-def batch_problems(nprob: int = 64, seed0: int = 0, max_nnz: int = 10 ** 6) -> list:
-    """The batched workload: independent 3- and 4-way planted count tensors of uneven
-    size.  Problem i (seed seed0 + i): order 3 or 4; mode sizes log-uniform in
-    [10^2, 10^5] (redrawn while their product reaches 2^60, or while no nonzero count
-    fits the bounds below); nnz log-uniform in [10^4, max_nnz], at most a tenth of the
-    cells and at least 50 N_k / s for every mode k (N_k = Khatri-Rao rows), so that
-    the sampled right-hand sides are not empty; Zipf(alpha) popularity with alpha
-    uniform in [1.0, 1.3]; CP rank uniform in 5..50; s = 2^u, u uniform in 14..17,
-    lowered to a power of two at most 1/128 of the fewest Khatri-Rao rows of any mode
-    (the method's regime s << N_k: with s near N_k and skewed leverage almost all of the
-    mass is deterministic and the rejection loop of Alg. 2 rarely finds a row below
-    tau) and at least 16 r (mode sizes redrawn otherwise); tau = 1/s.  Returns dicts with coo, rank, samples, tau, zipf_alpha, seed."""
+def batch_specs(nprob: int = 64, seed0: int = 0, max_nnz: int = 10 ** 7) -> list:
+    """The parameters of the batched workload's problems (see batch_problems): dicts
+    with dims, nnz (the target count), rank, samples, tau, zipf_alpha, seed."""
     out = []
     for i in range(nprob):
         g = _rng(seed0 + i, 31)
@@ -288,6 +279,26 @@ def batch_problems(nprob: int = 64, seed0: int = 0, max_nnz: int = 10 ** 6) -> l
             if lo <= hi:
                 break
         nnz = int(round(min(max(10 ** lg_nnz, lo), hi)))
-        coo = planted_cp_tensor(dims, rank, target_nnz=nnz, seed=seed0 + i, zipf_alpha=alpha)
-        out.append(dict(coo=coo, rank=rank, samples=s, tau=1.0 / s, zipf_alpha=alpha, seed=seed0 + i))
+        out.append(dict(dims=dims, nnz=nnz, rank=rank, samples=s, tau=1.0 / s, zipf_alpha=alpha, seed=seed0 + i))
+    return out
+
+
+def batch_problems(nprob: int = 64, seed0: int = 0, max_nnz: int = 10 ** 6) -> list:
+    """The batched workload: independent 3- and 4-way planted count tensors of uneven
+    size.  Problem i (seed seed0 + i): order 3 or 4; mode sizes log-uniform in
+    [10^2, 10^5] (redrawn while their product reaches 2^60, or while no nonzero count
+    fits the bounds below); nnz log-uniform in [10^4, max_nnz], at most a tenth of the
+    cells and at least 50 N_k / s for every mode k (N_k = Khatri-Rao rows), so that
+    the sampled right-hand sides are not empty; Zipf(alpha) popularity with alpha
+    uniform in [1.0, 1.3]; CP rank uniform in 5..50; s = 2^u, u uniform in 14..17,
+    lowered to a power of two at most 1/128 of the fewest Khatri-Rao rows of any mode
+    (the method's regime s << N_k: with s near N_k and skewed leverage almost all of the
+    mass is deterministic and the rejection loop of Alg. 2 rarely finds a row below
+    tau) and at least 16 r (mode sizes redrawn otherwise); tau = 1/s.  Returns dicts with coo, rank, samples, tau, zipf_alpha, seed."""
+    out = []
+    for sp in batch_specs(nprob, seed0, max_nnz):
+        coo = planted_cp_tensor(sp["dims"], sp["rank"], target_nnz=sp["nnz"], seed=sp["seed"],
+                                zipf_alpha=sp["zipf_alpha"])
+        out.append(dict(coo=coo, rank=sp["rank"], samples=sp["samples"], tau=sp["tau"], zipf_alpha=sp["zipf_alpha"],
+                        seed=sp["seed"]))
     return out

@@ -128,3 +128,16 @@ def planted_cp_tensor_gpu(dims, rank, *, events, seed=0, zipf_alpha=1.1, log_cou
     vals = torch.cat(out_val)
     del out_val
     return idx, vals
+
+
+def batch_problems_gpu(nprob=64, seed0=0, max_nnz=10 ** 7, device="cuda"):
+    """The batched workload of ``synth.batch_specs`` generated on the GPU: per problem
+    the planted model's tensor from 1.3 events per target nonzero (duplicates merged,
+    so the count lands near the target), as (spec, idx, vals) with device tensors."""
+    import synth
+    out = []
+    for sp in synth.batch_specs(nprob, seed0, max_nnz):
+        idx, vals = planted_cp_tensor_gpu(sp["dims"], sp["rank"], events=int(1.3 * sp["nnz"]), seed=sp["seed"],
+                                          zipf_alpha=sp["zipf_alpha"], device=device)
+        out.append((sp, idx, vals))
+    return out
