@@ -144,14 +144,14 @@ template <class FT>
 int refresh_distribution(FT* A, int64_t n, int r, uint64_t* C, DistInfo* info, double* Pm,
                          double* GA, const BlockSums& S, SmallFactor* fac, int* warn, void* scan_scratch,
                          bool normalize_out, double* lev_out, cudaStream_t st, int dist = CPA_DIST_LEVERAGE,
-                         const FT* src = nullptr, int lda = 0) {
+                         const FT* src = nullptr, int lda = 0, int* status = nullptr) {
   const FT* in = src ? src : A;
-  CPA_TRY(gram_rows<FT>(in, n, r, GA, S, st, src ? lda : r));
+  CPA_TRY(gram_rows<FT>(in, n, r, GA, S, st, src ? lda : r, status));
   // a rank-deficient factor matters only to leverage scores (warning bit 0: no warning)
   CPA_TRY(factor_spd(GA, r, 1, 1, 1e-12, fac, warn, dist == CPA_DIST_LEVERAGE ? CPA_WARN_RANK_DEFICIENT_LEV : 0,
                      st, info));
   CPA_TRY(lev_rows<FT>(in, n, r, fac, lev_out, C, info, normalize_out || src ? A : nullptr, st, dist,
-                       src ? lda : r));
+                       src ? lda : r, status));
   CPA_TRY(cdf_from_q(C, C, n, info, Pm, scan_scratch, st));
   return CPA_OK;
 }
@@ -465,7 +465,7 @@ struct Plan {
         CPA_TRY(prof.mark(2));
         CPA_TRY(prof.mark(3));
         CPA_TRY(refresh_distribution<FT>(Fk, nk, r, Cm[k], info + k, Pm[k], GA, sums_lev, flev, warn, scan_ws,
-                                         true, nullptr, st, dist, Mt, ldm));
+                                         true, nullptr, st, dist, Mt, ldm, MB.status));
       } else {
         CPA_TRY(sampled_mttkrp<FT>(X, k, F, r, SB[k].idx_packed, SB[k].wgt, DevCount{&SB[k].state->sbar, s},
                                    Mt, Gs, MB, st, prof.on ? evs : nullptr, &fork));
@@ -474,7 +474,7 @@ struct Plan {
         CPA_TRY(solve_rows<FT>(Mt, nk, r, fsolve, Fk, st, GA));
         CPA_TRY(prof.mark(3));
         CPA_TRY(refresh_distribution<FT>(Fk, nk, r, Cm[k], info + k, Pm[k], GA, sums_lev, flev, warn, scan_ws,
-                                         true, nullptr, st, dist));
+                                         true, nullptr, st, dist, nullptr, 0, MB.status));
       }
       k_finish_update<<<1, 64, 0, st>>>(flev, r, lam, dstats, SB[k].state, MB.total, warn);
       CPA_LAUNCH_CHECK();
@@ -537,7 +537,8 @@ struct Plan {
     for (int m = 0; m < D; ++m) {
       if (prec == CPA_MIXED)
         CPA_TRY(refresh_distribution<float>(static_cast<float*>(Fm[m]), X->dims[m], r, Cm[m], info + m,
-                                            Pm[m], GA, sums_lev, flev, warn, scan_ws, false, nullptr, st, dist));
+                                            Pm[m], GA, sums_lev, flev, warn, scan_ws, false, nullptr, st, dist,
+                                            nullptr, 0, MB.status));
       else
         CPA_TRY(refresh_distribution<double>(static_cast<double*>(Fm[m]), X->dims[m], r, Cm[m], info + m,
                                              Pm[m], GA, sums_lev, flev, warn, scan_ws, false, nullptr, st, dist));
@@ -617,14 +618,14 @@ struct Plan {
       CPA_TRY(sampled_mttkrp_fold<FT>(X, k, F, r, B.idx_packed, B.wgt, DevCount{&B.state->sbar, s}, Mt, ldm, Gs,
                                       fsolve, warn, MB, st));
       CPA_TRY(refresh_distribution<FT>(Fk, nk, r, Cm[k], info + k, Pm[k], GA, sums_lev, flev, warn, scan_ws, true,
-                                       nullptr, st, dist, Mt, ldm));
+                                       nullptr, st, dist, Mt, ldm, MB.status));
     } else {
       CPA_TRY(sampled_mttkrp<FT>(X, k, F, r, B.idx_packed, B.wgt, DevCount{&B.state->sbar, s}, Mt, Gs, MB,
                                  st));
       CPA_TRY(factor_spd(Gs, r, 0, 0, 1e-13, fsolve, warn, CPA_WARN_SINGULAR_GRAM, st));
       CPA_TRY(solve_rows<FT>(Mt, nk, r, fsolve, Fk, st));
       CPA_TRY(refresh_distribution<FT>(Fk, nk, r, Cm[k], info + k, Pm[k], GA, sums_lev, flev, warn, scan_ws, true,
-                                       nullptr, st, dist));
+                                       nullptr, st, dist, nullptr, 0, MB.status));
     }
     k_copy_lambda<<<1, 64, 0, st>>>(flev, r, lam);
     CPA_LAUNCH_CHECK();

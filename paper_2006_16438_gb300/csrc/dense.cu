@@ -4,13 +4,15 @@
 // 64, so they are skinny (n x r times r x n) and bound by FP64 issue on this part.
 // The r x r factorisation runs in one thread block.
 #include "dense.cuh"
+#include "ffloat.cuh"
 
 namespace cpa {
 
 namespace {
 
 constexpr int kGramRows = 32;   // rows staged per tile
-constexpr int kGramThreads = 256;
+constexpr int kGramThreads = 256;      // threads when a thread owns several pairs
+constexpr int kGramMaxThreads = 1024;  // one pair per thread up to this many pairs
 
 // Upper-triangle pair p -> (a, b), a <= b, row-major over a.
 __device__ __forceinline__ void pair_of(int p, int r, int* a, int* b) {
@@ -31,7 +33,7 @@ __device__ __forceinline__ void gram_block_finish(const double* acc, int np, int
   double* mine = S.part + (size_t)blockIdx.x * np;
 #pragma unroll
   for (int q = 0; q < PMAX; ++q) {
-    const int p = threadIdx.x + q * kGramThreads;
+    const int p = threadIdx.x + q * (int)blockDim.x;
     if (p < np) mine[p] = acc[q];
   }
   if (!last_block_to_arrive(S.ticket)) return;
@@ -49,9 +51,10 @@ __device__ __forceinline__ void gram_block_finish(const double* acc, int np, int
 // leverage scores and the fit).  The tile is converted to FP64 once when staged: on
 // GB300 a conversion issues on the FP64 pipe like a multiply-add.
 template <class FT, int PMAX>
-__global__ void __launch_bounds__(kGramThreads) k_gram_rows(const FT* __restrict__ A,
+__global__ void __launch_bounds__(kGramMaxThreads) k_gram_rows(const FT* __restrict__ A,
                                                             int64_t n, int r, int lda,
                                                             double* __restrict__ G, BlockSums S) {
+  const int nt = blockDim.x;
   extern __shared__ __align__(16) unsigned char gram_smem[];
   double* tile = reinterpret_cast<double*>(gram_smem);  // kGramRows * r
   const int np = r * (r + 1) / 2;
@@ -59,7 +62,7 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_rows(const FT* __restrict
   double acc[PMAX];
 #pragma unroll
   for (int q = 0; q < PMAX; ++q) {
-    const int p = threadIdx.x + q * kGramThreads;
+    const int p = threadIdx.x + q * nt;
     if (p < np) pair_of(p, r, &pa[q], &pb[q]); else pa[q] = pb[q] = 0;
     acc[q] = 0.0;
   }
@@ -68,14 +71,14 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_rows(const FT* __restrict
     const int rows = (int)((n - row0) < kGramRows ? (n - row0) : kGramRows);
     __syncthreads();
     const FT* src = A + row0 * lda;
-    for (int i = threadIdx.x; i < kGramRows * r; i += kGramThreads) {
+    for (int i = threadIdx.x; i < kGramRows * r; i += nt) {
       const int rr = i / r, c = i - rr * r;
       tile[i] = rr < rows ? (double)src[(int64_t)rr * lda + c] : 0.0;
     }
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < PMAX; ++q) {
-      const int p = threadIdx.x + q * kGramThreads;
+      const int p = threadIdx.x + q * nt;
       if (p < np) {
         double s = 0.0;
         for (int i = 0; i < rows; ++i) s = fma(tile[i * r + pa[q]], tile[i * r + pb[q]], s);
@@ -94,8 +97,9 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_rows(const FT* __restrict
 constexpr int kGramRowsFF = 64;
 
 template <int PMAX>
-__global__ void __launch_bounds__(kGramThreads) k_gram_rows_ff(const float* __restrict__ A, int64_t n, int r,
+__global__ void __launch_bounds__(kGramMaxThreads) k_gram_rows_ff(const float* __restrict__ A, int64_t n, int r,
                                                                int lda, double* __restrict__ G, BlockSums S) {
+  const int nt = blockDim.x;
   extern __shared__ __align__(16) unsigned char gram_smem[];
   float* tile = reinterpret_cast<float*>(gram_smem);  // kGramRowsFF * r
   const int np = r * (r + 1) / 2;
@@ -103,7 +107,7 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_rows_ff(const float* __re
   double acc[PMAX];
 #pragma unroll
   for (int q = 0; q < PMAX; ++q) {
-    const int p = threadIdx.x + q * kGramThreads;
+    const int p = threadIdx.x + q * nt;
     if (p < np) pair_of(p, r, &pa[q], &pb[q]); else pa[q] = pb[q] = 0;
     acc[q] = 0.0;
   }
@@ -111,14 +115,14 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_rows_ff(const float* __re
     const int rows = (int)((n - row0) < kGramRowsFF ? (n - row0) : kGramRowsFF);
     __syncthreads();
     const float* src = A + row0 * lda;
-    for (int i = threadIdx.x; i < kGramRowsFF * r; i += kGramThreads) {
+    for (int i = threadIdx.x; i < kGramRowsFF * r; i += nt) {
       const int rr = i / r, c = i - rr * r;
       tile[i] = rr < rows ? src[(int64_t)rr * lda + c] : 0.f;
     }
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < PMAX; ++q) {
-      const int p = threadIdx.x + q * kGramThreads;
+      const int p = threadIdx.x + q * nt;
       if (p < np) {
         float hi = 0.f, lo = 0.f;
         for (int i = 0; i < rows; ++i) {
@@ -830,23 +834,51 @@ __global__ void __launch_bounds__(kRowThreads) k_lev_rows_tpr(const FT* A, int64
   }
 }
 
-// ---- leverage of many FP32 rows on the FP32 pipe ---------------------------
-// Float-pair ("double-float") arithmetic: a value is hi + lo with |lo| <= ulp(hi)/2.
-// TwoSum gives the exact error of a float addition; fma(a, b, -ab) that of a product.
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  const float z = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
-}
-// (hi, lo) += (ah + al) (bh + bl), the product's al*bl term dropped (below 2^-46).
-__device__ __forceinline__ void ff_fma(float ah, float al, float bh, float bl, float& hi, float& lo) {
-  const float p = __fmul_rn(ah, bh);
-  const float e = __fmaf_rn(ah, bh, -p);
-  const float cross = __fmaf_rn(ah, bl, __fmul_rn(al, bh));
-  float s, t;
-  two_sum(hi, p, s, t);
-  hi = s;
-  lo = __fadd_rn(lo, __fadd_rn(t, __fadd_rn(e, cross)));
+// ---- leverage of many FP32 rows on the FP32 pipe (float pairs: ffloat.cuh) ----
+// ---- FP64 rows of many-row factors on the FP32 pipe --------------------------
+// GB300's FP64 pipe runs at 1/64 of the FP32 rate, so the Gram and the leverage
+// quadratic forms of FP64 factors with >= kManyRows rows take float-pair arithmetic:
+// each FP64 value is split once into floats hi + lo (hi = the value with its low 29
+// mantissa bits cleared, exact; lo = the rest rounded, 2^-48 relative), products and
+// sums as in the FP32-row kernels (about 2^-44 relative), tiles added in FP64.
+template <int PMAX>
+__global__ void __launch_bounds__(kGramMaxThreads) k_gram_rows_ffd(const double* __restrict__ A, int64_t n, int r,
+                                                                int lda, double* __restrict__ G, BlockSums S) {
+  const int nt = blockDim.x;
+  extern __shared__ __align__(16) unsigned char gram_smem2[];
+  float2* tile = reinterpret_cast<float2*>(gram_smem2);  // kGramRowsFF * r
+  const int np = r * (r + 1) / 2;
+  int pa[PMAX], pb[PMAX];
+  double acc[PMAX];
+#pragma unroll
+  for (int q = 0; q < PMAX; ++q) {
+    const int p = threadIdx.x + q * nt;
+    if (p < np) pair_of(p, r, &pa[q], &pb[q]); else pa[q] = pb[q] = 0;
+    acc[q] = 0.0;
+  }
+  for (int64_t row0 = (int64_t)blockIdx.x * kGramRowsFF; row0 < n; row0 += (int64_t)gridDim.x * kGramRowsFF) {
+    const int rows = (int)((n - row0) < kGramRowsFF ? (n - row0) : kGramRowsFF);
+    __syncthreads();
+    const double* src = A + row0 * lda;
+    for (int i = threadIdx.x; i < kGramRowsFF * r; i += nt) {
+      const int rr = i / r, c = i - rr * r;
+      tile[i] = rr < rows ? split_ff(src[(int64_t)rr * lda + c]) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < PMAX; ++q) {
+      const int p = threadIdx.x + q * nt;
+      if (p < np) {
+        float hi = 0.f, lo = 0.f;
+        for (int i = 0; i < rows; ++i) {
+          const float2 a = tile[i * r + pa[q]], b = tile[i * r + pb[q]];
+          ff_fma(a.x, a.y, b.x, b.y, hi, lo);
+        }
+        acc[q] += (double)hi + (double)lo;
+      }
+    }
+  }
+  gram_block_finish<PMAX>(acc, np, r, G, S);
 }
 
 // Leverage scores (kind 0 factors: l = ||L^{-1} P^T (S a)||^2) of FP32 rows, one
@@ -951,80 +983,6 @@ __global__ void __launch_bounds__(kRowThreads) k_lev_rows_ff(const float* A, int
       atomicAdd((unsigned long long*)&info->nnzq, (unsigned long long)my_nz);
     }
   }
-}
-
-// ---- FP64 rows of many-row factors on the FP32 pipe --------------------------
-// GB300's FP64 pipe runs at 1/64 of the FP32 rate, so the Gram and the leverage
-// quadratic forms of FP64 factors with >= kManyRows rows take float-pair arithmetic:
-// each FP64 value is split once into floats hi + lo (hi = the value with its low 29
-// mantissa bits cleared, exact; lo = the rest rounded, 2^-48 relative), products and
-// sums as in the FP32-row kernels (about 2^-44 relative), tiles added in FP64.
-// The split takes integer operations only (a conversion or an FP64 subtraction would
-// issue on the slow FP64 pipe): hi's bits are the sign, the rebiased exponent and the
-// top 23 stored mantissa bits of v; lo is the remaining 29 mantissa bits, scaled by
-// 2^(E - 1075) and normalised to a float by their leading one (its lowest bits dropped
-// when there are more than 24: 2^-47 relative to v).  Values whose hi or lo falls outside
-// FP32's normal range (zero, magnitudes below about 2^-97 or from 2^128) take the
-// conversions.
-__device__ __forceinline__ float2 split_ff(double v) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-  const unsigned hi32 = (unsigned)(b >> 32);
-  const unsigned sign = hi32 & 0x80000000u;
-  const int E = (int)((hi32 >> 20) & 0x7ffu);
-  const int fe = E - 896;  // FP32 exponent field of hi
-  const unsigned low = (unsigned)b & 0x1fffffffu;  // v - hi = low * 2^(E - 1075)
-  const int top = low ? 31 - __clz(low) : 0;       // position of lo's leading one (0..28)
-  const int le = E - 1075 + top + 127;             // FP32 exponent field of lo
-  if (fe >= 1 && fe <= 254 && (!low || le >= 1)) {
-    const float h = __uint_as_float(sign | ((unsigned)fe << 23) | ((unsigned)(b >> 29) & 0x7fffffu));
-    float l = 0.f;
-    if (low) {
-      const unsigned m = top >= 23 ? (low >> (top - 23)) : (low << (23 - top));
-      l = __uint_as_float(sign | ((unsigned)le << 23) | (m & 0x7fffffu));
-    }
-    return make_float2(h, l);
-  }
-  const double vh = __longlong_as_double((long long)(b & ~((1ull << 29) - 1)));
-  return make_float2((float)vh, (float)(v - vh));
-}
-
-template <int PMAX>
-__global__ void __launch_bounds__(kGramThreads) k_gram_rows_ffd(const double* __restrict__ A, int64_t n, int r,
-                                                                int lda, double* __restrict__ G, BlockSums S) {
-  extern __shared__ __align__(16) unsigned char gram_smem2[];
-  float2* tile = reinterpret_cast<float2*>(gram_smem2);  // kGramRowsFF * r
-  const int np = r * (r + 1) / 2;
-  int pa[PMAX], pb[PMAX];
-  double acc[PMAX];
-#pragma unroll
-  for (int q = 0; q < PMAX; ++q) {
-    const int p = threadIdx.x + q * kGramThreads;
-    if (p < np) pair_of(p, r, &pa[q], &pb[q]); else pa[q] = pb[q] = 0;
-    acc[q] = 0.0;
-  }
-  for (int64_t row0 = (int64_t)blockIdx.x * kGramRowsFF; row0 < n; row0 += (int64_t)gridDim.x * kGramRowsFF) {
-    const int rows = (int)((n - row0) < kGramRowsFF ? (n - row0) : kGramRowsFF);
-    __syncthreads();
-    const double* src = A + row0 * lda;
-    for (int i = threadIdx.x; i < kGramRowsFF * r; i += kGramThreads) {
-      const int rr = i / r, c = i - rr * r;
-      tile[i] = rr < rows ? split_ff(src[(int64_t)rr * lda + c]) : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < PMAX; ++q) {
-      const int p = threadIdx.x + q * kGramThreads;
-      if (p < np) {
-        float hi = 0.f, lo = 0.f;
-        for (int i = 0; i < rows; ++i) {
-          const float2 a = tile[i * r + pa[q]], b = tile[i * r + pb[q]];
-          ff_fma(a.x, a.y, b.x, b.y, hi, lo);
-        }
-        acc[q] += (double)hi + (double)lo;
-      }
-    }
-  }
-  gram_block_finish<PMAX>(acc, np, r, G, S);
 }
 
 // Leverage scores of FP64 rows (kind 0 factors), one thread per row, in float-pair
@@ -1132,11 +1090,12 @@ __global__ void __launch_bounds__(kRowThreads) k_lev_rows_ffd(const double* A, i
 }  // namespace
 
 template <class FT>
-int gram_rows(const FT* A, int64_t n, int r, double* G, const BlockSums& S, cudaStream_t st, int lda) {
+int gram_rows(const FT* A, int64_t n, int r, double* G, const BlockSums& S, cudaStream_t st, int lda, int* status) {
   if (lda <= 0) lda = r;
   if (r < 1 || r > kMaxRank) return CPA_ERR_ARG;
   if (!S.ticket || S.max_blocks < 1) return CPA_ERR_ARG;
   const int np = r * (r + 1) / 2;
+  const unsigned one_pair = (unsigned)((np + 31) / 32 * 32);  // threads of the one-pair-per-thread layout
   if (n <= 0) {
     CPA_CUDA_TRY(cudaMemsetAsync(G, 0, sizeof(double) * r * r, st));
     return CPA_OK;
@@ -1149,10 +1108,12 @@ int gram_rows(const FT* A, int64_t n, int r, double* G, const BlockSums& S, cuda
     return (unsigned)(g < cap ? g : cap);
   };
   if constexpr (sizeof(FT) == 4) {
+    if (n >= kManyRows && status && lev_tensor_cores() && tc_rows_ok(reinterpret_cast<const float*>(A), r, lda))
+      return gram_rows_tc(reinterpret_cast<const float*>(A), n, r, lda, G, S, status, st);
     const unsigned grid = grid_for(kGramRowsFF);
     const size_t smem = sizeof(float) * kGramRowsFF * r;
-    if (np <= kGramThreads)
-      k_gram_rows_ff<1><<<grid, kGramThreads, smem, st>>>(A, n, r, lda, G, S);
+    if (np <= kGramMaxThreads)
+      k_gram_rows_ff<1><<<grid, one_pair, smem, st>>>(A, n, r, lda, G, S);
     else if (np <= 4 * kGramThreads)
       k_gram_rows_ff<4><<<grid, kGramThreads, smem, st>>>(A, n, r, lda, G, S);
     else
@@ -1163,8 +1124,8 @@ int gram_rows(const FT* A, int64_t n, int r, double* G, const BlockSums& S, cuda
   if (n >= kManyRows) {  // FP64 rows of a many-row factor: float pairs on the FP32 pipe
     const unsigned grid = grid_for(kGramRowsFF);
     const size_t smem = sizeof(float2) * kGramRowsFF * r;
-    if (np <= kGramThreads)
-      k_gram_rows_ffd<1><<<grid, kGramThreads, smem, st>>>(reinterpret_cast<const double*>(A), n, r, lda, G, S);
+    if (np <= kGramMaxThreads)
+      k_gram_rows_ffd<1><<<grid, one_pair, smem, st>>>(reinterpret_cast<const double*>(A), n, r, lda, G, S);
     else if (np <= 4 * kGramThreads)
       k_gram_rows_ffd<4><<<grid, kGramThreads, smem, st>>>(reinterpret_cast<const double*>(A), n, r, lda, G, S);
     else
@@ -1174,8 +1135,8 @@ int gram_rows(const FT* A, int64_t n, int r, double* G, const BlockSums& S, cuda
   }
   const unsigned grid = grid_for(kGramRows);
   const size_t smem = sizeof(double) * kGramRows * r;
-  if (np <= kGramThreads)
-    k_gram_rows<FT, 1><<<grid, kGramThreads, smem, st>>>(A, n, r, lda, G, S);
+  if (np <= kGramMaxThreads)
+    k_gram_rows<FT, 1><<<grid, one_pair, smem, st>>>(A, n, r, lda, G, S);
   else if (np <= 4 * kGramThreads)
     k_gram_rows<FT, 4><<<grid, kGramThreads, smem, st>>>(A, n, r, lda, G, S);
   else
@@ -1183,8 +1144,8 @@ int gram_rows(const FT* A, int64_t n, int r, double* G, const BlockSums& S, cuda
   CPA_LAUNCH_CHECK();
   return CPA_OK;
 }
-template int gram_rows<double>(const double*, int64_t, int, double*, const BlockSums&, cudaStream_t, int);
-template int gram_rows<float>(const float*, int64_t, int, double*, const BlockSums&, cudaStream_t, int);
+template int gram_rows<double>(const double*, int64_t, int, double*, const BlockSums&, cudaStream_t, int, int*);
+template int gram_rows<float>(const float*, int64_t, int, double*, const BlockSums&, cudaStream_t, int, int*);
 
 // Threads of the r x r factorisation block: a multiple of 32 in [32, 256]
 // (CPA_FACTOR_THREADS overrides the default, for tuning).
@@ -1217,7 +1178,7 @@ int factor_spd(const double* G, int r, int normalize, int pivot, double rel_tol,
 
 template <class FT>
 int lev_rows(const FT* A, int64_t n, int r, const SmallFactor* f, double* lev, uint64_t* q,
-             DistInfo* info, FT* A_out, cudaStream_t st, int dist, int lda) {
+             DistInfo* info, FT* A_out, cudaStream_t st, int dist, int lda, int* status) {
   if (lda <= 0) lda = r;
   if (lda != r && A_out == A) return CPA_ERR_ARG;  // in place only at stride r
   if (dist != CPA_DIST_LEVERAGE && dist != CPA_DIST_UNIFORM && dist != CPA_DIST_LENGTH_SQUARED)
@@ -1225,7 +1186,13 @@ int lev_rows(const FT* A, int64_t n, int r, const SmallFactor* f, double* lev, u
   if (r < 1 || r > kMaxRank) return CPA_ERR_ARG;
   if (n <= 0) return CPA_OK;
   if constexpr (sizeof(FT) == 4) {
-    if (n >= kManyRows && dist == CPA_DIST_LEVERAGE) {
+    if (n >= kManyRows && dist == CPA_DIST_LEVERAGE && status && lev_tensor_cores() &&
+        tc_rows_ok(reinterpret_cast<const float*>(A), r, lda))
+      return lev_rows_tc(reinterpret_cast<const float*>(A), n, r, lda, f, lev, q, info,
+                         reinterpret_cast<float*>(A_out), status, st);
+  }
+  if (n >= kManyRows && dist == CPA_DIST_LEVERAGE) {  // float pairs on the FP32 pipe
+    if constexpr (sizeof(FT) == 4) {
       auto bytes = [](int rr) {
         return sizeof(float) * ((size_t)2 * rr * rr + 3 * rr + 1) + sizeof(float2) * (size_t)kRowThreads * (rr | 1) +
                16;
@@ -1235,13 +1202,9 @@ int lev_rows(const FT* A, int64_t n, int r, const SmallFactor* f, double* lev, u
         return cudaFuncSetAttribute(k_lev_rows_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes(kMaxRank));
       }));
       const unsigned grid = grid_cap(ceil_div(n, kRowThreads), 8);
-      k_lev_rows_ff<<<grid, kRowThreads, bytes(r), st>>>(A, n, r, lda, f, lev, q, info, A_out);
-      CPA_LAUNCH_CHECK();
-      return CPA_OK;
-    }
-  }
-  if constexpr (sizeof(FT) == 8) {
-    if (n >= kManyRows && dist == CPA_DIST_LEVERAGE) {
+      k_lev_rows_ff<<<grid, kRowThreads, bytes(r), st>>>(reinterpret_cast<const float*>(A), n, r, lda, f, lev, q,
+                                                         info, reinterpret_cast<float*>(A_out));
+    } else {
       auto bytes = [](int rr) {
         return sizeof(double) * (size_t)rr + sizeof(float) * ((size_t)2 * rr * rr + 2 * rr) +
                sizeof(float2) * (size_t)kRowThreads * (rr | 1);
@@ -1252,11 +1215,11 @@ int lev_rows(const FT* A, int64_t n, int r, const SmallFactor* f, double* lev, u
                                     (int)bytes(kMaxRank));
       }));
       const unsigned grid = grid_cap(ceil_div(n, kRowThreads), 8);
-      k_lev_rows_ffd<<<grid, kRowThreads, bytes(r), st>>>(reinterpret_cast<const double*>(A), n, r, lda, f, lev,
-                                                         q, info, reinterpret_cast<double*>(A_out));
-      CPA_LAUNCH_CHECK();
-      return CPA_OK;
+      k_lev_rows_ffd<<<grid, kRowThreads, bytes(r), st>>>(reinterpret_cast<const double*>(A), n, r, lda, f, lev, q,
+                                                          info, reinterpret_cast<double*>(A_out));
     }
+    CPA_LAUNCH_CHECK();
+    return CPA_OK;
   }
   if (n >= kManyRows) {
     auto bytes = [](int rr) {
@@ -1280,9 +1243,9 @@ int lev_rows(const FT* A, int64_t n, int r, const SmallFactor* f, double* lev, u
   return CPA_OK;
 }
 template int lev_rows<double>(const double*, int64_t, int, const SmallFactor*, double*, uint64_t*,
-                              DistInfo*, double*, cudaStream_t, int, int);
+                              DistInfo*, double*, cudaStream_t, int, int, int*);
 template int lev_rows<float>(const float*, int64_t, int, const SmallFactor*, double*, uint64_t*,
-                             DistInfo*, float*, cudaStream_t, int, int);
+                             DistInfo*, float*, cudaStream_t, int, int, int*);
 
 template <class FT>
 int solve_rows(const FT* M, int64_t n, int r, const SmallFactor* f, FT* A, cudaStream_t st,

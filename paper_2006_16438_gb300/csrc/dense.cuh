@@ -39,8 +39,11 @@ struct DistInfo {
 // (S: a workspace of block_sums_bytes(max_blocks, r (r + 1) / 2) bytes with its
 // ticket zeroed), so the result is reproducible bit for bit.
 // lda: row stride of A in elements (0: r).
+// status (device, may be null): a run's status word; with it, FP32 factors of many rows
+// take the tensor-core kernel (lev_tc.cu), which records a timed-out wait there.
 template <class FT>
-int gram_rows(const FT* A, int64_t n, int r, double* G, const BlockSums& S, cudaStream_t st, int lda = 0);
+int gram_rows(const FT* A, int64_t n, int r, double* G, const BlockSums& S, cudaStream_t st, int lda = 0,
+              int* status = nullptr);
 // Width of the block sums of gram_rows for rank r.
 inline int gram_sums_width(int r) { return r * (r + 1) / 2; }
 
@@ -70,7 +73,20 @@ int factor_spd(const double* G, int r, int normalize, int pivot, double rel_tol,
 template <class FT>
 int lev_rows(const FT* A, int64_t n, int r, const SmallFactor* f, double* lev,
              uint64_t* q, DistInfo* info, FT* A_out, cudaStream_t st, int dist = CPA_DIST_LEVERAGE,
-             int lda = 0);
+             int lda = 0, int* status = nullptr);
+
+// The tensor-core leverage kernels for FP32 factors (lev_tc.cu): kind::tf32 products
+// with the hi/lo split (about FP32 accuracy).  On by default for the mixed-precision
+// refresh of factors with >= 65,536 rows; CPA_LEV_FLOAT_PAIR=1 selects the float-pair
+// kernels (2^-44, the FP64 path's) instead.
+bool lev_tensor_cores();
+// The rows can be streamed by the bulk copies of the tensor-core kernels: a 16-byte
+// aligned base (row strides lda >= r; lda 0 means r).
+bool tc_rows_ok(const float* A, int r, int lda);
+int gram_rows_tc(const float* A, int64_t n, int r, int lda, double* G, const BlockSums& S, int* status,
+                 cudaStream_t st);
+int lev_rows_tc(const float* A, int64_t n, int r, int lda, const SmallFactor* f, double* lev, uint64_t* q,
+                DistInfo* info, float* A_out, int* status, cudaStream_t st);
 
 // A = M G^{-1} row by row with the factor of G (kind 0: two triangular solves;
 // kind 1: A = M F).

@@ -736,6 +736,9 @@ int launch_mttkrp_slabs(const cpa_index* X, int k, const FactorPtrs& F, int r, c
                                                       B.bnd, ctr, fold);
   CPA_LAUNCH_CHECK();
   const int64_t cap = (int64_t)kHeavyPerSample * (sbar.max > 0 ? sbar.max : 1);
+  // the heavy pieces: two blocks per SM take them from a counter (measured: eight
+  // per SM are no faster, the pass is bound by the L2 atomics)
+  const unsigned hgrid = (unsigned)sms * 2;
   for (int p = 0; p < P; ++p) {
     unsigned long long* pctr = ctr + 4 + 3 * p;
     if constexpr (sizeof(FT) == 4) {
@@ -745,10 +748,10 @@ int launch_mttkrp_slabs(const cpa_index* X, int k, const FactorPtrs& F, int r, c
         const int nq = ldm / 4;
         if (nq <= 8) {
           k_slab_light_v4<VT, 1><<<grid, kThreads, 0, st>>>(fx, nq, sbar, p, Uf, B.los, B.bnd, Mf, pctr, heavy, cap);
-          k_slab_heavy_v4<VT, 1><<<(unsigned)sms * 2, kThreads, 0, st>>>(fx, nq, Uf, Mf, pctr, heavy, cap);
+          k_slab_heavy_v4<VT, 1><<<hgrid, kThreads, 0, st>>>(fx, nq, Uf, Mf, pctr, heavy, cap);
         } else {
           k_slab_light_v4<VT, 2><<<grid, kThreads, 0, st>>>(fx, nq, sbar, p, Uf, B.los, B.bnd, Mf, pctr, heavy, cap);
-          k_slab_heavy_v4<VT, 2><<<(unsigned)sms * 2, kThreads, 0, st>>>(fx, nq, Uf, Mf, pctr, heavy, cap);
+          k_slab_heavy_v4<VT, 2><<<hgrid, kThreads, 0, st>>>(fx, nq, Uf, Mf, pctr, heavy, cap);
         }
         CPA_LAUNCH_CHECK();
         continue;
@@ -757,11 +760,11 @@ int launch_mttkrp_slabs(const cpa_index* X, int k, const FactorPtrs& F, int r, c
     if (r <= 32) {
       k_slab_light<FT, VT, 1><<<grid, kThreads, 0, st>>>(fx, r, sbar, p, U, ldu, B.los, B.bnd, M, ldm, pctr, heavy,
                                                          cap);
-      k_slab_heavy<FT, VT, 1><<<(unsigned)sms * 2, kThreads, 0, st>>>(fx, r, U, ldu, M, ldm, pctr, heavy, cap);
+      k_slab_heavy<FT, VT, 1><<<hgrid, kThreads, 0, st>>>(fx, r, U, ldu, M, ldm, pctr, heavy, cap);
     } else {
       k_slab_light<FT, VT, 2><<<grid, kThreads, 0, st>>>(fx, r, sbar, p, U, ldu, B.los, B.bnd, M, ldm, pctr, heavy,
                                                          cap);
-      k_slab_heavy<FT, VT, 2><<<(unsigned)sms * 2, kThreads, 0, st>>>(fx, r, U, ldu, M, ldm, pctr, heavy, cap);
+      k_slab_heavy<FT, VT, 2><<<hgrid, kThreads, 0, st>>>(fx, r, U, ldu, M, ldm, pctr, heavy, cap);
     }
     CPA_LAUNCH_CHECK();
   }

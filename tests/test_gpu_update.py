@@ -145,12 +145,13 @@ def test_epoch_graph_keyed_by_fit_mode():
 
 
 @pytest.mark.parametrize("r", [8, 25])
-def test_mixed_float_pair_leverage_matches_fp64_rows(r):
+def test_mixed_float_pair_leverage_matches_fp64_rows(monkeypatch, r):
     """Mixed precision with factors that are exact in FP32 and a first mode of 70,000
     rows: the factor Gram (k_gram_rows_ff) and the leverage rows (k_lev_rows_ff) of
     the FP32 factors run in float-pair arithmetic (about 2^-44), so the leverage
     distributions, and with them the sampled rows and counts, equal the FP64
     oracle's; weights to 1e-12."""
+    monkeypatch.setenv("CPA_LEV_FLOAT_PAIR", "1")  # the float-pair kernels instead of the tensor cores
     dims = (70000, 40, 30)
     coo = synth.random_sparse_tensor(dims, 300000, seed=11)
     facs = [a.astype(np.float32).astype(np.float64) for a in synth.gaussian_factors(dims, r, seed=12)]
@@ -229,3 +230,34 @@ def test_mode_update_mixed_many_rows_within_2e4(r):
     An, lam = oracle.normalize(A)
     assert relerr(fs[0].cpu().numpy(), An) < 2e-4
     assert relerr(got["lam"].cpu().numpy(), lam) < 2e-4
+
+
+@pytest.mark.parametrize("r", [8, 25, 40])
+def test_mixed_tensor_core_leverage_close_to_fp64(r):
+    """Mixed precision on a first mode of 70,000 rows: its factor Gram and leverage
+    rows run on the tensor cores (tcgen05 kind::tf32, three-product hi/lo split, about
+    FP32 accuracy), so the sampling distribution of that mode is the FP64 one to about
+    1e-6 relative.  Updates of the other modes sample from it: nearly all of the FP64
+    oracle's rows are drawn (a draw flips only where a CDF boundary moved past it), the
+    weights of the common rows agree within 1e-4 and the new factor is within 2e-4 of the
+    oracle's solve on the GPU's own rows."""
+    dims = (70000, 40, 30)
+    coo = synth.random_sparse_tensor(dims, 300000, seed=13 + r)
+    facs = synth.gaussian_factors(dims, r, seed=14 + r)
+    gi = cpa.cpa_index_build(coo)
+    oi = oracle.Index(coo)
+    for k in (1, 2):
+        fs = [torch.from_numpy(a).cuda() for a in facs]
+        got = cpa.cpa_mode_update(gi, fs, k, rank=r, samples=4000, tau=1.0 / 4000, seed=5, it=1,
+                                  precision=binding.MIXED)
+        ref = oracle.mode_update(oi, facs, k, rank=r, samples=4000, tau=1.0 / 4000, seed=5, it=1)
+        gidx = got["idx"].cpu().numpy().astype(np.uint64)
+        gw = got["wgt"].cpu().numpy()
+        common, gi_pos, ri_pos = np.intersect1d(gidx, ref["idx"], return_indices=True)
+        assert common.size >= 0.95 * ref["idx"].size
+        assert relerr(gw[gi_pos], ref["wgt"][ri_pos]) < 1e-4
+        M, G, _ = oracle.sampled_mttkrp(oi, k, facs, gidx, gw)
+        A, _ = oracle.solve(G, M)
+        An, lam = oracle.normalize(A)
+        assert relerr(fs[k].cpu().numpy(), An) < 2e-4
+        assert relerr(got["lam"].cpu().numpy(), lam) < 2e-4
