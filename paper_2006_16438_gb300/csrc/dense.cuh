@@ -75,11 +75,17 @@ int lev_rows(const FT* A, int64_t n, int r, const SmallFactor* f, double* lev,
              uint64_t* q, DistInfo* info, FT* A_out, cudaStream_t st, int dist = CPA_DIST_LEVERAGE,
              int lda = 0, int* status = nullptr);
 
-// The tensor-core leverage kernels for FP32 factors (lev_tc.cu): kind::tf32 products
-// with the hi/lo split (about FP32 accuracy).  On by default for the mixed-precision
-// refresh of factors with >= 65,536 rows; CPA_LEV_FLOAT_PAIR=1 selects the float-pair
-// kernels (2^-44, the FP64 path's) instead.
+// The fast leverage kernels for FP32 factors, on by default for the mixed-precision
+// refresh of factors with >= 65,536 rows (about FP32 accuracy): the Gram on the FP32
+// pipe with bulk-copy streaming (gram_stream.cu, r <= kGramStreamMaxRank) and the row
+// forms as tcgen05 kind::tf32 products with the hi/lo split (lev_tc.cu).
+// CPA_LEV_FLOAT_PAIR=1 selects the float-pair kernels (2^-44, the FP64 path's) instead;
+// CPA_GRAM_TC=1 takes the tensor-core Gram of lev_tc.cu.
 bool lev_tensor_cores();
+bool gram_tensor_cores();
+constexpr int kGramStreamMaxRank = 32;
+int gram_rows_stream(const float* A, int64_t n, int r, int lda, double* G, const BlockSums& S, int* status,
+                     cudaStream_t st);
 // The rows can be streamed by the bulk copies of the tensor-core kernels: a 16-byte
 // aligned base (row strides lda >= r; lda 0 means r).
 bool tc_rows_ok(const float* A, int r, int lda);

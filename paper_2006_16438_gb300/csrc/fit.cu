@@ -315,6 +315,122 @@ __global__ void __launch_bounds__(kEstThreads) k_fit_est(const int32_t* __restri
   }
 }
 
+// FP64 estimate with the FP64 work at its floor (two multiplies and one multiply-add
+// per coordinate and sample; GB300's FP64 pipe is the bound): per round a warp takes 16
+// samples, copies their factor rows into shared memory (cp.async, one row per copy
+// instruction, coalesced), and two lanes evaluate each sample's model value from there
+// (lane h takes the coordinates c = h mod 2, in two chains), so no lane idles on padding
+// and the only cross-lane step is one pair sum.  The copies of the next round are issued
+// before this round is evaluated (two buffers per warp); the coordinates are loaded two
+// rounds ahead.  Per block: the sum over its samples of phi_j (m_j - x_j)^2.
+constexpr int kErWarps = 4;
+constexpr int kErSamples = 16;  // samples per warp and round
+constexpr int kErMaxRank = 32;
+
+template <int MD>
+__global__ void __launch_bounds__(32 * kErWarps, 2) k_fit_est_rows(const int32_t* __restrict__ coords, int64_t stride,
+                                                                   const double* __restrict__ xs, int64_t S,
+                                                                   int64_t s_nz, double phi_nz, double phi_z,
+                                                                   FactorPtrs F, const double* __restrict__ lambda,
+                                                                   int r, int D, double* __restrict__ partial) {
+  extern __shared__ __align__(16) double er_smem[];
+  __shared__ double red[kErWarps];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rs = r | 1;                      // odd row stride: the two lanes' reads spread over the banks
+  const int bufd = MD * kErSamples * rs;     // doubles of one buffer
+  double* lam = er_smem;                     // kErMaxRank
+  double* rows = er_smem + kErMaxRank + (size_t)warp * 2 * bufd;
+  for (int c = threadIdx.x; c < r; c += blockDim.x) lam[c] = lambda[c];
+  __syncthreads();
+  const int64_t gw = (int64_t)blockIdx.x * kErWarps + warp, nw = (int64_t)gridDim.x * kErWarps;
+  const int64_t nrounds = S > gw * kErSamples ? (S - 1 - gw * kErSamples) / (nw * kErSamples) + 1 : 0;
+  // lane l holds the coordinates of sample l & 15 for the modes m = (l >> 4) + 2 u
+  constexpr int MH = (MD + 1) / 2;
+  auto load_coords = [&](int64_t k, int32_t (&cv)[MH]) {
+    const int64_t j = (gw + k * nw) * kErSamples + (lane & 15);
+#pragma unroll
+    for (int u = 0; u < MH; ++u) {
+      const int m = (lane >> 4) + 2 * u;
+      cv[u] = (k < nrounds && j < S && m < D) ? __ldg(coords + (int64_t)m * stride + j) : 0;
+    }
+  };
+  auto load_x = [&](int64_t k) {
+    const int64_t j = (gw + k * nw) * kErSamples + (lane & 15);
+    return (k < nrounds && j < S && lane < 16) ? xs[j] : 0.0;
+  };
+  auto issue = [&](int b, const int32_t (&cv)[MH]) {
+    double* dst = rows + (size_t)b * bufd;
+#pragma unroll
+    for (int m = 0; m < MD; ++m) {
+      if (m >= D) break;
+      const double* Am = static_cast<const double*>(F.A[m]);
+#pragma unroll
+      for (int sm = 0; sm < kErSamples; ++sm) {
+        const int row = __shfl_sync(0xffffffffu, cv[m >> 1], sm + 16 * (m & 1));
+        if (lane < r) cp_async8(dst + (m * kErSamples + sm) * rs + lane, Am + (int64_t)row * r + lane);
+      }
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  int32_t cnext[MH];
+  double acc = 0.0;
+  if (nrounds > 0) {
+    load_coords(0, cnext);
+    issue(0, cnext);
+    load_coords(1, cnext);
+  }
+  double xcur = load_x(0);
+  const int sm = lane >> 1, h = lane & 1;
+  for (int64_t k = 0; k < nrounds; ++k) {
+    if (k + 1 < nrounds) issue((int)((k + 1) & 1), cnext);
+    else asm volatile("cp.async.commit_group;\n" ::: "memory");  // an empty group keeps the count
+    load_coords(k + 2, cnext);
+    const double xnext = load_x(k + 1);
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // this round's rows have landed
+    __syncwarp();
+    const double* R = rows + (size_t)(k & 1) * bufd + sm * rs;
+    double m0 = 0.0, m1 = 0.0;
+    for (int c = h; c < r; c += 4) {
+      double t = lam[c];
+#pragma unroll
+      for (int m = 0; m < MD - 1; ++m)
+        if (m < D - 1) t *= R[m * kErSamples * rs + c];
+      m0 = fma(t, R[(D - 1) * kErSamples * rs + c], m0);
+      const int c2 = c + 2;
+      if (c2 < r) {
+        double t2 = lam[c2];
+#pragma unroll
+        for (int m = 0; m < MD - 1; ++m)
+          if (m < D - 1) t2 *= R[m * kErSamples * rs + c2];
+        m1 = fma(t2, R[(D - 1) * kErSamples * rs + c2], m1);
+      }
+    }
+    double mv = m0 + m1;
+    mv += __shfl_xor_sync(0xffffffffu, mv, 1);
+    const double xv = __shfl_sync(0xffffffffu, xcur, sm);
+    const int64_t j = (gw + k * nw) * kErSamples + sm;
+    if (h == 0 && j < S) {
+      const double res = mv - xv;
+      acc += (j < s_nz ? phi_nz : phi_z) * res * res;
+    }
+    xcur = xnext;
+    __syncwarp();  // the buffer is refilled two rounds on
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) red[warp] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int w = 0; w < kErWarps; ++w) b += red[w];
+    partial[blockIdx.x] = b;
+  }
+}
+
+size_t fit_est_rows_smem(int r, int md) {
+  return sizeof(double) * ((size_t)kErMaxRank + (size_t)kErWarps * 2 * md * kErSamples * (r | 1));
+}
+
 // F_hat = the partials summed in a fixed order; fit = 1 - sqrt(F_hat) / ||X||.
 __global__ void k_fit_est_final(const double* __restrict__ partial, int nb, double norm_x2,
                                 double* __restrict__ fit_out) {
@@ -480,6 +596,16 @@ int fit_sample_sort(const cpa_index* X, FitSample* S, cudaStream_t st) {
   return CPA_OK;
 }
 
+// CPA_FIT_EST_ROWS=0 keeps the eight-lanes-per-sample FP64 estimate (for comparison).
+static bool rows_est_enabled() {
+  static int on = -1;
+  if (on < 0) {
+    const char* e = getenv("CPA_FIT_EST_ROWS");
+    on = (e && atoi(e) == 0) ? 0 : 1;
+  }
+  return on == 1;
+}
+
 template <class FT>
 int fit_estimate_enqueue(const cpa_index* X, const FitSample& S, const FactorPtrs& F, const double* lambda,
                          int r, double* fit_dev, cudaStream_t st) {
@@ -498,7 +624,23 @@ int fit_estimate_enqueue(const cpa_index* X, const FitSample& S, const FactorPtr
       k_fit_est<FT, CPL, kMaxOrder><<<nb, kEstThreads, 0, st>>>(S.coords, S.stride, S.xs, n, S.s_nz, S.phi[0],
                                                                 S.phi[1], F, lambda, r, D, S.partial);
   };
-  if (r <= 8) launch(std::integral_constant<int, 1>());
+  if (sizeof(FT) == 8 && r <= kErMaxRank && D <= 4 && rows_est_enabled()) {
+    const size_t smem = fit_est_rows_smem(r, D <= 3 ? 3 : 4);
+    static std::atomic<unsigned long long> attr{0};
+    CPA_CUDA_TRY(set_attr_once(attr, [] {
+      cudaError_t e = cudaFuncSetAttribute(k_fit_est_rows<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)fit_est_rows_smem(kErMaxRank, 3));
+      if (e != cudaSuccess) return e;
+      return cudaFuncSetAttribute(k_fit_est_rows<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)fit_est_rows_smem(kErMaxRank, 4));
+    }));
+    if (D <= 3)
+      k_fit_est_rows<3><<<nb, 32 * kErWarps, smem, st>>>(S.coords, S.stride, S.xs, n, S.s_nz, S.phi[0], S.phi[1], F,
+                                                          lambda, r, D, S.partial);
+    else
+      k_fit_est_rows<4><<<nb, 32 * kErWarps, smem, st>>>(S.coords, S.stride, S.xs, n, S.s_nz, S.phi[0], S.phi[1], F,
+                                                          lambda, r, D, S.partial);
+  } else if (r <= 8) launch(std::integral_constant<int, 1>());
   else if (r <= 16) launch(std::integral_constant<int, 2>());
   else if (r <= 32) launch(std::integral_constant<int, 4>());
   else launch(std::integral_constant<int, 8>());

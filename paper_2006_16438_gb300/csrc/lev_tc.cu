@@ -39,6 +39,19 @@ __device__ __forceinline__ double clamp01_tc(double p) {
   return b < 0x3ff0000000000000ll ? p : 1.0;
 }
 
+// The fixed-point sampling weight q = round(2^62 min(l / r, 1)) of an FP32 leverage
+// score: f = l (2^62 / r) in FP32 (qscale = 2^62 / r), clamped, converted by integer
+// operations (an FP32 value >= 2^23 is an integer: its significand shifted into place).
+__device__ __forceinline__ uint64_t q_from_f32(float l, float qscale) {
+  const float f = l * qscale;
+  if (!(f > 0.f)) return 0;  // zero, negative or NaN
+  if (f >= 4611686018427387904.f) return 1ull << 62;
+  const uint32_t b = __float_as_uint(f);
+  const int e = (int)(b >> 23) - 127;
+  if (e < 23) return (uint64_t)__float2uint_rn(f);
+  return (uint64_t)((b & 0x7fffffu) | 0x800000u) << (e - 23);
+}
+
 // Index of the upper-triangle entry (a, b), a <= b, of an r x r matrix, row-major.
 __device__ __forceinline__ int tri_index(int a, int b, int r) { return a * r - a * (a - 1) / 2 + (b - a); }
 
@@ -277,7 +290,8 @@ template <int NC>
 __global__ void __launch_bounds__(kLevThreads) k_lev_rows_tc(const float* __restrict__ A, int64_t n, int r, int lda,
                                                              int nraw, const SmallFactor* __restrict__ f,
                                                              double* __restrict__ lev, uint64_t* __restrict__ q,
-                                                             DistInfo* info, float* A_out, int* __restrict__ status) {
+                                                             DistInfo* info, float* A_out, float qscale,
+                                                             int* __restrict__ status) {
   constexpr uint32_t kSBO_A = (NC / 4) * tc::kLBO;  // 8-row groups of a 128 x NC tile
   constexpr uint32_t kTileA = 128 * NC * 4;
   constexpr uint32_t kTileB = NC * NC * 4;
@@ -409,10 +423,9 @@ __global__ void __launch_bounds__(kLevThreads) k_lev_rows_tc(const float* __rest
         }
         const int64_t row = row0_of(t - 1) + tid;
         if (row < n) {
-          const double ld = (double)l;
-          if (lev) lev[row] = ld;
+          if (lev) lev[row] = (double)l;
           if (q) {
-            const uint64_t qi = __double2ull_rn(clamp01_tc(ld / (double)r) * 4611686018427387904.0);  // 2^62
+            const uint64_t qi = q_from_f32(l, qscale);
             q[row] = qi;
             my_max = qi > my_max ? qi : my_max;
             my_nz += qi > 0;
@@ -447,13 +460,20 @@ __global__ void __launch_bounds__(kLevThreads) k_lev_rows_tc(const float* __rest
           *reinterpret_cast<float4*>(base + off) = h4;
           *reinterpret_cast<float4*>(base + kTileA + off) = l4;
         }
-        if (A_out) {  // the rows divided by lambda, coalesced
+        if (A_out) {  // the rows divided by lambda, coalesced: element e = rr r + c
           const int64_t left = n - r0;
           const int rows = left < 128 ? (int)left : 128;
           float* dst = A_out + r0 * r;
+          const int step_r = kLevThreads / r, step_c = kLevThreads - step_r * r;
+          int rr = tid / r, c = tid - rr * r;
           for (int e = tid; e < rows * r; e += kLevThreads) {
-            const int rr = e / r, c = e - rr * r;
             dst[e] = rw[rr * lda + c] * ilam[c];
+            rr += step_r;
+            c += step_c;
+            if (c >= r) {
+              c -= r;
+              ++rr;
+            }
           }
         }
       }
@@ -536,6 +556,11 @@ bool lev_tensor_cores() {
   return !(e && atoi(e) != 0);
 }
 
+bool gram_tensor_cores() {
+  const char* e = getenv("CPA_GRAM_TC");
+  return e && atoi(e) != 0;
+}
+
 bool tc_rows_ok(const float* A, int r, int lda) {
   return r >= 1 && r <= kMaxRank && (lda == 0 || lda >= r) && ((uintptr_t)A & 15u) == 0;
 }
@@ -582,12 +607,13 @@ int lev_rows_tc(const float* A, int64_t n, int r, int lda, const SmallFactor* f,
   const int64_t cap = (int64_t)num_sms() * 2;
   const unsigned grid = (unsigned)(ntiles < cap ? ntiles : cap);
   const int nraw = lev_ring_slots(lda);
+  const float qscale = (float)(4611686018427387904.0 / r);
   if (r <= 32)
     k_lev_rows_tc<32><<<grid, kLevThreads, lev_smem_bytes(32, lda), st>>>(A, n, r, lda, nraw, f, lev, q, info,
-                                                                          A_out, status);
+                                                                          A_out, qscale, status);
   else
     k_lev_rows_tc<64><<<grid, kLevThreads, lev_smem_bytes(64, lda), st>>>(A, n, r, lda, nraw, f, lev, q, info,
-                                                                          A_out, status);
+                                                                          A_out, qscale, status);
   CPA_LAUNCH_CHECK();
   return CPA_OK;
 }

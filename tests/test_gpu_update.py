@@ -261,3 +261,29 @@ def test_mixed_tensor_core_leverage_close_to_fp64(r):
         An, lam = oracle.normalize(A)
         assert relerr(fs[k].cpu().numpy(), An) < 2e-4
         assert relerr(got["lam"].cpu().numpy(), lam) < 2e-4
+
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("r", [8, 25, 30])
+def test_mixed_refresh_of_folded_mode(r):
+    """A mixed-precision update of a 70,000-row mode: the solve is folded into the
+    sampled MTTKRP, and the refresh streams the unnormalised rows (row stride r rounded
+    up to 4 floats) through the FP32-pipe Gram and the tensor-core row forms, which
+    write the normalised factor.  The factor and lambda are within 2e-4 of the FP64
+    oracle's solve on the GPU's own sampled rows."""
+    dims = (70000, 40, 30)
+    coo = synth.random_sparse_tensor(dims, 300000, seed=31 + r)
+    facs = synth.gaussian_factors(dims, r, seed=32 + r)
+    gi = cpa.cpa_index_build(coo)
+    oi = oracle.Index(coo)
+    fs = [torch.from_numpy(a).cuda() for a in facs]
+    got = cpa.cpa_mode_update(gi, fs, 0, rank=r, samples=4000, tau=1.0 / 4000, seed=5, it=1,
+                              precision=binding.MIXED)
+    idx = got["idx"].cpu().numpy().astype(np.uint64)
+    wgt = got["wgt"].cpu().numpy()
+    M, G, _ = oracle.sampled_mttkrp(oi, 0, facs, idx, wgt)
+    A, _ = oracle.solve(G, M)
+    An, lam = oracle.normalize(A)
+    assert relerr(fs[0].cpu().numpy(), An) < 2e-4
+    assert relerr(got["lam"].cpu().numpy(), lam) < 2e-4
