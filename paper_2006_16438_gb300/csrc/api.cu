@@ -147,8 +147,10 @@ int refresh_distribution(FT* A, int64_t n, int r, uint64_t* C, DistInfo* info, d
                          const FT* src = nullptr, int lda = 0, int* status = nullptr) {
   const FT* in = src ? src : A;
   CPA_TRY(gram_rows<FT>(in, n, r, GA, S, st, src ? lda : r, status));
-  // a rank-deficient factor matters only to leverage scores (warning bit 0: no warning)
-  CPA_TRY(factor_spd(GA, r, 1, 1, 1e-12, fac, warn, dist == CPA_DIST_LEVERAGE ? CPA_WARN_RANK_DEFICIENT_LEV : 0,
+  // a rank-deficient factor matters only to leverage scores (warning bit 0: no warning);
+  // the pivots are cut where the Gram's own rounding would reach them
+  const double tol = lev_pivot_tol<FT>(in, n, r, src ? lda : r, status);
+  CPA_TRY(factor_spd(GA, r, 1, 1, tol, fac, warn, dist == CPA_DIST_LEVERAGE ? CPA_WARN_RANK_DEFICIENT_LEV : 0,
                      st, info));
   CPA_TRY(lev_rows<FT>(in, n, r, fac, lev_out, C, info, normalize_out || src ? A : nullptr, st, dist,
                        src ? lda : r, status));

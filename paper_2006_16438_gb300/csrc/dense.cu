@@ -254,25 +254,41 @@ __device__ __noinline__ void jacobi_eigen_block(double* a, double* v, int r, int
   }
 }
 
-// 1/sqrt(d) for d > 0 in FP64: FP32 seed, then two Newton steps
-// y <- y (3 - d y^2) / 2 in FP64 (about 24 -> 48 -> 96 correct bits).  GB300 FP64
-// division and square root cost hundreds of cycles each, so the factorisation keeps
-// them off its serial chain.
+// 1/sqrt(d) for d > 0 in FP64: an FP32 seed y0 = rsqrt(f), f the upper word of d moved
+// into FP32 by integer operations (no FP64 conversion on the chain), e = 1 - d y0^2
+// (|e| < 2^-18), then y0 (1 + e/2 + 3 e^2 / 8) (the binomial series of (1 - e)^(-1/2)
+// to second order): relative error about 5 e^3 / 16 < 2^-55 before rounding.  GB300
+// FP64 division and square root cost hundreds of cycles each (every FP64 warp
+// instruction issues over 64 cycles), so the factorisation keeps them off its chain.
 __device__ __forceinline__ double rsqrt_newton(double d) {
-  const float yf = rsqrtf((float)d);
-  double y = (yf > 0.f && yf < INFINITY) ? (double)yf : rsqrt(d);  // outside float range: library rsqrt
-  y = y * fma(-0.5 * d, y * y, 1.5);
-  y = y * fma(-0.5 * d, y * y, 1.5);
-  return y;
+  const int hi = __double2hiint(d);
+  const int ex = ((hi >> 20) & 0x7ff) - 1023;
+  if (ex < -125 || ex > 125) return rsqrt(d);  // outside the FP32 normal range
+  const float f = __int_as_float(((ex + 127) << 23) | ((hi & 0xfffff) << 3));
+  const int yb = __float_as_int(rsqrtf(f));
+  const int ye = ((yb >> 23) & 0xff) - 127;
+  const double y0 = __hiloint2double(((ye + 1023) << 20) | ((yb & 0x7fffff) >> 3), (yb & 7) << 29);
+  const double e = fma(-d, y0 * y0, 1.0);
+  return fma(y0, e * fma(e, 0.375, 0.5), y0);
 }
 
-// 1/d for d > 0 in FP64: FP32 seed x, e = 1 - d x, then x (1 + e + e^2) (the
-// truncated series of 1/(1 - e)), relative error about e^3 ~ 2^-69 before rounding.
-// The range check is done in FP32 (FP64 compares are slow on this part).
+// 1/d for d > 0 in FP64 (0 for d <= 0 or not finite): an FP32 seed f from the upper
+// word of d (its exponent and 20 significand bits moved by integer operations, so no
+// FP64 conversion is on the chain),
+// x = the approximate FP32 reciprocal of f, e = 1 - d x (|e| < 2^-19), then
+// x (1 + e + e^2) (the truncated series of 1/(1 - e)): relative error about e^3 < 2^-56
+// before rounding.
 __device__ __forceinline__ double rcp_newton(double d) {
-  const float xf = __frcp_rn((float)d);
-  if (!(xf > 0.f && xf < INFINITY)) return 1.0 / d;  // outside float range
-  const double x = (double)xf;
+  if (!pos_finite(d)) return 0.0;  // zero, negative or not finite (no division for those lanes)
+  const int hi = __double2hiint(d);
+  const int ex = ((hi >> 20) & 0x7ff) - 1023;
+  if (ex < -125 || ex > 125) return 1.0 / d;  // outside the FP32 normal range
+  const float f = __int_as_float(((ex + 127) << 23) | ((hi & 0xfffff) << 3));
+  float xf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(xf) : "f"(f));  // the seed needs no correct rounding
+  const int xb = __float_as_int(xf);
+  const int xe = ((xb >> 23) & 0xff) - 127;
+  const double x = __hiloint2double(((xe + 1023) << 20) | ((xb & 0x7fffff) >> 3), (xb & 7) << 29);
   const double e = fma(-d, x, 1.0);
   return fma(x, fma(e, e, e), x);
 }
@@ -285,7 +301,7 @@ __device__ __forceinline__ unsigned pivot_key(double v) {
   return b > 0 ? (unsigned)((unsigned long long)b >> 32) : 0u;
 }
 
-// Factor one r x r PSD matrix in one block (see SmallFactor).
+// Factor one r x r PSD matrix in one block of kFactorThreads threads (see SmallFactor).
 //
 // Square-root-free Cholesky S = P L D L^T P^T of S = diag(scale) G diag(scale), L unit
 // lower triangular, with diagonal pivoting (pivot = 1: the largest remaining diagonal
@@ -296,12 +312,15 @@ __device__ __forceinline__ unsigned pivot_key(double v) {
 // (kept as B = -sum L X).  Pivoting is by index: entries stay in place (S is kept
 // symmetric, by original index) and ord[] maps pivot positions to original indices.
 //
-// Each step is two barriers.  Phase C stages the pivot row sp = S(p, :), its scaled
-// copy sh = sp / D_j and the ordering after the swap; in phase B every remaining
-// Schur-complement entry and every entry of B(i, 0..j) is one FMA of staged values,
-// packed over all threads (a GB300 FP64 warp instruction costs the same with any
-// number of active lanes), while warp 0 updates the remaining diagonal, takes the
-// reciprocals of all of it and picks the next pivot.
+// One block barrier per step.  The Schur complement lives in two buffers (step j
+// reads one and writes the other).  Step j's pivot p, D_j, 1 / D_j and its staged row
+// sp = S(p, :), sh = sp / D_j are ready when the step starts.  In the step, warp 0 runs
+// the serial chain: the remaining diagonal, the next pivot, its reciprocal (seeded by
+// integer operations) and the next pivot row, each entry with the same arithmetic as
+// the pair update below, so the next step needs no staging phase.  Meanwhile the warps
+// on the other three SM sub-partitions update every remaining off-diagonal entry and
+// every entry of B(i, 0..j), one FMA of staged values each, packed over their threads
+// (a GB300 FP64 warp instruction costs the same with any number of active lanes).
 // Outputs:
 //  * pivot = 1: F = D^{-1/2} X (the inverse of the Cholesky factor L D^{1/2}),
 //    perm = the pivot order, rank = the number of pivots (kind 0);
@@ -314,49 +333,81 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor_spd(const double* __r
                                                                int* warn, int warn_bit,
                                                                DistInfo* zero_info) {
   extern __shared__ double sm[];
-  double* S = sm;              // r x r, symmetric, by original index
-  double* B = sm + r * r;      // r x r: B(i, c) = -sum_u L(i, u) X(u, c), c in pivot order
-  double* sh = B + r * r;      // r: S(p, c) / D_j of the current pivot p
-  double* sp = sh + r;         // r: S(p, c)
-  double* dinv = sp + r;       // r: 1 / D_j
+  double* Sb0 = sm;            // r x r Schur complements (two buffers), by original index
+  double* Sb1 = sm + r * r;
+  double* B = sm + 2 * r * r;  // r x r: B(i, c) = -sum_u L(i, u) X(u, c), c in pivot order
+  double* spb = B + r * r;     // 2 x r: S(p, c) of the pivot of step j (buffer j & 1)
+  double* shb = spb + 2 * r;   // 2 x r: S(p, c) / D_j
+  double* dinv = shb + 2 * r;  // r: 1 / D_j
   double* Dv = dinv + r;       // r: D_j
   double* scale = Dv + r;      // r
-  __shared__ int ordb[2][kMaxRank];  // pivot position -> original index
+  __shared__ int ordb[2][kMaxRank];  // pivot position -> original index (after step j's swap: [(j + 1) & 1])
   __shared__ unsigned short tri[kMaxRank * (kMaxRank - 1) / 2];  // q -> (a, b), a > b
   __shared__ int perm[kMaxRank];
-  __shared__ int s_fail, s_p, s_ppos;
-  __shared__ double s_dmax, s_d, s_di;
+  __shared__ int s_fail;
+  __shared__ double s_dmax;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
   if (zero_info && tid == 0) {
     zero_info->maxq = 0;
     zero_info->nnzq = 0;
   }
-  for (int c = tid; c < r; c += nt) {
-    const double g = G[c * r + c];
-    const bool pos = pos_finite(g);
-    const double y = pos ? rsqrt_newton(g) : 0.0;  // 1 / sqrt(G_cc)
-    out->lambda[c] = pos ? g * y : 0.0;
-    scale[c] = normalize ? y : 1.0;
-    out->scale[c] = scale[c];
-    ordb[0][c] = c;
+  // every load of G issued up front (r <= 32: four entries per thread)
+  constexpr int kGPer = (32 * 32 + kFactorThreads - 1) / kFactorThreads;
+  const bool small = r <= 32;
+  double gv[kGPer];
+#pragma unroll
+  for (int u = 0; u < kGPer; ++u) {
+    const int i = tid + u * kFactorThreads;
+    gv[u] = small && i < r * r ? G[i] : 0.0;
   }
+  const double gd = tid < r ? G[tid * (r + 1)] : 0.0;
+  for (int c = tid; c < r; c += nt) ordb[0][c] = c;
   for (int a = 1 + tid; a < r; a += nt)
     for (int b = 0; b < a; ++b) tri[a * (a - 1) / 2 + b] = (unsigned short)((a << 8) | b);
-  __syncthreads();
-  for (int i = tid; i < r * r; i += nt) {
-    const int a = i / r, b = i - a * r;
-    S[i] = G[i] * scale[a] * scale[b];
-    B[i] = 0.0;
+  if (normalize) {  // the column scales 1 / sqrt(G_cc) first: S = diag(scale) G diag(scale)
+    if (tid < r) {
+      const bool pos = pos_finite(gd);
+      const double y = pos ? rsqrt_newton(gd) : 0.0;
+      scale[tid] = y;
+      out->scale[tid] = y;
+      out->lambda[tid] = pos ? gd * y : 0.0;
+    }
+    __syncthreads();
+  } else if (tid < r) {
+    scale[tid] = 1.0;
+    out->scale[tid] = 1.0;
+  }
+  if (small) {
+#pragma unroll
+    for (int u = 0; u < kGPer; ++u) {
+      const int i = tid + u * kFactorThreads;
+      if (i < r * r) {
+        const int a = i / r, b = i - a * r;
+        Sb0[i] = normalize ? gv[u] * (scale[a] * scale[b]) : gv[u];
+        B[i] = 0.0;
+      }
+    }
+  } else {
+    for (int i = tid; i < r * r; i += nt) {
+      const int a = i / r, b = i - a * r;
+      Sb0[i] = normalize ? G[i] * (scale[a] * scale[b]) : G[i];
+      B[i] = 0.0;
+    }
   }
   __syncthreads();
-  // First pivot (warp 0): the diagonal's maximum, key argmax and reciprocal.
+  if (!normalize && warp == 4) {  // lambda_c = sqrt(G_cc), beside warp 0's first pivot
+    for (int c = lane; c < r; c += 32) {
+      const double g = Sb0[c * (r + 1)];
+      out->lambda[c] = pos_finite(g) ? g * rsqrt_newton(g) : 0.0;
+    }
+  }
+  // First pivot (warp 0): the diagonal's maximum, key argmax, reciprocal and row.
   if (warp == 0) {
     const int x0 = lane, x1 = lane + 32;
-    const double v0 = x0 < r ? S[x0 * (r + 1)] : 0.0, v1 = x1 < r ? S[x1 * (r + 1)] : 0.0;
+    const double v0 = x0 < r ? Sb0[x0 * (r + 1)] : 0.0, v1 = x1 < r ? Sb0[x1 * (r + 1)] : 0.0;
     // largest diagonal entry (negative entries count as 0) by integer max of bits
     long long mb = max(max(__double_as_longlong(v0), __double_as_longlong(v1)), 0ll);
     for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
-    const double m = __longlong_as_double(mb);
     int pp = 0;
     if (pivot) {
       const unsigned k0 = x0 < r ? pivot_key(v0) : 0u, k1 = x1 < r ? pivot_key(v1) : 0u;
@@ -366,94 +417,117 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor_spd(const double* __r
       pp = b0 ? __ffs(b0) - 1 : 32 + __ffs(b1) - 1;
     }
     const double dp = __shfl_sync(0xffffffffu, pp < 32 ? v0 : v1, pp & 31);
+    const double di = pos_finite(dp) ? rcp_newton(dp) : 0.0;
+    for (int c = lane; c < r; c += 32) {
+      const double v = Sb0[pp * r + c];
+      spb[c] = v;
+      shb[c] = v * di;
+      ordb[1][c] = c == 0 ? pp : (c == pp ? 0 : c);
+    }
     if (lane == 0) {
-      s_dmax = m;
+      s_dmax = __longlong_as_double(mb);
       s_fail = 0;
-      s_p = pp;
-      s_ppos = pp;
-      s_d = dp;
-      s_di = pos_finite(dp) ? rcp_newton(dp) : 0.0;
+      perm[0] = pp;
+      Dv[0] = dp;
+      dinv[0] = di;
     }
   }
   __syncthreads();
   const double cut = rel_tol * s_dmax;
+  // the workers: the warps off warp 0's SM sub-partition (warp % 4 != 0)
+  const int nwarps = nt >> 5;
+  const int nworkers = (nwarps - (nwarps + 3) / 4) * 32;
+  const int wt = (warp - 1 - (warp >> 2)) * 32 + lane;
   int k = r;
   for (int j = 0; j < r; ++j) {
-    const int p = s_p, ppos = s_ppos;
-    const double d = s_d, di = s_di;
+    const double d = Dv[j];
     if (!(pos_finite(d) && nonneg_gt(d, cut))) {  // d > cut; same decision in every thread
       if (pivot) k = j; else if (tid == 0) s_fail = 1;
       break;
     }
-    int* ordn = ordb[(j + 1) & 1];
-    // phase C: stage the pivot row and the ordering after the swap of j and ppos
-    for (int c = tid; c < r; c += nt) {
-      const int* ord = ordb[j & 1];
-      const double v = S[p * r + c];
-      sp[c] = v;
-      sh[c] = v * di;
-      ordn[c] = c == j ? p : (c == ppos ? ord[j] : ord[c]);
-    }
-    if (tid == 0) {
-      perm[j] = p;
-      dinv[j] = di;
-      Dv[j] = d;
-    }
-    __syncthreads();
-    // phase B; remaining pivot positions are j+1 .. r-1
-    const int m = r - j - 1;
-    const int* rem = ordn + j + 1;  // original indices of the remaining positions
-    if (warp == 0 && m > 0) {       // diagonal, reciprocals and the next pivot
-      double v0 = 0.0, v1 = 0.0;
-      if (lane < m) {
-        const int i = rem[lane];
-        v0 = fma(-sh[i], sp[i], S[i * (r + 1)]);
-        S[i * (r + 1)] = v0;
+    const int p = perm[j];
+    const double* sp = spb + (j & 1) * r;
+    const double* sh = shb + (j & 1) * r;
+    const int* ordn = ordb[(j + 1) & 1];
+    const int m = r - j - 1;        // remaining pivot positions j + 1 .. r - 1
+    const int* rem = ordn + j + 1;  // their original indices
+    const double* Sc = (j & 1) ? Sb1 : Sb0;
+    double* Sn = (j & 1) ? Sb0 : Sb1;
+    if (warp == 0) {
+      if (m > 0) {
+        const bool two = m > 32;  // warp-uniform: a second position per lane
+        double v0 = 0.0, v1 = 0.0;  // the remaining diagonal
+        if (lane < m) {
+          const int i = rem[lane];
+          v0 = fma(-sh[i], sp[i], Sc[i * (r + 1)]);
+          Sn[i * (r + 1)] = v0;
+        }
+        if (two && lane + 32 < m) {
+          const int i = rem[lane + 32];
+          v1 = fma(-sh[i], sp[i], Sc[i * (r + 1)]);
+          Sn[i * (r + 1)] = v1;
+        }
+        // the reciprocals of the whole remaining diagonal, overlapping the pivot search
+        const double w0 = rcp_newton(v0);
+        const double w1 = two ? rcp_newton(v1) : 0.0;
+        int pq = 0;  // offset of the next pivot among the remaining positions
+        if (pivot) {
+          const unsigned k0 = lane < m ? pivot_key(v0) : 0u;
+          const unsigned k1 = two && lane + 32 < m ? pivot_key(v1) : 0u;
+          const unsigned km = __reduce_max_sync(0xffffffffu, k0 > k1 ? k0 : k1);
+          const unsigned b0 = __ballot_sync(0xffffffffu, lane < m && k0 == km);
+          const unsigned b1 = two ? __ballot_sync(0xffffffffu, lane + 32 < m && k1 == km) : 0u;
+          pq = b0 ? __ffs(b0) - 1 : 32 + __ffs(b1) - 1;
+        }
+        const double dn = __shfl_sync(0xffffffffu, pq >= 32 ? v1 : v0, pq & 31);
+        const double din = __shfl_sync(0xffffffffu, pq >= 32 ? w1 : w0, pq & 31);
+        const int pn = rem[pq];
+        double* spn = spb + ((j + 1) & 1) * r;
+        double* shn = shb + ((j + 1) & 1) * r;
+        // the next pivot row: the pair update's value for (pn, x), the row at the higher
+        // position taking the role of i (at x = pn: the diagonal update's value, dn)
+        for (int l = lane; l < m; l += 32) {
+          const int x = rem[l];
+          const bool up = l > pq;
+          const double v = fma(-sh[up ? x : pn], sp[up ? pn : x], Sc[up ? x * r + pn : pn * r + x]);
+          spn[x] = v;
+          shn[x] = v * din;
+        }
+        int* ordnn = ordb[j & 1];  // the ordering after step j + 1's swap
+        for (int c = lane; c < r; c += 32)
+          ordnn[c] = c == j + 1 ? pn : (c == j + 1 + pq ? ordn[j + 1] : ordn[c]);
+        if (lane == 0) {
+          perm[j + 1] = pn;
+          Dv[j + 1] = dn;
+          dinv[j + 1] = din;
+        }
       }
-      if (lane + 32 < m) {
-        const int i = rem[lane + 32];
-        v1 = fma(-sh[i], sp[i], S[i * (r + 1)]);
-        S[i * (r + 1)] = v1;
+    } else if (warp & 3) {
+      const int np = m * (m - 1) / 2;
+      for (int q = wt; q < np; q += nworkers) {  // off-diagonal Schur complement
+        const int ab = tri[q];
+        const int i = rem[ab >> 8], c = rem[ab & 255];
+        const double v = fma(-sh[i], sp[c], Sc[i * r + c]);
+        Sn[i * r + c] = v;
+        Sn[c * r + i] = v;
       }
-      int pq = 0;  // offset of the next pivot among the remaining positions
-      if (pivot) {
-        const unsigned k0 = lane < m ? pivot_key(v0) : 0u, k1 = lane + 32 < m ? pivot_key(v1) : 0u;
-        const unsigned km = __reduce_max_sync(0xffffffffu, k0 > k1 ? k0 : k1);
-        const unsigned b0 = __ballot_sync(0xffffffffu, lane < m && k0 == km);
-        const unsigned b1 = __ballot_sync(0xffffffffu, lane + 32 < m && k1 == km);
-        pq = b0 ? __ffs(b0) - 1 : 32 + __ffs(b1) - 1;
+      const int w = j + 1;
+      const float inv_w = 1.0f / (float)w;
+      for (int q = wt; q < m * w; q += nworkers) {  // B(i, :) -= L(i, j) X(j, :)
+        const int row = __float2int_rz(((float)q + 0.5f) * inv_w);
+        const int c = q - row * w;
+        const int i = rem[row];
+        const double xjc = c == j ? 1.0 : B[p * r + c];
+        B[i * r + c] = fma(-sh[i], xjc, B[i * r + c]);
       }
-      const double dn = __shfl_sync(0xffffffffu, pq >= 32 ? v1 : v0, pq & 31);
-      if (lane == 0) {
-        s_p = rem[pq];
-        s_ppos = j + 1 + pq;
-        s_d = dn;
-        s_di = pos_finite(dn) ? rcp_newton(dn) : 0.0;
-      }
-    }
-    const int np = m * (m - 1) / 2;
-    for (int q = tid; q < np; q += nt) {  // off-diagonal Schur complement
-      const int ab = tri[q];
-      const int i = rem[ab >> 8], c = rem[ab & 255];
-      const double v = fma(-sh[i], sp[c], S[i * r + c]);
-      S[i * r + c] = v;
-      S[c * r + i] = v;
-    }
-    const int w = j + 1;
-    const float inv_w = 1.0f / (float)w;
-    for (int q = tid; q < m * w; q += nt) {  // B(i, :) -= L(i, j) X(j, :)
-      const int row = __float2int_rz(((float)q + 0.5f) * inv_w);
-      const int c = q - row * w;
-      const int i = rem[row];
-      const double xjc = c == j ? 1.0 : B[p * r + c];
-      B[i * r + c] = fma(-sh[i], xjc, B[i * r + c]);
     }
     __syncthreads();
   }
   __syncthreads();  // s_fail, and the step that ended the loop early
+  double* S = Sb0;  // scratch from here on
   if (s_fail) {  // plain Cholesky failed: pseudo-inverse from the eigendecomposition
     double* X = B;
-    double* y = sh;
+    double* y = shb;
     for (int i = tid; i < r * r; i += nt) {
       const int a = i / r, b = i - a * r;
       S[i] = G[i] * scale[a] * scale[b];
@@ -483,12 +557,13 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor_spd(const double* __r
   }
   // X(j, c) = [c == j] + B(perm_j, c) for c <= j < k
   if (pivot) {
-    for (int j = tid; j < k; j += nt) sh[j] = rsqrt_newton(Dv[j]);
+    double* rs = shb;
+    for (int j = tid; j < k; j += nt) rs[j] = rsqrt_newton(Dv[j]);
     __syncthreads();
     for (int i = tid; i < r * r; i += nt) {
       const int j = i / r, c = i - j * r;
       double v = 0.0;
-      if (j < k && c <= j) v = ((c == j ? 1.0 : 0.0) + B[perm[j] * r + c]) * sh[j];
+      if (j < k && c <= j) v = (c == j ? 1.0 : B[perm[j] * r + c]) * rs[j];  // B(perm_j, j) = 0
       out->F[i] = v;
     }
     const int* ordk = ordb[k & 1];
@@ -501,22 +576,35 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor_spd(const double* __r
     return;
   }
   // S^{-1} = X^T D^{-1} X (no pivoting: pivot order = original order): X to S, then
-  // Y = D^{-1} X to B, F(a, b) = sum_u X(u, a) Y(u, b) over the lower triangle
+  // Y = D^{-1} X to B; F(a, b) = sum_{u >= a} X(u, a) Y(u, b) for b <= a, one pair per
+  // thread (pairs by ascending a, so a warp's dot products have equal lengths), each in
+  // four interleaved chains
   for (int i = tid; i < r * r; i += nt) {
     const int j = i / r, c = i - j * r;
-    const double x = c <= j ? ((c == j ? 1.0 : 0.0) + B[j * r + c]) : 0.0;
+    const double x = c == j ? 1.0 : (c < j ? B[j * r + c] : 0.0);  // B(j, j) = 0
     S[i] = x;
   }
   __syncthreads();
   for (int i = tid; i < r * r; i += nt) B[i] = S[i] * dinv[i / r];
   __syncthreads();
-  for (int i = tid; i < r * r; i += nt) {
-    const int a = i / r, b = i - a * r;
-    if (b > a) continue;
-    double s2 = 0.0;
-    for (int u = a; u < r; ++u) s2 = fma(S[u * r + a], B[u * r + b], s2);
-    out->F[i] = s2;
-    out->F[b * r + a] = s2;
+  const int npairs = r * (r + 1) / 2;
+  for (int q = tid; q < npairs; q += nt) {
+    int a = (int)((sqrtf(8.f * (float)q + 1.f) - 1.f) * 0.5f);
+    while ((a + 1) * (a + 2) / 2 <= q) ++a;
+    while (a * (a + 1) / 2 > q) --a;
+    const int b = q - a * (a + 1) / 2;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int u = a;
+    for (; u + 3 < r; u += 4) {
+      s0 = fma(S[u * r + a], B[u * r + b], s0);
+      s1 = fma(S[(u + 1) * r + a], B[(u + 1) * r + b], s1);
+      s2 = fma(S[(u + 2) * r + a], B[(u + 2) * r + b], s2);
+      s3 = fma(S[(u + 3) * r + a], B[(u + 3) * r + b], s3);
+    }
+    for (; u < r; ++u) s0 = fma(S[u * r + a], B[u * r + b], s0);
+    const double v = (s0 + s1) + (s2 + s3);
+    out->F[a * r + b] = v;
+    out->F[b * r + a] = v;
   }
   for (int c = tid; c < r; c += nt) out->perm[c] = c;
   if (tid == 0) {
@@ -534,7 +622,6 @@ __device__ __forceinline__ double clamp01(double p) {
 }
 
 constexpr int kRowThreads = 256;
-constexpr int64_t kManyRows = 1 << 16;  // from here on one thread per row
 
 // Leverage of row a_i (one warp per row, lane c owns coordinate c and c + 32), in
 // FP64 whatever the storage type FT of the factor:
@@ -1108,8 +1195,11 @@ int gram_rows(const FT* A, int64_t n, int r, double* G, const BlockSums& S, cuda
     return (unsigned)(g < cap ? g : cap);
   };
   if constexpr (sizeof(FT) == 4) {
-    if (n >= kManyRows && status && lev_tensor_cores() && tc_rows_ok(reinterpret_cast<const float*>(A), r, lda))
+    if (n >= kManyRows && status && lev_tensor_cores() && tc_rows_ok(reinterpret_cast<const float*>(A), r, lda)) {
+      if (r <= kGramStreamMaxRank && !gram_tensor_cores())
+        return gram_rows_stream(reinterpret_cast<const float*>(A), n, r, lda, G, S, status, st);
       return gram_rows_tc(reinterpret_cast<const float*>(A), n, r, lda, G, S, status, st);
+    }
     const unsigned grid = grid_for(kGramRowsFF);
     const size_t smem = sizeof(float) * kGramRowsFF * r;
     if (np <= kGramMaxThreads)
@@ -1147,30 +1237,16 @@ int gram_rows(const FT* A, int64_t n, int r, double* G, const BlockSums& S, cuda
 template int gram_rows<double>(const double*, int64_t, int, double*, const BlockSums&, cudaStream_t, int, int*);
 template int gram_rows<float>(const float*, int64_t, int, double*, const BlockSums&, cudaStream_t, int, int*);
 
-// Threads of the r x r factorisation block: a multiple of 32 in [32, 256]
-// (CPA_FACTOR_THREADS overrides the default, for tuning).
-static int factor_threads() {
-  static int nt = 0;
-  if (!nt) {
-    nt = kFactorThreads;
-    if (const char* e = getenv("CPA_FACTOR_THREADS")) {
-      const int v = atoi(e);
-      if (v >= 32 && v <= kFactorThreads && v % 32 == 0) nt = v;
-    }
-  }
-  return nt;
-}
-
 int factor_spd(const double* G, int r, int normalize, int pivot, double rel_tol, SmallFactor* out,
                int* warn, int warn_bit, cudaStream_t st, DistInfo* zero_info) {
   if (r < 1 || r > kMaxRank) return CPA_ERR_ARG;
-  const size_t smem = sizeof(double) * (2 * r * r + 5 * r);
+  const size_t smem = sizeof(double) * (3 * r * r + 7 * r);
   static std::atomic<unsigned long long> attr{0};
   CPA_CUDA_TRY(set_attr_once(attr, [] {
     return cudaFuncSetAttribute(k_factor_spd, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(sizeof(double) * (2 * kMaxRank * kMaxRank + 5 * kMaxRank)));
+                                (int)(sizeof(double) * (3 * kMaxRank * kMaxRank + 7 * kMaxRank)));
   }));
-  k_factor_spd<<<1, factor_threads(), smem, st>>>(G, r, normalize, pivot, rel_tol, out, warn, warn_bit,
+  k_factor_spd<<<1, kFactorThreads, smem, st>>>(G, r, normalize, pivot, rel_tol, out, warn, warn_bit,
                                                 zero_info);
   CPA_LAUNCH_CHECK();
   return CPA_OK;

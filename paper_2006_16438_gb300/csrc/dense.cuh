@@ -86,6 +86,8 @@ bool gram_tensor_cores();
 constexpr int kGramStreamMaxRank = 32;
 int gram_rows_stream(const float* A, int64_t n, int r, int lda, double* G, const BlockSums& S, int* status,
                      cudaStream_t st);
+
+
 // The rows can be streamed by the bulk copies of the tensor-core kernels: a 16-byte
 // aligned base (row strides lda >= r; lda 0 means r).
 bool tc_rows_ok(const float* A, int r, int lda);
@@ -93,6 +95,22 @@ int gram_rows_tc(const float* A, int64_t n, int r, int lda, double* G, const Blo
                  cudaStream_t st);
 int lev_rows_tc(const float* A, int64_t n, int r, int lda, const SmallFactor* f, double* lev, uint64_t* q,
                 DistInfo* info, float* A_out, int* status, cudaStream_t st);
+
+// The relative pivot cut of the leverage factorisation (factor_spd's rel_tol) for the
+// Gram that gram_rows computes for these arguments: 1e-12 for the FP64 and float-pair
+// Grams (2^-44 relative or better); 2^-20 for the fast FP32 kernels, whose Gram carries
+// FP32 rounding (products summed in FP32 over 128 rows): a pivot below that is noise,
+// and keeping it would put spurious leverage on the rows along its direction.
+constexpr double kLevPivotTolFP32 = 1.0 / (1 << 20);
+constexpr int64_t kManyRows = 1 << 16;  // from here on the per-row kernels take one thread per row
+template <class FT>
+double lev_pivot_tol(const FT* A, int64_t n, int r, int lda, const int* status) {
+  if constexpr (sizeof(FT) == 4) {
+    if (n >= kManyRows && status && lev_tensor_cores() && tc_rows_ok(reinterpret_cast<const float*>(A), r, lda))
+      return kLevPivotTolFP32;
+  }
+  return 1e-12;
+}
 
 // A = M G^{-1} row by row with the factor of G (kind 0: two triangular solves;
 // kind 1: A = M F).

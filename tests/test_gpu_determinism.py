@@ -56,13 +56,15 @@ def test_fp64_reruns_bit_identical_uber_shaped_50_iterations():
 def test_long_run_rows_bit_exact_against_oracle():
     """A 4-way planted count tensor with 2e5 nonzeros (planted rank 25, Zipf(1.1)),
     r = 25, s = 2^14, hybrid sampling: 10 outer iterations of single mode updates, the
-    GPU and the oracle each continuing from its own factors.  At every update the
-    sampled rows and counts are equal bit for bit.  The factors: the early iterations
-    of Alg. 3 from a random start amplify any difference in the last bits (about 10^5
-    over 10 iterations here: the oracle itself, started from factors perturbed by
-    1e-15 relative, ends 1e-10 away from its unperturbed run), so the GPU's distance
-    from the oracle is held to 1e-10 for the first five iterations and, at every
-    update, to 20 times the oracle's own distance under that perturbation."""
+    GPU and the oracle each continuing from its own factors.  At every update:
+    * the sampled rows, counts and sample sizes are equal bit for bit (the oracle on its
+      own trajectory);
+    * the GPU's new factor and lambda are within 1e-10 of the oracle's update taken from
+      the GPU's current factors (each step's arithmetic, at every step of the run).
+    The two trajectories' factors are held to 1e-10 for the first five iterations only:
+    the early iterations of Alg. 3 from a random start amplify any difference in the last
+    bits (the oracle itself, started from factors perturbed by 1e-15 relative, ends about
+    1e-10 away from its unperturbed run after 10 iterations)."""
     dims, r, s = (120, 90, 110, 80), 25, 2 ** 14
     coo = synth.planted_cp_tensor(dims, r, target_nnz=200000, seed=31, zipf_alpha=1.1)
     assert coo.nnz >= 196000
@@ -71,24 +73,23 @@ def test_long_run_rows_bit_exact_against_oracle():
     oi = oracle.Index(coo)
     fg = [cu(a) for a in init]
     fo = [a.copy() for a in init]
-    noise = np.random.default_rng(1)
-    fp = [a * (1.0 + 1e-15 * noise.standard_normal(a.shape)) for a in init]
     for it in range(10):
         for k in range(len(dims)):
+            before = [f.cpu().numpy() for f in fg]
             got = cpa.cpa_mode_update(gi, fg, k, rank=r, samples=s, tau=1.0 / s, seed=5, it=it)
             ref = oracle.mode_update(oi, fo, k, rank=r, samples=s, tau=1.0 / s, seed=5, it=it)
-            per = oracle.mode_update(oi, fp, k, rank=r, samples=s, tau=1.0 / s, seed=5, it=it)
+            one = oracle.mode_update(oi, before, k, rank=r, samples=s, tau=1.0 / s, seed=5, it=it)
             assert got["sbar"] == ref["sbar"] and got["sdet"] == ref["sdet"], (it, k)
             np.testing.assert_array_equal(got["idx"].cpu().numpy().astype(np.uint64), ref["idx"])
             np.testing.assert_array_equal(got["cnt"].cpu().numpy().astype(np.uint32), ref["cnt"])
+            np.testing.assert_array_equal(got["idx"].cpu().numpy().astype(np.uint64), one["idx"])
             fo[k] = ref["A"]
-            fp[k] = per["A"]
-            e = relerr(fg[k].cpu().numpy(), ref["A"])
-            e_self = relerr(per["A"], ref["A"])
+            step = relerr(fg[k].cpu().numpy(), one["A"])
+            assert step < 1e-10, (it, k, step)
+            assert relerr(got["lam"].cpu().numpy(), one["lam"]) < 1e-10, (it, k)
             if it < 5:
+                e = relerr(fg[k].cpu().numpy(), ref["A"])
                 assert e < 1e-10, (it, k, e)
-            assert e <= 20.0 * e_self + 1e-12, (it, k, e, e_self)
-            assert relerr(got["lam"].cpu().numpy(), ref["lam"]) <= 20.0 * relerr(per["lam"], ref["lam"]) + 1e-12
 
 
 @pytest.mark.parametrize("dims,nnz,k", [((2, 300, 200), 60000, 0), ((5, 70, 90), 25000, 0),
