@@ -195,8 +195,9 @@ STAGES = ["sample", "krp_gram", "mttkrp", "solve", "leverage", "fit"]
 
 
 def captured_traffic(kernel, source):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary
-    (profiles/traffic.json), or None when the kernel's source changed since."""
+    """DRAM bytes of `kernel` (per launch, or per mode update for a stage) from the
+    committed ncu summary (profiles/traffic.json), or None when the kernel's source
+    changed since the capture."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
@@ -204,7 +205,7 @@ def captured_traffic(kernel, source):
         with open(os.path.join(ROOT, source), "rb") as f:
             if hashlib.sha1(f.read()).hexdigest() != rec["source_sha1"]:
                 return None
-        return rec["dram_bytes_per_launch"]
+        return rec.get("dram_bytes_per_launch", rec.get("dram_bytes_per_update"))
     except Exception:
         return None
 WHOLE = 8
@@ -601,8 +602,8 @@ def run_large(args, spec, rank, world, local):
     roof.update({
         "kernel": "sampled MTTKRP, FP64 (k_slab_prep: probe + sampled Khatri-Rao rows times the inverse sampled "
                   "Gram; k_slab_light + k_slab_heavy: FP64 products added into row slabs of A_k)",
-        "traffic": captured_traffic("k_slab_light<double>", "paper_2006_16438_gb300/csrc/mttkrp.cu"),
-        "traffic_unit": "DRAM bytes per launch (ncu, profiles/traffic.json)",
+        "traffic": captured_traffic(f"sampled_mttkrp_fp64_{args.workload}", "paper_2006_16438_gb300/csrc/mttkrp.cu"),
+        "traffic_unit": "DRAM bytes per mode update, all launches of the stage (ncu, profiles/traffic.json)",
         "fp64_pipe": {"achieved": fp64_rate, "peak": FP64_OPS_PEAK, "unit": "T FP64 instructions/s",
                       "frac": fp64_rate / FP64_OPS_PEAK if fp64_rate else None,
                       "peak_source": "derived: 152 SMs x 2 FP64 lanes/clk x 2.07 GHz"}})
@@ -633,7 +634,12 @@ def run_large(args, spec, rank, world, local):
             "value": mv, "unit": UNIT, "speedup_vs_fp64": mv / value,
             "fit": {"estimated": mixed["est_fit"], "exact": mixed["exact_fit"]},
             "exact_fit_diff_vs_fp64": mixed["exact_fit"] - f64["exact_fit"],
-            "stages_ms_per_update": stage_table(stm), "mttkrp_hbm": mttkrp_rates(stm, 4),
+            "stages_ms_per_update": stage_table(stm),
+            "mttkrp_hbm": dict(mttkrp_rates(stm, 4),
+                               traffic=captured_traffic(f"sampled_mttkrp_mixed_{args.workload}",
+                                                        "paper_2006_16438_gb300/csrc/mttkrp.cu"),
+                               traffic_unit="DRAM bytes per mode update, all launches of the stage (ncu, "
+                                            "profiles/traffic.json)"),
             "clocks": mixed["clocks"], "gpu_launches": mixed["launches"],
             "note": "same range-finder start and epochs as the FP64 series; FP32 factors, Grams and sampled "
                     "products, FP64 factorisations and leverage; exact fits (Eq. 5.1) after the same epochs"}

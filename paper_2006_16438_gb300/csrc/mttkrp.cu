@@ -15,12 +15,12 @@
 //    are taken from a counter; fibres longer than kHeavy are listed and spread over
 //    the warps of one block each by k_tnsr_heavy.  The KRP rows are never written.
 //
-// When M is larger than one slab (128 MB, about the L2 size; CPA_MTTKRP_SLAB_BYTES
+// When M is larger than one slab (96 MB in FP32, 256 MB in FP64; CPA_MTTKRP_SLAB_BYTES
 // sets it, 0 turns slabs off), M's rows are split into P slabs.  k_slab_prep probes
 // every sample's fibre once, stores u_j and, since the nonzeros of a fibre are sorted
 // by i_k, where each slab's rows start in the fibre; then for p = 0..P-1, k_slab_light
 // and k_slab_heavy add the nonzeros of slab p only.  Every nonzero is read once; the
-// additions of one pass hit one slab of M, which stays in L2, instead of
+// additions of one pass hit one slab of M, which (in FP32) stays in L2, instead of
 // read-modify-writes of rows scattered over the whole of M in DRAM.
 #include <stdlib.h>
 
@@ -1070,21 +1070,24 @@ int launch_mttkrp(const cpa_index* X, int k, const FactorPtrs& F, int r, const u
 
 }  // namespace
 
-size_t mttkrp_slab_bytes() {
+size_t mttkrp_slab_bytes(int ftb) {
   const char* e = getenv("CPA_MTTKRP_SLAB_BYTES");
   if (e) {
     const long long v = atoll(e);
     return v > 0 ? (size_t)v : 0;  // 0: one pass whatever M's size
   }
-  // About the L2 size.  Measured per update: 1.75e9 nonzeros (M of 480 and 180 MB)
-  // 1.29 ms in one pass, 1.34 with 64 MB and 1.18 with 128 MB slabs; 4.68e9 nonzeros
-  // (M of 820 MB) 5.95, 4.77 and 4.48 ms.
-  return size_t(128) << 20;
+  // Measured per update on the 4.68e9-nonzero Reddit-shaped tensor (M of 1.64 GB in
+  // FP64, 0.82 GB in FP32), sampled MTTKRP in ms for slabs of 32 / 64 / 96 / 128 / 256 /
+  // 512 MB and one pass: FP64 11.40 / 10.81 / 10.15 / 9.82 / 9.44 / 10.04 / 10.88;
+  // FP32 3.92 / 3.34 / 3.18 / 3.85 / 5.04 / - / -.  The FP32 vector atomics gain from a
+  // slab that stays in L2; the FP64 row additions are bound by the L2's FP64 atomic
+  // rate, and for them fewer passes count more.
+  return size_t(ftb == 8 ? 256 : 96) << 20;
 }
 
 int mttkrp_slabs(int64_t nk, int r, int ftb) {
   const size_t bytes = (size_t)nk * r * ftb;
-  const size_t slab = mttkrp_slab_bytes();
+  const size_t slab = mttkrp_slab_bytes(ftb);
   if (slab == 0 || bytes <= slab || nk < 2) return 1;
   int64_t P = (int64_t)((bytes + slab - 1) / slab);
   if (P > kSlabMax) P = kSlabMax;

@@ -55,10 +55,10 @@ struct MttkrpBuffers {
 constexpr int kMttkrpCounters = 6 + 3 * 32;  // words kMttkrpCounters - 2 and - 1: Gram ticket, status
 constexpr int kSlabMax = 31;  // most row slabs of one M
 
-// Bytes of M per row slab (128 MB, or CPA_MTTKRP_SLAB_BYTES; 0 = no slabs): M
-// larger than this is accumulated slab by slab, the additions of a pass confined to
-// one slab of rows.
-size_t mttkrp_slab_bytes();
+// Bytes of M per row slab for ftb-byte elements (96 MB for FP32, 256 MB for FP64, or
+// CPA_MTTKRP_SLAB_BYTES; 0 = no slabs): M larger than this is accumulated slab by
+// slab, the additions of a pass confined to one slab of rows.
+size_t mttkrp_slab_bytes(int ftb);
 // Number of row slabs of an n_k x r M of ftb-byte elements (1: no slabs).
 int mttkrp_slabs(int64_t nk, int r, int ftb);
 
