@@ -67,6 +67,10 @@ def parse():
                    help="elements of the estimated fit's sample (billion-nonzero workloads)")
     p.add_argument("--fraction", "--amazon-fraction", dest="fraction", type=float, default=1.0,
                    help="fraction of the amazon- or reddit-shaped tensor's events (dims kept)")
+    p.add_argument("--shrink", type=int, default=1,
+                   help="amazon/reddit: every dimension divided by this and the events by its cube (the same "
+                        "planted model at a few GB, for profiler captures); the estimated fit's sample shrinks "
+                        "with the events")
     p.add_argument("--cpu-fraction", type=float, default=1.0 / 1024,
                    help="fraction of the events in the oracle's same-shape tensor (billion-nonzero workloads)")
     p.add_argument("--cpu-procs", type=int, default=0,
@@ -460,10 +464,16 @@ LARGE = {
 REF_SHRINK = 16
 
 
-def large_workload_name(spec, nnz, frac):
-    return (f"{spec['name']} {'x'.join(str(n) for n in spec['dims'])} planted {spec['values']}, {nnz} nnz"
-            f"{'' if frac == 1.0 else f' ({frac:g} of the events)'}, r=25, s=2^17, tau=2^-17, range-finder "
-            "start, estimated fit 2^27")
+def large_workload_name(spec, nnz, frac, fit_samples=1 << 27, shrink=1):
+    fs = int(fit_samples)
+    fit = f"2^{fs.bit_length() - 1}" if fs & (fs - 1) == 0 else str(fs)
+    scale = ""
+    if shrink > 1:
+        scale = f" (the model with dimensions / {shrink} and events / {shrink}^3)"
+    elif frac != 1.0:
+        scale = f" ({frac:g} of the events)"
+    return (f"{spec['name']} {'x'.join(str(n) for n in spec['dims'])} planted {spec['values']}, {nnz} nnz{scale}, "
+            f"r=25, s=2^17, tau=2^-17, range-finder start, estimated fit {fit}")
 
 
 def large_mttkrp_bytes(st, dims, b_f):
@@ -495,6 +505,11 @@ def run_large(args, spec, rank, world, local):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     stream = torch.cuda.current_stream()
     frac = args.fraction
+    shrink = max(1, args.shrink)
+    if shrink > 1:  # the same model at a profiler-sized scale
+        spec = dict(spec, dims=tuple(max(RANK, n // shrink) for n in spec["dims"]))
+        frac = frac / shrink ** 3
+        args.fit_samples = max(1 << 16, args.fit_samples // shrink ** 3)
     dims = spec["dims"]
     t0 = time.perf_counter()
     idx, vals = sgpu.planted_cp_tensor_gpu(dims, RANK, events=int(spec["events_per_nnz"] * spec["nnz"] * frac),
@@ -602,7 +617,8 @@ def run_large(args, spec, rank, world, local):
     roof.update({
         "kernel": "sampled MTTKRP, FP64 (k_slab_prep: probe + sampled Khatri-Rao rows times the inverse sampled "
                   "Gram; k_slab_light + k_slab_heavy: FP64 products added into row slabs of A_k)",
-        "traffic": captured_traffic(f"sampled_mttkrp_fp64_{args.workload}", "paper_2006_16438_gb300/csrc/mttkrp.cu"),
+        "traffic": (captured_traffic(f"sampled_mttkrp_fp64_{args.workload}", "paper_2006_16438_gb300/csrc/mttkrp.cu")
+                    if shrink == 1 and frac == 1.0 else None),
         "traffic_unit": "DRAM bytes per mode update, all launches of the stage (ncu, profiles/traffic.json)",
         "fp64_pipe": {"achieved": fp64_rate, "peak": FP64_OPS_PEAK, "unit": "T FP64 instructions/s",
                       "frac": fp64_rate / FP64_OPS_PEAK if fp64_rate else None,
@@ -612,7 +628,7 @@ def run_large(args, spec, rank, world, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": f64["total_ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": large_workload_name(spec, nnz, frac),
+        "config": {"workload": large_workload_name(spec, nnz, frac, args.fit_samples, shrink),
                    "step": "1 epoch = 5 outer iterations x 3 mode updates + estimated fit",
                    "l2": f"inputs far larger than L2 ({index.device_bytes() / 1e9:.0f} GB of index)",
                    "parallelism": f"{world} independent replicas" if world > 1 else "single GPU"},
@@ -636,8 +652,9 @@ def run_large(args, spec, rank, world, local):
             "exact_fit_diff_vs_fp64": mixed["exact_fit"] - f64["exact_fit"],
             "stages_ms_per_update": stage_table(stm),
             "mttkrp_hbm": dict(mttkrp_rates(stm, 4),
-                               traffic=captured_traffic(f"sampled_mttkrp_mixed_{args.workload}",
-                                                        "paper_2006_16438_gb300/csrc/mttkrp.cu"),
+                               traffic=(captured_traffic(f"sampled_mttkrp_mixed_{args.workload}",
+                                                         "paper_2006_16438_gb300/csrc/mttkrp.cu")
+                                        if shrink == 1 and frac == 1.0 else None),
                                traffic_unit="DRAM bytes per mode update, all launches of the stage (ncu, "
                                             "profiles/traffic.json)"),
             "clocks": mixed["clocks"], "gpu_launches": mixed["launches"],

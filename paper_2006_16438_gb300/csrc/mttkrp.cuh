@@ -27,7 +27,7 @@ struct DetBuffers {
   int64_t* crow = nullptr;
   int* cmid = nullptr;
 };
-constexpr int kDetTile = 256;                 // sorted items per tile
+constexpr int kDetTile = 128;                 // sorted items per tile
 constexpr int64_t kDetMaxItems = 1ll << 24;   // largest tensor (nonzeros) of the reproducible path
 
 // Device buffers of one sampled MTTKRP for up to s samples.

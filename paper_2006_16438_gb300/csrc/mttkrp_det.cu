@@ -194,29 +194,42 @@ __global__ void __launch_bounds__(kThreads) k_det_tiles(const uint64_t* __restri
         kl = keys[g + lane];
         vl = vals[g + lane];
       }
-      for (int q = 0; q < nb; ++q) {
-        const uint64_t kq = __shfl_sync(0xffffffffu, kl, q);
-        const double x = __longlong_as_double((long long)__shfl_sync(0xffffffffu, vl, q));
-        const int64_t row = item_row(kq);
-        const int64_t j = (int64_t)(kq >> 32);
-        if (row != cur) {
-          if (cur >= 0) flush(false);
-          cur = row;
-          run = 0;
-        }
-        const int ch = (int)(run & 3);
+      // eight items at a time: their factor rows are loaded before any is added
+      for (int q0 = 0; q0 < nb; q0 += 8) {
+        uint64_t kb[8];
+        double xb[8], ub[8][CPL];
 #pragma unroll
-        for (int v = 0; v < CPL; ++v) {
-          const int c = lane + 32 * v;
-          if (c < r) {
-            const double u = U[j * r + c];
+        for (int t8 = 0; t8 < 8; ++t8) {
+          const int q = q0 + t8 < nb ? q0 + t8 : nb - 1;
+          kb[t8] = __shfl_sync(0xffffffffu, kl, q);
+          xb[t8] = __longlong_as_double((long long)__shfl_sync(0xffffffffu, vl, q));
+          const int64_t j = (int64_t)(kb[t8] >> 32);
+#pragma unroll
+          for (int v = 0; v < CPL; ++v) {
+            const int c = lane + 32 * v;
+            ub[t8][v] = c < r ? U[j * r + c] : 0.0;
+          }
+        }
+#pragma unroll
+        for (int t8 = 0; t8 < 8; ++t8) {
+          if (q0 + t8 >= nb) break;
+          const int64_t row = item_row(kb[t8]);
+          if (row != cur) {
+            if (cur >= 0) flush(false);
+            cur = row;
+            run = 0;
+          }
+          const int ch = (int)(run & 3);
+#pragma unroll
+          for (int v = 0; v < CPL; ++v) {
+            const double x = xb[t8], u = ub[t8][v];
             if (ch == 0) c0[v] = fma(x, u, c0[v]);
             else if (ch == 1) c1[v] = fma(x, u, c1[v]);
             else if (ch == 2) c2[v] = fma(x, u, c2[v]);
             else c3[v] = fma(x, u, c3[v]);
           }
+          ++run;
         }
-        ++run;
       }
     }
     if (cur >= 0) flush(true);

@@ -95,7 +95,7 @@ def test_long_run_rows_bit_exact_against_oracle():
 @pytest.mark.parametrize("dims,nnz,k", [((2, 300, 200), 60000, 0), ((5, 70, 90), 25000, 0),
                                         ((40, 30, 20), 8000, 2)])
 def test_sampled_mttkrp_rows_across_tiles(dims, nnz, k):
-    """Rows whose sampled nonzeros span many 256-item tiles (two or five rows in mode
+    """Rows whose sampled nonzeros span many 128-item tiles (two or five rows in mode
     0) and rows inside one tile: M equals the oracle's within 1e-12, and two calls
     give the same M bit for bit."""
     coo = synth.random_sparse_tensor(dims, nnz, seed=41)
