@@ -360,7 +360,11 @@ def main():
         mk_ms = stg[2]
         mk_bytes = mttkrp_bytes(acc, d - 1, b_f) + nk_bytes
         mk_gbs = mk_bytes / (mk_ms / 1000.0) / 1e9 if mk_ms > 0 else None
-        mk = {"bound": "hbm", "kernel": "k_tnsr_mttkrp (probe + sampled KRP + sampled MTTKRP)",
+        mk_kernel = ("k_det_prep + k_det_expand + radix sort + k_det_tiles + k_det_fixup (probe + sampled KRP; "
+                     "the sampled nonzeros sorted by row and reduced in fixed tiles: reproducible FP64)"
+                     if b_f == 8 and os.environ.get("CPA_DET_MTTKRP", "1") != "0"
+                     else "k_tnsr_mttkrp + k_tnsr_heavy (probe + sampled KRP + sampled MTTKRP, atomics)")
+        mk = {"bound": "hbm", "kernel": mk_kernel,
               "achieved": mk_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
               "frac": (mk_gbs / peaks["hbm_gbs"]) if mk_gbs else None,
               "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",

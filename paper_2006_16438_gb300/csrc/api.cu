@@ -555,7 +555,7 @@ struct Plan {
     for (int m = 0; m < D; ++m) F.A[m] = Fm[m];
     if (kind == CPA_FIT_ESTIMATED)
       return prec == CPA_MIXED ? fit_estimate_enqueue<float>(X, est, F, lam, r, fitd, st)
-                               : fit_estimate_enqueue<double>(X, est, F, lam, r, fitd, st);
+                               : fit_estimate_enqueue<double>(X, est, F, lam, r, fitd, st, static_cast<double*>(M));
     return prec == CPA_MIXED ? fit_enqueue<float>(X, F, lam, r, fit_ws, sums_lev, fitd, st)
                              : fit_enqueue<double>(X, F, lam, r, fit_ws, sums_lev, fitd, st);
   }

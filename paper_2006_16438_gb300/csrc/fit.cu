@@ -327,6 +327,8 @@ constexpr int kErWarps = 4;
 constexpr int kErSamples = 16;  // samples per warp and round
 constexpr int kErMaxRank = 32;
 
+// lambda null: lambda is folded into the rows of one factor of F (one multiply fewer
+// per coordinate).
 template <int MD>
 __global__ void __launch_bounds__(32 * kErWarps, 2) k_fit_est_rows(const int32_t* __restrict__ coords, int64_t stride,
                                                                    const double* __restrict__ xs, int64_t S,
@@ -340,7 +342,8 @@ __global__ void __launch_bounds__(32 * kErWarps, 2) k_fit_est_rows(const int32_t
   const int bufd = MD * kErSamples * rs;     // doubles of one buffer
   double* lam = er_smem;                     // kErMaxRank
   double* rows = er_smem + kErMaxRank + (size_t)warp * 2 * bufd;
-  for (int c = threadIdx.x; c < r; c += blockDim.x) lam[c] = lambda[c];
+  for (int c = threadIdx.x; c < r; c += blockDim.x) lam[c] = lambda ? lambda[c] : 1.0;
+  const bool folded = lambda == nullptr;
   __syncthreads();
   const int64_t gw = (int64_t)blockIdx.x * kErWarps + warp, nw = (int64_t)gridDim.x * kErWarps;
   const int64_t nrounds = S > gw * kErSamples ? (S - 1 - gw * kErSamples) / (nw * kErSamples) + 1 : 0;
@@ -391,16 +394,16 @@ __global__ void __launch_bounds__(32 * kErWarps, 2) k_fit_est_rows(const int32_t
     const double* R = rows + (size_t)(k & 1) * bufd + sm * rs;
     double m0 = 0.0, m1 = 0.0;
     for (int c = h; c < r; c += 4) {
-      double t = lam[c];
+      double t = folded ? R[c] : lam[c] * R[c];
 #pragma unroll
-      for (int m = 0; m < MD - 1; ++m)
+      for (int m = 1; m < MD - 1; ++m)
         if (m < D - 1) t *= R[m * kErSamples * rs + c];
       m0 = fma(t, R[(D - 1) * kErSamples * rs + c], m0);
       const int c2 = c + 2;
       if (c2 < r) {
-        double t2 = lam[c2];
+        double t2 = folded ? R[c2] : lam[c2] * R[c2];
 #pragma unroll
-        for (int m = 0; m < MD - 1; ++m)
+        for (int m = 1; m < MD - 1; ++m)
           if (m < D - 1) t2 *= R[m * kErSamples * rs + c2];
         m1 = fma(t2, R[(D - 1) * kErSamples * rs + c2], m1);
       }
@@ -425,6 +428,14 @@ __global__ void __launch_bounds__(32 * kErWarps, 2) k_fit_est_rows(const int32_t
     for (int w = 0; w < kErWarps; ++w) b += red[w];
     partial[blockIdx.x] = b;
   }
+}
+
+// out = A diag(lambda) for an n x r row-major factor (lambda folded into its rows).
+__global__ void k_scale_cols(const double* __restrict__ A, int64_t n, int r, const double* __restrict__ lambda,
+                             double* __restrict__ out) {
+  const int64_t total = n * r;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = A[e] * lambda[e % r];
 }
 
 size_t fit_est_rows_smem(int r, int md) {
@@ -608,7 +619,7 @@ static bool rows_est_enabled() {
 
 template <class FT>
 int fit_estimate_enqueue(const cpa_index* X, const FitSample& S, const FactorPtrs& F, const double* lambda,
-                         int r, double* fit_dev, cudaStream_t st) {
+                         int r, double* fit_dev, cudaStream_t st, double* fold_scratch) {
   const int64_t n = S.s_nz + S.s_z;
   const int nb = est_blocks(n);
   const int D = X->order;
@@ -634,12 +645,26 @@ int fit_estimate_enqueue(const cpa_index* X, const FitSample& S, const FactorPtr
       return cudaFuncSetAttribute(k_fit_est_rows<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)fit_est_rows_smem(kErMaxRank, 4));
     }));
+    // lambda folded into the rows of the mode with the fewest rows (any mode will do:
+    // the kernel multiplies the D rows of a sample and drops its lambda multiply)
+    FactorPtrs G = F;
+    const double* lam = lambda;
+    if (fold_scratch) {
+      int mf = 0;
+      for (int m = 1; m < D; ++m)
+        if (X->dims[m] < X->dims[mf]) mf = m;
+      const int64_t cnt = X->dims[mf] * r;
+      k_scale_cols<<<(unsigned)std::min<int64_t>(ceil_div(cnt, 256), 4096), 256, 0, st>>>(
+          static_cast<const double*>(F.A[mf]), X->dims[mf], r, lambda, fold_scratch);
+      G.A[mf] = fold_scratch;
+      lam = nullptr;
+    }
     if (D <= 3)
-      k_fit_est_rows<3><<<nb, 32 * kErWarps, smem, st>>>(S.coords, S.stride, S.xs, n, S.s_nz, S.phi[0], S.phi[1], F,
-                                                          lambda, r, D, S.partial);
+      k_fit_est_rows<3><<<nb, 32 * kErWarps, smem, st>>>(S.coords, S.stride, S.xs, n, S.s_nz, S.phi[0], S.phi[1], G,
+                                                          lam, r, D, S.partial);
     else
-      k_fit_est_rows<4><<<nb, 32 * kErWarps, smem, st>>>(S.coords, S.stride, S.xs, n, S.s_nz, S.phi[0], S.phi[1], F,
-                                                          lambda, r, D, S.partial);
+      k_fit_est_rows<4><<<nb, 32 * kErWarps, smem, st>>>(S.coords, S.stride, S.xs, n, S.s_nz, S.phi[0], S.phi[1], G,
+                                                          lam, r, D, S.partial);
   } else if (r <= 8) launch(std::integral_constant<int, 1>());
   else if (r <= 16) launch(std::integral_constant<int, 2>());
   else if (r <= 32) launch(std::integral_constant<int, 4>());
@@ -650,8 +675,8 @@ int fit_estimate_enqueue(const cpa_index* X, const FitSample& S, const FactorPtr
   return CPA_OK;
 }
 template int fit_estimate_enqueue<double>(const cpa_index*, const FitSample&, const FactorPtrs&, const double*,
-                                          int, double*, cudaStream_t);
+                                          int, double*, cudaStream_t, double*);
 template int fit_estimate_enqueue<float>(const cpa_index*, const FitSample&, const FactorPtrs&, const double*,
-                                         int, double*, cudaStream_t);
+                                         int, double*, cudaStream_t, double*);
 
 }  // namespace cpa

@@ -52,8 +52,10 @@ int fit_sample_sort(const cpa_index* X, FitSample* S, cudaStream_t st);
 
 // Enqueues F_hat = sum_j phi_j (m_j - x_j)^2 over the sample and *fit_dev =
 // 1 - sqrt(F_hat) / ||X|| (fit_dev[1] = F_hat).  Deterministic for a given grid.
+// fold_scratch (FP64, may be null): min_m n_m x r doubles the FP64 kernel may use for
+// the factor with lambda folded into its rows.
 template <class FT>
 int fit_estimate_enqueue(const cpa_index* X, const FitSample& S, const FactorPtrs& F, const double* lambda,
-                         int r, double* fit_dev, cudaStream_t st);
+                         int r, double* fit_dev, cudaStream_t st, double* fold_scratch = nullptr);
 
 }  // namespace cpa
