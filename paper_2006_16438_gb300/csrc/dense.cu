@@ -1087,9 +1087,11 @@ __global__ void __launch_bounds__(kRowThreads) k_lev_rows_ffd(const double* A, i
   // 8 r + 4 (2 r^2 + 2 r) bytes before it: 8-byte aligned
   float2* xs = reinterpret_cast<float2*>(scl + r);  // kRowThreads * ld (S a as float pairs)
   __shared__ int perm[kMaxRank];
+  __shared__ int ipos[kMaxRank];  // kind 0: position of column c in the pivot order
   const int ld = r | 1;
   const int kind = f->kind;
   const int k = kind == 0 ? f->rank : r;
+  const double inv_r = 1.0 / (double)r;
   for (int i = threadIdx.x; i < r * r; i += blockDim.x) {
     const double v = f->F[i];
     const float h = (float)v;
@@ -1104,7 +1106,10 @@ __global__ void __launch_bounds__(kRowThreads) k_lev_rows_ffd(const double* A, i
     const double l = f->lambda[i];
     ilam[i] = pos_finite(l) ? 1.0 / l : 1.0;
     perm[i] = f->perm[i];
+    ipos[f->perm[i]] = kind == 0 ? i : f->perm[i];
   }
+  if (kind != 0)
+    for (int i = threadIdx.x; i < r; i += blockDim.x) ipos[i] = i;
   uint64_t my_max = 0;
   uint32_t my_nz = 0;
   for (int64_t row0 = (int64_t)blockIdx.x * kRowThreads; row0 < n; row0 += (int64_t)gridDim.x * kRowThreads) {
@@ -1116,7 +1121,7 @@ __global__ void __launch_bounds__(kRowThreads) k_lev_rows_ffd(const double* A, i
       const float p = __fmul_rn(x.x, sch[c]);
       const float rest = __fmaf_rn(x.x, scl[c], __fmaf_rn(x.y, sch[c], __fmaf_rn(x.x, sch[c], -p)));
       const float h = __fadd_rn(p, rest);
-      xs[rr * ld + c] = make_float2(h, __fsub_rn(rest, __fsub_rn(h, p)));
+      xs[rr * ld + ipos[c]] = make_float2(h, __fsub_rn(rest, __fsub_rn(h, p)));  // pivot order (kind 0)
     }
     __syncthreads();
     if (threadIdx.x < rows) {
@@ -1128,7 +1133,7 @@ __global__ void __launch_bounds__(kRowThreads) k_lev_rows_ffd(const double* A, i
         for (int c = 0; c < k; ++c) {
           float th = 0.f, tl = 0.f;
           for (int u = 0; u <= c; ++u) {
-            const float2 bu = b[perm[u]];
+            const float2 bu = b[u];
             ff_fma(Fh[c * r + u], Fl[c * r + u], bu.x, bu.y, th, tl);
           }
           float s, e;
@@ -1146,7 +1151,7 @@ __global__ void __launch_bounds__(kRowThreads) k_lev_rows_ffd(const double* A, i
       }
       if (lev) lev[row] = l;
       if (q) {
-        double pr = l / (double)r;
+        double pr = l * inv_r;
         pr = clamp01(pr);
         const uint64_t qi = __double2ull_rn(pr * 4611686018427387904.0);  // 2^62
         q[row] = qi;
