@@ -366,9 +366,12 @@ int cpa_philox4x64(const uint64_t* ctr, const uint64_t* key, int64_t n, uint64_t
 
 /* Leverage scores of a factor matrix (Definition 3.4): lev_i = a_i^T (A^T A)^+ a_i,
  * the squared row norms of any orthonormal basis of range(A).  A^T A is formed in
- * FP64 and factored by Cholesky; if that fails the pseudo-inverse from a Jacobi
+ * FP64 (from 65,536 rows on in float-pair arithmetic, about 2^-44 relative) and
+ * factored by Cholesky; if that fails the pseudo-inverse from a Jacobi
  * eigendecomposition is used and CPA_WARN_RANK_DEFICIENT_LEV is returned.
- *   A (device) n x r row-major doubles; lev (device) n doubles; 1 <= r <= 64. */
+ *   A (device) n x r row-major doubles; lev (device) n doubles; 1 <= r <= 64.
+ * Errors: CPA_ERR_ARG, CPA_ERR_OOM, CPA_ERR_CUDA (also when a bulk copy of the
+ * streaming Gram did not complete within its bounded wait). */
 int cpa_leverage(const double* A, int64_t n, int32_t r, double* lev, void* stream);
 
 /* The leverage scores of cpa_leverage, computed without allocating any memory.

@@ -1014,22 +1014,22 @@ int cpa_leverage(const double* A, int64_t n, int32_t r, double* lev, void* strea
     a.used = 0;
     double* G = a.take<double>(r * r);
     SmallFactor* f = a.take<SmallFactor>(1);
-    int* warn = a.take<int>(1);
+    int* warn = a.take<int>(2);  // warning bits, then the status word of the streaming Gram
     BlockSums sums = a.take_sums(kSumMaxBlocks, gram_sums_width(r));
     if (pass == 0) {
       CPA_TRY(buf.alloc(a.used, st));
       a.base = (char*)buf.p;
       continue;
     }
-    CPA_CUDA_TRY(cudaMemsetAsync(warn, 0, sizeof(int), st));
+    CPA_CUDA_TRY(cudaMemsetAsync(warn, 0, 2 * sizeof(int), st));
     CPA_CUDA_TRY(cudaMemsetAsync(sums.ticket, 0, sizeof(unsigned), st));
-    CPA_TRY(gram_rows<double>(A, n, r, G, sums, st));
+    CPA_TRY(gram_rows<double>(A, n, r, G, sums, st, r, warn + 1));
     CPA_TRY(factor_spd(G, r, 1, 1, 1e-12, f, warn, CPA_WARN_RANK_DEFICIENT_LEV, st));
     CPA_TRY(lev_rows<double>(A, n, r, f, lev, nullptr, nullptr, (double*)nullptr, st));
-    int hwarn = 0;
-    CPA_CUDA_TRY(cudaMemcpyAsync(&hwarn, warn, sizeof(int), cudaMemcpyDeviceToHost, st));
+    int hwarn[2] = {0, 0};
+    CPA_CUDA_TRY(cudaMemcpyAsync(hwarn, warn, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     CPA_CUDA_TRY(cudaStreamSynchronize(st));
-    return hwarn;
+    return hwarn[1] ? hwarn[1] : hwarn[0];
   }
   return CPA_OK;
 }

@@ -1072,31 +1072,40 @@ __global__ void __launch_bounds__(kRowThreads) k_lev_rows_ff(const float* A, int
   }
 }
 
+constexpr int kLevBatch = 5;  // row elements a thread loads before it stages them
+
 // Leverage scores of FP64 rows (kind 0 factors), one thread per row, in float-pair
 // arithmetic as k_lev_rows_ff; the rows are written out divided by lambda in FP64.
+// F is staged as float pairs with each row padded by zeros to r4 (a multiple of 4)
+// entries, and the block's rows S a as float pairs in pivot order with a stride ld
+// = r4 + 2 (16-byte rows, and eight consecutive rows on distinct 16-byte bank groups),
+// so the inner loop takes four products per two 16-byte loads of F (the same address
+// in every thread) and two of the row; the zeros of F past the diagonal make the
+// products past u = c vanish.  The normalised row is written while the row is staged.
 __global__ void __launch_bounds__(kRowThreads) k_lev_rows_ffd(const double* A, int64_t n, int r, int lda,
                                                               const SmallFactor* __restrict__ f,
                                                               double* __restrict__ lev, uint64_t* __restrict__ q,
                                                               DistInfo* info, double* A_out) {
   extern __shared__ __align__(16) unsigned char ffd_smem[];
-  double* ilam = reinterpret_cast<double*>(ffd_smem);  // r: 1 / lambda_c (1 for a zero column)
-  float* Fh = reinterpret_cast<float*>(ilam + r);       // r * r
-  float* Fl = Fh + r * r;                               // r * r
-  float* sch = Fl + r * r;                              // r
-  float* scl = sch + r;                                 // r
-  // 8 r + 4 (2 r^2 + 2 r) bytes before it: 8-byte aligned
-  float2* xs = reinterpret_cast<float2*>(scl + r);  // kRowThreads * ld (S a as float pairs)
-  __shared__ int perm[kMaxRank];
+  const int r4 = (r + 3) & ~3, ld = r4 + 2;
+  float2* Ff = reinterpret_cast<float2*>(ffd_smem);  // r x r4: F as float pairs
+  float2* xs = Ff + r * r4;                           // kRowThreads x ld: S a in pivot order
+  double* ilam = reinterpret_cast<double*>(xs + kRowThreads * ld);  // r: 1 / lambda_c (1 for a zero column)
+  float* sch = reinterpret_cast<float*>(ilam + r);                  // r
+  float* scl = sch + r;                                             // r
   __shared__ int ipos[kMaxRank];  // kind 0: position of column c in the pivot order
-  const int ld = r | 1;
   const int kind = f->kind;
   const int k = kind == 0 ? f->rank : r;
   const double inv_r = 1.0 / (double)r;
-  for (int i = threadIdx.x; i < r * r; i += blockDim.x) {
-    const double v = f->F[i];
+  for (int i = threadIdx.x; i < r * r4; i += blockDim.x) {
+    const int c = i / r4, u = i - c * r4;
+    const double v = u < r ? f->F[c * r + u] : 0.0;
     const float h = (float)v;
-    Fh[i] = h;
-    Fl[i] = (float)(v - (double)h);
+    Ff[i] = make_float2(h, (float)(v - (double)h));
+  }
+  for (int i = threadIdx.x; i < kRowThreads * (r4 - r); i += blockDim.x) {  // zero padding of the rows
+    const int t = i / (r4 - r);
+    xs[t * ld + r + (i - t * (r4 - r))] = make_float2(0.f, 0.f);
   }
   for (int i = threadIdx.x; i < r; i += blockDim.x) {
     const double sc = f->scale[i];
@@ -1105,23 +1114,51 @@ __global__ void __launch_bounds__(kRowThreads) k_lev_rows_ffd(const double* A, i
     scl[i] = (float)(sc - (double)h);
     const double l = f->lambda[i];
     ilam[i] = pos_finite(l) ? 1.0 / l : 1.0;
-    perm[i] = f->perm[i];
-    ipos[f->perm[i]] = kind == 0 ? i : f->perm[i];
+    ipos[i] = i;
   }
-  if (kind != 0)
-    for (int i = threadIdx.x; i < r; i += blockDim.x) ipos[i] = i;
+  __syncthreads();
+  if (kind == 0)
+    for (int i = threadIdx.x; i < r; i += blockDim.x) ipos[f->perm[i]] = i;
+  // the staging walk: element i = threadIdx.x + t kRowThreads of the block's rows, its
+  // (row, column) advanced by (step_r, step_c) with a carry instead of a division
+  const int step_r = kRowThreads / r, step_c = kRowThreads - step_r * r;
+  const int rr0 = threadIdx.x / r, c0 = threadIdx.x - rr0 * r;
   uint64_t my_max = 0;
   uint32_t my_nz = 0;
   for (int64_t row0 = (int64_t)blockIdx.x * kRowThreads; row0 < n; row0 += (int64_t)gridDim.x * kRowThreads) {
     const int rows = (int)(n - row0 < kRowThreads ? n - row0 : kRowThreads);
     __syncthreads();
-    for (int i = threadIdx.x; i < rows * r; i += kRowThreads) {
-      const int rr = i / r, c = i - rr * r;
-      const float2 x = split_ff(A[(row0 + rr) * lda + c]);
-      const float p = __fmul_rn(x.x, sch[c]);
-      const float rest = __fmaf_rn(x.x, scl[c], __fmaf_rn(x.y, sch[c], __fmaf_rn(x.x, sch[c], -p)));
-      const float h = __fadd_rn(p, rest);
-      xs[rr * ld + ipos[c]] = make_float2(h, __fsub_rn(rest, __fsub_rn(h, p)));  // pivot order (kind 0)
+    // kLevBatch loads issued ahead of their stores (A_out may be A, so the compiler
+    // keeps each load behind the previous store otherwise)
+    int rr = rr0, c = c0;
+    const int total = rows * r;
+    for (int i0 = threadIdx.x; i0 < total; i0 += kLevBatch * kRowThreads) {
+      double v[kLevBatch];
+      int rb[kLevBatch], cb[kLevBatch];
+#pragma unroll
+      for (int j = 0; j < kLevBatch; ++j) {
+        rb[j] = rr;
+        cb[j] = c;
+        v[j] = i0 + j * kRowThreads < total ? A[(row0 + rr) * lda + c] : 0.0;
+        rr += step_r;
+        c += step_c;
+        if (c >= r) {
+          c -= r;
+          ++rr;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kLevBatch; ++j) {
+        const int i = i0 + j * kRowThreads;
+        if (i >= total) break;
+        const int cc = cb[j];
+        if (A_out) A_out[row0 * r + i] = v[j] * ilam[cc];  // same element when A_out = A (lda = r)
+        const float2 x = split_ff(v[j]);
+        const float p = __fmul_rn(x.x, sch[cc]);
+        const float rest = __fmaf_rn(x.x, scl[cc], __fmaf_rn(x.y, sch[cc], __fmaf_rn(x.x, sch[cc], -p)));
+        const float h = __fadd_rn(p, rest);
+        xs[rb[j] * ld + ipos[cc]] = make_float2(h, __fsub_rn(rest, __fsub_rn(h, p)));
+      }
     }
     __syncthreads();
     if (threadIdx.x < rows) {
@@ -1129,24 +1166,32 @@ __global__ void __launch_bounds__(kRowThreads) k_lev_rows_ffd(const double* A, i
       const int64_t row = row0 + threadIdx.x;
       double l = 0.0;
       if (kind == 0) {
+        const float4* b4 = reinterpret_cast<const float4*>(b);
         float lh = 0.f, ll = 0.f;
-        for (int c = 0; c < k; ++c) {
+        for (int c2 = 0; c2 < k; ++c2) {
+          const float4* f4 = reinterpret_cast<const float4*>(Ff + c2 * r4);
           float th = 0.f, tl = 0.f;
-          for (int u = 0; u <= c; ++u) {
-            const float2 bu = b[u];
-            ff_fma(Fh[c * r + u], Fl[c * r + u], bu.x, bu.y, th, tl);
+          for (int u = 0; u <= c2; u += 4) {  // F(c2, u') = 0 for u' > c2
+            const float4 f0 = f4[u >> 1], f1 = f4[(u >> 1) + 1];
+            const float4 x0 = b4[u >> 1], x1 = b4[(u >> 1) + 1];
+            ff_fma(f0.x, f0.y, x0.x, x0.y, th, tl);
+            ff_fma(f0.z, f0.w, x0.z, x0.w, th, tl);
+            ff_fma(f1.x, f1.y, x1.x, x1.y, th, tl);
+            ff_fma(f1.z, f1.w, x1.z, x1.w, th, tl);
           }
-          float s, e;
-          two_sum(th, tl, s, e);
-          ff_fma(s, e, s, e, lh, ll);
+          float s2, e2;
+          two_sum(th, tl, s2, e2);
+          ff_fma(s2, e2, s2, e2, lh, ll);
         }
-        l = (double)lh + (double)ll;
+        l = f2d_exact(lh) + f2d_exact(ll);
       } else {
-        for (int c = 0; c < r; ++c) {
+        for (int c2 = 0; c2 < r; ++c2) {
           double t = 0.0;
-          for (int u = 0; u < r; ++u)
-            t = fma((double)Fh[c * r + u] + (double)Fl[c * r + u], (double)b[u].x + (double)b[u].y, t);
-          l = fma((double)b[c].x + (double)b[c].y, t, l);
+          for (int u = 0; u < r; ++u) {
+            const float2 fu = Ff[c2 * r4 + u];
+            t = fma((double)fu.x + (double)fu.y, (double)b[u].x + (double)b[u].y, t);
+          }
+          l = fma((double)b[c2].x + (double)b[c2].y, t, l);
         }
       }
       if (lev) lev[row] = l;
@@ -1157,12 +1202,6 @@ __global__ void __launch_bounds__(kRowThreads) k_lev_rows_ffd(const double* A, i
         q[row] = qi;
         my_max = qi > my_max ? qi : my_max;
         my_nz += qi > 0;
-      }
-    }
-    if (A_out) {
-      for (int i = threadIdx.x; i < rows * r; i += kRowThreads) {
-        const int rr = i / r, c = i - rr * r;
-        A_out[row0 * r + i] = A[(row0 + rr) * lda + c] * ilam[c];
       }
     }
   }
@@ -1217,6 +1256,8 @@ int gram_rows(const FT* A, int64_t n, int r, double* G, const BlockSums& S, cuda
     return CPA_OK;
   }
   if (n >= kManyRows) {  // FP64 rows of a many-row factor: float pairs on the FP32 pipe
+    if (status && r <= kGramStreamFP64MaxRank && ((uintptr_t)A & 15u) == 0 && gram_stream_fp64())
+      return gram_rows_stream(reinterpret_cast<const double*>(A), n, r, lda, G, S, status, st);
     const unsigned grid = grid_for(kGramRowsFF);
     const size_t smem = sizeof(float2) * kGramRowsFF * r;
     if (np <= kGramMaxThreads)
@@ -1286,9 +1327,10 @@ int lev_rows(const FT* A, int64_t n, int r, const SmallFactor* f, double* lev, u
       k_lev_rows_ff<<<grid, kRowThreads, bytes(r), st>>>(reinterpret_cast<const float*>(A), n, r, lda, f, lev, q,
                                                          info, reinterpret_cast<float*>(A_out));
     } else {
-      auto bytes = [](int rr) {
-        return sizeof(double) * (size_t)rr + sizeof(float) * ((size_t)2 * rr * rr + 2 * rr) +
-               sizeof(float2) * (size_t)kRowThreads * (rr | 1);
+      auto bytes = [](int rr) {  // F (r x r4 pairs), rows (kRowThreads x (r4 + 2) pairs), 1 / lambda, scales
+        const size_t r4 = (size_t)((rr + 3) & ~3);
+        return sizeof(float2) * ((size_t)rr * r4 + (size_t)kRowThreads * (r4 + 2)) + sizeof(double) * rr +
+               sizeof(float) * 2 * rr;
       };
       static std::atomic<unsigned long long> attr{0};
       CPA_CUDA_TRY(set_attr_once(attr, [&] {

@@ -86,6 +86,13 @@ bool gram_tensor_cores();
 constexpr int kGramStreamMaxRank = 32;
 int gram_rows_stream(const float* A, int64_t n, int r, int lda, double* G, const BlockSums& S, int* status,
                      cudaStream_t st);
+// The FP64 refresh's Gram of many rows, in float pairs on the FP32 pipe with the same
+// streaming (about 2^-44 relative), r <= kGramStreamFP64MaxRank; CPA_GRAM_STREAM_FP64=0
+// takes the one-pair-per-thread float-pair kernel instead.
+bool gram_stream_fp64();
+constexpr int kGramStreamFP64MaxRank = 28;
+int gram_rows_stream(const double* A, int64_t n, int r, int lda, double* G, const BlockSums& S, int* status,
+                     cudaStream_t st);
 
 
 // The rows can be streamed by the bulk copies of the tensor-core kernels: a 16-byte

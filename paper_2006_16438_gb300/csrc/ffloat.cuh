@@ -17,15 +17,29 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
 }
 
-// (hi, lo) += (ah + al) (bh + bl), the product's al*bl term dropped (below 2^-46).
+// (hi, lo) += (ah + al) (bh + bl), the product's al*bl term dropped (below 2^-46): the
+// rounding error of ah*bh (exact by the FMA) and the cross terms folded into it by two
+// more FMAs, TwoSum of the running high part, twelve FP32 instructions in all.
 __device__ __forceinline__ void ff_fma(float ah, float al, float bh, float bl, float& hi, float& lo) {
   const float p = __fmul_rn(ah, bh);
-  const float e = __fmaf_rn(ah, bh, -p);
-  const float cross = __fmaf_rn(ah, bl, __fmul_rn(al, bh));
+  const float low = __fmaf_rn(ah, bl, __fmaf_rn(al, bh, __fmaf_rn(ah, bh, -p)));
   float s, t;
   two_sum(hi, p, s, t);
   hi = s;
-  lo = __fadd_rn(lo, __fadd_rn(t, __fadd_rn(e, cross)));
+  lo = __fadd_rn(lo, __fadd_rn(t, low));
+}
+
+// The FP64 value of a float by integer operations (exact; the FP32-to-FP64 conversion
+// issues on the FP64 pipe): sign, exponent rebiased by 1023 - 127, significand moved
+// up by 29 bits.  Zeros are built the same way; subnormals, infinities and NaNs take
+// the conversion.
+__device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned mag = u & 0x7fffffffu;
+  if (mag == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+  const unsigned e = mag >> 23;
+  if (e == 0u || e == 255u) return (double)f;
+  return __hiloint2double((int)((u & 0x80000000u) | ((mag >> 3) + (896u << 20))), (int)(u << 29));
 }
 
 // (ah + al)(bh + bl) as a normalised pair (al*bl dropped).
@@ -45,33 +59,34 @@ __device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
   return make_float2(h, __fsub_rn(e, __fsub_rn(h, s)));
 }
 
-// Splits an FP64 value into floats hi + lo with integer operations only (a conversion
-// or an FP64 subtraction would issue on the FP64 pipe): hi's bits are the sign, the
-// rebiased exponent and the top 23 stored mantissa bits of v; lo is the remaining 29
-// mantissa bits, scaled by 2^(E - 1075) and normalised to a float by their leading one
-// (its lowest bits dropped when there are more than 24: 2^-47 relative to v).  Values
-// whose hi or lo falls outside FP32's normal range (zero, magnitudes below about 2^-97
-// or from 2^128) take the conversions.
+// Splits an FP64 value into floats hi + lo without the FP64 pipe (a conversion or an
+// FP64 subtraction issues there, and a rarely taken branch to one is still issued,
+// predicated off, for every element): hi's bits are the sign, the rebiased exponent
+// and the top 23 stored mantissa bits of v; lo is the remaining 29 mantissa bits as an
+// integer, rounded to a float by the integer-to-float conversion (2^-48 relative to v)
+// and scaled by 2^(E - 1075) with an integer add to its exponent field.  Outside FP32's
+// normal range the pair saturates: |v| < 2^-126 gives (0, 0), a lo below 2^-126 gives
+// lo = 0 (so the 2^-48 holds for |v| >= 2^-97), |v| >= 2^128 gives (+-inf, 0) and a NaN
+// (NaN, 0).
 __device__ __forceinline__ float2 split_ff(double v) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(v);
   const unsigned hi32 = (unsigned)(b >> 32);
   const unsigned sign = hi32 & 0x80000000u;
   const int E = (int)((hi32 >> 20) & 0x7ffu);
   const int fe = E - 896;  // FP32 exponent field of hi
+  unsigned hb = sign | ((unsigned)fe << 23) | ((unsigned)(b >> 29) & 0x7fffffu);
   const unsigned low = (unsigned)b & 0x1fffffffu;  // v - hi = low * 2^(E - 1075)
-  const int top = low ? 31 - __clz(low) : 0;       // position of lo's leading one (0..28)
-  const int le = E - 1075 + top + 127;             // FP32 exponent field of lo
-  if (fe >= 1 && fe <= 254 && (!low || le >= 1)) {
-    const float h = __uint_as_float(sign | ((unsigned)fe << 23) | ((unsigned)(b >> 29) & 0x7fffffu));
-    float l = 0.f;
-    if (low) {
-      const unsigned m = top >= 23 ? (low >> (top - 23)) : (low << (23 - top));
-      l = __uint_as_float(sign | ((unsigned)le << 23) | (m & 0x7fffffu));
-    }
-    return make_float2(h, l);
+  const unsigned lf = __float_as_uint(__uint2float_rn(low));
+  const int le = (int)(lf >> 23) + E - 1075;       // FP32 exponent field of lo
+  unsigned lb = low && le >= 1 ? sign | (lf + ((unsigned)(E - 1075) << 23)) : 0u;
+  if (fe < 1) {
+    hb = sign;
+    lb = 0u;
+  } else if (fe > 254) {
+    hb = sign | (E == 2047 && (b << 12) ? 0x7fc00000u : 0x7f800000u);
+    lb = 0u;
   }
-  const double vh = __longlong_as_double((long long)(b & ~((1ull << 29) - 1)));
-  return make_float2((float)vh, (float)(v - vh));
+  return make_float2(__uint_as_float(hb), __uint_as_float(lb));
 }
 
 }  // namespace cpa

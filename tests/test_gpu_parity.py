@@ -60,6 +60,27 @@ def test_leverage_vs_oracle(n, r):
         assert relerr(lev_gpu.cpu().numpy(), lev_ref) < 1e-11
 
 
+# From 65,536 rows on the Gram and the row forms run in float pairs on the FP32 pipe:
+# the streaming Gram (r <= 28, tiles of 16 rows, ragged tails; 4 x 4 blocks for r = 1
+# and 8, 5 x 5 with two rows per pass for r = 25) and the one-pair-per-thread kernel
+# (CPA_GRAM_STREAM_FP64=0, and r = 29, 32, 40), each checked against the oracle's QR
+# leverage and for bit-identical reruns.
+@pytest.mark.parametrize("stream_gram", ["1", "0"])
+@pytest.mark.parametrize("n,r", [(65536, 1), (70001, 8), (100003, 25), (70003, 28), (81920, 29), (66001, 32),
+                                 (70000, 40)])
+def test_leverage_many_rows_vs_oracle(n, r, stream_gram, monkeypatch):
+    monkeypatch.setenv("CPA_GRAM_STREAM_FP64", stream_gram)
+    g = np.random.default_rng(n + r)
+    A = g.standard_normal((n, r)) * np.exp(0.5 * g.standard_normal(r))
+    A[: n // 9] *= 7.0  # a block of heavy rows
+    lev_gpu, warn = cpa.cpa_leverage(cu(A))
+    lev_ref, rank = oracle.leverage(A)
+    assert warn == 0 and rank == r
+    assert relerr(lev_gpu.cpu().numpy(), lev_ref) < 1e-11
+    lev_again, _ = cpa.cpa_leverage(cu(A))
+    assert torch.equal(lev_gpu, lev_again)
+
+
 def test_leverage_rank_deficient():
     g = np.random.default_rng(2)
     B = g.standard_normal((40, 3))
