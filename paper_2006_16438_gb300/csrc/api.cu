@@ -543,7 +543,8 @@ struct Plan {
                                             nullptr, 0, MB.status));
       else
         CPA_TRY(refresh_distribution<double>(static_cast<double*>(Fm[m]), X->dims[m], r, Cm[m], info + m,
-                                             Pm[m], GA, sums_lev, flev, warn, scan_ws, false, nullptr, st, dist));
+                                             Pm[m], GA, sums_lev, flev, warn, scan_ws, false, nullptr, st, dist,
+                                             nullptr, 0, MB.status));
     }
     return CPA_OK;
   }

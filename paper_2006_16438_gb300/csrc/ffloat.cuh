@@ -29,34 +29,24 @@ __device__ __forceinline__ void ff_fma(float ah, float al, float bh, float bl, f
   lo = __fadd_rn(lo, __fadd_rn(t, low));
 }
 
-// The FP64 value of a float by integer operations (exact; the FP32-to-FP64 conversion
-// issues on the FP64 pipe): sign, exponent rebiased by 1023 - 127, significand moved
-// up by 29 bits.  Zeros are built the same way; subnormals, infinities and NaNs take
-// the conversion.
+// The FP64 value of a float by integer operations only (exact; the FP32-to-FP64
+// conversion issues on the FP64 pipe, and a rarely taken branch to it is still issued,
+// predicated off, on every call): sign, exponent rebiased by 1023 - 127, significand
+// moved up by 29 bits; infinities and NaNs keep an all-ones exponent, and a subnormal
+// m 2^-149 is normalised by its leading one.
 __device__ __forceinline__ double f2d_exact(float f) {
   const unsigned u = __float_as_uint(f);
-  const unsigned mag = u & 0x7fffffffu;
-  if (mag == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+  const unsigned sign = u & 0x80000000u, mag = u & 0x7fffffffu;
   const unsigned e = mag >> 23;
-  if (e == 0u || e == 255u) return (double)f;
-  return __hiloint2double((int)((u & 0x80000000u) | ((mag >> 3) + (896u << 20))), (int)(u << 29));
-}
-
-// (ah + al)(bh + bl) as a normalised pair (al*bl dropped).
-__device__ __forceinline__ float2 ff_mul(float2 a, float2 b) {
-  const float p = __fmul_rn(a.x, b.x);
-  const float e = __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, __fmaf_rn(a.x, b.x, -p)));
-  const float s = __fadd_rn(p, e);
-  return make_float2(s, __fsub_rn(e, __fsub_rn(s, p)));
-}
-
-// (ah + al) + (bh + bl) as a normalised pair.
-__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
-  float s, e;
-  two_sum(a.x, b.x, s, e);
-  e = __fadd_rn(e, __fadd_rn(a.y, b.y));
-  const float h = __fadd_rn(s, e);
-  return make_float2(h, __fsub_rn(e, __fsub_rn(h, s)));
+  unsigned hi = sign | ((mag >> 3) + (896u << 20)), lo = u << 29;
+  if (e == 255u) hi = sign | 0x7ff00000u | ((mag & 0x7fffffu) >> 3);
+  if (e == 0u) {
+    const int k = mag ? 31 - __clz(mag) : 0;  // leading one of the subnormal's significand
+    const unsigned long long m = ((unsigned long long)mag << (52 - k)) & ((1ull << 52) - 1);
+    hi = mag ? sign | ((unsigned)(k + 874) << 20) | (unsigned)(m >> 32) : sign;
+    lo = mag ? (unsigned)m : 0u;
+  }
+  return __hiloint2double((int)hi, (int)lo);
 }
 
 // Splits an FP64 value into floats hi + lo without the FP64 pipe (a conversion or an
