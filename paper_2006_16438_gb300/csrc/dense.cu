@@ -254,43 +254,51 @@ __device__ __noinline__ void jacobi_eigen_block(double* a, double* v, int r, int
   }
 }
 
-// 1/sqrt(d) for d > 0 in FP64: an FP32 seed y0 = rsqrt(f), f the upper word of d moved
-// into FP32 by integer operations (no FP64 conversion on the chain), e = 1 - d y0^2
-// (|e| < 2^-18), then y0 (1 + e/2 + 3 e^2 / 8) (the binomial series of (1 - e)^(-1/2)
-// to second order): relative error about 5 e^3 / 16 < 2^-55 before rounding.  GB300
-// FP64 division and square root cost hundreds of cycles each (every FP64 warp
-// instruction issues over 64 cycles), so the factorisation keeps them off its chain.
+// 1/sqrt(d) for d > 0 in FP64, without a branch (so the compiler can overlap it with
+// the pivot search): d = m 4^k with m in [1, 4) by integer operations, an FP32 seed
+// y0 = rsqrt(f) from m's exponent and upper 20 significand bits, e = 1 - m y0^2
+// (|e| < 2^-18), y0 (1 + e/2 + 3 e^2 / 8) (the binomial series of (1 - e)^(-1/2) to
+// second order: relative error about 5 e^3 / 16 < 2^-55 before rounding), then the
+// exponent lowered by k.  The power-of-4 scaling is exact, so the result is the one the
+// same steps give on d itself.  GB300 FP64 division and square root cost hundreds of
+// cycles each (every FP64 warp instruction issues over 64 cycles), so the
+// factorisation keeps them off its chain.  d must be a positive normal number
+// (anything else gives 0).
 __device__ __forceinline__ double rsqrt_newton(double d) {
-  const int hi = __double2hiint(d);
-  const int ex = ((hi >> 20) & 0x7ff) - 1023;
-  if (ex < -125 || ex > 125) return rsqrt(d);  // outside the FP32 normal range
-  const float f = __int_as_float(((ex + 127) << 23) | ((hi & 0xfffff) << 3));
+  const unsigned long long ub = (unsigned long long)__double_as_longlong(d);
+  const int E = (int)((ub >> 52) & 0x7ffu);
+  const int ex = E - 1023, k = ex >> 1, em = ex - 2 * k;  // d = m 4^k, m = 1.f 2^em, em in {0, 1}
+  const double m = __longlong_as_double((long long)((ub & 0x000fffffffffffffull) | ((unsigned long long)(1023 + em) << 52)));
+  const float f = __int_as_float(((em + 127) << 23) | (int)((ub >> 29) & 0x7ffff8u));
   const int yb = __float_as_int(rsqrtf(f));
   const int ye = ((yb >> 23) & 0xff) - 127;
   const double y0 = __hiloint2double(((ye + 1023) << 20) | ((yb & 0x7fffff) >> 3), (yb & 7) << 29);
-  const double e = fma(-d, y0 * y0, 1.0);
-  return fma(y0, e * fma(e, 0.375, 0.5), y0);
+  const double e = fma(-m, y0 * y0, 1.0);
+  const double y = fma(y0, e * fma(e, 0.375, 0.5), y0);  // 1 / sqrt(m), in (0.5, 1]
+  const long long r = __double_as_longlong(y) - (long long)k * (1ll << 52);
+  return E >= 1 && E <= 2046 && !(ub >> 63) ? __longlong_as_double(r) : 0.0;
 }
 
-// 1/d for d > 0 in FP64 (0 for d <= 0 or not finite): an FP32 seed f from the upper
-// word of d (its exponent and 20 significand bits moved by integer operations, so no
-// FP64 conversion is on the chain),
-// x = the approximate FP32 reciprocal of f, e = 1 - d x (|e| < 2^-19), then
-// x (1 + e + e^2) (the truncated series of 1/(1 - e)): relative error about e^3 < 2^-56
-// before rounding.
+// 1/d for d > 0 in FP64 (0 for d <= 0, not finite, subnormal or from 2^1022 on),
+// without a branch: d = m 2^ex with m in [1, 2) by integer operations, an FP32 seed
+// from m's upper 20 significand bits, x = its approximate FP32 reciprocal, e = 1 - m x
+// (|e| < 2^-19), x (1 + e + e^2) (the truncated series of 1/(1 - e): relative error
+// about e^3 < 2^-56 before rounding), then the exponent lowered by ex.  The
+// power-of-2 scaling is exact, so the result is the one the same steps give on d.
 __device__ __forceinline__ double rcp_newton(double d) {
-  if (!pos_finite(d)) return 0.0;  // zero, negative or not finite (no division for those lanes)
-  const int hi = __double2hiint(d);
-  const int ex = ((hi >> 20) & 0x7ff) - 1023;
-  if (ex < -125 || ex > 125) return 1.0 / d;  // outside the FP32 normal range
-  const float f = __int_as_float(((ex + 127) << 23) | ((hi & 0xfffff) << 3));
+  const unsigned long long ub = (unsigned long long)__double_as_longlong(d);
+  const int E = (int)((ub >> 52) & 0xfffu);  // with the sign bit: negative d gives E > 2047
+  const double m = __longlong_as_double((long long)((ub & 0x000fffffffffffffull) | 0x3ff0000000000000ull));
+  const float f = __int_as_float((127 << 23) | (int)((ub >> 29) & 0x7ffff8u));
   float xf;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(xf) : "f"(f));  // the seed needs no correct rounding
   const int xb = __float_as_int(xf);
   const int xe = ((xb >> 23) & 0xff) - 127;
   const double x = __hiloint2double(((xe + 1023) << 20) | ((xb & 0x7fffff) >> 3), (xb & 7) << 29);
-  const double e = fma(-d, x, 1.0);
-  return fma(x, fma(e, e, e), x);
+  const double e = fma(-m, x, 1.0);
+  const double y = fma(x, fma(e, e, e), x);  // 1 / m, in (0.5, 1]
+  const long long r = __double_as_longlong(y) - (long long)(E - 1023) * (1ll << 52);
+  return E >= 1 && E <= 2044 ? __longlong_as_double(r) : 0.0;
 }
 
 // Order-preserving 32-bit key of a double for the pivot search: the upper word of a
