@@ -16,6 +16,10 @@
 // partials are added in warp order, the blocks' partials in block order (a fixed grid):
 // the result is reproducible bit for bit.  Every wait is bounded: on a timeout the
 // status word records CPA_ERR_CUDA and the warp drains its copies (bounded again).
+//
+// The second kernel of this file, k_gram_rows_ffs, streams the rows of an FP64 factor
+// the same way for the FP64 refresh and forms G in float-pair arithmetic (about 2^-44
+// relative), which is instruction bound rather than HBM bound on this part.
 #include "dense.cuh"
 #include "ffloat.cuh"
 #include "tc.cuh"
